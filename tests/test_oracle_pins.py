@@ -1,0 +1,385 @@
+"""Pins of the FP64 oracle against facts fixed outside it.
+
+Each test checks the oracle against something other than its own formulas:
+an independent library (cuRAND's host Philox, scipy constants and
+quadrature), a closed form, a brute-force ray tracer of the eikonal
+equation, an invariant, or a geometric brute force.  Each is chosen so that a
+plausible slip (a dropped factor, a wrong sign, a transposed operand) fails.
+"""
+import ctypes
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.constants as SC
+from scipy import integrate, stats
+
+import oracle as O
+from paper_2309_15861_gb300 import inputs as I
+from tests import _eikonal
+
+C_M_NS = SC.c * 1e-9
+
+
+# ---------------------------------------------------------------- Philox
+def _curand_host():
+    for path in ("/usr/local/cuda/lib64/libcurand.so", "libcurand.so", "libcurand.so.10"):
+        try:
+            return ctypes.CDLL(path)
+        except OSError:
+            continue
+    return None
+
+
+@pytest.mark.parametrize("seed", [1, 0xDEADBEEF, 0x123456789ABCDEF])
+def test_philox_matches_curand_host_generator(seed):
+    """cuRAND's host PHILOX4_32_10 generator emits block j of its stream from
+    counter (0, 0, j, 0) and key (seed lo, seed hi); the oracle's Philox must
+    reproduce that stream bit for bit."""
+    cr = _curand_host()
+    if cr is None:
+        pytest.skip("libcurand not available")
+    gen = ctypes.c_void_p()
+    assert cr.curandCreateGeneratorHost(ctypes.byref(gen), 161) == 0  # PHILOX4_32_10
+    try:
+        assert cr.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed)) == 0
+        n = 4 * 512
+        buf = np.zeros(n, dtype=np.uint32)
+        assert cr.curandGenerate(gen, ctypes.c_void_p(buf.ctypes.data), ctypes.c_size_t(n)) == 0
+    finally:
+        cr.curandDestroyGenerator(gen)
+    key = [seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF]
+    ours = np.concatenate([O.philox([0, 0, j, 0], key) for j in range(n // 4)])
+    np.testing.assert_array_equal(ours, buf)
+
+
+def test_philox_uses_every_counter_word_and_key_word():
+    base = O.philox([1, 2, 3, 4], [5, 6])
+    for i in range(4):
+        c = [1, 2, 3, 4]
+        c[i] ^= 1
+        assert not np.array_equal(O.philox(c, [5, 6]), base)
+    for i in range(2):
+        k = [5, 6]
+        k[i] ^= 1
+        assert not np.array_equal(O.philox([1, 2, 3, 4], k), base)
+
+
+def test_u01_mapping_is_exact_in_binary32():
+    for x in [0, 1, 255, 256, 0x7FFFFFFF, 0xFFFFFFFF, 0x12345678]:
+        u = O.u01(x)
+        assert 0.0 < u < 1.0
+        assert float(np.float32(u)) == u
+        assert u == ((x >> 9) + 0.5) / 2 ** 23
+
+
+# ---------------------------------------------------------------- yield
+def _one_seg(eps=1e-5, z=10000.0, L=1.0, charge=-1, d=(0.0, 0.0, -1.0), dE=0.0):
+    s = np.zeros(1, dtype=I.SEG_DTYPE)
+    s["z"] = z
+    s["dx"], s["dy"], s["dz"] = d
+    s["L"] = L
+    s["eps"] = eps
+    s["charge"] = charge
+    s["dE"] = dE
+    return s[0]
+
+
+def test_frank_tamm_yield_against_codata_prefactor_and_quadrature():
+    """N = mu_r pi z^2 e^2 / (h eps0 c0) int dlambda/lambda^2 (1 - 1/(beta n)^2) L
+    with CODATA constants from scipy and the wavelength integral done by
+    quadrature; catches a wrong prefactor, band factor, charge or length."""
+    atm = I.atmosphere_single_exponential()
+    par = I.Params(lambda1=300.0, lambda2=600.0, bunch=1.0)
+    pref = math.pi * SC.e ** 2 / (SC.h * SC.epsilon_0 * SC.c)
+    lam_int, _ = integrate.quad(lambda lam: 1.0 / lam ** 2, 300e-9, 600e-9)
+    for charge, L, eps, z in [(-1, 1.0, 1e-5, 10000.0), (2, 3.5, 2e-6, 4000.0),
+                              (1, 0.25, 1e-4, 3000.0)]:
+        seg = _one_seg(eps=eps, z=z, L=L, charge=charge)
+        y = O.yield_of(seg, atm, par)
+        h_mid = z - 0.5 * L
+        n = 1.0 + 2.9e-4 * math.exp(-h_mid / 8400.0)
+        beta = 1.0 - float(np.float32(eps))
+        want = pref * charge ** 2 * lam_int * (1.0 - 1.0 / (beta * n) ** 2) * L
+        assert y["Nc"] == pytest.approx(want, rel=2e-9)
+        assert y["cos_tc"] == pytest.approx(1.0 / (beta * n), rel=1e-14)
+        assert y["n_c"] == math.ceil(want)
+        assert y["w_c"] * y["n_c"] == pytest.approx(y["Nc"], rel=1e-14)
+    # 300-600 nm: 2 pi alpha (1/l1 - 1/l2) = 76417.7 photons/m at sin^2 = 1
+    assert 2 * math.pi * SC.alpha * (1 / 300e-9 - 1 / 600e-9) == pytest.approx(76417.7, abs=0.1)
+
+
+def test_cherenkov_threshold_and_beta_one_limit():
+    atm = I.atmosphere_single_exponential()
+    par = I.Params(bunch=1.0)
+    z = 10000.0
+    n = 1.0 + 2.9e-4 * math.exp(-(z - 0.5) / 8400.0)
+    eps_thr = 1.0 - 1.0 / n
+    below = O.yield_of(_one_seg(eps=float(np.float32(eps_thr * 1.001)), z=z), atm, par)
+    above = O.yield_of(_one_seg(eps=float(np.float32(eps_thr * 0.999)), z=z), atm, par)
+    assert below["Nc"] == 0.0 and below["n_c"] == 0
+    assert above["Nc"] > 0 and above["n_c"] >= 1
+    lim = O.yield_of(_one_seg(eps=0.0, z=z), atm, par)
+    assert lim["sin_tc"] ** 2 == pytest.approx(1.0 - 1.0 / n ** 2, rel=1e-12)
+    assert O.yield_of(_one_seg(charge=0), atm, par)["n_c"] == 0
+
+
+def test_bunching_and_fluorescence_yield():
+    atm = I.atmosphere_layered()
+    par = I.Params(bunch=5.0, fluor_yield=5.0)
+    seg = _one_seg(eps=1e-5, z=8000.0, L=4.0, dE=1.7)
+    y = O.yield_of(seg, atm, par)
+    assert y["n_c"] == math.ceil(y["Nc"] / 5.0) and y["w_c"] <= 5.0 + 1e-12
+    assert y["Nf"] == pytest.approx(5.0 * float(np.float32(1.7)), rel=1e-15)
+    assert y["n_f"] == math.ceil(y["Nf"] / 5.0)
+    assert y["w_f"] * y["n_f"] == pytest.approx(y["Nf"], rel=1e-14)
+
+
+def test_wavelengths_follow_one_over_lambda_squared():
+    atm = I.atmosphere_single_exponential()
+    par = I.Params(lambda1=300.0, lambda2=600.0, bunch=1.0)
+    seg = _one_seg(eps=0.0, z=6000.0, L=20.0)
+    nb = int(O.yield_of(seg, atm, par)["n_c"])
+    lam = np.array([O.photon(seg, 7, k, atm, par)[3] for k in range(min(nb, 4000))])
+    cdf = lambda l: (1 / 300.0 - 1 / l) / (1 / 300.0 - 1 / 600.0)
+    assert stats.kstest(lam, cdf).pvalue > 1e-3
+    assert lam.min() >= 300.0 and lam.max() <= 600.0
+
+
+# ---------------------------------------------------------------- cone
+def test_rotation_matrix_properties():
+    rng = np.random.default_rng(3)
+    dirs = list(rng.normal(size=(50, 3))) + [np.array([0, 0, -1.0]), np.array([0, 0, 1.0]),
+                                             np.array([1.0, 0, 0]), np.array([0, 1e-9, 1.0])]
+    for d in dirs:
+        d = d / np.linalg.norm(d)
+        M = O.rotation(d)
+        np.testing.assert_allclose(M @ M.T, np.eye(3), atol=1e-13)
+        assert np.linalg.det(M) == pytest.approx(1.0, abs=1e-13)
+        np.testing.assert_allclose(M @ np.array([0, 0, -1.0]), d, atol=1e-9)
+        np.testing.assert_allclose(M, M.T, atol=1e-15)          # half turn: symmetric
+
+
+def test_cone_angle_and_azimuth_are_preserved():
+    """Every photon sits at theta_c from the track; the azimuth difference of
+    two photons of one step equals 2 pi (u2 - u2') from their Philox words."""
+    atm = I.atmosphere_layered()
+    par = I.Params(bunch=1.0)
+    rng = np.random.default_rng(5)
+    for t in range(10):
+        d = rng.normal(size=3)
+        d[2] = -abs(d[2]) - 0.3
+        d /= np.linalg.norm(d)
+        seg = _one_seg(eps=2e-6, z=7000.0, L=2.0, d=tuple(d.astype(np.float32)))
+        dd = np.array([seg["dx"], seg["dy"], seg["dz"]], dtype=np.float64)
+        dd /= np.linalg.norm(dd)
+        y = O.yield_of(seg, atm, par)
+        e1 = np.cross(dd, [0.3, 0.5, 0.8]); e1 /= np.linalg.norm(e1)
+        e2 = np.cross(e1, dd)     # (e1, e2, -d) right-handed, as (x, y, z) about -z
+        az, u2 = [], []
+        for k in range(8):
+            r_e, dg, t_e, lam, w, proc = O.photon(seg, 100 + t, k, atm, par)
+            assert proc == 0
+            assert np.linalg.norm(dg) == pytest.approx(1.0, abs=1e-14)
+            assert math.acos(np.clip(dg @ dd, -1, 1)) == pytest.approx(math.acos(y["cos_tc"]), abs=1e-10)
+            az.append(math.atan2(dg @ e2, dg @ e1))
+            x = O.philox([100 + t, 0, k, 0], [1, 0])
+            u2.append(O.u01(x[2]))
+            ell = np.linalg.norm(r_e - np.array([0, 0, 7000.0]))
+            assert t_e == pytest.approx(ell / ((1 - float(np.float32(2e-6))) * C_M_NS), rel=1e-12)
+        for k in range(1, 8):
+            da = (az[k] - az[0]) - 2 * math.pi * (u2[k] - u2[0])
+            da = (da + math.pi) % (2 * math.pi) - math.pi
+            assert abs(da) < 1e-9
+
+
+def test_fluorescence_is_isotropic():
+    atm = I.atmosphere_layered()
+    par = I.Params(bunch=1.0, fluor_yield=50.0)
+    seg = _one_seg(eps=0.5, z=9000.0, L=2.0, dE=80.0)      # below Cherenkov threshold
+    y = O.yield_of(seg, atm, par)
+    assert y["n_c"] == 0 and y["n_f"] == 4000
+    dz = np.array([O.photon(seg, 3, k, atm, par)[1][2] for k in range(4000)])
+    assert stats.kstest(dz, "uniform", args=(-1, 2)).pvalue > 1e-3
+    lam = np.array([O.photon(seg, 3, k, atm, par)[3] for k in range(0, 4000, 4)])
+    assert stats.kstest(lam, "uniform", args=(340, 110)).pvalue > 1e-3
+
+
+# ---------------------------------------------------------------- propagation
+def _dirs(rng, n, max_zen_deg):
+    zen = np.radians(rng.uniform(0, max_zen_deg, n))
+    az = rng.uniform(0, 2 * np.pi, n)
+    return np.stack([np.sin(zen) * np.cos(az), np.sin(zen) * np.sin(az), -np.cos(zen)], 1)
+
+
+def test_straight_flat_single_exponential_closed_form():
+    """Refraction off, flat Earth, n - 1 = a e^{-h/H}: landing point, time and
+    optical depth have closed forms."""
+    atm = I.atmosphere_single_exponential(refraction=False, absorption=True)
+    a, H = 2.9e-4, 8400.0
+    rng = np.random.default_rng(11)
+    for d in _dirs(rng, 20, 70):
+        r_e = np.array([rng.uniform(-500, 500), rng.uniform(-500, 500), rng.uniform(3000, 30000)])
+        lam = rng.uniform(300, 600)
+        res = O.propagate(atm, r_e, d, t_e=5.0, lam=lam)
+        dz = abs(d[2])
+        dh = r_e[2] - atm.h_obs
+        P = r_e + d * dh / dz
+        np.testing.assert_allclose(res["P"], P, rtol=0, atol=1e-9)
+        np.testing.assert_allclose(res["dL"], d, atol=1e-14)
+        ex = math.exp(-atm.h_obs / H) - math.exp(-r_e[2] / H)
+        t = 5.0 + (dh + a * H * ex) / (C_M_NS * dz)
+        assert res["t"] == pytest.approx(t, rel=0, abs=1e-9)
+        tau = (I.RHO_SEA / atm.rho_ref) * H * ex / (atm.L0 * (lam / 400.0) ** 4 * dz)
+        assert res["tau"] == pytest.approx(tau, rel=1e-11)
+
+
+def test_straight_spherical_line_sphere_intersection():
+    atm = I.atmosphere_layered(refraction=False)
+    rng = np.random.default_rng(12)
+    r_obs = atm.R_E + atm.h_obs
+    for d in _dirs(rng, 12, 75):
+        r_e = np.array([rng.uniform(-3e4, 3e4), rng.uniform(-3e4, 3e4), rng.uniform(5000, 35000)])
+        res = O.propagate(atm, r_e, d, t_e=0.0, lam=450.0)
+        Rv = r_e + np.array([0, 0, atm.R_E])
+        b = -(Rv @ d)
+        s = b - math.sqrt(b * b - (Rv @ Rv - r_obs ** 2))
+        P = r_e + s * d
+        np.testing.assert_allclose(res["P"], P, atol=2e-6)
+        np.testing.assert_allclose(res["dL"], d, atol=1e-12)
+
+        def n_along(u):
+            p = r_e + u * d
+            h = np.linalg.norm(p + [0, 0, atm.R_E]) - atm.R_E
+            return 1.0 + atm.K * float(atm.density(h))
+        pts = sorted([u for u in np.linspace(0, s, 2) ])
+        Lopt, _ = integrate.quad(n_along, 0.0, s, epsabs=1e-9, epsrel=1e-13, limit=400)
+        assert res["t"] == pytest.approx(Lopt / C_M_NS, abs=2e-6)
+
+
+@pytest.mark.parametrize("spherical", [False, True])
+def test_refracted_rays_match_brute_force_eikonal(spherical):
+    atm = I.atmosphere_layered(spherical=spherical)
+    rng = np.random.default_rng(21 + spherical)
+    N = 12
+    d = _dirs(rng, N, 65)
+    r_e = np.stack([rng.uniform(-2e4, 2e4, N), rng.uniform(-2e4, 2e4, N),
+                    rng.uniform(4000, 16000, N)], 1)
+    P, D, Lopt, Ltau = _eikonal.trace(atm, r_e, d, ds=2.0)
+    for i in range(N):
+        res = O.propagate(atm, r_e[i], d[i], t_e=0.0, lam=400.0)
+        assert res["status"] == O.OR_TRACED
+        np.testing.assert_allclose(res["P"], P[i], atol=2e-4)
+        np.testing.assert_allclose(res["dL"], D[i], atol=1e-9)
+        # RK4 loses accuracy where grad n jumps at layer edges (~1e-5 m of
+        # optical path, not monotone in the step): 5e-4 ns = 0.15 mm
+        assert res["t"] == pytest.approx(Lopt[i] / C_M_NS, abs=5e-4)
+        assert res["tau"] == pytest.approx(Ltau[i] / atm.L0, rel=1e-6)
+
+
+def test_refraction_invariants_vertical_and_flat_limit():
+    atm = I.atmosphere_layered(spherical=False)
+    # vertical rays are not bent
+    res = O.propagate(atm, [12.5, -7.0, 15000.0], [0, 0, -1.0])
+    np.testing.assert_allclose(res["P"][:2], [12.5, -7.0], atol=1e-12)
+    # Snell: n sin(theta) is the same at emission and arrival
+    d = np.array([0.5, 0.2, -0.8]); d /= np.linalg.norm(d)
+    res = O.propagate(atm, [0, 0, 12000.0], d)
+    n_e = 1 + O.delta(atm, 12000.0)
+    assert res["n_obs"] * math.hypot(*res["dL"][:2]) == pytest.approx(n_e * math.hypot(*d[:2]), rel=1e-13)
+    # a spherical Earth of huge radius approaches the flat result
+    big = I.atmosphere_layered(spherical=True)
+    big.R_E = 1e13
+    flat = O.propagate(atm, [100.0, 50.0, 12000.0], d, lam=380.0)
+    sph = O.propagate(big, [100.0, 50.0, 12000.0], d, lam=380.0)
+    np.testing.assert_allclose(sph["P"], flat["P"], atol=1e-4)
+    # residual curvature: drop D^2 / 2R ~ 3e-6 m over D ~ 7.5 km -> 1e-5 ns
+    assert sph["t"] == pytest.approx(flat["t"], abs=5e-5)
+    assert sph["tau"] == pytest.approx(flat["tau"], rel=1e-7)
+
+
+def test_fermat_refracted_path_is_shortest_in_optical_length():
+    atm = I.atmosphere_layered(spherical=True)
+    rng = np.random.default_rng(31)
+    for d in _dirs(rng, 6, 70):
+        r_e = np.array([0.0, 0.0, rng.uniform(6000, 20000)])
+        res = O.propagate(atm, r_e, d)
+        P = res["P"]
+        chord = P - r_e
+        Ls = np.linalg.norm(chord)
+
+        def n_along(u):
+            p = r_e + u * chord / Ls
+            h = np.linalg.norm(p + [0, 0, atm.R_E]) - atm.R_E
+            return 1.0 + atm.K * float(atm.density(h))
+        Lchord, _ = integrate.quad(n_along, 0, Ls, epsabs=1e-10, epsrel=1e-14, limit=400,
+                                   points=None)
+        Lref = res["t"] * C_M_NS
+        assert Lref <= Lchord + 1e-7
+        assert Lchord - Lref < 1e-3 * Ls * 1e-3
+
+
+def test_escaped_and_turned_rays():
+    atm = I.atmosphere_layered(spherical=True)
+    assert O.propagate(atm, [0, 0, 9000.0], [0.3, 0, 0.95])["status"] == O.OR_ESCAPED
+    # almost horizontal at 30 km: misses the observation sphere
+    d = np.array([1.0, 0.0, -0.001]); d /= np.linalg.norm(d)
+    assert O.propagate(atm, [0, 0, 30000.0], d)["status"] == O.OR_TURNED
+    assert O.propagate(atm, [0, 0, 1500.0], [0, 0, -1.0])["status"] == O.OR_UNDER
+
+
+# ---------------------------------------------------------------- hit test
+def test_hit_decision_matches_brute_force_distance():
+    """Impact parameter from the oracle vs. the minimum distance found by
+    sampling points along the line."""
+    atm = I.atmosphere_single_exponential()
+    rng = np.random.default_rng(41)
+    tels = np.zeros(3, dtype=I.TEL_DTYPE)
+    tels["x"] = [0.0, 14.0, -9.0]
+    tels["y"] = [0.0, 3.0, 11.0]
+    tels["z"] = atm.h_obs
+    tels["R"] = [6.0, 4.0, 5.0]
+    segs = np.zeros(200, dtype=I.SEG_DTYPE)
+    segs["x"] = rng.uniform(-120, 120, 200)
+    segs["y"] = rng.uniform(-120, 120, 200)
+    segs["z"] = rng.uniform(4000, 7000, 200)
+    segs["dz"] = -1.0
+    segs["L"] = 1.0
+    segs["eps"] = 1e-5
+    segs["charge"] = -1
+    hits, counts, sums, st = O.trace(segs, atm, tels, I.Params(bunch=1.0))
+    assert len(hits) > 0
+    for h in hits[:50]:
+        r_e, dg, t_e, lam, w, _ = O.photon(segs[h["seg"]], h["seg"], h["k"], atm, I.Params(bunch=1.0))
+        res = O.propagate(atm, r_e, dg, t_e, lam)
+        T = tels[h["tel"]]
+        C3 = np.array([T["x"], T["y"], T["z"]], dtype=np.float64)
+        s = np.linspace(-40, 40, 400001)
+        pts = res["P"][None, :] + s[:, None] * res["dL"][None, :]
+        dmin = np.min(np.linalg.norm(pts - C3[None, :], axis=1))
+        assert dmin == pytest.approx(h["dperp"], abs=1e-6)
+        assert h["dperp"] < T["R"]
+    # the sorted list, the counts and the sums agree
+    assert np.all(np.diff(hits["tel"].astype(np.int64) * 10 ** 12 + hits["seg"] * 10 ** 4 + hits["k"]) > 0)
+    assert counts.sum() == len(hits)
+    for j in range(3):
+        assert sums[0, j] == pytest.approx(hits["weight"][hits["tel"] == j].sum(), rel=1e-14)
+
+
+# ---------------------------------------------------------------- inputs
+def test_shower_generator_distributions():
+    atm = I.atmosphere_layered()
+    s = I.segments_shower(200_000, atm, seed=3, zenith_deg=0.0)
+    assert s.dtype.itemsize == 64
+    r = np.hypot(s["x"], s["y"])
+    assert stats.kstest(r, "expon", args=(0, 80)).pvalue > 1e-4
+    nrm = np.sqrt(s["dx"].astype(np.float64) ** 2 + s["dy"] ** 2 + s["dz"] ** 2)
+    assert np.abs(nrm - 1).max() < 3e-7
+    assert (s["z"] > atm.h_obs).all()
+    X = atm.thickness(s["z"])
+    X_obs = float(atm.thickness(np.array([atm.h_obs]))[0])
+    g = stats.gamma(6, scale=70.0)                        # Gaisser-Hillas, Xmax 350, lambda 70
+    assert stats.kstest(X, lambda x: g.cdf(x) / g.cdf(X_obs)).pvalue > 1e-4
+    L = s["L"]
+    assert L.min() >= 0.5 and L.max() <= 5.0
