@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Throughput of the photon generation + propagation path on GB300.
+
+Metric: traced photon bunches (rays) per second, batched FP32 path, against
+the plain FP64 GPU path, at oracle tolerance.  One step = one call of the
+whole path (yield, generation, refracted propagation with absorption, hit
+test, sort, per-telescope counts and sums) over the 2e7-step 1 TeV vertical
+gamma shower (5-layer atmosphere, spherical Earth, absorption, bunch size 5,
+10 x 10 telescopes at 100 m).  Inputs are synthetic and seeded; the
+segment array (1.28 GB) is larger than L2, so no flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank traces its own shower (weak scaling) with
+no data-path collective; the timed region is bracketed by barriers and the
+maximum over ranks is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "traced photons/s, 1 GB300: batched FP32 vs plain FP64 at oracle tolerance"
+UNIT = "rays/s"
+
+# Algorithmic binary32 operations per unit of work, counted from the kernel
+# source (trace_kernels.cu): per quadrature node of the refracted spherical
+# integrand, per ray outside the nodes (Philox, cone, emission point,
+# vacuum line in FP32 pairs, landing point, arrival time, absorption) and
+# per candidate telescope.  MUFU (ex2, rsqrt, rcp, sincos) counted apart.
+OPS_NODE = 41
+MUFU_NODE = 5
+NODES_PER_CELL = 4
+OPS_RAY = 260
+MUFU_RAY = 6
+FP32_LANES_PER_SM = 128
+MUFU_LANES_PER_SM = 16
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(w, budget_s=12.0, block=256, seed=0):
+    """The FP64 oracle on contiguous blocks of the same workload (host cores)."""
+    import oracle as O
+    O.build()
+    rng = np.random.default_rng(seed)
+    n = len(w.segments)
+    starts = rng.permutation(n // block)
+    rays = 0
+    t0 = time.perf_counter()
+    blocks = 0
+    for b in starts:
+        lo = int(b) * block
+        _, _, _, st = O.trace(w.segments[lo:lo + block], w.atmosphere, w.telescopes, w.params,
+                              n_showers=w.n_showers, seg_base=lo)
+        rays += st["rays"]
+        blocks += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": rays / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{blocks} random blocks of {block} consecutive steps ({blocks * block} of {n} "
+                      f"steps, {rays} rays) of the same shower, {dt:.1f} s, FP64 oracle with OpenMP"}
+
+
+def reference_arm(args, rank):
+    """The oracle timed on the host cores, on bounded samples of the workload."""
+    if rank != 0:
+        return 0
+    from paper_2309_15861_gb300 import inputs as I
+    w = I.workload_shower_1tev(n=args.n_segs, seed=1)
+    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    vals = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(w, budget_s=per_step, seed=i)
+        if i >= args.warmup:
+            vals.append(r)
+    v = statistics.median([r["value"] for r in vals])
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "segments": len(w.segments), "telescopes": len(w.telescopes),
+                       "bunch": w.params.bunch},
+            "cpu_baseline": {"kind": "oracle", "cores": vals[0]["cores"], "sample": vals[0]["sample"],
+                             "value": v, "unit": UNIT},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-segs", type=int, default=20_000_000)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--cell-width", type=float, default=0.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local = _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        return reference_arm(args, rank)
+
+    import torch
+    import paper_2309_15861_gb300 as G
+    from paper_2309_15861_gb300 import build as B, inputs as I
+    B.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    t_gen = time.perf_counter()
+    w = I.workload_shower_1tev(n=args.n_segs, seed=1 + rank)
+    t_gen = time.perf_counter() - t_gen
+    ctx = G.Context(local)
+    extra = dict(use_graph=1, precision=args.precision, block=args.block, ctas_per_sm=args.ctas_per_sm,
+                 cell_width=args.cell_width)
+    ctx.setup(w, **extra)
+    dev = f"cuda:{local}"
+    segs = torch.from_numpy(w.segments.view(np.uint8).reshape(-1)).to(dev)
+    n = len(w.segments)
+    cap = max(1 << 20, n // 4)
+    hits = torch.empty(cap * 48, dtype=torch.uint8, device=dev)
+    counts = torch.zeros(len(w.telescopes), dtype=torch.int64, device=dev)
+    sums = torch.zeros(len(w.telescopes), dtype=torch.float64, device=dev)
+    code, nh, st = ctx.trace(segs, n, 1, hits, cap, counts, sums, raise_on_error=False)
+    if code == G.ERR_HIT_CAPACITY:
+        cap = int(nh * 1.25) + 1024
+        hits = torch.empty(cap * 48, dtype=torch.uint8, device=dev)
+        code, nh, st = ctx.trace(segs, n, 1, hits, cap, counts, sums)
+    for _ in range(args.warmup):
+        ctx.trace(segs, n, 1, hits, cap, counts, sums)
+    launches_per_step = None
+    # ---- timed region (device-resident inputs)
+    clocks = Clocks(local)
+    barrier()
+    clocks.start()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kms, sms = [], []
+    e0.record(s)
+    for _ in range(args.steps):
+        code, nh, st = ctx.trace(segs, n, 1, hits, cap, counts, sums)
+        a, b = ctx.last_timing()
+        kms.append(a)
+        sms.append(b)
+    e1.record(s)
+    torch.cuda.synchronize()
+    barrier()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        r = torch.tensor([float(st["rays"])], device=dev)
+        dist.all_reduce(r)
+        rays_all = float(r.item())
+    else:
+        rays_all = float(st["rays"])
+    ms_step = ms / args.steps
+    value = rays_all * args.steps / (ms / 1e3)
+    key_bits = (len(w.telescopes) - 1).bit_length() + (n - 1).bit_length() + 16
+    passes = (key_bits + 7) // 8
+    launches_per_step = 1 + 5 * passes + 3
+
+    # ---- roofline of the dominant kernel (generation + propagation + hits)
+    k_ms = statistics.mean(kms)
+    ops = st["rays"] * OPS_RAY + st["cells"] * NODES_PER_CELL * OPS_NODE
+    mufu = st["rays"] * MUFU_RAY + st["cells"] * NODES_PER_CELL * MUFU_NODE
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    peak_ops = n_sm * FP32_LANES_PER_SM * f_max
+    achieved = ops / (k_ms / 1e3)
+    roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s (FP32 pipe)",
+            "frac": achieved / peak_ops, "traffic": None,
+            "kernel": "k_trace_fused", "kernel_ms": k_ms, "sort_ms": statistics.mean(sms),
+            "mufu_frac": (mufu / (k_ms / 1e3)) / (n_sm * MUFU_LANES_PER_SM * f_max),
+            "ops_per_ray": ops / max(1, st["rays"]), "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                                                                 f"{f_max / 1e6:.0f} MHz (max SM clock)"}
+
+    # ---- plain FP64 GPU path on the same workload
+    fp64 = None
+    if not args.no_fp64:
+        ctx.trace(segs, n, 1, hits, cap, counts, sums, fp64=True)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(s)
+        code, nh64, st64 = ctx.trace(segs, n, 1, hits, cap, counts, sums, fp64=True)
+        f1.record(s)
+        torch.cuda.synchronize()
+        fms = f0.elapsed_time(f1)
+        fp64 = {"value": st64["rays"] / (fms / 1e3), "unit": UNIT, "ms_per_step": fms,
+                "speedup_of_fp32": (st64["rays"] / (fms / 1e3)) and value / (st64["rays"] / (fms / 1e3))}
+
+    # ---- end to end through the host-buffer entry point
+    e2e = None
+    if not args.no_e2e:
+        pinned = torch.from_numpy(w.segments.view(np.uint8).reshape(-1)).pin_memory()
+        hbuf = torch.empty(cap * 48, dtype=torch.uint8).pin_memory()
+        cbuf = torch.zeros(len(w.telescopes), dtype=torch.int64).pin_memory()
+        sbuf = torch.zeros(len(w.telescopes), dtype=torch.float64).pin_memory()
+        seg_np = pinned.numpy().view(I.SEG_DTYPE)
+        hits_np = hbuf.numpy().view(G.HIT_DTYPE)
+        ctx.set_params(w.params, **{**extra, "use_graph": 0})
+        ctx.trace_host(seg_np, 1, cap, hits_out=hits_np, counts_out=cbuf.numpy(), sums_out=sbuf.numpy())
+        k2 = max(3, args.steps // 4)
+        barrier()
+        t0 = time.perf_counter()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(s)
+        for _ in range(k2):
+            code, hh, cc, ss, st2 = ctx.trace_host(seg_np, 1, cap, hits_out=hits_np, counts_out=cbuf.numpy(),
+                                                   sums_out=sbuf.numpy())
+        g1.record(s)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        barrier()
+        e2e = {"value": st2["rays"] * k2 / wall, "unit": UNIT,
+               "h2d_bytes_per_step": int(n * 64),
+               "d2h_bytes_per_step": int(len(hh) * 48 + cbuf.numel() * 8 + sbuf.numel() * 8),
+               "ms_per_step": wall * 1e3 / k2}
+        ctx.set_params(w.params, **extra)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(w)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "segments": n, "rays_per_step": st["rays"], "hits_per_step": nh,
+                       "telescopes": len(w.telescopes), "bunch": w.params.bunch, "atmosphere": "5-layer, spherical, absorbing",
+                       "precision": ["float-pair", "fp64-guard"][args.precision], "graph": True,
+                       "l2": "inputs (1.28 GB) larger than L2; no flush", "parallelism": f"replicas x{world}",
+                       "generation_s": round(t_gen, 1)},
+            "roofline": roof, "fp64_plain": fp64, "e2e": e2e, "cpu_baseline": cpu,
+            "clocks": ck, "gpu_launches": launches_per_step * args.steps,
+            "stats": {k: int(v) for k, v in st.items()},
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    ctx.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,206 @@
+/*
+ * clight.h -- C ABI of the GB300 (sm_103a) library for Cherenkov and
+ * fluorescence light generation and atmospheric propagation to telescopes.
+ *
+ * The calls follow the paper's statement of the problem (Baack &
+ * Alameddine, "Comparison and efficiency of GPU accelerated optical light
+ * propagation in CORSIKA 8", ICRC 2023): charged-particle track steps go in
+ * (Sec. 1.2), together with the atmosphere the light crosses (Sec. 1.2,
+ * Sec. 2) and the telescope array it lands on; photon bunches come out as
+ * per-telescope hit lists, counts and photon sums (Sec. 1, "common memory
+ * block" of photon data; Sec. 2, propagation to ground).
+ *
+ * Conventions
+ *  - Pointers named d_* are device pointers owned by the caller; h_* are host
+ *    pointers owned by the caller.  The library owns its context: the
+ *    atmosphere tables, the telescope grid, scratch buffers and CUDA graphs.
+ *  - Every call is ordered on the CUDA stream passed as `stream`
+ *    (a cudaStream_t; NULL = legacy default stream).  Calls that return host
+ *    results synchronise that stream once before returning.
+ *  - Errors are return codes; nothing aborts, throws or faults the GPU to
+ *    signal an error.  clight_status_string() names each code.
+ *  - A context is used by one host thread and one stream at a time.
+ *  - Units: metres, nanoseconds, nanometres, g/cm^3, MeV.
+ *
+ * Limits: at most 8 atmosphere layers, 64 quadrature cells, 2^31 segments
+ * per call, 2^24 telescopes x showers, and a sort key of 64 bits holding
+ * (shower*n_tel + tel, segment, bunch).  A bunch index that does not fit
+ * the key returns CLIGHT_ERR_LIMIT.
+ */
+#ifndef CLIGHT_H
+#define CLIGHT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CLIGHT_OK = 0,
+    CLIGHT_ERR_ARG = 1,           /* invalid argument (null, negative size, bad table) */
+    CLIGHT_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+    CLIGHT_ERR_HIT_CAPACITY = 3,  /* more hits than hit_capacity; *h_n_hits = required */
+    CLIGHT_ERR_BAD_SEGMENT = 4,   /* NaN/inf field, L < 0, zero direction, shower >= n_showers */
+    CLIGHT_ERR_LIMIT = 5,         /* a size or index exceeds a documented limit */
+    CLIGHT_ERR_NO_DEVICE = 6      /* no usable CUDA device */
+} clight_status;
+
+/* Charged-particle track step (64 bytes, little endian).  Sec. 1.2: steps of
+ * "a couple of meters" over which the atmosphere is taken as homogeneous. */
+typedef struct {
+    double x, y, z;     /* start of the step, local frame (z up, origin at sea
+                           level below the array centre), m */
+    double t0;          /* time at the start of the step, ns */
+    float dx, dy, dz;   /* direction of flight; normalised by the library */
+    float L;            /* step length, m (>= 0) */
+    float eps;          /* 1 - beta of the particle */
+    float dE;           /* energy deposited over the step, MeV (fluorescence) */
+    int32_t charge;     /* charge number z */
+    uint32_t shower;    /* shower index, < n_showers */
+} clight_segment;
+
+/* Telescope sphere (16 bytes). */
+typedef struct {
+    float x, y, z, R;   /* centre (m) and radius (m) */
+} clight_telescope;
+
+/* Layered exponential atmosphere: on [h_lo[i], h_lo[i+1]) the density is
+ * rho_i(h) = b_i / (100 c_i) exp(-h / c_i) g/cm^3 (b_i in g/cm^2, c_i in m),
+ * zero at and above h_top; n - 1 = K rho.  Extinction length
+ * L_ext(lambda) = L0 (lambda / lambda_ref)^4; optical depth
+ * tau = int rho / rho_ref ds / L_ext. */
+typedef struct {
+    int32_t n_layers;               /* 1..8, h_lo increasing */
+    int32_t spherical;              /* 0 = flat Earth, 1 = spherical Earth of radius R_E */
+    double h_lo[8], b[8], c[8];
+    double h_top;                   /* top of the atmosphere, m */
+    double K;                       /* refractivity per density, cm^3/g */
+    double rho_ref;                 /* density normalising tau, g/cm^3 */
+    double L0;                      /* extinction length at lambda_ref, m */
+    double lambda_ref;              /* nm */
+    double R_E;                     /* Earth radius, m */
+    double h_obs;                   /* observation level, m */
+    int32_t refraction;             /* 1 = refracted rays, 0 = straight lines */
+    int32_t absorption;             /* 1 = weight photons by exp(-tau) */
+} clight_atmosphere;
+
+/* Precision of the fused FP32 path's few extended-precision steps. */
+enum {
+    CLIGHT_PREC_FLOAT_PAIR = 0,     /* FP32 pairs (double-float) -- default */
+    CLIGHT_PREC_FP64_GUARD = 1      /* native FP64 for the same steps */
+};
+
+typedef struct {
+    double lambda1, lambda2;        /* Cherenkov band, nm */
+    double bunch;                   /* maximum photons per bunch (> 0) */
+    uint32_t seed, stream;          /* Philox-4x32-10 key words */
+    double fluor_yield;             /* photons per MeV deposited; 0 = no fluorescence */
+    double fl_lambda1, fl_lambda2;  /* fluorescence band, nm */
+    int64_t seg_base;               /* global index of d_segs[0] (keys the random numbers) */
+    int32_t precision;              /* CLIGHT_PREC_* */
+    int32_t block;                  /* threads per block of the fused kernel (0 = default) */
+    int32_t ctas_per_sm;            /* persistent CTAs per SM (0 = default) */
+    int32_t use_graph;              /* capture the whole pipeline in a CUDA graph and replay */
+    float cell_width;               /* quadrature cell width in scale heights (0 = default) */
+    int32_t key_bunch_bits;         /* bits of the bunch index in the sort key (0 = 16) */
+} clight_params;
+
+/* One telescope hit (48 bytes). */
+typedef struct {
+    int64_t seg;                    /* global segment index (seg_base + i) */
+    uint32_t k;                     /* bunch index within the segment (Cherenkov first) */
+    uint32_t tel;                   /* telescope index */
+    float x_rel, y_rel;             /* crossing of the plane z = z_tel, relative to the centre, m */
+    float cx, cy;                   /* direction cosines at arrival */
+    float lambda;                   /* wavelength, nm */
+    float weight;                   /* photons in the bunch times exp(-tau) */
+    double t;                       /* arrival time at that crossing, ns */
+} clight_hit;
+
+typedef struct {
+    int64_t rays;       /* bunches generated and traced */
+    int64_t escaped;    /* pointing away from the Earth */
+    int64_t under;      /* emitted at or below the observation level */
+    int64_t turned;     /* never reach the observation level */
+    int64_t reached;    /* arrived at the observation level */
+    int64_t hits;       /* ray-telescope hits (a ray may hit several) */
+    int64_t guarded;    /* segments whose bunch count was recomputed in FP64 */
+    int64_t status;     /* OR of CLIGHT_ERR_* bits seen in the kernels (1 << code) */
+    int64_t cells;      /* altitude cells integrated, summed over arrived rays */
+} clight_stats;
+
+typedef struct clight_ctx clight_ctx;
+
+/* Create a context on CUDA device `device`.  Allocates nothing large yet.
+ * Returns CLIGHT_ERR_NO_DEVICE if the device cannot be used. */
+clight_status clight_create(clight_ctx **out, int device);
+
+/* Destroy a context and free everything it owns.  NULL is accepted. */
+void clight_destroy(clight_ctx *ctx);
+
+/* Copy the atmosphere model (host struct) into the context and build the
+ * altitude cells of the ray quadrature.  ERR_ARG on an invalid table. */
+clight_status clight_set_atmosphere(clight_ctx *ctx, const clight_atmosphere *atm);
+
+/* Copy n telescopes (host array) into the context and build their uniform
+ * grid.  ERR_ARG if n < 1 or a radius is not positive. */
+clight_status clight_set_telescopes(clight_ctx *ctx, const clight_telescope *h_tels, int32_t n);
+
+/* Set generation and launch parameters.  ERR_ARG on an invalid value. */
+clight_status clight_set_params(clight_ctx *ctx, const clight_params *par);
+
+/* Generate, propagate and hit-test every photon bunch of n_segs segments
+ * (Sec. 1.1, 1.2, 2) on the fused FP32 path: one persistent work-stealing
+ * launch over the segments, then a sort of the hits by
+ * (shower, telescope, segment, bunch) and per-(shower, telescope) counts and
+ * FP64 photon sums.
+ *   d_segs        n_segs segments (device, read only)
+ *   d_hits        hit_capacity records (device); the first *h_n_hits are
+ *                 written, sorted
+ *   d_counts      n_showers * n_tel int64 (device) or NULL
+ *   d_sums        n_showers * n_tel double (device) or NULL
+ *   h_stats       statistics (host) or NULL
+ *   h_n_hits      number of hits (host); on CLIGHT_ERR_HIT_CAPACITY the
+ *                 required capacity, and nothing beyond hit_capacity is
+ *                 written, counts and sums are left zero.
+ * Synchronises `stream` once.  Kernel-detected input errors are returned as
+ * CLIGHT_ERR_BAD_SEGMENT / CLIGHT_ERR_LIMIT after the run. */
+clight_status clight_trace(clight_ctx *ctx, const clight_segment *d_segs, int64_t n_segs,
+                           int32_t n_showers, clight_hit *d_hits, int64_t hit_capacity,
+                           int64_t *d_counts, double *d_sums, clight_stats *h_stats,
+                           int64_t *h_n_hits, void *stream);
+
+/* The same computation with FP64 arithmetic throughout: one thread per
+ * segment, no work stealing, no graph (the plain double-precision path the
+ * fused one is measured against).  Same arguments and outputs. */
+clight_status clight_trace_fp64(clight_ctx *ctx, const clight_segment *d_segs, int64_t n_segs,
+                                int32_t n_showers, clight_hit *d_hits, int64_t hit_capacity,
+                                int64_t *d_counts, double *d_sums, clight_stats *h_stats,
+                                int64_t *h_n_hits, void *stream);
+
+/* clight_trace on HOST buffers: copies the segments to the device, runs the
+ * fused path, copies hits, counts and sums back.  Device staging buffers are
+ * owned by the context.  h_counts / h_sums may be NULL. */
+clight_status clight_trace_host(clight_ctx *ctx, const clight_segment *h_segs, int64_t n_segs,
+                                int32_t n_showers, clight_hit *h_hits, int64_t hit_capacity,
+                                int64_t *h_counts, double *h_sums, clight_stats *h_stats,
+                                int64_t *h_n_hits, void *stream);
+
+/* Device time of the last clight_trace / clight_trace_fp64 call, measured
+ * with CUDA events recorded on the launch stream around its phases:
+ * ms[0] = generation + propagation + hit kernel, ms[1] = sort and per-
+ * telescope reduction.  ERR_ARG if ms is NULL or no call has run. */
+clight_status clight_last_timing(clight_ctx *ctx, float ms[2]);
+
+/* Human-readable name of a status code (static string). */
+const char *clight_status_string(clight_status s);
+
+/* Version of this ABI (major * 10000 + minor * 100 + patch). */
+int clight_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CLIGHT_H */

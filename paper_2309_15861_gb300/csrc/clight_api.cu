@@ -1,0 +1,543 @@
+// clight_api.cu -- the C ABI declared in include/clight.h: context, tables,
+// scratch memory, the launch sequence and its CUDA-graph replay.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+
+using namespace clight;
+
+// Device buffer that only grows; every reallocation bumps *gen so that a
+// captured graph holding the old address is rebuilt.
+template <class T> struct Buf {
+    T *p = nullptr;
+    int64_t n = 0;
+    cudaError_t ensure(int64_t need, uint64_t *gen)
+    {
+        need = std::max<int64_t>(need, 1);
+        if (p && need <= n) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+        cudaError_t e = cudaMalloc((void **)&p, sizeof(T) * (size_t)need);
+        if (e == cudaSuccess) n = need;
+        ++*gen;
+        return e;
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+};
+
+
+struct GraphKey {
+    const void *segs;
+    int64_t n_segs;
+    int32_t n_showers;
+    const void *hits;
+    int64_t cap;
+    const void *counts;
+    const void *sums;
+    uint64_t version;
+    bool operator==(const GraphKey &o) const
+    {
+        return segs == o.segs && n_segs == o.n_segs && n_showers == o.n_showers && hits == o.hits &&
+               cap == o.cap && counts == o.counts && sums == o.sums && version == o.version;
+    }
+};
+
+struct clight_ctx {
+    int device = 0, n_sm = 0;
+    bool atm_set = false, tel_set = false;
+    uint64_t version = 1;             // bumped by every set_* call
+    DevAtm atm{};
+    DevTel tel{};
+    DevPar par{};
+    clight_params upar{};
+    clight_atmosphere uatm{};
+    // telescope tables (device)
+    float4 *d_tel = nullptr;
+    int *d_cell_start = nullptr, *d_cell_tel = nullptr;
+    // scratch (device)
+    unsigned long long *d_ctr = nullptr;
+    Buf<clight_hit> rec;
+    Buf<unsigned long long> keys, keys_alt;
+    Buf<uint32_t> vals, vals_alt, hist, bsums;
+    Buf<int64_t> gstart, gend;
+    uint64_t scratch_gen = 0;
+    // staging for the host-buffer entry point
+    Buf<clight_segment> stage_segs;
+    Buf<clight_hit> stage_hits;
+    Buf<int64_t> stage_counts;
+    Buf<double> stage_sums;
+    // pinned host copy of the counters
+    unsigned long long *h_ctr = nullptr;
+    // graph replay
+    cudaStream_t cap_stream = nullptr;
+    cudaEvent_t ev = nullptr;
+    cudaEvent_t t0 = nullptr, t1 = nullptr, t2 = nullptr;   // phase timing
+    bool timed = false;
+    cudaGraphExec_t gexec = nullptr;
+    GraphKey gkey{};
+};
+
+#define CK(x)                                   \
+    do {                                        \
+        cudaError_t e_ = (x);                   \
+        if (e_ != cudaSuccess) return CLIGHT_ERR_CUDA; \
+    } while (0)
+
+static int bits_for(int64_t x)   // bits needed to hold values 0..x
+{
+    int b = 0;
+    while (x > 0) { ++b; x >>= 1; }
+    return b;
+}
+
+extern "C" {
+
+const char *clight_status_string(clight_status s)
+{
+    switch (s) {
+    case CLIGHT_OK: return "ok";
+    case CLIGHT_ERR_ARG: return "invalid argument";
+    case CLIGHT_ERR_CUDA: return "CUDA runtime error";
+    case CLIGHT_ERR_HIT_CAPACITY: return "hit capacity exceeded";
+    case CLIGHT_ERR_BAD_SEGMENT: return "invalid segment";
+    case CLIGHT_ERR_LIMIT: return "size or index beyond a documented limit";
+    case CLIGHT_ERR_NO_DEVICE: return "no usable CUDA device";
+    }
+    return "unknown status";
+}
+
+int clight_version(void) { return 10000; }
+
+clight_status clight_last_timing(clight_ctx *c, float ms[2])
+{
+    if (!c || !ms || !c->timed) return CLIGHT_ERR_ARG;
+    if (cudaEventElapsedTime(&ms[0], c->t0, c->t1) != cudaSuccess) return CLIGHT_ERR_CUDA;
+    if (cudaEventElapsedTime(&ms[1], c->t1, c->t2) != cudaSuccess) return CLIGHT_ERR_CUDA;
+    return CLIGHT_OK;
+}
+
+clight_status clight_create(clight_ctx **out, int device)
+{
+    if (!out) return CLIGHT_ERR_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return CLIGHT_ERR_NO_DEVICE;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return CLIGHT_ERR_NO_DEVICE;
+    clight_ctx *c = new clight_ctx();
+    c->device = device;
+    cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device);
+    if (cudaMalloc((void **)&c->d_ctr, sizeof(unsigned long long) * CTR_N) != cudaSuccess ||
+        cudaMallocHost((void **)&c->h_ctr, sizeof(unsigned long long) * CTR_N) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreate(&c->t0) != cudaSuccess || cudaEventCreate(&c->t1) != cudaSuccess ||
+        cudaEventCreate(&c->t2) != cudaSuccess) {
+        clight_destroy(c);
+        return CLIGHT_ERR_CUDA;
+    }
+    clight_params p{};
+    p.lambda1 = 300; p.lambda2 = 600; p.bunch = 1; p.seed = 1; p.stream = 0;
+    p.fl_lambda1 = 340; p.fl_lambda2 = 450;
+    *out = c;
+    clight_set_params(c, &p);
+    return CLIGHT_OK;
+}
+
+void clight_destroy(clight_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    void *dev[] = {c->d_tel, c->d_cell_start, c->d_cell_tel, c->d_ctr};
+    for (void *p : dev)
+        if (p) cudaFree(p);
+    c->rec.release(); c->keys.release(); c->keys_alt.release(); c->vals.release(); c->vals_alt.release();
+    c->hist.release(); c->bsums.release(); c->gstart.release(); c->gend.release();
+    c->stage_segs.release(); c->stage_hits.release(); c->stage_counts.release(); c->stage_sums.release();
+    if (c->h_ctr) cudaFreeHost(c->h_ctr);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->ev) cudaEventDestroy(c->ev);
+    if (c->t0) cudaEventDestroy(c->t0);
+    if (c->t1) cudaEventDestroy(c->t1);
+    if (c->t2) cudaEventDestroy(c->t2);
+    delete c;
+}
+
+clight_status clight_set_atmosphere(clight_ctx *c, const clight_atmosphere *a)
+{
+    if (!c || !a) return CLIGHT_ERR_ARG;
+    if (a->n_layers < 1 || a->n_layers > kMaxLayers) return CLIGHT_ERR_ARG;
+    for (int i = 0; i < a->n_layers; ++i) {
+        if (!(a->c[i] > 0) || !(a->b[i] >= 0) || !std::isfinite(a->h_lo[i])) return CLIGHT_ERR_ARG;
+        if (i > 0 && !(a->h_lo[i] > a->h_lo[i - 1])) return CLIGHT_ERR_ARG;
+    }
+    if (!(a->K >= 0) || !(a->rho_ref > 0) || !(a->h_top > a->h_obs) || !std::isfinite(a->h_obs))
+        return CLIGHT_ERR_ARG;
+    if (a->absorption && (!(a->L0 > 0) || !(a->lambda_ref > 0))) return CLIGHT_ERR_ARG;
+    if (a->spherical && !(a->R_E > 0)) return CLIGHT_ERR_ARG;
+    if (a->n_layers > 1 && a->h_lo[0] > a->h_obs) return CLIGHT_ERR_ARG;
+    DevAtm &A = c->atm;
+    A = DevAtm{};
+    A.n_layers = a->n_layers;
+    A.spherical = a->spherical ? 1 : 0;
+    A.refraction = a->refraction ? 1 : 0;
+    A.absorption = a->absorption ? 1 : 0;
+    const double LOG2E = 1.4426950408889634;
+    auto Bc = [&](int i) { return a->b[i] / (100.0 * a->c[i]); };   // rho = Bc e^{-h/c}
+    for (int i = 0; i < a->n_layers; ++i) {
+        A.h_lo[i] = (float)a->h_lo[i];
+        A.h_lo_d[i] = a->h_lo[i];
+        A.kb[i] = (float)(a->K * Bc(i));
+        A.kb_d[i] = a->K * Bc(i);
+        A.rb[i] = (float)(Bc(i) / a->rho_ref);
+        A.rb_d[i] = Bc(i) / a->rho_ref;
+        A.nl2c[i] = (float)(-LOG2E / a->c[i]);
+        A.inv_c_d[i] = 1.0 / a->c[i];
+    }
+    A.h_top = (float)a->h_top; A.h_top_d = a->h_top;
+    A.h_obs = (float)a->h_obs; A.h_obs_d = a->h_obs;
+    A.R_E = (float)a->R_E; A.R_E_d = a->spherical ? a->R_E : 0.0;
+    A.r_obs_d = a->R_E + a->h_obs; A.r_obs = (float)A.r_obs_d;
+    auto delta_at = [&](double h) {
+        if (h >= a->h_top) return 0.0;
+        int i = 0;
+        for (int j = 1; j < a->n_layers; ++j)
+            if (h >= a->h_lo[j]) i = j;
+        return a->K * Bc(i) * std::exp(-h / a->c[i]);
+    };
+    A.delta_obs_d = delta_at(a->h_obs);
+    A.delta_obs = (float)A.delta_obs_d;
+    A.n_obs = (float)(1.0 + A.delta_obs_d);
+    A.inv_L0_d = a->absorption ? 1.0 / a->L0 : 0.0;
+    A.inv_L0 = (float)A.inv_L0_d;
+    A.lambda_ref_d = a->absorption ? a->lambda_ref : 1.0;
+    A.lambda_ref = (float)A.lambda_ref_d;
+    // 4-node Gauss-Legendre on [-1, 1] (closed form)
+    const double r65 = std::sqrt(6.0 / 5.0), r30 = std::sqrt(30.0);
+    const double xs = std::sqrt(3.0 / 7.0 - 2.0 / 7.0 * r65), xl = std::sqrt(3.0 / 7.0 + 2.0 / 7.0 * r65);
+    const double ws = (18.0 + r30) / 36.0, wl = (18.0 - r30) / 36.0;
+    const double gx[4] = {-xl, -xs, xs, xl}, gw[4] = {wl, ws, ws, wl};
+    for (int i = 0; i < 4; ++i) {
+        A.gl_x[i] = (float)gx[i]; A.gl_w[i] = (float)gw[i];
+        A.gl_x_d[i] = gx[i]; A.gl_w_d[i] = gw[i];
+    }
+    c->uatm = *a;
+    c->atm_set = true;
+    ++c->version;
+    // cells are built with the current cell width (params)
+    float cw = c->upar.cell_width > 0 ? c->upar.cell_width : 1.0f;
+    int nc = 0;
+    for (int i = 0; i < a->n_layers; ++i) {
+        double lo = std::max(a->h_lo[i], a->h_obs);
+        double hi = (i + 1 < a->n_layers) ? a->h_lo[i + 1] : a->h_top;
+        hi = std::min(hi, a->h_top);
+        if (i == 0 && a->h_lo[0] > a->h_obs) lo = a->h_obs;
+        if (!(hi > lo)) continue;
+        int m = (int)std::ceil((hi - lo) / (cw * a->c[i]));
+        m = std::max(1, m);
+        for (int q = 0; q < m; ++q) {
+            if (nc >= kMaxCells) return CLIGHT_ERR_LIMIT;
+            double l0 = lo + (hi - lo) * q / m, l1 = (q + 1 == m) ? hi : lo + (hi - lo) * (q + 1) / m;
+            DevCell &C = A.cells[nc];
+            C.lo = (float)l0; C.hi = (float)l1;
+            C.kb = A.kb[i]; C.rb = A.rb[i]; C.nl2c = A.nl2c[i];
+            A.cell_lo_d[nc] = (double)C.lo;   // identical edges in both precisions
+            A.cell_hi_d[nc] = (double)C.hi;
+            A.cell_kb_d[nc] = A.kb_d[i]; A.cell_rb_d[nc] = A.rb_d[i]; A.cell_ic_d[nc] = A.inv_c_d[i];
+            ++nc;
+        }
+    }
+    A.n_cells = nc;
+    return CLIGHT_OK;
+}
+
+clight_status clight_set_telescopes(clight_ctx *c, const clight_telescope *t, int32_t n)
+{
+    if (!c || !t || n < 1) return CLIGHT_ERR_ARG;
+    float xmin = 1e30f, xmax = -1e30f, ymin = 1e30f, ymax = -1e30f, zmin = 1e30f, zmax = -1e30f, rmax = 0;
+    for (int i = 0; i < n; ++i) {
+        if (!(t[i].R > 0) || !std::isfinite(t[i].x) || !std::isfinite(t[i].y) || !std::isfinite(t[i].z))
+            return CLIGHT_ERR_ARG;
+        xmin = std::min(xmin, t[i].x - t[i].R); xmax = std::max(xmax, t[i].x + t[i].R);
+        ymin = std::min(ymin, t[i].y - t[i].R); ymax = std::max(ymax, t[i].y + t[i].R);
+        zmin = std::min(zmin, t[i].z); zmax = std::max(zmax, t[i].z);
+        rmax = std::max(rmax, t[i].R);
+    }
+    // uniform grid: cells of at least 2 Rmax, about one telescope per cell
+    double area = std::max(1.0, (double)(xmax - xmin) * (double)(ymax - ymin));
+    double gs = std::max(2.0 * rmax, std::sqrt(area / n));
+    int nx = (int)std::ceil((xmax - xmin) / gs) + 1, ny = (int)std::ceil((ymax - ymin) / gs) + 1;
+    while ((int64_t)nx * ny > (1 << 22)) { gs *= 2; nx = (int)std::ceil((xmax - xmin) / gs) + 1; ny = (int)std::ceil((ymax - ymin) / gs) + 1; }
+    std::vector<int> count((size_t)nx * ny + 1, 0), cell_of(n);
+    for (int i = 0; i < n; ++i) {
+        int ix = std::min(nx - 1, std::max(0, (int)std::floor((t[i].x - xmin) / gs)));
+        int iy = std::min(ny - 1, std::max(0, (int)std::floor((t[i].y - ymin) / gs)));
+        cell_of[i] = iy * nx + ix;
+        count[cell_of[i] + 1]++;
+    }
+    for (size_t q = 1; q < count.size(); ++q) count[q] += count[q - 1];
+    std::vector<int> fill(count.begin(), count.end() - 1), tel_idx(n);
+    for (int i = 0; i < n; ++i) tel_idx[fill[cell_of[i]]++] = i;
+    std::vector<float4> tv(n);
+    for (int i = 0; i < n; ++i) tv[i] = make_float4(t[i].x, t[i].y, t[i].z, t[i].R);
+    cudaSetDevice(c->device);
+    if (c->d_tel) cudaFree(c->d_tel);
+    if (c->d_cell_start) cudaFree(c->d_cell_start);
+    if (c->d_cell_tel) cudaFree(c->d_cell_tel);
+    c->d_tel = nullptr; c->d_cell_start = nullptr; c->d_cell_tel = nullptr;
+    CK(cudaMalloc((void **)&c->d_tel, sizeof(float4) * n));
+    CK(cudaMalloc((void **)&c->d_cell_start, sizeof(int) * count.size()));
+    CK(cudaMalloc((void **)&c->d_cell_tel, sizeof(int) * n));
+    CK(cudaMemcpy(c->d_tel, tv.data(), sizeof(float4) * n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_cell_start, count.data(), sizeof(int) * count.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_cell_tel, tel_idx.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+    DevTel &T = c->tel;
+    T.tel = c->d_tel; T.cell_start = c->d_cell_start; T.cell_tel = c->d_cell_tel;
+    T.n_tel = n; T.nx = nx; T.ny = ny;
+    T.gx0 = xmin; T.gy0 = ymin; T.gs = (float)gs; T.inv_gs = (float)(1.0 / gs);
+    T.xmin = xmin; T.xmax = xmax; T.ymin = ymin; T.ymax = ymax; T.Rmax = rmax; T.zmin = zmin; T.zmax = zmax;
+    c->tel_set = true;
+    ++c->version;
+    return CLIGHT_OK;
+}
+
+clight_status clight_set_params(clight_ctx *c, const clight_params *p)
+{
+    if (!c || !p) return CLIGHT_ERR_ARG;
+    if (!(p->lambda1 > 0) || !(p->lambda2 > p->lambda1) || !(p->bunch > 0) || !(p->fluor_yield >= 0) ||
+        !(p->fl_lambda1 > 0) || !(p->fl_lambda2 >= p->fl_lambda1) || p->seg_base < 0)
+        return CLIGHT_ERR_ARG;
+    if (p->block != 0 && (p->block < 32 || p->block > 256 || p->block % 32)) return CLIGHT_ERR_ARG;
+    if (p->ctas_per_sm < 0 || p->ctas_per_sm > 32) return CLIGHT_ERR_ARG;
+    if (p->precision != CLIGHT_PREC_FLOAT_PAIR && p->precision != CLIGHT_PREC_FP64_GUARD) return CLIGHT_ERR_ARG;
+    if (p->cell_width < 0 || p->cell_width > 8) return CLIGHT_ERR_ARG;
+    if (p->key_bunch_bits < 0 || p->key_bunch_bits > 32) return CLIGHT_ERR_ARG;
+    float old_cw = c->upar.cell_width;
+    c->upar = *p;
+    DevPar &P = c->par;
+    const double alpha = 7.2973525643e-3, pi = 3.14159265358979323846;
+    P.band_d = 2.0 * pi * alpha * (1.0 / p->lambda1 - 1.0 / p->lambda2) * 1e9;
+    P.band = (float)P.band_d;
+    P.bunch_d = p->bunch;
+    P.bunch = (float)p->bunch;
+    P.inv_bunch = (float)(1.0 / p->bunch);
+    P.il1_d = 1.0 / p->lambda1;
+    P.dil_d = 1.0 / p->lambda1 - 1.0 / p->lambda2;
+    P.il1 = (float)P.il1_d;
+    P.dil = (float)P.dil_d;
+    P.fl1_d = p->fl_lambda1;
+    P.fdl_d = p->fl_lambda2 - p->fl_lambda1;
+    P.fl1 = (float)P.fl1_d;
+    P.fdl = (float)P.fdl_d;
+    P.fyield_d = p->fluor_yield;
+    P.fyield = (float)p->fluor_yield;
+    P.seed = p->seed;
+    P.stream = p->stream;
+    P.seg_base = p->seg_base;
+    ++c->version;
+    if (c->atm_set && p->cell_width != old_cw) {
+        clight_atmosphere a = c->uatm;
+        return clight_set_atmosphere(c, &a);
+    }
+    return CLIGHT_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ pipeline
+namespace {
+
+struct Plan {
+    int key_bits, group_shift;
+    int64_t n_groups, tiles;
+};
+
+clight_status prepare(clight_ctx *c, int64_t n_segs, int32_t n_showers, int64_t cap, Plan &pl)
+{
+    if (!c->atm_set || !c->tel_set) return CLIGHT_ERR_ARG;
+    if (n_segs < 0 || n_showers < 1 || cap < 0) return CLIGHT_ERR_ARG;
+    if (n_segs > (int64_t(1) << 31)) return CLIGHT_ERR_LIMIT;
+    if ((int64_t)n_showers * c->tel.n_tel > (int64_t(1) << 24)) return CLIGHT_ERR_LIMIT;
+    if (cap > (int64_t(1) << 32) - 1) return CLIGHT_ERR_LIMIT;
+    int gbits = bits_for((int64_t)n_showers * c->tel.n_tel - 1);
+    int sbits = bits_for(std::max<int64_t>(n_segs - 1, 0));
+    int kbits = c->upar.key_bunch_bits > 0 ? c->upar.key_bunch_bits : 16;
+    if (gbits + sbits + kbits > 64) kbits = 64 - gbits - sbits;
+    if (kbits < 8) return CLIGHT_ERR_LIMIT;
+    pl.key_bits = gbits + sbits + kbits;
+    pl.group_shift = sbits + kbits;
+    pl.n_groups = (int64_t)n_showers * c->tel.n_tel;
+    pl.tiles = std::max<int64_t>(1, (cap + sort_tile_items() - 1) / sort_tile_items());
+    c->par.n_showers = n_showers;
+    c->par.seg_bits = sbits;
+    c->par.k_bits = kbits;
+    cudaSetDevice(c->device);
+    uint64_t *g = &c->scratch_gen;
+    if (c->rec.ensure(cap, g) || c->keys.ensure(cap, g) || c->keys_alt.ensure(cap, g) ||
+        c->vals.ensure(cap, g) || c->vals_alt.ensure(cap, g) || c->hist.ensure(256 * pl.tiles, g) ||
+        c->bsums.ensure(scan_block_sums_needed(256 * pl.tiles), g) || c->gstart.ensure(pl.n_groups, g) ||
+        c->gend.ensure(pl.n_groups, g))
+        return CLIGHT_ERR_CUDA;
+    return CLIGHT_OK;
+}
+
+cudaError_t enqueue(clight_ctx *c, const clight_segment *segs, int64_t n_segs, const Plan &pl, clight_hit *hits,
+                    int64_t cap, int64_t *counts, double *sums, bool fp64, cudaStream_t s)
+{
+    DevOut O;
+    O.rec = c->rec.p;
+    O.keys = c->keys.p;
+    O.vals = c->vals.p;
+    O.capacity = cap;
+    O.ctr = c->d_ctr;
+    SortScratch S;
+    S.keys_alt = c->keys_alt.p;
+    S.vals_alt = c->vals_alt.p;
+    S.hist = c->hist.p;
+    S.block_sums = c->bsums.p;
+    S.max_tiles = pl.tiles;
+    S.gstart = c->gstart.p;
+    S.gend = c->gend.p;
+    cudaError_t e = cudaMemsetAsync(c->d_ctr, 0, sizeof(unsigned long long) * CTR_N, s);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaEventRecord(c->t0, s)) != cudaSuccess) return e;
+    if (n_segs > 0) {
+        if (fp64) {
+            e = launch_trace_fp64(segs, n_segs, c->atm, c->tel, c->par, O, s);
+        } else {
+            int block = c->upar.block > 0 ? c->upar.block : 256;
+            int per_sm = c->upar.ctas_per_sm > 0 ? c->upar.ctas_per_sm : 2 * 256 / block;
+            int64_t groups = (n_segs + 31) / 32;
+            int64_t grid = std::min<int64_t>((int64_t)c->n_sm * per_sm, (groups * 32 + block - 1) / block);
+            grid = std::max<int64_t>(grid, 1);
+            e = launch_trace_fused(segs, n_segs, c->atm, c->tel, c->par, O, c->upar.precision, (int)grid, block, s);
+        }
+        if (e != cudaSuccess) return e;
+    }
+    if ((e = cudaEventRecord(c->t1, s)) != cudaSuccess) return e;
+    e = launch_sort_and_finalize(O, S, pl.key_bits, pl.group_shift, pl.n_groups, hits, counts, sums, s);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaEventRecord(c->t2, s)) != cudaSuccess) return e;
+    return cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(unsigned long long) * CTR_N, cudaMemcpyDeviceToHost, s);
+}
+
+clight_status finish(clight_ctx *c, int64_t cap, clight_stats *st, int64_t *n_hits)
+{
+    const unsigned long long *h = c->h_ctr;
+    unsigned long long cursor = h[CTR_CURSOR];
+    if (n_hits) *n_hits = (int64_t)cursor;
+    unsigned long long bits = h[CTR_STATS + ST_STATUS];
+    if (st) {
+        st->rays = (int64_t)h[CTR_STATS + ST_RAYS];
+        st->escaped = (int64_t)h[CTR_STATS + ST_ESCAPED];
+        st->under = (int64_t)h[CTR_STATS + ST_UNDER];
+        st->turned = (int64_t)h[CTR_STATS + ST_TURNED];
+        st->reached = (int64_t)h[CTR_STATS + ST_REACHED];
+        st->hits = (int64_t)h[CTR_STATS + ST_HITS];
+        st->guarded = (int64_t)h[CTR_STATS + ST_GUARDED];
+        st->status = (int64_t)bits;
+        st->cells = (int64_t)h[CTR_STATS + ST_CELLS];
+    }
+    c->timed = true;
+    if ((int64_t)cursor > cap) return CLIGHT_ERR_HIT_CAPACITY;
+    if (bits & (1ull << CLIGHT_ERR_BAD_SEGMENT)) return CLIGHT_ERR_BAD_SEGMENT;
+    if (bits & (1ull << CLIGHT_ERR_LIMIT)) return CLIGHT_ERR_LIMIT;
+    return CLIGHT_OK;
+}
+
+clight_status run(clight_ctx *c, const clight_segment *segs, int64_t n_segs, int32_t n_showers, clight_hit *hits,
+                  int64_t cap, int64_t *counts, double *sums, clight_stats *st, int64_t *n_hits, void *stream,
+                  bool fp64)
+{
+    if (!c || (n_segs > 0 && !segs) || (cap > 0 && !hits) || !n_hits) return CLIGHT_ERR_ARG;
+    Plan pl;
+    clight_status r = prepare(c, n_segs, n_showers, cap, pl);
+    if (r != CLIGHT_OK) return r;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!fp64 && c->upar.use_graph) {
+        GraphKey k{segs, n_segs, n_showers, hits, cap, counts, sums, c->version * 1000003ull + c->scratch_gen};
+        if (!c->gexec || !(k == c->gkey)) {
+            if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+            cudaGraph_t g;
+            CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = enqueue(c, segs, n_segs, pl, hits, cap, counts, sums, false, c->cap_stream);
+            cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+            if (e != cudaSuccess || e2 != cudaSuccess) return CLIGHT_ERR_CUDA;
+            e = cudaGraphInstantiate(&c->gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) { c->gexec = nullptr; return CLIGHT_ERR_CUDA; }
+            c->gkey = k;
+        }
+        CK(cudaEventRecord(c->ev, s));
+        CK(cudaStreamWaitEvent(c->cap_stream, c->ev, 0));
+        CK(cudaGraphLaunch(c->gexec, c->cap_stream));
+        CK(cudaEventRecord(c->ev, c->cap_stream));
+        CK(cudaStreamWaitEvent(s, c->ev, 0));         // later work on `stream` follows the graph
+        CK(cudaStreamSynchronize(c->cap_stream));
+    } else {
+        CK(enqueue(c, segs, n_segs, pl, hits, cap, counts, sums, fp64, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return finish(c, cap, st, n_hits);
+}
+
+}  // namespace
+
+extern "C" {
+
+clight_status clight_trace(clight_ctx *c, const clight_segment *d_segs, int64_t n_segs, int32_t n_showers,
+                           clight_hit *d_hits, int64_t cap, int64_t *d_counts, double *d_sums, clight_stats *st,
+                           int64_t *h_n_hits, void *stream)
+{
+    return run(c, d_segs, n_segs, n_showers, d_hits, cap, d_counts, d_sums, st, h_n_hits, stream, false);
+}
+
+clight_status clight_trace_fp64(clight_ctx *c, const clight_segment *d_segs, int64_t n_segs, int32_t n_showers,
+                                clight_hit *d_hits, int64_t cap, int64_t *d_counts, double *d_sums,
+                                clight_stats *st, int64_t *h_n_hits, void *stream)
+{
+    return run(c, d_segs, n_segs, n_showers, d_hits, cap, d_counts, d_sums, st, h_n_hits, stream, true);
+}
+
+clight_status clight_trace_host(clight_ctx *c, const clight_segment *h_segs, int64_t n_segs, int32_t n_showers,
+                                clight_hit *h_hits, int64_t cap, int64_t *h_counts, double *h_sums,
+                                clight_stats *st, int64_t *h_n_hits, void *stream)
+{
+    if (!c || (n_segs > 0 && !h_segs) || (cap > 0 && !h_hits) || !h_n_hits || n_showers < 1 || !c->tel_set)
+        return CLIGHT_ERR_ARG;
+    cudaSetDevice(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t ng = (int64_t)n_showers * c->tel.n_tel;
+    uint64_t *g = &c->scratch_gen;
+    if (c->stage_segs.ensure(n_segs, g) || c->stage_hits.ensure(cap, g) || c->stage_counts.ensure(ng, g) ||
+        c->stage_sums.ensure(ng, g))
+        return CLIGHT_ERR_CUDA;
+    if (n_segs > 0)
+        CK(cudaMemcpyAsync(c->stage_segs.p, h_segs, sizeof(clight_segment) * (size_t)n_segs, cudaMemcpyHostToDevice, s));
+    clight_status r = run(c, c->stage_segs.p, n_segs, n_showers, c->stage_hits.p, cap, c->stage_counts.p,
+                          c->stage_sums.p, st, h_n_hits, stream, false);
+    if (r != CLIGHT_OK && r != CLIGHT_ERR_BAD_SEGMENT && r != CLIGHT_ERR_LIMIT) return r;
+    int64_t n = std::min<int64_t>(*h_n_hits, cap);
+    if (n > 0) CK(cudaMemcpyAsync(h_hits, c->stage_hits.p, sizeof(clight_hit) * (size_t)n, cudaMemcpyDeviceToHost, s));
+    if (h_counts) CK(cudaMemcpyAsync(h_counts, c->stage_counts.p, sizeof(int64_t) * ng, cudaMemcpyDeviceToHost, s));
+    if (h_sums) CK(cudaMemcpyAsync(h_sums, c->stage_sums.p, sizeof(double) * ng, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return r;
+}
+
+}  // extern "C"

@@ -1,0 +1,101 @@
+// internal.h -- structures shared by the host side and the kernels of the
+// clight library (not part of the public ABI).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/clight.h"
+
+namespace clight {
+
+constexpr int kMaxLayers = 8;
+constexpr int kMaxCells = 64;
+constexpr int kGLNodes = 4;
+
+// One altitude cell of the ray quadrature: inside it the density is
+// rho = B exp(-h/c) of a single layer, so delta = kb 2^(h nl2c) and
+// rho/rho_ref = rb 2^(h nl2c).
+struct DevCell {
+    float lo, hi, kb, rb, nl2c, pad0, pad1, pad2;
+};
+
+// Atmosphere as the kernels see it (passed by value as a kernel parameter,
+// so every access is a uniform constant-bank read).
+struct DevAtm {
+    int n_layers, n_cells, spherical, refraction, absorption, pad;
+    float h_lo[kMaxLayers], kb[kMaxLayers], rb[kMaxLayers], nl2c[kMaxLayers];
+    double h_lo_d[kMaxLayers], kb_d[kMaxLayers], rb_d[kMaxLayers], inv_c_d[kMaxLayers];
+    float h_top, h_obs, R_E, r_obs;          // binary32 copies
+    double h_top_d, h_obs_d, R_E_d, r_obs_d;  // binary64 copies
+    float delta_obs, n_obs;                   // n(h_obs) - 1 and n(h_obs)
+    double delta_obs_d;
+    float inv_L0, lambda_ref;                 // tau = I * (lambda_ref/lambda)^4 * inv_L0
+    double inv_L0_d, lambda_ref_d;
+    float gl_x[kGLNodes], gl_w[kGLNodes];     // Gauss-Legendre on [-1, 1]
+    double gl_x_d[kGLNodes], gl_w_d[kGLNodes];
+    DevCell cells[kMaxCells];
+    double cell_lo_d[kMaxCells], cell_hi_d[kMaxCells], cell_kb_d[kMaxCells], cell_rb_d[kMaxCells],
+        cell_ic_d[kMaxCells];                 // binary64 copies; ic = 1/c
+};
+
+// Telescopes and their uniform grid (device pointers owned by the context).
+struct DevTel {
+    const float4 *tel;          // x, y, z, R
+    const int *cell_start;      // nx*ny + 1
+    const int *cell_tel;        // telescope indices, grouped by cell
+    int n_tel, nx, ny, pad;
+    float gx0, gy0, gs, inv_gs; // grid origin and cell size
+    float xmin, xmax, ymin, ymax, Rmax, zmin, zmax, pad2;
+};
+
+struct DevPar {
+    float band, inv_bunch;       // 2 pi alpha (1/l1 - 1/l2) [1/m], 1/B
+    double band_d, bunch_d;
+    float il1, dil;              // 1/lambda1, 1/lambda1 - 1/lambda2 (1/nm)
+    double il1_d, dil_d;
+    float fl1, fdl;              // fluorescence band start and width (nm)
+    double fl1_d, fdl_d;
+    float fyield;                // photons per MeV
+    double fyield_d;
+    uint32_t seed, stream;
+    int64_t seg_base;
+    int n_showers, seg_bits, k_bits, pad;
+    float bunch;
+};
+
+struct DevOut {
+    clight_hit *rec;             // unsorted hit records (scratch)
+    unsigned long long *keys;    // sort keys, parallel to rec
+    uint32_t *vals;              // 0..n-1
+    int64_t capacity;
+    unsigned long long *ctr;     // [0] work counter, [1] hit cursor, [2..9] stats
+};
+
+// Offsets inside DevOut::ctr.
+enum { CTR_WORK = 0, CTR_CURSOR = 1, CTR_STATS = 2, CTR_N = 16 };
+enum { ST_RAYS = 0, ST_ESCAPED, ST_UNDER, ST_TURNED, ST_REACHED, ST_HITS, ST_GUARDED, ST_STATUS, ST_CELLS };
+
+// kernel launchers (trace_kernels.cu)
+cudaError_t launch_trace_fused(const clight_segment *segs, int64_t n_segs, const DevAtm &A,
+                               const DevTel &T, const DevPar &P, const DevOut &O, int precision,
+                               int grid, int block, cudaStream_t s);
+cudaError_t launch_trace_fp64(const clight_segment *segs, int64_t n_segs, const DevAtm &A,
+                              const DevTel &T, const DevPar &P, const DevOut &O, cudaStream_t s);
+int fused_smem_bytes(int block);
+
+// sort and finalize (sort_kernels.cu)
+struct SortScratch {
+    unsigned long long *keys_alt;
+    uint32_t *vals_alt;
+    uint32_t *hist;              // 256 * max_tiles
+    uint32_t *block_sums;        // scan partials
+    int64_t max_tiles;
+    int64_t *gstart, *gend;      // per group
+};
+int sort_tile_items();
+int64_t scan_block_sums_needed(int64_t n);
+cudaError_t launch_sort_and_finalize(const DevOut &O, const SortScratch &S, int key_bits,
+                                     int group_shift, int64_t n_groups, clight_hit *out,
+                                     int64_t *counts, double *sums, cudaStream_t s);
+
+}  // namespace clight

@@ -1,0 +1,927 @@
+// trace_kernels.cu -- photon generation, refracted propagation and the
+// telescope hit test on sm_103a.
+//
+// Paper: Baack & Alameddine, "Comparison and efficiency of GPU accelerated
+// optical light propagation in CORSIKA 8" (ICRC 2023).
+//   Sec. 1.2      Frank-Tamm yield with its threshold, n constant over a step
+//   Sec. 1.1      fluorescence yield N = Y dE (Eq. 1), isotropic emission
+//   Sec. 1.2.1    cone vector p and the rotation M_Rod (here applied as
+//                 cos(theta_c) d + sin(theta_c)(cos c M x + sin c M y))
+//   Fig. 1        create at the origin, rotate, move to the emission point
+//   Sec. 2        propagation to the ground with refraction
+//
+// Propagation.  Sec. 2 runs a straight line and then applies refraction
+// corrections.  Here the correction is computed, not approximated: the
+// straight vacuum line from the emission point is intersected with the
+// observation level exactly (FP32 pairs), and the refracted ray's deviation
+// from it -- angle (or distance), optical path and optical depth -- comes
+// from the Snell / Bouguer invariant as integrals over altitude, written in
+// a form free of cancellation and evaluated by 4-node Gauss-Legendre on
+// altitude cells no wider than a fixed fraction of the local scale height.
+// The bulk of the arithmetic is binary32; FP32 pairs (or binary64, by
+// parameter) carry only the emission point, the vacuum path, the landing
+// point and the arrival time.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "df.cuh"
+#include "internal.h"
+
+namespace clight {
+
+#define FULL_MASK 0xffffffffu
+
+// ------------------------------------------------------------------ numerics
+template <class T> struct Num;
+template <> struct Num<float> {
+    static __device__ __forceinline__ float ex2(float x) { return exp2f(x); }
+    static __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+    static __device__ __forceinline__ float sqr(float x) { return sqrtf(x); }
+    static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+    static __device__ __forceinline__ void sincos2pi(float u, float *s, float *c) { sincospif(2.0f * u, s, c); }
+};
+template <> struct Num<double> {
+    static __device__ __forceinline__ double ex2(double x) { return exp2(x); }
+    static __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+    static __device__ __forceinline__ double sqr(double x) { return sqrt(x); }
+    static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+    static __device__ __forceinline__ void sincos2pi(double u, double *s, double *c) { sincospi(2.0 * u, s, c); }
+};
+
+template <class P> __device__ __forceinline__ P p_from(double x);
+template <> __device__ __forceinline__ df p_from<df>(double x) { return df_from_double(x); }
+template <> __device__ __forceinline__ double p_from<double>(double x) { return x; }
+template <class P> __device__ __forceinline__ P p_fromf(float x);
+template <> __device__ __forceinline__ df p_fromf<df>(float x) { return df_make(x); }
+template <> __device__ __forceinline__ double p_fromf<double>(float x) { return (double)x; }
+template <class P> __device__ __forceinline__ P p_fromd(double x);
+template <> __device__ __forceinline__ double p_fromd<double>(double x) { return x; }
+__device__ __forceinline__ float p_f(df a) { return __fadd_rn(a.hi, a.lo); }
+__device__ __forceinline__ float p_f(double a) { return (float)a; }
+__device__ __forceinline__ double p_d(df a) { return df_to_double(a); }
+__device__ __forceinline__ double p_d(double a) { return a; }
+__device__ __forceinline__ df p_sqrt(df a) { return df_sqrt(a); }
+__device__ __forceinline__ double p_sqrt(double a) { return sqrt(a); }
+template <class T> __device__ __forceinline__ T to_t(df a);
+template <> __device__ __forceinline__ float to_t<float>(df a) { return p_f(a); }
+template <class T> __device__ __forceinline__ T to_t(double a) { return (T)a; }
+
+// ------------------------------------------------------------------ Philox
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): per round two 32x32->64
+// products with 0xD2511F53 and 0xCD9E8D57, the Weyl key increments
+// 0x9E3779B9 and 0xBB67AE85.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// (m + 1/2) 2^-23 from the top 23 bits: exact in binary32 and binary64.
+template <class T> __device__ __forceinline__ T u01(uint32_t x)
+{
+    return (T)(x >> 9) * (T)1.1920928955078125e-07 + (T)5.9604644775390625e-08;
+}
+
+// ------------------------------------------------------------------ atmosphere
+template <class T> struct AtmT;
+template <> struct AtmT<float> {
+    static __device__ __forceinline__ float delta(const DevAtm &A, float h)
+    {
+        if (h >= A.h_top) return 0.0f;
+        int i = 0;
+#pragma unroll
+        for (int j = 1; j < kMaxLayers; ++j)
+            if (j < A.n_layers && h >= A.h_lo[j]) i = j;
+        return A.kb[i] * exp2f(h * A.nl2c[i]);
+    }
+};
+template <> struct AtmT<double> {
+    static __device__ __forceinline__ double delta(const DevAtm &A, double h)
+    {
+        if (h >= A.h_top_d) return 0.0;
+        int i = 0;
+        for (int j = 1; j < A.n_layers; ++j)
+            if (h >= A.h_lo_d[j]) i = j;
+        return A.kb_d[i] * exp(-h * A.inv_c_d[i]);
+    }
+};
+
+// Altitude without cancellation: |r + R_E z| - R_E = (x^2 + y^2 + z (z + 2 R_E)) / (|r + R_E z| + R_E).
+template <class T> __device__ __forceinline__ T altitude(const DevAtm &A, T x, T y, T z)
+{
+    if (!A.spherical) return z;
+    const T RE = (T)A.R_E_d;
+    T num = x * x + y * y + z * (z + (T)2 * RE);
+    T zc = z + RE;
+    return num / (Num<T>::sqr(x * x + y * y + zc * zc) + RE);
+}
+
+// ------------------------------------------------------------------ segment
+// Everything one track step contributes to its photons (Sec. 1.2: the
+// atmosphere is homogeneous over a step, so theta_c and the yield are
+// per-step quantities).
+template <class T, class P> struct Seg {
+    P x0, y0, z0, t0;
+    T dx, dy, dz;        // unit direction (binary32 part)
+    T lx, ly, lz;        // its normalisation correction (pair low part)
+    T e1x, e1y, e1z, e2x, e2y, e2z;   // M_Rod x, M_Rod y
+    T sin_tc, kappa;     // sin(theta_c), 1 - cos(theta_c)
+    T L, inv_bc;         // step length, 1/(beta c) in ns/m
+    T w_c, w_f;
+    uint32_t n_c, n_f;
+    uint32_t shower;
+    int bad;             // 0 ok, else CLIGHT_ERR_* code
+    int guarded;
+};
+
+constexpr double kInvC = 3.3356409519815204;    // ns/m
+
+__device__ __forceinline__ bool finite_f(float v) { return isfinite(v); }
+
+// Yield and bunch count in binary64 (the plain path, and the guard of the
+// FP32 path when its count is not certain).  Frank-Tamm (Sec. 1.2):
+// N = 2 pi alpha z^2 (1/l1 - 1/l2) (1 - 1/(beta n)^2) L for beta n > 1.
+__device__ __forceinline__ void yield_fp64(const clight_segment &s, const DevAtm &A, const DevPar &P,
+                                           double ux, double uy, double uz, double *Nc, double *sin2,
+                                           double *cos_tc, double *Nf)
+{
+    double xm = s.x + 0.5 * (double)s.L * ux, ym = s.y + 0.5 * (double)s.L * uy,
+           zm = s.z + 0.5 * (double)s.L * uz;
+    double h;
+    if (A.spherical) {
+        double zc = zm + A.R_E_d;
+        h = sqrt(xm * xm + ym * ym + zc * zc) - A.R_E_d;
+    } else {
+        h = zm;
+    }
+    double dl = AtmT<double>::delta(A, h);
+    double bn = (1.0 - (double)s.eps) * (1.0 + dl);
+    double z2 = (double)s.charge * (double)s.charge;
+    *Nc = 0.0;
+    *sin2 = 0.0;
+    *cos_tc = 1.0;
+    if (z2 > 0.0 && bn > 1.0 && s.L > 0.0f) {
+        *cos_tc = 1.0 / bn;
+        *sin2 = 1.0 - 1.0 / (bn * bn);
+        *Nc = P.band_d * z2 * (*sin2) * (double)s.L;
+    }
+    *Nf = (P.fyield_d > 0.0 && s.dE > 0.0f && s.L > 0.0f) ? P.fyield_d * (double)s.dE : 0.0;
+}
+
+template <class T, class P>
+__device__ __forceinline__ void make_frame(Seg<T, P> &g)
+{
+    // A = unit bisector of the flight direction and -z; M x = 2 A_x A - x,
+    // M y = 2 A_y A - y (columns of M_Rod = 2 A A^T - 1).
+    T ax = g.dx, ay = g.dy, az = g.dz - (T)1;
+    T na2 = ax * ax + ay * ay + az * az;
+    if (na2 > (T)0) {
+        T inv = Num<T>::rsq(na2);
+        ax *= inv; ay *= inv; az *= inv;
+    } else {
+        ax = (T)1; ay = (T)0; az = (T)0;
+    }
+    g.e1x = (T)2 * ax * ax - (T)1; g.e1y = (T)2 * ax * ay;        g.e1z = (T)2 * ax * az;
+    g.e2x = (T)2 * ay * ax;        g.e2y = (T)2 * ay * ay - (T)1; g.e2z = (T)2 * ay * az;
+}
+
+// binary32 segment set-up with the binary64 guard on the integer bunch count.
+__device__ void load_segment_f(const clight_segment &s, const DevAtm &A, const DevPar &P,
+                               Seg<float, df> &g)
+{
+    g.bad = 0;
+    g.guarded = 0;
+    g.n_c = g.n_f = 0;
+    g.w_c = g.w_f = 0.0f;
+    g.shower = s.shower;
+    bool ok = isfinite(s.x) && isfinite(s.y) && isfinite(s.z) && isfinite(s.t0) && finite_f(s.dx) &&
+              finite_f(s.dy) && finite_f(s.dz) && finite_f(s.L) && finite_f(s.eps) && finite_f(s.dE) &&
+              s.L >= 0.0f && s.eps >= 0.0f && s.eps < 1.0f && (int)s.shower < P.n_showers &&
+              s.shower < 0x7fffffffu;
+    float n2 = s.dx * s.dx + s.dy * s.dy + s.dz * s.dz;
+    if (!ok || !(n2 > 0.0f)) {
+        g.bad = CLIGHT_ERR_BAD_SEGMENT;
+        g.dx = 0; g.dy = 0; g.dz = -1; g.lx = g.ly = g.lz = 0;
+        g.x0 = g.y0 = g.z0 = g.t0 = df_make(0.0f);
+        g.L = 0; g.inv_bc = 0; g.sin_tc = 0; g.kappa = 0;
+        make_frame(g);
+        return;
+    }
+    // unit direction as a pair: d (1 - e/2 + 3 e^2/8), e = |d|^2 - 1 exactly
+    df sq = two_prod(s.dx, s.dx) + two_prod(s.dy, s.dy) + two_prod(s.dz, s.dz);
+    float e = p_f(sq - 1.0f);
+    float f = 1.0f / sqrtf(1.0f + e);            // normalisation of the binary32 part
+    g.dx = s.dx * f; g.dy = s.dy * f; g.dz = s.dz * f;
+    // residual of the rounded unit vector (pair low part)
+    df r2 = two_prod(g.dx, g.dx) + two_prod(g.dy, g.dy) + two_prod(g.dz, g.dz);
+    float e2 = p_f(r2 - 1.0f);
+    g.lx = -0.5f * e2 * g.dx; g.ly = -0.5f * e2 * g.dy; g.lz = -0.5f * e2 * g.dz;
+    g.x0 = df_from_double(s.x);
+    g.y0 = df_from_double(s.y);
+    g.z0 = df_from_double(s.z);
+    g.t0 = df_from_double(s.t0);
+    g.L = s.L;
+    g.inv_bc = 3.3356409519815204f / (1.0f - s.eps);      // 1/(beta c), ns/m
+    make_frame(g);
+
+    // midpoint altitude and refractivity (n constant over the step)
+    float hL = 0.5f * s.L;
+    float xm = (float)s.x + hL * g.dx, ym = (float)s.y + hL * g.dy, zm = (float)s.z + hL * g.dz;
+    float hm = altitude<float>(A, xm, ym, zm);
+    float dl = AtmT<float>::delta(A, hm);
+    float eps = s.eps;
+    float z2 = (float)s.charge * (float)s.charge;
+    // beta n - 1 = delta - eps - eps delta, kept as a small number
+    float g1 = __fmaf_rn(-eps, dl, dl - eps);
+    // error bound of g1 (delta known to ~1.5e-6 relative; generous factor)
+    float eg = 4.0e-6f * dl + 2.4e-7f * (dl + eps);
+    bool guard = false;
+    float Nc = 0.0f;
+    if (z2 > 0.0f && s.L > 0.0f) {
+        if (g1 > eg) {
+            float bn = 1.0f + g1;
+            float sin2 = g1 * (2.0f + g1) / (bn * bn);
+            Nc = P.band * z2 * sin2 * s.L;
+            g.sin_tc = sqrtf(sin2);
+            g.kappa = g1 / bn;
+            float x = Nc * P.inv_bunch;
+            float ex = x * (eg / g1 * 2.0f + 2.0e-6f) + 1.0e-6f;
+            if (ceilf(x - ex) != ceilf(x + ex)) guard = true;
+            else g.n_c = (uint32_t)ceilf(x);
+        } else if (g1 > -eg) {
+            guard = true;
+        }
+    }
+    if (!guard && g.n_c == 0) { g.sin_tc = 0.0f; g.kappa = 0.0f; }
+    float Nf = 0.0f;
+    bool fguard = false;
+    if (P.fyield > 0.0f && s.dE > 0.0f && s.L > 0.0f) {
+        Nf = P.fyield * s.dE;
+        float x = Nf * P.inv_bunch;
+        float ex = x * 1.0e-6f + 1.0e-7f;
+        if (ceilf(x - ex) != ceilf(x + ex)) fguard = true;
+        else g.n_f = (uint32_t)ceilf(x);
+    }
+    if (guard || fguard) {
+        g.guarded = 1;
+        double Ncd, sin2d, cosd, Nfd;
+        yield_fp64(s, A, P, (double)g.dx + (double)g.lx, (double)g.dy + (double)g.ly,
+                   (double)g.dz + (double)g.lz, &Ncd, &sin2d, &cosd, &Nfd);
+        if (guard) {
+            double nb = ceil(Ncd / P.bunch_d);
+            g.n_c = (uint32_t)nb;
+            Nc = (float)Ncd;
+            g.sin_tc = (float)sqrt(sin2d);
+            g.kappa = (float)(1.0 - cosd);
+            if (g.n_c > 0) g.w_c = (float)(Ncd / nb);
+        }
+        if (fguard) {
+            double nb = ceil(Nfd / P.bunch_d);
+            g.n_f = (uint32_t)nb;
+            Nf = (float)Nfd;
+            if (g.n_f > 0) g.w_f = (float)(Nfd / nb);
+        }
+    }
+    if (!guard && g.n_c > 0) g.w_c = Nc / (float)g.n_c;
+    if (!fguard && g.n_f > 0) g.w_f = Nf / (float)g.n_f;
+}
+
+// binary64 segment set-up (plain path).
+__device__ void load_segment_d(const clight_segment &s, const DevAtm &A, const DevPar &P,
+                               Seg<double, double> &g)
+{
+    g.bad = 0;
+    g.guarded = 0;
+    g.n_c = g.n_f = 0;
+    g.w_c = g.w_f = 0.0;
+    g.shower = s.shower;
+    bool ok = isfinite(s.x) && isfinite(s.y) && isfinite(s.z) && isfinite(s.t0) && finite_f(s.dx) &&
+              finite_f(s.dy) && finite_f(s.dz) && finite_f(s.L) && finite_f(s.eps) && finite_f(s.dE) &&
+              s.L >= 0.0f && s.eps >= 0.0f && s.eps < 1.0f && (int)s.shower < P.n_showers &&
+              s.shower < 0x7fffffffu;
+    double n2 = (double)s.dx * s.dx + (double)s.dy * s.dy + (double)s.dz * s.dz;
+    if (!ok || !(n2 > 0.0)) {
+        g.bad = CLIGHT_ERR_BAD_SEGMENT;
+        return;
+    }
+    double inv = 1.0 / sqrt(n2);
+    g.dx = s.dx * inv; g.dy = s.dy * inv; g.dz = s.dz * inv;
+    g.lx = g.ly = g.lz = 0.0;
+    g.x0 = s.x; g.y0 = s.y; g.z0 = s.z; g.t0 = s.t0;
+    g.L = s.L;
+    g.inv_bc = kInvC / (1.0 - (double)s.eps);
+    make_frame(g);
+    double Nc, sin2, cos_tc, Nf;
+    yield_fp64(s, A, P, g.dx, g.dy, g.dz, &Nc, &sin2, &cos_tc, &Nf);
+    g.sin_tc = sqrt(sin2);
+    g.kappa = 1.0 - cos_tc;
+    if (Nc > 0.0) {
+        double nb = ceil(Nc / P.bunch_d);
+        g.n_c = (uint32_t)nb;
+        g.w_c = Nc / nb;
+    }
+    if (Nf > 0.0) {
+        double nb = ceil(Nf / P.bunch_d);
+        g.n_f = (uint32_t)nb;
+        g.w_f = Nf / nb;
+    }
+}
+
+// ------------------------------------------------------------------ one ray
+template <class T, class P> struct RayOut {
+    P X, Y;            // crossing of the plane z = h_obs
+    P t;               // arrival time there
+    T cx, cy, cz;      // arrival direction
+    T lambda, weight;
+    int status;        // 0 reached, 1 escaped, 2 under, 3 turned
+    uint32_t cells;    // quadrature cells integrated
+};
+
+// Quadrature of the refracted ray's deviation from the vacuum line.
+//   I0: integral whose p_v multiple is the angle (spherical) or horizontal
+//       distance (flat) the refracted ray falls short of the vacuum line;
+//   I1: optical path minus vacuum path length;
+//   I2: density-weighted path (rho / rho_ref) ds.
+// r = R_E + h (spherical) or 1 (flat); q_v = r^2 - p_v^2,
+// q = n^2 q_v + (n^2 - n_e^2) p_v^2 = n^2 r^2 - (n_e p_v)^2.
+template <class T, bool WARP>
+__device__ __forceinline__ void ray_quadrature(const DevAtm &A, T hcap, T he, T de, T pv2, T bf2,
+                                               bool sph, bool refr, T &I0, T &I1, T &I2, uint32_t &ncell)
+{
+    I0 = I1 = I2 = (T)0;
+    const T RE = (T)A.R_E_d;
+    const T ne = (T)1 + de;
+    for (int c = 0; c < A.n_cells; ++c) {
+        const DevCell &C = A.cells[c];
+        T lo = sizeof(T) == 4 ? (T)C.lo : (T)A.cell_lo_d[c];
+        bool act = hcap > lo;
+        if (WARP) {
+            if (!__any_sync(FULL_MASK, act)) break;
+        } else {
+            if (!act) break;
+        }
+        if (!act) continue;
+        ++ncell;
+        T chi = sizeof(T) == 4 ? (T)C.hi : (T)A.cell_hi_d[c];
+        T hi = hcap < chi ? hcap : chi;
+        T mid = (T)0.5 * (lo + hi), half = (T)0.5 * (hi - lo);
+        T kb = sizeof(T) == 4 ? (T)C.kb : (T)A.cell_kb_d[c];
+        T rb = sizeof(T) == 4 ? (T)C.rb : (T)A.cell_rb_d[c];
+        T nl = sizeof(T) == 4 ? (T)C.nl2c : (T)-A.cell_ic_d[c];
+        T s0 = 0, s1 = 0, s2 = 0;
+#pragma unroll
+        for (int gi = 0; gi < kGLNodes; ++gi) {
+            T xg, wg;
+            if (sizeof(T) == 4) { xg = (T)A.gl_x[gi]; wg = (T)A.gl_w[gi]; }
+            else { xg = (T)A.gl_x_d[gi]; wg = (T)A.gl_w_d[gi]; }
+            T h = mid + half * xg;
+            // float: 2^(h nl) with nl = -log2(e)/c; double: e^(h nl) with nl = -1/c
+            T ex = sizeof(T) == 4 ? (T)Num<float>::ex2((float)(h * nl)) : (T)exp((double)(h * nl));
+            T dl = kb * ex;
+            T rr = rb * ex;
+            T r = sph ? RE + h : (T)1;
+            T qv = sph ? (h - he) * ((T)2 * RE + h + he) + bf2 : bf2;
+            if (refr) {
+                T n = (T)1 + dl;
+                T n2 = n * n;
+                T gg = (dl - de) * ((T)2 + dl + de);          // n^2 - n_e^2
+                T q = n2 * qv + gg * pv2;
+                T rq = Num<T>::rsq(q), rqv = Num<T>::rsq(qv);
+                T sq = q * rq, sqv = qv * rqv;
+                T cm = rq * rqv;
+                T a = dl * ((T)2 + dl);                         // n^2 - 1
+                s0 += wg * (-r * gg * cm / (ne * sqv + sq));
+                s1 += wg * (r * (n2 * a * qv - gg * pv2) * cm / (n2 * sqv + sq));
+                s2 += wg * (rr * n * r * rq);
+            } else {
+                T rqv = Num<T>::rsq(qv);
+                s1 += wg * (dl * r * rqv);
+                s2 += wg * (rr * r * rqv);
+            }
+        }
+        I0 += s0 * half;
+        I1 += s1 * half;
+        I2 += s2 * half;
+    }
+}
+
+template <class T, class P, bool WARP>
+__device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global, uint32_t k, bool active,
+                                          const DevAtm &A, const DevPar &Pp, RayOut<T, P> &o)
+{
+    // ---- generation (Sec. 1.1, 1.2, 1.2.1; Fig. 1)
+    uint32_t proc = k < g.n_c ? 0u : 1u;
+    uint32_t kk = proc ? k - g.n_c : k;
+    uint4 x = philox4x32_10(make_uint4((uint32_t)(uint64_t)seg_global,
+                                       (uint32_t)((uint64_t)seg_global >> 32), kk, proc),
+                            Pp.seed, Pp.stream);
+    T u0 = u01<T>(x.x), u1 = u01<T>(x.y), u2 = u01<T>(x.z), u3 = u01<T>(x.w);
+    P dgx, dgy, dgz;
+    T lam, w;
+    if (proc == 0) {
+        T il1 = sizeof(T) == 4 ? (T)Pp.il1 : (T)Pp.il1_d;
+        T dil = sizeof(T) == 4 ? (T)Pp.dil : (T)Pp.dil_d;
+        lam = (T)1 / (il1 - u0 * dil);                     // density ~ 1/lambda^2
+        T sc, cc;
+        Num<T>::sincos2pi(u2, &sc, &cc);
+        T st = g.sin_tc;
+        T sx = -g.kappa * g.dx + st * (cc * g.e1x + sc * g.e2x);
+        T sy = -g.kappa * g.dy + st * (cc * g.e1y + sc * g.e2y);
+        T sz = -g.kappa * g.dz + st * (cc * g.e1z + sc * g.e2z);
+        // cos(theta_c) d + sin(theta_c)(cos c e1 + sin c e2), d kept as a pair
+        dgx = p_fromf<P>(g.dx) + (g.lx + sx);
+        dgy = p_fromf<P>(g.dy) + (g.ly + sy);
+        dgz = p_fromf<P>(g.dz) + (g.lz + sz);
+        w = g.w_c;
+    } else {
+        T fl1 = sizeof(T) == 4 ? (T)Pp.fl1 : (T)Pp.fl1_d;
+        T fdl = sizeof(T) == 4 ? (T)Pp.fdl : (T)Pp.fdl_d;
+        lam = fl1 + u0 * fdl;
+        T cz = (T)2 * u3 - (T)1;                            // exact
+        T sz = Num<T>::sqr(((T)1 - cz) * ((T)1 + cz));
+        T sp, cp;
+        Num<T>::sincos2pi(u2, &sp, &cp);
+        dgx = p_fromf<P>(0.0f) + sz * cp;
+        dgy = p_fromf<P>(0.0f) + sz * sp;
+        dgz = p_fromf<P>(0.0f) + cz;
+        w = g.w_f;
+    }
+    T ell = u1 * g.L;
+    P xe = g.x0 + ell * (g.dx + g.lx);
+    P ye = g.y0 + ell * (g.dy + g.ly);
+    P ze = g.z0 + ell * (g.dz + g.lz);
+    P te = g.t0 + ell * g.inv_bc;
+    o.lambda = lam;
+    o.status = 0;
+
+    T dx = to_t<T>(dgx), dy = to_t<T>(dgy), dz = to_t<T>(dgz);
+    T xef = to_t<T>(xe), yef = to_t<T>(ye), zef = to_t<T>(ze);
+    const bool sph = A.spherical != 0, refr = A.refraction != 0;
+    const T h_obs = sizeof(T) == 4 ? (T)A.h_obs : (T)A.h_obs_d;
+    const T RE = (T)A.R_E_d;
+    const P Hobs = p_from<P>(A.h_obs_d);          // exact constants for the pair arithmetic
+    const P REp = p_from<P>(A.R_E_d);
+    const P K2 = p_from<P>(A.h_obs_d + 2.0 * A.R_E_d);
+
+    // ---- vacuum straight line to the observation level (exact geometry)
+    P s_v, Pvx, Pvy, Pvz, sqd;
+    T he, pv2, bf2, bf;
+    bool esc = false, under = false, turned = false;
+    if (sph) {
+        P Rz = ze + REp;
+        // b = -(d . R_e) = r_e cos(psi_e)
+        P b = -(dgz * Rz) - (dx * xef + dy * yef);
+        he = altitude<T>(A, xef, yef, zef);
+        esc = !(p_f(b) > 0.0f);
+        under = he <= h_obs;
+        P dzo = ze - Hobs;
+        P C = dzo * (ze + K2) + (xef * xef + yef * yef);
+        P disc = b * b - C;
+        turned = !(p_f(disc) > 0.0f);
+        if (!(esc || under || turned)) {
+            sqd = p_sqrt(disc);
+            s_v = C / (b + sqd);
+        } else {
+            sqd = p_fromf<P>(0.0f);
+            s_v = p_fromf<P>(0.0f);
+        }
+        T Rzf = to_t<T>(Rz);
+        T c1 = dy * Rzf - dz * yef, c2 = dz * xef - dx * Rzf, c3 = dx * yef - dy * xef;
+        pv2 = c1 * c1 + c2 * c2 + c3 * c3;                   // (r_e sin psi_e)^2
+        bf = to_t<T>(b);
+        bf2 = bf * bf;                                       // (r_e cos psi_e)^2
+    } else {
+        he = zef;
+        esc = !(p_f(dgz) < 0.0f);
+        under = !(p_f(ze - Hobs) > 0.0f);
+        if (!(esc || under)) s_v = (ze - Hobs) / (-dgz);
+        else s_v = p_fromf<P>(0.0f);
+        pv2 = dx * dx + dy * dy;                             // sin^2 theta_e
+        bf = -dz;
+        bf2 = bf * bf;                                       // cos^2 theta_e
+        sqd = p_fromf<P>(0.0f);
+    }
+    if (!active) { o.status = 4; }
+    else if (esc) { o.status = 1; }
+    else if (under) { o.status = 2; }
+    else if (turned) { o.status = 3; }
+    bool go = o.status == 0;
+
+    // ---- refraction, optical path and optical depth by quadrature
+    T de = AtmT<T>::delta(A, he);
+    T htop = sizeof(T) == 4 ? (T)A.h_top : (T)A.h_top_d;
+    T hcap = go ? (he < htop ? he : htop) : (T)-1e30;
+    T I0, I1, I2;
+    o.cells = 0;
+    ray_quadrature<T, WARP>(A, hcap, he, de, pv2, bf2, sph, refr, I0, I1, I2, o.cells);
+    if (!go) return;
+
+    const T n_obs = sizeof(T) == 4 ? (T)A.n_obs : (T)1 + (T)A.delta_obs_d;
+    const T d_obs = sizeof(T) == 4 ? (T)A.delta_obs : (T)A.delta_obs_d;
+    const T ne = (T)1 + de;
+    T dLx, dLy, dLz;
+    P X, Y, tt;
+    T chord = 0;
+    if (sph) {
+        const T r_obs = (T)A.r_obs_d;
+        Pvx = xe + s_v * dgx;
+        Pvy = ye + s_v * dgy;
+        Pvz = ze + s_v * dgz;
+        T RLx = to_t<T>(Pvx), RLy = to_t<T>(Pvy), RLz = to_t<T>(Pvz + REp);
+        T sqf = to_t<T>(sqd);                                // r_obs cos(psi) of the vacuum line
+        T ir = (T)1 / r_obs;
+        // T_v = r_obs d + cos(psi_v) R_L: in-plane tangent scaled by p_v
+        T Tx = r_obs * dx + sqf * ir * RLx, Ty = r_obs * dy + sqf * ir * RLy, Tz = r_obs * dz + sqf * ir * RLz;
+        T Rhx = RLx * ir, Rhy = RLy * ir, Rhz = RLz * ir;
+        P PLx = Pvx, PLy = Pvy, PLz = Pvz;
+        if (refr) {
+            T pv = Num<T>::sqr(pv2);
+            T dphi = I0 * pv;
+            T sfac = r_obs * I0;                              // r_obs dphi / p_v
+            T c2 = (T)0.5 * r_obs * dphi * dphi;
+            PLx = Pvx + (sfac * Tx - c2 * Rhx);
+            PLy = Pvy + (sfac * Ty - c2 * Rhy);
+            PLz = Pvz + (sfac * Tz - c2 * Rhz);
+            T qvL = sqf * sqf;
+            T gL = (d_obs - de) * ((T)2 + d_obs + de);
+            T qL = n_obs * n_obs * qvL + gL * pv2;
+            T inr = (T)1 / (n_obs * r_obs);
+            T cpsi = Num<T>::sqr(qL) * inr;
+            T spsi = ne * pv * inr;
+            T at = ne * inr - cpsi * I0;
+            T ar = cpsi + spsi * dphi;
+            dLx = at * Tx - ar * Rhx;
+            dLy = at * Ty - ar * Rhy;
+            dLz = at * Tz - ar * Rhz;
+        } else {
+            dLx = dx; dLy = dy; dLz = dz;
+        }
+        // from the observation sphere back to the tangent plane z = h_obs
+        T zeta = -to_t<T>(PLz - Hobs);
+        chord = zeta / dLz;
+        X = PLx + chord * dLx;
+        Y = PLy + chord * dLy;
+    } else {
+        X = xe + s_v * dgx;
+        Y = ye + s_v * dgy;
+        if (refr) {
+            X = X + I0 * dx;
+            Y = Y + I0 * dy;
+            T qL = n_obs * n_obs * bf2 + (d_obs - de) * ((T)2 + d_obs + de) * pv2;
+            T f = ne / n_obs;
+            dLx = f * dx;
+            dLy = f * dy;
+            dLz = -Num<T>::sqr(qL) / n_obs;
+        } else {
+            dLx = dx; dLy = dy; dLz = dz;
+        }
+    }
+    // time: t_e + (vacuum path + optical excess + chord) / c
+    const T invc = (T)kInvC;
+    P sv_t = s_v * p_from<P>(kInvC);
+    tt = te + sv_t + (I1 + n_obs * chord) * invc;
+    T tau = 0;
+    if (A.absorption) {
+        T lr = (sizeof(T) == 4 ? (T)A.lambda_ref : (T)A.lambda_ref_d) / lam;
+        T lr2 = lr * lr;
+        tau = I2 * lr2 * lr2 * (sizeof(T) == 4 ? (T)A.inv_L0 : (T)A.inv_L0_d);
+    }
+    o.X = X;
+    o.Y = Y;
+    o.t = tt;
+    o.cx = dLx; o.cy = dLy; o.cz = dLz;
+    o.weight = A.absorption ? w * (sizeof(T) == 4 ? (T)expf((float)-tau) : (T)exp((double)-tau)) : w;
+}
+
+// ------------------------------------------------------------------ hits
+__device__ __forceinline__ void write_hit(const DevOut &O, unsigned long long idx, int64_t seg, uint32_t k,
+                                          uint32_t tel, float xr, float yr, float cx, float cy, float lam,
+                                          float w, double t, unsigned long long key)
+{
+    if ((int64_t)idx >= O.capacity) return;
+    float4 *p = reinterpret_cast<float4 *>(O.rec + idx);
+    uint32_t slo = (uint32_t)(uint64_t)seg, shi = (uint32_t)((uint64_t)seg >> 32);
+    p[0] = make_float4(__uint_as_float(slo), __uint_as_float(shi), __uint_as_float(k), __uint_as_float(tel));
+    p[1] = make_float4(xr, yr, cx, cy);
+    unsigned long long tb = (unsigned long long)__double_as_longlong(t);
+    p[2] = make_float4(lam, w, __uint_as_float((uint32_t)tb), __uint_as_float((uint32_t)(tb >> 32)));
+    O.keys[idx] = key;
+    O.vals[idx] = (uint32_t)idx;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Test the arrival line against the telescopes near the crossing point and
+// append every hit.  A sphere of radius R is hit when the line passes closer
+// than R to its centre; its centre can then lie at most R / |cz| from the
+// crossing point, which bounds the cells searched.
+template <class T, class P, bool WARP>
+__device__ __forceinline__ int hit_test(const RayOut<T, P> &o, int64_t seg_local, int64_t seg_global, uint32_t k,
+                                        uint32_t shower, const DevAtm &A, const DevTel &Tl, const DevPar &Pp,
+                                        const DevOut &O, unsigned &status_bits)
+{
+    if (o.status != 0) return 0;
+    float Xf = (float)p_d(o.X), Yf = (float)p_d(o.Y);
+    float cz = (float)o.cz, cx = (float)o.cx, cy = (float)o.cy;
+    if (!(isfinite(Xf) && isfinite(Yf) && cz < 0.0f)) return 0;
+    float acz = fabsf(cz);
+    float dzmax = fmaxf(fabsf(Tl.zmax - A.h_obs), fabsf(Tl.zmin - A.h_obs));
+    float rs = (Tl.Rmax + dzmax * sqrtf(fmaxf(0.0f, 1.0f - acz * acz))) / fmaxf(acz, 1e-6f) + 1e-3f;
+    if (Xf + rs < Tl.xmin || Xf - rs > Tl.xmax || Yf + rs < Tl.ymin || Yf - rs > Tl.ymax) return 0;
+    int ix0 = max(0, (int)floorf((Xf - rs - Tl.gx0) * Tl.inv_gs));
+    int ix1 = min(Tl.nx - 1, (int)floorf((Xf + rs - Tl.gx0) * Tl.inv_gs));
+    int iy0 = max(0, (int)floorf((Yf - rs - Tl.gy0) * Tl.inv_gs));
+    int iy1 = min(Tl.ny - 1, (int)floorf((Yf + rs - Tl.gy0) * Tl.inv_gs));
+    int nh = 0;
+    const double h_obs = A.h_obs_d;
+    for (int iy = iy0; iy <= iy1; ++iy) {
+        for (int ix = ix0; ix <= ix1; ++ix) {
+            int cell = iy * Tl.nx + ix;
+            int b = __ldg(Tl.cell_start + cell), e = __ldg(Tl.cell_start + cell + 1);
+            for (int q = b; q < e; ++q) {
+                int j = __ldg(Tl.cell_tel + q);
+                float4 tp = __ldg(Tl.tel + j);
+                // crossing point relative to the centre, at the plane z = z_j
+                float dzj = tp.z - (float)h_obs;
+                float sj = dzj / cz;
+                float xr = p_f(o.X - (T)tp.x) + sj * cx;
+                float yr = p_f(o.Y - (T)tp.y) + sj * cy;
+                // impact parameter
+                float wx = -xr, wy = -yr;                       // centre minus crossing point
+                float wd = wx * cx + wy * cy;
+                float d2 = wx * wx + wy * wy - wd * wd;
+                if (d2 < tp.w * tp.w) {
+                    ++nh;
+                    double tj = p_d(o.t) + (double)(A.n_obs * sj) * kInvC;
+                    uint32_t group = shower * (uint32_t)Tl.n_tel + (uint32_t)j;
+                    unsigned long long key;
+                    if (Pp.k_bits < 32 && k >= (1u << Pp.k_bits)) {
+                        status_bits |= 1u << CLIGHT_ERR_LIMIT;
+                        key = ~0ull;
+                    } else {
+                        key = ((unsigned long long)group << (Pp.seg_bits + Pp.k_bits)) |
+                              ((unsigned long long)seg_local << Pp.k_bits) | (unsigned long long)k;
+                    }
+                    unsigned long long idx;
+                    if (WARP) {
+                        unsigned m = __activemask();
+                        int leader = __ffs(m) - 1;
+                        unsigned long long base = 0;
+                        if ((int)(threadIdx.x & 31) == leader) base = atomicAdd(O.ctr + CTR_CURSOR, (unsigned long long)__popc(m));
+                        base = __shfl_sync(m, base, leader);
+                        idx = base + __popc(m & lanemask_lt());
+                    } else {
+                        idx = atomicAdd(O.ctr + CTR_CURSOR, 1ull);
+                    }
+                    write_hit(O, idx, seg_global, k, (uint32_t)j, xr, yr, cx, cy, (float)o.lambda,
+                              (float)o.weight, tj, key);
+                }
+            }
+        }
+    }
+    return nh;
+}
+
+// ------------------------------------------------------------------ fused kernel
+// Shared-memory record of a warp's 32 segments, one field per row so that
+// lanes reading one field of different segments hit different banks.
+enum SegField {
+    F_X0H, F_X0L, F_Y0H, F_Y0L, F_Z0H, F_Z0L, F_T0H, F_T0L,
+    F_DX, F_DY, F_DZ, F_LX, F_LY, F_LZ, F_E1X, F_E1Y, F_E1Z, F_E2X, F_E2Y, F_E2Z,
+    F_SIN, F_KAP, F_L, F_IBC, F_WC, F_WF, F_NC, F_NF, F_SHOWER, F_INCL, F_COUNT
+};
+
+int fused_smem_bytes(int block) { return (block / 32) * F_COUNT * 32 * (int)sizeof(float); }
+
+template <class P> struct PStore;
+template <> struct PStore<df> {
+    static __device__ __forceinline__ void put(float *row_h, float *row_l, int l, df v) { row_h[l] = v.hi; row_l[l] = v.lo; }
+    static __device__ __forceinline__ df get(const float *row_h, const float *row_l, int l) { return {row_h[l], row_l[l]}; }
+};
+template <> struct PStore<double> {
+    static __device__ __forceinline__ void put(float *row_h, float *row_l, int l, double v)
+    {
+        unsigned long long b = (unsigned long long)__double_as_longlong(v);
+        row_h[l] = __uint_as_float((uint32_t)b);
+        row_l[l] = __uint_as_float((uint32_t)(b >> 32));
+    }
+    static __device__ __forceinline__ double get(const float *row_h, const float *row_l, int l)
+    {
+        unsigned long long b = (unsigned long long)__float_as_uint(row_h[l]) |
+                               ((unsigned long long)__float_as_uint(row_l[l]) << 32);
+        return __longlong_as_double((long long)b);
+    }
+};
+
+__device__ __forceinline__ Seg<float, double> to_fp64_guard(const Seg<float, df> &a)
+{
+    Seg<float, double> b;
+    b.x0 = df_to_double(a.x0); b.y0 = df_to_double(a.y0); b.z0 = df_to_double(a.z0); b.t0 = df_to_double(a.t0);
+    b.dx = a.dx; b.dy = a.dy; b.dz = a.dz; b.lx = a.lx; b.ly = a.ly; b.lz = a.lz;
+    b.e1x = a.e1x; b.e1y = a.e1y; b.e1z = a.e1z; b.e2x = a.e2x; b.e2y = a.e2y; b.e2z = a.e2z;
+    b.sin_tc = a.sin_tc; b.kappa = a.kappa; b.L = a.L; b.inv_bc = a.inv_bc; b.w_c = a.w_c; b.w_f = a.w_f;
+    b.n_c = a.n_c; b.n_f = a.n_f; b.shower = a.shower; b.bad = a.bad; b.guarded = a.guarded;
+    return b;
+}
+
+template <class P>
+__global__ void __launch_bounds__(256, 2)
+k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid_constant__ DevAtm A,
+              const __grid_constant__ DevTel Tl, const __grid_constant__ DevPar Pp, const __grid_constant__ DevOut O)
+{
+    extern __shared__ float smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float *S = smem + warp * (F_COUNT * 32);
+    uint32_t c_rays = 0, c_esc = 0, c_under = 0, c_turn = 0, c_reach = 0, c_hits = 0, c_guard = 0, c_cells = 0;
+    unsigned status_bits = 0;
+    for (;;) {
+        unsigned long long grp = 0;
+        if (lane == 0) grp = atomicAdd(O.ctr + CTR_WORK, 1ull);
+        grp = __shfl_sync(FULL_MASK, grp, 0);
+        int64_t s_first = (int64_t)grp * 32;
+        if (s_first >= n_segs) break;
+        int64_t si = s_first + lane;
+        // ---- per-segment set-up, one segment per lane
+        Seg<float, df> g;
+        uint32_t nb = 0;
+        if (si < n_segs) {
+            clight_segment s;
+            const float4 *src = reinterpret_cast<const float4 *>(segs + si);
+            float4 *dst = reinterpret_cast<float4 *>(&s);
+            dst[0] = __ldg(src); dst[1] = __ldg(src + 1); dst[2] = __ldg(src + 2); dst[3] = __ldg(src + 3);
+            load_segment_f(s, A, Pp, g);
+            if (g.bad) status_bits |= 1u << g.bad;
+            c_guard += g.guarded;
+            nb = g.n_c + g.n_f;
+            if (nb < g.n_c || nb > 0x7fffffffu) { status_bits |= 1u << CLIGHT_ERR_LIMIT; nb = 0; }
+        } else {
+            g.n_c = g.n_f = 0;
+        }
+        // warp inclusive scan of the bunch counts -> flattened ray index
+        uint32_t incl = nb;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t v = __shfl_up_sync(FULL_MASK, incl, o);
+            if (lane >= o) incl += v;
+        }
+        uint32_t total = __shfl_sync(FULL_MASK, incl, 31);
+        __syncwarp();
+        if (si < n_segs) {
+            PStore<df>::put(S + F_X0H * 32, S + F_X0L * 32, lane, g.x0);
+            PStore<df>::put(S + F_Y0H * 32, S + F_Y0L * 32, lane, g.y0);
+            PStore<df>::put(S + F_Z0H * 32, S + F_Z0L * 32, lane, g.z0);
+            PStore<df>::put(S + F_T0H * 32, S + F_T0L * 32, lane, g.t0);
+            S[F_DX * 32 + lane] = g.dx; S[F_DY * 32 + lane] = g.dy; S[F_DZ * 32 + lane] = g.dz;
+            S[F_LX * 32 + lane] = g.lx; S[F_LY * 32 + lane] = g.ly; S[F_LZ * 32 + lane] = g.lz;
+            S[F_E1X * 32 + lane] = g.e1x; S[F_E1Y * 32 + lane] = g.e1y; S[F_E1Z * 32 + lane] = g.e1z;
+            S[F_E2X * 32 + lane] = g.e2x; S[F_E2Y * 32 + lane] = g.e2y; S[F_E2Z * 32 + lane] = g.e2z;
+            S[F_SIN * 32 + lane] = g.sin_tc; S[F_KAP * 32 + lane] = g.kappa;
+            S[F_L * 32 + lane] = g.L; S[F_IBC * 32 + lane] = g.inv_bc;
+            S[F_WC * 32 + lane] = g.w_c; S[F_WF * 32 + lane] = g.w_f;
+            S[F_NC * 32 + lane] = __uint_as_float(g.n_c);
+            S[F_NF * 32 + lane] = __uint_as_float(g.n_f);
+            S[F_SHOWER * 32 + lane] = __uint_as_float(g.shower);
+        }
+        S[F_INCL * 32 + lane] = __uint_as_float(incl);
+        __syncwarp();
+        // ---- flattened bunch loop: lane j takes ray j of the warp's segments
+        uint32_t rounds = (total + 31) / 32;
+        for (uint32_t r = 0; r < rounds; ++r) {
+            uint32_t j = r * 32 + lane;
+            bool active = j < total;
+            uint32_t jj = active ? j : total - 1;
+            int l = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1)
+                if (__float_as_uint(S[F_INCL * 32 + l + step - 1]) <= jj) l += step;
+            uint32_t excl = __float_as_uint(S[F_INCL * 32 + l]) - (__float_as_uint(S[F_NC * 32 + l]) +
+                                                                   __float_as_uint(S[F_NF * 32 + l]));
+            uint32_t k = jj - excl;
+            Seg<float, df> q;
+            q.x0 = PStore<df>::get(S + F_X0H * 32, S + F_X0L * 32, l);
+            q.y0 = PStore<df>::get(S + F_Y0H * 32, S + F_Y0L * 32, l);
+            q.z0 = PStore<df>::get(S + F_Z0H * 32, S + F_Z0L * 32, l);
+            q.t0 = PStore<df>::get(S + F_T0H * 32, S + F_T0L * 32, l);
+            q.dx = S[F_DX * 32 + l]; q.dy = S[F_DY * 32 + l]; q.dz = S[F_DZ * 32 + l];
+            q.lx = S[F_LX * 32 + l]; q.ly = S[F_LY * 32 + l]; q.lz = S[F_LZ * 32 + l];
+            q.e1x = S[F_E1X * 32 + l]; q.e1y = S[F_E1Y * 32 + l]; q.e1z = S[F_E1Z * 32 + l];
+            q.e2x = S[F_E2X * 32 + l]; q.e2y = S[F_E2Y * 32 + l]; q.e2z = S[F_E2Z * 32 + l];
+            q.sin_tc = S[F_SIN * 32 + l]; q.kappa = S[F_KAP * 32 + l];
+            q.L = S[F_L * 32 + l]; q.inv_bc = S[F_IBC * 32 + l];
+            q.w_c = S[F_WC * 32 + l]; q.w_f = S[F_WF * 32 + l];
+            q.n_c = __float_as_uint(S[F_NC * 32 + l]); q.n_f = __float_as_uint(S[F_NF * 32 + l]);
+            q.shower = __float_as_uint(S[F_SHOWER * 32 + l]);
+            int64_t seg_local = s_first + l;
+            int64_t seg_global = Pp.seg_base + seg_local;
+            int nh = 0;
+            if (sizeof(P) == 8) {
+                Seg<float, double> qd = to_fp64_guard(q);
+                RayOut<float, double> o;
+                trace_ray<float, double, true>(qd, seg_global, k, active, A, Pp, o);
+                nh = hit_test<float, double, true>(o, seg_local, seg_global, k, q.shower, A, Tl, Pp, O, status_bits);
+                if (active) {
+                    ++c_rays;
+                    c_esc += o.status == 1; c_under += o.status == 2; c_turn += o.status == 3; c_reach += o.status == 0;
+                    c_cells += o.status == 0 ? o.cells : 0;
+                }
+            } else {
+                RayOut<float, df> o;
+                trace_ray<float, df, true>(q, seg_global, k, active, A, Pp, o);
+                nh = hit_test<float, df, true>(o, seg_local, seg_global, k, q.shower, A, Tl, Pp, O, status_bits);
+                if (active) {
+                    ++c_rays;
+                    c_esc += o.status == 1; c_under += o.status == 2; c_turn += o.status == 3; c_reach += o.status == 0;
+                    c_cells += o.status == 0 ? o.cells : 0;
+                }
+            }
+            c_hits += nh;
+        }
+        __syncwarp();
+    }
+    // ---- statistics: one atomic per warp and counter
+    uint32_t vals[9] = {c_rays, c_esc, c_under, c_turn, c_reach, c_hits, c_guard, 0u, c_cells};
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        if (i == ST_STATUS) continue;
+        uint32_t v = vals[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+        if (lane == 0 && v) atomicAdd(O.ctr + CTR_STATS + i, (unsigned long long)v);
+    }
+    unsigned sb = status_bits;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sb |= __shfl_xor_sync(FULL_MASK, sb, o);
+    if (lane == 0 && sb) atomicOr(O.ctr + CTR_STATS + ST_STATUS, (unsigned long long)sb);
+}
+
+// ------------------------------------------------------------------ plain FP64
+// One thread per segment, binary64 throughout, every bunch of the segment in
+// turn, one atomic per hit.
+__global__ void __launch_bounds__(128)
+k_trace_fp64(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid_constant__ DevAtm A,
+             const __grid_constant__ DevTel Tl, const __grid_constant__ DevPar Pp, const __grid_constant__ DevOut O)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_segs) return;
+    unsigned status_bits = 0;
+    Seg<double, double> g;
+    load_segment_d(segs[i], A, Pp, g);
+    uint32_t c_rays = 0, c_esc = 0, c_under = 0, c_turn = 0, c_reach = 0, c_hits = 0, c_cells = 0;
+    if (g.bad) {
+        status_bits |= 1u << g.bad;
+    } else {
+        uint32_t nb = g.n_c + g.n_f;
+        if (nb < g.n_c || nb > 0x7fffffffu) { status_bits |= 1u << CLIGHT_ERR_LIMIT; nb = 0; }
+        int64_t seg_global = Pp.seg_base + i;
+        for (uint32_t k = 0; k < nb; ++k) {
+            RayOut<double, double> o;
+            trace_ray<double, double, false>(g, seg_global, k, true, A, Pp, o);
+            ++c_rays;
+            c_esc += o.status == 1; c_under += o.status == 2; c_turn += o.status == 3; c_reach += o.status == 0;
+            c_cells += o.status == 0 ? o.cells : 0;
+            c_hits += hit_test<double, double, false>(o, i, seg_global, k, g.shower, A, Tl, Pp, O, status_bits);
+        }
+    }
+    uint32_t vals[9] = {c_rays, c_esc, c_under, c_turn, c_reach, c_hits, 0u, 0u, c_cells};
+    for (int q = 0; q < 9; ++q)
+        if (vals[q] && q != ST_STATUS) atomicAdd(O.ctr + CTR_STATS + q, (unsigned long long)vals[q]);
+    if (status_bits) atomicOr(O.ctr + CTR_STATS + ST_STATUS, (unsigned long long)status_bits);
+}
+
+// ------------------------------------------------------------------ launchers
+cudaError_t launch_trace_fused(const clight_segment *segs, int64_t n_segs, const DevAtm &A, const DevTel &T,
+                               const DevPar &P, const DevOut &O, int precision, int grid, int block,
+                               cudaStream_t s)
+{
+    int smem = fused_smem_bytes(block);     // <= 30 KB for block <= 256: no opt-in needed
+    if (precision == CLIGHT_PREC_FP64_GUARD)
+        k_trace_fused<double><<<grid, block, smem, s>>>(segs, n_segs, A, T, P, O);
+    else
+        k_trace_fused<df><<<grid, block, smem, s>>>(segs, n_segs, A, T, P, O);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trace_fp64(const clight_segment *segs, int64_t n_segs, const DevAtm &A, const DevTel &T,
+                              const DevPar &P, const DevOut &O, cudaStream_t s)
+{
+    int block = 128;
+    int64_t grid = (n_segs + block - 1) / block;
+    if (grid < 1) grid = 1;
+    k_trace_fp64<<<(unsigned)grid, block, 0, s>>>(segs, n_segs, A, T, P, O);
+    return cudaGetLastError();
+}
+
+}  // namespace clight

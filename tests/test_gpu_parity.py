@@ -1,0 +1,240 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Every case runs the same seeded synthetic inputs through both and compares
+hits element by element (tests/_parity.py states the tolerances), plus the
+per-telescope counts, photon sums and ray statistics.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2309_15861_gb300 as G
+from paper_2309_15861_gb300 import inputs as I
+from tests import _parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def ctx(torch_cuda):
+    c = G.Context(0)
+    yield c
+    c.close()
+
+
+def _oracle(w, seg_base=0, segs=None):
+    s = w.segments if segs is None else segs
+    return O.trace(s, w.atmosphere, w.telescopes, w.params, n_showers=w.n_showers, seg_base=seg_base)
+
+
+def _dperp_fn(w):
+    nbc, nbf = O.bunch_counts(w.segments, w.atmosphere, w.params)
+
+    def f(h):
+        out = O.eval_rays(w.segments, h["seg"], h["k"], h["tel"], nbc, nbf, w.atmosphere,
+                          w.telescopes, w.params)
+        return out[:, 4]
+    return f
+
+
+def _check(ctx, w, fp64=False, **kw):
+    ctx.setup(w, **kw)
+    gh, gc, gs, gst = G.run_workload(ctx, w, fp64=fp64)
+    rh, rc, rs, rst = _oracle(w)
+    rep = _parity.compare(gh, rh, w.telescopes, ref_dperp_of=_dperp_fn(w))
+    shower = w.segments["shower"]
+    _parity.compare_counts(gc, rc, gh, rh, len(w.telescopes), lambda s: shower[s])
+    # photon sums agree to binary32 weight precision
+    np.testing.assert_allclose(gs, rs, rtol=5e-5, atol=1e-9)
+    assert gst["rays"] == rst["rays"]
+    assert gst["escaped"] == rst["escaped"]
+    assert gst["under"] == rst["under"]
+    assert abs(gst["turned"] - rst["turned"]) <= max(2, rst["turned"] // 10000)
+    assert gst["status"] == 0
+    # the sorted order: (shower, tel, seg, k)
+    key = shower[gh["seg"]].astype(np.int64) * 10 ** 15 + gh["tel"].astype(np.int64) * 10 ** 11 + gh["seg"] * 10 ** 3 + gh["k"]
+    assert np.all(np.diff(key) > 0)
+    return rep, gst, rst
+
+
+def test_flat_vertical_plain_case(ctx):
+    w = I.workload_flat_vertical()
+    rep, gst, rst = _check(ctx, w)
+    assert rst["rays"] == 799
+
+
+def _dense_flat(n=20000, refraction=True, seed=3):
+    w = I.workload_flat_vertical(n=n, seed=seed)
+    rng = np.random.default_rng(seed)
+    s = w.segments
+    s["eps"] = rng.uniform(1e-6, 1e-4, n).astype(np.float32)      # beta >= 0.9999
+    s["x"] = rng.uniform(-160, 160, n)
+    s["y"] = rng.uniform(-160, 160, n)
+    th = np.radians(rng.uniform(0, 30, n))
+    ph = rng.uniform(0, 2 * np.pi, n)
+    d = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), -np.cos(th)], 1)
+    s["dx"], s["dy"], s["dz"] = d[:, 0], d[:, 1], d[:, 2]
+    w.atmosphere.refraction = refraction
+    w.params = I.Params(bunch=3.0, seed=seed)
+    return w
+
+
+@pytest.mark.parametrize("refraction", [True, False])
+def test_dense_flat_with_and_without_refraction(ctx, refraction):
+    w = _dense_flat(refraction=refraction)
+    rep, gst, rst = _check(ctx, w)
+    assert rep["n_common"] > 200
+
+
+def test_shower_spherical_absorbing(ctx):
+    w = I.workload_shower_1tev(n=40_000, seed=5)
+    rep, gst, rst = _check(ctx, w)
+    assert rep["n_common"] > 1000
+
+
+def test_inclined_shower_441_telescopes(ctx):
+    w = I.workload_inclined(n=40_000, seed=7)
+    rep, gst, rst = _check(ctx, w)
+    assert rep["n_common"] > 500
+
+
+def test_batch_with_fluorescence(ctx):
+    w = I.batch_showers(n_showers=6, seed=9, scale=2e-3)
+    rep, gst, rst = _check(ctx, w)
+    assert w.n_showers == 6 and rep["n_common"] > 0
+
+
+def test_fp64_plain_path(ctx):
+    w = I.workload_shower_1tev(n=8000, seed=11)
+    rep, gst, rst = _check(ctx, w, fp64=True)
+    assert rep["max_t"] < 1e-3
+
+
+def test_fp64_guard_precision_mode(ctx):
+    w = I.workload_inclined(n=10_000, seed=13)
+    _check(ctx, w, precision=G.PREC_FP64_GUARD)
+
+
+def test_graph_replay_and_determinism(ctx, torch_cuda):
+    torch = torch_cuda
+    w = I.workload_shower_1tev(n=30_000, seed=17)
+    a = G.run_workload(ctx, w) if ctx.setup(w) is None else None
+    ctx.setup(w, use_graph=1)
+    segs = torch.from_numpy(w.segments.view(np.uint8).reshape(-1)).cuda()
+    cap = 200_000
+    hits = torch.empty(cap * 48, dtype=torch.uint8, device="cuda")
+    counts = torch.zeros(len(w.telescopes), dtype=torch.int64, device="cuda")
+    sums = torch.zeros(len(w.telescopes), dtype=torch.float64, device="cuda")
+    outs = []
+    for _ in range(3):
+        code, nh, st = ctx.trace(segs, len(w.segments), 1, hits, cap, counts, sums)
+        outs.append((hits[: nh * 48].cpu().numpy().copy(), counts.cpu().numpy().copy(), sums.cpu().numpy().copy()))
+    for o in outs[1:]:
+        assert np.array_equal(o[0], outs[0][0])
+        assert np.array_equal(o[1], outs[0][1])
+        assert np.array_equal(o[2], outs[0][2])
+    h0 = outs[0][0].view(G.HIT_DTYPE)
+    assert np.array_equal(h0, a[0])
+
+
+def test_two_shards_merge_to_the_whole(ctx):
+    w = I.workload_shower_1tev(n=20_000, seed=19)
+    ctx.setup(w)
+    full = G.run_workload(ctx, w)
+    parts = []
+    for lo, hi in ((0, 7777), (7777, 20_000)):
+        sub = I.Workload(w.name, w.segments[lo:hi], w.atmosphere, w.telescopes, w.params)
+        ctx.set_params(w.params, seg_base=lo)
+        parts.append(G.run_workload(ctx, sub))
+    m = np.concatenate([parts[0][0], parts[1][0]])
+    m = m[np.lexsort((m["k"], m["seg"], m["tel"]))]
+    assert np.array_equal(m, full[0])
+    np.testing.assert_array_equal(parts[0][1] + parts[1][1], full[1])
+
+
+def test_host_buffer_entry_point(ctx):
+    w = I.workload_shower_1tev(n=10_000, seed=23)
+    ctx.setup(w)
+    dev = G.run_workload(ctx, w)
+    code, h, c, s, st = ctx.trace_host(w.segments, 1, 100_000)
+    assert code == G.OK
+    assert np.array_equal(h, dev[0])
+    np.testing.assert_array_equal(c, dev[1])
+    np.testing.assert_array_equal(s, dev[2])
+
+
+def test_edge_cases(ctx, torch_cuda):
+    torch = torch_cuda
+    w = I.workload_shower_1tev(n=5_000, seed=29)
+    ctx.setup(w)
+    segs = torch.from_numpy(w.segments.view(np.uint8).reshape(-1)).cuda()
+    hits = torch.empty(4096 * 48, dtype=torch.uint8, device="cuda")
+    # empty input
+    code, nh, st = ctx.trace(segs, 0, 1, hits, 4096)
+    assert code == G.OK and nh == 0 and st["rays"] == 0
+    # capacity overflow reports the required size and writes nothing beyond
+    code, nh, st = ctx.trace(segs, 5_000, 1, hits, 3, raise_on_error=False)
+    assert code == G.ERR_HIT_CAPACITY and nh > 3
+    code2, nh2, _ = ctx.trace(segs, 5_000, 1, hits, 4096)
+    assert code2 == G.OK and nh2 == nh
+    # ragged sizes: 1, 31, 33 segments each equal to the oracle
+    for n in (1, 31, 33, 1000):
+        sub = I.Workload(w.name, w.segments[:n], w.atmosphere, w.telescopes, w.params)
+        gh, gc, gs, gst = G.run_workload(ctx, sub)
+        rh, rc, rs, rst = _oracle(sub)
+        assert gst["rays"] == rst["rays"]
+        _parity.compare(gh, rh, w.telescopes, ref_dperp_of=_dperp_fn(sub))
+    # a NaN segment is reported, the rest still traced
+    bad = w.segments[:64].copy()
+    bad["x"][5] = np.nan
+    bad["shower"][9] = 7
+    sub = I.Workload(w.name, bad, w.atmosphere, w.telescopes, w.params)
+    d = torch.from_numpy(bad.view(np.uint8).reshape(-1)).cuda()
+    code, nh, st = ctx.trace(d, 64, 1, hits, 4096, raise_on_error=False)
+    assert code == G.ERR_BAD_SEGMENT
+    assert st["status"] & (1 << G.ERR_BAD_SEGMENT)
+    # invalid arguments are rejected on the host
+    with pytest.raises(G.ClightError):
+        ctx.trace(segs, -1, 1, hits, 4096)
+    with pytest.raises(G.ClightError):
+        ctx.trace(segs, 10, 0, hits, 4096)
+
+
+def test_full_size_single_shower_sampled(ctx, torch_cuda):
+    """The 2e7-step, 100-telescope shower in the launch configuration the
+    benchmark times, checked on contiguous blocks the oracle recomputes."""
+    torch = torch_cuda
+    w = I.workload_shower_1tev(n=20_000_000, seed=1)
+    ctx.setup(w, use_graph=1)
+    gh, gc, gs, gst = G.run_workload(ctx, w, capacity=8_000_000)
+    rng = np.random.default_rng(0)
+    starts = np.sort(rng.choice(20_000_000 // 256, 60, replace=False)) * 256
+    rays = 0
+    for b in starts:
+        seg = w.segments[b:b + 256]
+        rh, rc, rs, rst = _oracle(w, seg_base=int(b), segs=seg)
+        rays += rst["rays"]
+        sel = gh[(gh["seg"] >= b) & (gh["seg"] < b + 256)]
+        sub = I.Workload(w.name, seg, w.atmosphere, w.telescopes, w.params)
+        nbc, nbf = O.bunch_counts(seg, w.atmosphere, w.params)
+
+        def dp(h, seg=seg, nbc=nbc, nbf=nbf, b=b):
+            p = I.Params(**{**w.params.__dict__})
+            out = O.eval_rays(seg, h["seg"] - b, h["k"], h["tel"], nbc, nbf, w.atmosphere,
+                              w.telescopes, p)
+            return out[:, 4]
+        # the oracle's records carry global segment indices through seg_base
+        _parity.compare(sel, rh, w.telescopes, ref_dperp_of=dp)
+    assert rays > 10_000
+    # properties that hold at any size
+    assert gst["rays"] == gst["escaped"] + gst["under"] + gst["turned"] + gst["reached"]
+    assert gc.sum() == len(gh)
+    np.testing.assert_allclose(gs.sum(), gh["weight"].astype(np.float64).sum(), rtol=1e-9)
