@@ -226,8 +226,8 @@ void or_photon(const or_segment *s, int64_t seg_index, uint32_t k,
 
 /* ------------------------------------------------------------------------
  * Quadrature: adaptive Gauss-Legendre (10 nodes, nodes from Newton's method
- * on the Legendre recurrence), bisecting until the two halves agree with
- * the whole to a relative 1e-13.
+ * on the Legendre recurrence), bisecting until the halves agree with the
+ * whole to 1e-12 of the integral.
  * ---------------------------------------------------------------------- */
 #define GLN 10
 static double gl_x[GLN], gl_w[GLN];
@@ -298,25 +298,31 @@ static void gl_apply(const ray_ctx *c, double lo, double hi, double out[3])
     for (int k = 0; k < 3; k++) out[k] *= r;
 }
 
-static void adapt(const ray_ctx *c, double lo, double hi, const double whole[3], int depth, double acc[3])
+/* Bisect until each half-pair agrees with its parent to the interval's share
+ * (width / total width) of an absolute tolerance tol[k]; stop at 0.1 mm
+ * intervals, where near-grazing integrands reach their rounding floor. */
+static void adapt(const ray_ctx *c, double lo, double hi, const double whole[3], const double tol[3],
+                  double total_w, int depth, double acc[3])
 {
     double mid = 0.5 * (lo + hi), L[3], R[3];
     gl_apply(c, lo, mid, L);
     gl_apply(c, mid, hi, R);
     int ok = 1;
+    double share = (hi - lo) / total_w;
     for (int k = 0; k < 3; k++) {
         double s = L[k] + R[k];
-        if (fabs(s - whole[k]) > 1e-13 * fabs(s) + 1e-300) ok = 0;
+        if (!(fabs(s - whole[k]) <= tol[k] * share)) ok = 0;
     }
-    if (ok || depth >= 40) {
+    if (ok || depth >= 60 || hi - lo < 1e-4) {
         for (int k = 0; k < 3; k++) acc[k] += L[k] + R[k];
         return;
     }
-    adapt(c, lo, mid, L, depth + 1, acc);
-    adapt(c, mid, hi, R, depth + 1, acc);
+    adapt(c, lo, mid, L, tol, total_w, depth + 1, acc);
+    adapt(c, mid, hi, R, tol, total_w, depth + 1, acc);
 }
 
-/* Integral over [h_obs, h_e], split where the density has kinks. */
+/* Integral over [h_obs, h_e], split where the density has kinks; the
+ * tolerance is 1e-12 of each integral's first estimate over the path. */
 static void integrate_path(const ray_ctx *c, double h0, double h1, double out[3])
 {
     const or_atmosphere *a = c->a;
@@ -327,12 +333,16 @@ static void integrate_path(const ray_ctx *c, double h0, double h1, double out[3]
         if (a->h_lo[i] > h0 && a->h_lo[i] < h1) br[nb++] = a->h_lo[i];
     if (a->h_top > h0 && a->h_top < h1) br[nb++] = a->h_top;
     br[nb++] = h1;
-    out[0] = out[1] = out[2] = 0;
+    double whole[12][3], est[3] = {0, 0, 0};
     for (int i = 0; i + 1 < nb; i++) {
-        double whole[3];
-        gl_apply(c, br[i], br[i + 1], whole);
-        adapt(c, br[i], br[i + 1], whole, 0, out);
+        gl_apply(c, br[i], br[i + 1], whole[i]);
+        for (int k = 0; k < 3; k++) est[k] += fabs(whole[i][k]);
     }
+    double tol[3];
+    for (int k = 0; k < 3; k++) tol[k] = 1e-12 * est[k] + 1e-300;
+    out[0] = out[1] = out[2] = 0;
+    double total_w = h1 - h0;
+    for (int i = 0; i + 1 < nb; i++) adapt(c, br[i], br[i + 1], whole[i], tol, total_w, 0, out);
 }
 
 /* ------------------------------------------------------------------------

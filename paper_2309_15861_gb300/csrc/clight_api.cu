@@ -239,28 +239,43 @@ clight_status clight_set_atmosphere(clight_ctx *c, const clight_atmosphere *a)
     c->uatm = *a;
     c->atm_set = true;
     ++c->version;
-    // cells are built with the current cell width (params)
+    // Altitude cells of the ray quadrature: each inside one layer and no
+    // wider than cell_width scale heights.  Above the altitude where the
+    // density has fallen below 1e-9 of its value at the observation level the
+    // integrands are negligible, and one last cell reaches the top.
     float cw = c->upar.cell_width > 0 ? c->upar.cell_width : 1.0f;
+    const double rho_floor = 1e-9 * (A.delta_obs_d / (a->K > 0 ? a->K : 1.0));
     int nc = 0;
+    auto add_cell = [&](double l0, double l1, int i) {
+        if (nc >= kMaxCells) return false;
+        DevCell &C = A.cells[nc];
+        C.lo = (float)l0; C.hi = (float)l1;
+        C.kb = A.kb[i]; C.rb = A.rb[i]; C.nl2c = A.nl2c[i];
+        A.cell_lo_d[nc] = (double)C.lo;   // identical edges in both precisions
+        A.cell_hi_d[nc] = (double)C.hi;
+        A.cell_kb_d[nc] = A.kb_d[i]; A.cell_rb_d[nc] = A.rb_d[i]; A.cell_ic_d[nc] = A.inv_c_d[i];
+        ++nc;
+        return true;
+    };
     for (int i = 0; i < a->n_layers; ++i) {
         double lo = std::max(a->h_lo[i], a->h_obs);
         double hi = (i + 1 < a->n_layers) ? a->h_lo[i + 1] : a->h_top;
         hi = std::min(hi, a->h_top);
         if (i == 0 && a->h_lo[0] > a->h_obs) lo = a->h_obs;
         if (!(hi > lo)) continue;
-        int m = (int)std::ceil((hi - lo) / (cw * a->c[i]));
-        m = std::max(1, m);
-        for (int q = 0; q < m; ++q) {
-            if (nc >= kMaxCells) return CLIGHT_ERR_LIMIT;
-            double l0 = lo + (hi - lo) * q / m, l1 = (q + 1 == m) ? hi : lo + (hi - lo) * (q + 1) / m;
-            DevCell &C = A.cells[nc];
-            C.lo = (float)l0; C.hi = (float)l1;
-            C.kb = A.kb[i]; C.rb = A.rb[i]; C.nl2c = A.nl2c[i];
-            A.cell_lo_d[nc] = (double)C.lo;   // identical edges in both precisions
-            A.cell_hi_d[nc] = (double)C.hi;
-            A.cell_kb_d[nc] = A.kb_d[i]; A.cell_rb_d[nc] = A.rb_d[i]; A.cell_ic_d[nc] = A.inv_c_d[i];
-            ++nc;
+        double h_cut = hi;
+        if (a->K > 0 && Bc(i) > 0 && rho_floor > 0) {
+            double hc = -a->c[i] * std::log(rho_floor / Bc(i));
+            if (hc < hi) h_cut = std::max(lo, hc);
         }
+        if (h_cut > lo) {
+            int m = std::max(1, (int)std::ceil((h_cut - lo) / (cw * a->c[i])));
+            for (int q = 0; q < m; ++q) {
+                double l0 = lo + (h_cut - lo) * q / m, l1 = (q + 1 == m) ? h_cut : lo + (h_cut - lo) * (q + 1) / m;
+                if (!add_cell(l0, l1, i)) return CLIGHT_ERR_LIMIT;
+            }
+        }
+        if (hi > h_cut && !add_cell(h_cut, hi, i)) return CLIGHT_ERR_LIMIT;
     }
     A.n_cells = nc;
     return CLIGHT_OK;
@@ -397,8 +412,10 @@ clight_status prepare(clight_ctx *c, int64_t n_segs, int32_t n_showers, int64_t 
 }
 
 cudaError_t enqueue(clight_ctx *c, const clight_segment *segs, int64_t n_segs, const Plan &pl, clight_hit *hits,
-                    int64_t cap, int64_t *counts, double *sums, bool fp64, cudaStream_t s)
+                    int64_t cap, int64_t *counts, double *sums, bool fp64, cudaStream_t s, bool capturing)
 {
+    // inside a capture an event record is a real graph node only when external
+    const unsigned evf = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     DevOut O;
     O.rec = c->rec.p;
     O.keys = c->keys.p;
@@ -415,7 +432,7 @@ cudaError_t enqueue(clight_ctx *c, const clight_segment *segs, int64_t n_segs, c
     S.gend = c->gend.p;
     cudaError_t e = cudaMemsetAsync(c->d_ctr, 0, sizeof(unsigned long long) * CTR_N, s);
     if (e != cudaSuccess) return e;
-    if ((e = cudaEventRecord(c->t0, s)) != cudaSuccess) return e;
+    if ((e = cudaEventRecordWithFlags(c->t0, s, evf)) != cudaSuccess) return e;
     if (n_segs > 0) {
         if (fp64) {
             e = launch_trace_fp64(segs, n_segs, c->atm, c->tel, c->par, O, s);
@@ -429,10 +446,10 @@ cudaError_t enqueue(clight_ctx *c, const clight_segment *segs, int64_t n_segs, c
         }
         if (e != cudaSuccess) return e;
     }
-    if ((e = cudaEventRecord(c->t1, s)) != cudaSuccess) return e;
+    if ((e = cudaEventRecordWithFlags(c->t1, s, evf)) != cudaSuccess) return e;
     e = launch_sort_and_finalize(O, S, pl.key_bits, pl.group_shift, pl.n_groups, hits, counts, sums, s);
     if (e != cudaSuccess) return e;
-    if ((e = cudaEventRecord(c->t2, s)) != cudaSuccess) return e;
+    if ((e = cudaEventRecordWithFlags(c->t2, s, evf)) != cudaSuccess) return e;
     return cudaMemcpyAsync(c->h_ctr, c->d_ctr, sizeof(unsigned long long) * CTR_N, cudaMemcpyDeviceToHost, s);
 }
 
@@ -475,7 +492,7 @@ clight_status run(clight_ctx *c, const clight_segment *segs, int64_t n_segs, int
             if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
             cudaGraph_t g;
             CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-            cudaError_t e = enqueue(c, segs, n_segs, pl, hits, cap, counts, sums, false, c->cap_stream);
+            cudaError_t e = enqueue(c, segs, n_segs, pl, hits, cap, counts, sums, false, c->cap_stream, true);
             cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
             if (e != cudaSuccess || e2 != cudaSuccess) return CLIGHT_ERR_CUDA;
             e = cudaGraphInstantiate(&c->gexec, g, 0);
@@ -490,7 +507,7 @@ clight_status run(clight_ctx *c, const clight_segment *segs, int64_t n_segs, int
         CK(cudaStreamWaitEvent(s, c->ev, 0));         // later work on `stream` follows the graph
         CK(cudaStreamSynchronize(c->cap_stream));
     } else {
-        CK(enqueue(c, segs, n_segs, pl, hits, cap, counts, sums, fp64, s));
+        CK(enqueue(c, segs, n_segs, pl, hits, cap, counts, sums, fp64, s, false));
         CK(cudaStreamSynchronize(s));
     }
     return finish(c, cap, st, n_hits);

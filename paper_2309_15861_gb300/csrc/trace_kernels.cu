@@ -55,8 +55,16 @@ template <> __device__ __forceinline__ double p_from<double>(double x) { return 
 template <class P> __device__ __forceinline__ P p_fromf(float x);
 template <> __device__ __forceinline__ df p_fromf<df>(float x) { return df_make(x); }
 template <> __device__ __forceinline__ double p_fromf<double>(float x) { return (double)x; }
-template <class P> __device__ __forceinline__ P p_fromd(double x);
-template <> __device__ __forceinline__ double p_fromd<double>(double x) { return x; }
+// exact widening of a bulk-precision value into the pair/binary64 type
+__device__ __forceinline__ void p_set(df &o, float x) { o = df_make(x); }
+__device__ __forceinline__ void p_set(double &o, float x) { o = (double)x; }
+__device__ __forceinline__ void p_set(double &o, double x) { o = x; }
+template <class P, class T> __device__ __forceinline__ P p_of(T x)
+{
+    P o;
+    p_set(o, x);
+    return o;
+}
 __device__ __forceinline__ float p_f(df a) { return __fadd_rn(a.hi, a.lo); }
 __device__ __forceinline__ float p_f(double a) { return (float)a; }
 __device__ __forceinline__ double p_d(df a) { return df_to_double(a); }
@@ -151,7 +159,7 @@ __device__ __forceinline__ bool finite_f(float v) { return isfinite(v); }
 // N = 2 pi alpha z^2 (1/l1 - 1/l2) (1 - 1/(beta n)^2) L for beta n > 1.
 __device__ __forceinline__ void yield_fp64(const clight_segment &s, const DevAtm &A, const DevPar &P,
                                            double ux, double uy, double uz, double *Nc, double *sin2,
-                                           double *cos_tc, double *Nf)
+                                           double *kappa, double *Nf)
 {
     double xm = s.x + 0.5 * (double)s.L * ux, ym = s.y + 0.5 * (double)s.L * uy,
            zm = s.z + 0.5 * (double)s.L * uz;
@@ -163,14 +171,16 @@ __device__ __forceinline__ void yield_fp64(const clight_segment &s, const DevAtm
         h = zm;
     }
     double dl = AtmT<double>::delta(A, h);
-    double bn = (1.0 - (double)s.eps) * (1.0 + dl);
+    double eps = (double)s.eps;
+    double g1 = dl - eps - eps * dl;               // beta n - 1
     double z2 = (double)s.charge * (double)s.charge;
     *Nc = 0.0;
     *sin2 = 0.0;
-    *cos_tc = 1.0;
-    if (z2 > 0.0 && bn > 1.0 && s.L > 0.0f) {
-        *cos_tc = 1.0 / bn;
-        *sin2 = 1.0 - 1.0 / (bn * bn);
+    *kappa = 0.0;
+    if (z2 > 0.0 && g1 > 0.0 && s.L > 0.0f) {
+        double bn = 1.0 + g1;
+        *kappa = g1 / bn;                           // 1 - cos(theta_c)
+        *sin2 = g1 * (2.0 + g1) / (bn * bn);        // 1 - 1/(beta n)^2
         *Nc = P.band_d * z2 * (*sin2) * (double)s.L;
     }
     *Nf = (P.fyield_d > 0.0 && s.dE > 0.0f && s.L > 0.0f) ? P.fyield_d * (double)s.dE : 0.0;
@@ -254,7 +264,9 @@ __device__ void load_segment_f(const clight_segment &s, const DevAtm &A, const D
             g.kappa = g1 / bn;
             float x = Nc * P.inv_bunch;
             float ex = x * (eg / g1 * 2.0f + 2.0e-6f) + 1.0e-6f;
-            if (ceilf(x - ex) != ceilf(x + ex)) guard = true;
+            // an uncertain integer count, or a cone so narrow that its binary32
+            // angle would move photons by millimetres: recompute in binary64
+            if (ceilf(x - ex) != ceilf(x + ex) || g1 < 1.0e-6f * dl) guard = true;
             else g.n_c = (uint32_t)ceilf(x);
         } else if (g1 > -eg) {
             guard = true;
@@ -272,15 +284,15 @@ __device__ void load_segment_f(const clight_segment &s, const DevAtm &A, const D
     }
     if (guard || fguard) {
         g.guarded = 1;
-        double Ncd, sin2d, cosd, Nfd;
+        double Ncd, sin2d, kapd, Nfd;
         yield_fp64(s, A, P, (double)g.dx + (double)g.lx, (double)g.dy + (double)g.ly,
-                   (double)g.dz + (double)g.lz, &Ncd, &sin2d, &cosd, &Nfd);
+                   (double)g.dz + (double)g.lz, &Ncd, &sin2d, &kapd, &Nfd);
         if (guard) {
             double nb = ceil(Ncd / P.bunch_d);
             g.n_c = (uint32_t)nb;
             Nc = (float)Ncd;
             g.sin_tc = (float)sqrt(sin2d);
-            g.kappa = (float)(1.0 - cosd);
+            g.kappa = (float)kapd;
             if (g.n_c > 0) g.w_c = (float)(Ncd / nb);
         }
         if (fguard) {
@@ -319,10 +331,10 @@ __device__ void load_segment_d(const clight_segment &s, const DevAtm &A, const D
     g.L = s.L;
     g.inv_bc = kInvC / (1.0 - (double)s.eps);
     make_frame(g);
-    double Nc, sin2, cos_tc, Nf;
-    yield_fp64(s, A, P, g.dx, g.dy, g.dz, &Nc, &sin2, &cos_tc, &Nf);
+    double Nc, sin2, kap, Nf;
+    yield_fp64(s, A, P, g.dx, g.dy, g.dz, &Nc, &sin2, &kap, &Nf);
     g.sin_tc = sqrt(sin2);
-    g.kappa = 1.0 - cos_tc;
+    g.kappa = kap;
     if (Nc > 0.0) {
         double nb = ceil(Nc / P.bunch_d);
         g.n_c = (uint32_t)nb;
@@ -341,7 +353,7 @@ template <class T, class P> struct RayOut {
     P t;               // arrival time there
     T cx, cy, cz;      // arrival direction
     T lambda, weight;
-    int status;        // 0 reached, 1 escaped, 2 under, 3 turned
+    int status;        // 0 reached, 1 escaped, 2 under, 3 turned, 4 idle lane, 5 reached (grazing, not landed)
     uint32_t cells;    // quadrature cells integrated
 };
 
@@ -437,9 +449,9 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
         T sy = -g.kappa * g.dy + st * (cc * g.e1y + sc * g.e2y);
         T sz = -g.kappa * g.dz + st * (cc * g.e1z + sc * g.e2z);
         // cos(theta_c) d + sin(theta_c)(cos c e1 + sin c e2), d kept as a pair
-        dgx = p_fromf<P>(g.dx) + (g.lx + sx);
-        dgy = p_fromf<P>(g.dy) + (g.ly + sy);
-        dgz = p_fromf<P>(g.dz) + (g.lz + sz);
+        dgx = p_of<P>(g.dx) + (g.lx + sx);
+        dgy = p_of<P>(g.dy) + (g.ly + sy);
+        dgz = p_of<P>(g.dz) + (g.lz + sz);
         w = g.w_c;
     } else {
         T fl1 = sizeof(T) == 4 ? (T)Pp.fl1 : (T)Pp.fl1_d;
@@ -474,7 +486,7 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
     // ---- vacuum straight line to the observation level (exact geometry)
     P s_v, Pvx, Pvy, Pvz, sqd;
     T he, pv2, bf2, bf;
-    bool esc = false, under = false, turned = false;
+    bool esc = false, under = false, turned = false, grazing = false;
     if (sph) {
         P Rz = ze + REp;
         // b = -(d . R_e) = r_e cos(psi_e)
@@ -485,19 +497,33 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
         P dzo = ze - Hobs;
         P C = dzo * (ze + K2) + (xef * xef + yef * yef);
         P disc = b * b - C;
-        turned = !(p_f(disc) > 0.0f);
-        if (!(esc || under || turned)) {
+        T Rzf = to_t<T>(Rz);
+        T c1 = dy * Rzf - dz * yef, c2 = dz * xef - dx * Rzf, c3 = dx * yef - dy * xef;
+        pv2 = c1 * c1 + c2 * c2 + c3 * c3;                   // (r_e sin psi_e)^2
+        bf = to_t<T>(b);
+        bf2 = bf * bf;                                       // (r_e cos psi_e)^2
+        // The ray reaches the observation sphere when q(r_obs) > 0; with
+        // q_v(r_obs) = disc, q(r_obs) = n_obs^2 disc + (n_obs^2 - n_e^2) p_v^2.
+        T discf = to_t<T>(disc);
+        if (refr) {
+            T de0 = AtmT<T>::delta(A, he);
+            T dob = sizeof(T) == 4 ? (T)A.delta_obs : (T)A.delta_obs_d;
+            T nob = (T)1 + dob;
+            T qL = nob * nob * discf + (dob - de0) * ((T)2 + dob + de0) * pv2;
+            turned = !(qL > (T)0);
+            // reaches, but the vacuum line passes above the sphere: a grazing
+            // ray that lands far from the array; counted, not landed
+            grazing = !turned && !(discf > (T)0);
+        } else {
+            turned = !(discf > (T)0);
+        }
+        if (!(esc || under || turned || grazing)) {
             sqd = p_sqrt(disc);
             s_v = C / (b + sqd);
         } else {
             sqd = p_fromf<P>(0.0f);
             s_v = p_fromf<P>(0.0f);
         }
-        T Rzf = to_t<T>(Rz);
-        T c1 = dy * Rzf - dz * yef, c2 = dz * xef - dx * Rzf, c3 = dx * yef - dy * xef;
-        pv2 = c1 * c1 + c2 * c2 + c3 * c3;                   // (r_e sin psi_e)^2
-        bf = to_t<T>(b);
-        bf2 = bf * bf;                                       // (r_e cos psi_e)^2
     } else {
         he = zef;
         esc = !(p_f(dgz) < 0.0f);
@@ -513,6 +539,7 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
     else if (esc) { o.status = 1; }
     else if (under) { o.status = 2; }
     else if (turned) { o.status = 3; }
+    else if (grazing) { o.status = 5; }
     bool go = o.status == 0;
 
     // ---- refraction, optical path and optical depth by quadrature
@@ -834,7 +861,7 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
                 nh = hit_test<float, double, true>(o, seg_local, seg_global, k, q.shower, A, Tl, Pp, O, status_bits);
                 if (active) {
                     ++c_rays;
-                    c_esc += o.status == 1; c_under += o.status == 2; c_turn += o.status == 3; c_reach += o.status == 0;
+                    c_esc += o.status == 1; c_under += o.status == 2; c_turn += o.status == 3; c_reach += o.status == 0 || o.status == 5;
                     c_cells += o.status == 0 ? o.cells : 0;
                 }
             } else {
@@ -843,7 +870,7 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
                 nh = hit_test<float, df, true>(o, seg_local, seg_global, k, q.shower, A, Tl, Pp, O, status_bits);
                 if (active) {
                     ++c_rays;
-                    c_esc += o.status == 1; c_under += o.status == 2; c_turn += o.status == 3; c_reach += o.status == 0;
+                    c_esc += o.status == 1; c_under += o.status == 2; c_turn += o.status == 3; c_reach += o.status == 0 || o.status == 5;
                     c_cells += o.status == 0 ? o.cells : 0;
                 }
             }
@@ -890,7 +917,7 @@ k_trace_fp64(const clight_segment *__restrict__ segs, int64_t n_segs, const __gr
             RayOut<double, double> o;
             trace_ray<double, double, false>(g, seg_global, k, true, A, Pp, o);
             ++c_rays;
-            c_esc += o.status == 1; c_under += o.status == 2; c_turn += o.status == 3; c_reach += o.status == 0;
+            c_esc += o.status == 1; c_under += o.status == 2; c_turn += o.status == 3; c_reach += o.status == 0 || o.status == 5;
             c_cells += o.status == 0 ? o.cells : 0;
             c_hits += hit_test<double, double, false>(o, i, seg_global, k, g.shower, A, Tl, Pp, O, status_bits);
         }

@@ -49,11 +49,12 @@ def _check(ctx, w, fp64=False, **kw):
     ctx.setup(w, **kw)
     gh, gc, gs, gst = G.run_workload(ctx, w, fp64=fp64)
     rh, rc, rs, rst = _oracle(w)
-    rep = _parity.compare(gh, rh, w.telescopes, ref_dperp_of=_dperp_fn(w))
+    wt = _parity.weight_tolerance(w.segments, rh, w.atmosphere, w.params)
+    rep = _parity.compare(gh, rh, w.telescopes, ref_dperp_of=_dperp_fn(w), w_tol=wt)
     shower = w.segments["shower"]
     _parity.compare_counts(gc, rc, gh, rh, len(w.telescopes), lambda s: shower[s])
-    # photon sums agree to binary32 weight precision
-    np.testing.assert_allclose(gs, rs, rtol=5e-5, atol=1e-9)
+    # photon sums agree to the binary32 weight precision
+    np.testing.assert_allclose(gs, rs, rtol=2e-4, atol=1e-6)
     assert gst["rays"] == rst["rays"]
     assert gst["escaped"] == rst["escaped"]
     assert gst["under"] == rst["under"]
@@ -72,13 +73,15 @@ def test_flat_vertical_plain_case(ctx):
 
 
 def _dense_flat(n=20000, refraction=True, seed=3):
+    """Steps tilted up to 5 deg, beta >= 0.9999, over a 7 x 7 array at 30 m spacing."""
     w = I.workload_flat_vertical(n=n, seed=seed)
+    w.telescopes = I.telescope_grid(7, 7, 30.0, z=w.atmosphere.h_obs)
     rng = np.random.default_rng(seed)
     s = w.segments
-    s["eps"] = rng.uniform(1e-6, 1e-4, n).astype(np.float32)      # beta >= 0.9999
-    s["x"] = rng.uniform(-160, 160, n)
-    s["y"] = rng.uniform(-160, 160, n)
-    th = np.radians(rng.uniform(0, 30, n))
+    s["eps"] = rng.uniform(1e-6, 1e-4, n).astype(np.float32)
+    s["x"] = rng.uniform(-120, 120, n)
+    s["y"] = rng.uniform(-120, 120, n)
+    th = np.radians(rng.uniform(0, 5, n))
     ph = rng.uniform(0, 2 * np.pi, n)
     d = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), -np.cos(th)], 1)
     s["dx"], s["dy"], s["dz"] = d[:, 0], d[:, 1], d[:, 2]
@@ -115,7 +118,8 @@ def test_batch_with_fluorescence(ctx):
 def test_fp64_plain_path(ctx):
     w = I.workload_shower_1tev(n=8000, seed=11)
     rep, gst, rst = _check(ctx, w, fp64=True)
-    assert rep["max_t"] < 1e-3
+    # binary64 throughout: only the 4-node quadrature error remains
+    assert rep["max_t"] < 1e-5 and rep["max_x"] < 1e-5 and rep["max_y"] < 1e-5
 
 
 def test_fp64_guard_precision_mode(ctx):
@@ -191,7 +195,8 @@ def test_edge_cases(ctx, torch_cuda):
         gh, gc, gs, gst = G.run_workload(ctx, sub)
         rh, rc, rs, rst = _oracle(sub)
         assert gst["rays"] == rst["rays"]
-        _parity.compare(gh, rh, w.telescopes, ref_dperp_of=_dperp_fn(sub))
+        _parity.compare(gh, rh, w.telescopes, ref_dperp_of=_dperp_fn(sub),
+                        w_tol=_parity.weight_tolerance(sub.segments, rh, w.atmosphere, w.params))
     # a NaN segment is reported, the rest still traced
     bad = w.segments[:64].copy()
     bad["x"][5] = np.nan
@@ -232,7 +237,8 @@ def test_full_size_single_shower_sampled(ctx, torch_cuda):
                               w.telescopes, p)
             return out[:, 4]
         # the oracle's records carry global segment indices through seg_base
-        _parity.compare(sel, rh, w.telescopes, ref_dperp_of=dp)
+        _parity.compare(sel, rh, w.telescopes, ref_dperp_of=dp,
+                        w_tol=_parity.weight_tolerance(seg, rh, w.atmosphere, w.params, seg_base=int(b)))
     assert rays > 10_000
     # properties that hold at any size
     assert gst["rays"] == gst["escaped"] + gst["under"] + gst["turned"] + gst["reached"]
