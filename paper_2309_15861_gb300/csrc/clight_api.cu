@@ -220,6 +220,16 @@ clight_status clight_set_atmosphere(clight_ctx *c, const clight_atmosphere *a)
             if (h >= a->h_lo[j]) i = j;
         return a->K * Bc(i) * std::exp(-h / a->c[i]);
     };
+    auto split = [](double x, float &hi, float &lo) {
+        hi = (float)x;
+        lo = (float)(x - (double)hi);
+    };
+    split(a->h_obs, A.hobs_hi, A.hobs_lo);
+    split(A.R_E_d, A.re_hi, A.re_lo);
+    split(a->h_obs + 2.0 * A.R_E_d, A.k2_hi, A.k2_lo);
+    A.k2_d = a->h_obs + 2.0 * A.R_E_d;
+    split(3.3356409519815204, A.invc_hi, A.invc_lo);   // ns per m
+    A.R_E = (float)A.R_E_d;
     A.delta_obs_d = delta_at(a->h_obs);
     A.delta_obs = (float)A.delta_obs_d;
     A.n_obs = (float)(1.0 + A.delta_obs_d);

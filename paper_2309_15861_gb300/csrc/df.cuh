@@ -17,6 +17,14 @@ struct df {
 
 __device__ __forceinline__ df df_make(float a) { return {a, 0.0f}; }
 
+// Hardware reciprocal estimate (MUFU.RCP, about 1 ulp), no IEEE fix-up path.
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Knuth TwoSum: s + e == a + b exactly.
 __device__ __forceinline__ df two_sum(float a, float b)
 {
@@ -51,6 +59,30 @@ __device__ __forceinline__ df df_from_double(double x)
 }
 
 __device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+
+// The same split with integer instructions only (GB300's binary64 pipe is
+// narrow): hi is x rounded to nearest-even binary32, lo the rest rounded to
+// binary32.  Valid for |x| in [2^-74, 2^127]; zero maps to zero, and smaller
+// magnitudes (which no position or time reaches) to zero as well.
+__device__ __forceinline__ df df_from_double_bits(double x)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    uint32_t sign = (uint32_t)(b >> 63) << 31;
+    int e = (int)((b >> 52) & 0x7ff);
+    if (e < 949) return {__uint_as_float(sign), 0.0f};
+    unsigned long long M = (1ull << 52) | (b & 0xFFFFFFFFFFFFFull);
+    uint32_t top = (uint32_t)(M >> 29);                 // 24 significant bits
+    uint32_t rem = (uint32_t)(M & 0x1FFFFFFFull);       // the 29 dropped bits
+    bool up = rem > (1u << 28) || (rem == (1u << 28) && (top & 1u));
+    int fe = e - 1023 + 127;
+    top += up ? 1u : 0u;
+    if (top == (1u << 24)) { top >>= 1; fe += 1; }
+    float hi = __uint_as_float(sign | ((uint32_t)fe << 23) | (top & 0x7FFFFFu));
+    int32_t r = (int32_t)rem - (up ? (1 << 29) : 0);    // x - hi in units of 2^(e-1075)
+    float scale = __uint_as_float((uint32_t)(e - 948) << 23);
+    float lo = __int2float_rn(r) * scale;
+    return {hi, sign ? -lo : lo};
+}
 
 __device__ __forceinline__ df operator+(df a, df b)
 {
@@ -87,26 +119,34 @@ __device__ __forceinline__ df operator*(df a, float b)
     return fast_two_sum(p.hi, p.lo);
 }
 
-// Quotient with two correction steps (~44 bits).
+// Quotient: a hardware reciprocal estimate (MUFU, ~1 ulp) and two correction
+// steps in pair arithmetic, each removing the residual of the previous
+// estimate (~44 bits).  No IEEE-rounded binary32 division is involved.
 __device__ __forceinline__ df operator/(df a, df b)
 {
-    float q1 = __fdiv_rn(a.hi, b.hi);
+    float rb = rcp_approx(b.hi);
+    rb = __fmaf_rn(rb, __fmaf_rn(-b.hi, rb, 1.0f), rb);    // one Newton step on 1/b.hi
+    float q1 = a.hi * rb;
     df r = a - b * q1;
-    float q2 = __fdiv_rn(r.hi, b.hi);
+    float q2 = r.hi * rb;
     r = r - b * q2;
-    float q3 = __fdiv_rn(r.hi, b.hi);
+    float q3 = r.hi * rb;
     df q = fast_two_sum(q1, q2);
     return q + q3;
 }
 
-// Square root: binary32 root plus one Newton correction in pair arithmetic.
+// Square root: s = a rsqrt(a) from the hardware estimate, then two Newton
+// corrections in pair arithmetic.
 __device__ __forceinline__ df df_sqrt(df a)
 {
     if (a.hi <= 0.0f) return {0.0f, 0.0f};
-    float s = __fsqrt_rn(a.hi);
+    float rs = rsqrtf(a.hi);
+    float s = a.hi * rs;
     df r = a - two_prod(s, s);
-    float c = __fdiv_rn(r.hi, 2.0f * s);
-    return fast_two_sum(s, c);
+    float c = 0.5f * r.hi * rs;
+    df x = fast_two_sum(s, c);
+    r = a - x * x;
+    return x + 0.5f * r.hi * rs;
 }
 
 __device__ __forceinline__ bool df_gt0(df a) { return a.hi > 0.0f || (a.hi == 0.0f && a.lo > 0.0f); }

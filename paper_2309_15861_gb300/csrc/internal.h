@@ -31,6 +31,9 @@ struct DevAtm {
     double delta_obs_d;
     float inv_L0, lambda_ref;                 // tau = I * (lambda_ref/lambda)^4 * inv_L0
     double inv_L0_d, lambda_ref_d;
+    // the same constants as FP32 pairs (hi, lo), so that no ray converts binary64
+    float hobs_hi, hobs_lo, re_hi, re_lo, k2_hi, k2_lo, invc_hi, invc_lo;  // h_obs, R_E, h_obs + 2 R_E, 1/c
+    double k2_d;                              // h_obs + 2 R_E
     float gl_x[kGLNodes], gl_w[kGLNodes];     // Gauss-Legendre on [-1, 1]
     double gl_x_d[kGLNodes], gl_w_d[kGLNodes];
     DevCell cells[kMaxCells];

@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "df.cuh"
 #include "internal.h"
@@ -35,6 +36,7 @@ namespace clight {
 // ------------------------------------------------------------------ numerics
 template <class T> struct Num;
 template <> struct Num<float> {
+    static __device__ __forceinline__ float div(float a, float b) { return a * rcp_approx(b); }
     static __device__ __forceinline__ float ex2(float x) { return exp2f(x); }
     static __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
     static __device__ __forceinline__ float sqr(float x) { return sqrtf(x); }
@@ -42,6 +44,7 @@ template <> struct Num<float> {
     static __device__ __forceinline__ void sincos2pi(float u, float *s, float *c) { sincospif(2.0f * u, s, c); }
 };
 template <> struct Num<double> {
+    static __device__ __forceinline__ double div(double a, double b) { return a / b; }
     static __device__ __forceinline__ double ex2(double x) { return exp2(x); }
     static __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
     static __device__ __forceinline__ double sqr(double x) { return sqrt(x); }
@@ -71,6 +74,15 @@ __device__ __forceinline__ double p_d(df a) { return df_to_double(a); }
 __device__ __forceinline__ double p_d(double a) { return a; }
 __device__ __forceinline__ df p_sqrt(df a) { return df_sqrt(a); }
 __device__ __forceinline__ double p_sqrt(double a) { return sqrt(a); }
+// constants held both as FP32 pairs and binary64 in DevAtm
+__device__ __forceinline__ void p_const(df &o, float hi, float lo, double) { o = {hi, lo}; }
+__device__ __forceinline__ void p_const(double &o, float, float, double d) { o = d; }
+template <class P> __device__ __forceinline__ P pc(float hi, float lo, double d)
+{
+    P o;
+    p_const(o, hi, lo, d);
+    return o;
+}
 template <class T> __device__ __forceinline__ T to_t(df a);
 template <> __device__ __forceinline__ float to_t<float>(df a) { return p_f(a); }
 template <class T> __device__ __forceinline__ T to_t(double a) { return (T)a; }
@@ -96,6 +108,11 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 template <class T> __device__ __forceinline__ T u01(uint32_t x)
 {
     return (T)(x >> 9) * (T)1.1920928955078125e-07 + (T)5.9604644775390625e-08;
+}
+// binary32: 1 + m 2^-23 from the bits, minus 1, plus 2^-24 (all exact)
+template <> __device__ __forceinline__ float u01<float>(uint32_t x)
+{
+    return (__uint_as_float((x >> 9) | 0x3f800000u) - 1.0f) + 5.9604644775390625e-08f;
 }
 
 // ------------------------------------------------------------------ atmosphere
@@ -126,10 +143,10 @@ template <> struct AtmT<double> {
 template <class T> __device__ __forceinline__ T altitude(const DevAtm &A, T x, T y, T z)
 {
     if (!A.spherical) return z;
-    const T RE = (T)A.R_E_d;
+    const T RE = sizeof(T) == 4 ? (T)A.R_E : (T)A.R_E_d;
     T num = x * x + y * y + z * (z + (T)2 * RE);
     T zc = z + RE;
-    return num / (Num<T>::sqr(x * x + y * y + zc * zc) + RE);
+    return Num<T>::div(num, Num<T>::sqr(x * x + y * y + zc * zc) + RE);
 }
 
 // ------------------------------------------------------------------ segment
@@ -152,7 +169,11 @@ template <class T, class P> struct Seg {
 
 constexpr double kInvC = 3.3356409519815204;    // ns/m
 
-__device__ __forceinline__ bool finite_f(float v) { return isfinite(v); }
+__device__ __forceinline__ bool finite_f(float v) { return (__float_as_uint(v) & 0x7f800000u) != 0x7f800000u; }
+__device__ __forceinline__ bool finite_d(double v)
+{
+    return ((unsigned long long)__double_as_longlong(v) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
+}
 
 // Yield and bunch count in binary64 (the plain path, and the guard of the
 // FP32 path when its count is not certain).  Frank-Tamm (Sec. 1.2):
@@ -212,7 +233,7 @@ __device__ void load_segment_f(const clight_segment &s, const DevAtm &A, const D
     g.n_c = g.n_f = 0;
     g.w_c = g.w_f = 0.0f;
     g.shower = s.shower;
-    bool ok = isfinite(s.x) && isfinite(s.y) && isfinite(s.z) && isfinite(s.t0) && finite_f(s.dx) &&
+    bool ok = finite_d(s.x) && finite_d(s.y) && finite_d(s.z) && finite_d(s.t0) && finite_f(s.dx) &&
               finite_f(s.dy) && finite_f(s.dz) && finite_f(s.L) && finite_f(s.eps) && finite_f(s.dE) &&
               s.L >= 0.0f && s.eps >= 0.0f && s.eps < 1.0f && (int)s.shower < P.n_showers &&
               s.shower < 0x7fffffffu;
@@ -228,23 +249,23 @@ __device__ void load_segment_f(const clight_segment &s, const DevAtm &A, const D
     // unit direction as a pair: d (1 - e/2 + 3 e^2/8), e = |d|^2 - 1 exactly
     df sq = two_prod(s.dx, s.dx) + two_prod(s.dy, s.dy) + two_prod(s.dz, s.dz);
     float e = p_f(sq - 1.0f);
-    float f = 1.0f / sqrtf(1.0f + e);            // normalisation of the binary32 part
+    float f = rsqrtf(1.0f + e);                  // normalisation of the binary32 part
     g.dx = s.dx * f; g.dy = s.dy * f; g.dz = s.dz * f;
     // residual of the rounded unit vector (pair low part)
     df r2 = two_prod(g.dx, g.dx) + two_prod(g.dy, g.dy) + two_prod(g.dz, g.dz);
     float e2 = p_f(r2 - 1.0f);
     g.lx = -0.5f * e2 * g.dx; g.ly = -0.5f * e2 * g.dy; g.lz = -0.5f * e2 * g.dz;
-    g.x0 = df_from_double(s.x);
-    g.y0 = df_from_double(s.y);
-    g.z0 = df_from_double(s.z);
-    g.t0 = df_from_double(s.t0);
+    g.x0 = df_from_double_bits(s.x);
+    g.y0 = df_from_double_bits(s.y);
+    g.z0 = df_from_double_bits(s.z);
+    g.t0 = df_from_double_bits(s.t0);
     g.L = s.L;
-    g.inv_bc = 3.3356409519815204f / (1.0f - s.eps);      // 1/(beta c), ns/m
+    g.inv_bc = Num<float>::div(3.3356409519815204f, 1.0f - s.eps);   // 1/(beta c), ns/m
     make_frame(g);
 
     // midpoint altitude and refractivity (n constant over the step)
     float hL = 0.5f * s.L;
-    float xm = (float)s.x + hL * g.dx, ym = (float)s.y + hL * g.dy, zm = (float)s.z + hL * g.dz;
+    float xm = g.x0.hi + hL * g.dx, ym = g.y0.hi + hL * g.dy, zm = g.z0.hi + hL * g.dz;
     float hm = altitude<float>(A, xm, ym, zm);
     float dl = AtmT<float>::delta(A, hm);
     float eps = s.eps;
@@ -258,12 +279,13 @@ __device__ void load_segment_f(const clight_segment &s, const DevAtm &A, const D
     if (z2 > 0.0f && s.L > 0.0f) {
         if (g1 > eg) {
             float bn = 1.0f + g1;
-            float sin2 = g1 * (2.0f + g1) / (bn * bn);
+            float ib = rcp_approx(bn);
+            float sin2 = g1 * (2.0f + g1) * ib * ib;
             Nc = P.band * z2 * sin2 * s.L;
             g.sin_tc = sqrtf(sin2);
-            g.kappa = g1 / bn;
+            g.kappa = g1 * ib;
             float x = Nc * P.inv_bunch;
-            float ex = x * (eg / g1 * 2.0f + 2.0e-6f) + 1.0e-6f;
+            float ex = x * (eg * rcp_approx(g1) * 2.0f + 2.0e-6f) + 1.0e-6f;
             // an uncertain integer count, or a cone so narrow that its binary32
             // angle would move photons by millimetres: recompute in binary64
             if (ceilf(x - ex) != ceilf(x + ex) || g1 < 1.0e-6f * dl) guard = true;
@@ -302,8 +324,8 @@ __device__ void load_segment_f(const clight_segment &s, const DevAtm &A, const D
             if (g.n_f > 0) g.w_f = (float)(Nfd / nb);
         }
     }
-    if (!guard && g.n_c > 0) g.w_c = Nc / (float)g.n_c;
-    if (!fguard && g.n_f > 0) g.w_f = Nf / (float)g.n_f;
+    if (!guard && g.n_c > 0) g.w_c = Nc * rcp_approx((float)g.n_c);
+    if (!fguard && g.n_f > 0) g.w_f = Nf * rcp_approx((float)g.n_f);
 }
 
 // binary64 segment set-up (plain path).
@@ -369,7 +391,7 @@ __device__ __forceinline__ void ray_quadrature(const DevAtm &A, T hcap, T he, T 
                                                bool sph, bool refr, T &I0, T &I1, T &I2, uint32_t &ncell)
 {
     I0 = I1 = I2 = (T)0;
-    const T RE = (T)A.R_E_d;
+    const T RE = sizeof(T) == 4 ? (T)A.R_E : (T)A.R_E_d;
     const T ne = (T)1 + de;
     for (int c = 0; c < A.n_cells; ++c) {
         const DevCell &C = A.cells[c];
@@ -410,8 +432,8 @@ __device__ __forceinline__ void ray_quadrature(const DevAtm &A, T hcap, T he, T 
                 T sq = q * rq, sqv = qv * rqv;
                 T cm = rq * rqv;
                 T a = dl * ((T)2 + dl);                         // n^2 - 1
-                s0 += wg * (-r * gg * cm / (ne * sqv + sq));
-                s1 += wg * (r * (n2 * a * qv - gg * pv2) * cm / (n2 * sqv + sq));
+                s0 += wg * Num<T>::div(-r * gg * cm, ne * sqv + sq);
+                s1 += wg * Num<T>::div(r * (n2 * a * qv - gg * pv2) * cm, n2 * sqv + sq);
                 s2 += wg * (rr * n * r * rq);
             } else {
                 T rqv = Num<T>::rsq(qv);
@@ -441,7 +463,7 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
     if (proc == 0) {
         T il1 = sizeof(T) == 4 ? (T)Pp.il1 : (T)Pp.il1_d;
         T dil = sizeof(T) == 4 ? (T)Pp.dil : (T)Pp.dil_d;
-        lam = (T)1 / (il1 - u0 * dil);                     // density ~ 1/lambda^2
+        lam = Num<T>::div((T)1, il1 - u0 * dil);           // density ~ 1/lambda^2
         T sc, cc;
         Num<T>::sincos2pi(u2, &sc, &cc);
         T st = g.sin_tc;
@@ -478,10 +500,10 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
     T xef = to_t<T>(xe), yef = to_t<T>(ye), zef = to_t<T>(ze);
     const bool sph = A.spherical != 0, refr = A.refraction != 0;
     const T h_obs = sizeof(T) == 4 ? (T)A.h_obs : (T)A.h_obs_d;
-    const T RE = (T)A.R_E_d;
-    const P Hobs = p_from<P>(A.h_obs_d);          // exact constants for the pair arithmetic
-    const P REp = p_from<P>(A.R_E_d);
-    const P K2 = p_from<P>(A.h_obs_d + 2.0 * A.R_E_d);
+    const T RE = sizeof(T) == 4 ? (T)A.R_E : (T)A.R_E_d;
+    const P Hobs = pc<P>(A.hobs_hi, A.hobs_lo, A.h_obs_d);     // exact constants for the pair arithmetic
+    const P REp = pc<P>(A.re_hi, A.re_lo, A.R_E_d);
+    const P K2 = pc<P>(A.k2_hi, A.k2_lo, A.k2_d);
 
     // ---- vacuum straight line to the observation level (exact geometry)
     P s_v, Pvx, Pvy, Pvz, sqd;
@@ -558,13 +580,13 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
     P X, Y, tt;
     T chord = 0;
     if (sph) {
-        const T r_obs = (T)A.r_obs_d;
+        const T r_obs = sizeof(T) == 4 ? (T)A.r_obs : (T)A.r_obs_d;
         Pvx = xe + s_v * dgx;
         Pvy = ye + s_v * dgy;
         Pvz = ze + s_v * dgz;
         T RLx = to_t<T>(Pvx), RLy = to_t<T>(Pvy), RLz = to_t<T>(Pvz + REp);
         T sqf = to_t<T>(sqd);                                // r_obs cos(psi) of the vacuum line
-        T ir = (T)1 / r_obs;
+        T ir = Num<T>::div((T)1, r_obs);
         // T_v = r_obs d + cos(psi_v) R_L: in-plane tangent scaled by p_v
         T Tx = r_obs * dx + sqf * ir * RLx, Ty = r_obs * dy + sqf * ir * RLy, Tz = r_obs * dz + sqf * ir * RLz;
         T Rhx = RLx * ir, Rhy = RLy * ir, Rhz = RLz * ir;
@@ -580,7 +602,7 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
             T qvL = sqf * sqf;
             T gL = (d_obs - de) * ((T)2 + d_obs + de);
             T qL = n_obs * n_obs * qvL + gL * pv2;
-            T inr = (T)1 / (n_obs * r_obs);
+            T inr = Num<T>::div((T)1, n_obs * r_obs);
             T cpsi = Num<T>::sqr(qL) * inr;
             T spsi = ne * pv * inr;
             T at = ne * inr - cpsi * I0;
@@ -593,7 +615,7 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
         }
         // from the observation sphere back to the tangent plane z = h_obs
         T zeta = -to_t<T>(PLz - Hobs);
-        chord = zeta / dLz;
+        chord = Num<T>::div(zeta, dLz);
         X = PLx + chord * dLx;
         Y = PLy + chord * dLy;
     } else {
@@ -603,21 +625,21 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
             X = X + I0 * dx;
             Y = Y + I0 * dy;
             T qL = n_obs * n_obs * bf2 + (d_obs - de) * ((T)2 + d_obs + de) * pv2;
-            T f = ne / n_obs;
+            T f = Num<T>::div(ne, n_obs);
             dLx = f * dx;
             dLy = f * dy;
-            dLz = -Num<T>::sqr(qL) / n_obs;
+            dLz = -Num<T>::div(Num<T>::sqr(qL), n_obs);
         } else {
             dLx = dx; dLy = dy; dLz = dz;
         }
     }
     // time: t_e + (vacuum path + optical excess + chord) / c
     const T invc = (T)kInvC;
-    P sv_t = s_v * p_from<P>(kInvC);
+    P sv_t = s_v * pc<P>(A.invc_hi, A.invc_lo, kInvC);
     tt = te + sv_t + (I1 + n_obs * chord) * invc;
     T tau = 0;
     if (A.absorption) {
-        T lr = (sizeof(T) == 4 ? (T)A.lambda_ref : (T)A.lambda_ref_d) / lam;
+        T lr = Num<T>::div(sizeof(T) == 4 ? (T)A.lambda_ref : (T)A.lambda_ref_d, lam);
         T lr2 = lr * lr;
         tau = I2 * lr2 * lr2 * (sizeof(T) == 4 ? (T)A.inv_L0 : (T)A.inv_L0_d);
     }
@@ -661,19 +683,18 @@ __device__ __forceinline__ int hit_test(const RayOut<T, P> &o, int64_t seg_local
                                         const DevOut &O, unsigned &status_bits)
 {
     if (o.status != 0) return 0;
-    float Xf = (float)p_d(o.X), Yf = (float)p_d(o.Y);
+    float Xf = p_f(o.X), Yf = p_f(o.Y);
     float cz = (float)o.cz, cx = (float)o.cx, cy = (float)o.cy;
     if (!(isfinite(Xf) && isfinite(Yf) && cz < 0.0f)) return 0;
     float acz = fabsf(cz);
     float dzmax = fmaxf(fabsf(Tl.zmax - A.h_obs), fabsf(Tl.zmin - A.h_obs));
-    float rs = (Tl.Rmax + dzmax * sqrtf(fmaxf(0.0f, 1.0f - acz * acz))) / fmaxf(acz, 1e-6f) + 1e-3f;
+    float rs = (Tl.Rmax + dzmax * sqrtf(fmaxf(0.0f, 1.0f - acz * acz))) * rcp_approx(fmaxf(acz, 1e-6f)) + 1e-3f;
     if (Xf + rs < Tl.xmin || Xf - rs > Tl.xmax || Yf + rs < Tl.ymin || Yf - rs > Tl.ymax) return 0;
     int ix0 = max(0, (int)floorf((Xf - rs - Tl.gx0) * Tl.inv_gs));
     int ix1 = min(Tl.nx - 1, (int)floorf((Xf + rs - Tl.gx0) * Tl.inv_gs));
     int iy0 = max(0, (int)floorf((Yf - rs - Tl.gy0) * Tl.inv_gs));
     int iy1 = min(Tl.ny - 1, (int)floorf((Yf + rs - Tl.gy0) * Tl.inv_gs));
     int nh = 0;
-    const double h_obs = A.h_obs_d;
     for (int iy = iy0; iy <= iy1; ++iy) {
         for (int ix = ix0; ix <= ix1; ++ix) {
             int cell = iy * Tl.nx + ix;
@@ -682,8 +703,8 @@ __device__ __forceinline__ int hit_test(const RayOut<T, P> &o, int64_t seg_local
                 int j = __ldg(Tl.cell_tel + q);
                 float4 tp = __ldg(Tl.tel + j);
                 // crossing point relative to the centre, at the plane z = z_j
-                float dzj = tp.z - (float)h_obs;
-                float sj = dzj / cz;
+                float dzj = tp.z - A.h_obs;
+                float sj = Num<float>::div(dzj, cz);
                 float xr = p_f(o.X - (T)tp.x) + sj * cx;
                 float yr = p_f(o.Y - (T)tp.y) + sj * cy;
                 // impact parameter
@@ -692,7 +713,8 @@ __device__ __forceinline__ int hit_test(const RayOut<T, P> &o, int64_t seg_local
                 float d2 = wx * wx + wy * wy - wd * wd;
                 if (d2 < tp.w * tp.w) {
                     ++nh;
-                    double tj = p_d(o.t) + (double)(A.n_obs * sj) * kInvC;
+                    P tjp = o.t + (T)(A.n_obs * sj) * (T)kInvC;
+                    double tj = p_d(tjp);                        // one conversion per hit
                     uint32_t group = shower * (uint32_t)Tl.n_tel + (uint32_t)j;
                     unsigned long long key;
                     if (Pp.k_bits < 32 && k >= (1u << Pp.k_bits)) {
@@ -854,7 +876,7 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
             int64_t seg_local = s_first + l;
             int64_t seg_global = Pp.seg_base + seg_local;
             int nh = 0;
-            if (sizeof(P) == 8) {
+            if (std::is_same<P, double>::value) {   // binary64 for the precise steps
                 Seg<float, double> qd = to_fp64_guard(q);
                 RayOut<float, double> o;
                 trace_ray<float, double, true>(qd, seg_global, k, active, A, Pp, o);
