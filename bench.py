@@ -41,7 +41,7 @@ UNIT = "rays/s"
 # per candidate telescope.  MUFU (ex2, rsqrt, rcp, sincos) counted apart.
 OPS_NODE = 41
 MUFU_NODE = 5
-NODES_PER_CELL = 4
+NODES_PER_CELL = 3
 OPS_RAY = 260
 MUFU_RAY = 6
 FP32_LANES_PER_SM = 128

@@ -102,7 +102,7 @@ typedef struct {
     int32_t block;                  /* threads per block of the fused kernel (0 = default) */
     int32_t ctas_per_sm;            /* persistent CTAs per SM (0 = default) */
     int32_t use_graph;              /* capture the whole pipeline in a CUDA graph and replay */
-    float cell_width;               /* quadrature cell width in scale heights (0 = default) */
+    float cell_width;               /* quadrature cell width in scale heights (0 = 1.5) */
     int32_t key_bunch_bits;         /* bits of the bunch index in the sort key (0 = 16) */
 } clight_params;
 

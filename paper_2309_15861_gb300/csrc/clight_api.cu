@@ -237,12 +237,10 @@ clight_status clight_set_atmosphere(clight_ctx *c, const clight_atmosphere *a)
     A.inv_L0 = (float)A.inv_L0_d;
     A.lambda_ref_d = a->absorption ? a->lambda_ref : 1.0;
     A.lambda_ref = (float)A.lambda_ref_d;
-    // 4-node Gauss-Legendre on [-1, 1] (closed form)
-    const double r65 = std::sqrt(6.0 / 5.0), r30 = std::sqrt(30.0);
-    const double xs = std::sqrt(3.0 / 7.0 - 2.0 / 7.0 * r65), xl = std::sqrt(3.0 / 7.0 + 2.0 / 7.0 * r65);
-    const double ws = (18.0 + r30) / 36.0, wl = (18.0 - r30) / 36.0;
-    const double gx[4] = {-xl, -xs, xs, xl}, gw[4] = {wl, ws, ws, wl};
-    for (int i = 0; i < 4; ++i) {
+    // 3-node Gauss-Legendre on [-1, 1] (closed form): 0, +-sqrt(3/5); 8/9, 5/9
+    const double xl = std::sqrt(3.0 / 5.0);
+    const double gx[3] = {-xl, 0.0, xl}, gw[3] = {5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0};
+    for (int i = 0; i < kGLNodes; ++i) {
         A.gl_x[i] = (float)gx[i]; A.gl_w[i] = (float)gw[i];
         A.gl_x_d[i] = gx[i]; A.gl_w_d[i] = gw[i];
     }
@@ -253,7 +251,7 @@ clight_status clight_set_atmosphere(clight_ctx *c, const clight_atmosphere *a)
     // wider than cell_width scale heights.  Above the altitude where the
     // density has fallen below 1e-9 of its value at the observation level the
     // integrands are negligible, and one last cell reaches the top.
-    float cw = c->upar.cell_width > 0 ? c->upar.cell_width : 1.0f;
+    float cw = c->upar.cell_width > 0 ? c->upar.cell_width : 1.5f;
     const double rho_floor = 1e-9 * (A.delta_obs_d / (a->K > 0 ? a->K : 1.0));
     int nc = 0;
     auto add_cell = [&](double l0, double l1, int i) {

@@ -10,7 +10,7 @@ namespace clight {
 
 constexpr int kMaxLayers = 8;
 constexpr int kMaxCells = 64;
-constexpr int kGLNodes = 4;
+constexpr int kGLNodes = 3;
 
 // One altitude cell of the ray quadrature: inside it the density is
 // rho = B exp(-h/c) of a single layer, so delta = kb 2^(h nl2c) and

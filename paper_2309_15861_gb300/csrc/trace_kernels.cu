@@ -16,11 +16,14 @@
 // observation level exactly (FP32 pairs), and the refracted ray's deviation
 // from it -- angle (or distance), optical path and optical depth -- comes
 // from the Snell / Bouguer invariant as integrals over altitude, written in
-// a form free of cancellation and evaluated by 4-node Gauss-Legendre on
-// altitude cells no wider than a fixed fraction of the local scale height.
+// a form free of cancellation and evaluated by 3-node Gauss-Legendre on
+// altitude cells no wider than a fixed multiple of the local scale height.
 // The bulk of the arithmetic is binary32; FP32 pairs (or binary64, by
 // parameter) carry only the emission point, the vacuum path, the landing
 // point and the arrival time.
+//
+// Geometry (flat / spherical Earth) and refraction (on / off) are template
+// parameters, so each launch runs a kernel holding only its own branch.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -34,30 +37,33 @@ namespace clight {
 #define FULL_MASK 0xffffffffu
 
 // ------------------------------------------------------------------ numerics
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 template <class T> struct Num;
 template <> struct Num<float> {
     static __device__ __forceinline__ float div(float a, float b) { return a * rcp_approx(b); }
-    static __device__ __forceinline__ float ex2(float x) { return exp2f(x); }
-    static __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+    static __device__ __forceinline__ float rsq(float x) { return rsqrt_approx(x); }
     static __device__ __forceinline__ float sqr(float x) { return sqrtf(x); }
-    static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
     static __device__ __forceinline__ void sincos2pi(float u, float *s, float *c) { sincospif(2.0f * u, s, c); }
 };
 template <> struct Num<double> {
     static __device__ __forceinline__ double div(double a, double b) { return a / b; }
-    static __device__ __forceinline__ double ex2(double x) { return exp2(x); }
     static __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
     static __device__ __forceinline__ double sqr(double x) { return sqrt(x); }
-    static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
     static __device__ __forceinline__ void sincos2pi(double u, double *s, double *c) { sincospi(2.0 * u, s, c); }
 };
 
-template <class P> __device__ __forceinline__ P p_from(double x);
-template <> __device__ __forceinline__ df p_from<df>(double x) { return df_from_double(x); }
-template <> __device__ __forceinline__ double p_from<double>(double x) { return x; }
-template <class P> __device__ __forceinline__ P p_fromf(float x);
-template <> __device__ __forceinline__ df p_fromf<df>(float x) { return df_make(x); }
-template <> __device__ __forceinline__ double p_fromf<double>(float x) { return (double)x; }
 // exact widening of a bulk-precision value into the pair/binary64 type
 __device__ __forceinline__ void p_set(df &o, float x) { o = df_make(x); }
 __device__ __forceinline__ void p_set(double &o, float x) { o = (double)x; }
@@ -68,13 +74,7 @@ template <class P, class T> __device__ __forceinline__ P p_of(T x)
     p_set(o, x);
     return o;
 }
-__device__ __forceinline__ float p_f(df a) { return __fadd_rn(a.hi, a.lo); }
-__device__ __forceinline__ float p_f(double a) { return (float)a; }
-__device__ __forceinline__ double p_d(df a) { return df_to_double(a); }
-__device__ __forceinline__ double p_d(double a) { return a; }
-__device__ __forceinline__ df p_sqrt(df a) { return df_sqrt(a); }
-__device__ __forceinline__ double p_sqrt(double a) { return sqrt(a); }
-// constants held both as FP32 pairs and binary64 in DevAtm
+// constants held both as FP32 pairs and binary64
 __device__ __forceinline__ void p_const(df &o, float hi, float lo, double) { o = {hi, lo}; }
 __device__ __forceinline__ void p_const(double &o, float, float, double d) { o = d; }
 template <class P> __device__ __forceinline__ P pc(float hi, float lo, double d)
@@ -83,9 +83,16 @@ template <class P> __device__ __forceinline__ P pc(float hi, float lo, double d)
     p_const(o, hi, lo, d);
     return o;
 }
+__device__ __forceinline__ float p_f(df a) { return __fadd_rn(a.hi, a.lo); }
+__device__ __forceinline__ float p_f(double a) { return (float)a; }
+__device__ __forceinline__ double p_d(df a) { return df_to_double(a); }
+__device__ __forceinline__ double p_d(double a) { return a; }
 template <class T> __device__ __forceinline__ T to_t(df a);
 template <> __device__ __forceinline__ float to_t<float>(df a) { return p_f(a); }
 template <class T> __device__ __forceinline__ T to_t(double a) { return (T)a; }
+// a pair as the precise type (the FP64-guard variant widens it to binary64)
+__device__ __forceinline__ void p_from_pair(df &o, df a) { o = a; }
+__device__ __forceinline__ void p_from_pair(double &o, df a) { o = df_to_double(a); }
 
 // ------------------------------------------------------------------ Philox
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): per round two 32x32->64
@@ -116,6 +123,8 @@ template <> __device__ __forceinline__ float u01<float>(uint32_t x)
 }
 
 // ------------------------------------------------------------------ atmosphere
+// delta = n - 1 at one altitude (binary32 through the library exp2f, 2 ulp;
+// the quadrature nodes use the raw MUFU estimate).
 template <class T> struct AtmT;
 template <> struct AtmT<float> {
     static __device__ __forceinline__ float delta(const DevAtm &A, float h)
@@ -139,11 +148,16 @@ template <> struct AtmT<double> {
     }
 };
 
-// Altitude without cancellation: |r + R_E z| - R_E = (x^2 + y^2 + z (z + 2 R_E)) / (|r + R_E z| + R_E).
-template <class T> __device__ __forceinline__ T altitude(const DevAtm &A, T x, T y, T z)
+template <class T> __device__ __forceinline__ T earth_radius(const DevAtm &A)
 {
-    if (!A.spherical) return z;
-    const T RE = sizeof(T) == 4 ? (T)A.R_E : (T)A.R_E_d;
+    return sizeof(T) == 4 ? (T)A.R_E : (T)A.R_E_d;
+}
+
+// Altitude without cancellation: |r + R_E z| - R_E = (x^2 + y^2 + z (z + 2 R_E)) / (|r + R_E z| + R_E).
+template <class T, bool SPH> __device__ __forceinline__ T altitude(const DevAtm &A, T x, T y, T z)
+{
+    if (!SPH) return z;
+    const T RE = earth_radius<T>(A);
     T num = x * x + y * y + z * (z + (T)2 * RE);
     T zc = z + RE;
     return Num<T>::div(num, Num<T>::sqr(x * x + y * y + zc * zc) + RE);
@@ -155,12 +169,14 @@ template <class T> __device__ __forceinline__ T altitude(const DevAtm &A, T x, T
 // per-step quantities).
 template <class T, class P> struct Seg {
     P x0, y0, z0, t0;
+    P rz0;               // z0 + R_E (spherical): Earth-centred height of the start
     T dx, dy, dz;        // unit direction (binary32 part)
     T lx, ly, lz;        // its normalisation correction (pair low part)
     T e1x, e1y, e1z, e2x, e2y, e2z;   // M_Rod x, M_Rod y
     T sin_tc, kappa;     // sin(theta_c), 1 - cos(theta_c)
     T L, inv_bc;         // step length, 1/(beta c) in ns/m
     T w_c, w_f;
+    T h_mid;             // midpoint altitude
     uint32_t n_c, n_f;
     uint32_t shower;
     int bad;             // 0 ok, else CLIGHT_ERR_* code
@@ -175,9 +191,17 @@ __device__ __forceinline__ bool finite_d(double v)
     return ((unsigned long long)__double_as_longlong(v) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
 }
 
+__device__ __forceinline__ bool segment_ok(const clight_segment &s, const DevPar &P)
+{
+    return finite_d(s.x) && finite_d(s.y) && finite_d(s.z) && finite_d(s.t0) && finite_f(s.dx) &&
+           finite_f(s.dy) && finite_f(s.dz) && finite_f(s.L) && finite_f(s.eps) && finite_f(s.dE) &&
+           s.L >= 0.0f && s.eps >= 0.0f && s.eps < 1.0f && (int)s.shower < P.n_showers && s.shower < 0x7fffffffu;
+}
+
 // Yield and bunch count in binary64 (the plain path, and the guard of the
 // FP32 path when its count is not certain).  Frank-Tamm (Sec. 1.2):
 // N = 2 pi alpha z^2 (1/l1 - 1/l2) (1 - 1/(beta n)^2) L for beta n > 1.
+template <bool SPH>
 __device__ __forceinline__ void yield_fp64(const clight_segment &s, const DevAtm &A, const DevPar &P,
                                            double ux, double uy, double uz, double *Nc, double *sin2,
                                            double *kappa, double *Nf)
@@ -185,7 +209,7 @@ __device__ __forceinline__ void yield_fp64(const clight_segment &s, const DevAtm
     double xm = s.x + 0.5 * (double)s.L * ux, ym = s.y + 0.5 * (double)s.L * uy,
            zm = s.z + 0.5 * (double)s.L * uz;
     double h;
-    if (A.spherical) {
+    if (SPH) {
         double zc = zm + A.R_E_d;
         h = sqrt(xm * xm + ym * ym + zc * zc) - A.R_E_d;
     } else {
@@ -215,7 +239,7 @@ __device__ __forceinline__ void make_frame(Seg<T, P> &g)
     T ax = g.dx, ay = g.dy, az = g.dz - (T)1;
     T na2 = ax * ax + ay * ay + az * az;
     if (na2 > (T)0) {
-        T inv = Num<T>::rsq(na2);
+        T inv = (T)1 / Num<T>::sqr(na2);
         ax *= inv; ay *= inv; az *= inv;
     } else {
         ax = (T)1; ay = (T)0; az = (T)0;
@@ -225,33 +249,30 @@ __device__ __forceinline__ void make_frame(Seg<T, P> &g)
 }
 
 // binary32 segment set-up with the binary64 guard on the integer bunch count.
-__device__ void load_segment_f(const clight_segment &s, const DevAtm &A, const DevPar &P,
-                               Seg<float, df> &g)
+template <bool SPH>
+__device__ void load_segment_f(const clight_segment &s, const DevAtm &A, const DevPar &P, Seg<float, df> &g)
 {
     g.bad = 0;
     g.guarded = 0;
     g.n_c = g.n_f = 0;
     g.w_c = g.w_f = 0.0f;
     g.shower = s.shower;
-    bool ok = finite_d(s.x) && finite_d(s.y) && finite_d(s.z) && finite_d(s.t0) && finite_f(s.dx) &&
-              finite_f(s.dy) && finite_f(s.dz) && finite_f(s.L) && finite_f(s.eps) && finite_f(s.dE) &&
-              s.L >= 0.0f && s.eps >= 0.0f && s.eps < 1.0f && (int)s.shower < P.n_showers &&
-              s.shower < 0x7fffffffu;
+    g.h_mid = 0.0f;
     float n2 = s.dx * s.dx + s.dy * s.dy + s.dz * s.dz;
-    if (!ok || !(n2 > 0.0f)) {
+    if (!segment_ok(s, P) || !(n2 > 0.0f)) {
         g.bad = CLIGHT_ERR_BAD_SEGMENT;
         g.dx = 0; g.dy = 0; g.dz = -1; g.lx = g.ly = g.lz = 0;
-        g.x0 = g.y0 = g.z0 = g.t0 = df_make(0.0f);
+        g.x0 = g.y0 = g.z0 = g.t0 = g.rz0 = df_make(0.0f);
         g.L = 0; g.inv_bc = 0; g.sin_tc = 0; g.kappa = 0;
         make_frame(g);
         return;
     }
-    // unit direction as a pair: d (1 - e/2 + 3 e^2/8), e = |d|^2 - 1 exactly
+    // unit direction as a pair: the binary32 part normalised, the residual
+    // -(|d|^2 - 1)/2 d (from exact products) as the low part
     df sq = two_prod(s.dx, s.dx) + two_prod(s.dy, s.dy) + two_prod(s.dz, s.dz);
     float e = p_f(sq - 1.0f);
-    float f = rsqrtf(1.0f + e);                  // normalisation of the binary32 part
+    float f = rsqrtf(1.0f + e);
     g.dx = s.dx * f; g.dy = s.dy * f; g.dz = s.dz * f;
-    // residual of the rounded unit vector (pair low part)
     df r2 = two_prod(g.dx, g.dx) + two_prod(g.dy, g.dy) + two_prod(g.dz, g.dz);
     float e2 = p_f(r2 - 1.0f);
     g.lx = -0.5f * e2 * g.dx; g.ly = -0.5f * e2 * g.dy; g.lz = -0.5f * e2 * g.dz;
@@ -259,6 +280,7 @@ __device__ void load_segment_f(const clight_segment &s, const DevAtm &A, const D
     g.y0 = df_from_double_bits(s.y);
     g.z0 = df_from_double_bits(s.z);
     g.t0 = df_from_double_bits(s.t0);
+    g.rz0 = SPH ? g.z0 + df{A.re_hi, A.re_lo} : g.z0;
     g.L = s.L;
     g.inv_bc = Num<float>::div(3.3356409519815204f, 1.0f - s.eps);   // 1/(beta c), ns/m
     make_frame(g);
@@ -266,7 +288,8 @@ __device__ void load_segment_f(const clight_segment &s, const DevAtm &A, const D
     // midpoint altitude and refractivity (n constant over the step)
     float hL = 0.5f * s.L;
     float xm = g.x0.hi + hL * g.dx, ym = g.y0.hi + hL * g.dy, zm = g.z0.hi + hL * g.dz;
-    float hm = altitude<float>(A, xm, ym, zm);
+    float hm = altitude<float, SPH>(A, xm, ym, zm);
+    g.h_mid = hm;
     float dl = AtmT<float>::delta(A, hm);
     float eps = s.eps;
     float z2 = (float)s.charge * (float)s.charge;
@@ -307,8 +330,8 @@ __device__ void load_segment_f(const clight_segment &s, const DevAtm &A, const D
     if (guard || fguard) {
         g.guarded = 1;
         double Ncd, sin2d, kapd, Nfd;
-        yield_fp64(s, A, P, (double)g.dx + (double)g.lx, (double)g.dy + (double)g.ly,
-                   (double)g.dz + (double)g.lz, &Ncd, &sin2d, &kapd, &Nfd);
+        yield_fp64<SPH>(s, A, P, (double)g.dx + (double)g.lx, (double)g.dy + (double)g.ly,
+                        (double)g.dz + (double)g.lz, &Ncd, &sin2d, &kapd, &Nfd);
         if (guard) {
             double nb = ceil(Ncd / P.bunch_d);
             g.n_c = (uint32_t)nb;
@@ -329,20 +352,16 @@ __device__ void load_segment_f(const clight_segment &s, const DevAtm &A, const D
 }
 
 // binary64 segment set-up (plain path).
-__device__ void load_segment_d(const clight_segment &s, const DevAtm &A, const DevPar &P,
-                               Seg<double, double> &g)
+template <bool SPH>
+__device__ void load_segment_d(const clight_segment &s, const DevAtm &A, const DevPar &P, Seg<double, double> &g)
 {
     g.bad = 0;
     g.guarded = 0;
     g.n_c = g.n_f = 0;
     g.w_c = g.w_f = 0.0;
     g.shower = s.shower;
-    bool ok = isfinite(s.x) && isfinite(s.y) && isfinite(s.z) && isfinite(s.t0) && finite_f(s.dx) &&
-              finite_f(s.dy) && finite_f(s.dz) && finite_f(s.L) && finite_f(s.eps) && finite_f(s.dE) &&
-              s.L >= 0.0f && s.eps >= 0.0f && s.eps < 1.0f && (int)s.shower < P.n_showers &&
-              s.shower < 0x7fffffffu;
     double n2 = (double)s.dx * s.dx + (double)s.dy * s.dy + (double)s.dz * s.dz;
-    if (!ok || !(n2 > 0.0)) {
+    if (!segment_ok(s, P) || !(n2 > 0.0)) {
         g.bad = CLIGHT_ERR_BAD_SEGMENT;
         return;
     }
@@ -350,11 +369,12 @@ __device__ void load_segment_d(const clight_segment &s, const DevAtm &A, const D
     g.dx = s.dx * inv; g.dy = s.dy * inv; g.dz = s.dz * inv;
     g.lx = g.ly = g.lz = 0.0;
     g.x0 = s.x; g.y0 = s.y; g.z0 = s.z; g.t0 = s.t0;
+    g.rz0 = SPH ? s.z + A.R_E_d : s.z;
     g.L = s.L;
     g.inv_bc = kInvC / (1.0 - (double)s.eps);
     make_frame(g);
     double Nc, sin2, kap, Nf;
-    yield_fp64(s, A, P, g.dx, g.dy, g.dz, &Nc, &sin2, &kap, &Nf);
+    yield_fp64<SPH>(s, A, P, g.dx, g.dy, g.dz, &Nc, &sin2, &kap, &Nf);
     g.sin_tc = sqrt(sin2);
     g.kappa = kap;
     if (Nc > 0.0) {
@@ -386,12 +406,12 @@ template <class T, class P> struct RayOut {
 //   I2: density-weighted path (rho / rho_ref) ds.
 // r = R_E + h (spherical) or 1 (flat); q_v = r^2 - p_v^2,
 // q = n^2 q_v + (n^2 - n_e^2) p_v^2 = n^2 r^2 - (n_e p_v)^2.
-template <class T, bool WARP>
-__device__ __forceinline__ void ray_quadrature(const DevAtm &A, T hcap, T he, T de, T pv2, T bf2,
-                                               bool sph, bool refr, T &I0, T &I1, T &I2, uint32_t &ncell)
+template <class T, bool WARP, bool SPH, bool REFR>
+__device__ __forceinline__ void ray_quadrature(const DevAtm &A, T hcap, T he, T de, T pv2, T bf2, T &I0, T &I1,
+                                               T &I2, uint32_t &ncell)
 {
     I0 = I1 = I2 = (T)0;
-    const T RE = sizeof(T) == 4 ? (T)A.R_E : (T)A.R_E_d;
+    const T RE = earth_radius<T>(A);
     const T ne = (T)1 + de;
     for (int c = 0; c < A.n_cells; ++c) {
         const DevCell &C = A.cells[c];
@@ -418,12 +438,12 @@ __device__ __forceinline__ void ray_quadrature(const DevAtm &A, T hcap, T he, T 
             else { xg = (T)A.gl_x_d[gi]; wg = (T)A.gl_w_d[gi]; }
             T h = mid + half * xg;
             // float: 2^(h nl) with nl = -log2(e)/c; double: e^(h nl) with nl = -1/c
-            T ex = sizeof(T) == 4 ? (T)Num<float>::ex2((float)(h * nl)) : (T)exp((double)(h * nl));
+            T ex = sizeof(T) == 4 ? (T)ex2_approx((float)(h * nl)) : (T)exp((double)(h * nl));
             T dl = kb * ex;
             T rr = rb * ex;
-            T r = sph ? RE + h : (T)1;
-            T qv = sph ? (h - he) * ((T)2 * RE + h + he) + bf2 : bf2;
-            if (refr) {
+            T r = SPH ? RE + h : (T)1;
+            T qv = SPH ? (h - he) * ((T)2 * RE + h + he) + bf2 : bf2;
+            if (REFR) {
                 T n = (T)1 + dl;
                 T n2 = n * n;
                 T gg = (dl - de) * ((T)2 + dl + de);          // n^2 - n_e^2
@@ -447,7 +467,7 @@ __device__ __forceinline__ void ray_quadrature(const DevAtm &A, T hcap, T he, T 
     }
 }
 
-template <class T, class P, bool WARP>
+template <class T, class P, bool WARP, bool SPH, bool REFR>
 __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global, uint32_t k, bool active,
                                           const DevAtm &A, const DevPar &Pp, RayOut<T, P> &o)
 {
@@ -483,9 +503,9 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
         T sz = Num<T>::sqr(((T)1 - cz) * ((T)1 + cz));
         T sp, cp;
         Num<T>::sincos2pi(u2, &sp, &cp);
-        dgx = p_fromf<P>(0.0f) + sz * cp;
-        dgy = p_fromf<P>(0.0f) + sz * sp;
-        dgz = p_fromf<P>(0.0f) + cz;
+        dgx = p_of<P>(sz * cp);
+        dgy = p_of<P>(sz * sp);
+        dgz = p_of<P>(cz);
         w = g.w_f;
     }
     T ell = u1 * g.L;
@@ -498,64 +518,65 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
 
     T dx = to_t<T>(dgx), dy = to_t<T>(dgy), dz = to_t<T>(dgz);
     T xef = to_t<T>(xe), yef = to_t<T>(ye), zef = to_t<T>(ze);
-    const bool sph = A.spherical != 0, refr = A.refraction != 0;
     const T h_obs = sizeof(T) == 4 ? (T)A.h_obs : (T)A.h_obs_d;
-    const T RE = sizeof(T) == 4 ? (T)A.R_E : (T)A.R_E_d;
     const P Hobs = pc<P>(A.hobs_hi, A.hobs_lo, A.h_obs_d);     // exact constants for the pair arithmetic
-    const P REp = pc<P>(A.re_hi, A.re_lo, A.R_E_d);
-    const P K2 = pc<P>(A.k2_hi, A.k2_lo, A.k2_d);
 
     // ---- vacuum straight line to the observation level (exact geometry)
-    P s_v, Pvx, Pvy, Pvz, sqd;
-    T he, pv2, bf2, bf;
+    P s_v;
+    T he, pv2, bf2, bf, sqf = 0;
     bool esc = false, under = false, turned = false, grazing = false;
-    if (sph) {
-        P Rz = ze + REp;
-        // b = -(d . R_e) = r_e cos(psi_e)
+    if (SPH) {
+        P Rz = g.rz0 + ell * (g.dz + g.lz);                 // z_e + R_E
+        // b = -(d . R_e) = r_e cos(psi_e); C = |R_e|^2 - r_obs^2
         P b = -(dgz * Rz) - (dx * xef + dy * yef);
-        he = altitude<T>(A, xef, yef, zef);
+        he = altitude<T, SPH>(A, xef, yef, zef);
         esc = !(p_f(b) > 0.0f);
         under = he <= h_obs;
         P dzo = ze - Hobs;
-        P C = dzo * (ze + K2) + (xef * xef + yef * yef);
-        P disc = b * b - C;
+        P C = dzo * (ze + pc<P>(A.k2_hi, A.k2_lo, A.k2_d)) + (xef * xef + yef * yef);
         T Rzf = to_t<T>(Rz);
         T c1 = dy * Rzf - dz * yef, c2 = dz * xef - dx * Rzf, c3 = dx * yef - dy * xef;
         pv2 = c1 * c1 + c2 * c2 + c3 * c3;                   // (r_e sin psi_e)^2
         bf = to_t<T>(b);
         bf2 = bf * bf;                                       // (r_e cos psi_e)^2
-        // The ray reaches the observation sphere when q(r_obs) > 0; with
-        // q_v(r_obs) = disc, q(r_obs) = n_obs^2 disc + (n_obs^2 - n_e^2) p_v^2.
-        T discf = to_t<T>(disc);
-        if (refr) {
+        // s_v = b - sqrt(b^2 - C) = (C / b) / (1 + sqrt(1 - x)), x = C / b^2,
+        // and 1 / (1 + sqrt(1 - x)) = 1/2 + g with g = x / (2 (1 + sqrt(1 - x))^2)
+        // small enough that binary32 carries it to ~1e-9 absolute.
+        T xx = Num<T>::div(to_t<T>(C), bf2);
+        T om = (T)1 - xx;                                    // disc / b^2
+        T discf = bf2 * om;
+        if (REFR) {
+            // reaches the observation sphere iff q(r_obs) > 0, with
+            // q_v(r_obs) = disc: q(r_obs) = n_obs^2 disc + (n_obs^2 - n_e^2) p_v^2
             T de0 = AtmT<T>::delta(A, he);
             T dob = sizeof(T) == 4 ? (T)A.delta_obs : (T)A.delta_obs_d;
             T nob = (T)1 + dob;
             T qL = nob * nob * discf + (dob - de0) * ((T)2 + dob + de0) * pv2;
             turned = !(qL > (T)0);
-            // reaches, but the vacuum line passes above the sphere: a grazing
-            // ray that lands far from the array; counted, not landed
-            grazing = !turned && !(discf > (T)0);
+            grazing = !turned && !(om > (T)0);   // reaches, but the vacuum line misses: not landed
         } else {
-            turned = !(discf > (T)0);
+            turned = !(om > (T)0);
         }
         if (!(esc || under || turned || grazing)) {
-            sqd = p_sqrt(disc);
-            s_v = C / (b + sqd);
+            T so = Num<T>::sqr(om);
+            T gx = Num<T>::div(xx, (T)2 * ((T)1 + so) * ((T)1 + so));
+            P f;
+            if (sizeof(T) == 4) p_from_pair(f, df{0.5f, (float)gx});
+            else f = p_of<P>((T)0.5 + gx);
+            s_v = (C / b) * f;
+            sqf = bf * so;                                   // r_obs cos(psi) of the vacuum line
         } else {
-            sqd = p_fromf<P>(0.0f);
-            s_v = p_fromf<P>(0.0f);
+            s_v = p_of<P>((T)0);
         }
     } else {
         he = zef;
         esc = !(p_f(dgz) < 0.0f);
         under = !(p_f(ze - Hobs) > 0.0f);
         if (!(esc || under)) s_v = (ze - Hobs) / (-dgz);
-        else s_v = p_fromf<P>(0.0f);
+        else s_v = p_of<P>((T)0);
         pv2 = dx * dx + dy * dy;                             // sin^2 theta_e
         bf = -dz;
         bf2 = bf * bf;                                       // cos^2 theta_e
-        sqd = p_fromf<P>(0.0f);
     }
     if (!active) { o.status = 4; }
     else if (esc) { o.status = 1; }
@@ -570,7 +591,7 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
     T hcap = go ? (he < htop ? he : htop) : (T)-1e30;
     T I0, I1, I2;
     o.cells = 0;
-    ray_quadrature<T, WARP>(A, hcap, he, de, pv2, bf2, sph, refr, I0, I1, I2, o.cells);
+    ray_quadrature<T, WARP, SPH, REFR>(A, hcap, he, de, pv2, bf2, I0, I1, I2, o.cells);
     if (!go) return;
 
     const T n_obs = sizeof(T) == 4 ? (T)A.n_obs : (T)1 + (T)A.delta_obs_d;
@@ -579,19 +600,18 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
     T dLx, dLy, dLz;
     P X, Y, tt;
     T chord = 0;
-    if (sph) {
+    if (SPH) {
         const T r_obs = sizeof(T) == 4 ? (T)A.r_obs : (T)A.r_obs_d;
-        Pvx = xe + s_v * dgx;
-        Pvy = ye + s_v * dgy;
-        Pvz = ze + s_v * dgz;
-        T RLx = to_t<T>(Pvx), RLy = to_t<T>(Pvy), RLz = to_t<T>(Pvz + REp);
-        T sqf = to_t<T>(sqd);                                // r_obs cos(psi) of the vacuum line
+        P Pvx = xe + s_v * dgx;
+        P Pvy = ye + s_v * dgy;
+        P Pvz = ze + s_v * dgz;
+        T RLx = to_t<T>(Pvx), RLy = to_t<T>(Pvy), RLz = to_t<T>(Pvz + pc<P>(A.re_hi, A.re_lo, A.R_E_d));
         T ir = Num<T>::div((T)1, r_obs);
         // T_v = r_obs d + cos(psi_v) R_L: in-plane tangent scaled by p_v
         T Tx = r_obs * dx + sqf * ir * RLx, Ty = r_obs * dy + sqf * ir * RLy, Tz = r_obs * dz + sqf * ir * RLz;
         T Rhx = RLx * ir, Rhy = RLy * ir, Rhz = RLz * ir;
         P PLx = Pvx, PLy = Pvy, PLz = Pvz;
-        if (refr) {
+        if (REFR) {
             T pv = Num<T>::sqr(pv2);
             T dphi = I0 * pv;
             T sfac = r_obs * I0;                              // r_obs dphi / p_v
@@ -621,7 +641,7 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
     } else {
         X = xe + s_v * dgx;
         Y = ye + s_v * dgy;
-        if (refr) {
+        if (REFR) {
             X = X + I0 * dx;
             Y = Y + I0 * dy;
             T qL = n_obs * n_obs * bf2 + (d_obs - de) * ((T)2 + d_obs + de) * pv2;
@@ -685,7 +705,7 @@ __device__ __forceinline__ int hit_test(const RayOut<T, P> &o, int64_t seg_local
     if (o.status != 0) return 0;
     float Xf = p_f(o.X), Yf = p_f(o.Y);
     float cz = (float)o.cz, cx = (float)o.cx, cy = (float)o.cy;
-    if (!(isfinite(Xf) && isfinite(Yf) && cz < 0.0f)) return 0;
+    if (!(finite_f(Xf) && finite_f(Yf) && cz < 0.0f)) return 0;
     float acz = fabsf(cz);
     float dzmax = fmaxf(fabsf(Tl.zmax - A.h_obs), fabsf(Tl.zmin - A.h_obs));
     float rs = (Tl.Rmax + dzmax * sqrtf(fmaxf(0.0f, 1.0f - acz * acz))) * rcp_approx(fmaxf(acz, 1e-6f)) + 1e-3f;
@@ -708,9 +728,8 @@ __device__ __forceinline__ int hit_test(const RayOut<T, P> &o, int64_t seg_local
                 float xr = p_f(o.X - (T)tp.x) + sj * cx;
                 float yr = p_f(o.Y - (T)tp.y) + sj * cy;
                 // impact parameter
-                float wx = -xr, wy = -yr;                       // centre minus crossing point
-                float wd = wx * cx + wy * cy;
-                float d2 = wx * wx + wy * wy - wd * wd;
+                float wd = xr * cx + yr * cy;
+                float d2 = xr * xr + yr * yr - wd * wd;
                 if (d2 < tp.w * tp.w) {
                     ++nh;
                     P tjp = o.t + (T)(A.n_obs * sj) * (T)kInvC;
@@ -748,45 +767,38 @@ __device__ __forceinline__ int hit_test(const RayOut<T, P> &o, int64_t seg_local
 // Shared-memory record of a warp's 32 segments, one field per row so that
 // lanes reading one field of different segments hit different banks.
 enum SegField {
-    F_X0H, F_X0L, F_Y0H, F_Y0L, F_Z0H, F_Z0L, F_T0H, F_T0L,
+    F_X0H, F_X0L, F_Y0H, F_Y0L, F_Z0H, F_Z0L, F_T0H, F_T0L, F_RZH, F_RZL,
     F_DX, F_DY, F_DZ, F_LX, F_LY, F_LZ, F_E1X, F_E1Y, F_E1Z, F_E2X, F_E2Y, F_E2Z,
-    F_SIN, F_KAP, F_L, F_IBC, F_WC, F_WF, F_NC, F_NF, F_SHOWER, F_INCL, F_COUNT
+    F_SIN, F_KAP, F_L, F_IBC, F_WC, F_WF, F_NC, F_NF, F_SHOWER, F_SEGI, F_INCL, F_COUNT
 };
 
 int fused_smem_bytes(int block) { return (block / 32) * F_COUNT * 32 * (int)sizeof(float); }
 
-template <class P> struct PStore;
-template <> struct PStore<df> {
-    static __device__ __forceinline__ void put(float *row_h, float *row_l, int l, df v) { row_h[l] = v.hi; row_l[l] = v.lo; }
-    static __device__ __forceinline__ df get(const float *row_h, const float *row_l, int l) { return {row_h[l], row_l[l]}; }
-};
-template <> struct PStore<double> {
-    static __device__ __forceinline__ void put(float *row_h, float *row_l, int l, double v)
-    {
-        unsigned long long b = (unsigned long long)__double_as_longlong(v);
-        row_h[l] = __uint_as_float((uint32_t)b);
-        row_l[l] = __uint_as_float((uint32_t)(b >> 32));
-    }
-    static __device__ __forceinline__ double get(const float *row_h, const float *row_l, int l)
-    {
-        unsigned long long b = (unsigned long long)__float_as_uint(row_h[l]) |
-                               ((unsigned long long)__float_as_uint(row_l[l]) << 32);
-        return __longlong_as_double((long long)b);
-    }
-};
-
-__device__ __forceinline__ Seg<float, double> to_fp64_guard(const Seg<float, df> &a)
+__device__ __forceinline__ void put_df(float *S, int fh, int fl, int l, df v)
 {
-    Seg<float, double> b;
-    b.x0 = df_to_double(a.x0); b.y0 = df_to_double(a.y0); b.z0 = df_to_double(a.z0); b.t0 = df_to_double(a.t0);
-    b.dx = a.dx; b.dy = a.dy; b.dz = a.dz; b.lx = a.lx; b.ly = a.ly; b.lz = a.lz;
-    b.e1x = a.e1x; b.e1y = a.e1y; b.e1z = a.e1z; b.e2x = a.e2x; b.e2y = a.e2y; b.e2z = a.e2z;
-    b.sin_tc = a.sin_tc; b.kappa = a.kappa; b.L = a.L; b.inv_bc = a.inv_bc; b.w_c = a.w_c; b.w_f = a.w_f;
-    b.n_c = a.n_c; b.n_f = a.n_f; b.shower = a.shower; b.bad = a.bad; b.guarded = a.guarded;
-    return b;
+    S[fh * 32 + l] = v.hi;
+    S[fl * 32 + l] = v.lo;
+}
+__device__ __forceinline__ df get_df(const float *S, int fh, int fl, int l) { return {S[fh * 32 + l], S[fl * 32 + l]}; }
+
+// Bitonic sort of one 32-bit key per lane across the warp (ascending).
+__device__ __forceinline__ uint32_t warp_sort_u32(uint32_t key, int lane)
+{
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            uint32_t other = __shfl_xor_sync(FULL_MASK, key, j);
+            bool up = (lane & k) == 0;
+            bool lower = (lane & j) == 0;
+            uint32_t mn = min(key, other), mx = max(key, other);
+            key = (lower == up) ? mn : mx;
+        }
+    }
+    return key;
 }
 
-template <class P>
+template <class P, bool SPH, bool REFR>
 __global__ void __launch_bounds__(256, 2)
 k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid_constant__ DevAtm A,
               const __grid_constant__ DevTel Tl, const __grid_constant__ DevPar Pp, const __grid_constant__ DevOut O)
@@ -806,43 +818,61 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
         // ---- per-segment set-up, one segment per lane
         Seg<float, df> g;
         uint32_t nb = 0;
+        uint32_t key = 0xFFFFFFE0u | (uint32_t)lane;          // empty lanes sort last
         if (si < n_segs) {
             clight_segment s;
             const float4 *src = reinterpret_cast<const float4 *>(segs + si);
             float4 *dst = reinterpret_cast<float4 *>(&s);
             dst[0] = __ldg(src); dst[1] = __ldg(src + 1); dst[2] = __ldg(src + 2); dst[3] = __ldg(src + 3);
-            load_segment_f(s, A, Pp, g);
+            load_segment_f<SPH>(s, A, Pp, g);
             if (g.bad) status_bits |= 1u << g.bad;
             c_guard += g.guarded;
             nb = g.n_c + g.n_f;
             if (nb < g.n_c || nb > 0x7fffffffu) { status_bits |= 1u << CLIGHT_ERR_LIMIT; nb = 0; }
+            // order the warp's segments by altitude (500 m bins), so that the
+            // rays of one round need similar numbers of quadrature cells
+            uint32_t bin = (uint32_t)fminf(fmaxf(g.h_mid * 2.0e-3f, 0.0f), 1.0e6f);
+            key = (bin << 5) | (uint32_t)lane;
         } else {
             g.n_c = g.n_f = 0;
         }
-        // warp inclusive scan of the bunch counts -> flattened ray index
-        uint32_t incl = nb;
+        key = warp_sort_u32(key, lane);
+        // the segment of source lane (key & 31) takes position `lane`; each
+        // source lane learns its position through shared memory
+        __syncwarp();
+        S[F_INCL * 32 + (key & 31u)] = __uint_as_float((uint32_t)lane);
+        __syncwarp();
+        const int pos = (int)__float_as_uint(S[F_INCL * 32 + lane]);
+        __syncwarp();
+        // inclusive scan of the bunch counts in sorted order
+        uint32_t incl = __shfl_sync(FULL_MASK, nb, (int)(key & 31u));
+        uint32_t total;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             uint32_t v = __shfl_up_sync(FULL_MASK, incl, o);
             if (lane >= o) incl += v;
         }
-        uint32_t total = __shfl_sync(FULL_MASK, incl, 31);
-        __syncwarp();
+        total = __shfl_sync(FULL_MASK, incl, 31);
         if (si < n_segs) {
-            PStore<df>::put(S + F_X0H * 32, S + F_X0L * 32, lane, g.x0);
-            PStore<df>::put(S + F_Y0H * 32, S + F_Y0L * 32, lane, g.y0);
-            PStore<df>::put(S + F_Z0H * 32, S + F_Z0L * 32, lane, g.z0);
-            PStore<df>::put(S + F_T0H * 32, S + F_T0L * 32, lane, g.t0);
-            S[F_DX * 32 + lane] = g.dx; S[F_DY * 32 + lane] = g.dy; S[F_DZ * 32 + lane] = g.dz;
-            S[F_LX * 32 + lane] = g.lx; S[F_LY * 32 + lane] = g.ly; S[F_LZ * 32 + lane] = g.lz;
-            S[F_E1X * 32 + lane] = g.e1x; S[F_E1Y * 32 + lane] = g.e1y; S[F_E1Z * 32 + lane] = g.e1z;
-            S[F_E2X * 32 + lane] = g.e2x; S[F_E2Y * 32 + lane] = g.e2y; S[F_E2Z * 32 + lane] = g.e2z;
-            S[F_SIN * 32 + lane] = g.sin_tc; S[F_KAP * 32 + lane] = g.kappa;
-            S[F_L * 32 + lane] = g.L; S[F_IBC * 32 + lane] = g.inv_bc;
-            S[F_WC * 32 + lane] = g.w_c; S[F_WF * 32 + lane] = g.w_f;
-            S[F_NC * 32 + lane] = __uint_as_float(g.n_c);
-            S[F_NF * 32 + lane] = __uint_as_float(g.n_f);
-            S[F_SHOWER * 32 + lane] = __uint_as_float(g.shower);
+            put_df(S, F_X0H, F_X0L, pos, g.x0);
+            put_df(S, F_Y0H, F_Y0L, pos, g.y0);
+            put_df(S, F_Z0H, F_Z0L, pos, g.z0);
+            put_df(S, F_T0H, F_T0L, pos, g.t0);
+            put_df(S, F_RZH, F_RZL, pos, g.rz0);
+            S[F_DX * 32 + pos] = g.dx; S[F_DY * 32 + pos] = g.dy; S[F_DZ * 32 + pos] = g.dz;
+            S[F_LX * 32 + pos] = g.lx; S[F_LY * 32 + pos] = g.ly; S[F_LZ * 32 + pos] = g.lz;
+            S[F_E1X * 32 + pos] = g.e1x; S[F_E1Y * 32 + pos] = g.e1y; S[F_E1Z * 32 + pos] = g.e1z;
+            S[F_E2X * 32 + pos] = g.e2x; S[F_E2Y * 32 + pos] = g.e2y; S[F_E2Z * 32 + pos] = g.e2z;
+            S[F_SIN * 32 + pos] = g.sin_tc; S[F_KAP * 32 + pos] = g.kappa;
+            S[F_L * 32 + pos] = g.L; S[F_IBC * 32 + pos] = g.inv_bc;
+            S[F_WC * 32 + pos] = g.w_c; S[F_WF * 32 + pos] = g.w_f;
+            S[F_NC * 32 + pos] = __uint_as_float(g.n_c);
+            S[F_NF * 32 + pos] = __uint_as_float(g.n_f);
+            S[F_SHOWER * 32 + pos] = __uint_as_float(g.shower);
+            S[F_SEGI * 32 + pos] = __uint_as_float((uint32_t)lane);
+        } else {
+            S[F_NC * 32 + pos] = __uint_as_float(0u);
+            S[F_NF * 32 + pos] = __uint_as_float(0u);
         }
         S[F_INCL * 32 + lane] = __uint_as_float(incl);
         __syncwarp();
@@ -856,14 +886,16 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
 #pragma unroll
             for (int step = 16; step > 0; step >>= 1)
                 if (__float_as_uint(S[F_INCL * 32 + l + step - 1]) <= jj) l += step;
-            uint32_t excl = __float_as_uint(S[F_INCL * 32 + l]) - (__float_as_uint(S[F_NC * 32 + l]) +
-                                                                   __float_as_uint(S[F_NF * 32 + l]));
+            uint32_t nc_l = __float_as_uint(S[F_NC * 32 + l]);
+            uint32_t nf_l = __float_as_uint(S[F_NF * 32 + l]);
+            uint32_t excl = __float_as_uint(S[F_INCL * 32 + l]) - (nc_l + nf_l);
             uint32_t k = jj - excl;
             Seg<float, df> q;
-            q.x0 = PStore<df>::get(S + F_X0H * 32, S + F_X0L * 32, l);
-            q.y0 = PStore<df>::get(S + F_Y0H * 32, S + F_Y0L * 32, l);
-            q.z0 = PStore<df>::get(S + F_Z0H * 32, S + F_Z0L * 32, l);
-            q.t0 = PStore<df>::get(S + F_T0H * 32, S + F_T0L * 32, l);
+            q.x0 = get_df(S, F_X0H, F_X0L, l);
+            q.y0 = get_df(S, F_Y0H, F_Y0L, l);
+            q.z0 = get_df(S, F_Z0H, F_Z0L, l);
+            q.t0 = get_df(S, F_T0H, F_T0L, l);
+            q.rz0 = get_df(S, F_RZH, F_RZL, l);
             q.dx = S[F_DX * 32 + l]; q.dy = S[F_DY * 32 + l]; q.dz = S[F_DZ * 32 + l];
             q.lx = S[F_LX * 32 + l]; q.ly = S[F_LY * 32 + l]; q.lz = S[F_LZ * 32 + l];
             q.e1x = S[F_E1X * 32 + l]; q.e1y = S[F_E1Y * 32 + l]; q.e1z = S[F_E1Z * 32 + l];
@@ -871,28 +903,36 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
             q.sin_tc = S[F_SIN * 32 + l]; q.kappa = S[F_KAP * 32 + l];
             q.L = S[F_L * 32 + l]; q.inv_bc = S[F_IBC * 32 + l];
             q.w_c = S[F_WC * 32 + l]; q.w_f = S[F_WF * 32 + l];
-            q.n_c = __float_as_uint(S[F_NC * 32 + l]); q.n_f = __float_as_uint(S[F_NF * 32 + l]);
+            q.n_c = nc_l; q.n_f = nf_l;
             q.shower = __float_as_uint(S[F_SHOWER * 32 + l]);
-            int64_t seg_local = s_first + l;
+            int64_t seg_local = s_first + (int64_t)__float_as_uint(S[F_SEGI * 32 + l]);
             int64_t seg_global = Pp.seg_base + seg_local;
             int nh = 0;
             if (std::is_same<P, double>::value) {   // binary64 for the precise steps
-                Seg<float, double> qd = to_fp64_guard(q);
+                Seg<float, double> qd;
+                p_from_pair(qd.x0, q.x0); p_from_pair(qd.y0, q.y0); p_from_pair(qd.z0, q.z0);
+                p_from_pair(qd.t0, q.t0); p_from_pair(qd.rz0, q.rz0);
+                qd.dx = q.dx; qd.dy = q.dy; qd.dz = q.dz; qd.lx = q.lx; qd.ly = q.ly; qd.lz = q.lz;
+                qd.e1x = q.e1x; qd.e1y = q.e1y; qd.e1z = q.e1z; qd.e2x = q.e2x; qd.e2y = q.e2y; qd.e2z = q.e2z;
+                qd.sin_tc = q.sin_tc; qd.kappa = q.kappa; qd.L = q.L; qd.inv_bc = q.inv_bc;
+                qd.w_c = q.w_c; qd.w_f = q.w_f; qd.n_c = q.n_c; qd.n_f = q.n_f; qd.shower = q.shower;
                 RayOut<float, double> o;
-                trace_ray<float, double, true>(qd, seg_global, k, active, A, Pp, o);
+                trace_ray<float, double, true, SPH, REFR>(qd, seg_global, k, active, A, Pp, o);
                 nh = hit_test<float, double, true>(o, seg_local, seg_global, k, q.shower, A, Tl, Pp, O, status_bits);
                 if (active) {
                     ++c_rays;
-                    c_esc += o.status == 1; c_under += o.status == 2; c_turn += o.status == 3; c_reach += o.status == 0 || o.status == 5;
+                    c_esc += o.status == 1; c_under += o.status == 2; c_turn += o.status == 3;
+                    c_reach += o.status == 0 || o.status == 5;
                     c_cells += o.status == 0 ? o.cells : 0;
                 }
             } else {
                 RayOut<float, df> o;
-                trace_ray<float, df, true>(q, seg_global, k, active, A, Pp, o);
+                trace_ray<float, df, true, SPH, REFR>(q, seg_global, k, active, A, Pp, o);
                 nh = hit_test<float, df, true>(o, seg_local, seg_global, k, q.shower, A, Tl, Pp, O, status_bits);
                 if (active) {
                     ++c_rays;
-                    c_esc += o.status == 1; c_under += o.status == 2; c_turn += o.status == 3; c_reach += o.status == 0 || o.status == 5;
+                    c_esc += o.status == 1; c_under += o.status == 2; c_turn += o.status == 3;
+                    c_reach += o.status == 0 || o.status == 5;
                     c_cells += o.status == 0 ? o.cells : 0;
                 }
             }
@@ -919,6 +959,7 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
 // ------------------------------------------------------------------ plain FP64
 // One thread per segment, binary64 throughout, every bunch of the segment in
 // turn, one atomic per hit.
+template <bool SPH, bool REFR>
 __global__ void __launch_bounds__(128)
 k_trace_fp64(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid_constant__ DevAtm A,
              const __grid_constant__ DevTel Tl, const __grid_constant__ DevPar Pp, const __grid_constant__ DevOut O)
@@ -927,7 +968,7 @@ k_trace_fp64(const clight_segment *__restrict__ segs, int64_t n_segs, const __gr
     if (i >= n_segs) return;
     unsigned status_bits = 0;
     Seg<double, double> g;
-    load_segment_d(segs[i], A, Pp, g);
+    load_segment_d<SPH>(segs[i], A, Pp, g);
     uint32_t c_rays = 0, c_esc = 0, c_under = 0, c_turn = 0, c_reach = 0, c_hits = 0, c_cells = 0;
     if (g.bad) {
         status_bits |= 1u << g.bad;
@@ -937,9 +978,10 @@ k_trace_fp64(const clight_segment *__restrict__ segs, int64_t n_segs, const __gr
         int64_t seg_global = Pp.seg_base + i;
         for (uint32_t k = 0; k < nb; ++k) {
             RayOut<double, double> o;
-            trace_ray<double, double, false>(g, seg_global, k, true, A, Pp, o);
+            trace_ray<double, double, false, SPH, REFR>(g, seg_global, k, true, A, Pp, o);
             ++c_rays;
-            c_esc += o.status == 1; c_under += o.status == 2; c_turn += o.status == 3; c_reach += o.status == 0 || o.status == 5;
+            c_esc += o.status == 1; c_under += o.status == 2; c_turn += o.status == 3;
+            c_reach += o.status == 0 || o.status == 5;
             c_cells += o.status == 0 ? o.cells : 0;
             c_hits += hit_test<double, double, false>(o, i, seg_global, k, g.shower, A, Tl, Pp, O, status_bits);
         }
@@ -951,15 +993,29 @@ k_trace_fp64(const clight_segment *__restrict__ segs, int64_t n_segs, const __gr
 }
 
 // ------------------------------------------------------------------ launchers
+template <class P>
+static void launch_fused_p(const clight_segment *segs, int64_t n_segs, const DevAtm &A, const DevTel &T,
+                           const DevPar &Pp, const DevOut &O, int grid, int block, cudaStream_t s)
+{
+    int smem = fused_smem_bytes(block);     // <= 34 KB for block <= 256: no opt-in needed
+    if (A.spherical && A.refraction)
+        k_trace_fused<P, true, true><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
+    else if (A.spherical)
+        k_trace_fused<P, true, false><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
+    else if (A.refraction)
+        k_trace_fused<P, false, true><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
+    else
+        k_trace_fused<P, false, false><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
+}
+
 cudaError_t launch_trace_fused(const clight_segment *segs, int64_t n_segs, const DevAtm &A, const DevTel &T,
                                const DevPar &P, const DevOut &O, int precision, int grid, int block,
                                cudaStream_t s)
 {
-    int smem = fused_smem_bytes(block);     // <= 30 KB for block <= 256: no opt-in needed
     if (precision == CLIGHT_PREC_FP64_GUARD)
-        k_trace_fused<double><<<grid, block, smem, s>>>(segs, n_segs, A, T, P, O);
+        launch_fused_p<double>(segs, n_segs, A, T, P, O, grid, block, s);
     else
-        k_trace_fused<df><<<grid, block, smem, s>>>(segs, n_segs, A, T, P, O);
+        launch_fused_p<df>(segs, n_segs, A, T, P, O, grid, block, s);
     return cudaGetLastError();
 }
 
@@ -969,7 +1025,14 @@ cudaError_t launch_trace_fp64(const clight_segment *segs, int64_t n_segs, const 
     int block = 128;
     int64_t grid = (n_segs + block - 1) / block;
     if (grid < 1) grid = 1;
-    k_trace_fp64<<<(unsigned)grid, block, 0, s>>>(segs, n_segs, A, T, P, O);
+    if (A.spherical && A.refraction)
+        k_trace_fp64<true, true><<<(unsigned)grid, block, 0, s>>>(segs, n_segs, A, T, P, O);
+    else if (A.spherical)
+        k_trace_fp64<true, false><<<(unsigned)grid, block, 0, s>>>(segs, n_segs, A, T, P, O);
+    else if (A.refraction)
+        k_trace_fp64<false, true><<<(unsigned)grid, block, 0, s>>>(segs, n_segs, A, T, P, O);
+    else
+        k_trace_fp64<false, false><<<(unsigned)grid, block, 0, s>>>(segs, n_segs, A, T, P, O);
     return cudaGetLastError();
 }
 
