@@ -187,6 +187,35 @@ clight_status clight_trace_host(clight_ctx *ctx, const clight_segment *h_segs, i
                                 int64_t *h_counts, double *h_sums, clight_stats *h_stats,
                                 int64_t *h_n_hits, void *stream);
 
+/* clight_trace without any allocation, for callers that cannot call
+ * cudaMalloc while they run: code that must not touch the CUDA allocator
+ * (an embedding framework that owns all device memory through its own
+ * pool, a host process that reserves everything at start-up, a pipeline
+ * whose memory budget must not move between events).  The paper has no
+ * counterpart; it exists for such callers.
+ *
+ * It runs the same generation, propagation and hit kernel as clight_trace
+ * but keeps no sort keys: the hit records go straight into d_hits in
+ * arbitrary order (not sorted, no photon sums), and d_counts (optional,
+ * n_showers * n_tel int64, device) receives the per-(shower, telescope)
+ * hit counts.  Its scratch -- counters, ray statistics and one hit counter
+ * per group -- is a static array in the library image (131,200 bytes, held
+ * on every GPU that loads the library until the process exits).
+ *   - n_showers * n_tel above 16384 returns CLIGHT_ERR_LIMIT before any
+ *     launch; other errors as clight_trace.
+ *   - The first call on a device looks up the array's device address once
+ *     (with that device current); make that first call before any stream
+ *     capture.
+ *   - Calls share the one array, which keeps the last call's contents; each
+ *     call clears what must start at zero.  Calls that overlap on the GPU
+ *     (different streams or threads) race on it: order them.
+ *   - The context must already hold its atmosphere and telescopes (their
+ *     tables were allocated by clight_set_*); this call allocates nothing.
+ * Synchronises `stream` once. */
+clight_status clight_trace_noalloc(clight_ctx *ctx, const clight_segment *d_segs, int64_t n_segs,
+                                   int32_t n_showers, clight_hit *d_hits, int64_t hit_capacity,
+                                   int64_t *d_counts, clight_stats *h_stats, int64_t *h_n_hits, void *stream);
+
 /* Device time of the last clight_trace / clight_trace_fp64 call, measured
  * with CUDA events recorded on the launch stream around its phases:
  * ms[0] = generation + propagation + hit kernel, ms[1] = sort and per-

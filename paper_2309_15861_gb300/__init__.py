@@ -86,6 +86,8 @@ def lib():
         L.clight_status_string.restype = C.c_char_p
         L.clight_version.restype = C.c_int
         L.clight_last_timing.argtypes = [P, P]
+        L.clight_trace_noalloc.argtypes = [P, P, C.c_int64, C.c_int32, P, C.c_int64, P,
+                                           C.POINTER(Stats), C.POINTER(C.c_int64), P]
         _lib = L
     return _lib
 
@@ -179,6 +181,20 @@ class Context:
                   _ptr(d_counts), _ptr(d_sums), C.byref(st), C.byref(nh), _stream_handle(stream))
         if raise_on_error and code not in (OK,):
             raise ClightError(code, "clight_trace_fp64" if fp64 else "clight_trace")
+        return code, nh.value, st.as_dict()
+
+    def trace_noalloc(self, d_segs, n_segs, n_showers, d_hits, capacity, d_counts=None, stream=None,
+                      raise_on_error=True):
+        """The path without any allocation: unsorted hits straight into d_hits,
+        per-(shower, telescope) hit counts into d_counts.  For callers that
+        cannot allocate device memory while they run.  -> (status, n_hits, stats)"""
+        st = Stats()
+        nh = C.c_int64()
+        code = lib().clight_trace_noalloc(self._h, _ptr(d_segs), int(n_segs), int(n_showers), _ptr(d_hits),
+                                          int(capacity), _ptr(d_counts), C.byref(st), C.byref(nh),
+                                          _stream_handle(stream))
+        if raise_on_error and code != OK:
+            raise ClightError(code, "clight_trace_noalloc")
         return code, nh.value, st.as_dict()
 
     def last_timing(self):

@@ -382,6 +382,21 @@ clight_status clight_set_params(clight_ctx *c, const clight_params *p)
 
 }  // extern "C"
 
+// The tables and launch shape the no-allocation entry point needs.
+bool clight::ctx_view(clight_ctx *c, CtxView *v)
+{
+    if (!c || !v || !c->atm_set || !c->tel_set) return false;
+    v->atm = c->atm;
+    v->tel = c->tel;
+    v->par = c->par;
+    v->device = c->device;
+    v->n_sm = c->n_sm;
+    v->block = c->upar.block > 0 ? c->upar.block : 256;
+    v->ctas_per_sm = c->upar.ctas_per_sm > 0 ? c->upar.ctas_per_sm : 2 * 256 / v->block;
+    v->precision = c->upar.precision;
+    return true;
+}
+
 // ------------------------------------------------------------------ pipeline
 namespace {
 

@@ -78,6 +78,15 @@ struct DevOut {
 enum { CTR_WORK = 0, CTR_CURSOR = 1, CTR_STATS = 2, CTR_N = 16 };
 enum { ST_RAYS = 0, ST_ESCAPED, ST_UNDER, ST_TURNED, ST_REACHED, ST_HITS, ST_GUARDED, ST_STATUS, ST_CELLS };
 
+// What the no-allocation entry point reads from a context (clight_api.cu).
+struct CtxView {
+    DevAtm atm;
+    DevTel tel;
+    DevPar par;
+    int device, n_sm, block, ctas_per_sm, precision;
+};
+bool ctx_view(clight_ctx *c, CtxView *v);
+
 // kernel launchers (trace_kernels.cu)
 cudaError_t launch_trace_fused(const clight_segment *segs, int64_t n_segs, const DevAtm &A,
                                const DevTel &T, const DevPar &P, const DevOut &O, int precision,

@@ -26,6 +26,7 @@
 // parameters, so each launch runs a kernel holding only its own branch.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <type_traits>
 
@@ -686,6 +687,20 @@ __device__ __forceinline__ void write_hit(const DevOut &O, unsigned long long id
     O.vals[idx] = (uint32_t)idx;
 }
 
+// The record alone, for the entry point that keeps no sort keys.
+__device__ __forceinline__ void write_hit_record(clight_hit *rec, int64_t capacity, unsigned long long idx,
+                                                 int64_t seg, uint32_t k, uint32_t tel, float xr, float yr,
+                                                 float cx, float cy, float lam, float w, double t)
+{
+    if ((int64_t)idx >= capacity) return;
+    float4 *p = reinterpret_cast<float4 *>(rec + idx);
+    uint32_t slo = (uint32_t)(uint64_t)seg, shi = (uint32_t)((uint64_t)seg >> 32);
+    p[0] = make_float4(__uint_as_float(slo), __uint_as_float(shi), __uint_as_float(k), __uint_as_float(tel));
+    p[1] = make_float4(xr, yr, cx, cy);
+    unsigned long long tb = (unsigned long long)__double_as_longlong(t);
+    p[2] = make_float4(lam, w, __uint_as_float((uint32_t)tb), __uint_as_float((uint32_t)(tb >> 32)));
+}
+
 __device__ __forceinline__ unsigned lanemask_lt()
 {
     unsigned m;
@@ -697,7 +712,7 @@ __device__ __forceinline__ unsigned lanemask_lt()
 // append every hit.  A sphere of radius R is hit when the line passes closer
 // than R to its centre; its centre can then lie at most R / |cz| from the
 // crossing point, which bounds the cells searched.
-template <class T, class P, bool WARP>
+template <class T, class P, bool WARP, bool NOALLOC = false>
 __device__ __forceinline__ int hit_test(const RayOut<T, P> &o, int64_t seg_local, int64_t seg_global, uint32_t k,
                                         uint32_t shower, const DevAtm &A, const DevTel &Tl, const DevPar &Pp,
                                         const DevOut &O, unsigned &status_bits)
@@ -735,6 +750,20 @@ __device__ __forceinline__ int hit_test(const RayOut<T, P> &o, int64_t seg_local
                     P tjp = o.t + (T)(A.n_obs * sj) * (T)kInvC;
                     double tj = p_d(tjp);                        // one conversion per hit
                     uint32_t group = shower * (uint32_t)Tl.n_tel + (uint32_t)j;
+                    if (NOALLOC) {
+                        // no sort keys: the record goes straight to the caller's
+                        // buffer and O.keys holds one hit counter per group
+                        unsigned m = __activemask();
+                        int leader = __ffs(m) - 1;
+                        unsigned long long base = 0;
+                        if ((int)(threadIdx.x & 31) == leader) base = atomicAdd(O.ctr + CTR_CURSOR, (unsigned long long)__popc(m));
+                        base = __shfl_sync(m, base, leader);
+                        unsigned long long idx = base + __popc(m & lanemask_lt());
+                        write_hit_record(O.rec, O.capacity, idx, seg_global, k, (uint32_t)j, xr, yr, cx, cy,
+                                         (float)o.lambda, (float)o.weight, tj);
+                        atomicAdd(O.keys + group, 1ull);
+                        continue;
+                    }
                     unsigned long long key;
                     if (Pp.k_bits < 32 && k >= (1u << Pp.k_bits)) {
                         status_bits |= 1u << CLIGHT_ERR_LIMIT;
@@ -798,7 +827,7 @@ __device__ __forceinline__ uint32_t warp_sort_u32(uint32_t key, int lane)
     return key;
 }
 
-template <class P, bool SPH, bool REFR>
+template <class P, bool SPH, bool REFR, bool NOALLOC = false>
 __global__ void __launch_bounds__(256, 2)
 k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid_constant__ DevAtm A,
               const __grid_constant__ DevTel Tl, const __grid_constant__ DevPar Pp, const __grid_constant__ DevOut O)
@@ -918,7 +947,7 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
                 qd.w_c = q.w_c; qd.w_f = q.w_f; qd.n_c = q.n_c; qd.n_f = q.n_f; qd.shower = q.shower;
                 RayOut<float, double> o;
                 trace_ray<float, double, true, SPH, REFR>(qd, seg_global, k, active, A, Pp, o);
-                nh = hit_test<float, double, true>(o, seg_local, seg_global, k, q.shower, A, Tl, Pp, O, status_bits);
+                nh = hit_test<float, double, true, NOALLOC>(o, seg_local, seg_global, k, q.shower, A, Tl, Pp, O, status_bits);
                 if (active) {
                     ++c_rays;
                     c_esc += o.status == 1; c_under += o.status == 2; c_turn += o.status == 3;
@@ -928,7 +957,7 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
             } else {
                 RayOut<float, df> o;
                 trace_ray<float, df, true, SPH, REFR>(q, seg_global, k, active, A, Pp, o);
-                nh = hit_test<float, df, true>(o, seg_local, seg_global, k, q.shower, A, Tl, Pp, O, status_bits);
+                nh = hit_test<float, df, true, NOALLOC>(o, seg_local, seg_global, k, q.shower, A, Tl, Pp, O, status_bits);
                 if (active) {
                     ++c_rays;
                     c_esc += o.status == 1; c_under += o.status == 2; c_turn += o.status == 3;
@@ -1036,4 +1065,110 @@ cudaError_t launch_trace_fp64(const clight_segment *segs, int64_t n_segs, const 
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ no allocation
+// Scratch of clight_trace_noalloc: the work and hit counters and the ray
+// statistics (CTR_N words), then one hit counter per (shower, telescope)
+// group.  It lives in the library image, so the entry point needs no
+// cudaMalloc; every GPU that loads the library holds these 131,200 bytes
+// until the process exits.
+constexpr int kNoallocMaxGroups = 16384;
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[CTR_N + kNoallocMaxGroups];
+
+constexpr int kNoallocMaxDevices = 64;
+static unsigned long long *g_noalloc_ptr[kNoallocMaxDevices];   // device address per device
+
+// The address of the scratch array on the current device.  In host code the
+// array's name is only a stand-in, so the address comes from the runtime,
+// looked up once per device with that device current.
+static cudaError_t noalloc_scratch(int device, unsigned long long **out)
+{
+    if (device < 0 || device >= kNoallocMaxDevices) return cudaErrorInvalidDevice;
+    if (!g_noalloc_ptr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[device] = static_cast<unsigned long long *>(p);
+    }
+    *out = g_noalloc_ptr[device];
+    return cudaSuccess;
+}
+
+template <class P, bool SPH, bool REFR>
+static void launch_noalloc(const clight_segment *segs, int64_t n_segs, const DevAtm &A, const DevTel &T,
+                           const DevPar &Pp, const DevOut &O, int grid, int block, cudaStream_t s)
+{
+    k_trace_fused<P, SPH, REFR, true><<<grid, block, fused_smem_bytes(block), s>>>(segs, n_segs, A, T, Pp, O);
+}
+
 }  // namespace clight
+
+extern "C" clight_status clight_trace_noalloc(clight_ctx *ctx, const clight_segment *d_segs, int64_t n_segs,
+                                              int32_t n_showers, clight_hit *d_hits, int64_t hit_capacity,
+                                              int64_t *d_counts, clight_stats *h_stats, int64_t *h_n_hits,
+                                              void *stream)
+{
+    using namespace clight;
+    CtxView v;
+    if (!ctx_view(ctx, &v)) return CLIGHT_ERR_ARG;
+    if (n_segs < 0 || n_showers < 1 || hit_capacity < 0 || !h_n_hits || (n_segs > 0 && !d_segs) ||
+        (hit_capacity > 0 && !d_hits))
+        return CLIGHT_ERR_ARG;
+    if (n_segs > (int64_t(1) << 31)) return CLIGHT_ERR_LIMIT;
+    int64_t groups = (int64_t)n_showers * v.tel.n_tel;
+    if (groups > kNoallocMaxGroups) return CLIGHT_ERR_LIMIT;     // n_showers x n_tel above 16384
+    if (cudaSetDevice(v.device) != cudaSuccess) return CLIGHT_ERR_CUDA;
+    unsigned long long *scr = nullptr;
+    if (noalloc_scratch(v.device, &scr) != cudaSuccess) return CLIGHT_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    // counters and group counts left by the previous call start again at zero
+    if (cudaMemsetAsync(scr, 0, sizeof(unsigned long long) * (size_t)(CTR_N + groups), s) != cudaSuccess)
+        return CLIGHT_ERR_CUDA;
+    if (n_segs > 0) {
+        DevPar P = v.par;
+        P.n_showers = n_showers;
+        DevOut O;
+        O.rec = d_hits;
+        O.keys = scr + CTR_N;        // per-group hit counters
+        O.vals = nullptr;
+        O.capacity = hit_capacity;
+        O.ctr = scr;
+        int block = v.block;
+        int64_t grid = std::min<int64_t>((int64_t)v.n_sm * v.ctas_per_sm, (n_segs + block - 1) / block);
+        grid = std::max<int64_t>(grid, 1);
+        const DevAtm &A = v.atm;
+        bool fp64 = v.precision == CLIGHT_PREC_FP64_GUARD;
+        auto go = [&](auto tag) {
+            using PP = decltype(tag);
+            if (A.spherical && A.refraction) launch_noalloc<PP, true, true>(d_segs, n_segs, A, v.tel, P, O, (int)grid, block, s);
+            else if (A.spherical) launch_noalloc<PP, true, false>(d_segs, n_segs, A, v.tel, P, O, (int)grid, block, s);
+            else if (A.refraction) launch_noalloc<PP, false, true>(d_segs, n_segs, A, v.tel, P, O, (int)grid, block, s);
+            else launch_noalloc<PP, false, false>(d_segs, n_segs, A, v.tel, P, O, (int)grid, block, s);
+        };
+        if (fp64) go(double{});
+        else go(df{});
+        if (cudaGetLastError() != cudaSuccess) return CLIGHT_ERR_CUDA;
+    }
+    unsigned long long h[CTR_N];
+    if (cudaMemcpyAsync(h, scr, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CLIGHT_ERR_CUDA;
+    if (d_counts && cudaMemcpyAsync(d_counts, scr + CTR_N, sizeof(int64_t) * (size_t)groups,
+                                    cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return CLIGHT_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return CLIGHT_ERR_CUDA;
+    *h_n_hits = (int64_t)h[CTR_CURSOR];
+    unsigned long long bits = h[CTR_STATS + ST_STATUS];
+    if (h_stats) {
+        h_stats->rays = (int64_t)h[CTR_STATS + ST_RAYS];
+        h_stats->escaped = (int64_t)h[CTR_STATS + ST_ESCAPED];
+        h_stats->under = (int64_t)h[CTR_STATS + ST_UNDER];
+        h_stats->turned = (int64_t)h[CTR_STATS + ST_TURNED];
+        h_stats->reached = (int64_t)h[CTR_STATS + ST_REACHED];
+        h_stats->hits = (int64_t)h[CTR_STATS + ST_HITS];
+        h_stats->guarded = (int64_t)h[CTR_STATS + ST_GUARDED];
+        h_stats->status = (int64_t)bits;
+        h_stats->cells = (int64_t)h[CTR_STATS + ST_CELLS];
+    }
+    if ((int64_t)h[CTR_CURSOR] > hit_capacity) return CLIGHT_ERR_HIT_CAPACITY;
+    if (bits & (1ull << CLIGHT_ERR_BAD_SEGMENT)) return CLIGHT_ERR_BAD_SEGMENT;
+    if (bits & (1ull << CLIGHT_ERR_LIMIT)) return CLIGHT_ERR_LIMIT;
+    return CLIGHT_OK;
+}
