@@ -34,16 +34,18 @@ sys.path.insert(0, ROOT)
 METRIC = "traced photons/s, 1 GB300: batched FP32 vs plain FP64 at oracle tolerance"
 UNIT = "rays/s"
 
-# Algorithmic binary32 operations per unit of work, counted from the kernel
-# source (trace_kernels.cu): per quadrature node of the refracted spherical
-# integrand, per ray outside the nodes (Philox, cone, emission point,
-# vacuum line in FP32 pairs, landing point, arrival time, absorption) and
-# per candidate telescope.  MUFU (ex2, rsqrt, rcp, sincos) counted apart.
-OPS_NODE = 41
+# Algorithmic operations per unit of work on the FMA/ALU pipes, counted
+# from the kernel source (trace_kernels.cu): per quadrature node of the
+# refracted spherical integrand, per altitude cell (node placement and
+# accumulation), and per ray outside the nodes (Philox rounds, cone,
+# emission point, vacuum line and landing point in FP32 pairs, arrival
+# time, absorption, hit search).  MUFU ops (ex2, rsqrt, rcp) counted apart.
+OPS_NODE = 39
 MUFU_NODE = 5
 NODES_PER_CELL = 3
-OPS_RAY = 260
-MUFU_RAY = 6
+OPS_CELL = 8
+OPS_RAY = 680
+MUFU_RAY = 12
 FP32_LANES_PER_SM = 128
 MUFU_LANES_PER_SM = 16
 
@@ -103,6 +105,29 @@ class Clocks:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def recorded_traffic(n_steps):
+    """DRAM bytes of one fused-kernel launch from the recorded ncu capture,
+    scaled by steps, or None when the kernel sources changed since."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_trace_fused_traffic.txt")
+    try:
+        lines = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    except OSError:
+        return None
+    rec = {}
+    for f in lines:
+        if f[0] == "sha256":
+            src = os.path.join(ROOT, "paper_2309_15861_gb300", "csrc", f[1])
+            try:
+                if hashlib.sha256(open(src, "rb").read()).hexdigest() != f[2]:
+                    return None
+            except OSError:
+                return None
+        else:
+            rec[f[0]] = float(f[1])
+    return rec["bytes_per_step"] * n_steps if "bytes_per_step" in rec else None
 
 
 def cpu_baseline(w, budget_s=12.0, block=256, seed=0):
@@ -249,7 +274,7 @@ def main():
 
     # ---- roofline of the dominant kernel (generation + propagation + hits)
     k_ms = statistics.mean(kms)
-    ops = st["rays"] * OPS_RAY + st["cells"] * NODES_PER_CELL * OPS_NODE
+    ops = st["rays"] * OPS_RAY + st["cells"] * (OPS_CELL + NODES_PER_CELL * OPS_NODE)
     mufu = st["rays"] * MUFU_RAY + st["cells"] * NODES_PER_CELL * MUFU_NODE
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     peaks = {}
@@ -260,8 +285,11 @@ def main():
     f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     peak_ops = n_sm * FP32_LANES_PER_SM * f_max
     achieved = ops / (k_ms / 1e3)
+    traffic = recorded_traffic(n)
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s (FP32 pipe)",
-            "frac": achieved / peak_ops, "traffic": None,
+            "frac": achieved / peak_ops, "traffic": traffic,
+            "traffic_note": "DRAM bytes per launch: ncu capture of 2e6 steps scaled by steps "
+                            "(profiles/k_trace_fused_traffic.txt); null if the kernel changed since",
             "kernel": "k_trace_fused", "kernel_ms": k_ms, "sort_ms": statistics.mean(sms),
             "mufu_frac": (mufu / (k_ms / 1e3)) / (n_sm * MUFU_LANES_PER_SM * f_max),
             "ops_per_ray": ops / max(1, st["rays"]), "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
