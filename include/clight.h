@@ -187,6 +187,30 @@ clight_status clight_trace_host(clight_ctx *ctx, const clight_segment *h_segs, i
                                 int64_t *h_counts, double *h_sums, clight_stats *h_stats,
                                 int64_t *h_n_hits, void *stream);
 
+/* Gradient of a scalar loss with respect to the atmosphere parameters
+ * theta = (c_1 .. c_L, K, L0): the layer scale heights, the refractivity
+ * coefficient and the extinction length (b_i, layer edges, the random
+ * numbers and the bunch counts held at their values of the forward call).
+ *   loss = sum_hits (gx x_rel + gy y_rel + gt t)
+ *        + sum_(shower, tel) gY Y,
+ *   Y = sum over rays with d_perp < R + soft_w of
+ *       weight exp(-tau) sigma((R - d_perp) / soft_s), sigma logistic,
+ * the soft-edged absorption-weighted yield of each telescope.
+ *   d_hits        the hits of clight_trace at the same parameters (device)
+ *   d_gx/gy/gt    per-hit upstream gradients (device float, NULL = zero)
+ *   d_gyield      per-(shower, tel) upstream gradients of Y (device double,
+ *                 NULL = zero)
+ *   d_yield       if not NULL receives Y (device double, n_showers * n_tel)
+ *   h_grad        n_layers + 2 doubles (host): d loss / d theta
+ * Each ray is recomputed from its random-number counter; derivatives are
+ * carried as binary32 tangents and summed per block in binary64, then over
+ * blocks in a fixed order.  Synchronises `stream` once. */
+clight_status clight_trace_adjoint(clight_ctx *ctx, const clight_segment *d_segs, int64_t n_segs,
+                                   int32_t n_showers, const clight_hit *d_hits, int64_t n_hits,
+                                   const float *d_gx, const float *d_gy, const float *d_gt,
+                                   const double *d_gyield, float soft_s, float soft_w, double *d_yield,
+                                   double *h_grad, void *stream);
+
 /* clight_trace without any allocation, for callers that cannot call
  * cudaMalloc while they run: code that must not touch the CUDA allocator
  * (an embedding framework that owns all device memory through its own

@@ -86,6 +86,8 @@ def lib():
         L.clight_status_string.restype = C.c_char_p
         L.clight_version.restype = C.c_int
         L.clight_last_timing.argtypes = [P, P]
+        L.clight_trace_adjoint.argtypes = [P, P, C.c_int64, C.c_int32, P, C.c_int64, P, P, P, P,
+                                           C.c_float, C.c_float, P, P, P]
         L.clight_trace_noalloc.argtypes = [P, P, C.c_int64, C.c_int32, P, C.c_int64, P,
                                            C.POINTER(Stats), C.POINTER(C.c_int64), P]
         _lib = L
@@ -182,6 +184,19 @@ class Context:
         if raise_on_error and code not in (OK,):
             raise ClightError(code, "clight_trace_fp64" if fp64 else "clight_trace")
         return code, nh.value, st.as_dict()
+
+    def trace_adjoint(self, d_segs, n_segs, n_showers, d_hits, n_hits, gx=None, gy=None, gt=None, gY=None,
+                      soft_s=0.5, soft_w=20.0, d_yield=None, stream=None, n_params=None):
+        """Gradient of sum(gx x + gy y + gt t) + sum(gY Y) with respect to
+        (c_1..c_L, K, L0); optionally the soft-edged yields Y into d_yield."""
+        n = n_params if n_params is not None else 10
+        out = np.zeros(max(n, 10))
+        code = lib().clight_trace_adjoint(self._h, _ptr(d_segs), int(n_segs), int(n_showers), _ptr(d_hits),
+                                          int(n_hits), _ptr(gx), _ptr(gy), _ptr(gt), _ptr(gY), float(soft_s),
+                                          float(soft_w), _ptr(d_yield), C.c_void_p(out.ctypes.data),
+                                          _stream_handle(stream))
+        _check(code, "clight_trace_adjoint")
+        return out
 
     def trace_noalloc(self, d_segs, n_segs, n_showers, d_hits, capacity, d_counts=None, stream=None,
                       raise_on_error=True):

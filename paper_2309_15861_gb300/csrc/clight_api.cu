@@ -74,6 +74,7 @@ struct clight_ctx {
     Buf<int64_t> gstart, gend;
     uint64_t scratch_gen = 0;
     // staging for the host-buffer entry point
+    Buf<double> adj_partial, adj_out;
     Buf<clight_segment> stage_segs;
     Buf<clight_hit> stage_hits;
     Buf<int64_t> stage_counts;
@@ -169,6 +170,7 @@ void clight_destroy(clight_ctx *c)
     c->rec.release(); c->keys.release(); c->keys_alt.release(); c->vals.release(); c->vals_alt.release();
     c->hist.release(); c->bsums.release(); c->gstart.release(); c->gend.release();
     c->stage_segs.release(); c->stage_hits.release(); c->stage_counts.release(); c->stage_sums.release();
+    c->adj_partial.release(); c->adj_out.release();
     if (c->h_ctr) cudaFreeHost(c->h_ctr);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->ev) cudaEventDestroy(c->ev);
@@ -259,6 +261,7 @@ clight_status clight_set_atmosphere(clight_ctx *c, const clight_atmosphere *a)
         DevCell &C = A.cells[nc];
         C.lo = (float)l0; C.hi = (float)l1;
         C.kb = A.kb[i]; C.rb = A.rb[i]; C.nl2c = A.nl2c[i];
+        C.pad0 = (float)i;                // the cell's layer (the adjoint's tangents)
         A.cell_lo_d[nc] = (double)C.lo;   // identical edges in both precisions
         A.cell_hi_d[nc] = (double)C.hi;
         A.cell_kb_d[nc] = A.kb_d[i]; A.cell_rb_d[nc] = A.rb_d[i]; A.cell_ic_d[nc] = A.inv_c_d[i];
@@ -581,3 +584,35 @@ clight_status clight_trace_host(clight_ctx *c, const clight_segment *h_segs, int
 }
 
 }  // extern "C"
+
+extern "C" clight_status clight_trace_adjoint(clight_ctx *c, const clight_segment *d_segs, int64_t n_segs,
+                                              int32_t n_showers, const clight_hit *d_hits, int64_t n_hits,
+                                              const float *d_gx, const float *d_gy, const float *d_gt,
+                                              const double *d_gyield, float soft_s, float soft_w, double *d_yield,
+                                              double *h_grad, void *stream)
+{
+    if (!c || !c->atm_set || !c->tel_set || !h_grad || n_segs < 0 || n_hits < 0 || n_showers < 1)
+        return CLIGHT_ERR_ARG;
+    if ((n_segs > 0 && !d_segs) || (n_hits > 0 && !d_hits) || !(soft_s > 0) || !(soft_w >= 0))
+        return CLIGHT_ERR_ARG;
+    if (n_segs > (int64_t(1) << 31)) return CLIGHT_ERR_LIMIT;
+    if ((int64_t)n_showers * c->tel.n_tel > (int64_t(1) << 24)) return CLIGHT_ERR_LIMIT;
+    cudaSetDevice(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int np = adjoint_params(c->atm.n_layers);
+    int blocks = c->n_sm * 8;
+    uint64_t *g = &c->scratch_gen;
+    if (c->adj_partial.ensure((int64_t)2 * blocks * np, g) || c->adj_out.ensure(np, g)) return CLIGHT_ERR_CUDA;
+    DevPar P = c->par;
+    P.n_showers = n_showers;
+    if (d_yield)
+        CK(cudaMemsetAsync(d_yield, 0, sizeof(double) * (size_t)n_showers * c->tel.n_tel, s));
+    CK(launch_adjoint(d_segs, n_segs, d_hits, n_hits, d_gx, d_gy, d_gt, d_gyield, d_yield, c->atm, c->tel, P,
+                      soft_s, soft_w, (float)c->uatm.K, (float)c->uatm.L0, c->adj_partial.p, blocks,
+                      c->adj_out.p, s));
+    double out[10];
+    CK(cudaMemcpyAsync(out, c->adj_out.p, sizeof(double) * (size_t)np, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int i = 0; i < c->atm.n_layers + 2; ++i) h_grad[i] = out[i];
+    return CLIGHT_OK;
+}

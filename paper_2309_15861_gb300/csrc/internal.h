@@ -95,6 +95,13 @@ cudaError_t launch_trace_fp64(const clight_segment *segs, int64_t n_segs, const 
                               const DevTel &T, const DevPar &P, const DevOut &O, cudaStream_t s);
 int fused_smem_bytes(int block);
 
+// tangent-linear adjoint (adjoint_kernels.cu)
+int adjoint_params(int n_layers);   // tangents carried: >= n_layers + 2
+cudaError_t launch_adjoint(const clight_segment *segs, int64_t n_segs, const clight_hit *hits, int64_t n_hits,
+                           const float *gx, const float *gy, const float *gt, const double *gY, double *yield,
+                           const DevAtm &A, const DevTel &T, const DevPar &P, float soft_s, float soft_w, float K,
+                           float L0, double *partial, int blocks, double *d_out, cudaStream_t s);
+
 // sort and finalize (sort_kernels.cu)
 struct SortScratch {
     unsigned long long *keys_alt;

@@ -1,0 +1,797 @@
+// ray.cuh -- device code shared by the forward kernels (trace_kernels.cu)
+// and the tangent-linear adjoint (adjoint_kernels.cu): numerics, Philox,
+// the atmosphere, the segment set-up, one ray, the hit test.
+//
+// Paper: Baack & Alameddine, "Comparison and efficiency of GPU accelerated
+// optical light propagation in CORSIKA 8" (ICRC 2023).
+//   Sec. 1.2      Frank-Tamm yield with its threshold, n constant over a step
+//   Sec. 1.1      fluorescence yield N = Y dE (Eq. 1), isotropic emission
+//   Sec. 1.2.1    cone vector p and the rotation M_Rod (here applied as
+//                 cos(theta_c) d + sin(theta_c)(cos c M x + sin c M y))
+//   Fig. 1        create at the origin, rotate, move to the emission point
+//   Sec. 2        propagation to the ground with refraction
+//
+// Propagation.  Sec. 2 runs a straight line and then applies refraction
+// corrections.  Here the correction is computed, not approximated: the
+// straight vacuum line from the emission point is intersected with the
+// observation level exactly (FP32 pairs), and the refracted ray's deviation
+// from it -- angle (or distance), optical path and optical depth -- comes
+// from the Snell / Bouguer invariant as integrals over altitude, written in
+// a form free of cancellation and evaluated by 3-node Gauss-Legendre on
+// altitude cells no wider than a fixed multiple of the local scale height.
+// The bulk of the arithmetic is binary32; FP32 pairs (or binary64, by
+// parameter) carry only the emission point, the vacuum path, the landing
+// point and the arrival time.
+//
+// Geometry (flat / spherical Earth) and refraction (on / off) are template
+// parameters, so each launch runs a kernel holding only its own branch.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <type_traits>
+
+#include "df.cuh"
+#include "internal.h"
+
+namespace clight {
+
+#define FULL_MASK 0xffffffffu
+
+// ------------------------------------------------------------------ numerics
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+template <class T> struct Num;
+template <> struct Num<float> {
+    static __device__ __forceinline__ float div(float a, float b) { return a * rcp_approx(b); }
+    static __device__ __forceinline__ float rsq(float x) { return rsqrt_approx(x); }
+    static __device__ __forceinline__ float sqr(float x) { return sqrtf(x); }
+    static __device__ __forceinline__ void sincos2pi(float u, float *s, float *c) { sincospif(2.0f * u, s, c); }
+};
+template <> struct Num<double> {
+    static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+    static __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+    static __device__ __forceinline__ double sqr(double x) { return sqrt(x); }
+    static __device__ __forceinline__ void sincos2pi(double u, double *s, double *c) { sincospi(2.0 * u, s, c); }
+};
+
+// exact widening of a bulk-precision value into the pair/binary64 type
+__device__ __forceinline__ void p_set(df &o, float x) { o = df_make(x); }
+__device__ __forceinline__ void p_set(double &o, float x) { o = (double)x; }
+__device__ __forceinline__ void p_set(double &o, double x) { o = x; }
+template <class P, class T> __device__ __forceinline__ P p_of(T x)
+{
+    P o;
+    p_set(o, x);
+    return o;
+}
+// constants held both as FP32 pairs and binary64
+__device__ __forceinline__ void p_const(df &o, float hi, float lo, double) { o = {hi, lo}; }
+__device__ __forceinline__ void p_const(double &o, float, float, double d) { o = d; }
+template <class P> __device__ __forceinline__ P pc(float hi, float lo, double d)
+{
+    P o;
+    p_const(o, hi, lo, d);
+    return o;
+}
+__device__ __forceinline__ float p_f(df a) { return __fadd_rn(a.hi, a.lo); }
+__device__ __forceinline__ float p_f(double a) { return (float)a; }
+__device__ __forceinline__ double p_d(df a) { return df_to_double(a); }
+__device__ __forceinline__ double p_d(double a) { return a; }
+template <class T> __device__ __forceinline__ T to_t(df a);
+template <> __device__ __forceinline__ float to_t<float>(df a) { return p_f(a); }
+template <class T> __device__ __forceinline__ T to_t(double a) { return (T)a; }
+// a pair as the precise type (the FP64-guard variant widens it to binary64)
+__device__ __forceinline__ void p_from_pair(df &o, df a) { o = a; }
+__device__ __forceinline__ void p_from_pair(double &o, df a) { o = df_to_double(a); }
+
+// ------------------------------------------------------------------ Philox
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): per round two 32x32->64
+// products with 0xD2511F53 and 0xCD9E8D57, the Weyl key increments
+// 0x9E3779B9 and 0xBB67AE85.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// (m + 1/2) 2^-23 from the top 23 bits: exact in binary32 and binary64.
+template <class T> __device__ __forceinline__ T u01(uint32_t x)
+{
+    return (T)(x >> 9) * (T)1.1920928955078125e-07 + (T)5.9604644775390625e-08;
+}
+// binary32: 1 + m 2^-23 from the bits, minus 1, plus 2^-24 (all exact)
+template <> __device__ __forceinline__ float u01<float>(uint32_t x)
+{
+    return (__uint_as_float((x >> 9) | 0x3f800000u) - 1.0f) + 5.9604644775390625e-08f;
+}
+
+// ------------------------------------------------------------------ atmosphere
+// delta = n - 1 at one altitude (binary32 through the library exp2f, 2 ulp;
+// the quadrature nodes use the raw MUFU estimate).
+template <class T> struct AtmT;
+template <> struct AtmT<float> {
+    static __device__ __forceinline__ float delta(const DevAtm &A, float h)
+    {
+        if (h >= A.h_top) return 0.0f;
+        int i = 0;
+#pragma unroll
+        for (int j = 1; j < kMaxLayers; ++j)
+            if (j < A.n_layers && h >= A.h_lo[j]) i = j;
+        return A.kb[i] * exp2f(h * A.nl2c[i]);
+    }
+};
+template <> struct AtmT<double> {
+    static __device__ __forceinline__ double delta(const DevAtm &A, double h)
+    {
+        if (h >= A.h_top_d) return 0.0;
+        int i = 0;
+        for (int j = 1; j < A.n_layers; ++j)
+            if (h >= A.h_lo_d[j]) i = j;
+        return A.kb_d[i] * exp(-h * A.inv_c_d[i]);
+    }
+};
+
+template <class T> __device__ __forceinline__ T earth_radius(const DevAtm &A)
+{
+    return sizeof(T) == 4 ? (T)A.R_E : (T)A.R_E_d;
+}
+
+// Altitude without cancellation: |r + R_E z| - R_E = (x^2 + y^2 + z (z + 2 R_E)) / (|r + R_E z| + R_E).
+template <class T, bool SPH> __device__ __forceinline__ T altitude(const DevAtm &A, T x, T y, T z)
+{
+    if (!SPH) return z;
+    const T RE = earth_radius<T>(A);
+    T num = x * x + y * y + z * (z + (T)2 * RE);
+    T zc = z + RE;
+    return Num<T>::div(num, Num<T>::sqr(x * x + y * y + zc * zc) + RE);
+}
+
+// ------------------------------------------------------------------ segment
+// Everything one track step contributes to its photons (Sec. 1.2: the
+// atmosphere is homogeneous over a step, so theta_c and the yield are
+// per-step quantities).
+template <class T, class P> struct Seg {
+    P x0, y0, z0, t0;
+    P rz0;               // z0 + R_E (spherical): Earth-centred height of the start
+    T dx, dy, dz;        // unit direction (binary32 part)
+    T lx, ly, lz;        // its normalisation correction (pair low part)
+    T e1x, e1y, e1z, e2x, e2y, e2z;   // M_Rod x, M_Rod y
+    T sin_tc, kappa;     // sin(theta_c), 1 - cos(theta_c)
+    T L, inv_bc;         // step length, 1/(beta c) in ns/m
+    T w_c, w_f;
+    T h_mid;             // midpoint altitude
+    uint32_t n_c, n_f;
+    uint32_t shower;
+    int bad;             // 0 ok, else CLIGHT_ERR_* code
+    int guarded;
+};
+
+constexpr double kInvC = 3.3356409519815204;    // ns/m
+
+__device__ __forceinline__ bool finite_f(float v) { return (__float_as_uint(v) & 0x7f800000u) != 0x7f800000u; }
+__device__ __forceinline__ bool finite_d(double v)
+{
+    return ((unsigned long long)__double_as_longlong(v) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
+}
+
+__device__ __forceinline__ bool segment_ok(const clight_segment &s, const DevPar &P)
+{
+    return finite_d(s.x) && finite_d(s.y) && finite_d(s.z) && finite_d(s.t0) && finite_f(s.dx) &&
+           finite_f(s.dy) && finite_f(s.dz) && finite_f(s.L) && finite_f(s.eps) && finite_f(s.dE) &&
+           s.L >= 0.0f && s.eps >= 0.0f && s.eps < 1.0f && (int)s.shower < P.n_showers && s.shower < 0x7fffffffu;
+}
+
+// Yield and bunch count in binary64 (the plain path, and the guard of the
+// FP32 path when its count is not certain).  Frank-Tamm (Sec. 1.2):
+// N = 2 pi alpha z^2 (1/l1 - 1/l2) (1 - 1/(beta n)^2) L for beta n > 1.
+template <bool SPH>
+__device__ __forceinline__ void yield_fp64(const clight_segment &s, const DevAtm &A, const DevPar &P,
+                                           double ux, double uy, double uz, double *Nc, double *sin2,
+                                           double *kappa, double *Nf)
+{
+    double xm = s.x + 0.5 * (double)s.L * ux, ym = s.y + 0.5 * (double)s.L * uy,
+           zm = s.z + 0.5 * (double)s.L * uz;
+    double h;
+    if (SPH) {
+        double zc = zm + A.R_E_d;
+        h = sqrt(xm * xm + ym * ym + zc * zc) - A.R_E_d;
+    } else {
+        h = zm;
+    }
+    double dl = AtmT<double>::delta(A, h);
+    double eps = (double)s.eps;
+    double g1 = dl - eps - eps * dl;               // beta n - 1
+    double z2 = (double)s.charge * (double)s.charge;
+    *Nc = 0.0;
+    *sin2 = 0.0;
+    *kappa = 0.0;
+    if (z2 > 0.0 && g1 > 0.0 && s.L > 0.0f) {
+        double bn = 1.0 + g1;
+        *kappa = g1 / bn;                           // 1 - cos(theta_c)
+        *sin2 = g1 * (2.0 + g1) / (bn * bn);        // 1 - 1/(beta n)^2
+        *Nc = P.band_d * z2 * (*sin2) * (double)s.L;
+    }
+    *Nf = (P.fyield_d > 0.0 && s.dE > 0.0f && s.L > 0.0f) ? P.fyield_d * (double)s.dE : 0.0;
+}
+
+template <class T, class P>
+__device__ __forceinline__ void make_frame(Seg<T, P> &g)
+{
+    // A = unit bisector of the flight direction and -z; M x = 2 A_x A - x,
+    // M y = 2 A_y A - y (columns of M_Rod = 2 A A^T - 1).
+    T ax = g.dx, ay = g.dy, az = g.dz - (T)1;
+    T na2 = ax * ax + ay * ay + az * az;
+    if (na2 > (T)0) {
+        T inv = (T)1 / Num<T>::sqr(na2);
+        ax *= inv; ay *= inv; az *= inv;
+    } else {
+        ax = (T)1; ay = (T)0; az = (T)0;
+    }
+    g.e1x = (T)2 * ax * ax - (T)1; g.e1y = (T)2 * ax * ay;        g.e1z = (T)2 * ax * az;
+    g.e2x = (T)2 * ay * ax;        g.e2y = (T)2 * ay * ay - (T)1; g.e2z = (T)2 * ay * az;
+}
+
+// binary32 segment set-up with the binary64 guard on the integer bunch count.
+template <bool SPH>
+__device__ void load_segment_f(const clight_segment &s, const DevAtm &A, const DevPar &P, Seg<float, df> &g)
+{
+    g.bad = 0;
+    g.guarded = 0;
+    g.n_c = g.n_f = 0;
+    g.w_c = g.w_f = 0.0f;
+    g.shower = s.shower;
+    g.h_mid = 0.0f;
+    float n2 = s.dx * s.dx + s.dy * s.dy + s.dz * s.dz;
+    if (!segment_ok(s, P) || !(n2 > 0.0f)) {
+        g.bad = CLIGHT_ERR_BAD_SEGMENT;
+        g.dx = 0; g.dy = 0; g.dz = -1; g.lx = g.ly = g.lz = 0;
+        g.x0 = g.y0 = g.z0 = g.t0 = g.rz0 = df_make(0.0f);
+        g.L = 0; g.inv_bc = 0; g.sin_tc = 0; g.kappa = 0;
+        make_frame(g);
+        return;
+    }
+    // unit direction as a pair: the binary32 part normalised, the residual
+    // -(|d|^2 - 1)/2 d (from exact products) as the low part
+    df sq = two_prod(s.dx, s.dx) + two_prod(s.dy, s.dy) + two_prod(s.dz, s.dz);
+    float e = p_f(sq - 1.0f);
+    float f = rsqrtf(1.0f + e);
+    g.dx = s.dx * f; g.dy = s.dy * f; g.dz = s.dz * f;
+    df r2 = two_prod(g.dx, g.dx) + two_prod(g.dy, g.dy) + two_prod(g.dz, g.dz);
+    float e2 = p_f(r2 - 1.0f);
+    g.lx = -0.5f * e2 * g.dx; g.ly = -0.5f * e2 * g.dy; g.lz = -0.5f * e2 * g.dz;
+    g.x0 = df_from_double_bits(s.x);
+    g.y0 = df_from_double_bits(s.y);
+    g.z0 = df_from_double_bits(s.z);
+    g.t0 = df_from_double_bits(s.t0);
+    g.rz0 = SPH ? g.z0 + df{A.re_hi, A.re_lo} : g.z0;
+    g.L = s.L;
+    g.inv_bc = Num<float>::div(3.3356409519815204f, 1.0f - s.eps);   // 1/(beta c), ns/m
+    make_frame(g);
+
+    // midpoint altitude and refractivity (n constant over the step)
+    float hL = 0.5f * s.L;
+    float xm = g.x0.hi + hL * g.dx, ym = g.y0.hi + hL * g.dy, zm = g.z0.hi + hL * g.dz;
+    float hm = altitude<float, SPH>(A, xm, ym, zm);
+    g.h_mid = hm;
+    float dl = AtmT<float>::delta(A, hm);
+    float eps = s.eps;
+    float z2 = (float)s.charge * (float)s.charge;
+    // beta n - 1 = delta - eps - eps delta, kept as a small number
+    float g1 = __fmaf_rn(-eps, dl, dl - eps);
+    // error bound of g1 (delta known to ~1.5e-6 relative; generous factor)
+    float eg = 4.0e-6f * dl + 2.4e-7f * (dl + eps);
+    bool guard = false;
+    float Nc = 0.0f;
+    if (z2 > 0.0f && s.L > 0.0f) {
+        if (g1 > eg) {
+            float bn = 1.0f + g1;
+            float ib = rcp_approx(bn);
+            float sin2 = g1 * (2.0f + g1) * ib * ib;
+            Nc = P.band * z2 * sin2 * s.L;
+            g.sin_tc = sqrtf(sin2);
+            g.kappa = g1 * ib;
+            float x = Nc * P.inv_bunch;
+            float ex = x * (eg * rcp_approx(g1) * 2.0f + 2.0e-6f) + 1.0e-6f;
+            // an uncertain integer count, or a cone so narrow that its binary32
+            // angle would move photons by millimetres: recompute in binary64
+            if (ceilf(x - ex) != ceilf(x + ex) || g1 < 1.0e-6f * dl) guard = true;
+            else g.n_c = (uint32_t)ceilf(x);
+        } else if (g1 > -eg) {
+            guard = true;
+        }
+    }
+    if (!guard && g.n_c == 0) { g.sin_tc = 0.0f; g.kappa = 0.0f; }
+    float Nf = 0.0f;
+    bool fguard = false;
+    if (P.fyield > 0.0f && s.dE > 0.0f && s.L > 0.0f) {
+        Nf = P.fyield * s.dE;
+        float x = Nf * P.inv_bunch;
+        float ex = x * 1.0e-6f + 1.0e-7f;
+        if (ceilf(x - ex) != ceilf(x + ex)) fguard = true;
+        else g.n_f = (uint32_t)ceilf(x);
+    }
+    if (guard || fguard) {
+        g.guarded = 1;
+        double Ncd, sin2d, kapd, Nfd;
+        yield_fp64<SPH>(s, A, P, (double)g.dx + (double)g.lx, (double)g.dy + (double)g.ly,
+                        (double)g.dz + (double)g.lz, &Ncd, &sin2d, &kapd, &Nfd);
+        if (guard) {
+            double nb = ceil(Ncd / P.bunch_d);
+            g.n_c = (uint32_t)nb;
+            Nc = (float)Ncd;
+            g.sin_tc = (float)sqrt(sin2d);
+            g.kappa = (float)kapd;
+            if (g.n_c > 0) g.w_c = (float)(Ncd / nb);
+        }
+        if (fguard) {
+            double nb = ceil(Nfd / P.bunch_d);
+            g.n_f = (uint32_t)nb;
+            Nf = (float)Nfd;
+            if (g.n_f > 0) g.w_f = (float)(Nfd / nb);
+        }
+    }
+    if (!guard && g.n_c > 0) g.w_c = Nc * rcp_approx((float)g.n_c);
+    if (!fguard && g.n_f > 0) g.w_f = Nf * rcp_approx((float)g.n_f);
+}
+
+// binary64 segment set-up (plain path).
+template <bool SPH>
+__device__ void load_segment_d(const clight_segment &s, const DevAtm &A, const DevPar &P, Seg<double, double> &g)
+{
+    g.bad = 0;
+    g.guarded = 0;
+    g.n_c = g.n_f = 0;
+    g.w_c = g.w_f = 0.0;
+    g.shower = s.shower;
+    double n2 = (double)s.dx * s.dx + (double)s.dy * s.dy + (double)s.dz * s.dz;
+    if (!segment_ok(s, P) || !(n2 > 0.0)) {
+        g.bad = CLIGHT_ERR_BAD_SEGMENT;
+        return;
+    }
+    double inv = 1.0 / sqrt(n2);
+    g.dx = s.dx * inv; g.dy = s.dy * inv; g.dz = s.dz * inv;
+    g.lx = g.ly = g.lz = 0.0;
+    g.x0 = s.x; g.y0 = s.y; g.z0 = s.z; g.t0 = s.t0;
+    g.rz0 = SPH ? s.z + A.R_E_d : s.z;
+    g.L = s.L;
+    g.inv_bc = kInvC / (1.0 - (double)s.eps);
+    make_frame(g);
+    double Nc, sin2, kap, Nf;
+    yield_fp64<SPH>(s, A, P, g.dx, g.dy, g.dz, &Nc, &sin2, &kap, &Nf);
+    g.sin_tc = sqrt(sin2);
+    g.kappa = kap;
+    if (Nc > 0.0) {
+        double nb = ceil(Nc / P.bunch_d);
+        g.n_c = (uint32_t)nb;
+        g.w_c = Nc / nb;
+    }
+    if (Nf > 0.0) {
+        double nb = ceil(Nf / P.bunch_d);
+        g.n_f = (uint32_t)nb;
+        g.w_f = Nf / nb;
+    }
+}
+
+// ------------------------------------------------------------------ one ray
+template <class T, class P> struct RayOut {
+    P X, Y;            // crossing of the plane z = h_obs
+    P t;               // arrival time there
+    T cx, cy, cz;      // arrival direction
+    T lambda, weight;
+    int status;        // 0 reached, 1 escaped, 2 under, 3 turned, 4 idle lane, 5 reached (grazing, not landed)
+    uint32_t cells;    // quadrature cells integrated
+};
+
+// Quadrature of the refracted ray's deviation from the vacuum line.
+//   I0: integral whose p_v multiple is the angle (spherical) or horizontal
+//       distance (flat) the refracted ray falls short of the vacuum line;
+//   I1: optical path minus vacuum path length;
+//   I2: density-weighted path (rho / rho_ref) ds.
+// r = R_E + h (spherical) or 1 (flat); q_v = r^2 - p_v^2,
+// q = n^2 q_v + (n^2 - n_e^2) p_v^2 = n^2 r^2 - (n_e p_v)^2.
+template <class T, bool WARP, bool SPH, bool REFR>
+__device__ __forceinline__ void ray_quadrature(const DevAtm &A, T hcap, T he, T de, T pv2, T bf2, T &I0, T &I1,
+                                               T &I2, uint32_t &ncell)
+{
+    I0 = I1 = I2 = (T)0;
+    const T RE = earth_radius<T>(A);
+    const T ne = (T)1 + de;
+    for (int c = 0; c < A.n_cells; ++c) {
+        const DevCell &C = A.cells[c];
+        T lo = sizeof(T) == 4 ? (T)C.lo : (T)A.cell_lo_d[c];
+        bool act = hcap > lo;
+        if (WARP) {
+            if (!__any_sync(FULL_MASK, act)) break;
+        } else {
+            if (!act) break;
+        }
+        if (!act) continue;
+        ++ncell;
+        T chi = sizeof(T) == 4 ? (T)C.hi : (T)A.cell_hi_d[c];
+        T hi = hcap < chi ? hcap : chi;
+        T mid = (T)0.5 * (lo + hi), half = (T)0.5 * (hi - lo);
+        T kb = sizeof(T) == 4 ? (T)C.kb : (T)A.cell_kb_d[c];
+        T rb = sizeof(T) == 4 ? (T)C.rb : (T)A.cell_rb_d[c];
+        T nl = sizeof(T) == 4 ? (T)C.nl2c : (T)-A.cell_ic_d[c];
+        T s0 = 0, s1 = 0, s2 = 0;
+#pragma unroll
+        for (int gi = 0; gi < kGLNodes; ++gi) {
+            T xg, wg;
+            if (sizeof(T) == 4) { xg = (T)A.gl_x[gi]; wg = (T)A.gl_w[gi]; }
+            else { xg = (T)A.gl_x_d[gi]; wg = (T)A.gl_w_d[gi]; }
+            T h = mid + half * xg;
+            // float: 2^(h nl) with nl = -log2(e)/c; double: e^(h nl) with nl = -1/c
+            T ex = sizeof(T) == 4 ? (T)ex2_approx((float)(h * nl)) : (T)exp((double)(h * nl));
+            T dl = kb * ex;
+            T rr = rb * ex;
+            T r = SPH ? RE + h : (T)1;
+            T qv = SPH ? (h - he) * ((T)2 * RE + h + he) + bf2 : bf2;
+            if (REFR) {
+                T n = (T)1 + dl;
+                T n2 = n * n;
+                T gg = (dl - de) * ((T)2 + dl + de);          // n^2 - n_e^2
+                T q = n2 * qv + gg * pv2;
+                T rq = Num<T>::rsq(q), rqv = Num<T>::rsq(qv);
+                T sq = q * rq, sqv = qv * rqv;
+                T cm = rq * rqv;
+                T a = dl * ((T)2 + dl);                         // n^2 - 1
+                s0 += wg * Num<T>::div(-r * gg * cm, ne * sqv + sq);
+                s1 += wg * Num<T>::div(r * (n2 * a * qv - gg * pv2) * cm, n2 * sqv + sq);
+                s2 += wg * (rr * n * r * rq);
+            } else {
+                T rqv = Num<T>::rsq(qv);
+                s1 += wg * (dl * r * rqv);
+                s2 += wg * (rr * r * rqv);
+            }
+        }
+        I0 += s0 * half;
+        I1 += s1 * half;
+        I2 += s2 * half;
+    }
+}
+
+template <class T, class P, bool WARP, bool SPH, bool REFR>
+__device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global, uint32_t k, bool active,
+                                          const DevAtm &A, const DevPar &Pp, RayOut<T, P> &o)
+{
+    // ---- generation (Sec. 1.1, 1.2, 1.2.1; Fig. 1)
+    uint32_t proc = k < g.n_c ? 0u : 1u;
+    uint32_t kk = proc ? k - g.n_c : k;
+    uint4 x = philox4x32_10(make_uint4((uint32_t)(uint64_t)seg_global,
+                                       (uint32_t)((uint64_t)seg_global >> 32), kk, proc),
+                            Pp.seed, Pp.stream);
+    T u0 = u01<T>(x.x), u1 = u01<T>(x.y), u2 = u01<T>(x.z), u3 = u01<T>(x.w);
+    P dgx, dgy, dgz;
+    T lam, w;
+    if (proc == 0) {
+        T il1 = sizeof(T) == 4 ? (T)Pp.il1 : (T)Pp.il1_d;
+        T dil = sizeof(T) == 4 ? (T)Pp.dil : (T)Pp.dil_d;
+        lam = Num<T>::div((T)1, il1 - u0 * dil);           // density ~ 1/lambda^2
+        T sc, cc;
+        Num<T>::sincos2pi(u2, &sc, &cc);
+        T st = g.sin_tc;
+        T sx = -g.kappa * g.dx + st * (cc * g.e1x + sc * g.e2x);
+        T sy = -g.kappa * g.dy + st * (cc * g.e1y + sc * g.e2y);
+        T sz = -g.kappa * g.dz + st * (cc * g.e1z + sc * g.e2z);
+        // cos(theta_c) d + sin(theta_c)(cos c e1 + sin c e2), d kept as a pair
+        dgx = p_of<P>(g.dx) + (g.lx + sx);
+        dgy = p_of<P>(g.dy) + (g.ly + sy);
+        dgz = p_of<P>(g.dz) + (g.lz + sz);
+        w = g.w_c;
+    } else {
+        T fl1 = sizeof(T) == 4 ? (T)Pp.fl1 : (T)Pp.fl1_d;
+        T fdl = sizeof(T) == 4 ? (T)Pp.fdl : (T)Pp.fdl_d;
+        lam = fl1 + u0 * fdl;
+        T cz = (T)2 * u3 - (T)1;                            // exact
+        T sz = Num<T>::sqr(((T)1 - cz) * ((T)1 + cz));
+        T sp, cp;
+        Num<T>::sincos2pi(u2, &sp, &cp);
+        dgx = p_of<P>(sz * cp);
+        dgy = p_of<P>(sz * sp);
+        dgz = p_of<P>(cz);
+        w = g.w_f;
+    }
+    T ell = u1 * g.L;
+    P xe = g.x0 + ell * (g.dx + g.lx);
+    P ye = g.y0 + ell * (g.dy + g.ly);
+    P ze = g.z0 + ell * (g.dz + g.lz);
+    P te = g.t0 + ell * g.inv_bc;
+    o.lambda = lam;
+    o.status = 0;
+
+    T dx = to_t<T>(dgx), dy = to_t<T>(dgy), dz = to_t<T>(dgz);
+    T xef = to_t<T>(xe), yef = to_t<T>(ye), zef = to_t<T>(ze);
+    const T h_obs = sizeof(T) == 4 ? (T)A.h_obs : (T)A.h_obs_d;
+    const P Hobs = pc<P>(A.hobs_hi, A.hobs_lo, A.h_obs_d);     // exact constants for the pair arithmetic
+
+    // ---- vacuum straight line to the observation level (exact geometry)
+    P s_v;
+    T he, pv2, bf2, bf, sqf = 0;
+    bool esc = false, under = false, turned = false, grazing = false;
+    if (SPH) {
+        P Rz = g.rz0 + ell * (g.dz + g.lz);                 // z_e + R_E
+        // b = -(d . R_e) = r_e cos(psi_e); C = |R_e|^2 - r_obs^2
+        P b = -(dgz * Rz) - (dx * xef + dy * yef);
+        he = altitude<T, SPH>(A, xef, yef, zef);
+        esc = !(p_f(b) > 0.0f);
+        under = he <= h_obs;
+        P dzo = ze - Hobs;
+        P C = dzo * (ze + pc<P>(A.k2_hi, A.k2_lo, A.k2_d)) + (xef * xef + yef * yef);
+        T Rzf = to_t<T>(Rz);
+        T c1 = dy * Rzf - dz * yef, c2 = dz * xef - dx * Rzf, c3 = dx * yef - dy * xef;
+        pv2 = c1 * c1 + c2 * c2 + c3 * c3;                   // (r_e sin psi_e)^2
+        bf = to_t<T>(b);
+        bf2 = bf * bf;                                       // (r_e cos psi_e)^2
+        // s_v = b - sqrt(b^2 - C) = (C / b) / (1 + sqrt(1 - x)), x = C / b^2,
+        // and 1 / (1 + sqrt(1 - x)) = 1/2 + g with g = x / (2 (1 + sqrt(1 - x))^2)
+        // small enough that binary32 carries it to ~1e-9 absolute.
+        T xx = Num<T>::div(to_t<T>(C), bf2);
+        T om = (T)1 - xx;                                    // disc / b^2
+        T discf = bf2 * om;
+        if (REFR) {
+            // reaches the observation sphere iff q(r_obs) > 0, with
+            // q_v(r_obs) = disc: q(r_obs) = n_obs^2 disc + (n_obs^2 - n_e^2) p_v^2
+            T de0 = AtmT<T>::delta(A, he);
+            T dob = sizeof(T) == 4 ? (T)A.delta_obs : (T)A.delta_obs_d;
+            T nob = (T)1 + dob;
+            T qL = nob * nob * discf + (dob - de0) * ((T)2 + dob + de0) * pv2;
+            turned = !(qL > (T)0);
+            grazing = !turned && !(om > (T)0);   // reaches, but the vacuum line misses: not landed
+        } else {
+            turned = !(om > (T)0);
+        }
+        if (!(esc || under || turned || grazing)) {
+            T so = Num<T>::sqr(om);
+            T gx = Num<T>::div(xx, (T)2 * ((T)1 + so) * ((T)1 + so));
+            P f;
+            if (sizeof(T) == 4) p_from_pair(f, df{0.5f, (float)gx});
+            else f = p_of<P>((T)0.5 + gx);
+            s_v = (C / b) * f;
+            sqf = bf * so;                                   // r_obs cos(psi) of the vacuum line
+        } else {
+            s_v = p_of<P>((T)0);
+        }
+    } else {
+        he = zef;
+        esc = !(p_f(dgz) < 0.0f);
+        under = !(p_f(ze - Hobs) > 0.0f);
+        if (!(esc || under)) s_v = (ze - Hobs) / (-dgz);
+        else s_v = p_of<P>((T)0);
+        pv2 = dx * dx + dy * dy;                             // sin^2 theta_e
+        bf = -dz;
+        bf2 = bf * bf;                                       // cos^2 theta_e
+    }
+    if (!active) { o.status = 4; }
+    else if (esc) { o.status = 1; }
+    else if (under) { o.status = 2; }
+    else if (turned) { o.status = 3; }
+    else if (grazing) { o.status = 5; }
+    bool go = o.status == 0;
+
+    // ---- refraction, optical path and optical depth by quadrature
+    T de = AtmT<T>::delta(A, he);
+    T htop = sizeof(T) == 4 ? (T)A.h_top : (T)A.h_top_d;
+    T hcap = go ? (he < htop ? he : htop) : (T)-1e30;
+    T I0, I1, I2;
+    o.cells = 0;
+    ray_quadrature<T, WARP, SPH, REFR>(A, hcap, he, de, pv2, bf2, I0, I1, I2, o.cells);
+    if (!go) return;
+
+    const T n_obs = sizeof(T) == 4 ? (T)A.n_obs : (T)1 + (T)A.delta_obs_d;
+    const T d_obs = sizeof(T) == 4 ? (T)A.delta_obs : (T)A.delta_obs_d;
+    const T ne = (T)1 + de;
+    T dLx, dLy, dLz;
+    P X, Y, tt;
+    T chord = 0;
+    if (SPH) {
+        const T r_obs = sizeof(T) == 4 ? (T)A.r_obs : (T)A.r_obs_d;
+        P Pvx = xe + s_v * dgx;
+        P Pvy = ye + s_v * dgy;
+        P Pvz = ze + s_v * dgz;
+        T RLx = to_t<T>(Pvx), RLy = to_t<T>(Pvy), RLz = to_t<T>(Pvz + pc<P>(A.re_hi, A.re_lo, A.R_E_d));
+        T ir = Num<T>::div((T)1, r_obs);
+        // T_v = r_obs d + cos(psi_v) R_L: in-plane tangent scaled by p_v
+        T Tx = r_obs * dx + sqf * ir * RLx, Ty = r_obs * dy + sqf * ir * RLy, Tz = r_obs * dz + sqf * ir * RLz;
+        T Rhx = RLx * ir, Rhy = RLy * ir, Rhz = RLz * ir;
+        P PLx = Pvx, PLy = Pvy, PLz = Pvz;
+        if (REFR) {
+            T pv = Num<T>::sqr(pv2);
+            T dphi = I0 * pv;
+            T sfac = r_obs * I0;                              // r_obs dphi / p_v
+            T c2 = (T)0.5 * r_obs * dphi * dphi;
+            PLx = Pvx + (sfac * Tx - c2 * Rhx);
+            PLy = Pvy + (sfac * Ty - c2 * Rhy);
+            PLz = Pvz + (sfac * Tz - c2 * Rhz);
+            T qvL = sqf * sqf;
+            T gL = (d_obs - de) * ((T)2 + d_obs + de);
+            T qL = n_obs * n_obs * qvL + gL * pv2;
+            T inr = Num<T>::div((T)1, n_obs * r_obs);
+            T cpsi = Num<T>::sqr(qL) * inr;
+            T spsi = ne * pv * inr;
+            T at = ne * inr - cpsi * I0;
+            T ar = cpsi + spsi * dphi;
+            dLx = at * Tx - ar * Rhx;
+            dLy = at * Ty - ar * Rhy;
+            dLz = at * Tz - ar * Rhz;
+        } else {
+            dLx = dx; dLy = dy; dLz = dz;
+        }
+        // from the observation sphere back to the tangent plane z = h_obs
+        T zeta = -to_t<T>(PLz - Hobs);
+        chord = Num<T>::div(zeta, dLz);
+        X = PLx + chord * dLx;
+        Y = PLy + chord * dLy;
+    } else {
+        X = xe + s_v * dgx;
+        Y = ye + s_v * dgy;
+        if (REFR) {
+            X = X + I0 * dx;
+            Y = Y + I0 * dy;
+            T qL = n_obs * n_obs * bf2 + (d_obs - de) * ((T)2 + d_obs + de) * pv2;
+            T f = Num<T>::div(ne, n_obs);
+            dLx = f * dx;
+            dLy = f * dy;
+            dLz = -Num<T>::div(Num<T>::sqr(qL), n_obs);
+        } else {
+            dLx = dx; dLy = dy; dLz = dz;
+        }
+    }
+    // time: t_e + (vacuum path + optical excess + chord) / c
+    const T invc = (T)kInvC;
+    P sv_t = s_v * pc<P>(A.invc_hi, A.invc_lo, kInvC);
+    tt = te + sv_t + (I1 + n_obs * chord) * invc;
+    T tau = 0;
+    if (A.absorption) {
+        T lr = Num<T>::div(sizeof(T) == 4 ? (T)A.lambda_ref : (T)A.lambda_ref_d, lam);
+        T lr2 = lr * lr;
+        tau = I2 * lr2 * lr2 * (sizeof(T) == 4 ? (T)A.inv_L0 : (T)A.inv_L0_d);
+    }
+    o.X = X;
+    o.Y = Y;
+    o.t = tt;
+    o.cx = dLx; o.cy = dLy; o.cz = dLz;
+    o.weight = A.absorption ? w * (sizeof(T) == 4 ? (T)expf((float)-tau) : (T)exp((double)-tau)) : w;
+}
+
+// ------------------------------------------------------------------ hits
+__device__ __forceinline__ void write_hit(const DevOut &O, unsigned long long idx, int64_t seg, uint32_t k,
+                                          uint32_t tel, float xr, float yr, float cx, float cy, float lam,
+                                          float w, double t, unsigned long long key)
+{
+    if ((int64_t)idx >= O.capacity) return;
+    float4 *p = reinterpret_cast<float4 *>(O.rec + idx);
+    uint32_t slo = (uint32_t)(uint64_t)seg, shi = (uint32_t)((uint64_t)seg >> 32);
+    p[0] = make_float4(__uint_as_float(slo), __uint_as_float(shi), __uint_as_float(k), __uint_as_float(tel));
+    p[1] = make_float4(xr, yr, cx, cy);
+    unsigned long long tb = (unsigned long long)__double_as_longlong(t);
+    p[2] = make_float4(lam, w, __uint_as_float((uint32_t)tb), __uint_as_float((uint32_t)(tb >> 32)));
+    O.keys[idx] = key;
+    O.vals[idx] = (uint32_t)idx;
+}
+
+// The record alone, for the entry point that keeps no sort keys.
+__device__ __forceinline__ void write_hit_record(clight_hit *rec, int64_t capacity, unsigned long long idx,
+                                                 int64_t seg, uint32_t k, uint32_t tel, float xr, float yr,
+                                                 float cx, float cy, float lam, float w, double t)
+{
+    if ((int64_t)idx >= capacity) return;
+    float4 *p = reinterpret_cast<float4 *>(rec + idx);
+    uint32_t slo = (uint32_t)(uint64_t)seg, shi = (uint32_t)((uint64_t)seg >> 32);
+    p[0] = make_float4(__uint_as_float(slo), __uint_as_float(shi), __uint_as_float(k), __uint_as_float(tel));
+    p[1] = make_float4(xr, yr, cx, cy);
+    unsigned long long tb = (unsigned long long)__double_as_longlong(t);
+    p[2] = make_float4(lam, w, __uint_as_float((uint32_t)tb), __uint_as_float((uint32_t)(tb >> 32)));
+}
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Test the arrival line against the telescopes near the crossing point and
+// append every hit.  A sphere of radius R is hit when the line passes closer
+// than R to its centre; its centre can then lie at most R / |cz| from the
+// crossing point, which bounds the cells searched.
+template <class T, class P, bool WARP, bool NOALLOC = false>
+__device__ __forceinline__ int hit_test(const RayOut<T, P> &o, int64_t seg_local, int64_t seg_global, uint32_t k,
+                                        uint32_t shower, const DevAtm &A, const DevTel &Tl, const DevPar &Pp,
+                                        const DevOut &O, unsigned &status_bits)
+{
+    if (o.status != 0) return 0;
+    float Xf = p_f(o.X), Yf = p_f(o.Y);
+    float cz = (float)o.cz, cx = (float)o.cx, cy = (float)o.cy;
+    if (!(finite_f(Xf) && finite_f(Yf) && cz < 0.0f)) return 0;
+    float acz = fabsf(cz);
+    float dzmax = fmaxf(fabsf(Tl.zmax - A.h_obs), fabsf(Tl.zmin - A.h_obs));
+    float rs = (Tl.Rmax + dzmax * sqrtf(fmaxf(0.0f, 1.0f - acz * acz))) * rcp_approx(fmaxf(acz, 1e-6f)) + 1e-3f;
+    if (Xf + rs < Tl.xmin || Xf - rs > Tl.xmax || Yf + rs < Tl.ymin || Yf - rs > Tl.ymax) return 0;
+    int ix0 = max(0, (int)floorf((Xf - rs - Tl.gx0) * Tl.inv_gs));
+    int ix1 = min(Tl.nx - 1, (int)floorf((Xf + rs - Tl.gx0) * Tl.inv_gs));
+    int iy0 = max(0, (int)floorf((Yf - rs - Tl.gy0) * Tl.inv_gs));
+    int iy1 = min(Tl.ny - 1, (int)floorf((Yf + rs - Tl.gy0) * Tl.inv_gs));
+    int nh = 0;
+    for (int iy = iy0; iy <= iy1; ++iy) {
+        for (int ix = ix0; ix <= ix1; ++ix) {
+            int cell = iy * Tl.nx + ix;
+            int b = __ldg(Tl.cell_start + cell), e = __ldg(Tl.cell_start + cell + 1);
+            for (int q = b; q < e; ++q) {
+                int j = __ldg(Tl.cell_tel + q);
+                float4 tp = __ldg(Tl.tel + j);
+                // crossing point relative to the centre, at the plane z = z_j
+                float dzj = tp.z - A.h_obs;
+                float sj = Num<float>::div(dzj, cz);
+                float xr = p_f(o.X - (T)tp.x) + sj * cx;
+                float yr = p_f(o.Y - (T)tp.y) + sj * cy;
+                // impact parameter
+                float wd = xr * cx + yr * cy;
+                float d2 = xr * xr + yr * yr - wd * wd;
+                if (d2 < tp.w * tp.w) {
+                    ++nh;
+                    P tjp = o.t + (T)(A.n_obs * sj) * (T)kInvC;
+                    double tj = p_d(tjp);                        // one conversion per hit
+                    uint32_t group = shower * (uint32_t)Tl.n_tel + (uint32_t)j;
+                    if (NOALLOC) {
+                        // no sort keys: the record goes straight to the caller's
+                        // buffer and O.keys holds one hit counter per group
+                        unsigned m = __activemask();
+                        int leader = __ffs(m) - 1;
+                        unsigned long long base = 0;
+                        if ((int)(threadIdx.x & 31) == leader) base = atomicAdd(O.ctr + CTR_CURSOR, (unsigned long long)__popc(m));
+                        base = __shfl_sync(m, base, leader);
+                        unsigned long long idx = base + __popc(m & lanemask_lt());
+                        write_hit_record(O.rec, O.capacity, idx, seg_global, k, (uint32_t)j, xr, yr, cx, cy,
+                                         (float)o.lambda, (float)o.weight, tj);
+                        atomicAdd(O.keys + group, 1ull);
+                        continue;
+                    }
+                    unsigned long long key;
+                    if (Pp.k_bits < 32 && k >= (1u << Pp.k_bits)) {
+                        status_bits |= 1u << CLIGHT_ERR_LIMIT;
+                        key = ~0ull;
+                    } else {
+                        key = ((unsigned long long)group << (Pp.seg_bits + Pp.k_bits)) |
+                              ((unsigned long long)seg_local << Pp.k_bits) | (unsigned long long)k;
+                    }
+                    unsigned long long idx;
+                    if (WARP) {
+                        unsigned m = __activemask();
+                        int leader = __ffs(m) - 1;
+                        unsigned long long base = 0;
+                        if ((int)(threadIdx.x & 31) == leader) base = atomicAdd(O.ctr + CTR_CURSOR, (unsigned long long)__popc(m));
+                        base = __shfl_sync(m, base, leader);
+                        idx = base + __popc(m & lanemask_lt());
+                    } else {
+                        idx = atomicAdd(O.ctr + CTR_CURSOR, 1ull);
+                    }
+                    write_hit(O, idx, seg_global, k, (uint32_t)j, xr, yr, cx, cy, (float)o.lambda,
+                              (float)o.weight, tj, key);
+                }
+            }
+        }
+    }
+    return nh;
+}
+
+}  // namespace clight
