@@ -66,6 +66,7 @@ struct clight_ctx {
     // telescope tables (device)
     float4 *d_tel = nullptr;
     int *d_cell_start = nullptr, *d_cell_tel = nullptr;
+    uint8_t *d_clr = nullptr;
     // scratch (device)
     unsigned long long *d_ctr = nullptr;
     Buf<clight_hit> rec;
@@ -164,7 +165,7 @@ void clight_destroy(clight_ctx *c)
     if (!c) return;
     cudaSetDevice(c->device);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
-    void *dev[] = {c->d_tel, c->d_cell_start, c->d_cell_tel, c->d_ctr};
+    void *dev[] = {c->d_tel, c->d_cell_start, c->d_cell_tel, c->d_clr, c->d_ctr};
     for (void *p : dev)
         if (p) cudaFree(p);
     c->rec.release(); c->keys.release(); c->keys_alt.release(); c->vals.release(); c->vals_alt.release();
@@ -321,18 +322,56 @@ clight_status clight_set_telescopes(clight_ctx *c, const clight_telescope *t, in
     for (int i = 0; i < n; ++i) tel_idx[fill[cell_of[i]]++] = i;
     std::vector<float4> tv(n);
     for (int i = 0; i < n; ++i) tv[i] = make_float4(t[i].x, t[i].y, t[i].z, t[i].R);
+
+    // clearance map over the array's box widened by 20 m: a ray whose search
+    // radius is below its cell's value cannot reach any sphere, so the hit
+    // test of most rays ends with one shared-memory byte.  A cell's value is
+    // the distance from the closed cell to the nearest centre, less 1 cm
+    // (rounding of the cell index), rounded down to the quantum.
+    const double margin = 20.0, q = kClrQuantum, reach = 255.0 * q;
+    double bx0 = xmin - margin, by0 = ymin - margin;
+    double wx = (double)(xmax - xmin) + 2 * margin, wy = (double)(ymax - ymin) + 2 * margin;
+    double cgs = std::max(0.5, std::sqrt(wx * wy / kClrMaxCells));
+    int cnx = (int)std::ceil(wx / cgs), cny = (int)std::ceil(wy / cgs);
+    while ((int64_t)cnx * cny > kClrMaxCells) { cgs *= 1.05; cnx = (int)std::ceil(wx / cgs); cny = (int)std::ceil(wy / cgs); }
+    std::vector<uint8_t> clr((size_t)cnx * cny, 255);
+    for (int i = 0; i < n; ++i) {
+        int ix0 = std::max(0, (int)std::floor((t[i].x - reach - bx0) / cgs) - 1);
+        int ix1 = std::min(cnx - 1, (int)std::floor((t[i].x + reach - bx0) / cgs) + 1);
+        int iy0 = std::max(0, (int)std::floor((t[i].y - reach - by0) / cgs) - 1);
+        int iy1 = std::min(cny - 1, (int)std::floor((t[i].y + reach - by0) / cgs) + 1);
+        for (int iy = iy0; iy <= iy1; ++iy)
+            for (int ix = ix0; ix <= ix1; ++ix) {
+                double lx = bx0 + ix * cgs, ly = by0 + iy * cgs;
+                double dx = std::max(0.0, std::max(lx - t[i].x, t[i].x - (lx + cgs)));
+                double dy = std::max(0.0, std::max(ly - t[i].y, t[i].y - (ly + cgs)));
+                double d = std::sqrt(dx * dx + dy * dy) - 0.01;
+                double v = d <= 0 ? 0.0 : std::floor(d / q);
+                uint8_t u = (uint8_t)std::min(255.0, v);
+                uint8_t &cell = clr[(size_t)iy * cnx + ix];
+                if (u < cell) cell = u;
+            }
+    }
+    int clr_bytes = (int)((clr.size() + 15) / 16 * 16);
+    clr.resize(clr_bytes, 0);
+
     cudaSetDevice(c->device);
     if (c->d_tel) cudaFree(c->d_tel);
     if (c->d_cell_start) cudaFree(c->d_cell_start);
     if (c->d_cell_tel) cudaFree(c->d_cell_tel);
-    c->d_tel = nullptr; c->d_cell_start = nullptr; c->d_cell_tel = nullptr;
+    if (c->d_clr) cudaFree(c->d_clr);
+    c->d_tel = nullptr; c->d_cell_start = nullptr; c->d_cell_tel = nullptr; c->d_clr = nullptr;
     CK(cudaMalloc((void **)&c->d_tel, sizeof(float4) * n));
     CK(cudaMalloc((void **)&c->d_cell_start, sizeof(int) * count.size()));
     CK(cudaMalloc((void **)&c->d_cell_tel, sizeof(int) * n));
+    CK(cudaMalloc((void **)&c->d_clr, (size_t)clr_bytes));
     CK(cudaMemcpy(c->d_tel, tv.data(), sizeof(float4) * n, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->d_cell_start, count.data(), sizeof(int) * count.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->d_cell_tel, tel_idx.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_clr, clr.data(), (size_t)clr_bytes, cudaMemcpyHostToDevice));
     DevTel &T = c->tel;
+    T.clr = c->d_clr; T.cnx = cnx; T.cny = cny; T.clr_bytes = clr_bytes;
+    T.cx0 = (float)bx0; T.cy0 = (float)by0; T.inv_cgs = (float)(1.0 / cgs);
     T.tel = c->d_tel; T.cell_start = c->d_cell_start; T.cell_tel = c->d_cell_tel;
     T.n_tel = n; T.nx = nx; T.ny = ny;
     T.gx0 = xmin; T.gy0 = ymin; T.gs = (float)gs; T.inv_gs = (float)(1.0 / gs);
@@ -395,7 +434,7 @@ bool clight::ctx_view(clight_ctx *c, CtxView *v)
     v->device = c->device;
     v->n_sm = c->n_sm;
     v->block = c->upar.block > 0 ? c->upar.block : 256;
-    v->ctas_per_sm = c->upar.ctas_per_sm > 0 ? c->upar.ctas_per_sm : 2 * 256 / v->block;
+    v->ctas_per_sm = c->upar.ctas_per_sm > 0 ? c->upar.ctas_per_sm : 3 * 256 / v->block;
     v->precision = c->upar.precision;
     return true;
 }
@@ -464,7 +503,7 @@ cudaError_t enqueue(clight_ctx *c, const clight_segment *segs, int64_t n_segs, c
             e = launch_trace_fp64(segs, n_segs, c->atm, c->tel, c->par, O, s);
         } else {
             int block = c->upar.block > 0 ? c->upar.block : 256;
-            int per_sm = c->upar.ctas_per_sm > 0 ? c->upar.ctas_per_sm : 2 * 256 / block;
+            int per_sm = c->upar.ctas_per_sm > 0 ? c->upar.ctas_per_sm : 3 * 256 / block;
             int64_t groups = (n_segs + 31) / 32;
             int64_t grid = std::min<int64_t>((int64_t)c->n_sm * per_sm, (groups * 32 + block - 1) / block);
             grid = std::max<int64_t>(grid, 1);

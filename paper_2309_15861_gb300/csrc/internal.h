@@ -49,7 +49,15 @@ struct DevTel {
     int n_tel, nx, ny, pad;
     float gx0, gy0, gs, inv_gs; // grid origin and cell size
     float xmin, xmax, ymin, ymax, Rmax, zmin, zmax, pad2;
+    // clearance map: per square cell of side cgs, a lower bound on the
+    // distance from any point of the cell to the nearest telescope centre,
+    // in units of kClrQuantum (255 = at least 255 units); nullptr if none
+    const uint8_t *clr;
+    int cnx, cny, clr_bytes, pad3;  // cells, bytes (a multiple of 16)
+    float cx0, cy0, inv_cgs, pad4;
 };
+constexpr float kClrQuantum = 0.25f;     // metres per unit of the clearance map
+constexpr int kClrMaxCells = 12288;      // 12 KB of shared memory per CTA
 
 struct DevPar {
     float band, inv_bunch;       // 2 pi alpha (1/l1 - 1/l2) [1/m], 1/B
@@ -93,7 +101,7 @@ cudaError_t launch_trace_fused(const clight_segment *segs, int64_t n_segs, const
                                int grid, int block, cudaStream_t s);
 cudaError_t launch_trace_fp64(const clight_segment *segs, int64_t n_segs, const DevAtm &A,
                               const DevTel &T, const DevPar &P, const DevOut &O, cudaStream_t s);
-int fused_smem_bytes(int block);
+int fused_smem_bytes(int block, const DevTel &T);
 
 // tangent-linear adjoint (adjoint_kernels.cu)
 int adjoint_params(int n_layers);   // tangents carried: >= n_layers + 2

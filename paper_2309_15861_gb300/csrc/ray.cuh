@@ -526,13 +526,14 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
 
     // ---- vacuum straight line to the observation level (exact geometry)
     P s_v;
-    T he, pv2, bf2, bf, sqf = 0;
+    T he, de, pv2, bf2, bf, sqf = 0;
     bool esc = false, under = false, turned = false, grazing = false;
     if (SPH) {
         P Rz = g.rz0 + ell * (g.dz + g.lz);                 // z_e + R_E
         // b = -(d . R_e) = r_e cos(psi_e); C = |R_e|^2 - r_obs^2
         P b = -(dgz * Rz) - (dx * xef + dy * yef);
         he = altitude<T, SPH>(A, xef, yef, zef);
+        de = AtmT<T>::delta(A, he);                          // n_e - 1
         esc = !(p_f(b) > 0.0f);
         under = he <= h_obs;
         P dzo = ze - Hobs;
@@ -551,10 +552,9 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
         if (REFR) {
             // reaches the observation sphere iff q(r_obs) > 0, with
             // q_v(r_obs) = disc: q(r_obs) = n_obs^2 disc + (n_obs^2 - n_e^2) p_v^2
-            T de0 = AtmT<T>::delta(A, he);
             T dob = sizeof(T) == 4 ? (T)A.delta_obs : (T)A.delta_obs_d;
             T nob = (T)1 + dob;
-            T qL = nob * nob * discf + (dob - de0) * ((T)2 + dob + de0) * pv2;
+            T qL = nob * nob * discf + (dob - de) * ((T)2 + dob + de) * pv2;
             turned = !(qL > (T)0);
             grazing = !turned && !(om > (T)0);   // reaches, but the vacuum line misses: not landed
         } else {
@@ -573,6 +573,7 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
         }
     } else {
         he = zef;
+        de = AtmT<T>::delta(A, he);
         esc = !(p_f(dgz) < 0.0f);
         under = !(p_f(ze - Hobs) > 0.0f);
         if (!(esc || under)) s_v = (ze - Hobs) / (-dgz);
@@ -589,7 +590,6 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
     bool go = o.status == 0;
 
     // ---- refraction, optical path and optical depth by quadrature
-    T de = AtmT<T>::delta(A, he);
     T htop = sizeof(T) == 4 ? (T)A.h_top : (T)A.h_top_d;
     T hcap = go ? (he < htop ? he : htop) : (T)-1e30;
     T I0, I1, I2;
@@ -717,7 +717,7 @@ __device__ __forceinline__ unsigned lanemask_lt()
 template <class T, class P, bool WARP, bool NOALLOC = false>
 __device__ __forceinline__ int hit_test(const RayOut<T, P> &o, int64_t seg_local, int64_t seg_global, uint32_t k,
                                         uint32_t shower, const DevAtm &A, const DevTel &Tl, const DevPar &Pp,
-                                        const DevOut &O, unsigned &status_bits)
+                                        const DevOut &O, unsigned &status_bits, const uint8_t *clr = nullptr)
 {
     if (o.status != 0) return 0;
     float Xf = p_f(o.X), Yf = p_f(o.Y);
@@ -727,6 +727,15 @@ __device__ __forceinline__ int hit_test(const RayOut<T, P> &o, int64_t seg_local
     float dzmax = fmaxf(fabsf(Tl.zmax - A.h_obs), fabsf(Tl.zmin - A.h_obs));
     float rs = (Tl.Rmax + dzmax * sqrtf(fmaxf(0.0f, 1.0f - acz * acz))) * rcp_approx(fmaxf(acz, 1e-6f)) + 1e-3f;
     if (Xf + rs < Tl.xmin || Xf - rs > Tl.xmax || Yf + rs < Tl.ymin || Yf - rs > Tl.ymax) return 0;
+    if (clr) {
+        // every centre the line can pass within R of lies within rs of the
+        // crossing point; the clearance map bounds the nearest centre from below
+        float fx = (Xf - Tl.cx0) * Tl.inv_cgs, fy = (Yf - Tl.cy0) * Tl.inv_cgs;
+        if (fx >= 0.0f && fy >= 0.0f && fx < (float)Tl.cnx && fy < (float)Tl.cny) {
+            int ci = (int)fy * Tl.cnx + (int)fx;
+            if (rs < (float)clr[ci] * kClrQuantum) return 0;
+        }
+    }
     int ix0 = max(0, (int)floorf((Xf - rs - Tl.gx0) * Tl.inv_gs));
     int ix1 = min(Tl.nx - 1, (int)floorf((Xf + rs - Tl.gx0) * Tl.inv_gs));
     int iy0 = max(0, (int)floorf((Yf - rs - Tl.gy0) * Tl.inv_gs));

@@ -22,7 +22,8 @@ enum SegField {
     F_SIN, F_KAP, F_L, F_IBC, F_WC, F_WF, F_NC, F_NF, F_SHOWER, F_SEGI, F_INCL, F_COUNT
 };
 
-int fused_smem_bytes(int block) { return (block / 32) * F_COUNT * 32 * (int)sizeof(float); }
+static int seg_smem_bytes(int block) { return (block / 32) * F_COUNT * 32 * (int)sizeof(float); }
+int fused_smem_bytes(int block, const DevTel &T) { return seg_smem_bytes(block) + (T.clr ? T.clr_bytes : 0); }
 
 __device__ __forceinline__ void put_df(float *S, int fh, int fl, int l, df v)
 {
@@ -49,13 +50,22 @@ __device__ __forceinline__ uint32_t warp_sort_u32(uint32_t key, int lane)
 }
 
 template <class P, bool SPH, bool REFR, bool NOALLOC = false>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, 3)
 k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid_constant__ DevAtm A,
               const __grid_constant__ DevTel Tl, const __grid_constant__ DevPar Pp, const __grid_constant__ DevOut O)
 {
     extern __shared__ float smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float *S = smem + warp * (F_COUNT * 32);
+    // the clearance map, staged once per CTA behind the segment records
+    const uint8_t *clr = nullptr;
+    if (Tl.clr) {
+        uint4 *dst = reinterpret_cast<uint4 *>(smem + (blockDim.x >> 5) * (F_COUNT * 32));
+        const uint4 *src = reinterpret_cast<const uint4 *>(Tl.clr);
+        for (int i = threadIdx.x; i < (Tl.clr_bytes >> 4); i += blockDim.x) dst[i] = __ldg(src + i);
+        __syncthreads();
+        clr = reinterpret_cast<const uint8_t *>(dst);
+    }
     uint32_t c_rays = 0, c_esc = 0, c_under = 0, c_turn = 0, c_reach = 0, c_hits = 0, c_guard = 0, c_cells = 0;
     unsigned status_bits = 0;
     for (;;) {
@@ -168,7 +178,7 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
                 qd.w_c = q.w_c; qd.w_f = q.w_f; qd.n_c = q.n_c; qd.n_f = q.n_f; qd.shower = q.shower;
                 RayOut<float, double> o;
                 trace_ray<float, double, true, SPH, REFR>(qd, seg_global, k, active, A, Pp, o);
-                nh = hit_test<float, double, true, NOALLOC>(o, seg_local, seg_global, k, q.shower, A, Tl, Pp, O, status_bits);
+                nh = hit_test<float, double, true, NOALLOC>(o, seg_local, seg_global, k, q.shower, A, Tl, Pp, O, status_bits, clr);
                 if (active) {
                     ++c_rays;
                     c_esc += o.status == 1; c_under += o.status == 2; c_turn += o.status == 3;
@@ -178,7 +188,7 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
             } else {
                 RayOut<float, df> o;
                 trace_ray<float, df, true, SPH, REFR>(q, seg_global, k, active, A, Pp, o);
-                nh = hit_test<float, df, true, NOALLOC>(o, seg_local, seg_global, k, q.shower, A, Tl, Pp, O, status_bits);
+                nh = hit_test<float, df, true, NOALLOC>(o, seg_local, seg_global, k, q.shower, A, Tl, Pp, O, status_bits, clr);
                 if (active) {
                     ++c_rays;
                     c_esc += o.status == 1; c_under += o.status == 2; c_turn += o.status == 3;
@@ -247,7 +257,7 @@ template <class P>
 static void launch_fused_p(const clight_segment *segs, int64_t n_segs, const DevAtm &A, const DevTel &T,
                            const DevPar &Pp, const DevOut &O, int grid, int block, cudaStream_t s)
 {
-    int smem = fused_smem_bytes(block);     // <= 34 KB for block <= 256: no opt-in needed
+    int smem = fused_smem_bytes(block, T);  // <= 46 KB for block <= 256: no opt-in needed
     if (A.spherical && A.refraction)
         k_trace_fused<P, true, true><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
     else if (A.spherical)
@@ -318,7 +328,7 @@ template <class P, bool SPH, bool REFR>
 static void launch_noalloc(const clight_segment *segs, int64_t n_segs, const DevAtm &A, const DevTel &T,
                            const DevPar &Pp, const DevOut &O, int grid, int block, cudaStream_t s)
 {
-    k_trace_fused<P, SPH, REFR, true><<<grid, block, fused_smem_bytes(block), s>>>(segs, n_segs, A, T, Pp, O);
+    k_trace_fused<P, SPH, REFR, true><<<grid, block, fused_smem_bytes(block, T), s>>>(segs, n_segs, A, T, Pp, O);
 }
 
 }  // namespace clight
