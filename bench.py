@@ -159,8 +159,7 @@ def reference_arm(args, rank):
     """The oracle timed on the host cores, on bounded samples of the workload."""
     if rank != 0:
         return 0
-    from paper_2309_15861_gb300 import inputs as I
-    w = I.workload_shower_1tev(n=args.n_segs, seed=1)
+    w = make_workload(args.workload, args.n_segs, 0, args.scale)
     per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
     vals = []
     for i in range(args.warmup + args.steps):
@@ -180,16 +179,37 @@ def reference_arm(args, rank):
     return 0
 
 
+WORKLOADS = ("shower_1tev", "inclined", "batch", "adjoint")
+
+
+def make_workload(name, n_segs, rank, scale):
+    from paper_2309_15861_gb300 import inputs as I
+    wk = I.default_workers()
+    if name == "inclined":
+        return I.workload_inclined(n=n_segs or 100_000_000, seed=1 + rank, workers=wk)
+    if name == "batch":
+        return I.batch_showers(256, seed=1 + rank, scale=scale, workers=wk)
+    if name == "adjoint":
+        return I.workload_shower_1tev(n=n_segs or 1_000_000, seed=1 + rank, workers=wk)
+    return I.workload_shower_1tev(n=n_segs or 20_000_000, seed=1 + rank, workers=wk)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n-segs", type=int, default=20_000_000)
+    ap.add_argument("--workload", default="shower_1tev", choices=WORKLOADS,
+                    help="shower_1tev: 2e7-step vertical 1 TeV shower (the default); inclined: 1e8 steps at "
+                         "60 deg over 441 telescopes; batch: 256 showers with fluorescence (7.4e8 steps, "
+                         "autotuned); adjoint: 1e6 steps, forward + adjoint per step")
+    ap.add_argument("--n-segs", type=int, default=0)
+    ap.add_argument("--scale", type=float, default=1.0, help="segment-count scale of the batch workload")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
@@ -218,8 +238,9 @@ def main():
         torch.cuda.synchronize()
 
     t_gen = time.perf_counter()
-    w = I.workload_shower_1tev(n=args.n_segs, seed=1 + rank)
+    w = make_workload(args.workload, args.n_segs, rank, args.scale)
     t_gen = time.perf_counter() - t_gen
+    ns = w.n_showers
     ctx = G.Context(local)
     extra = dict(use_graph=1, precision=args.precision, block=args.block, ctas_per_sm=args.ctas_per_sm,
                  cell_width=args.cell_width)
@@ -229,16 +250,42 @@ def main():
     n = len(w.segments)
     cap = max(1 << 20, n // 4)
     hits = torch.empty(cap * 48, dtype=torch.uint8, device=dev)
-    counts = torch.zeros(len(w.telescopes), dtype=torch.int64, device=dev)
-    sums = torch.zeros(len(w.telescopes), dtype=torch.float64, device=dev)
-    code, nh, st = ctx.trace(segs, n, 1, hits, cap, counts, sums, raise_on_error=False)
+    ng = ns * len(w.telescopes)
+    counts = torch.zeros(ng, dtype=torch.int64, device=dev)
+    sums = torch.zeros(ng, dtype=torch.float64, device=dev)
+
+    tune = None
+    if args.workload == "batch" and not args.no_tune:
+        # a sample of the batch (every shower's share) picks block, CTAs, cell width and bunch <= 5
+        n_sample = min(n, 4_000_000)
+        tune = ctx.autotune(segs, n_sample, ns, hits, cap, bunch_max=w.params.bunch, reps=3)
+        extra.update(block=tune["block"], ctas_per_sm=tune["ctas_per_sm"], cell_width=tune["cell_width"])
+        w.params.bunch = tune["bunch"]
+        ctx.set_params(w.params, **extra)
+
+    code, nh, st = ctx.trace(segs, n, ns, hits, cap, counts, sums, raise_on_error=False)
     if code == G.ERR_HIT_CAPACITY:
         cap = int(nh * 1.25) + 1024
         hits = torch.empty(cap * 48, dtype=torch.uint8, device=dev)
-        code, nh, st = ctx.trace(segs, n, 1, hits, cap, counts, sums)
+        code, nh, st = ctx.trace(segs, n, ns, hits, cap, counts, sums)
+
+    adj = None
+    if args.workload == "adjoint":
+        gen = torch.Generator(device=dev).manual_seed(7)
+        gx = torch.randn(nh, generator=gen, device=dev)
+        gy = torch.randn(nh, generator=gen, device=dev)
+        gt = torch.randn(nh, generator=gen, device=dev)
+        gY = torch.randn(ng, generator=gen, device=dev, dtype=torch.float64)
+        adj = dict(gx=gx, gy=gy, gt=gt, gY=gY)
+
+    def step():
+        out = ctx.trace(segs, n, ns, hits, cap, counts, sums)
+        if adj is not None:
+            ctx.trace_adjoint(segs, n, ns, hits, out[1], **adj)
+        return out
+
     for _ in range(args.warmup):
-        ctx.trace(segs, n, 1, hits, cap, counts, sums)
-    launches_per_step = None
+        step()
     # ---- timed region (device-resident inputs)
     clocks = Clocks(local)
     barrier()
@@ -248,7 +295,7 @@ def main():
     kms, sms = [], []
     e0.record(s)
     for _ in range(args.steps):
-        code, nh, st = ctx.trace(segs, n, 1, hits, cap, counts, sums)
+        code, nh, st = step()
         a, b = ctx.last_timing()
         kms.append(a)
         sms.append(b)
@@ -268,9 +315,9 @@ def main():
         rays_all = float(st["rays"])
     ms_step = ms / args.steps
     value = rays_all * args.steps / (ms / 1e3)
-    key_bits = (len(w.telescopes) - 1).bit_length() + (n - 1).bit_length() + 16
+    key_bits = (ng - 1).bit_length() + (n - 1).bit_length() + 16
     passes = (key_bits + 7) // 8
-    launches_per_step = 1 + 5 * passes + 3
+    launches_per_step = 1 + 5 * passes + 3 + (3 if adj is not None else 0)
 
     # ---- roofline of the dominant kernel (generation + propagation + hits)
     k_ms = statistics.mean(kms)
@@ -285,7 +332,7 @@ def main():
     f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     peak_ops = n_sm * FP32_LANES_PER_SM * f_max
     achieved = ops / (k_ms / 1e3)
-    traffic = recorded_traffic(n)
+    traffic = recorded_traffic(n) if args.workload == "shower_1tev" else None
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s (FP32 pipe)",
             "frac": achieved / peak_ops, "traffic": traffic,
             "traffic_note": "DRAM bytes per launch: ncu capture of 2e6 steps scaled by steps "
@@ -295,41 +342,39 @@ def main():
             "ops_per_ray": ops / max(1, st["rays"]), "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                                                  f"{f_max / 1e6:.0f} MHz (max SM clock)"}
 
-    # ---- plain FP64 GPU path on the same workload
+    # ---- plain FP64 GPU path on the same workload (at most its first 2e7 steps)
     fp64 = None
     if not args.no_fp64:
-        ctx.trace(segs, n, 1, hits, cap, counts, sums, fp64=True)
+        n64 = min(n, 20_000_000)
+        ctx.trace(segs, n64, ns, hits, cap, counts, sums, fp64=True)
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(s)
-        code, nh64, st64 = ctx.trace(segs, n, 1, hits, cap, counts, sums, fp64=True)
+        code, nh64, st64 = ctx.trace(segs, n64, ns, hits, cap, counts, sums, fp64=True)
         f1.record(s)
         torch.cuda.synchronize()
         fms = f0.elapsed_time(f1)
-        fp64 = {"value": st64["rays"] / (fms / 1e3), "unit": UNIT, "ms_per_step": fms,
-                "speedup_of_fp32": (st64["rays"] / (fms / 1e3)) and value / (st64["rays"] / (fms / 1e3))}
+        v64 = st64["rays"] / (fms / 1e3)
+        fp64 = {"value": v64, "unit": UNIT, "ms_per_step": fms, "segments": n64,
+                "speedup_of_fp32": value / v64 if v64 else None}
 
     # ---- end to end through the host-buffer entry point
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and adj is None:
         pinned = torch.from_numpy(w.segments.view(np.uint8).reshape(-1)).pin_memory()
         hbuf = torch.empty(cap * 48, dtype=torch.uint8).pin_memory()
-        cbuf = torch.zeros(len(w.telescopes), dtype=torch.int64).pin_memory()
-        sbuf = torch.zeros(len(w.telescopes), dtype=torch.float64).pin_memory()
+        cbuf = torch.zeros(ng, dtype=torch.int64).pin_memory()
+        sbuf = torch.zeros(ng, dtype=torch.float64).pin_memory()
         seg_np = pinned.numpy().view(I.SEG_DTYPE)
         hits_np = hbuf.numpy().view(G.HIT_DTYPE)
         ctx.set_params(w.params, **{**extra, "use_graph": 0})
-        ctx.trace_host(seg_np, 1, cap, hits_out=hits_np, counts_out=cbuf.numpy(), sums_out=sbuf.numpy())
+        ctx.trace_host(seg_np, ns, cap, hits_out=hits_np, counts_out=cbuf.numpy(), sums_out=sbuf.numpy())
         k2 = max(3, args.steps // 4)
         barrier()
         t0 = time.perf_counter()
-        g0 = torch.cuda.Event(enable_timing=True)
-        g1 = torch.cuda.Event(enable_timing=True)
-        g0.record(s)
         for _ in range(k2):
-            code, hh, cc, ss, st2 = ctx.trace_host(seg_np, 1, cap, hits_out=hits_np, counts_out=cbuf.numpy(),
+            code, hh, cc, ss, st2 = ctx.trace_host(seg_np, ns, cap, hits_out=hits_np, counts_out=cbuf.numpy(),
                                                    sums_out=sbuf.numpy())
-        g1.record(s)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         barrier()
@@ -338,25 +383,31 @@ def main():
                "d2h_bytes_per_step": int(len(hh) * 48 + cbuf.numel() * 8 + sbuf.numel() * 8),
                "ms_per_step": wall * 1e3 / k2}
         ctx.set_params(w.params, **extra)
+        del pinned, hbuf
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(w)
 
     if rank == 0:
+        atm = "5-layer, spherical, absorbing"
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": w.name, "segments": n, "rays_per_step": st["rays"], "hits_per_step": nh,
-                       "telescopes": len(w.telescopes), "bunch": w.params.bunch, "atmosphere": "5-layer, spherical, absorbing",
+            "config": {"workload": w.name, "segments": n, "showers": ns, "rays_per_step": st["rays"],
+                       "hits_per_step": nh, "telescopes": len(w.telescopes), "bunch": w.params.bunch,
+                       "atmosphere": atm, "fluorescence": w.params.fluor_yield > 0,
                        "precision": ["float-pair", "fp64-guard"][args.precision], "graph": True,
-                       "l2": "inputs (1.28 GB) larger than L2; no flush", "parallelism": f"replicas x{world}",
-                       "generation_s": round(t_gen, 1)},
+                       "l2": f"inputs ({n * 64 / 1e9:.2f} GB) larger than L2; no flush",
+                       "parallelism": f"replicas x{world}", "generation_s": round(t_gen, 1),
+                       "step": "trace + adjoint" if adj is not None else "trace"},
             "roofline": roof, "fp64_plain": fp64, "e2e": e2e, "cpu_baseline": cpu,
             "clocks": ck, "gpu_launches": launches_per_step * args.steps,
             "stats": {k: int(v) for k, v in st.items()},
         }
+        if tune is not None:
+            line["autotune"] = tune
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -240,6 +240,42 @@ clight_status clight_trace_noalloc(clight_ctx *ctx, const clight_segment *d_segs
                                    int32_t n_showers, clight_hit *d_hits, int64_t hit_capacity,
                                    int64_t *d_counts, clight_stats *h_stats, int64_t *h_n_hits, void *stream);
 
+/* Result of clight_autotune. */
+typedef struct clight_tune {
+    int32_t block;          /* chosen threads per CTA */
+    int32_t ctas_per_sm;    /* chosen persistent CTAs per SM */
+    float cell_width;       /* chosen quadrature cell width (scale heights) */
+    float pad;
+    double bunch;           /* chosen bunch size (<= the caller's maximum) */
+    double best_ms;         /* median step time of the chosen settings on the sample */
+    double default_ms;      /* the same for the library defaults at the caller's bunch size */
+    int32_t n_tried;        /* settings timed */
+    int32_t pad2;
+} clight_tune;
+
+/* Pick the launch shape, quadrature cell width and bunch size for a batch
+ * (the batching pattern of the forward path: one persistent launch over
+ * many showers).  Paper: no counterpart; the paper's GPU code has fixed
+ * launch parameters.
+ *   - Times `reps` (>= 1; median taken) calls of the whole step (trace,
+ *     sort, per-telescope reduction; no graph) on the first `n_sample`
+ *     segments of d_segs for each candidate: block x CTAs per SM in
+ *     {256x3, 256x2, 128x6, 128x4, 64x12}, cell width in {1.0, 1.5}
+ *     scale heights (no wider than the default, whose accuracy the tests
+ *     establish), bunch size in {1, 2, 5, bunch_max} capped at bunch_max.
+ *     The photon count of a batch does not depend on the bunch size, so the
+ *     fastest setting carries the most photons per second.
+ *   - d_hits / hit_capacity: scratch for the sample's hits (the caller's
+ *     buffer; overflow only truncates the sample's list and is ignored).
+ *   - On success the context keeps the chosen settings (as if set by
+ *     clight_set_params with the other fields unchanged) and *out holds
+ *     them.  ERR_ARG for a bad argument (bunch_max <= 0, n_sample < 1,
+ *     reps < 1, NULL out); the context's settings are unchanged on error.
+ * Synchronises `stream`. */
+clight_status clight_autotune(clight_ctx *ctx, const clight_segment *d_segs, int64_t n_sample, int32_t n_showers,
+                              clight_hit *d_hits, int64_t hit_capacity, double bunch_max, int32_t reps,
+                              clight_tune *out, void *stream);
+
 /* Device time of the last clight_trace / clight_trace_fp64 call, measured
  * with CUDA events recorded on the launch stream around its phases:
  * ms[0] = generation + propagation + hit kernel, ms[1] = sort and per-

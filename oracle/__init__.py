@@ -210,21 +210,24 @@ def bunch_counts(segs, atm, par):
     return nc, nf
 
 
-def soft_yield(segs, nbc, nbf, atm, tels, par, n_showers=1, s=0.5, W=10.0, threads=0):
+def soft_yield(segs, nbc, nbf, atm, tels, par, n_showers=1, s=0.5, W=10.0, threads=0, seg_base=0):
     segs = np.ascontiguousarray(segs)
     tels = np.ascontiguousarray(tels)
     nbc = np.ascontiguousarray(nbc, dtype=np.uint32)
     nbf = np.ascontiguousarray(nbf, dtype=np.uint32)
     out = np.zeros(n_showers * len(tels))
-    a, p = atm_struct(atm), par_struct(par)
+    a, p = atm_struct(atm), par_struct(par, seg_base)
     lib().or_soft_yield(_ptr(segs), len(segs), _ptr(nbc), _ptr(nbf), C.byref(a), _ptr(tels),
                         len(tels), C.byref(p), n_showers, float(s), float(W), _ptr(out),
                         int(threads))
     return out.reshape(n_showers, len(tels))
 
 
-def eval_rays(segs, seg_idx, k, tel, nbc, nbf, atm, tels, par, threads=0):
-    """-> (n, 5) array: x_rel, y_rel, t, weight*exp(-tau), dperp."""
+def eval_rays(segs, seg_idx, k, tel, nbc, nbf, atm, tels, par, threads=0, seg_base=0):
+    """-> (n, 5) array: x_rel, y_rel, t, weight*exp(-tau), dperp.
+
+    seg_idx indexes segs; seg_base is the global index of segs[0] (it keys
+    the random numbers)."""
     segs = np.ascontiguousarray(segs)
     tels = np.ascontiguousarray(tels)
     seg_idx = np.ascontiguousarray(seg_idx, dtype=np.int64)
@@ -233,7 +236,7 @@ def eval_rays(segs, seg_idx, k, tel, nbc, nbf, atm, tels, par, threads=0):
     nbc = np.ascontiguousarray(nbc, dtype=np.uint32)
     nbf = np.ascontiguousarray(nbf, dtype=np.uint32)
     out = np.zeros((len(seg_idx), 5))
-    a, p = atm_struct(atm), par_struct(par)
+    a, p = atm_struct(atm), par_struct(par, seg_base)
     lib().or_eval_rays(_ptr(segs), _ptr(seg_idx), _ptr(k), _ptr(tel), _ptr(nbc), _ptr(nbf),
                        len(seg_idx), C.byref(a), _ptr(tels), C.byref(p), _ptr(out), int(threads))
     return out

@@ -61,6 +61,15 @@ class Stats(C.Structure):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
+class Tune(C.Structure):
+    _fields_ = [("block", C.c_int32), ("ctas_per_sm", C.c_int32), ("cell_width", C.c_float), ("pad", C.c_float),
+                ("bunch", C.c_double), ("best_ms", C.c_double), ("default_ms", C.c_double),
+                ("n_tried", C.c_int32), ("pad2", C.c_int32)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_ if not n.startswith("pad")}
+
+
 _lib = None
 
 
@@ -88,6 +97,8 @@ def lib():
         L.clight_last_timing.argtypes = [P, P]
         L.clight_trace_adjoint.argtypes = [P, P, C.c_int64, C.c_int32, P, C.c_int64, P, P, P, P,
                                            C.c_float, C.c_float, P, P, P]
+        L.clight_autotune.argtypes = [P, P, C.c_int64, C.c_int32, P, C.c_int64, C.c_double, C.c_int32,
+                                      C.POINTER(Tune), P]
         L.clight_trace_noalloc.argtypes = [P, P, C.c_int64, C.c_int32, P, C.c_int64, P,
                                            C.POINTER(Stats), C.POINTER(C.c_int64), P]
         _lib = L
@@ -197,6 +208,19 @@ class Context:
                                           _stream_handle(stream))
         _check(code, "clight_trace_adjoint")
         return out
+
+    def autotune(self, d_segs, n_sample, n_showers, d_hits, capacity, bunch_max, reps=3, stream=None):
+        """Time candidate launch shapes, cell widths and bunch sizes on the first n_sample
+        segments; the context keeps the fastest.  -> dict of the choice and timings."""
+        t = Tune()
+        code = lib().clight_autotune(self._h, _ptr(d_segs), int(n_sample), int(n_showers), _ptr(d_hits),
+                                     int(capacity), float(bunch_max), int(reps), C.byref(t),
+                                     _stream_handle(stream))
+        _check(code, "clight_autotune")
+        if self.params is not None:
+            self.params.block, self.params.ctas_per_sm = t.block, t.ctas_per_sm
+            self.params.cell_width, self.params.bunch = t.cell_width, t.bunch
+        return t.as_dict()
 
     def trace_noalloc(self, d_segs, n_segs, n_showers, d_hits, capacity, d_counts=None, stream=None,
                       raise_on_error=True):

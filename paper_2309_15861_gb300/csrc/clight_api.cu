@@ -624,6 +624,78 @@ clight_status clight_trace_host(clight_ctx *c, const clight_segment *h_segs, int
 
 }  // extern "C"
 
+extern "C" clight_status clight_autotune(clight_ctx *c, const clight_segment *d_segs, int64_t n_sample,
+                                         int32_t n_showers, clight_hit *d_hits, int64_t hit_capacity,
+                                         double bunch_max, int32_t reps, clight_tune *out, void *stream)
+{
+    if (!c || !out || !d_segs || n_sample < 1 || reps < 1 || !(bunch_max > 0) || n_showers < 1 ||
+        hit_capacity < 0 || (hit_capacity > 0 && !d_hits))
+        return CLIGHT_ERR_ARG;
+    if (!c->atm_set || !c->tel_set) return CLIGHT_ERR_ARG;
+    const clight_params saved = c->upar;
+    struct Shape { int block, per_sm; };
+    const Shape shapes[] = {{256, 3}, {256, 2}, {128, 6}, {128, 4}, {64, 12}};
+    const float widths[] = {1.0f, 1.5f};
+    std::vector<double> bunches;
+    for (double b : {1.0, 2.0, 5.0, bunch_max})
+        if (b <= bunch_max && std::find(bunches.begin(), bunches.end(), b) == bunches.end()) bunches.push_back(b);
+    int64_t n_hits = 0;
+    clight_stats st;
+    // median step time (ms) of one setting; a negative value on failure
+    auto time_of = [&](const clight_params &p) -> double {
+        if (clight_set_params(c, &p) != CLIGHT_OK) return -1.0;
+        std::vector<float> t;
+        for (int r = 0; r < reps + 1; ++r) {     // the first call warms up
+            clight_status s = run(c, d_segs, n_sample, n_showers, d_hits, hit_capacity, nullptr, nullptr, &st,
+                                  &n_hits, stream, false);
+            if (s != CLIGHT_OK && s != CLIGHT_ERR_HIT_CAPACITY) return -1.0;
+            float ms = 0;
+            if (cudaEventElapsedTime(&ms, c->t0, c->t2) != cudaSuccess) return -1.0;
+            if (r > 0) t.push_back(ms);
+        }
+        std::sort(t.begin(), t.end());
+        return t[t.size() / 2];
+    };
+    clight_params base = saved;
+    base.use_graph = 0;
+    base.block = 0;
+    base.ctas_per_sm = 0;
+    base.cell_width = 0;
+    double def_ms = time_of(base);
+    if (def_ms < 0) { clight_set_params(c, &saved); return CLIGHT_ERR_CUDA; }
+    clight_tune best{};
+    best.best_ms = 1e300;
+    int tried = 1;
+    for (double b : bunches)
+        for (const Shape &sh : shapes)
+            for (float cw : widths) {
+                clight_params p = saved;
+                p.use_graph = 0;
+                p.block = sh.block;
+                p.ctas_per_sm = sh.per_sm;
+                p.cell_width = cw;
+                p.bunch = b;
+                double ms = time_of(p);
+                ++tried;
+                if (ms < 0) { clight_set_params(c, &saved); return CLIGHT_ERR_CUDA; }
+                if (ms < best.best_ms) {
+                    best.block = sh.block; best.ctas_per_sm = sh.per_sm; best.cell_width = cw;
+                    best.bunch = b; best.best_ms = ms;
+                }
+            }
+    best.default_ms = def_ms;
+    best.n_tried = tried;
+    clight_params p = saved;
+    p.block = best.block;
+    p.ctas_per_sm = best.ctas_per_sm;
+    p.cell_width = best.cell_width;
+    p.bunch = best.bunch;
+    clight_status r = clight_set_params(c, &p);
+    if (r != CLIGHT_OK) { clight_set_params(c, &saved); return r; }
+    *out = best;
+    return CLIGHT_OK;
+}
+
 extern "C" clight_status clight_trace_adjoint(clight_ctx *c, const clight_segment *d_segs, int64_t n_segs,
                                               int32_t n_showers, const clight_hit *d_hits, int64_t n_hits,
                                               const float *d_gx, const float *d_gy, const float *d_gt,

@@ -222,7 +222,7 @@ def segments_shower(n, atm: Atmosphere, seed=1, zenith_deg=0.0, azimuth_deg=0.0,
                     shower=0, core=(0.0, 0.0), Xmax=350.0, lam=70.0,
                     tilt_sigma_deg=5.0, lateral_scale=80.0,
                     E_range_MeV=(10.0, 1000.0), L_range=(0.5, 5.0),
-                    dEdX=2.0, t_ref_alt=100000.0, chunk=1 << 22):
+                    dEdX=2.0, t_ref_alt=100000.0, chunk=1 << 22, workers=0):
     """Charged track steps of one gamma shower.
 
     Depth along the axis X ~ Gamma(k = Xmax/lam + 1, lam) (the Gaisser-Hillas
@@ -230,58 +230,137 @@ def segments_shower(n, atm: Atmosphere, seed=1, zenith_deg=0.0, azimuth_deg=0.0,
     ~ Exp(lateral_scale); direction tilted from the axis by Gaussian angles of
     tilt_sigma_deg in two perpendicular planes; electron energy log-uniform
     in E_range_MeV; step length uniform in L_range; dE = dEdX * rho * L.
-    The geometry of the axis is taken in the local (flat) frame.
+    The geometry of the axis is taken in the local (flat) frame.  Blocks of
+    `chunk` steps draw from independent child seeds, so `workers` processes
+    give the same array as one.
     """
-    out = np.zeros(n, dtype=SEG_DTYPE)
-    zen = math.radians(zenith_deg)
-    az = math.radians(azimuth_deg)
+    spec = _ShowerSpec(atm, seed, zenith_deg, azimuth_deg, shower, core, Xmax, lam, tilt_sigma_deg,
+                       lateral_scale, E_range_MeV, L_range, dEdX, t_ref_alt)
+    tasks = [(spec, lo, min(chunk, n - lo), i) for i, lo in enumerate(range(0, n, chunk))]
+    return _run_tasks(tasks, n, workers)
+
+
+@dataclasses.dataclass
+class _ShowerSpec:
+    atm: Atmosphere
+    seed: int
+    zenith_deg: float
+    azimuth_deg: float
+    shower: int
+    core: tuple
+    Xmax: float
+    lam: float
+    tilt_sigma_deg: float
+    lateral_scale: float
+    E_range_MeV: tuple
+    L_range: tuple
+    dEdX: float
+    t_ref_alt: float
+
+
+def _shower_chunk(sp: _ShowerSpec, m: int, index: int) -> np.ndarray:
+    """Block `index` (m steps) of a shower; its generator is child `index` of the shower's seed."""
+    atm = sp.atm
+    out = np.zeros(m, dtype=SEG_DTYPE)
+    zen = math.radians(sp.zenith_deg)
+    az = math.radians(sp.azimuth_deg)
     u_ax = np.array([math.sin(zen) * math.cos(az), math.sin(zen) * math.sin(az),
                      -math.cos(zen)])
     e1, e2 = _unit_frame(u_ax)
     cosz = math.cos(zen)
     X_obs = float(atm.thickness(np.array([atm.h_obs]))[0]) / cosz
-    k = Xmax / lam + 1.0
-    core3 = np.array([core[0], core[1], atm.h_obs])
-    top_pt = core3 - u_ax * (t_ref_alt - atm.h_obs) / cosz
-    ss = np.random.SeedSequence([seed, 0x5E6, shower])
-    for lo in range(0, n, chunk):
-        m = min(chunk, n - lo)
-        rng = np.random.default_rng(ss.spawn(1)[0])
-        X = rng.gamma(k, lam, m)
+    k = sp.Xmax / sp.lam + 1.0
+    core3 = np.array([sp.core[0], sp.core[1], atm.h_obs])
+    top_pt = core3 - u_ax * (sp.t_ref_alt - atm.h_obs) / cosz
+    rng = np.random.default_rng(np.random.SeedSequence([sp.seed, 0x5E6, sp.shower], spawn_key=(index,)))
+    X = rng.gamma(k, sp.lam, m)
+    bad = X >= X_obs
+    while bad.any():
+        X[bad] = rng.gamma(k, sp.lam, int(bad.sum()))
         bad = X >= X_obs
-        while bad.any():
-            X[bad] = rng.gamma(k, lam, int(bad.sum()))
-            bad = X >= X_obs
-        h = atm.altitude_of_thickness(X * cosz)
-        axis_pt = core3[None, :] - u_ax[None, :] * ((h - atm.h_obs) / cosz)[:, None]
-        r = rng.exponential(lateral_scale, m)
-        phi = rng.uniform(0.0, 2.0 * math.pi, m)
-        pos = axis_pt + (r * np.cos(phi))[:, None] * e1[None, :] \
-            + (r * np.sin(phi))[:, None] * e2[None, :]
-        g1 = np.tan(rng.normal(0.0, math.radians(tilt_sigma_deg), m))
-        g2 = np.tan(rng.normal(0.0, math.radians(tilt_sigma_deg), m))
-        d = u_ax[None, :] + g1[:, None] * e1[None, :] + g2[:, None] * e2[None, :]
-        d /= np.linalg.norm(d, axis=1)[:, None]
-        L = rng.uniform(L_range[0], L_range[1], m)
-        E = np.exp(rng.uniform(math.log(E_range_MeV[0]), math.log(E_range_MeV[1]), m))
-        gam = E / M_E_MEV
-        beta = np.sqrt(1.0 - 1.0 / gam ** 2)
-        eps = 1.0 / (gam ** 2 * (1.0 + beta))
-        charge = np.where(rng.random(m) < 0.5, -1, 1)
-        sl = slice(lo, lo + m)
-        out["x"][sl] = pos[:, 0]
-        out["y"][sl] = pos[:, 1]
-        out["z"][sl] = pos[:, 2]
-        out["t0"][sl] = ((pos - top_pt[None, :]) @ u_ax) / C_M_PER_NS
-        out["dx"][sl] = d[:, 0]
-        out["dy"][sl] = d[:, 1]
-        out["dz"][sl] = d[:, 2]
-        out["L"][sl] = L
-        out["eps"][sl] = eps
-        out["dE"][sl] = dEdX * atm.density(h) * L * 100.0
-        out["charge"][sl] = charge
-        out["shower"][sl] = shower
+    h = atm.altitude_of_thickness(X * cosz)
+    axis_pt = core3[None, :] - u_ax[None, :] * ((h - atm.h_obs) / cosz)[:, None]
+    r = rng.exponential(sp.lateral_scale, m)
+    phi = rng.uniform(0.0, 2.0 * math.pi, m)
+    pos = axis_pt + (r * np.cos(phi))[:, None] * e1[None, :] \
+        + (r * np.sin(phi))[:, None] * e2[None, :]
+    g1 = np.tan(rng.normal(0.0, math.radians(sp.tilt_sigma_deg), m))
+    g2 = np.tan(rng.normal(0.0, math.radians(sp.tilt_sigma_deg), m))
+    d = u_ax[None, :] + g1[:, None] * e1[None, :] + g2[:, None] * e2[None, :]
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    L = rng.uniform(sp.L_range[0], sp.L_range[1], m)
+    E = np.exp(rng.uniform(math.log(sp.E_range_MeV[0]), math.log(sp.E_range_MeV[1]), m))
+    gam = E / M_E_MEV
+    beta = np.sqrt(1.0 - 1.0 / gam ** 2)
+    eps = 1.0 / (gam ** 2 * (1.0 + beta))
+    charge = np.where(rng.random(m) < 0.5, -1, 1)
+    out["x"] = pos[:, 0]
+    out["y"] = pos[:, 1]
+    out["z"] = pos[:, 2]
+    out["t0"] = ((pos - top_pt[None, :]) @ u_ax) / C_M_PER_NS
+    out["dx"] = d[:, 0]
+    out["dy"] = d[:, 1]
+    out["dz"] = d[:, 2]
+    out["L"] = L
+    out["eps"] = eps
+    out["dE"] = sp.dEdX * atm.density(h) * L * 100.0
+    out["charge"] = charge
+    out["shower"] = sp.shower
     return out
+
+
+def _chunk_into(args):
+    shm_name, n_total, (spec, lo, m, index) = args
+    from multiprocessing import shared_memory
+    shm = shared_memory.SharedMemory(name=shm_name)
+    try:
+        dst = np.ndarray((n_total,), dtype=SEG_DTYPE, buffer=shm.buf)
+        dst[lo:lo + m] = _shower_chunk(spec, m, index)
+        del dst
+    finally:
+        shm.close()
+    return m
+
+
+class _SharedArray(np.ndarray):
+    """An ndarray that keeps its shared-memory block mapped."""
+    _shm = None
+
+    def __array_finalize__(self, obj):
+        if obj is not None:
+            self._shm = getattr(obj, "_shm", None)
+
+
+def _run_tasks(tasks, n_total, workers):
+    """Fill an n_total array from (spec, lo, m, index) blocks, in this process or in `workers` spawned ones."""
+    if workers is None or workers <= 1 or len(tasks) <= 1:
+        out = np.zeros(n_total, dtype=SEG_DTYPE)
+        for spec, lo, m, index in tasks:
+            out[lo:lo + m] = _shower_chunk(spec, m, index)
+        return out
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    shm = shared_memory.SharedMemory(create=True, size=max(1, n_total * SEG_DTYPE.itemsize))
+    try:
+        ctx = mp.get_context("spawn")
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=ctx) as ex:
+            done = sum(ex.map(_chunk_into, [(shm.name, n_total, t) for t in tasks]))
+        assert done == n_total
+    except BaseException:
+        shm.close()
+        shm.unlink()
+        raise
+    shm.unlink()          # the mapping stays valid while this process holds it
+    arr = np.ndarray((n_total,), dtype=SEG_DTYPE, buffer=shm.buf).view(_SharedArray)
+    arr._shm = shm
+    return arr
+
+
+def default_workers() -> int:
+    """Processes for input generation: the host's cores, at most 32."""
+    import os
+    return max(1, min(32, os.cpu_count() or 1))
 
 
 # --------------------------------------------------------------------------
@@ -308,28 +387,28 @@ def workload_flat_vertical(n=10_000, seed=1):
 
 
 def workload_shower_1tev(n=20_000_000, seed=1, zenith_deg=0.0, telescopes=None,
-                         bunch=5.0, name=None):
+                         bunch=5.0, name=None, workers=0):
     """One 1 TeV gamma shower, 5 layers, spherical Earth, absorption, B=5."""
     atm = atmosphere_layered()
     tel = telescopes if telescopes is not None else telescope_grid(10, 10, 100.0, z=atm.h_obs)
-    segs = segments_shower(n, atm, seed=seed, zenith_deg=zenith_deg)
+    segs = segments_shower(n, atm, seed=seed, zenith_deg=zenith_deg, workers=workers)
     nm = name or f"shower_1tev_z{int(zenith_deg)}_{n:.0e}".replace("+0", "")
     return Workload(nm, segs, atm, tel, Params(bunch=bunch, seed=seed),
                     description=f"1 TeV gamma shower, zenith {zenith_deg} deg, {n} steps, "
                                 f"{len(tel)} telescopes, B={bunch}")
 
 
-def workload_inclined(n=100_000_000, seed=1):
+def workload_inclined(n=100_000_000, seed=1, workers=0):
     """Zenith 60 deg, 21 x 21 telescopes on a 400 m square at 20 m spacing."""
     atm = atmosphere_layered()
     return workload_shower_1tev(n, seed=seed, zenith_deg=60.0,
                                 telescopes=telescope_grid(21, 21, 20.0, z=atm.h_obs),
-                                name=f"shower_1tev_z60_{n:.0e}".replace("+0", ""))
+                                name=f"shower_1tev_z60_{n:.0e}".replace("+0", ""), workers=workers)
 
 
 def batch_showers(n_showers=256, seed=1, segs_per_10gev=20_000,
                   E_range_GeV=(10.0, 10_000.0), zen_max_deg=45.0, scale=1.0,
-                  fluor_yield=5.0, bunch=5.0):
+                  fluor_yield=5.0, bunch=5.0, workers=0):
     """Many showers with uneven sizes plus fluorescence (yield per MeV)."""
     atm = atmosphere_layered()
     rng = np.random.default_rng(np.random.SeedSequence([seed, 0xBA7]))
@@ -337,10 +416,16 @@ def batch_showers(n_showers=256, seed=1, segs_per_10gev=20_000,
     zen = rng.uniform(0.0, zen_max_deg, n_showers)
     az = rng.uniform(0.0, 360.0, n_showers)
     counts = np.maximum(1, np.round(segs_per_10gev * E / 10.0 * scale)).astype(np.int64)
-    parts = [segments_shower(int(counts[i]), atm, seed=seed, zenith_deg=float(zen[i]),
-                             azimuth_deg=float(az[i]), shower=i)
-             for i in range(n_showers)]
-    segs = np.concatenate(parts)
+    chunk = 1 << 22
+    tasks, lo = [], 0
+    for i in range(n_showers):
+        spec = _ShowerSpec(atm, seed, float(zen[i]), float(az[i]), i, (0.0, 0.0), 350.0, 70.0, 5.0, 80.0,
+                           (10.0, 1000.0), (0.5, 5.0), 2.0, 100000.0)
+        n_i = int(counts[i])
+        for j, a in enumerate(range(0, n_i, chunk)):
+            tasks.append((spec, lo + a, min(chunk, n_i - a), j))
+        lo += n_i
+    segs = _run_tasks(tasks, lo, workers)
     tel = telescope_grid(10, 10, 100.0, z=atm.h_obs)
     return Workload(f"batch_{n_showers}_showers", segs, atm, tel,
                     Params(bunch=bunch, seed=seed, fluor_yield=fluor_yield),

@@ -213,34 +213,60 @@ def test_edge_cases(ctx, torch_cuda):
         ctx.trace(segs, 10, 0, hits, 4096)
 
 
-def test_full_size_single_shower_sampled(ctx, torch_cuda):
-    """The 2e7-step, 100-telescope shower in the launch configuration the
-    benchmark times, checked on contiguous blocks the oracle recomputes."""
-    torch = torch_cuda
-    w = I.workload_shower_1tev(n=20_000_000, seed=1)
-    ctx.setup(w, use_graph=1)
-    gh, gc, gs, gst = G.run_workload(ctx, w, capacity=8_000_000)
-    rng = np.random.default_rng(0)
-    starts = np.sort(rng.choice(20_000_000 // 256, 60, replace=False)) * 256
-    rays = 0
+def _sampled_check(ctx, w, n_blocks=60, block=256, capacity=8_000_000, seed=0):
+    """Trace the whole workload on the device, then recompute n_blocks
+    contiguous blocks of segments with the oracle (keyed by their global
+    indices) and compare the hits of those blocks element by element."""
+    n = len(w.segments)
+    gh, gc, gs, gst = G.run_workload(ctx, w, capacity=capacity)
+    rng = np.random.default_rng(seed)
+    starts = np.sort(rng.choice(n // block, n_blocks, replace=False)) * block
+    rays = common = 0
     for b in starts:
-        seg = w.segments[b:b + 256]
+        seg = w.segments[b:b + block]
         rh, rc, rs, rst = _oracle(w, seg_base=int(b), segs=seg)
         rays += rst["rays"]
-        sel = gh[(gh["seg"] >= b) & (gh["seg"] < b + 256)]
-        sub = I.Workload(w.name, seg, w.atmosphere, w.telescopes, w.params)
+        sel = gh[(gh["seg"] >= b) & (gh["seg"] < b + block)]
         nbc, nbf = O.bunch_counts(seg, w.atmosphere, w.params)
 
         def dp(h, seg=seg, nbc=nbc, nbf=nbf, b=b):
-            p = I.Params(**{**w.params.__dict__})
             out = O.eval_rays(seg, h["seg"] - b, h["k"], h["tel"], nbc, nbf, w.atmosphere,
-                              w.telescopes, p)
+                              w.telescopes, w.params, seg_base=int(b))
             return out[:, 4]
-        # the oracle's records carry global segment indices through seg_base
-        _parity.compare(sel, rh, w.telescopes, ref_dperp_of=dp,
-                        w_tol=_parity.weight_tolerance(seg, rh, w.atmosphere, w.params, seg_base=int(b)))
-    assert rays > 10_000
+        rep = _parity.compare(sel, rh, w.telescopes, ref_dperp_of=dp,
+                              w_tol=_parity.weight_tolerance(seg, rh, w.atmosphere, w.params, seg_base=int(b)))
+        common += rep["n_common"]
     # properties that hold at any size
     assert gst["rays"] == gst["escaped"] + gst["under"] + gst["turned"] + gst["reached"]
-    assert gc.sum() == len(gh)
+    assert gc.sum() == len(gh) and gst["status"] == 0
     np.testing.assert_allclose(gs.sum(), gh["weight"].astype(np.float64).sum(), rtol=1e-9)
+    shower = w.segments["shower"]
+    key = shower[gh["seg"]].astype(np.int64) * 10 ** 15 + gh["tel"].astype(np.int64) * 10 ** 11 + gh["seg"] * 10 ** 3 + gh["k"]
+    assert np.all(np.diff(key) > 0)
+    return rays, common, gst
+
+
+def test_full_size_single_shower_sampled(ctx, torch_cuda):
+    """The 2e7-step, 100-telescope shower in the launch configuration the
+    benchmark times, checked on contiguous blocks the oracle recomputes."""
+    w = I.workload_shower_1tev(n=20_000_000, seed=1, workers=I.default_workers())
+    ctx.setup(w, use_graph=1)
+    rays, common, gst = _sampled_check(ctx, w)
+    assert rays > 10_000 and common > 0
+
+
+def test_full_size_inclined_sampled(ctx, torch_cuda):
+    """The 1e8-step shower at 60 degrees zenith over 441 telescopes at 20 m."""
+    w = I.workload_inclined(n=100_000_000, seed=1, workers=I.default_workers())
+    ctx.setup(w, use_graph=1)
+    rays, common, gst = _sampled_check(ctx, w, n_blocks=40, block=128, capacity=60_000_000)
+    assert rays > 5_000 and common > 100
+
+
+def test_batch_256_showers_sampled(ctx, torch_cuda):
+    """256 showers (E log-uniform 10 GeV-10 TeV, zenith 0-45 deg) with
+    fluorescence, at a tenth of the segment counts (7.4e7 steps)."""
+    w = I.batch_showers(256, seed=1, scale=0.1, workers=I.default_workers())
+    ctx.setup(w, use_graph=1)
+    rays, common, gst = _sampled_check(ctx, w, n_blocks=60, block=128, capacity=40_000_000)
+    assert rays > 5_000 and common > 0 and w.n_showers == 256
