@@ -425,77 +425,77 @@ k_adjoint_hits(const clight_segment *__restrict__ segs, const clight_hit *__rest
 }
 
 // Soft yield Y_g = sum over rays with d_perp < R + W of weight sigma((R - d_perp)/s):
-// its value (optional) and sum_g gY_g dY_g.
+// its value (optional) and sum_g gY_g dY_g, over the candidate rays the
+// forward kernel's candidate pass compacted (local segment << 32 | bunch),
+// so that every lane of a warp carries a ray that needs its tangents.
 template <int NP, bool SPH, bool REFR>
 __global__ void __launch_bounds__(128)
-k_adjoint_soft(const clight_segment *__restrict__ segs, int64_t n_segs, const double *__restrict__ gY,
-               double *__restrict__ yield, const __grid_constant__ DevAtm A, const __grid_constant__ DevTel Tl,
-               const __grid_constant__ DevPar Pp, const __grid_constant__ AdjPar J, double *__restrict__ partial)
+k_adjoint_soft(const clight_segment *__restrict__ segs, const unsigned long long *__restrict__ cand, int64_t n_cand,
+               const double *__restrict__ gY, double *__restrict__ yield, const __grid_constant__ DevAtm A,
+               const __grid_constant__ DevTel Tl, const __grid_constant__ DevPar Pp, const __grid_constant__ AdjPar J,
+               double *__restrict__ partial)
 {
     double acc[NP];
 #pragma unroll
     for (int p = 0; p < NP; ++p) acc[p] = 0.0;
-    for (int64_t si = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; si < n_segs; si += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_cand; i += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long ck = cand[i];
+        int64_t si = (int64_t)(ck >> 32);
+        uint32_t k = (uint32_t)ck;
         clight_segment s = segs[si];
         Seg<float, df> g;
         load_segment_f<SPH>(s, A, Pp, g);
-        if (g.bad) continue;
-        uint32_t nb = g.n_c + g.n_f;
+        if (g.bad || k >= g.n_c + g.n_f) continue;
         int64_t seg_global = Pp.seg_base + si;
-        for (uint32_t k = 0; k < nb; ++k) {
-            RayOut<float, df> o;
-            trace_ray<float, df, false, SPH, REFR>(g, seg_global, k, true, A, Pp, o);
-            if (o.status != 0) continue;
-            float Xf = p_f(o.X), Yf = p_f(o.Y), cz = (float)o.cz, cx = (float)o.cx, cy = (float)o.cy;
-            if (!(finite_f(Xf) && finite_f(Yf) && cz < 0.0f)) continue;
-            float acz = fabsf(cz);
-            float reach = Tl.Rmax + J.soft_w;
-            float dzmax = fmaxf(fabsf(Tl.zmax - A.h_obs), fabsf(Tl.zmin - A.h_obs));
-            float rs = (reach + dzmax * sqrtf(fmaxf(0.0f, 1.0f - acz * acz))) / fmaxf(acz, 1e-6f) + 1e-3f;
-            if (Xf + rs < Tl.xmin - J.soft_w || Xf - rs > Tl.xmax + J.soft_w || Yf + rs < Tl.ymin - J.soft_w ||
-                Yf - rs > Tl.ymax + J.soft_w)
-                continue;
-            bool have_t = false;
-            TanOut<NP> T;
-            int ix0 = max(0, (int)floorf((Xf - rs - Tl.gx0) * Tl.inv_gs));
-            int ix1 = min(Tl.nx - 1, (int)floorf((Xf + rs - Tl.gx0) * Tl.inv_gs));
-            int iy0 = max(0, (int)floorf((Yf - rs - Tl.gy0) * Tl.inv_gs));
-            int iy1 = min(Tl.ny - 1, (int)floorf((Yf + rs - Tl.gy0) * Tl.inv_gs));
-            for (int iy = iy0; iy <= iy1; ++iy)
-                for (int ix = ix0; ix <= ix1; ++ix) {
-                    int cell = iy * Tl.nx + ix;
-                    int cb = __ldg(Tl.cell_start + cell), ce = __ldg(Tl.cell_start + cell + 1);
-                    for (int q = cb; q < ce; ++q) {
-                        int j = __ldg(Tl.cell_tel + q);
-                        float4 tp = __ldg(Tl.tel + j);
-                        float sj = (tp.z - A.h_obs) / cz;
-                        float xr = p_f(o.X - tp.x) + sj * cx;
-                        float yr = p_f(o.Y - tp.y) + sj * cy;
-                        float wd = xr * cx + yr * cy;
-                        float d2 = fmaxf(xr * xr + yr * yr - wd * wd, 0.0f);
-                        float dperp = sqrtf(d2);
-                        if (!(dperp < tp.w + J.soft_w)) continue;
-                        float u = (tp.w - dperp) / J.soft_s;
-                        float sg = 1.0f / (1.0f + expf(-u));
-                        int64_t grp = (int64_t)g.shower * Tl.n_tel + j;
-                        float val = (float)o.weight * sg;
-                        if (yield) atomicAdd(yield + grp, (double)val);
-                        if (gY) {
-                            if (!have_t) {
-                                tangent_ray<NP, SPH, REFR>(g, s, seg_global, k, A, Pp, J, T);
-                                have_t = true;
-                            }
-                            Dual<NP> dxr, dyr, dtj, ddp;
-                            tel_dual<NP>(T, tp, A.h_obs, xr, yr, cx, cy, cz, dxr, dyr, dtj, ddp);
-                            float dsg = sg * (1.0f - sg) / J.soft_s;      // d sigma / d(R - d_perp)
-                            double gy = gY[grp];
-#pragma unroll
-                            for (int p = 0; p < NP; ++p)
-                                acc[p] += gy * (double)(T.weight.d[p] * sg - (float)o.weight * dsg * ddp.d[p]);
+        RayOut<float, df> o;
+        trace_ray<float, df, false, SPH, REFR>(g, seg_global, k, true, A, Pp, o);
+        if (o.status != 0) continue;
+        float Xf = p_f(o.X), Yf = p_f(o.Y), cz = (float)o.cz, cx = (float)o.cx, cy = (float)o.cy;
+        if (!(finite_f(Xf) && finite_f(Yf) && cz < 0.0f)) continue;
+        float acz = fabsf(cz);
+        float reach = Tl.Rmax + J.soft_w;
+        float dzmax = fmaxf(fabsf(Tl.zmax - A.h_obs), fabsf(Tl.zmin - A.h_obs));
+        float rs = (reach + dzmax * sqrtf(fmaxf(0.0f, 1.0f - acz * acz))) / fmaxf(acz, 1e-6f) + 1e-3f;
+        bool have_t = false;
+        TanOut<NP> T;
+        int ix0 = max(0, (int)floorf((Xf - rs - Tl.gx0) * Tl.inv_gs));
+        int ix1 = min(Tl.nx - 1, (int)floorf((Xf + rs - Tl.gx0) * Tl.inv_gs));
+        int iy0 = max(0, (int)floorf((Yf - rs - Tl.gy0) * Tl.inv_gs));
+        int iy1 = min(Tl.ny - 1, (int)floorf((Yf + rs - Tl.gy0) * Tl.inv_gs));
+        for (int iy = iy0; iy <= iy1; ++iy)
+            for (int ix = ix0; ix <= ix1; ++ix) {
+                int cell = iy * Tl.nx + ix;
+                int cb = __ldg(Tl.cell_start + cell), ce = __ldg(Tl.cell_start + cell + 1);
+                for (int q = cb; q < ce; ++q) {
+                    int j = __ldg(Tl.cell_tel + q);
+                    float4 tp = __ldg(Tl.tel + j);
+                    float sj = (tp.z - A.h_obs) / cz;
+                    float xr = p_f(o.X - tp.x) + sj * cx;
+                    float yr = p_f(o.Y - tp.y) + sj * cy;
+                    float wd = xr * cx + yr * cy;
+                    float d2 = fmaxf(xr * xr + yr * yr - wd * wd, 0.0f);
+                    float dperp = sqrtf(d2);
+                    if (!(dperp < tp.w + J.soft_w)) continue;
+                    float u = (tp.w - dperp) / J.soft_s;
+                    float sg = 1.0f / (1.0f + expf(-u));
+                    int64_t grp = (int64_t)g.shower * Tl.n_tel + j;
+                    float val = (float)o.weight * sg;
+                    if (yield) atomicAdd(yield + grp, (double)val);
+                    if (gY) {
+                        if (!have_t) {
+                            tangent_ray<NP, SPH, REFR>(g, s, seg_global, k, A, Pp, J, T);
+                            have_t = true;
                         }
+                        Dual<NP> dxr, dyr, dtj, ddp;
+                        tel_dual<NP>(T, tp, A.h_obs, xr, yr, cx, cy, cz, dxr, dyr, dtj, ddp);
+                        float dsg = sg * (1.0f - sg) / J.soft_s;      // d sigma / d(R - d_perp)
+                        double gy = gY[grp];
+#pragma unroll
+                        for (int p = 0; p < NP; ++p)
+                            acc[p] += gy * (double)(T.weight.d[p] * sg - (float)o.weight * dsg * ddp.d[p]);
                     }
                 }
-        }
+            }
     }
     block_partials<NP>(acc, partial);
 }
@@ -512,35 +512,39 @@ __global__ void k_adjoint_final(const double *__restrict__ partial, int n_blocks
 }
 
 template <int NP, bool SPH, bool REFR>
-static cudaError_t adjoint_np(const clight_segment *segs, int64_t n_segs, const clight_hit *hits, int64_t n_hits,
+static cudaError_t adjoint_np(const clight_segment *segs, const unsigned long long *cand, int64_t n_cand,
+                              const clight_hit *hits, int64_t n_hits,
                               const float *gx, const float *gy, const float *gt, const double *gY, double *yield,
                               const DevAtm &A, const DevTel &T, const DevPar &P, const AdjPar &J, double *partial,
                               int blocks, double *d_out, cudaStream_t s)
 {
     k_adjoint_hits<NP, SPH, REFR><<<blocks, 128, 0, s>>>(segs, hits, n_hits, gx, gy, gt, A, T, P, J, partial);
-    k_adjoint_soft<NP, SPH, REFR><<<blocks, 128, 0, s>>>(segs, n_segs, gY, yield, A, T, P, J, partial + (size_t)blocks * NP);
+    k_adjoint_soft<NP, SPH, REFR><<<blocks, 128, 0, s>>>(segs, cand, n_cand, gY, yield, A, T, P, J,
+                                                         partial + (size_t)blocks * NP);
     k_adjoint_final<NP><<<1, 32, 0, s>>>(partial, 2 * blocks, d_out);
     return cudaGetLastError();
 }
 
 template <int NP>
-static cudaError_t adjoint_geo(const clight_segment *segs, int64_t n_segs, const clight_hit *hits, int64_t n_hits,
+static cudaError_t adjoint_geo(const clight_segment *segs, const unsigned long long *cand, int64_t n_cand,
+                               const clight_hit *hits, int64_t n_hits,
                                const float *gx, const float *gy, const float *gt, const double *gY, double *yield,
                                const DevAtm &A, const DevTel &T, const DevPar &P, const AdjPar &J, double *partial,
                                int blocks, double *d_out, cudaStream_t s)
 {
     if (A.spherical && A.refraction)
-        return adjoint_np<NP, true, true>(segs, n_segs, hits, n_hits, gx, gy, gt, gY, yield, A, T, P, J, partial, blocks, d_out, s);
+        return adjoint_np<NP, true, true>(segs, cand, n_cand, hits, n_hits, gx, gy, gt, gY, yield, A, T, P, J, partial, blocks, d_out, s);
     if (A.spherical)
-        return adjoint_np<NP, true, false>(segs, n_segs, hits, n_hits, gx, gy, gt, gY, yield, A, T, P, J, partial, blocks, d_out, s);
+        return adjoint_np<NP, true, false>(segs, cand, n_cand, hits, n_hits, gx, gy, gt, gY, yield, A, T, P, J, partial, blocks, d_out, s);
     if (A.refraction)
-        return adjoint_np<NP, false, true>(segs, n_segs, hits, n_hits, gx, gy, gt, gY, yield, A, T, P, J, partial, blocks, d_out, s);
-    return adjoint_np<NP, false, false>(segs, n_segs, hits, n_hits, gx, gy, gt, gY, yield, A, T, P, J, partial, blocks, d_out, s);
+        return adjoint_np<NP, false, true>(segs, cand, n_cand, hits, n_hits, gx, gy, gt, gY, yield, A, T, P, J, partial, blocks, d_out, s);
+    return adjoint_np<NP, false, false>(segs, cand, n_cand, hits, n_hits, gx, gy, gt, gY, yield, A, T, P, J, partial, blocks, d_out, s);
 }
 
 int adjoint_params(int n_layers) { return n_layers <= 1 ? 3 : (n_layers <= 5 ? 7 : 10); }
 
-cudaError_t launch_adjoint(const clight_segment *segs, int64_t n_segs, const clight_hit *hits, int64_t n_hits,
+cudaError_t launch_adjoint(const clight_segment *segs, const unsigned long long *cand, int64_t n_cand,
+                           const clight_hit *hits, int64_t n_hits,
                            const float *gx, const float *gy, const float *gt, const double *gY, double *yield,
                            const DevAtm &A, const DevTel &T, const DevPar &P, float soft_s, float soft_w, float K,
                            float L0, double *partial, int blocks, double *d_out, cudaStream_t s)
@@ -552,9 +556,9 @@ cudaError_t launch_adjoint(const clight_segment *segs, int64_t n_segs, const cli
     J.L0 = L0;
     J.n_layers = A.n_layers;
     int np = adjoint_params(A.n_layers);
-    if (np == 3) return adjoint_geo<3>(segs, n_segs, hits, n_hits, gx, gy, gt, gY, yield, A, T, P, J, partial, blocks, d_out, s);
-    if (np == 7) return adjoint_geo<7>(segs, n_segs, hits, n_hits, gx, gy, gt, gY, yield, A, T, P, J, partial, blocks, d_out, s);
-    return adjoint_geo<10>(segs, n_segs, hits, n_hits, gx, gy, gt, gY, yield, A, T, P, J, partial, blocks, d_out, s);
+    if (np == 3) return adjoint_geo<3>(segs, cand, n_cand, hits, n_hits, gx, gy, gt, gY, yield, A, T, P, J, partial, blocks, d_out, s);
+    if (np == 7) return adjoint_geo<7>(segs, cand, n_cand, hits, n_hits, gx, gy, gt, gY, yield, A, T, P, J, partial, blocks, d_out, s);
+    return adjoint_geo<10>(segs, cand, n_cand, hits, n_hits, gx, gy, gt, gY, yield, A, T, P, J, partial, blocks, d_out, s);
 }
 
 }  // namespace clight

@@ -76,6 +76,7 @@ struct clight_ctx {
     uint64_t scratch_gen = 0;
     // staging for the host-buffer entry point
     Buf<double> adj_partial, adj_out;
+    Buf<unsigned long long> adj_cand, adj_ctr;   // soft-yield candidates and their cursor
     Buf<clight_segment> stage_segs;
     Buf<clight_hit> stage_hits;
     Buf<int64_t> stage_counts;
@@ -171,7 +172,7 @@ void clight_destroy(clight_ctx *c)
     c->rec.release(); c->keys.release(); c->keys_alt.release(); c->vals.release(); c->vals_alt.release();
     c->hist.release(); c->bsums.release(); c->gstart.release(); c->gend.release();
     c->stage_segs.release(); c->stage_hits.release(); c->stage_counts.release(); c->stage_sums.release();
-    c->adj_partial.release(); c->adj_out.release();
+    c->adj_partial.release(); c->adj_out.release(); c->adj_cand.release(); c->adj_ctr.release();
     if (c->h_ctr) cudaFreeHost(c->h_ctr);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->ev) cudaEventDestroy(c->ev);
@@ -713,13 +714,42 @@ extern "C" clight_status clight_trace_adjoint(clight_ctx *c, const clight_segmen
     int np = adjoint_params(c->atm.n_layers);
     int blocks = c->n_sm * 8;
     uint64_t *g = &c->scratch_gen;
-    if (c->adj_partial.ensure((int64_t)2 * blocks * np, g) || c->adj_out.ensure(np, g)) return CLIGHT_ERR_CUDA;
+    if (c->adj_partial.ensure((int64_t)2 * blocks * np, g) || c->adj_out.ensure(np, g) ||
+        c->adj_ctr.ensure(CTR_N, g))
+        return CLIGHT_ERR_CUDA;
     DevPar P = c->par;
     P.n_showers = n_showers;
     if (d_yield)
         CK(cudaMemsetAsync(d_yield, 0, sizeof(double) * (size_t)n_showers * c->tel.n_tel, s));
-    CK(launch_adjoint(d_segs, n_segs, d_hits, n_hits, d_gx, d_gy, d_gt, d_gyield, d_yield, c->atm, c->tel, P,
-                      soft_s, soft_w, (float)c->uatm.K, (float)c->uatm.L0, c->adj_partial.p, blocks,
+    // candidate pass: the rays near a telescope, compacted by the forward
+    // kernel (grown and repeated if the list overflows)
+    int64_t n_cand = 0;
+    if ((d_gyield || d_yield) && n_segs > 0) {
+        int block = c->upar.block > 0 ? c->upar.block : 256;
+        int per_sm = c->upar.ctas_per_sm > 0 ? c->upar.ctas_per_sm : 3 * 256 / block;
+        int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)c->n_sm * per_sm,
+                                                              ((n_segs + 31) / 32 * 32 + block - 1) / block));
+        int64_t cap = std::max<int64_t>(1 << 20, c->adj_cand.n > 0 ? c->adj_cand.n : n_segs);
+        for (int attempt = 0; attempt < 2; ++attempt) {
+            if (c->adj_cand.ensure(cap, g)) return CLIGHT_ERR_CUDA;
+            DevOut Oc{};
+            Oc.keys = c->adj_cand.p;
+            Oc.capacity = cap;
+            Oc.ctr = c->adj_ctr.p;
+            Oc.soft_w = soft_w;
+            CK(cudaMemsetAsync(c->adj_ctr.p, 0, sizeof(unsigned long long) * CTR_N, s));
+            CK(launch_soft_candidates(d_segs, n_segs, c->atm, c->tel, P, Oc, (int)grid, block, s));
+            unsigned long long cur = 0;
+            CK(cudaMemcpyAsync(&cur, c->adj_ctr.p + CTR_CURSOR, sizeof(cur), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            n_cand = (int64_t)cur;
+            if (n_cand <= cap) break;
+            if (attempt == 1) return CLIGHT_ERR_LIMIT;
+            cap = n_cand + n_cand / 8 + 1024;
+        }
+    }
+    CK(launch_adjoint(d_segs, c->adj_cand.p, n_cand, d_hits, n_hits, d_gx, d_gy, d_gt, d_gyield, d_yield, c->atm,
+                      c->tel, P, soft_s, soft_w, (float)c->uatm.K, (float)c->uatm.L0, c->adj_partial.p, blocks,
                       c->adj_out.p, s));
     double out[10];
     CK(cudaMemcpyAsync(out, c->adj_out.p, sizeof(double) * (size_t)np, cudaMemcpyDeviceToHost, s));

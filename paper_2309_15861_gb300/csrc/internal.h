@@ -80,6 +80,7 @@ struct DevOut {
     uint32_t *vals;              // 0..n-1
     int64_t capacity;
     unsigned long long *ctr;     // [0] work counter, [1] hit cursor, [2..9] stats
+    float soft_w;                // candidate pass of the adjoint: aperture widening (m)
 };
 
 // Offsets inside DevOut::ctr.
@@ -99,13 +100,20 @@ bool ctx_view(clight_ctx *c, CtxView *v);
 cudaError_t launch_trace_fused(const clight_segment *segs, int64_t n_segs, const DevAtm &A,
                                const DevTel &T, const DevPar &P, const DevOut &O, int precision,
                                int grid, int block, cudaStream_t s);
+// Candidate pass of the soft-yield adjoint: every ray whose arrival line
+// passes within R + O.soft_w of a telescope centre appends
+// (local segment << 32 | bunch) to O.keys (capacity O.capacity, cursor
+// O.ctr[CTR_CURSOR]).
+cudaError_t launch_soft_candidates(const clight_segment *segs, int64_t n_segs, const DevAtm &A, const DevTel &T,
+                                   const DevPar &Pp, const DevOut &O, int grid, int block, cudaStream_t s);
 cudaError_t launch_trace_fp64(const clight_segment *segs, int64_t n_segs, const DevAtm &A,
                               const DevTel &T, const DevPar &P, const DevOut &O, cudaStream_t s);
 int fused_smem_bytes(int block, const DevTel &T);
 
 // tangent-linear adjoint (adjoint_kernels.cu)
 int adjoint_params(int n_layers);   // tangents carried: >= n_layers + 2
-cudaError_t launch_adjoint(const clight_segment *segs, int64_t n_segs, const clight_hit *hits, int64_t n_hits,
+cudaError_t launch_adjoint(const clight_segment *segs, const unsigned long long *cand, int64_t n_cand,
+                           const clight_hit *hits, int64_t n_hits,
                            const float *gx, const float *gy, const float *gt, const double *gY, double *yield,
                            const DevAtm &A, const DevTel &T, const DevPar &P, float soft_s, float soft_w, float K,
                            float L0, double *partial, int blocks, double *d_out, cudaStream_t s);

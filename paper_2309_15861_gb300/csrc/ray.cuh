@@ -803,4 +803,48 @@ __device__ __forceinline__ int hit_test(const RayOut<T, P> &o, int64_t seg_local
     return nh;
 }
 
+// Candidate test of the soft-yield adjoint: does the arrival line pass
+// within R_j + W of some telescope centre?  The same search as hit_test with
+// every radius widened by W.
+template <class T, class P>
+__device__ __forceinline__ bool soft_candidate(const RayOut<T, P> &o, const DevAtm &A, const DevTel &Tl, float W,
+                                               const uint8_t *clr)
+{
+    if (o.status != 0) return false;
+    float Xf = p_f(o.X), Yf = p_f(o.Y);
+    float cz = (float)o.cz, cx = (float)o.cx, cy = (float)o.cy;
+    if (!(finite_f(Xf) && finite_f(Yf) && cz < 0.0f)) return false;
+    float acz = fabsf(cz);
+    float dzmax = fmaxf(fabsf(Tl.zmax - A.h_obs), fabsf(Tl.zmin - A.h_obs));
+    float rs = (Tl.Rmax + W + dzmax * sqrtf(fmaxf(0.0f, 1.0f - acz * acz))) * rcp_approx(fmaxf(acz, 1e-6f)) + 1e-3f;
+    if (Xf + rs < Tl.xmin || Xf - rs > Tl.xmax || Yf + rs < Tl.ymin || Yf - rs > Tl.ymax) return false;
+    if (clr) {
+        float fx = (Xf - Tl.cx0) * Tl.inv_cgs, fy = (Yf - Tl.cy0) * Tl.inv_cgs;
+        if (fx >= 0.0f && fy >= 0.0f && fx < (float)Tl.cnx && fy < (float)Tl.cny) {
+            int ci = (int)fy * Tl.cnx + (int)fx;
+            if (rs < (float)clr[ci] * kClrQuantum) return false;
+        }
+    }
+    int ix0 = max(0, (int)floorf((Xf - rs - Tl.gx0) * Tl.inv_gs));
+    int ix1 = min(Tl.nx - 1, (int)floorf((Xf + rs - Tl.gx0) * Tl.inv_gs));
+    int iy0 = max(0, (int)floorf((Yf - rs - Tl.gy0) * Tl.inv_gs));
+    int iy1 = min(Tl.ny - 1, (int)floorf((Yf + rs - Tl.gy0) * Tl.inv_gs));
+    for (int iy = iy0; iy <= iy1; ++iy)
+        for (int ix = ix0; ix <= ix1; ++ix) {
+            int cell = iy * Tl.nx + ix;
+            int b = __ldg(Tl.cell_start + cell), e = __ldg(Tl.cell_start + cell + 1);
+            for (int q = b; q < e; ++q) {
+                float4 tp = __ldg(Tl.tel + __ldg(Tl.cell_tel + q));
+                float sj = Num<float>::div(tp.z - A.h_obs, cz);
+                float xr = p_f(o.X - (T)tp.x) + sj * cx;
+                float yr = p_f(o.Y - (T)tp.y) + sj * cy;
+                float wd = xr * cx + yr * cy;
+                float d2 = fmaxf(xr * xr + yr * yr - wd * wd, 0.0f);
+                float rw = tp.w + W;
+                if (d2 < rw * rw) return true;
+            }
+        }
+    return false;
+}
+
 }  // namespace clight

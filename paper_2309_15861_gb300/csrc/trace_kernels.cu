@@ -49,7 +49,7 @@ __device__ __forceinline__ uint32_t warp_sort_u32(uint32_t key, int lane)
     return key;
 }
 
-template <class P, bool SPH, bool REFR, bool NOALLOC = false>
+template <class P, bool SPH, bool REFR, bool NOALLOC = false, bool SOFT = false>
 __global__ void __launch_bounds__(256, 3)
 k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid_constant__ DevAtm A,
               const __grid_constant__ DevTel Tl, const __grid_constant__ DevPar Pp, const __grid_constant__ DevOut O)
@@ -182,6 +182,27 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
                 if (active) {
                     ++c_rays;
                     c_esc += o.status == 1; c_under += o.status == 2; c_turn += o.status == 3;
+                    c_reach += o.status == 0 || o.status == 5;
+                    c_cells += o.status == 0 ? o.cells : 0;
+                }
+            } else if (SOFT) {
+                // candidate pass of the soft-yield adjoint: compact the rays
+                // near a telescope into O.keys
+                RayOut<float, df> o;
+                trace_ray<float, df, true, SPH, REFR>(q, seg_global, k, active, A, Pp, o);
+                bool cand = active && soft_candidate<float, df>(o, A, Tl, O.soft_w, clr);
+                unsigned m = __ballot_sync(FULL_MASK, cand);
+                if (m) {
+                    unsigned long long base = 0;
+                    if (lane == 0) base = atomicAdd(O.ctr + CTR_CURSOR, (unsigned long long)__popc(m));
+                    base = __shfl_sync(FULL_MASK, base, 0);
+                    unsigned long long idx = base + __popc(m & lanemask_lt());
+                    if (cand && (int64_t)idx < O.capacity)
+                        O.keys[idx] = ((unsigned long long)seg_local << 32) | (unsigned long long)k;
+                }
+                nh = cand ? 1 : 0;
+                if (active) {
+                    ++c_rays;
                     c_reach += o.status == 0 || o.status == 5;
                     c_cells += o.status == 0 ? o.cells : 0;
                 }
@@ -322,6 +343,21 @@ static cudaError_t noalloc_scratch(int device, unsigned long long **out)
     }
     *out = g_noalloc_ptr[device];
     return cudaSuccess;
+}
+
+cudaError_t launch_soft_candidates(const clight_segment *segs, int64_t n_segs, const DevAtm &A, const DevTel &T,
+                                   const DevPar &Pp, const DevOut &O, int grid, int block, cudaStream_t s)
+{
+    int smem = fused_smem_bytes(block, T);
+    if (A.spherical && A.refraction)
+        k_trace_fused<df, true, true, false, true><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
+    else if (A.spherical)
+        k_trace_fused<df, true, false, false, true><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
+    else if (A.refraction)
+        k_trace_fused<df, false, true, false, true><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
+    else
+        k_trace_fused<df, false, false, false, true><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
+    return cudaGetLastError();
 }
 
 template <class P, bool SPH, bool REFR>
