@@ -160,7 +160,7 @@ def reference_arm(args, rank):
     if rank != 0:
         return 0
     w = make_workload(args.workload, args.n_segs, 0, args.scale)
-    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
     vals = []
     for i in range(args.warmup + args.steps):
         r = cpu_baseline(w, budget_s=per_step, seed=i)
