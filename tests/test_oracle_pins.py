@@ -383,3 +383,107 @@ def test_shower_generator_distributions():
     assert stats.kstest(X, lambda x: g.cdf(x) / g.cdf(X_obs)).pvalue > 1e-4
     L = s["L"]
     assert L.min() >= 0.5 and L.max() <= 5.0
+
+
+# ---------------------------------------------------------------- adjoint reference
+def _fluorescence_steps(n, seed):
+    """Uncharged steps (no Cherenkov light) that emit fluorescence only."""
+    rng = np.random.default_rng(seed)
+    s = np.zeros(n, dtype=I.SEG_DTYPE)
+    s["x"] = rng.uniform(-50, 50, n)
+    s["y"] = rng.uniform(-50, 50, n)
+    s["z"] = rng.uniform(5000, 15000, n)
+    s["dz"] = -1.0
+    s["L"] = 1.0
+    s["eps"] = 1e-3
+    s["dE"] = rng.uniform(0.5, 2.0, n)
+    s["charge"] = 0
+    return s
+
+
+def test_oracle_gradient_matches_closed_form_for_straight_rays():
+    """Refraction off, flat Earth, one exponential layer, fluorescence only:
+    the emission does not depend on the atmosphere, the ray is straight, and
+    t - t_e = (s + K b/(100 |dz|) (e^{-h_obs/c} - e^{-h_e/c})) / c_light,
+    tau = b (e^{-h_obs/c} - e^{-h_e/c}) / (100 rho_ref |dz| L0 (lambda/lambda_ref)^4).
+    Central differences of the oracle (h = 1e-4 relative) against the
+    derivatives of these in K, c and L0."""
+    atm = I.atmosphere_single_exponential(refraction=False, absorption=True, spherical=False)
+    par = I.Params(bunch=1.0, seed=3, fluor_yield=5.0)
+    segs = _fluorescence_steps(40, seed=2)
+    tel = np.zeros(1, dtype=I.TEL_DTYPE)
+    tel["z"] = atm.h_obs
+    tel["R"] = 1e6
+    nbc, nbf = O.bunch_counts(segs, atm, par)
+    assert nbc.sum() == 0 and nbf.sum() > 100
+    rows = []
+    for i in range(len(segs)):
+        for k in range(int(nbf[i])):
+            r, d, te, lam, w, proc = O.photon(segs[i], i, k, atm, par)
+            if d[2] < -0.2:
+                rows.append((i, k, r[2], abs(d[2]), lam, w, te))
+    rows = np.array(rows)
+    si, kk = rows[:, 0].astype(np.int64), rows[:, 1].astype(np.uint32)
+    he, adz, lam, w = rows[:, 2], rows[:, 3], rows[:, 4], rows[:, 5]
+    tt = np.zeros(len(rows), dtype=np.uint32)
+    b, c, K, L0, ho = atm.b[0], atm.c[0], atm.K, atm.L0, atm.h_obs
+
+    def ev(a):
+        return O.eval_rays(segs, si, kk, tt, nbc, nbf, a, tel, par)
+
+    base = ev(atm)
+    # the closed form of the values themselves
+    E = np.exp(-ho / c) - np.exp(-he / c)
+    t_cf = rows[:, 6] + ((he - ho) / adz + K * b / (100 * adz) * E) / C_M_NS
+    tau = b * E / (100 * atm.rho_ref * adz * L0 * (lam / atm.lambda_ref) ** 4)
+    np.testing.assert_allclose(base[:, 2], t_cf, rtol=1e-12, atol=1e-9)
+    np.testing.assert_allclose(base[:, 3], w * np.exp(-tau), rtol=1e-10)
+    dE_dc = (ho * np.exp(-ho / c) - he * np.exp(-he / c)) / c ** 2
+    expect = {
+        "K": (b / (100 * adz) * E / C_M_NS, np.zeros(len(rows))),
+        "c": (K * b / (100 * adz) * dE_dc / C_M_NS, -w * np.exp(-tau) * tau / E * dE_dc),
+        "L0": (np.zeros(len(rows)), w * np.exp(-tau) * tau / L0),
+    }
+    for name, (dt, dw) in expect.items():
+        val = {"K": K, "c": c, "L0": L0}[name]
+        h = 1e-4 * val
+        out = []
+        for sgn in (1, -1):
+            a = I.Atmosphere(**{**atm.__dict__})
+            if name == "c":
+                a.c = [c + sgn * h]
+            else:
+                setattr(a, name, val + sgn * h)
+            out.append(ev(a))
+        fd = (out[0] - out[1]) / (2 * h)
+        np.testing.assert_allclose(fd[:, 2], dt, rtol=1e-6, atol=1e-12 * np.abs(dt).max())
+        np.testing.assert_allclose(fd[:, 3], dw, rtol=1e-6, atol=1e-9 * np.abs(dw).max() + 1e-300)
+        np.testing.assert_allclose(fd[:, 0], 0.0, atol=1e-9)      # straight rays do not move
+
+
+def test_eval_rays_reproduces_the_traced_hits():
+    w = I.workload_shower_1tev(n=3000, seed=7)
+    h, cnt, sums, st = O.trace(w.segments, w.atmosphere, w.telescopes, w.params)
+    assert len(h) > 50
+    nbc, nbf = O.bunch_counts(w.segments, w.atmosphere, w.params)
+    ev = O.eval_rays(w.segments, h["seg"], h["k"], h["tel"], nbc, nbf, w.atmosphere, w.telescopes, w.params)
+    np.testing.assert_allclose(ev[:, 0], h["x_rel"], atol=1e-9)
+    np.testing.assert_allclose(ev[:, 1], h["y_rel"], atol=1e-9)
+    np.testing.assert_allclose(ev[:, 2], h["t"], rtol=0, atol=1e-9)
+    np.testing.assert_allclose(ev[:, 3], h["weight"], rtol=1e-12)
+    np.testing.assert_allclose(ev[:, 4], h["dperp"], atol=1e-9)
+
+
+def test_soft_yield_limits():
+    """s -> 0 gives the hard-aperture photon sums; the cut at R + W does not matter."""
+    w = I.workload_shower_1tev(n=3000, seed=9)
+    h, cnt, sums, st = O.trace(w.segments, w.atmosphere, w.telescopes, w.params)
+    nbc, nbf = O.bunch_counts(w.segments, w.atmosphere, w.params)
+    hard = O.soft_yield(w.segments, nbc, nbf, w.atmosphere, w.telescopes, w.params, s=1e-9, W=0.01)
+    edge = np.abs(h["dperp"] - w.telescopes["R"][h["tel"]]) < 1e-6
+    assert not edge.any()
+    np.testing.assert_allclose(hard, sums, rtol=1e-9, atol=1e-9)
+    y20 = O.soft_yield(w.segments, nbc, nbf, w.atmosphere, w.telescopes, w.params, s=0.5, W=20.0)
+    y40 = O.soft_yield(w.segments, nbc, nbf, w.atmosphere, w.telescopes, w.params, s=0.5, W=40.0)
+    np.testing.assert_allclose(y20, y40, rtol=1e-12, atol=1e-15 * y40.max())
+    assert y20.sum() > 0
