@@ -210,6 +210,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--cut-study", action="store_true",
+                    help="also time the Cherenkov angular cut (array centre and per telescope, 6 deg) and "
+                         "report its speedup and photon loss against the uncut step")
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
@@ -342,6 +345,31 @@ def main():
             "ops_per_ray": ops / max(1, st["rays"]), "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                                                  f"{f_max / 1e6:.0f} MHz (max SM clock)"}
 
+    # ---- angular segment cut: the same step with the cut on
+    cut = None
+    if args.cut_study:
+        import dataclasses
+        base_sum, base_hits = float(sums.sum().item()), nh
+        cut = []
+        for mode in (1, 2):
+            p2 = dataclasses.replace(w.params, cut_mode=mode, cut_deg=6.0, cut_centre=I.array_centre(w.telescopes))
+            ctx.set_params(p2, **extra)
+            for _ in range(3):
+                ctx.trace(segs, n, ns, hits, cap, counts, sums)
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            kc = max(5, args.steps // 4)
+            c0.record(s)
+            for _ in range(kc):
+                code, nh_c, st_c = ctx.trace(segs, n, ns, hits, cap, counts, sums)
+            c1.record(s)
+            torch.cuda.synchronize()
+            cms = c0.elapsed_time(c1) / kc
+            cut.append({"mode": ["", "array centre", "each telescope"][mode], "deg": 6.0,
+                        "segments_cut": int(st_c["cut"]), "rays": int(st_c["rays"]), "ms_per_step": cms,
+                        "speedup": ms_step / cms, "hits_kept": nh_c / max(1, base_hits),
+                        "photon_loss": 1.0 - float(sums.sum().item()) / base_sum if base_sum else None})
+        ctx.set_params(w.params, **extra)
+
     # ---- plain FP64 GPU path on the same workload (at most its first 2e7 steps)
     fp64 = None
     if not args.no_fp64:
@@ -408,6 +436,8 @@ def main():
         }
         if tune is not None:
             line["autotune"] = tune
+        if cut is not None:
+            line["angular_cut"] = cut
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

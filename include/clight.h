@@ -91,6 +91,16 @@ enum {
     CLIGHT_PREC_FP64_GUARD = 1      /* native FP64 for the same steps */
 };
 
+/* Cherenkov angular segment cut (Sec. 1.2.1, optimisation): a step emits
+ * no Cherenkov light when its flight direction makes more than cut_deg with
+ * the direction from its midpoint to the array centre (CENTRE) or to every
+ * telescope centre (TELESCOPES).  Fluorescence is not affected. */
+enum {
+    CLIGHT_CUT_OFF = 0,
+    CLIGHT_CUT_CENTRE = 1,
+    CLIGHT_CUT_TELESCOPES = 2
+};
+
 typedef struct {
     double lambda1, lambda2;        /* Cherenkov band, nm */
     double bunch;                   /* maximum photons per bunch (> 0) */
@@ -104,6 +114,10 @@ typedef struct {
     int32_t use_graph;              /* capture the whole pipeline in a CUDA graph and replay */
     float cell_width;               /* quadrature cell width in scale heights (0 = 1.5) */
     int32_t key_bunch_bits;         /* bits of the bunch index in the sort key (0 = 16) */
+    int32_t cut_mode;               /* CLIGHT_CUT_* */
+    int32_t cut_pad;
+    double cut_deg;                 /* cut angle in degrees, (0, 180) (0 = 6) */
+    double cut_centre[3];           /* array centre for CLIGHT_CUT_CENTRE, m, local frame */
 } clight_params;
 
 /* One telescope hit (48 bytes). */
@@ -128,6 +142,7 @@ typedef struct {
     int64_t guarded;    /* segments whose bunch count was recomputed in FP64 */
     int64_t status;     /* OR of CLIGHT_ERR_* bits seen in the kernels (1 << code) */
     int64_t cells;      /* altitude cells integrated, summed over arrived rays */
+    int64_t cut;        /* steps whose Cherenkov light the angular cut removed */
 } clight_stats;
 
 typedef struct clight_ctx clight_ctx;

@@ -32,7 +32,9 @@ def build(force: bool = False) -> str:
             os.path.getmtime(src), os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=gnu11", "-fopenmp", "-fPIC", "-shared", src, "-o", tmp, "-lm"]
+    # no contraction into FMA: the same binary64 expressions give the same
+    # bits on every host (the angular cut's decisions depend on it)
+    cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", src, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
@@ -51,7 +53,8 @@ class _Par(C.Structure):
     _fields_ = [("lambda1", C.c_double), ("lambda2", C.c_double), ("bunch", C.c_double),
                 ("seed", C.c_uint32), ("stream", C.c_uint32), ("fluor_yield", C.c_double),
                 ("fl_lambda1", C.c_double), ("fl_lambda2", C.c_double),
-                ("seg_base", C.c_int64)]
+                ("seg_base", C.c_int64), ("cut_mode", C.c_int32), ("cut_deg", C.c_double),
+                ("cut_centre", C.c_double * 3), ("cut_tels", C.c_void_p), ("cut_n_tel", C.c_int32)]
 
 
 _lib = None
@@ -108,12 +111,27 @@ def atm_struct(atm) -> _Atm:
     return s
 
 
-def par_struct(p, seg_base: int = 0) -> _Par:
+def par_struct(p, seg_base: int = 0, tels=None) -> _Par:
+    """The C parameter block.  For the per-telescope angular cut `tels` must
+    be given and must stay alive while the block is used."""
     s = _Par()
     s.seg_base = int(seg_base)
     s.lambda1, s.lambda2, s.bunch = p.lambda1, p.lambda2, p.bunch
     s.seed, s.stream = p.seed & 0xFFFFFFFF, p.stream & 0xFFFFFFFF
     s.fluor_yield, s.fl_lambda1, s.fl_lambda2 = p.fluor_yield, p.fl_lambda1, p.fl_lambda2
+    mode = int(getattr(p, "cut_mode", 0))
+    s.cut_mode = mode
+    s.cut_deg = float(getattr(p, "cut_deg", 6.0))
+    if mode == 1:
+        if p.cut_centre is None:
+            raise ValueError("the centre cut needs Params.cut_centre")
+        for i in range(3):
+            s.cut_centre[i] = float(p.cut_centre[i])
+    if mode == 2:
+        if tels is None:
+            raise ValueError("the per-telescope cut needs the telescopes")
+        s.cut_tels = tels.ctypes.data
+        s.cut_n_tel = len(tels)
     return s
 
 
@@ -130,11 +148,12 @@ def u01(x: int) -> float:
     return lib().or_u01(int(x) & 0xFFFFFFFF)
 
 
-def yield_of(seg, atm, par):
+def yield_of(seg, atm, par, tels=None):
     """-> dict(n_c, w_c, n_f, w_f, cos_tc, sin_tc, Nc, Nf, delta, h_mid)."""
     s = np.ascontiguousarray(np.asarray(seg).reshape(1))
     o = np.zeros(10)
-    a, p = atm_struct(atm), par_struct(par)
+    tels = None if tels is None else np.ascontiguousarray(tels)
+    a, p = atm_struct(atm), par_struct(par, 0, tels)
     lib().or_yield(_ptr(s), C.byref(a), C.byref(p), _ptr(o))
     keys = ["n_c", "w_c", "n_f", "w_f", "cos_tc", "sin_tc", "Nc", "Nf", "delta", "h_mid"]
     return dict(zip(keys, o.tolist()))
@@ -147,11 +166,12 @@ def rotation(d):
     return M.reshape(3, 3)
 
 
-def photon(seg, seg_index, k, atm, par):
+def photon(seg, seg_index, k, atm, par, tels=None):
     """-> (r_e[3], d[3], t_e, lambda, weight, process)."""
     s = np.ascontiguousarray(np.asarray(seg).reshape(1))
     o = np.zeros(10)
-    a, p = atm_struct(atm), par_struct(par)
+    tels = None if tels is None else np.ascontiguousarray(tels)
+    a, p = atm_struct(atm), par_struct(par, 0, tels)
     lib().or_photon(_ptr(s), int(seg_index), int(k), C.byref(a), C.byref(p), _ptr(o))
     return o[0:3].copy(), o[3:6].copy(), o[6], o[7], o[8], int(o[9])
 
@@ -180,7 +200,7 @@ def trace(segs, atm, tels, par, n_showers=1, capacity=None, threads=0, seg_base=
     seg_base is the global index of segs[0] (it keys the random numbers)."""
     segs = np.ascontiguousarray(segs)
     tels = np.ascontiguousarray(tels)
-    a, p = atm_struct(atm), par_struct(par, seg_base)
+    a, p = atm_struct(atm), par_struct(par, seg_base, tels)
     n_tel = len(tels)
     counts = np.zeros(n_showers * n_tel, dtype=np.int64)
     sums = np.zeros(n_showers * n_tel, dtype=np.float64)
@@ -199,12 +219,13 @@ def trace(segs, atm, tels, par, n_showers=1, capacity=None, threads=0, seg_base=
     return hits[:total], counts.reshape(n_showers, n_tel), sums.reshape(n_showers, n_tel), st
 
 
-def bunch_counts(segs, atm, par):
-    """Nominal Cherenkov and fluorescence bunch counts of every segment."""
+def bunch_counts(segs, atm, par, tels=None):
+    """Nominal Cherenkov and fluorescence bunch counts of every segment
+    (`tels` is needed for the per-telescope angular cut)."""
     nc = np.zeros(len(segs), dtype=np.uint32)
     nf = np.zeros(len(segs), dtype=np.uint32)
     for i in range(len(segs)):
-        y = yield_of(segs[i], atm, par)
+        y = yield_of(segs[i], atm, par, tels)
         nc[i] = int(y["n_c"])
         nf[i] = int(y["n_f"])
     return nc, nf
@@ -216,7 +237,7 @@ def soft_yield(segs, nbc, nbf, atm, tels, par, n_showers=1, s=0.5, W=10.0, threa
     nbc = np.ascontiguousarray(nbc, dtype=np.uint32)
     nbf = np.ascontiguousarray(nbf, dtype=np.uint32)
     out = np.zeros(n_showers * len(tels))
-    a, p = atm_struct(atm), par_struct(par, seg_base)
+    a, p = atm_struct(atm), par_struct(par, seg_base, tels)
     lib().or_soft_yield(_ptr(segs), len(segs), _ptr(nbc), _ptr(nbf), C.byref(a), _ptr(tels),
                         len(tels), C.byref(p), n_showers, float(s), float(W), _ptr(out),
                         int(threads))
@@ -236,7 +257,7 @@ def eval_rays(segs, seg_idx, k, tel, nbc, nbf, atm, tels, par, threads=0, seg_ba
     nbc = np.ascontiguousarray(nbc, dtype=np.uint32)
     nbf = np.ascontiguousarray(nbf, dtype=np.uint32)
     out = np.zeros((len(seg_idx), 5))
-    a, p = atm_struct(atm), par_struct(par, seg_base)
+    a, p = atm_struct(atm), par_struct(par, seg_base, tels)
     lib().or_eval_rays(_ptr(segs), _ptr(seg_idx), _ptr(k), _ptr(tel), _ptr(nbc), _ptr(nbf),
                        len(seg_idx), C.byref(a), _ptr(tels), C.byref(p), _ptr(out), int(threads))
     return out

@@ -100,6 +100,32 @@ static void unit3(const float d[3], double u[3])
  * Fluorescence (Eq. 1, Sec. 1.1): N = Y dE with a constant yield Y.
  * Bunching (reading): n_b = ceil(N / B) bunches of weight N / n_b.
  * ---------------------------------------------------------------------- */
+/* ------------------------------------------------------------------------
+ * Angular segment cut (Sec. 1.2.1, optimisation): a step keeps its
+ * Cherenkov light when its flight direction d lies within the cut angle of
+ * the vector v from the step midpoint m to the array centre (mode 1) or to
+ * some telescope centre (mode 2): d . v >= |v| cos(cut).
+ * ---------------------------------------------------------------------- */
+static int cut_one(const double d[3], const double m[3], const double c[3], double cosc)
+{
+    double v0 = c[0] - m[0], v1 = c[1] - m[1], v2 = c[2] - m[2];
+    double dot = d[0] * v0 + d[1] * v1 + d[2] * v2;
+    double nv = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
+    return dot - nv * cosc >= 0.0;
+}
+
+static int cut_keeps(const double d[3], const double m[3], const or_params *p)
+{
+    double deg = p->cut_deg > 0 ? p->cut_deg : 6.0;
+    double cosc = cos(deg * (OR_PI / 180.0));
+    if (p->cut_mode == 1) return cut_one(d, m, p->cut_centre, cosc);
+    for (int j = 0; j < p->cut_n_tel; j++) {
+        double c[3] = {p->cut_tels[j].x, p->cut_tels[j].y, p->cut_tels[j].z};
+        if (cut_one(d, m, c, cosc)) return 1;
+    }
+    return 0;
+}
+
 void or_yield(const or_segment *s, const or_atmosphere *a, const or_params *p, double out[10])
 {
     double d[3];
@@ -111,6 +137,7 @@ void or_yield(const or_segment *s, const or_atmosphere *a, const or_params *p, d
     double n = 1.0 + delta;
     double beta = 1.0 - (double)s->eps;
     double z2 = (double)s->charge * (double)s->charge;
+    if (p->cut_mode != 0 && z2 > 0 && !cut_keeps(d, rm, p)) z2 = 0;
     double n_c = 0, w_c = 0, cos_tc = 1, sin_tc = 0, Nc = 0;
     if (z2 > 0 && beta * n > 1.0 && s->L > 0) {
         cos_tc = 1.0 / (beta * n);

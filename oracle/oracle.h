@@ -58,6 +58,13 @@ typedef struct {
     double fluor_yield;           /* photons per MeV deposited (0 = off) */
     double fl_lambda1, fl_lambda2;
     int64_t seg_base;             /* global index of segs[0] (Philox counter) */
+    /* Cherenkov angular segment cut (Sec. 1.2.1, optimisation):
+     * 0 off, 1 array centre, 2 each telescope */
+    int32_t cut_mode;
+    double cut_deg;               /* degrees (0 = 6) */
+    double cut_centre[3];         /* mode 1 */
+    const or_telescope *cut_tels; /* mode 2 */
+    int32_t cut_n_tel;
 } or_params;
 
 typedef struct {            /* oracle output record, all FP64 */

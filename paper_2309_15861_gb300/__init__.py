@@ -50,12 +50,14 @@ class Params(C.Structure):
                 ("seed", C.c_uint32), ("stream", C.c_uint32), ("fluor_yield", C.c_double),
                 ("fl_lambda1", C.c_double), ("fl_lambda2", C.c_double), ("seg_base", C.c_int64),
                 ("precision", C.c_int32), ("block", C.c_int32), ("ctas_per_sm", C.c_int32),
-                ("use_graph", C.c_int32), ("cell_width", C.c_float), ("key_bunch_bits", C.c_int32)]
+                ("use_graph", C.c_int32), ("cell_width", C.c_float), ("key_bunch_bits", C.c_int32),
+                ("cut_mode", C.c_int32), ("cut_pad", C.c_int32), ("cut_deg", C.c_double),
+                ("cut_centre", C.c_double * 3)]
 
 
 class Stats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in
-                ("rays", "escaped", "under", "turned", "reached", "hits", "guarded", "status", "cells")]
+                ("rays", "escaped", "under", "turned", "reached", "hits", "guarded", "status", "cells", "cut")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -122,6 +124,13 @@ def params_struct(p: inputs.Params, **kw) -> Params:
     s.lambda1, s.lambda2, s.bunch = p.lambda1, p.lambda2, p.bunch
     s.seed, s.stream = p.seed & 0xFFFFFFFF, p.stream & 0xFFFFFFFF
     s.fluor_yield, s.fl_lambda1, s.fl_lambda2 = p.fluor_yield, p.fl_lambda1, p.fl_lambda2
+    s.cut_mode = int(getattr(p, "cut_mode", 0))
+    s.cut_deg = float(getattr(p, "cut_deg", 6.0))
+    if s.cut_mode == 1:
+        if p.cut_centre is None:
+            raise ValueError("the centre cut needs Params.cut_centre")
+        for i in range(3):
+            s.cut_centre[i] = float(p.cut_centre[i])
     for k, v in kw.items():
         setattr(s, k, v)
     return s

@@ -371,6 +371,21 @@ clight_status clight_set_telescopes(clight_ctx *c, const clight_telescope *t, in
     CK(cudaMemcpy(c->d_cell_tel, tel_idx.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->d_clr, clr.data(), (size_t)clr_bytes, cudaMemcpyHostToDevice));
     DevTel &T = c->tel;
+    {
+        double sx = 0, sy = 0, sz = 0;
+        for (int i = 0; i < n; ++i) { sx += t[i].x; sy += t[i].y; sz += t[i].z; }
+        sx /= n; sy /= n; sz /= n;
+        double r = 0;
+        for (int i = 0; i < n; ++i) {
+            double dx = t[i].x - sx, dy = t[i].y - sy, dz = t[i].z - sz;
+            r = std::max(r, std::sqrt(dx * dx + dy * dy + dz * dz));
+        }
+        T.mx = (float)sx; T.my = (float)sy; T.mz = (float)sz;
+        T.mr = (float)(r * (1 + 1e-6) + 1e-3);  // covers the rounding of the centre
+        double cab = 0;
+        for (int i = 0; i < n; ++i) cab = std::max(cab, (double)std::fabs(t[i].x) + std::fabs(t[i].y) + std::fabs(t[i].z));
+        T.cabs = (float)(cab * (1 + 1e-6));
+    }
     T.clr = c->d_clr; T.cnx = cnx; T.cny = cny; T.clr_bytes = clr_bytes;
     T.cx0 = (float)bx0; T.cy0 = (float)by0; T.inv_cgs = (float)(1.0 / cgs);
     T.tel = c->d_tel; T.cell_start = c->d_cell_start; T.cell_tel = c->d_cell_tel;
@@ -393,6 +408,11 @@ clight_status clight_set_params(clight_ctx *c, const clight_params *p)
     if (p->precision != CLIGHT_PREC_FLOAT_PAIR && p->precision != CLIGHT_PREC_FP64_GUARD) return CLIGHT_ERR_ARG;
     if (p->cell_width < 0 || p->cell_width > 8) return CLIGHT_ERR_ARG;
     if (p->key_bunch_bits < 0 || p->key_bunch_bits > 32) return CLIGHT_ERR_ARG;
+    if (p->cut_mode < CLIGHT_CUT_OFF || p->cut_mode > CLIGHT_CUT_TELESCOPES) return CLIGHT_ERR_ARG;
+    if (p->cut_mode != CLIGHT_CUT_OFF && (!(p->cut_deg >= 0) || !(p->cut_deg < 180) ||
+                                          !std::isfinite(p->cut_centre[0]) || !std::isfinite(p->cut_centre[1]) ||
+                                          !std::isfinite(p->cut_centre[2])))
+        return CLIGHT_ERR_ARG;
     float old_cw = c->upar.cell_width;
     c->upar = *p;
     DevPar &P = c->par;
@@ -415,6 +435,13 @@ clight_status clight_set_params(clight_ctx *c, const clight_params *p)
     P.seed = p->seed;
     P.stream = p->stream;
     P.seg_base = p->seg_base;
+    P.cut_mode = p->cut_mode;
+    const double cut_deg = p->cut_deg > 0 ? p->cut_deg : 6.0;
+    P.cut_cos_d = std::cos(cut_deg * (3.14159265358979323846 / 180.0));
+    P.cut_cos = (float)P.cut_cos_d;
+    P.cut_cx_d = p->cut_centre[0]; P.cut_cy_d = p->cut_centre[1]; P.cut_cz_d = p->cut_centre[2];
+    P.cut_cx = (float)P.cut_cx_d; P.cut_cy = (float)P.cut_cy_d; P.cut_cz = (float)P.cut_cz_d;
+    P.cut_rad = (float)(cut_deg * (3.14159265358979323846 / 180.0));
     ++c->version;
     if (c->atm_set && p->cell_width != old_cw) {
         clight_atmosphere a = c->uatm;
@@ -432,6 +459,13 @@ bool clight::ctx_view(clight_ctx *c, CtxView *v)
     v->atm = c->atm;
     v->tel = c->tel;
     v->par = c->par;
+    v->par.cut_tel = c->tel.tel;
+    v->par.cut_n_tel = c->tel.n_tel;
+    v->par.cut_tx = c->tel.mx; v->par.cut_ty = c->tel.my; v->par.cut_tz = c->tel.mz; v->par.cut_tr = c->tel.mr;
+    v->par.cut_cell_start = c->tel.cell_start; v->par.cut_cell_tel = c->tel.cell_tel;
+    v->par.cut_cabs = std::max(c->tel.cabs, (float)(std::fabs(v->par.cut_cx_d) + std::fabs(v->par.cut_cy_d) + std::fabs(v->par.cut_cz_d)));
+    v->par.cut_nx = c->tel.nx; v->par.cut_ny = c->tel.ny;
+    v->par.cut_gx0 = c->tel.gx0; v->par.cut_gy0 = c->tel.gy0; v->par.cut_inv_gs = c->tel.inv_gs;
     v->device = c->device;
     v->n_sm = c->n_sm;
     v->block = c->upar.block > 0 ? c->upar.block : 256;
@@ -467,6 +501,13 @@ clight_status prepare(clight_ctx *c, int64_t n_segs, int32_t n_showers, int64_t 
     c->par.n_showers = n_showers;
     c->par.seg_bits = sbits;
     c->par.k_bits = kbits;
+    c->par.cut_tel = c->tel.tel;
+    c->par.cut_n_tel = c->tel.n_tel;
+    c->par.cut_tx = c->tel.mx; c->par.cut_ty = c->tel.my; c->par.cut_tz = c->tel.mz; c->par.cut_tr = c->tel.mr;
+    c->par.cut_cell_start = c->tel.cell_start; c->par.cut_cell_tel = c->tel.cell_tel;
+    c->par.cut_cabs = std::max(c->tel.cabs, (float)(std::fabs(c->par.cut_cx_d) + std::fabs(c->par.cut_cy_d) + std::fabs(c->par.cut_cz_d)));
+    c->par.cut_nx = c->tel.nx; c->par.cut_ny = c->tel.ny;
+    c->par.cut_gx0 = c->tel.gx0; c->par.cut_gy0 = c->tel.gy0; c->par.cut_inv_gs = c->tel.inv_gs;
     cudaSetDevice(c->device);
     uint64_t *g = &c->scratch_gen;
     if (c->rec.ensure(cap, g) || c->keys.ensure(cap, g) || c->keys_alt.ensure(cap, g) ||
@@ -535,6 +576,7 @@ clight_status finish(clight_ctx *c, int64_t cap, clight_stats *st, int64_t *n_hi
         st->guarded = (int64_t)h[CTR_STATS + ST_GUARDED];
         st->status = (int64_t)bits;
         st->cells = (int64_t)h[CTR_STATS + ST_CELLS];
+        st->cut = (int64_t)h[CTR_STATS + ST_CUT];
     }
     c->timed = true;
     if ((int64_t)cursor > cap) return CLIGHT_ERR_HIT_CAPACITY;
@@ -719,6 +761,13 @@ extern "C" clight_status clight_trace_adjoint(clight_ctx *c, const clight_segmen
         return CLIGHT_ERR_CUDA;
     DevPar P = c->par;
     P.n_showers = n_showers;
+    P.cut_tel = c->tel.tel;
+    P.cut_n_tel = c->tel.n_tel;
+    P.cut_tx = c->tel.mx; P.cut_ty = c->tel.my; P.cut_tz = c->tel.mz; P.cut_tr = c->tel.mr;
+    P.cut_cell_start = c->tel.cell_start; P.cut_cell_tel = c->tel.cell_tel;
+    P.cut_cabs = std::max(c->tel.cabs, (float)(std::fabs(P.cut_cx_d) + std::fabs(P.cut_cy_d) + std::fabs(P.cut_cz_d)));
+    P.cut_nx = c->tel.nx; P.cut_ny = c->tel.ny;
+    P.cut_gx0 = c->tel.gx0; P.cut_gy0 = c->tel.gy0; P.cut_inv_gs = c->tel.inv_gs;
     if (d_yield)
         CK(cudaMemsetAsync(d_yield, 0, sizeof(double) * (size_t)n_showers * c->tel.n_tel, s));
     // candidate pass: the rays near a telescope, compacted by the forward

@@ -55,6 +55,8 @@ struct DevTel {
     const uint8_t *clr;
     int cnx, cny, clr_bytes, pad3;  // cells, bytes (a multiple of 16)
     float cx0, cy0, inv_cgs, pad4;
+    float mx, my, mz, mr;           // mean centre, largest distance of a centre from it (rounded up)
+    float cabs;                     // largest |x| + |y| + |z| of a centre
 };
 constexpr float kClrQuantum = 0.25f;     // metres per unit of the clearance map
 constexpr int kClrMaxCells = 12288;      // 12 KB of shared memory per CTA
@@ -72,6 +74,23 @@ struct DevPar {
     int64_t seg_base;
     int n_showers, seg_bits, k_bits, pad;
     float bunch;
+    // angular segment cut (CLIGHT_CUT_*): cos of the angle, the centre, and
+    // for the per-telescope mode the telescope centres
+    int cut_mode, cut_n_tel;
+    float cut_cos;
+    double cut_cos_d;
+    float cut_cx, cut_cy, cut_cz;
+    double cut_cx_d, cut_cy_d, cut_cz_d;
+    const float4 *cut_tel;
+    // per-telescope mode: the array's mean centre and the largest distance of
+    // a telescope centre from it (rounded up), and the cut angle in radians
+    float cut_tx, cut_ty, cut_tz, cut_tr, cut_rad;
+    float cut_cabs;              // bound of |c|_1 over the cut's target centres
+    // and the telescope grid (CSR), to try the telescopes near the point
+    // where the step's line meets the array plane first
+    const int *cut_cell_start, *cut_cell_tel;
+    int cut_nx, cut_ny;
+    float cut_gx0, cut_gy0, cut_inv_gs;
 };
 
 struct DevOut {
@@ -85,7 +104,7 @@ struct DevOut {
 
 // Offsets inside DevOut::ctr.
 enum { CTR_WORK = 0, CTR_CURSOR = 1, CTR_STATS = 2, CTR_N = 16 };
-enum { ST_RAYS = 0, ST_ESCAPED, ST_UNDER, ST_TURNED, ST_REACHED, ST_HITS, ST_GUARDED, ST_STATUS, ST_CELLS };
+enum { ST_RAYS = 0, ST_ESCAPED, ST_UNDER, ST_TURNED, ST_REACHED, ST_HITS, ST_GUARDED, ST_STATUS, ST_CELLS, ST_CUT };
 
 // What the no-allocation entry point reads from a context (clight_api.cu).
 struct CtxView {

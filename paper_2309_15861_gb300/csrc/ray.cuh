@@ -184,6 +184,7 @@ template <class T, class P> struct Seg {
     uint32_t shower;
     int bad;             // 0 ok, else CLIGHT_ERR_* code
     int guarded;
+    int cut;             // 1: the angular cut removed the step's Cherenkov light
 };
 
 constexpr double kInvC = 3.3356409519815204;    // ns/m
@@ -234,6 +235,127 @@ __device__ __forceinline__ void yield_fp64(const clight_segment &s, const DevAtm
     *Nf = (P.fyield_d > 0.0 && s.dE > 0.0f && s.L > 0.0f) ? P.fyield_d * (double)s.dE : 0.0;
 }
 
+// ------------------------------------------------------------------ angular cut
+// Sec. 1.2.1 (optimisation): a step keeps its Cherenkov light when its
+// flight direction d is within the cut angle of the vector v from the step
+// midpoint m to a target centre C, i.e. d . v >= |v| cos(cut).  The binary64
+// form below is the decision (the oracle evaluates the same expression, in
+// the same order, without contraction); binary32 decides only when its
+// error bound leaves no doubt.
+__device__ __forceinline__ bool cut_keep_d(const double d[3], const double m[3], double cx, double cy, double cz,
+                                           double cosc)
+{
+    double vx = __dsub_rn(cx, m[0]), vy = __dsub_rn(cy, m[1]), vz = __dsub_rn(cz, m[2]);
+    double dot = __dadd_rn(__dadd_rn(__dmul_rn(d[0], vx), __dmul_rn(d[1], vy)), __dmul_rn(d[2], vz));
+    double nv = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)), __dmul_rn(vz, vz)));
+    return __dsub_rn(dot, __dmul_rn(nv, cosc)) >= 0.0;
+}
+
+// +1 keep, -1 drop, 0 not certain in binary32.  Without a square root: for
+// a cut below 90 degrees, d . v >= |v| cos <=> d . v >= 0 and
+// (d . v)^2 - cos^2 |v|^2 >= 0.  mabs bounds |m|_1 + |c|_1 (the absolute
+// error of v is below 1.2e-7 mabs).
+__device__ __forceinline__ int cut_test_f(float dx, float dy, float dz, float mx, float my, float mz, float cx,
+                                          float cy, float cz, float cos2, float mabs)
+{
+    float vx = cx - mx, vy = cy - my, vz = cz - mz;
+    float dot = dx * vx + dy * vy + dz * vz;
+    float v2 = vx * vx + vy * vy + vz * vz;
+    float f = dot * fabsf(dot) - cos2 * v2;          // sign(dot) (d.v)^2 - cos^2 |v|^2
+    float eb = 4.0e-6f * (v2 + mabs * mabs);
+    return f > eb ? 1 : (f < -eb ? -1 : 0);
+}
+
+// Does the step keep its Cherenkov light?  (dxf, dyf, dzf): the unit
+// direction in binary32.  The binary64 direction and midpoint (rounded as
+// the oracle rounds them) are formed only when binary32 is not certain.
+__device__ __forceinline__ void cut_exact_dm(const clight_segment &s, double d[3], double m[3])
+{
+    double n = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn((double)s.dx, (double)s.dx),
+                                              __dmul_rn((double)s.dy, (double)s.dy)),
+                                    __dmul_rn((double)s.dz, (double)s.dz)));
+    d[0] = __ddiv_rn((double)s.dx, n); d[1] = __ddiv_rn((double)s.dy, n); d[2] = __ddiv_rn((double)s.dz, n);
+    double hl = __dmul_rn(0.5, (double)s.L);
+    m[0] = __dadd_rn(s.x, __dmul_rn(hl, d[0]));
+    m[1] = __dadd_rn(s.y, __dmul_rn(hl, d[1]));
+    m[2] = __dadd_rn(s.z, __dmul_rn(hl, d[2]));
+}
+
+static __device__ __forceinline__ bool cut_keeps(const clight_segment &s, float dxf, float dyf, float dzf,
+                                              const DevPar &P)
+{
+    float hl = 0.5f * s.L;
+    float mx = (float)s.x + hl * dxf, my = (float)s.y + hl * dyf, mz = (float)s.z + hl * dzf;
+    const float cos2 = P.cut_cos * P.cut_cos;
+    float mabs = fabsf(mx) + fabsf(my) + fabsf(mz) + P.cut_cabs;
+    double d[3], m[3];
+    if (P.cut_mode == CLIGHT_CUT_CENTRE) {
+        int r = cut_test_f(dxf, dyf, dzf, mx, my, mz, P.cut_cx, P.cut_cy, P.cut_cz, cos2, mabs);
+        if (r != 0) return r > 0;
+        cut_exact_dm(s, d, m);
+        return cut_keep_d(d, m, P.cut_cx_d, P.cut_cy_d, P.cut_cz_d, P.cut_cos_d);
+    }
+    // the whole array first: seen from m, every telescope centre lies within
+    // rho = asin(r / |v0|) of the mean centre, so the smallest angle to a
+    // telescope is within [a0 - rho, a0 + rho] (2e-3 rad of margin)
+    {
+        float vx = P.cut_tx - mx, vy = P.cut_ty - my, vz = P.cut_tz - mz;
+        float nv = sqrtf(vx * vx + vy * vy + vz * vz);
+        if (nv > 2.0f * P.cut_tr) {
+            float iv = 1.0f / nv;
+            float ex = dxf - vx * iv, ey = dyf - vy * iv, ez = dzf - vz * iv;
+            float a0 = 2.0f * asinf(fminf(1.0f, 0.5f * sqrtf(ex * ex + ey * ey + ez * ez)));
+            float rho = asinf(P.cut_tr * iv);
+            if (a0 - rho > P.cut_rad + 2e-3f) return false;
+            if (a0 + rho < P.cut_rad - 2e-3f) return true;
+        }
+    }
+    // the telescopes around the point where the step's line meets the array
+    // plane are the likeliest to be inside the cone: a quick accept
+    if (dzf < -0.05f) {
+        float tp = (P.cut_tz - mz) / dzf;
+        if (tp > 0.0f) {
+            float px = mx + tp * dxf, py = my + tp * dyf;
+            int ix = (int)floorf((px - P.cut_gx0) * P.cut_inv_gs), iy = (int)floorf((py - P.cut_gy0) * P.cut_inv_gs);
+            for (int cy = max(iy - 1, 0); cy <= min(iy + 1, P.cut_ny - 1); ++cy)
+                for (int cx = max(ix - 1, 0); cx <= min(ix + 1, P.cut_nx - 1); ++cx) {
+                    int c = cy * P.cut_nx + cx;
+                    int b = __ldg(P.cut_cell_start + c), e = __ldg(P.cut_cell_start + c + 1);
+                    for (int q = b; q < e; ++q) {
+                        float4 t = __ldg(P.cut_tel + __ldg(P.cut_cell_tel + q));
+                        if (cut_test_f(dxf, dyf, dzf, mx, my, mz, t.x, t.y, t.z, cos2, mabs) > 0) return true;
+                    }
+                }
+        }
+    }
+    // all telescopes, four at a time
+    bool unsure = false;
+    int j = 0;
+    for (; j + 4 <= P.cut_n_tel; j += 4) {
+        float4 t0 = __ldg(P.cut_tel + j), t1 = __ldg(P.cut_tel + j + 1);
+        float4 t2 = __ldg(P.cut_tel + j + 2), t3 = __ldg(P.cut_tel + j + 3);
+        int r0 = cut_test_f(dxf, dyf, dzf, mx, my, mz, t0.x, t0.y, t0.z, cos2, mabs);
+        int r1 = cut_test_f(dxf, dyf, dzf, mx, my, mz, t1.x, t1.y, t1.z, cos2, mabs);
+        int r2 = cut_test_f(dxf, dyf, dzf, mx, my, mz, t2.x, t2.y, t2.z, cos2, mabs);
+        int r3 = cut_test_f(dxf, dyf, dzf, mx, my, mz, t3.x, t3.y, t3.z, cos2, mabs);
+        if (r0 > 0 || r1 > 0 || r2 > 0 || r3 > 0) return true;
+        if (r0 == 0 || r1 == 0 || r2 == 0 || r3 == 0) unsure = true;
+    }
+    for (; j < P.cut_n_tel; ++j) {
+        float4 t = __ldg(P.cut_tel + j);
+        int r = cut_test_f(dxf, dyf, dzf, mx, my, mz, t.x, t.y, t.z, cos2, mabs);
+        if (r > 0) return true;
+        if (r == 0) unsure = true;
+    }
+    if (!unsure) return false;
+    cut_exact_dm(s, d, m);
+    for (int j = 0; j < P.cut_n_tel; ++j) {
+        float4 t = __ldg(P.cut_tel + j);
+        if (cut_keep_d(d, m, (double)t.x, (double)t.y, (double)t.z, P.cut_cos_d)) return true;
+    }
+    return false;
+}
+
 template <class T, class P>
 __device__ __forceinline__ void make_frame(Seg<T, P> &g)
 {
@@ -257,6 +379,7 @@ __device__ void load_segment_f(const clight_segment &s, const DevAtm &A, const D
 {
     g.bad = 0;
     g.guarded = 0;
+    g.cut = 0;
     g.n_c = g.n_f = 0;
     g.w_c = g.w_f = 0.0f;
     g.shower = s.shower;
@@ -296,6 +419,10 @@ __device__ void load_segment_f(const clight_segment &s, const DevAtm &A, const D
     float dl = AtmT<float>::delta(A, hm);
     float eps = s.eps;
     float z2 = (float)s.charge * (float)s.charge;
+    if (P.cut_mode != CLIGHT_CUT_OFF && z2 > 0.0f && !cut_keeps(s, g.dx, g.dy, g.dz, P)) {
+        g.cut = 1;
+        z2 = 0.0f;
+    }
     // beta n - 1 = delta - eps - eps delta, kept as a small number
     float g1 = __fmaf_rn(-eps, dl, dl - eps);
     // error bound of g1 (delta known to ~1.5e-6 relative; generous factor)
@@ -330,6 +457,7 @@ __device__ void load_segment_f(const clight_segment &s, const DevAtm &A, const D
         if (ceilf(x - ex) != ceilf(x + ex)) fguard = true;
         else g.n_f = (uint32_t)ceilf(x);
     }
+    if (g.cut) guard = false;
     if (guard || fguard) {
         g.guarded = 1;
         double Ncd, sin2d, kapd, Nfd;
@@ -360,6 +488,7 @@ __device__ void load_segment_d(const clight_segment &s, const DevAtm &A, const D
 {
     g.bad = 0;
     g.guarded = 0;
+    g.cut = 0;
     g.n_c = g.n_f = 0;
     g.w_c = g.w_f = 0.0;
     g.shower = s.shower;
@@ -378,6 +507,10 @@ __device__ void load_segment_d(const clight_segment &s, const DevAtm &A, const D
     make_frame(g);
     double Nc, sin2, kap, Nf;
     yield_fp64<SPH>(s, A, P, g.dx, g.dy, g.dz, &Nc, &sin2, &kap, &Nf);
+    if (P.cut_mode != CLIGHT_CUT_OFF && s.charge != 0 && !cut_keeps(s, (float)g.dx, (float)g.dy, (float)g.dz, P)) {
+        g.cut = 1;
+        Nc = 0.0;
+    }
     g.sin_tc = sqrt(sin2);
     g.kappa = kap;
     if (Nc > 0.0) {

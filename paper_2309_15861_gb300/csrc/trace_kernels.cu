@@ -67,6 +67,7 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
         clr = reinterpret_cast<const uint8_t *>(dst);
     }
     uint32_t c_rays = 0, c_esc = 0, c_under = 0, c_turn = 0, c_reach = 0, c_hits = 0, c_guard = 0, c_cells = 0;
+    uint32_t c_cut = 0;
     unsigned status_bits = 0;
     for (;;) {
         unsigned long long grp = 0;
@@ -87,6 +88,7 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
             load_segment_f<SPH>(s, A, Pp, g);
             if (g.bad) status_bits |= 1u << g.bad;
             c_guard += g.guarded;
+            c_cut += g.cut;
             nb = g.n_c + g.n_f;
             if (nb < g.n_c || nb > 0x7fffffffu) { status_bits |= 1u << CLIGHT_ERR_LIMIT; nb = 0; }
             // order the warp's segments by altitude (500 m bins), so that the
@@ -222,9 +224,9 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
         __syncwarp();
     }
     // ---- statistics: one atomic per warp and counter
-    uint32_t vals[9] = {c_rays, c_esc, c_under, c_turn, c_reach, c_hits, c_guard, 0u, c_cells};
+    uint32_t vals[10] = {c_rays, c_esc, c_under, c_turn, c_reach, c_hits, c_guard, 0u, c_cells, c_cut};
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
+    for (int i = 0; i < 10; ++i) {
         if (i == ST_STATUS) continue;
         uint32_t v = vals[i];
 #pragma unroll
@@ -251,6 +253,7 @@ k_trace_fp64(const clight_segment *__restrict__ segs, int64_t n_segs, const __gr
     Seg<double, double> g;
     load_segment_d<SPH>(segs[i], A, Pp, g);
     uint32_t c_rays = 0, c_esc = 0, c_under = 0, c_turn = 0, c_reach = 0, c_hits = 0, c_cells = 0;
+    uint32_t c_cut = g.cut;
     if (g.bad) {
         status_bits |= 1u << g.bad;
     } else {
@@ -267,8 +270,8 @@ k_trace_fp64(const clight_segment *__restrict__ segs, int64_t n_segs, const __gr
             c_hits += hit_test<double, double, false>(o, i, seg_global, k, g.shower, A, Tl, Pp, O, status_bits);
         }
     }
-    uint32_t vals[9] = {c_rays, c_esc, c_under, c_turn, c_reach, c_hits, 0u, 0u, c_cells};
-    for (int q = 0; q < 9; ++q)
+    uint32_t vals[10] = {c_rays, c_esc, c_under, c_turn, c_reach, c_hits, 0u, 0u, c_cells, c_cut};
+    for (int q = 0; q < 10; ++q)
         if (vals[q] && q != ST_STATUS) atomicAdd(O.ctr + CTR_STATS + q, (unsigned long long)vals[q]);
     if (status_bits) atomicOr(O.ctr + CTR_STATS + ST_STATUS, (unsigned long long)status_bits);
 }
@@ -433,6 +436,7 @@ extern "C" clight_status clight_trace_noalloc(clight_ctx *ctx, const clight_segm
         h_stats->guarded = (int64_t)h[CTR_STATS + ST_GUARDED];
         h_stats->status = (int64_t)bits;
         h_stats->cells = (int64_t)h[CTR_STATS + ST_CELLS];
+        h_stats->cut = (int64_t)h[CTR_STATS + ST_CUT];
     }
     if ((int64_t)h[CTR_CURSOR] > hit_capacity) return CLIGHT_ERR_HIT_CAPACITY;
     if (bits & (1ull << CLIGHT_ERR_BAD_SEGMENT)) return CLIGHT_ERR_BAD_SEGMENT;

@@ -160,6 +160,15 @@ class Params:
     fluor_yield: float = 0.0      # photons per MeV deposited
     fl_lambda1: float = 340.0     # nm, fluorescence band
     fl_lambda2: float = 450.0
+    cut_mode: int = 0             # Cherenkov angular cut: 0 off, 1 array centre, 2 each telescope
+    cut_deg: float = 6.0          # cut angle, degrees
+    cut_centre: tuple = None      # array centre for cut_mode 1 (see array_centre)
+
+
+def array_centre(tels: np.ndarray) -> tuple:
+    """Mean of the telescope centres (the 'experiment centre' of the angular cut)."""
+    return (float(np.mean(tels["x"].astype(np.float64))), float(np.mean(tels["y"].astype(np.float64))),
+            float(np.mean(tels["z"].astype(np.float64))))
 
 
 def telescope_grid(nx, ny, spacing, R=6.0, z=2000.0):

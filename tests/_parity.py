@@ -32,7 +32,11 @@ def _key(h):
 
 def weight_tolerance(segs, ref, atm, par, seg_base=0):
     """Per-hit weight tolerance of the oracle hits (see the module docstring)."""
+    import dataclasses
     import oracle as O
+    # the angular cut only removes whole steps: the kept steps' yields are the uncut ones
+    if getattr(par, "cut_mode", 0):
+        par = dataclasses.replace(par, cut_mode=0)
     tol = np.full(len(ref), TOL_W)
     cache = {}
     for i, h in enumerate(ref):

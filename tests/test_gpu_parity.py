@@ -4,6 +4,8 @@ Every case runs the same seeded synthetic inputs through both and compares
 hits element by element (tests/_parity.py states the tolerances), plus the
 per-telescope counts, photon sums and ray statistics.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -36,7 +38,7 @@ def _oracle(w, seg_base=0, segs=None):
 
 
 def _dperp_fn(w):
-    nbc, nbf = O.bunch_counts(w.segments, w.atmosphere, w.params)
+    nbc, nbf = O.bunch_counts(w.segments, w.atmosphere, w.params, w.telescopes)
 
     def f(h):
         out = O.eval_rays(w.segments, h["seg"], h["k"], h["tel"], nbc, nbf, w.atmosphere,
@@ -113,6 +115,19 @@ def test_batch_with_fluorescence(ctx):
     w = I.batch_showers(n_showers=6, seed=9, scale=2e-3)
     rep, gst, rst = _check(ctx, w)
     assert w.n_showers == 6 and rep["n_common"] > 0
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_angular_cut(ctx, mode):
+    """Sec. 1.2.1 optimisation: the same steps lose their Cherenkov light on
+    both sides (mode 1: array centre, mode 2: each telescope)."""
+    w = I.workload_shower_1tev(n=20_000, seed=37) if mode == 1 else I.workload_inclined(n=10_000, seed=41)
+    w.params = dataclasses.replace(w.params, cut_mode=mode, cut_deg=6.0, cut_centre=I.array_centre(w.telescopes))
+    rep, gst, rst = _check(ctx, w)
+    assert gst["cut"] > 0 and rep["n_common"] > 0
+    # the fp64 plain path makes the same decisions
+    rep64, gst64, _ = _check(ctx, w, fp64=True)
+    assert gst64["cut"] == gst["cut"]
 
 
 def test_fp64_plain_path(ctx):

@@ -487,3 +487,64 @@ def test_soft_yield_limits():
     y40 = O.soft_yield(w.segments, nbc, nbf, w.atmosphere, w.telescopes, w.params, s=0.5, W=40.0)
     np.testing.assert_allclose(y20, y40, rtol=1e-12, atol=1e-15 * y40.max())
     assert y20.sum() > 0
+
+
+# ---------------------------------------------------------------- angular cut
+def _aimed_steps(targets_and_angles, z=10000.0):
+    """One vertical-ish step per (target point, extra angle): the step at
+    (0, 0, z) points at the target, then tilts by the extra angle about y."""
+    s = np.zeros(len(targets_and_angles), dtype=I.SEG_DTYPE)
+    for i, (tgt, extra) in enumerate(targets_and_angles):
+        v = np.asarray(tgt, dtype=np.float64) - np.array([0.0, 0.0, z])
+        v /= np.linalg.norm(v)
+        a = math.radians(extra)
+        R = np.array([[math.cos(a), 0, math.sin(a)], [0, 1, 0], [-math.sin(a), 0, math.cos(a)]])
+        d = R @ v
+        s[i]["x"], s[i]["y"], s[i]["z"] = 0.0, 0.0, z
+        s[i]["dx"], s[i]["dy"], s[i]["dz"] = d
+    s["L"] = 1e-3          # the midpoint is the start to 1e-4 rad
+    s["eps"] = 1e-6
+    s["charge"] = -1
+    return s
+
+
+def test_angular_cut_decisions_against_brute_force_angles():
+    """Sec. 1.2.1: Cherenkov light of a step survives when its direction is
+    within the cut angle of the direction to the array centre (mode 1) or to
+    some telescope (mode 2).  Angles by arccos, away from the boundary."""
+    atm = I.atmosphere_layered()
+    tels = I.telescope_grid(3, 3, 300.0, z=atm.h_obs)
+    centre = I.array_centre(tels)
+    far = (tels["x"][0], tels["y"][0], tels["z"][0])            # a corner telescope
+    cases = [(centre, 0.0), (centre, 5.0), (centre, 7.0), (centre, -5.5), (centre, 20.0),
+             (far, 1.0), (far, 5.0), (far, 8.0)]
+    segs = _aimed_steps(cases)
+    for mode in (1, 2):
+        par = I.Params(bunch=1.0, cut_mode=mode, cut_deg=6.0, cut_centre=centre)
+        for s, (tgt, extra) in zip(segs, cases):
+            d = np.array([s["dx"], s["dy"], s["dz"]], dtype=np.float64)
+            d /= np.linalg.norm(d)
+            m = np.array([s["x"], s["y"], s["z"]]) + 0.5 * float(s["L"]) * d
+            targets = [np.array(centre)] if mode == 1 else [np.array([t["x"], t["y"], t["z"]], float) for t in tels]
+            ang = min(math.degrees(math.acos(np.clip(d @ (c - m) / np.linalg.norm(c - m), -1, 1))) for c in targets)
+            assert abs(ang - 6.0) > 0.05
+            y = O.yield_of(s, atm, par, tels)
+            y0 = O.yield_of(s, atm, I.Params(bunch=1.0))
+            assert y0["n_c"] > 0
+            assert (y["n_c"] > 0) == (ang < 6.0), (mode, tgt, extra, ang)
+            if y["n_c"] > 0:
+                assert y["n_c"] == y0["n_c"] and y["w_c"] == y0["w_c"]
+
+
+def test_angular_cut_keeps_a_subset_of_the_hits():
+    """With the cut the oracle's hits are exactly the uncut hits of the kept
+    steps (same keys, same values); fluorescence is untouched."""
+    w = I.workload_shower_1tev(n=4000, seed=21)
+    h0, c0, s0, st0 = O.trace(w.segments, w.atmosphere, w.telescopes, w.params)
+    par = I.Params(**{**w.params.__dict__, "cut_mode": 1, "cut_deg": 6.0,
+                      "cut_centre": I.array_centre(w.telescopes)})
+    h1, c1, s1, st1 = O.trace(w.segments, w.atmosphere, w.telescopes, par)
+    assert st1["rays"] < st0["rays"] and len(h1) > 0
+    nc1, _ = O.bunch_counts(w.segments, w.atmosphere, par)
+    kept = nc1[h0["seg"]] > 0
+    np.testing.assert_array_equal(h1, h0[kept])
