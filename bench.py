@@ -77,6 +77,15 @@ class Clocks:
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (FileNotFoundError, OSError):
             self.proc = None
+            return
+        # nvidia-smi's start-up holds the driver for a few hundred ms: let it
+        # reach its first sample before the timed region opens
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < 10.0 and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
+        time.sleep(0.2)
 
     def stop(self):
         if self.proc is None:
