@@ -219,6 +219,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--fl-beaming", action="store_true",
+                    help="beam the fluorescence toward the array (Sec. 1.1.1); the batch workload's default is "
+                         "isotropic emission")
     ap.add_argument("--cut-study", action="store_true",
                     help="also time the Cherenkov angular cut (array centre and per telescope, 6 deg) and "
                          "report its speedup and photon loss against the uncut step")
@@ -252,6 +255,10 @@ def main():
     t_gen = time.perf_counter()
     w = make_workload(args.workload, args.n_segs, rank, args.scale)
     t_gen = time.perf_counter() - t_gen
+    if args.fl_beaming:
+        import dataclasses
+        c, r = I.beam_cone(w.telescopes)
+        w.params = dataclasses.replace(w.params, fl_beaming=1, beam_centre=c, beam_radius=r)
     ns = w.n_showers
     ctx = G.Context(local)
     extra = dict(use_graph=1, precision=args.precision, block=args.block, ctas_per_sm=args.ctas_per_sm,
@@ -438,6 +445,7 @@ def main():
                        "precision": ["float-pair", "fp64-guard"][args.precision], "graph": True,
                        "l2": f"inputs ({n * 64 / 1e9:.2f} GB) larger than L2; no flush",
                        "parallelism": f"replicas x{world}", "generation_s": round(t_gen, 1),
+                       "fl_beaming": bool(args.fl_beaming),
                        "step": "trace + adjoint" if adj is not None else "trace"},
             "roofline": roof, "fp64_plain": fp64, "e2e": e2e, "cpu_baseline": cpu,
             "clocks": ck, "gpu_launches": launches_per_step * args.steps,

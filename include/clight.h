@@ -118,6 +118,16 @@ typedef struct {
     int32_t cut_pad;
     double cut_deg;                 /* cut angle in degrees, (0, 180) (0 = 6) */
     double cut_centre[3];           /* array centre for CLIGHT_CUT_CENTRE, m, local frame */
+    /* Fluorescence beaming (Sec. 1.1.1, optimisation): when on, a step whose
+     * midpoint m lies at D = |C - m| >= 2 beam_radius from beam_centre C emits
+     * its fluorescence only into the cone about C - m of half-angle
+     * alpha = asin(beam_radius / D) + 5e-3 + L / D, uniformly in solid angle,
+     * and its photon number is scaled by the cone's share sin^2(alpha / 2).
+     * beam_radius must hold every telescope sphere (centre distance + R). */
+    int32_t fl_beaming;             /* 0 off, 1 on */
+    int32_t beam_pad;
+    double beam_centre[3];          /* m, local frame */
+    double beam_radius;             /* m */
 } clight_params;
 
 /* One telescope hit (48 bytes). */

@@ -54,7 +54,8 @@ class _Par(C.Structure):
                 ("seed", C.c_uint32), ("stream", C.c_uint32), ("fluor_yield", C.c_double),
                 ("fl_lambda1", C.c_double), ("fl_lambda2", C.c_double),
                 ("seg_base", C.c_int64), ("cut_mode", C.c_int32), ("cut_deg", C.c_double),
-                ("cut_centre", C.c_double * 3), ("cut_tels", C.c_void_p), ("cut_n_tel", C.c_int32)]
+                ("cut_centre", C.c_double * 3), ("cut_tels", C.c_void_p), ("cut_n_tel", C.c_int32),
+                ("fl_beaming", C.c_int32), ("beam_centre", C.c_double * 3), ("beam_radius", C.c_double)]
 
 
 _lib = None
@@ -132,6 +133,11 @@ def par_struct(p, seg_base: int = 0, tels=None) -> _Par:
             raise ValueError("the per-telescope cut needs the telescopes")
         s.cut_tels = tels.ctypes.data
         s.cut_n_tel = len(tels)
+    if getattr(p, "fl_beaming", 0):
+        s.fl_beaming = 1
+        for i in range(3):
+            s.beam_centre[i] = float(p.beam_centre[i])
+        s.beam_radius = float(p.beam_radius)
     return s
 
 

@@ -126,6 +126,32 @@ static int cut_keeps(const double d[3], const double m[3], const or_params *p)
     return 0;
 }
 
+/* ------------------------------------------------------------------------
+ * Fluorescence beaming (Sec. 1.1.1, optimisation): instead of isotropic
+ * emission, a step emits into the cone from its midpoint m towards the
+ * array centre C that holds every telescope (radius R_b about C), and its
+ * photon number is scaled by the cone's solid-angle share.  Reading of the
+ * cone: beaming only when D = |C - m| >= 2 R_b; half-angle
+ * alpha = asin(R_b / D) + 5e-3 (refraction) + L / D (emission anywhere on
+ * the step); share (1 - cos alpha) / 2 = sin^2(alpha / 2).
+ * Returns 1 and the axis u and 1 - cos(alpha) when the step is beamed.
+ * ---------------------------------------------------------------------- */
+static int beam_cone(const or_segment *s, const double d[3], const or_params *p, double u[3], double *omc)
+{
+    if (!p->fl_beaming) return 0;
+    double m[3] = {s->x + 0.5 * s->L * d[0], s->y + 0.5 * s->L * d[1], s->z + 0.5 * s->L * d[2]};
+    double v[3] = {p->beam_centre[0] - m[0], p->beam_centre[1] - m[1], p->beam_centre[2] - m[2]};
+    double D2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    double R = p->beam_radius;
+    if (!(D2 >= 4.0 * R * R)) return 0;
+    double D = sqrt(D2);
+    double alpha = asin(R / D) + 5e-3 + (double)s->L / D;
+    double sh = sin(0.5 * alpha);
+    *omc = 2.0 * sh * sh;
+    u[0] = v[0] / D; u[1] = v[1] / D; u[2] = v[2] / D;
+    return 1;
+}
+
 void or_yield(const or_segment *s, const or_atmosphere *a, const or_params *p, double out[10])
 {
     double d[3];
@@ -151,6 +177,8 @@ void or_yield(const or_segment *s, const or_atmosphere *a, const or_params *p, d
     double n_f = 0, w_f = 0, Nf = 0;
     if (p->fluor_yield > 0 && s->dE > 0 && s->L > 0) {
         Nf = p->fluor_yield * (double)s->dE;
+        double u[3], omc;
+        if (beam_cone(s, d, p, u, &omc)) Nf *= 0.5 * omc;
         n_f = ceil(Nf / p->bunch);
         w_f = n_f > 0 ? Nf / n_f : 0.0;
     }
@@ -217,10 +245,23 @@ static void photon_of(const or_segment *s, int64_t seg_index, uint32_t k, const 
         w = y->w_c;
     } else {
         lambda = p->fl_lambda1 + u0 * (p->fl_lambda2 - p->fl_lambda1);
-        double ct = 2.0 * u3 - 1.0;
-        double st = sqrt((1.0 - ct) * (1.0 + ct));
-        double ph = 2.0 * OR_PI * u2;
-        dg[0] = st * cos(ph); dg[1] = st * sin(ph); dg[2] = ct;
+        double u[3], omc;
+        if (beam_cone(s, d, p, u, &omc)) {
+            /* uniform in solid angle inside the cone about u, rotated like the
+             * Cherenkov cone (M_Rod of the axis, Sec. 1.2.1) */
+            double ct = 1.0 - u3 * omc;
+            double st = sqrt((1.0 - ct) * (1.0 + ct));
+            double ph = 2.0 * OR_PI * u2;
+            double pv[3] = {cos(ph) * st, sin(ph) * st, -ct};
+            double M[9];
+            or_rotation(u, M);
+            for (int i = 0; i < 3; i++) dg[i] = M[3 * i] * pv[0] + M[3 * i + 1] * pv[1] + M[3 * i + 2] * pv[2];
+        } else {
+            double ct = 2.0 * u3 - 1.0;
+            double st = sqrt((1.0 - ct) * (1.0 + ct));
+            double ph = 2.0 * OR_PI * u2;
+            dg[0] = st * cos(ph); dg[1] = st * sin(ph); dg[2] = ct;
+        }
         w = y->w_f;
     }
     double ell = u1 * (double)s->L;

@@ -65,6 +65,10 @@ typedef struct {
     double cut_centre[3];         /* mode 1 */
     const or_telescope *cut_tels; /* mode 2 */
     int32_t cut_n_tel;
+    /* fluorescence beaming (Sec. 1.1.1, optimisation) */
+    int32_t fl_beaming;
+    double beam_centre[3];
+    double beam_radius;
 } or_params;
 
 typedef struct {            /* oracle output record, all FP64 */

@@ -52,7 +52,8 @@ class Params(C.Structure):
                 ("precision", C.c_int32), ("block", C.c_int32), ("ctas_per_sm", C.c_int32),
                 ("use_graph", C.c_int32), ("cell_width", C.c_float), ("key_bunch_bits", C.c_int32),
                 ("cut_mode", C.c_int32), ("cut_pad", C.c_int32), ("cut_deg", C.c_double),
-                ("cut_centre", C.c_double * 3)]
+                ("cut_centre", C.c_double * 3), ("fl_beaming", C.c_int32), ("beam_pad", C.c_int32),
+                ("beam_centre", C.c_double * 3), ("beam_radius", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -131,6 +132,11 @@ def params_struct(p: inputs.Params, **kw) -> Params:
             raise ValueError("the centre cut needs Params.cut_centre")
         for i in range(3):
             s.cut_centre[i] = float(p.cut_centre[i])
+    if getattr(p, "fl_beaming", 0):
+        s.fl_beaming = 1
+        for i in range(3):
+            s.beam_centre[i] = float(p.beam_centre[i])
+        s.beam_radius = float(p.beam_radius)
     for k, v in kw.items():
         setattr(s, k, v)
     return s

@@ -209,13 +209,21 @@ __device__ void tangent_ray(const Seg<float, df> &g, const clight_segment &s, in
         w = Nc / (float)g.n_c;
     } else {
         lam = Pp.fl1 + u0 * Pp.fdl;
-        float cz = 2.0f * u3 - 1.0f;
-        float sz = sqrtf((1.0f - cz) * (1.0f + cz));
         float sp, cp;
         sincospif(2.0f * u2, &sp, &cp);
-        dgx = dc<NP>(sz * cp);
-        dgy = dc<NP>(sz * sp);
-        dgz = dc<NP>(cz);
+        float fx, fy, fz;
+        if (g.bomc > 0.0f) {
+            cone_direction<float>(g.bux, g.buy, g.buz, u3 * g.bomc, sp, cp, fx, fy, fz);
+        } else {
+            fz = 2.0f * u3 - 1.0f;
+            float sz = sqrtf((1.0f - fz) * (1.0f + fz));
+            fx = sz * cp;
+            fy = sz * sp;
+        }
+        // the emission geometry does not depend on the atmosphere
+        dgx = dc<NP>(fx);
+        dgy = dc<NP>(fy);
+        dgz = dc<NP>(fz);
         w = dc<NP>(g.w_f);
     }
     float ell = u1 * g.L;

@@ -413,6 +413,11 @@ clight_status clight_set_params(clight_ctx *c, const clight_params *p)
                                           !std::isfinite(p->cut_centre[0]) || !std::isfinite(p->cut_centre[1]) ||
                                           !std::isfinite(p->cut_centre[2])))
         return CLIGHT_ERR_ARG;
+    if (p->fl_beaming != 0 && p->fl_beaming != 1) return CLIGHT_ERR_ARG;
+    if (p->fl_beaming && (!(p->beam_radius > 0) || !std::isfinite(p->beam_radius) ||
+                          !std::isfinite(p->beam_centre[0]) || !std::isfinite(p->beam_centre[1]) ||
+                          !std::isfinite(p->beam_centre[2])))
+        return CLIGHT_ERR_ARG;
     float old_cw = c->upar.cell_width;
     c->upar = *p;
     DevPar &P = c->par;
@@ -442,6 +447,11 @@ clight_status clight_set_params(clight_ctx *c, const clight_params *p)
     P.cut_cx_d = p->cut_centre[0]; P.cut_cy_d = p->cut_centre[1]; P.cut_cz_d = p->cut_centre[2];
     P.cut_cx = (float)P.cut_cx_d; P.cut_cy = (float)P.cut_cy_d; P.cut_cz = (float)P.cut_cz_d;
     P.cut_rad = (float)(cut_deg * (3.14159265358979323846 / 180.0));
+    P.beam = p->fl_beaming;
+    P.beam_cx_d = p->beam_centre[0]; P.beam_cy_d = p->beam_centre[1]; P.beam_cz_d = p->beam_centre[2];
+    P.beam_r_d = p->beam_radius;
+    P.beam_cx = (float)P.beam_cx_d; P.beam_cy = (float)P.beam_cy_d; P.beam_cz = (float)P.beam_cz_d;
+    P.beam_r = (float)P.beam_r_d;
     ++c->version;
     if (c->atm_set && p->cell_width != old_cw) {
         clight_atmosphere a = c->uatm;

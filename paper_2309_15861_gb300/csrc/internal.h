@@ -59,7 +59,7 @@ struct DevTel {
     float cabs;                     // largest |x| + |y| + |z| of a centre
 };
 constexpr float kClrQuantum = 0.25f;     // metres per unit of the clearance map
-constexpr int kClrMaxCells = 12288;      // 12 KB of shared memory per CTA
+constexpr int kClrMaxCells = 10240;      // 10 KB of shared memory per CTA
 
 struct DevPar {
     float band, inv_bunch;       // 2 pi alpha (1/l1 - 1/l2) [1/m], 1/B
@@ -91,6 +91,10 @@ struct DevPar {
     const int *cut_cell_start, *cut_cell_tel;
     int cut_nx, cut_ny;
     float cut_gx0, cut_gy0, cut_inv_gs;
+    // fluorescence beaming: on/off, cone centre and radius
+    int beam;
+    float beam_cx, beam_cy, beam_cz, beam_r;
+    double beam_cx_d, beam_cy_d, beam_cz_d, beam_r_d;
 };
 
 struct DevOut {

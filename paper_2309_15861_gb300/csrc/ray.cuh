@@ -185,6 +185,8 @@ template <class T, class P> struct Seg {
     int bad;             // 0 ok, else CLIGHT_ERR_* code
     int guarded;
     int cut;             // 1: the angular cut removed the step's Cherenkov light
+    T bux, buy, buz;     // beamed fluorescence: cone axis
+    T bomc;              // and 1 - cos(half-angle); 0 = isotropic emission
 };
 
 constexpr double kInvC = 3.3356409519815204;    // ns/m
@@ -200,6 +202,82 @@ __device__ __forceinline__ bool segment_ok(const clight_segment &s, const DevPar
     return finite_d(s.x) && finite_d(s.y) && finite_d(s.z) && finite_d(s.t0) && finite_f(s.dx) &&
            finite_f(s.dy) && finite_f(s.dz) && finite_f(s.L) && finite_f(s.eps) && finite_f(s.dE) &&
            s.L >= 0.0f && s.eps >= 0.0f && s.eps < 1.0f && (int)s.shower < P.n_showers && s.shower < 0x7fffffffu;
+}
+
+// ------------------------------------------------------------------ fluorescence beaming
+// Sec. 1.1.1 (optimisation): a step whose midpoint m lies at D = |C - m| >=
+// 2 R_b from the array centre C emits its fluorescence into the cone about
+// C - m of half-angle alpha = asin(R_b / D) + 5e-3 + L / D, uniformly in
+// solid angle, with its photon number scaled by sin^2(alpha / 2).
+// binary64: the decision and the cone as the oracle forms them.
+__device__ __forceinline__ int beam_cone_d(double mx, double my, double mz, double L, const DevPar &P, double &ux,
+                                           double &uy, double &uz, double &omc)
+{
+    double vx = __dsub_rn(P.beam_cx_d, mx), vy = __dsub_rn(P.beam_cy_d, my), vz = __dsub_rn(P.beam_cz_d, mz);
+    double D2 = __dadd_rn(__dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)), __dmul_rn(vz, vz));
+    double R = P.beam_r_d;
+    if (!(D2 >= __dmul_rn(__dmul_rn(4.0, R), R))) return 0;
+    double D = __dsqrt_rn(D2);
+    double a = asin(R / D) + 5e-3 + L / D;
+    double sh = sin(0.5 * a);
+    omc = 2.0 * sh * sh;
+    ux = vx / D; uy = vy / D; uz = vz / D;
+    return 1;
+}
+
+// binary32, with the switch decided in binary64 where binary32 is not certain
+template <class P>
+__device__ __forceinline__ int beam_cone_t(const Seg<float, P> &g, const DevPar &Pp, float &ux, float &uy, float &uz,
+                                           float &omc)
+{
+    float hl = 0.5f * g.L;
+    float mx = p_f(g.x0) + hl * g.dx, my = p_f(g.y0) + hl * g.dy, mz = p_f(g.z0) + hl * g.dz;
+    float vx = Pp.beam_cx - mx, vy = Pp.beam_cy - my, vz = Pp.beam_cz - mz;
+    float D2 = vx * vx + vy * vy + vz * vz;
+    float R = Pp.beam_r, F = 4.0f * R * R;
+    if (fabsf(D2 - F) <= 1.0e-5f * (D2 + F)) {
+        double dx = (double)g.dx + g.lx, dy = (double)g.dy + g.ly, dz = (double)g.dz + g.lz;
+        double hd = 0.5 * (double)g.L, a, b, c, o;
+        if (!beam_cone_d(p_d(g.x0) + hd * dx, p_d(g.y0) + hd * dy, p_d(g.z0) + hd * dz, (double)g.L, Pp, a, b, c, o))
+            return 0;
+    } else if (!(D2 > F)) {
+        return 0;
+    }
+    float D = sqrtf(D2), iD = 1.0f / D;
+    float a = asinf(R * iD) + 5.0e-3f + g.L * iD;
+    float sh = sinf(0.5f * a);
+    omc = 2.0f * sh * sh;
+    ux = vx * iD; uy = vy * iD; uz = vz * iD;
+    return 1;
+}
+__device__ __forceinline__ int beam_cone_t(const Seg<double, double> &g, const DevPar &Pp, double &ux, double &uy,
+                                           double &uz, double &omc)
+{
+    double hd = 0.5 * g.L;
+    return beam_cone_d(g.x0 + hd * g.dx, g.y0 + hd * g.dy, g.z0 + hd * g.dz, g.L, Pp, ux, uy, uz, omc);
+}
+
+// A direction at polar angle acos(ct) and azimuth 2 pi u about the axis u,
+// rotated like the Cherenkov cone (M_Rod of the axis, Sec. 1.2.1).
+template <class T>
+__device__ __forceinline__ void cone_direction(T ux, T uy, T uz, T omct, T sp, T cp, T &x, T &y, T &z)
+{
+    // omct = 1 - cos(theta), small near the axis: no cancellation in sin(theta)
+    T ct = (T)1 - omct;
+    T ax = ux, ay = uy, az = uz - (T)1;
+    T na2 = ax * ax + ay * ay + az * az;
+    if (na2 > (T)0) {
+        T inv = (T)1 / sqrt(na2);
+        ax *= inv; ay *= inv; az *= inv;
+    } else {
+        ax = (T)1; ay = (T)0; az = (T)0;
+    }
+    T st = sqrt(omct * ((T)2 - omct));
+    T e1x = (T)2 * ax * ax - (T)1, e1y = (T)2 * ax * ay, e1z = (T)2 * ax * az;
+    T e2x = (T)2 * ay * ax, e2y = (T)2 * ay * ay - (T)1, e2z = (T)2 * ay * az;
+    x = ct * ux + st * (cp * e1x + sp * e2x);
+    y = ct * uy + st * (cp * e1y + sp * e2y);
+    z = ct * uz + st * (cp * e1z + sp * e2z);
 }
 
 // Yield and bunch count in binary64 (the plain path, and the guard of the
@@ -233,6 +311,10 @@ __device__ __forceinline__ void yield_fp64(const clight_segment &s, const DevAtm
         *Nc = P.band_d * z2 * (*sin2) * (double)s.L;
     }
     *Nf = (P.fyield_d > 0.0 && s.dE > 0.0f && s.L > 0.0f) ? P.fyield_d * (double)s.dE : 0.0;
+    if (*Nf > 0.0 && P.beam) {
+        double a, b, c, omc;
+        if (beam_cone_d(xm, ym, zm, (double)s.L, P, a, b, c, omc)) *Nf *= 0.5 * omc;
+    }
 }
 
 // ------------------------------------------------------------------ angular cut
@@ -281,9 +363,11 @@ __device__ __forceinline__ void cut_exact_dm(const clight_segment &s, double d[3
     m[2] = __dadd_rn(s.z, __dmul_rn(hl, d[2]));
 }
 
-static __device__ __forceinline__ bool cut_keeps(const clight_segment &s, float dxf, float dyf, float dzf,
-                                              const DevPar &P)
+static __device__ __noinline__ bool cut_keeps_v(double sx, double sy, double sz, float sL, float sdx, float sdy,
+                                                float sdz, float dxf, float dyf, float dzf, const DevPar &P)
 {
+    clight_segment s;
+    s.x = sx; s.y = sy; s.z = sz; s.L = sL; s.dx = sdx; s.dy = sdy; s.dz = sdz;
     float hl = 0.5f * s.L;
     float mx = (float)s.x + hl * dxf, my = (float)s.y + hl * dyf, mz = (float)s.z + hl * dzf;
     const float cos2 = P.cut_cos * P.cut_cos;
@@ -374,7 +458,9 @@ __device__ __forceinline__ void make_frame(Seg<T, P> &g)
 }
 
 // binary32 segment set-up with the binary64 guard on the integer bunch count.
-template <bool SPH>
+// EXT = false drops the optional angular cut and fluorescence beaming from
+// the compiled code (the launcher picks it when neither is on).
+template <bool SPH, bool EXT = true>
 __device__ void load_segment_f(const clight_segment &s, const DevAtm &A, const DevPar &P, Seg<float, df> &g)
 {
     g.bad = 0;
@@ -384,6 +470,7 @@ __device__ void load_segment_f(const clight_segment &s, const DevAtm &A, const D
     g.w_c = g.w_f = 0.0f;
     g.shower = s.shower;
     g.h_mid = 0.0f;
+    g.bux = g.buy = g.buz = g.bomc = 0.0f;
     float n2 = s.dx * s.dx + s.dy * s.dy + s.dz * s.dz;
     if (!segment_ok(s, P) || !(n2 > 0.0f)) {
         g.bad = CLIGHT_ERR_BAD_SEGMENT;
@@ -419,7 +506,8 @@ __device__ void load_segment_f(const clight_segment &s, const DevAtm &A, const D
     float dl = AtmT<float>::delta(A, hm);
     float eps = s.eps;
     float z2 = (float)s.charge * (float)s.charge;
-    if (P.cut_mode != CLIGHT_CUT_OFF && z2 > 0.0f && !cut_keeps(s, g.dx, g.dy, g.dz, P)) {
+    if (EXT && P.cut_mode != CLIGHT_CUT_OFF && z2 > 0.0f &&
+        !cut_keeps_v(s.x, s.y, s.z, s.L, s.dx, s.dy, s.dz, g.dx, g.dy, g.dz, P)) {
         g.cut = 1;
         z2 = 0.0f;
     }
@@ -452,8 +540,13 @@ __device__ void load_segment_f(const clight_segment &s, const DevAtm &A, const D
     bool fguard = false;
     if (P.fyield > 0.0f && s.dE > 0.0f && s.L > 0.0f) {
         Nf = P.fyield * s.dE;
+        float rel = 1.0e-6f;
+        if (EXT && P.beam && beam_cone_t(g, P, g.bux, g.buy, g.buz, g.bomc)) {
+            Nf *= 0.5f * g.bomc;
+            rel = 1.0e-5f;                   // asin, sin and the geometry in binary32
+        }
         float x = Nf * P.inv_bunch;
-        float ex = x * 1.0e-6f + 1.0e-7f;
+        float ex = x * rel + 1.0e-7f;
         if (ceilf(x - ex) != ceilf(x + ex)) fguard = true;
         else g.n_f = (uint32_t)ceilf(x);
     }
@@ -492,6 +585,7 @@ __device__ void load_segment_d(const clight_segment &s, const DevAtm &A, const D
     g.n_c = g.n_f = 0;
     g.w_c = g.w_f = 0.0;
     g.shower = s.shower;
+    g.bux = g.buy = g.buz = g.bomc = 0.0;
     double n2 = (double)s.dx * s.dx + (double)s.dy * s.dy + (double)s.dz * s.dz;
     if (!segment_ok(s, P) || !(n2 > 0.0)) {
         g.bad = CLIGHT_ERR_BAD_SEGMENT;
@@ -507,10 +601,11 @@ __device__ void load_segment_d(const clight_segment &s, const DevAtm &A, const D
     make_frame(g);
     double Nc, sin2, kap, Nf;
     yield_fp64<SPH>(s, A, P, g.dx, g.dy, g.dz, &Nc, &sin2, &kap, &Nf);
-    if (P.cut_mode != CLIGHT_CUT_OFF && s.charge != 0 && !cut_keeps(s, (float)g.dx, (float)g.dy, (float)g.dz, P)) {
+    if (P.cut_mode != CLIGHT_CUT_OFF && s.charge != 0 && !cut_keeps_v(s.x, s.y, s.z, s.L, s.dx, s.dy, s.dz, (float)g.dx, (float)g.dy, (float)g.dz, P)) {
         g.cut = 1;
         Nc = 0.0;
     }
+    if (Nf > 0.0 && P.beam && !beam_cone_t(g, P, g.bux, g.buy, g.buz, g.bomc)) g.bomc = 0.0;
     g.sin_tc = sqrt(sin2);
     g.kappa = kap;
     if (Nc > 0.0) {
@@ -603,7 +698,7 @@ __device__ __forceinline__ void ray_quadrature(const DevAtm &A, T hcap, T he, T 
     }
 }
 
-template <class T, class P, bool WARP, bool SPH, bool REFR>
+template <class T, class P, bool WARP, bool SPH, bool REFR, bool EXT = true>
 __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global, uint32_t k, bool active,
                                           const DevAtm &A, const DevPar &Pp, RayOut<T, P> &o)
 {
@@ -635,13 +730,21 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
         T fl1 = sizeof(T) == 4 ? (T)Pp.fl1 : (T)Pp.fl1_d;
         T fdl = sizeof(T) == 4 ? (T)Pp.fdl : (T)Pp.fdl_d;
         lam = fl1 + u0 * fdl;
-        T cz = (T)2 * u3 - (T)1;                            // exact
-        T sz = Num<T>::sqr(((T)1 - cz) * ((T)1 + cz));
         T sp, cp;
         Num<T>::sincos2pi(u2, &sp, &cp);
-        dgx = p_of<P>(sz * cp);
-        dgy = p_of<P>(sz * sp);
-        dgz = p_of<P>(cz);
+        if (EXT && g.bomc > (T)0) {
+            T bx, by, bz;
+            cone_direction<T>(g.bux, g.buy, g.buz, u3 * g.bomc, sp, cp, bx, by, bz);
+            dgx = p_of<P>(bx);
+            dgy = p_of<P>(by);
+            dgz = p_of<P>(bz);
+        } else {
+            T cz = (T)2 * u3 - (T)1;                        // exact
+            T sz = Num<T>::sqr(((T)1 - cz) * ((T)1 + cz));
+            dgx = p_of<P>(sz * cp);
+            dgy = p_of<P>(sz * sp);
+            dgz = p_of<P>(cz);
+        }
         w = g.w_f;
     }
     T ell = u1 * g.L;

@@ -19,7 +19,8 @@ namespace clight {
 enum SegField {
     F_X0H, F_X0L, F_Y0H, F_Y0L, F_Z0H, F_Z0L, F_T0H, F_T0L, F_RZH, F_RZL,
     F_DX, F_DY, F_DZ, F_LX, F_LY, F_LZ, F_E1X, F_E1Y, F_E1Z, F_E2X, F_E2Y, F_E2Z,
-    F_SIN, F_KAP, F_L, F_IBC, F_WC, F_WF, F_NC, F_NF, F_SHOWER, F_SEGI, F_INCL, F_COUNT
+    F_SIN, F_KAP, F_L, F_IBC, F_WC, F_WF, F_NC, F_NF, F_SHOWER, F_SEGI, F_BUX, F_BUY, F_BUZ, F_BOMC,
+    F_INCL, F_COUNT
 };
 
 static int seg_smem_bytes(int block) { return (block / 32) * F_COUNT * 32 * (int)sizeof(float); }
@@ -49,7 +50,7 @@ __device__ __forceinline__ uint32_t warp_sort_u32(uint32_t key, int lane)
     return key;
 }
 
-template <class P, bool SPH, bool REFR, bool NOALLOC = false, bool SOFT = false>
+template <class P, bool SPH, bool REFR, bool NOALLOC = false, bool SOFT = false, bool EXT = true>
 __global__ void __launch_bounds__(256, 3)
 k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid_constant__ DevAtm A,
               const __grid_constant__ DevTel Tl, const __grid_constant__ DevPar Pp, const __grid_constant__ DevOut O)
@@ -85,7 +86,7 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
             const float4 *src = reinterpret_cast<const float4 *>(segs + si);
             float4 *dst = reinterpret_cast<float4 *>(&s);
             dst[0] = __ldg(src); dst[1] = __ldg(src + 1); dst[2] = __ldg(src + 2); dst[3] = __ldg(src + 3);
-            load_segment_f<SPH>(s, A, Pp, g);
+            load_segment_f<SPH, EXT>(s, A, Pp, g);
             if (g.bad) status_bits |= 1u << g.bad;
             c_guard += g.guarded;
             c_cut += g.cut;
@@ -132,6 +133,10 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
             S[F_NF * 32 + pos] = __uint_as_float(g.n_f);
             S[F_SHOWER * 32 + pos] = __uint_as_float(g.shower);
             S[F_SEGI * 32 + pos] = __uint_as_float((uint32_t)lane);
+            if (EXT) {
+                S[F_BUX * 32 + pos] = g.bux; S[F_BUY * 32 + pos] = g.buy; S[F_BUZ * 32 + pos] = g.buz;
+                S[F_BOMC * 32 + pos] = g.bomc;
+            }
         } else {
             S[F_NC * 32 + pos] = __uint_as_float(0u);
             S[F_NF * 32 + pos] = __uint_as_float(0u);
@@ -167,6 +172,12 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
             q.w_c = S[F_WC * 32 + l]; q.w_f = S[F_WF * 32 + l];
             q.n_c = nc_l; q.n_f = nf_l;
             q.shower = __float_as_uint(S[F_SHOWER * 32 + l]);
+            if (EXT) {
+                q.bux = S[F_BUX * 32 + l]; q.buy = S[F_BUY * 32 + l]; q.buz = S[F_BUZ * 32 + l];
+                q.bomc = S[F_BOMC * 32 + l];
+            } else {
+                q.bux = q.buy = q.buz = q.bomc = 0.0f;
+            }
             int64_t seg_local = s_first + (int64_t)__float_as_uint(S[F_SEGI * 32 + l]);
             int64_t seg_global = Pp.seg_base + seg_local;
             int nh = 0;
@@ -178,8 +189,9 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
                 qd.e1x = q.e1x; qd.e1y = q.e1y; qd.e1z = q.e1z; qd.e2x = q.e2x; qd.e2y = q.e2y; qd.e2z = q.e2z;
                 qd.sin_tc = q.sin_tc; qd.kappa = q.kappa; qd.L = q.L; qd.inv_bc = q.inv_bc;
                 qd.w_c = q.w_c; qd.w_f = q.w_f; qd.n_c = q.n_c; qd.n_f = q.n_f; qd.shower = q.shower;
+                qd.bux = q.bux; qd.buy = q.buy; qd.buz = q.buz; qd.bomc = q.bomc;
                 RayOut<float, double> o;
-                trace_ray<float, double, true, SPH, REFR>(qd, seg_global, k, active, A, Pp, o);
+                trace_ray<float, double, true, SPH, REFR, EXT>(qd, seg_global, k, active, A, Pp, o);
                 nh = hit_test<float, double, true, NOALLOC>(o, seg_local, seg_global, k, q.shower, A, Tl, Pp, O, status_bits, clr);
                 if (active) {
                     ++c_rays;
@@ -191,7 +203,7 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
                 // candidate pass of the soft-yield adjoint: compact the rays
                 // near a telescope into O.keys
                 RayOut<float, df> o;
-                trace_ray<float, df, true, SPH, REFR>(q, seg_global, k, active, A, Pp, o);
+                trace_ray<float, df, true, SPH, REFR, EXT>(q, seg_global, k, active, A, Pp, o);
                 bool cand = active && soft_candidate<float, df>(o, A, Tl, O.soft_w, clr);
                 unsigned m = __ballot_sync(FULL_MASK, cand);
                 if (m) {
@@ -210,7 +222,7 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
                 }
             } else {
                 RayOut<float, df> o;
-                trace_ray<float, df, true, SPH, REFR>(q, seg_global, k, active, A, Pp, o);
+                trace_ray<float, df, true, SPH, REFR, EXT>(q, seg_global, k, active, A, Pp, o);
                 nh = hit_test<float, df, true, NOALLOC>(o, seg_local, seg_global, k, q.shower, A, Tl, Pp, O, status_bits, clr);
                 if (active) {
                     ++c_rays;
@@ -277,19 +289,30 @@ k_trace_fp64(const clight_segment *__restrict__ segs, int64_t n_segs, const __gr
 }
 
 // ------------------------------------------------------------------ launchers
+template <class P, bool EXT>
+static void launch_fused_pe(const clight_segment *segs, int64_t n_segs, const DevAtm &A, const DevTel &T,
+                            const DevPar &Pp, const DevOut &O, int grid, int block, cudaStream_t s)
+{
+    int smem = fused_smem_bytes(block, T);  // <= 47 KB for block <= 256: no opt-in needed
+    if (A.spherical && A.refraction)
+        k_trace_fused<P, true, true, false, false, EXT><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
+    else if (A.spherical)
+        k_trace_fused<P, true, false, false, false, EXT><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
+    else if (A.refraction)
+        k_trace_fused<P, false, true, false, false, EXT><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
+    else
+        k_trace_fused<P, false, false, false, false, EXT><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
+}
+
+// the variant without the angular cut and beaming when neither is on
 template <class P>
 static void launch_fused_p(const clight_segment *segs, int64_t n_segs, const DevAtm &A, const DevTel &T,
                            const DevPar &Pp, const DevOut &O, int grid, int block, cudaStream_t s)
 {
-    int smem = fused_smem_bytes(block, T);  // <= 46 KB for block <= 256: no opt-in needed
-    if (A.spherical && A.refraction)
-        k_trace_fused<P, true, true><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
-    else if (A.spherical)
-        k_trace_fused<P, true, false><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
-    else if (A.refraction)
-        k_trace_fused<P, false, true><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
+    if (Pp.cut_mode != CLIGHT_CUT_OFF || Pp.beam)
+        launch_fused_pe<P, true>(segs, n_segs, A, T, Pp, O, grid, block, s);
     else
-        k_trace_fused<P, false, false><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
+        launch_fused_pe<P, false>(segs, n_segs, A, T, Pp, O, grid, block, s);
 }
 
 cudaError_t launch_trace_fused(const clight_segment *segs, int64_t n_segs, const DevAtm &A, const DevTel &T,

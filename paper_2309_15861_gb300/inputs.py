@@ -163,12 +163,24 @@ class Params:
     cut_mode: int = 0             # Cherenkov angular cut: 0 off, 1 array centre, 2 each telescope
     cut_deg: float = 6.0          # cut angle, degrees
     cut_centre: tuple = None      # array centre for cut_mode 1 (see array_centre)
+    fl_beaming: int = 0           # fluorescence beamed toward the array (see beam_cone)
+    beam_centre: tuple = None
+    beam_radius: float = None
 
 
 def array_centre(tels: np.ndarray) -> tuple:
     """Mean of the telescope centres (the 'experiment centre' of the angular cut)."""
     return (float(np.mean(tels["x"].astype(np.float64))), float(np.mean(tels["y"].astype(np.float64))),
             float(np.mean(tels["z"].astype(np.float64))))
+
+
+def beam_cone(tels: np.ndarray) -> tuple:
+    """(centre, radius) of the sphere about the mean telescope centre that
+    holds every telescope sphere (the target of fluorescence beaming)."""
+    c = np.array(array_centre(tels))
+    xyz = np.stack([tels["x"], tels["y"], tels["z"]], axis=1).astype(np.float64)
+    r = float(np.max(np.linalg.norm(xyz - c[None, :], axis=1) + tels["R"].astype(np.float64)))
+    return tuple(float(v) for v in c), r
 
 
 def telescope_grid(nx, ny, spacing, R=6.0, z=2000.0):

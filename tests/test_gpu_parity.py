@@ -130,6 +130,18 @@ def test_angular_cut(ctx, mode):
     assert gst64["cut"] == gst["cut"]
 
 
+def test_fluorescence_beaming(ctx):
+    """Sec. 1.1.1 optimisation: beamed fluorescence (cone toward the array,
+    photon number scaled by its solid-angle share) on both sides."""
+    w = I.batch_showers(n_showers=6, seed=43, scale=2e-3)
+    c, r = I.beam_cone(w.telescopes)
+    w.params = dataclasses.replace(w.params, fl_beaming=1, beam_centre=c, beam_radius=r)
+    rep, gst, rst = _check(ctx, w)
+    assert rep["n_common"] > 0
+    rep64, gst64, rst64 = _check(ctx, w, fp64=True)
+    assert gst64["rays"] == gst["rays"]
+
+
 def test_fp64_plain_path(ctx):
     w = I.workload_shower_1tev(n=8000, seed=11)
     rep, gst, rst = _check(ctx, w, fp64=True)

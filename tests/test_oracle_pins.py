@@ -7,6 +7,7 @@ equation, an invariant, or a geometric brute force.  Each is chosen so that a
 plausible slip (a dropped factor, a wrong sign, a transposed operand) fails.
 """
 import ctypes
+import dataclasses
 import math
 import os
 
@@ -548,3 +549,76 @@ def test_angular_cut_keeps_a_subset_of_the_hits():
     nc1, _ = O.bunch_counts(w.segments, w.atmosphere, par)
     kept = nc1[h0["seg"]] > 0
     np.testing.assert_array_equal(h1, h0[kept])
+
+
+# ---------------------------------------------------------------- fluorescence beaming
+def _fluor_workload(n, seed, beaming, dE=(20.0, 40.0), xy=3000.0, z=(3000.0, 9000.0)):
+    atm = I.atmosphere_layered()
+    tels = I.telescope_grid(4, 4, 100.0, z=atm.h_obs)
+    rng = np.random.default_rng(seed)
+    s = np.zeros(n, dtype=I.SEG_DTYPE)
+    s["x"] = rng.uniform(-xy, xy, n)
+    s["y"] = rng.uniform(-xy, xy, n)
+    s["z"] = rng.uniform(z[0], z[1], n)
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    s["dx"], s["dy"], s["dz"] = d[:, 0], d[:, 1], d[:, 2]
+    s["L"] = rng.uniform(0.5, 5.0, n)
+    s["eps"] = 1e-3
+    s["dE"] = rng.uniform(dE[0], dE[1], n)
+    s["charge"] = 0
+    c, r = I.beam_cone(tels)
+    par = I.Params(bunch=1.0, seed=seed, fluor_yield=5.0, fl_beaming=beaming, beam_centre=c, beam_radius=r)
+    return I.Workload("fluor", s, atm, tels, par)
+
+
+def test_beamed_fluorescence_fills_its_cone_uniformly():
+    """Sec. 1.1.1: beamed directions lie in the cone about the step-to-array
+    axis, uniform in solid angle (cos of the angle to the axis uniform on
+    [cos alpha, 1]); the photon number scales by sin^2(alpha/2)."""
+    w = _fluor_workload(200, 3, 1, dE=(2000.0, 4000.0))
+    c, R = np.array(w.params.beam_centre), w.params.beam_radius
+    cosines = []
+    for i, s in enumerate(w.segments[:60]):
+        d = np.array([s["dx"], s["dy"], s["dz"]], dtype=np.float64)
+        d /= np.linalg.norm(d)
+        m = np.array([s["x"], s["y"], s["z"]]) + 0.5 * float(s["L"]) * d
+        D = np.linalg.norm(c - m)
+        alpha = math.asin(R / D) + 5e-3 + float(s["L"]) / D
+        u = (c - m) / D
+        y = O.yield_of(s, w.atmosphere, w.params)
+        y0 = O.yield_of(s, w.atmosphere, dataclasses.replace(w.params, fl_beaming=0))
+        np.testing.assert_allclose(y["Nf"], y0["Nf"] * math.sin(alpha / 2) ** 2, rtol=1e-12)
+        for k in range(int(y["n_f"])):
+            r, dg, te, lam, wt, proc = O.photon(s, i, k, w.atmosphere, w.params)
+            assert proc == 1
+            cosines.append((dg @ u - math.cos(alpha)) / (1 - math.cos(alpha)))
+    cosines = np.array(cosines)
+    assert cosines.min() >= -1e-12 and cosines.max() <= 1 + 1e-12 and len(cosines) > 200
+    assert stats.kstest(cosines, "uniform").pvalue > 1e-3
+
+
+def test_beaming_loses_no_hits_and_keeps_the_mean():
+    """Every hit of isotropic emission left its step inside that step's
+    cone, so beaming removes no reachable direction; the beamed photon sums
+    agree with the isotropic ones within their statistical error."""
+    kw = dict(dE=(300.0, 500.0), xy=1000.0, z=(3000.0, 4500.0))
+    wi = _fluor_workload(1200, 5, 0, **kw)
+    wb = _fluor_workload(1200, 5, 1, **kw)
+    hi, ci, si, sti = O.trace(wi.segments, wi.atmosphere, wi.telescopes, wi.params)
+    hb, cb, sb, stb = O.trace(wb.segments, wb.atmosphere, wb.telescopes, wb.params)
+    assert len(hi) > 30 and stb["rays"] < 0.2 * sti["rays"]
+    c, R = np.array(wb.params.beam_centre), wb.params.beam_radius
+    for h in hi:
+        s = wi.segments[h["seg"]]
+        d = np.array([s["dx"], s["dy"], s["dz"]], dtype=np.float64)
+        d /= np.linalg.norm(d)
+        m = np.array([s["x"], s["y"], s["z"]]) + 0.5 * float(s["L"]) * d
+        D = np.linalg.norm(c - m)
+        assert D >= 2 * R
+        alpha = math.asin(R / D) + 5e-3 + float(s["L"]) / D
+        r, dg, te, lam, wt, proc = O.photon(s, int(h["seg"]), int(h["k"]), wi.atmosphere, wi.params)
+        assert math.acos(np.clip(dg @ (c - m) / D, -1, 1)) < alpha
+    # means: isotropic photons hit with bunch weight 1 (Poisson); beamed ones carry the cone share
+    tot_i, tot_b = si.sum(), sb.sum()
+    assert abs(tot_b - tot_i) < 5 * math.sqrt(tot_i) + 5 * math.sqrt(max(1.0, (sb ** 2).sum() / max(1, len(hb)))), (tot_i, tot_b)
