@@ -219,6 +219,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--propagator", default="exact", choices=["exact", "straight"],
+                    help="exact: the refracted ray's deviation integrated (default); straight: the vacuum "
+                         "line with first-order refraction corrections (Sec. 2's method, approximate)")
     ap.add_argument("--fl-beaming", action="store_true",
                     help="beam the fluorescence toward the array (Sec. 1.1.1); the batch workload's default is "
                          "isotropic emission")
@@ -262,7 +265,7 @@ def main():
     ns = w.n_showers
     ctx = G.Context(local)
     extra = dict(use_graph=1, precision=args.precision, block=args.block, ctas_per_sm=args.ctas_per_sm,
-                 cell_width=args.cell_width)
+                 cell_width=args.cell_width, propagator=1 if args.propagator == "straight" else 0)
     ctx.setup(w, **extra)
     dev = f"cuda:{local}"
     segs = torch.from_numpy(w.segments.view(np.uint8).reshape(-1)).to(dev)
@@ -445,7 +448,7 @@ def main():
                        "precision": ["float-pair", "fp64-guard"][args.precision], "graph": True,
                        "l2": f"inputs ({n * 64 / 1e9:.2f} GB) larger than L2; no flush",
                        "parallelism": f"replicas x{world}", "generation_s": round(t_gen, 1),
-                       "fl_beaming": bool(args.fl_beaming),
+                       "fl_beaming": bool(args.fl_beaming), "propagator": args.propagator,
                        "step": "trace + adjoint" if adj is not None else "trace"},
             "roofline": roof, "fp64_plain": fp64, "e2e": e2e, "cpu_baseline": cpu,
             "clocks": ck, "gpu_launches": launches_per_step * args.steps,

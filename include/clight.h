@@ -125,10 +125,20 @@ typedef struct {
      * and its photon number is scaled by the cone's share sin^2(alpha / 2).
      * beam_radius must hold every telescope sphere (centre distance + R). */
     int32_t fl_beaming;             /* 0 off, 1 on */
-    int32_t beam_pad;
+    /* Propagator (Sec. 2): CLIGHT_PROP_EXACT integrates the refracted ray's
+     * deviation from the vacuum line; CLIGHT_PROP_STRAIGHT keeps the vacuum
+     * line and applies first-order corrections in n - 1 (closed forms per
+     * exponential layer, evaluated with the zenith angle at emission): the
+     * paper's straight line plus refraction corrections, approximate. */
+    int32_t propagator;
     double beam_centre[3];          /* m, local frame */
     double beam_radius;             /* m */
 } clight_params;
+
+enum {
+    CLIGHT_PROP_EXACT = 0,
+    CLIGHT_PROP_STRAIGHT = 1
+};
 
 /* One telescope hit (48 bytes). */
 typedef struct {

@@ -28,6 +28,7 @@ assert HIT_DTYPE.itemsize == 48
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA runtime error", 3: "hit capacity exceeded",
           4: "invalid segment", 5: "limit exceeded", 6: "no usable CUDA device"}
 OK, ERR_ARG, ERR_CUDA, ERR_HIT_CAPACITY, ERR_BAD_SEGMENT, ERR_LIMIT, ERR_NO_DEVICE = range(7)
+PROP_EXACT, PROP_STRAIGHT = 0, 1
 PREC_FLOAT_PAIR, PREC_FP64_GUARD = 0, 1
 
 
@@ -52,7 +53,7 @@ class Params(C.Structure):
                 ("precision", C.c_int32), ("block", C.c_int32), ("ctas_per_sm", C.c_int32),
                 ("use_graph", C.c_int32), ("cell_width", C.c_float), ("key_bunch_bits", C.c_int32),
                 ("cut_mode", C.c_int32), ("cut_pad", C.c_int32), ("cut_deg", C.c_double),
-                ("cut_centre", C.c_double * 3), ("fl_beaming", C.c_int32), ("beam_pad", C.c_int32),
+                ("cut_centre", C.c_double * 3), ("fl_beaming", C.c_int32), ("propagator", C.c_int32),
                 ("beam_centre", C.c_double * 3), ("beam_radius", C.c_double)]
 
 

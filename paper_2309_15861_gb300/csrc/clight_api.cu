@@ -237,6 +237,28 @@ clight_status clight_set_atmosphere(clight_ctx *c, const clight_atmosphere *a)
     A.delta_obs_d = delta_at(a->h_obs);
     A.delta_obs = (float)A.delta_obs_d;
     A.n_obs = (float)(1.0 + A.delta_obs_d);
+    {
+        // closed-form layer integrals for the straight-line propagator
+        double above_d = 0.0, above_r = 0.0;   // integrals over the layers above layer i
+        for (int i = a->n_layers - 1; i >= 0; --i) {
+            double top = i + 1 < a->n_layers ? a->h_lo[i + 1] : a->h_top;
+            double kd = a->K * Bc(i), kr = Bc(i) / a->rho_ref, ci = a->c[i];
+            double et = std::exp(-top / ci);
+            A.lay_c[i] = (float)ci;
+            A.lay_E[i] = (float)(above_d - ci * kd * et);
+            A.lay_F[i] = (float)(above_r - ci * kr * et);
+            double bottom = i > 0 ? a->h_lo[i] : (a->n_layers > 1 ? a->h_lo[0] : std::min(a->h_lo[0], a->h_obs));
+            double eb = std::exp(-bottom / ci);
+            above_d += ci * kd * (eb - et);
+            above_r += ci * kr * (eb - et);
+        }
+        int io = 0;
+        for (int j = 1; j < a->n_layers; ++j)
+            if (a->h_obs >= a->h_lo[j]) io = j;
+        double eo = std::exp(-a->h_obs / a->c[io]);
+        A.D_obs = (float)(a->c[io] * a->K * Bc(io) * eo + A.lay_E[io]);
+        A.R_obs = (float)(a->c[io] * Bc(io) / a->rho_ref * eo + A.lay_F[io]);
+    }
     A.inv_L0_d = a->absorption ? 1.0 / a->L0 : 0.0;
     A.inv_L0 = (float)A.inv_L0_d;
     A.lambda_ref_d = a->absorption ? a->lambda_ref : 1.0;
@@ -414,6 +436,7 @@ clight_status clight_set_params(clight_ctx *c, const clight_params *p)
                                           !std::isfinite(p->cut_centre[2])))
         return CLIGHT_ERR_ARG;
     if (p->fl_beaming != 0 && p->fl_beaming != 1) return CLIGHT_ERR_ARG;
+    if (p->propagator != CLIGHT_PROP_EXACT && p->propagator != CLIGHT_PROP_STRAIGHT) return CLIGHT_ERR_ARG;
     if (p->fl_beaming && (!(p->beam_radius > 0) || !std::isfinite(p->beam_radius) ||
                           !std::isfinite(p->beam_centre[0]) || !std::isfinite(p->beam_centre[1]) ||
                           !std::isfinite(p->beam_centre[2])))
@@ -448,6 +471,7 @@ clight_status clight_set_params(clight_ctx *c, const clight_params *p)
     P.cut_cx = (float)P.cut_cx_d; P.cut_cy = (float)P.cut_cy_d; P.cut_cz = (float)P.cut_cz_d;
     P.cut_rad = (float)(cut_deg * (3.14159265358979323846 / 180.0));
     P.beam = p->fl_beaming;
+    P.prop = p->propagator;
     P.beam_cx_d = p->beam_centre[0]; P.beam_cy_d = p->beam_centre[1]; P.beam_cz_d = p->beam_centre[2];
     P.beam_r_d = p->beam_radius;
     P.beam_cx = (float)P.beam_cx_d; P.beam_cy = (float)P.beam_cy_d; P.beam_cz = (float)P.beam_cz_d;

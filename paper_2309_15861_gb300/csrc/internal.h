@@ -36,6 +36,11 @@ struct DevAtm {
     double k2_d;                              // h_obs + 2 R_E
     float gl_x[kGLNodes], gl_w[kGLNodes];     // Gauss-Legendre on [-1, 1]
     double gl_x_d[kGLNodes], gl_w_d[kGLNodes];
+    // straight-line propagator: per layer c_i and the constants E_i, F_i of
+    // int_h^top delta = c_i delta(h) + E_i, int_h^top rho/rho_ref = c_i rho(h)/rho_ref + F_i,
+    // and both integrals from h_obs
+    float lay_c[kMaxLayers], lay_E[kMaxLayers], lay_F[kMaxLayers];
+    float D_obs, R_obs;
     DevCell cells[kMaxCells];
     double cell_lo_d[kMaxCells], cell_hi_d[kMaxCells], cell_kb_d[kMaxCells], cell_rb_d[kMaxCells],
         cell_ic_d[kMaxCells];                 // binary64 copies; ic = 1/c
@@ -91,6 +96,7 @@ struct DevPar {
     const int *cut_cell_start, *cut_cell_tel;
     int cut_nx, cut_ny;
     float cut_gx0, cut_gy0, cut_inv_gs;
+    int prop;                    // CLIGHT_PROP_*
     // fluorescence beaming: on/off, cone centre and radius
     int beam;
     float beam_cx, beam_cy, beam_cz, beam_r;

@@ -698,7 +698,54 @@ __device__ __forceinline__ void ray_quadrature(const DevAtm &A, T hcap, T he, T 
     }
 }
 
-template <class T, class P, bool WARP, bool SPH, bool REFR, bool EXT = true>
+// First-order straight-line corrections in the form the landing code takes
+// (I0: the flat horizontal shortfall per unit sin, or the spherical angle
+// shortfall per unit p_v; I1: optical excess; I2: density path).
+template <class T, bool SPH, bool REFR>
+__device__ __forceinline__ void straight_corrections(const DevAtm &A, T he, T de, T pv2, T bf2, T &I0, T &I1,
+                                                     T &I2)
+{
+    const float hf = (float)he;
+    float Dh, Rh;                                     // int_h^top delta, rho / rho_ref
+    if (hf >= A.h_top) {
+        Dh = 0.0f; Rh = 0.0f;
+    } else {
+        int i = 0;
+#pragma unroll
+        for (int j = 1; j < kMaxLayers; ++j)
+            if (j < A.n_layers && hf >= A.h_lo[j]) i = j;
+        float ex = ex2_approx(hf * A.nl2c[i]);
+        Dh = A.lay_c[i] * A.kb[i] * ex + A.lay_E[i];
+        Rh = A.lay_c[i] * A.rb[i] * ex + A.lay_F[i];
+    }
+    T J = (T)(A.D_obs - Dh), Jr = (T)(A.R_obs - Rh);
+    const T h_obs = sizeof(T) == 4 ? (T)A.h_obs : (T)A.h_obs_d;
+    T corr = de * (he - h_obs) - J;
+    T mu2, s2, r2 = (T)1;
+    if (SPH) {
+        T re2 = bf2 + pv2;                            // r_e^2
+        mu2 = bf2 / re2;
+        s2 = pv2 / re2;
+        r2 = re2;
+    } else {
+        mu2 = bf2;
+        s2 = pv2;
+    }
+    T imu = Num<T>::rsq(mu2);                         // 1 / mu
+    T imu3 = imu * imu * imu;
+    I0 = SPH ? corr * imu3 * Num<T>::rsq(r2) * Num<T>::div((T)1, sizeof(T) == 4 ? (T)A.r_obs : (T)A.r_obs_d)
+             : corr * imu3;
+    I1 = REFR ? J * imu + s2 * corr * imu3 : J * imu; // a straight ray only gains delta ds
+    I2 = Jr * imu;
+}
+
+// Optional features of the per-ray code, fixed at compile time so that the
+// default kernel carries none of them: FEAT_EXT the angular cut and the
+// fluorescence beaming; FEAT_STRAIGHT the straight-line propagator only (no
+// quadrature); FEAT_RUNTIME both propagators, chosen by DevPar::prop.
+constexpr int FEAT_EXT = 1, FEAT_STRAIGHT = 2, FEAT_RUNTIME = 4, FEAT_ALL = FEAT_EXT | FEAT_RUNTIME;
+
+template <class T, class P, bool WARP, bool SPH, bool REFR, int FEAT = FEAT_ALL>
 __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global, uint32_t k, bool active,
                                           const DevAtm &A, const DevPar &Pp, RayOut<T, P> &o)
 {
@@ -732,7 +779,7 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
         lam = fl1 + u0 * fdl;
         T sp, cp;
         Num<T>::sincos2pi(u2, &sp, &cp);
-        if (EXT && g.bomc > (T)0) {
+        if ((FEAT & FEAT_EXT) && g.bomc > (T)0) {
             T bx, by, bz;
             cone_direction<T>(g.bux, g.buy, g.buz, u3 * g.bomc, sp, cp, bx, by, bz);
             dgx = p_of<P>(bx);
@@ -830,7 +877,17 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
     T hcap = go ? (he < htop ? he : htop) : (T)-1e30;
     T I0, I1, I2;
     o.cells = 0;
-    ray_quadrature<T, WARP, SPH, REFR>(A, hcap, he, de, pv2, bf2, I0, I1, I2, o.cells);
+    if ((FEAT & FEAT_STRAIGHT) || ((FEAT & FEAT_RUNTIME) && Pp.prop == CLIGHT_PROP_STRAIGHT)) {
+        // straight line plus first-order corrections (Sec. 2): with
+        // mu = cos(zenith at emission), J = int_{h_obs}^{h_e} delta dh and
+        // corr = delta_e (h_e - h_obs) - J, to first order in delta the flat
+        // ray falls short horizontally by sin / mu^3 * corr, its optical path
+        // exceeds the vacuum one by J / mu + sin^2 / mu^3 * corr, and its
+        // density path is int rho / rho_ref dh / mu (layer closed forms).
+        straight_corrections<T, SPH, REFR>(A, go ? he : h_obs, de, pv2, bf2, I0, I1, I2);
+    } else {
+        ray_quadrature<T, WARP, SPH, REFR>(A, hcap, he, de, pv2, bf2, I0, I1, I2, o.cells);
+    }
     if (!go) return;
 
     const T n_obs = sizeof(T) == 4 ? (T)A.n_obs : (T)1 + (T)A.delta_obs_d;

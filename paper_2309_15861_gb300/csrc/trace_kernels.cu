@@ -50,11 +50,12 @@ __device__ __forceinline__ uint32_t warp_sort_u32(uint32_t key, int lane)
     return key;
 }
 
-template <class P, bool SPH, bool REFR, bool NOALLOC = false, bool SOFT = false, bool EXT = true>
+template <class P, bool SPH, bool REFR, bool NOALLOC = false, bool SOFT = false, int FEAT = FEAT_ALL>
 __global__ void __launch_bounds__(256, 3)
 k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid_constant__ DevAtm A,
               const __grid_constant__ DevTel Tl, const __grid_constant__ DevPar Pp, const __grid_constant__ DevOut O)
 {
+    constexpr bool EXT = (FEAT & FEAT_EXT) != 0;
     extern __shared__ float smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float *S = smem + warp * (F_COUNT * 32);
@@ -191,7 +192,7 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
                 qd.w_c = q.w_c; qd.w_f = q.w_f; qd.n_c = q.n_c; qd.n_f = q.n_f; qd.shower = q.shower;
                 qd.bux = q.bux; qd.buy = q.buy; qd.buz = q.buz; qd.bomc = q.bomc;
                 RayOut<float, double> o;
-                trace_ray<float, double, true, SPH, REFR, EXT>(qd, seg_global, k, active, A, Pp, o);
+                trace_ray<float, double, true, SPH, REFR, FEAT>(qd, seg_global, k, active, A, Pp, o);
                 nh = hit_test<float, double, true, NOALLOC>(o, seg_local, seg_global, k, q.shower, A, Tl, Pp, O, status_bits, clr);
                 if (active) {
                     ++c_rays;
@@ -203,7 +204,7 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
                 // candidate pass of the soft-yield adjoint: compact the rays
                 // near a telescope into O.keys
                 RayOut<float, df> o;
-                trace_ray<float, df, true, SPH, REFR, EXT>(q, seg_global, k, active, A, Pp, o);
+                trace_ray<float, df, true, SPH, REFR, FEAT>(q, seg_global, k, active, A, Pp, o);
                 bool cand = active && soft_candidate<float, df>(o, A, Tl, O.soft_w, clr);
                 unsigned m = __ballot_sync(FULL_MASK, cand);
                 if (m) {
@@ -222,7 +223,7 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
                 }
             } else {
                 RayOut<float, df> o;
-                trace_ray<float, df, true, SPH, REFR, EXT>(q, seg_global, k, active, A, Pp, o);
+                trace_ray<float, df, true, SPH, REFR, FEAT>(q, seg_global, k, active, A, Pp, o);
                 nh = hit_test<float, df, true, NOALLOC>(o, seg_local, seg_global, k, q.shower, A, Tl, Pp, O, status_bits, clr);
                 if (active) {
                     ++c_rays;
@@ -289,30 +290,38 @@ k_trace_fp64(const clight_segment *__restrict__ segs, int64_t n_segs, const __gr
 }
 
 // ------------------------------------------------------------------ launchers
-template <class P, bool EXT>
+template <class P, int FEAT>
 static void launch_fused_pe(const clight_segment *segs, int64_t n_segs, const DevAtm &A, const DevTel &T,
                             const DevPar &Pp, const DevOut &O, int grid, int block, cudaStream_t s)
 {
     int smem = fused_smem_bytes(block, T);  // <= 47 KB for block <= 256: no opt-in needed
     if (A.spherical && A.refraction)
-        k_trace_fused<P, true, true, false, false, EXT><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
+        k_trace_fused<P, true, true, false, false, FEAT><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
     else if (A.spherical)
-        k_trace_fused<P, true, false, false, false, EXT><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
+        k_trace_fused<P, true, false, false, false, FEAT><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
     else if (A.refraction)
-        k_trace_fused<P, false, true, false, false, EXT><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
+        k_trace_fused<P, false, true, false, false, FEAT><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
     else
-        k_trace_fused<P, false, false, false, false, EXT><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
+        k_trace_fused<P, false, false, false, false, FEAT><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
 }
 
-// the variant without the angular cut and beaming when neither is on
+// the variant without the angular cut, beaming and the straight-line propagator when none is on
 template <class P>
 static void launch_fused_p(const clight_segment *segs, int64_t n_segs, const DevAtm &A, const DevTel &T,
                            const DevPar &Pp, const DevOut &O, int grid, int block, cudaStream_t s)
 {
-    if (Pp.cut_mode != CLIGHT_CUT_OFF || Pp.beam)
-        launch_fused_pe<P, true>(segs, n_segs, A, T, Pp, O, grid, block, s);
+    const bool ext = Pp.cut_mode != CLIGHT_CUT_OFF || Pp.beam;
+    const bool str = Pp.prop == CLIGHT_PROP_STRAIGHT;
+    if (!std::is_same<P, df>::value)
+        launch_fused_pe<P, FEAT_ALL>(segs, n_segs, A, T, Pp, O, grid, block, s);
+    else if (ext && str)
+        launch_fused_pe<P, FEAT_EXT | FEAT_STRAIGHT>(segs, n_segs, A, T, Pp, O, grid, block, s);
+    else if (ext)
+        launch_fused_pe<P, FEAT_EXT>(segs, n_segs, A, T, Pp, O, grid, block, s);
+    else if (str)
+        launch_fused_pe<P, FEAT_STRAIGHT>(segs, n_segs, A, T, Pp, O, grid, block, s);
     else
-        launch_fused_pe<P, false>(segs, n_segs, A, T, Pp, O, grid, block, s);
+        launch_fused_pe<P, 0>(segs, n_segs, A, T, Pp, O, grid, block, s);
 }
 
 cudaError_t launch_trace_fused(const clight_segment *segs, int64_t n_segs, const DevAtm &A, const DevTel &T,

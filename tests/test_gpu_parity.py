@@ -142,6 +142,43 @@ def test_fluorescence_beaming(ctx):
     assert gst64["rays"] == gst["rays"]
 
 
+def _straight_errors(ctx, w):
+    ctx.setup(w, propagator=G.PROP_STRAIGHT)
+    gh, gc, gs, gst = G.run_workload(ctx, w)
+    rh, rc, rs, rst = _oracle(w)
+    assert gst["rays"] == rst["rays"]
+    rep = _parity.compare(gh, rh, w.telescopes, ref_dperp_of=_dperp_fn(w), tol_xy=1.0, tol_t=1.0,
+                          edge=0.5, w_tol=np.full(len(rh), 1e-2))
+    ctx.setup(w)
+    return rep
+
+
+def test_straight_line_propagator_is_first_order():
+    """Sec. 2's straight line plus refraction corrections, written to first
+    order in n - 1: against the exact oracle its error shrinks like
+    (n - 1)^2 when the refractivity is scaled down by 10."""
+    pytest.importorskip("torch")
+    ctx = G.Context(0)
+    try:
+        w = I.workload_shower_1tev(n=20_000, seed=53)
+        r1 = _straight_errors(ctx, w)
+        w10 = I.workload_shower_1tev(n=20_000, seed=53)
+        w10.atmosphere.K = w.atmosphere.K / 10.0
+        r10 = _straight_errors(ctx, w10)
+        print("straight-line errors", r1, r10)
+        assert r1["max_x"] < 0.05 and r1["max_t"] < 0.05
+        # first order: the error falls ~100x; allow for the binary32 floor
+        assert r10["max_x"] < 0.05 * r1["max_x"] + 2e-4
+        assert r10["max_t"] < 0.05 * r1["max_t"] + 2e-4
+        # at 60 degrees the zenith-angle factors grow; the error stays far below the tolerances
+        wi = I.workload_inclined(n=6_000, seed=59)
+        ri = _straight_errors(ctx, wi)
+        print("straight-line errors at 60 deg", ri)
+        assert ri["max_x"] < 0.01 and ri["max_t"] < 0.01
+    finally:
+        ctx.close()
+
+
 def test_fp64_plain_path(ctx):
     w = I.workload_shower_1tev(n=8000, seed=11)
     rep, gst, rst = _check(ctx, w, fp64=True)
