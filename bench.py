@@ -222,6 +222,8 @@ def main():
     ap.add_argument("--propagator", default="exact", choices=["exact", "straight"],
                     help="exact: the refracted ray's deviation integrated (default); straight: the vacuum "
                          "line with first-order refraction corrections (Sec. 2's method, approximate)")
+    ap.add_argument("--disp-B", type=float, default=0.0,
+                    help="dispersion: n - 1 = delta(h) (1 + B/lambda^2)/(1 + B/400^2), B in nm^2 (0 = none)")
     ap.add_argument("--fl-beaming", action="store_true",
                     help="beam the fluorescence toward the array (Sec. 1.1.1); the batch workload's default is "
                          "isotropic emission")
@@ -258,6 +260,9 @@ def main():
     t_gen = time.perf_counter()
     w = make_workload(args.workload, args.n_segs, rank, args.scale)
     t_gen = time.perf_counter() - t_gen
+    if args.disp_B > 0:
+        w.atmosphere.disp_B = args.disp_B
+        w.atmosphere.disp_lref = 400.0
     if args.fl_beaming:
         import dataclasses
         c, r = I.beam_cone(w.telescopes)
@@ -449,6 +454,7 @@ def main():
                        "l2": f"inputs ({n * 64 / 1e9:.2f} GB) larger than L2; no flush",
                        "parallelism": f"replicas x{world}", "generation_s": round(t_gen, 1),
                        "fl_beaming": bool(args.fl_beaming), "propagator": args.propagator,
+                       "dispersion_B_nm2": args.disp_B,
                        "step": "trace + adjoint" if adj is not None else "trace"},
             "roofline": roof, "fp64_plain": fp64, "e2e": e2e, "cpu_baseline": cpu,
             "clocks": ck, "gpu_launches": launches_per_step * args.steps,

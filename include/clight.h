@@ -83,6 +83,15 @@ typedef struct {
     double h_obs;                   /* observation level, m */
     int32_t refraction;             /* 1 = refracted rays, 0 = straight lines */
     int32_t absorption;             /* 1 = weight photons by exp(-tau) */
+    /* Dispersion (Sec. 1.2 keeps n(lambda) inside the Frank-Tamm integral;
+     * the form is a stated reading): n(lambda, h) - 1 = delta(h) g(lambda),
+     * g = (1 + disp_B / lambda^2) / (1 + disp_B / disp_lref^2), delta(h) the
+     * refractivity of the layers at disp_lref.  The yield integrates over
+     * the band above threshold, each photon takes its own wavelength and
+     * Cherenkov angle, and its ray sees delta(h) g(lambda).  disp_B = 0:
+     * no dispersion.  Not supported by clight_trace_adjoint. */
+    double disp_B;                  /* nm^2, >= 0 */
+    double disp_lref;               /* nm, > 0 when disp_B > 0 */
 } clight_atmosphere;
 
 /* Precision of the fused FP32 path's few extended-precision steps. */

@@ -46,7 +46,8 @@ class _Atm(C.Structure):
                 ("h_top", C.c_double), ("K", C.c_double), ("rho_ref", C.c_double),
                 ("L0", C.c_double), ("lambda_ref", C.c_double),
                 ("R_E", C.c_double), ("h_obs", C.c_double),
-                ("spherical", C.c_int), ("refraction", C.c_int), ("absorption", C.c_int)]
+                ("spherical", C.c_int), ("refraction", C.c_int), ("absorption", C.c_int),
+                ("disp_B", C.c_double), ("disp_lref", C.c_double)]
 
 
 class _Par(C.Structure):
@@ -78,6 +79,8 @@ def lib():
         L.or_delta.restype = C.c_double
         L.or_density.argtypes = [P, C.c_double]
         L.or_density.restype = C.c_double
+        L.or_disp_g.argtypes = [P, C.c_double]
+        L.or_disp_g.restype = C.c_double
         L.or_trace.argtypes = [P, C.c_int64, P, P, C.c_int, P, C.c_int, P, C.c_int64,
                                P, P, P, C.c_int]
         L.or_trace.restype = C.c_int64
@@ -109,6 +112,8 @@ def atm_struct(atm) -> _Atm:
     s.spherical = int(atm.spherical)
     s.refraction = int(atm.refraction)
     s.absorption = int(atm.absorption)
+    s.disp_B = float(getattr(atm, "disp_B", 0.0))
+    s.disp_lref = float(getattr(atm, "disp_lref", 400.0))
     return s
 
 
@@ -190,6 +195,10 @@ def propagate(atm, r_e, d, t_e=0.0, lam=400.0):
     a = atm_struct(atm)
     lib().or_propagate(C.byref(a), _ptr(r), _ptr(dd), float(t_e), float(lam), _ptr(o))
     return dict(status=int(o[0]), P=o[1:4].copy(), dL=o[4:7].copy(), t=o[7], tau=o[8], n_obs=o[9])
+
+
+def disp_g(atm, lam):
+    return lib().or_disp_g(C.byref(atm_struct(atm)), float(lam))
 
 
 def delta(atm, h):

@@ -152,6 +152,53 @@ static int beam_cone(const or_segment *s, const double d[3], const or_params *p,
     return 1;
 }
 
+/* ------------------------------------------------------------------------
+ * Dispersion.  Sec. 1.2 keeps n(lambda, l) inside the Frank-Tamm double
+ * integral but gives no formula for it.  Reading: n - 1 = delta(h) g(lambda)
+ * with the Cauchy form g = (1 + B/lambda^2) / (1 + B/lambda_d^2), delta(h)
+ * being the refractivity at lambda_d; B is a stated parameter.  In
+ * u = 1/lambda the yield is 2 pi alpha z^2 L int (1 - 1/(beta n(u))^2) du
+ * over the band where beta n > 1, and the emitted u has that integrand as
+ * its density; cos(theta_c) = 1/(beta n(u)) per photon.
+ * ---------------------------------------------------------------------- */
+double or_disp_g(const or_atmosphere *a, double lambda)
+{
+    if (!(a->disp_B > 0)) return 1.0;
+    return (1.0 + a->disp_B / (lambda * lambda)) / (1.0 + a->disp_B / (a->disp_lref * a->disp_lref));
+}
+
+/* beta n(u) - 1 = delta g(u) (1 - eps) - eps, u in 1/nm */
+static double disp_g1(const or_atmosphere *a, double delta, double eps, double u)
+{
+    double g = (1.0 + a->disp_B * u * u) / (1.0 + a->disp_B / (a->disp_lref * a->disp_lref));
+    double dg = delta * g;
+    return dg - eps - eps * dg;
+}
+
+static double disp_f(const or_atmosphere *a, double delta, double eps, double u)
+{
+    double g1 = disp_g1(a, delta, eps, u);
+    if (!(g1 > 0)) return 0.0;
+    return g1 * (2.0 + g1) / ((1.0 + g1) * (1.0 + g1));
+}
+
+/* the band of u = 1/lambda above threshold: [u_lo, u_hi], 0 if empty */
+static int disp_band(const or_atmosphere *a, const or_params *p, double delta, double eps, double *u_lo,
+                     double *u_hi)
+{
+    double u1 = 1.0 / p->lambda1, u2 = 1.0 / p->lambda2;
+    if (!(delta > 0)) return 0;
+    double G = eps / (delta * (1.0 - eps));
+    double g0 = 1.0 + a->disp_B / (a->disp_lref * a->disp_lref);
+    double t = (G * g0 - 1.0) / a->disp_B;
+    double ut = t > 0 ? sqrt(t) : 0.0;
+    *u_lo = ut > u2 ? ut : u2;
+    *u_hi = u1;
+    return *u_lo < *u_hi;
+}
+
+static double disp_integral(const or_atmosphere *a, double delta, double eps, double u_lo, double u_hi);
+
 void or_yield(const or_segment *s, const or_atmosphere *a, const or_params *p, double out[10])
 {
     double d[3];
@@ -165,7 +212,16 @@ void or_yield(const or_segment *s, const or_atmosphere *a, const or_params *p, d
     double z2 = (double)s->charge * (double)s->charge;
     if (p->cut_mode != 0 && z2 > 0 && !cut_keeps(d, rm, p)) z2 = 0;
     double n_c = 0, w_c = 0, cos_tc = 1, sin_tc = 0, Nc = 0;
-    if (z2 > 0 && beta * n > 1.0 && s->L > 0) {
+    double u_lo, u_hi;
+    if (a->disp_B > 0) {
+        /* the full wavelength integral; cos_tc / sin_tc are then per photon */
+        if (z2 > 0 && s->L > 0 && disp_band(a, p, delta, (double)s->eps, &u_lo, &u_hi)) {
+            Nc = 2.0 * OR_PI * OR_ALPHA * z2 * 1e9 * disp_integral(a, delta, (double)s->eps, u_lo, u_hi) *
+                 (double)s->L;
+            n_c = ceil(Nc / p->bunch);
+            w_c = n_c > 0 ? Nc / n_c : 0.0;
+        }
+    } else if (z2 > 0 && beta * n > 1.0 && s->L > 0) {
         cos_tc = 1.0 / (beta * n);
         double sin2 = 1.0 - 1.0 / (beta * beta * n * n);
         sin_tc = sqrt(sin2);
@@ -209,6 +265,7 @@ void or_rotation(const double din[3], double M[9])
 
 typedef struct {
     double n_c, w_c, n_f, w_f, cos_tc, sin_tc;
+    double delta;                 /* refractivity at the midpoint (dispersion: per photon theta_c) */
 } seg_yield;
 
 /* Photon of bunch k (Sec. 1.2 and Fig. 1: created at the origin pointing
@@ -219,7 +276,7 @@ typedef struct {
  * key (seed, stream); u0 -> wavelength, u1 -> emission point,
  * u2 -> azimuth, u3 -> cos(theta) of fluorescence. */
 static void photon_of(const or_segment *s, int64_t seg_index, uint32_t k, const seg_yield *y,
-                      const or_params *p, double out[10])
+                      const or_atmosphere *a, const or_params *p, double out[10])
 {
     double d[3];
     float df[3] = {s->dx, s->dy, s->dz};
@@ -234,11 +291,39 @@ static void photon_of(const or_segment *s, int64_t seg_index, uint32_t k, const 
     double u0 = or_u01(x[0]), u1 = or_u01(x[1]), u2 = or_u01(x[2]), u3 = or_u01(x[3]);
     double lambda, dg[3], w;
     if (process == 0) {
-        /* wavelength density proportional to 1/lambda^2 (Frank-Tamm) */
-        double inv = 1.0 / p->lambda1 - u0 * (1.0 / p->lambda1 - 1.0 / p->lambda2);
-        lambda = 1.0 / inv;
+        double cos_tc = y->cos_tc, sin_tc = y->sin_tc;
+        if (a->disp_B > 0) {
+            /* u = 1/lambda with density (1 - 1/(beta n(u))^2) on the band above
+             * threshold, by rejection: proposal 0 uses (u0, u3), proposal m >= 1
+             * word pair (m - 1) % 2 of Philox with counter word 3 = 2 + (m - 1) / 2;
+             * after 64 proposals the last one stands (reading) */
+            double eps = (double)s->eps, ulo, uhi;
+            disp_band(a, p, y->delta, eps, &ulo, &uhi);
+            double fmax = disp_f(a, y->delta, eps, uhi);
+            double v = u0, w = u3, u = ulo;
+            uint32_t xr[4];
+            for (int m = 0;; m++) {
+                u = ulo + v * (uhi - ulo);
+                if (w * fmax < disp_f(a, y->delta, eps, u) || m == 64) break;
+                if (m % 2 == 0) {
+                    uint32_t c2[4] = {ctr[0], ctr[1], ctr[2], 2u + (uint32_t)(m / 2)};
+                    or_philox4x32_10(c2, key, xr);
+                    v = or_u01(xr[0]); w = or_u01(xr[1]);
+                } else {
+                    v = or_u01(xr[2]); w = or_u01(xr[3]);
+                }
+            }
+            lambda = 1.0 / u;
+            double g1 = disp_g1(a, y->delta, eps, u);
+            cos_tc = 1.0 / (1.0 + g1);
+            sin_tc = sqrt(g1 * (2.0 + g1)) / (1.0 + g1);
+        } else {
+            /* wavelength density proportional to 1/lambda^2 (Frank-Tamm) */
+            double inv = 1.0 / p->lambda1 - u0 * (1.0 / p->lambda1 - 1.0 / p->lambda2);
+            lambda = 1.0 / inv;
+        }
         double c = 2.0 * OR_PI * u2;
-        double pv[3] = {cos(c) * y->sin_tc, sin(c) * y->sin_tc, -y->cos_tc};
+        double pv[3] = {cos(c) * sin_tc, sin(c) * sin_tc, -cos_tc};
         double M[9];
         or_rotation(d, M);
         for (int i = 0; i < 3; i++) dg[i] = M[3 * i] * pv[0] + M[3 * i + 1] * pv[1] + M[3 * i + 2] * pv[2];
@@ -282,6 +367,7 @@ static void yield_struct(const or_segment *s, const or_atmosphere *a, const or_p
     or_yield(s, a, p, o);
     y->n_c = o[0]; y->w_c = o[1]; y->n_f = o[2]; y->w_f = o[3];
     y->cos_tc = o[4]; y->sin_tc = o[5];
+    y->delta = o[8];
 }
 
 void or_photon(const or_segment *s, int64_t seg_index, uint32_t k,
@@ -289,7 +375,7 @@ void or_photon(const or_segment *s, int64_t seg_index, uint32_t k,
 {
     seg_yield y;
     yield_struct(s, a, p, &y);
-    photon_of(s, seg_index, k, &y, p, out);
+    photon_of(s, seg_index, k, &y, a, p, out);
 }
 
 /* ------------------------------------------------------------------------
@@ -324,6 +410,20 @@ static void gl_init(void)
 }
 
 __attribute__((constructor)) static void or_init(void) { gl_init(); }
+
+/* int_{u_lo}^{u_hi} (1 - 1/(beta n(u))^2) du by Gauss-Legendre on 8 panels
+ * (the integrand is a smooth rational function of u^2). */
+static double disp_integral(const or_atmosphere *a, double delta, double eps, double u_lo, double u_hi)
+{
+    gl_init();
+    const int panels = 8;
+    double h = (u_hi - u_lo) / panels, sum = 0;
+    for (int q = 0; q < panels; q++) {
+        double lo = u_lo + q * h, mid = lo + 0.5 * h;
+        for (int i = 0; i < GLN; i++) sum += 0.5 * h * gl_w[i] * disp_f(a, delta, eps, mid + 0.5 * h * gl_x[i]);
+    }
+    return sum;
+}
 
 typedef struct {
     const or_atmosphere *a;
@@ -432,6 +532,12 @@ static void integrate_path(const ray_ctx *c, double h0, double h1, double out[3]
 void or_propagate(const or_atmosphere *a, const double r_e[3], const double din[3],
                   double t_e, double lambda, double out[10])
 {
+    or_atmosphere ad;
+    if (a->disp_B > 0) {          /* n - 1 = delta(h) g(lambda): K scaled for this photon */
+        ad = *a;
+        ad.K = a->K * or_disp_g(a, lambda);
+        a = &ad;
+    }
     double nd = sqrt(din[0] * din[0] + din[1] * din[1] + din[2] * din[2]);
     double d[3] = {din[0] / nd, din[1] / nd, din[2] / nd};
     for (int i = 0; i < 10; i++) out[i] = 0;
@@ -590,7 +696,7 @@ int64_t or_trace(const or_segment *segs, int64_t n_segs,
         uint32_t nb = (uint32_t)(y.n_c + y.n_f);
         for (uint32_t k = 0; k < nb; k++) {
             double ph[10], pr[10];
-            photon_of(s, p->seg_base + i, k, &y, p, ph);
+            photon_of(s, p->seg_base + i, k, &y, a, p, ph);
             or_propagate(a, ph, ph + 3, ph[6], ph[7], pr);
             st[tid * 5 + 0]++;
             int status = (int)pr[0];
@@ -663,6 +769,7 @@ static void frozen_yield(const or_segment *s, const or_atmosphere *a, const or_p
     y->w_f = nbf > 0 ? o[7] / nbf : 0;
     y->cos_tc = o[4];
     y->sin_tc = o[5];
+    y->delta = o[8];
 }
 
 static double logistic(double x) { return 1.0 / (1.0 + exp(-x)); }
@@ -690,7 +797,7 @@ void or_soft_yield(const or_segment *segs, int64_t n_segs, const uint32_t *n_bun
         uint32_t nb = n_bunch_c[i] + n_bunch_f[i];
         for (uint32_t k = 0; k < nb; k++) {
             double ph[10], pr[10];
-            photon_of(&segs[i], p->seg_base + i, k, &y, p, ph);
+            photon_of(&segs[i], p->seg_base + i, k, &y, a, p, ph);
             or_propagate(a, ph, ph + 3, ph[6], ph[7], pr);
             if ((int)pr[0] != OR_TRACED) continue;
             double w = ph[8] * exp(-pr[8]);
@@ -727,7 +834,7 @@ void or_eval_rays(const or_segment *segs, const int64_t *seg_idx, const uint32_t
         seg_yield y;
         frozen_yield(&segs[si], a, p, n_bunch_c[si], n_bunch_f[si], &y);
         double ph[10], pr[10];
-        photon_of(&segs[si], p->seg_base + si, k[i], &y, p, ph);
+        photon_of(&segs[si], p->seg_base + si, k[i], &y, a, p, ph);
         or_propagate(a, ph, ph + 3, ph[6], ph[7], pr);
         double *o = out + 5 * i;
         if ((int)pr[0] != OR_TRACED) {

@@ -49,6 +49,9 @@ typedef struct {
     double L0, lambda_ref;        /* extinction length L0 (lambda/lambda_ref)^4 */
     double R_E, h_obs;
     int spherical, refraction, absorption;
+    /* dispersion (reading): n(lambda, h) - 1 = delta(h) g(lambda),
+     * g = (1 + B/lambda^2) / (1 + B/lambda_d^2); B = 0: none */
+    double disp_B, disp_lref;     /* nm^2, nm */
 } or_atmosphere;
 
 typedef struct {
@@ -99,6 +102,8 @@ void or_propagate(const or_atmosphere *a, const double r_e[3], const double d[3]
 
 /* Refractive-index excess and density at altitude h. */
 double or_delta(const or_atmosphere *a, double h);
+/* The dispersion factor g(lambda) (1 without dispersion). */
+double or_disp_g(const or_atmosphere *a, double lambda);
 double or_density(const or_atmosphere *a, double h);
 
 /* Full trace.  Writes at most `capacity` hits, sorted by

@@ -43,7 +43,8 @@ class Atmosphere(C.Structure):
                 ("h_lo", C.c_double * 8), ("b", C.c_double * 8), ("c", C.c_double * 8),
                 ("h_top", C.c_double), ("K", C.c_double), ("rho_ref", C.c_double),
                 ("L0", C.c_double), ("lambda_ref", C.c_double), ("R_E", C.c_double),
-                ("h_obs", C.c_double), ("refraction", C.c_int32), ("absorption", C.c_int32)]
+                ("h_obs", C.c_double), ("refraction", C.c_int32), ("absorption", C.c_int32),
+                ("disp_B", C.c_double), ("disp_lref", C.c_double)]
 
 
 class Params(C.Structure):
@@ -118,6 +119,7 @@ def atmosphere_struct(a: inputs.Atmosphere) -> Atmosphere:
     s.h_top, s.K, s.rho_ref = a.h_top, a.K, a.rho_ref
     s.L0, s.lambda_ref, s.R_E, s.h_obs = a.L0, a.lambda_ref, a.R_E, a.h_obs
     s.refraction, s.absorption = int(a.refraction), int(a.absorption)
+    s.disp_B, s.disp_lref = float(getattr(a, "disp_B", 0.0)), float(getattr(a, "disp_lref", 400.0))
     return s
 
 

@@ -195,6 +195,8 @@ clight_status clight_set_atmosphere(clight_ctx *c, const clight_atmosphere *a)
     if (a->absorption && (!(a->L0 > 0) || !(a->lambda_ref > 0))) return CLIGHT_ERR_ARG;
     if (a->spherical && !(a->R_E > 0)) return CLIGHT_ERR_ARG;
     if (a->n_layers > 1 && a->h_lo[0] > a->h_obs) return CLIGHT_ERR_ARG;
+    if (!(a->disp_B >= 0) || !std::isfinite(a->disp_B) || (a->disp_B > 0 && !(a->disp_lref > 0)))
+        return CLIGHT_ERR_ARG;
     DevAtm &A = c->atm;
     A = DevAtm{};
     A.n_layers = a->n_layers;
@@ -259,6 +261,11 @@ clight_status clight_set_atmosphere(clight_ctx *c, const clight_atmosphere *a)
         A.D_obs = (float)(a->c[io] * a->K * Bc(io) * eo + A.lay_E[io]);
         A.R_obs = (float)(a->c[io] * Bc(io) / a->rho_ref * eo + A.lay_F[io]);
     }
+    A.disp = a->disp_B > 0 ? 1 : 0;
+    A.disp_B_d = a->disp_B;
+    A.disp_ig0_d = A.disp ? 1.0 / (1.0 + a->disp_B / (a->disp_lref * a->disp_lref)) : 1.0;
+    A.disp_B = (float)A.disp_B_d;
+    A.disp_ig0 = (float)A.disp_ig0_d;
     A.inv_L0_d = a->absorption ? 1.0 / a->L0 : 0.0;
     A.inv_L0 = (float)A.inv_L0_d;
     A.lambda_ref_d = a->absorption ? a->lambda_ref : 1.0;
@@ -447,6 +454,8 @@ clight_status clight_set_params(clight_ctx *c, const clight_params *p)
     const double alpha = 7.2973525643e-3, pi = 3.14159265358979323846;
     P.band_d = 2.0 * pi * alpha * (1.0 / p->lambda1 - 1.0 / p->lambda2) * 1e9;
     P.band = (float)P.band_d;
+    P.fta_d = 2.0 * pi * alpha * 1e9;
+    P.fta = (float)P.fta_d;
     P.bunch_d = p->bunch;
     P.bunch = (float)p->bunch;
     P.inv_bunch = (float)(1.0 / p->bunch);
@@ -781,6 +790,7 @@ extern "C" clight_status clight_trace_adjoint(clight_ctx *c, const clight_segmen
 {
     if (!c || !c->atm_set || !c->tel_set || !h_grad || n_segs < 0 || n_hits < 0 || n_showers < 1)
         return CLIGHT_ERR_ARG;
+    if (c->atm.disp) return CLIGHT_ERR_ARG;       // the tangents assume no dispersion
     if ((n_segs > 0 && !d_segs) || (n_hits > 0 && !d_hits) || !(soft_s > 0) || !(soft_w >= 0))
         return CLIGHT_ERR_ARG;
     if (n_segs > (int64_t(1) << 31)) return CLIGHT_ERR_LIMIT;

@@ -41,6 +41,10 @@ struct DevAtm {
     // and both integrals from h_obs
     float lay_c[kMaxLayers], lay_E[kMaxLayers], lay_F[kMaxLayers];
     float D_obs, R_obs;
+    // dispersion: n - 1 = delta(h) (1 + B/lambda^2) inv_g0
+    int disp;
+    float disp_B, disp_ig0;
+    double disp_B_d, disp_ig0_d;
     DevCell cells[kMaxCells];
     double cell_lo_d[kMaxCells], cell_hi_d[kMaxCells], cell_kb_d[kMaxCells], cell_rb_d[kMaxCells],
         cell_ic_d[kMaxCells];                 // binary64 copies; ic = 1/c
@@ -68,6 +72,8 @@ constexpr int kClrMaxCells = 10240;      // 10 KB of shared memory per CTA
 
 struct DevPar {
     float band, inv_bunch;       // 2 pi alpha (1/l1 - 1/l2) [1/m], 1/B
+    float fta;                   // 2 pi alpha 1e9 (the yield per unit of u = 1/lambda in 1/nm)
+    double fta_d;
     double band_d, bunch_d;
     float il1, dil;              // 1/lambda1, 1/lambda1 - 1/lambda2 (1/nm)
     double il1_d, dil_d;

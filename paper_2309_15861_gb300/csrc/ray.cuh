@@ -280,6 +280,139 @@ __device__ __forceinline__ void cone_direction(T ux, T uy, T uz, T omct, T sp, T
     z = ct * uz + st * (cp * e1z + sp * e2z);
 }
 
+template <class T> __device__ __forceinline__ T fmax_t(T a, T b) { return a > b ? a : b; }
+
+// ------------------------------------------------------------------ dispersion
+// Sec. 1.2 keeps n(lambda) inside the Frank-Tamm integral.  With
+// n - 1 = delta(h) g(lambda), g = (1 + B u^2) ig0 and u = 1/lambda (1/nm),
+// beta n(u) - 1 = db g(u) - eps with db = delta (1 - eps); the yield is
+// 2 pi alpha z^2 L int (1 - 1/(beta n)^2) du over the band where beta n > 1,
+// and a photon's u has that integrand as its density.
+template <class T> __device__ __forceinline__ T disp_gu(const DevAtm &A, T u)
+{
+    return sizeof(T) == 4 ? ((T)1 + (T)A.disp_B * u * u) * (T)A.disp_ig0
+                          : ((T)1 + (T)A.disp_B_d * u * u) * (T)A.disp_ig0_d;
+}
+template <class T> __device__ __forceinline__ T disp_f(const DevAtm &A, T db, T eps, T u)
+{
+    T g1 = db * disp_gu<T>(A, u) - eps;
+    if (!(g1 > (T)0)) return (T)0;
+    T ib = (T)1 / ((T)1 + g1);
+    return g1 * ((T)2 + g1) * ib * ib;
+}
+// the band [ulo, uhi] of u above threshold; false if empty
+template <class T> __device__ __forceinline__ bool disp_band(const DevAtm &A, const DevPar &P, T db, T eps, T &ulo,
+                                                             T &uhi)
+{
+    if (!(db > (T)0)) return false;
+    const T B = sizeof(T) == 4 ? (T)A.disp_B : (T)A.disp_B_d;
+    const T ig0 = sizeof(T) == 4 ? (T)A.disp_ig0 : (T)A.disp_ig0_d;
+    const T il1 = sizeof(T) == 4 ? (T)P.il1 : (T)P.il1_d, dil = sizeof(T) == 4 ? (T)P.dil : (T)P.dil_d;
+    T t = (eps / (db * ig0) - (T)1) / B;             // u_threshold^2
+    T ut = t > (T)0 ? sqrt(t) : (T)0;
+    T u2 = il1 - dil;
+    ulo = ut > u2 ? ut : u2;
+    uhi = il1;
+    return ulo < uhi;
+}
+// int_ulo^uhi (1 - 1/(beta n)^2) du, 3-node Gauss-Legendre on `panels` panels
+template <class T> __device__ __forceinline__ T disp_integral(const DevAtm &A, T db, T eps, T ulo, T uhi, int panels)
+{
+    T h = (uhi - ulo) / (T)panels, s = (T)0;
+    for (int q = 0; q < panels; ++q) {
+        T mid = ulo + ((T)q + (T)0.5) * h;
+#pragma unroll
+        for (int i = 0; i < kGLNodes; ++i) {
+            T xg = sizeof(T) == 4 ? (T)A.gl_x[i] : (T)A.gl_x_d[i];
+            T wg = sizeof(T) == 4 ? (T)A.gl_w[i] : (T)A.gl_w_d[i];
+            s += wg * disp_f<T>(A, db, eps, mid + (T)0.5 * h * xg);
+        }
+    }
+    return (T)0.5 * h * s;
+}
+// binary64 acceptance of a wavelength proposal, in the oracle's form
+// (g1 = delta g - eps - eps delta g), for proposals binary32 cannot decide
+__device__ __forceinline__ bool disp_accept_d(const DevAtm &A, const DevPar &P, double delta, double eps, double v,
+                                              double w)
+{
+    double db = delta * (1.0 - eps), ulo, uhi;
+    if (!disp_band<double>(A, P, db, eps, ulo, uhi)) return false;
+    auto f = [&](double u) {
+        double dg = delta * disp_gu<double>(A, u);
+        double g1 = dg - eps - eps * dg;
+        return g1 > 0 ? g1 * (2.0 + g1) / ((1.0 + g1) * (1.0 + g1)) : 0.0;
+    };
+    double u = ulo + v * (uhi - ulo);
+    return w * f(uhi) < f(u);
+}
+
+// Wavelength of a Cherenkov photon with dispersion: u = 1/lambda by
+// rejection on the band above threshold.  Proposal 0 uses (u0, u3); proposal
+// m >= 1 uses word pair (m - 1) % 2 of Philox with counter word 3 =
+// 2 + (m - 1) / 2; after 64 proposals the last one stands.  binary32, with
+// proposals too close to call decided in binary64 from the midpoint
+// refractivity recomputed at (xm, ym, zm).
+static __device__ __noinline__ float disp_sample_f(const DevAtm &A, const DevPar &P, float db, float eps, float u0,
+                                                   float u3, int64_t seg_global, uint32_t kk, double xm, double ym,
+                                                   double zm, bool sph)
+{
+    float ulo, uhi;
+    disp_band<float>(A, P, db, eps, ulo, uhi);
+    float fmax = disp_f<float>(A, db, eps, uhi);
+    float gt = db * disp_gu<float>(A, uhi);
+    float band = 1.0e-6f * (1.0f + (gt + eps) / fmaxf(gt - eps, 1e-30f)) * fmax;
+    float v = u0, wv = u3, u = ulo;
+    uint4 xr = make_uint4(0u, 0u, 0u, 0u);
+    double dmid = -1.0;
+    for (int m = 0;; ++m) {
+        u = ulo + v * (uhi - ulo);
+        float diff = wv * fmax - disp_f<float>(A, db, eps, u);
+        bool acc;
+        if (fabsf(diff) <= band) {
+            if (dmid < 0.0)
+                dmid = AtmT<double>::delta(A, sph ? altitude<double, true>(A, xm, ym, zm) : zm);
+            acc = disp_accept_d(A, P, dmid, (double)eps, (double)v, (double)wv);
+        } else {
+            acc = diff < 0.0f;
+        }
+        if (acc || m == 64) break;
+        if ((m & 1) == 0) {
+            xr = philox4x32_10(make_uint4((uint32_t)(uint64_t)seg_global, (uint32_t)((uint64_t)seg_global >> 32), kk,
+                                          2u + (uint32_t)(m >> 1)),
+                               P.seed, P.stream);
+            v = u01<float>(xr.x); wv = u01<float>(xr.y);
+        } else {
+            v = u01<float>(xr.z); wv = u01<float>(xr.w);
+        }
+    }
+    return u;
+}
+
+// the same in binary64 (plain path)
+static __device__ __noinline__ double disp_sample_d(const DevAtm &A, const DevPar &P, double db, double eps,
+                                                    double u0, double u3, int64_t seg_global, uint32_t kk)
+{
+    double ulo, uhi;
+    disp_band<double>(A, P, db, eps, ulo, uhi);
+    double fmax = disp_f<double>(A, db, eps, uhi);
+    double v = u0, wv = u3, u = ulo;
+    uint4 xr = make_uint4(0u, 0u, 0u, 0u);
+    for (int m = 0;; ++m) {
+        u = ulo + v * (uhi - ulo);
+        if (wv * fmax < disp_f<double>(A, db, eps, u) || m == 64) break;
+        if ((m & 1) == 0) {
+            xr = philox4x32_10(make_uint4((uint32_t)(uint64_t)seg_global, (uint32_t)((uint64_t)seg_global >> 32), kk,
+                                          2u + (uint32_t)(m >> 1)),
+                               P.seed, P.stream);
+            v = u01<double>(xr.x); wv = u01<double>(xr.y);
+        } else {
+            v = u01<double>(xr.z); wv = u01<double>(xr.w);
+        }
+    }
+    return u;
+}
+
+
 // Yield and bunch count in binary64 (the plain path, and the guard of the
 // FP32 path when its count is not certain).  Frank-Tamm (Sec. 1.2):
 // N = 2 pi alpha z^2 (1/l1 - 1/l2) (1 - 1/(beta n)^2) L for beta n > 1.
@@ -304,7 +437,15 @@ __device__ __forceinline__ void yield_fp64(const clight_segment &s, const DevAtm
     *Nc = 0.0;
     *sin2 = 0.0;
     *kappa = 0.0;
-    if (z2 > 0.0 && g1 > 0.0 && s.L > 0.0f) {
+    double ulo, uhi;
+    if (A.disp) {
+        // the wavelength integral; the angle is per photon (db and eps passed on)
+        double db = dl * (1.0 - eps);
+        if (z2 > 0.0 && s.L > 0.0f && disp_band<double>(A, P, db, eps, ulo, uhi))
+            *Nc = P.fta_d * z2 * disp_integral<double>(A, db, eps, ulo, uhi, 16) * (double)s.L;
+        *sin2 = db;
+        *kappa = eps;
+    } else if (z2 > 0.0 && g1 > 0.0 && s.L > 0.0f) {
         double bn = 1.0 + g1;
         *kappa = g1 / bn;                           // 1 - cos(theta_c)
         *sin2 = g1 * (2.0 + g1) / (bn * bn);        // 1 - 1/(beta n)^2
@@ -460,7 +601,7 @@ __device__ __forceinline__ void make_frame(Seg<T, P> &g)
 // binary32 segment set-up with the binary64 guard on the integer bunch count.
 // EXT = false drops the optional angular cut and fluorescence beaming from
 // the compiled code (the launcher picks it when neither is on).
-template <bool SPH, bool EXT = true>
+template <bool SPH, bool EXT = true, bool DISP = true>
 __device__ void load_segment_f(const clight_segment &s, const DevAtm &A, const DevPar &P, Seg<float, df> &g)
 {
     g.bad = 0;
@@ -517,7 +658,26 @@ __device__ void load_segment_f(const clight_segment &s, const DevAtm &A, const D
     float eg = 4.0e-6f * dl + 2.4e-7f * (dl + eps);
     bool guard = false;
     float Nc = 0.0f;
-    if (z2 > 0.0f && s.L > 0.0f) {
+    if (DISP && A.disp) {
+        // dispersion: the band integral; per-photon angles from (db, eps)
+        float db = dl * (1.0f - eps), ulo, uhi;
+        if (z2 > 0.0f && s.L > 0.0f) {
+            bool band = disp_band<float>(A, P, db, eps, ulo, uhi);
+            if (band) {
+                Nc = P.fta * z2 * disp_integral<float>(A, db, eps, ulo, uhi, 4) * s.L;
+                float gt = db * disp_gu<float>(A, uhi);
+                float kap = (gt + eps) / fmaxf(gt - eps, 1e-30f);   // condition at the band top
+                float x = Nc * P.inv_bunch;
+                float ex = x * (2.0e-5f + 4.0e-6f * kap) + 1.0e-6f;
+                if (ceilf(x - ex) != ceilf(x + ex)) guard = true;
+                else g.n_c = (uint32_t)ceilf(x);
+            } else if (ulo < uhi * (1.0f + 1.0e-5f)) {
+                guard = true;                // the threshold sits at the band edge
+            }
+        }
+        g.sin_tc = db;
+        g.kappa = eps;
+    } else if (z2 > 0.0f && s.L > 0.0f) {
         if (g1 > eg) {
             float bn = 1.0f + g1;
             float ib = rcp_approx(bn);
@@ -535,7 +695,7 @@ __device__ void load_segment_f(const clight_segment &s, const DevAtm &A, const D
             guard = true;
         }
     }
-    if (!guard && g.n_c == 0) { g.sin_tc = 0.0f; g.kappa = 0.0f; }
+    if (!guard && g.n_c == 0 && !(DISP && A.disp)) { g.sin_tc = 0.0f; g.kappa = 0.0f; }
     float Nf = 0.0f;
     bool fguard = false;
     if (P.fyield > 0.0f && s.dE > 0.0f && s.L > 0.0f) {
@@ -560,7 +720,7 @@ __device__ void load_segment_f(const clight_segment &s, const DevAtm &A, const D
             double nb = ceil(Ncd / P.bunch_d);
             g.n_c = (uint32_t)nb;
             Nc = (float)Ncd;
-            g.sin_tc = (float)sqrt(sin2d);
+            g.sin_tc = (DISP && A.disp) ? (float)sin2d : (float)sqrt(sin2d);
             g.kappa = (float)kapd;
             if (g.n_c > 0) g.w_c = (float)(Ncd / nb);
         }
@@ -606,7 +766,7 @@ __device__ void load_segment_d(const clight_segment &s, const DevAtm &A, const D
         Nc = 0.0;
     }
     if (Nf > 0.0 && P.beam && !beam_cone_t(g, P, g.bux, g.buy, g.buz, g.bomc)) g.bomc = 0.0;
-    g.sin_tc = sqrt(sin2);
+    g.sin_tc = A.disp ? sin2 : sqrt(sin2);          // dispersion: (db, eps) for per-photon angles
     g.kappa = kap;
     if (Nc > 0.0) {
         double nb = ceil(Nc / P.bunch_d);
@@ -638,8 +798,8 @@ template <class T, class P> struct RayOut {
 // r = R_E + h (spherical) or 1 (flat); q_v = r^2 - p_v^2,
 // q = n^2 q_v + (n^2 - n_e^2) p_v^2 = n^2 r^2 - (n_e p_v)^2.
 template <class T, bool WARP, bool SPH, bool REFR>
-__device__ __forceinline__ void ray_quadrature(const DevAtm &A, T hcap, T he, T de, T pv2, T bf2, T &I0, T &I1,
-                                               T &I2, uint32_t &ncell)
+__device__ __forceinline__ void ray_quadrature(const DevAtm &A, T hcap, T he, T de, T pv2, T bf2, T gl, T &I0,
+                                               T &I1, T &I2, uint32_t &ncell)
 {
     I0 = I1 = I2 = (T)0;
     const T RE = earth_radius<T>(A);
@@ -658,7 +818,7 @@ __device__ __forceinline__ void ray_quadrature(const DevAtm &A, T hcap, T he, T 
         T chi = sizeof(T) == 4 ? (T)C.hi : (T)A.cell_hi_d[c];
         T hi = hcap < chi ? hcap : chi;
         T mid = (T)0.5 * (lo + hi), half = (T)0.5 * (hi - lo);
-        T kb = sizeof(T) == 4 ? (T)C.kb : (T)A.cell_kb_d[c];
+        T kb = (sizeof(T) == 4 ? (T)C.kb : (T)A.cell_kb_d[c]) * gl;
         T rb = sizeof(T) == 4 ? (T)C.rb : (T)A.cell_rb_d[c];
         T nl = sizeof(T) == 4 ? (T)C.nl2c : (T)-A.cell_ic_d[c];
         T s0 = 0, s1 = 0, s2 = 0;
@@ -702,8 +862,8 @@ __device__ __forceinline__ void ray_quadrature(const DevAtm &A, T hcap, T he, T 
 // (I0: the flat horizontal shortfall per unit sin, or the spherical angle
 // shortfall per unit p_v; I1: optical excess; I2: density path).
 template <class T, bool SPH, bool REFR>
-__device__ __forceinline__ void straight_corrections(const DevAtm &A, T he, T de, T pv2, T bf2, T &I0, T &I1,
-                                                     T &I2)
+__device__ __forceinline__ void straight_corrections(const DevAtm &A, T he, T de, T pv2, T bf2, T gl, T &I0,
+                                                     T &I1, T &I2)
 {
     const float hf = (float)he;
     float Dh, Rh;                                     // int_h^top delta, rho / rho_ref
@@ -718,7 +878,7 @@ __device__ __forceinline__ void straight_corrections(const DevAtm &A, T he, T de
         Dh = A.lay_c[i] * A.kb[i] * ex + A.lay_E[i];
         Rh = A.lay_c[i] * A.rb[i] * ex + A.lay_F[i];
     }
-    T J = (T)(A.D_obs - Dh), Jr = (T)(A.R_obs - Rh);
+    T J = (T)(A.D_obs - Dh) * gl, Jr = (T)(A.R_obs - Rh);
     const T h_obs = sizeof(T) == 4 ? (T)A.h_obs : (T)A.h_obs_d;
     T corr = de * (he - h_obs) - J;
     T mu2, s2, r2 = (T)1;
@@ -742,8 +902,10 @@ __device__ __forceinline__ void straight_corrections(const DevAtm &A, T he, T de
 // Optional features of the per-ray code, fixed at compile time so that the
 // default kernel carries none of them: FEAT_EXT the angular cut and the
 // fluorescence beaming; FEAT_STRAIGHT the straight-line propagator only (no
-// quadrature); FEAT_RUNTIME both propagators, chosen by DevPar::prop.
-constexpr int FEAT_EXT = 1, FEAT_STRAIGHT = 2, FEAT_RUNTIME = 4, FEAT_ALL = FEAT_EXT | FEAT_RUNTIME;
+// quadrature); FEAT_RUNTIME both propagators, chosen by DevPar::prop;
+// FEAT_DISP dispersion, active when DevAtm::disp.
+constexpr int FEAT_EXT = 1, FEAT_STRAIGHT = 2, FEAT_RUNTIME = 4, FEAT_DISP = 8,
+              FEAT_ALL = FEAT_EXT | FEAT_RUNTIME | FEAT_DISP;
 
 template <class T, class P, bool WARP, bool SPH, bool REFR, int FEAT = FEAT_ALL>
 __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global, uint32_t k, bool active,
@@ -759,15 +921,37 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
     P dgx, dgy, dgz;
     T lam, w;
     if (proc == 0) {
-        T il1 = sizeof(T) == 4 ? (T)Pp.il1 : (T)Pp.il1_d;
-        T dil = sizeof(T) == 4 ? (T)Pp.dil : (T)Pp.dil_d;
-        lam = Num<T>::div((T)1, il1 - u0 * dil);           // density ~ 1/lambda^2
+        T st = g.sin_tc, kap = g.kappa;
+        if ((FEAT & FEAT_DISP) && A.disp) {
+            // dispersion: u = 1/lambda by rejection on the band above threshold
+            // (proposal 0 from (u0, u3); proposal m >= 1 from word pair (m - 1) % 2
+            // of Philox with counter word 3 = 2 + (m - 1) / 2; the 64th stands)
+            T db = g.sin_tc, eps = g.kappa;
+            T u;
+            if (sizeof(T) == 4) {
+                double hl = 0.5 * (double)g.L;
+                u = (T)disp_sample_f(A, Pp, (float)db, (float)eps, (float)u0, (float)u3, seg_global, kk,
+                                     p_d(g.x0) + hl * ((double)g.dx + (double)g.lx),
+                                     p_d(g.y0) + hl * ((double)g.dy + (double)g.ly),
+                                     p_d(g.z0) + hl * ((double)g.dz + (double)g.lz), SPH);
+            } else {
+                u = (T)disp_sample_d(A, Pp, (double)db, (double)eps, (double)u0, (double)u3, seg_global, kk);
+            }
+            lam = (T)1 / u;
+            T g1 = db * disp_gu<T>(A, u) - eps;
+            T ib = (T)1 / ((T)1 + g1);
+            st = sqrt(g1 * ((T)2 + g1)) * ib;
+            kap = g1 * ib;
+        } else {
+            T il1 = sizeof(T) == 4 ? (T)Pp.il1 : (T)Pp.il1_d;
+            T dil = sizeof(T) == 4 ? (T)Pp.dil : (T)Pp.dil_d;
+            lam = Num<T>::div((T)1, il1 - u0 * dil);       // density ~ 1/lambda^2
+        }
         T sc, cc;
         Num<T>::sincos2pi(u2, &sc, &cc);
-        T st = g.sin_tc;
-        T sx = -g.kappa * g.dx + st * (cc * g.e1x + sc * g.e2x);
-        T sy = -g.kappa * g.dy + st * (cc * g.e1y + sc * g.e2y);
-        T sz = -g.kappa * g.dz + st * (cc * g.e1z + sc * g.e2z);
+        T sx = -kap * g.dx + st * (cc * g.e1x + sc * g.e2x);
+        T sy = -kap * g.dy + st * (cc * g.e1y + sc * g.e2y);
+        T sz = -kap * g.dz + st * (cc * g.e1z + sc * g.e2z);
         // cos(theta_c) d + sin(theta_c)(cos c e1 + sin c e2), d kept as a pair
         dgx = p_of<P>(g.dx) + (g.lx + sx);
         dgy = p_of<P>(g.dy) + (g.ly + sy);
@@ -794,6 +978,8 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
         }
         w = g.w_f;
     }
+    // dispersion: this photon's refractivity is delta(h) g(lambda)
+    const T gl = ((FEAT & FEAT_DISP) && A.disp) ? disp_gu<T>(A, (T)1 / lam) : (T)1;
     T ell = u1 * g.L;
     P xe = g.x0 + ell * (g.dx + g.lx);
     P ye = g.y0 + ell * (g.dy + g.ly);
@@ -816,7 +1002,7 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
         // b = -(d . R_e) = r_e cos(psi_e); C = |R_e|^2 - r_obs^2
         P b = -(dgz * Rz) - (dx * xef + dy * yef);
         he = altitude<T, SPH>(A, xef, yef, zef);
-        de = AtmT<T>::delta(A, he);                          // n_e - 1
+        de = AtmT<T>::delta(A, he) * gl;                     // n_e - 1
         esc = !(p_f(b) > 0.0f);
         under = he <= h_obs;
         P dzo = ze - Hobs;
@@ -835,7 +1021,7 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
         if (REFR) {
             // reaches the observation sphere iff q(r_obs) > 0, with
             // q_v(r_obs) = disc: q(r_obs) = n_obs^2 disc + (n_obs^2 - n_e^2) p_v^2
-            T dob = sizeof(T) == 4 ? (T)A.delta_obs : (T)A.delta_obs_d;
+            T dob = (sizeof(T) == 4 ? (T)A.delta_obs : (T)A.delta_obs_d) * gl;
             T nob = (T)1 + dob;
             T qL = nob * nob * discf + (dob - de) * ((T)2 + dob + de) * pv2;
             turned = !(qL > (T)0);
@@ -856,7 +1042,7 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
         }
     } else {
         he = zef;
-        de = AtmT<T>::delta(A, he);
+        de = AtmT<T>::delta(A, he) * gl;
         esc = !(p_f(dgz) < 0.0f);
         under = !(p_f(ze - Hobs) > 0.0f);
         if (!(esc || under)) s_v = (ze - Hobs) / (-dgz);
@@ -884,14 +1070,14 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
         // ray falls short horizontally by sin / mu^3 * corr, its optical path
         // exceeds the vacuum one by J / mu + sin^2 / mu^3 * corr, and its
         // density path is int rho / rho_ref dh / mu (layer closed forms).
-        straight_corrections<T, SPH, REFR>(A, go ? he : h_obs, de, pv2, bf2, I0, I1, I2);
+        straight_corrections<T, SPH, REFR>(A, go ? he : h_obs, de, pv2, bf2, gl, I0, I1, I2);
     } else {
-        ray_quadrature<T, WARP, SPH, REFR>(A, hcap, he, de, pv2, bf2, I0, I1, I2, o.cells);
+        ray_quadrature<T, WARP, SPH, REFR>(A, hcap, he, de, pv2, bf2, gl, I0, I1, I2, o.cells);
     }
     if (!go) return;
 
-    const T n_obs = sizeof(T) == 4 ? (T)A.n_obs : (T)1 + (T)A.delta_obs_d;
-    const T d_obs = sizeof(T) == 4 ? (T)A.delta_obs : (T)A.delta_obs_d;
+    const T d_obs = (sizeof(T) == 4 ? (T)A.delta_obs : (T)A.delta_obs_d) * gl;
+    const T n_obs = (T)1 + d_obs;
     const T ne = (T)1 + de;
     T dLx, dLy, dLz;
     P X, Y, tt;

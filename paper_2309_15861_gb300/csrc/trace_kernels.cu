@@ -87,7 +87,7 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
             const float4 *src = reinterpret_cast<const float4 *>(segs + si);
             float4 *dst = reinterpret_cast<float4 *>(&s);
             dst[0] = __ldg(src); dst[1] = __ldg(src + 1); dst[2] = __ldg(src + 2); dst[3] = __ldg(src + 3);
-            load_segment_f<SPH, EXT>(s, A, Pp, g);
+            load_segment_f<SPH, EXT, (FEAT & FEAT_DISP) != 0>(s, A, Pp, g);
             if (g.bad) status_bits |= 1u << g.bad;
             c_guard += g.guarded;
             c_cut += g.cut;
@@ -312,8 +312,10 @@ static void launch_fused_p(const clight_segment *segs, int64_t n_segs, const Dev
 {
     const bool ext = Pp.cut_mode != CLIGHT_CUT_OFF || Pp.beam;
     const bool str = Pp.prop == CLIGHT_PROP_STRAIGHT;
-    if (!std::is_same<P, df>::value)
+    if (!std::is_same<P, df>::value || (A.disp && (ext || str)))
         launch_fused_pe<P, FEAT_ALL>(segs, n_segs, A, T, Pp, O, grid, block, s);
+    else if (A.disp)
+        launch_fused_pe<P, FEAT_DISP>(segs, n_segs, A, T, Pp, O, grid, block, s);
     else if (ext && str)
         launch_fused_pe<P, FEAT_EXT | FEAT_STRAIGHT>(segs, n_segs, A, T, Pp, O, grid, block, s);
     else if (ext)

@@ -72,6 +72,8 @@ class Atmosphere:
     h_obs: float = 2000.0
     refraction: bool = True
     absorption: bool = True
+    disp_B: float = 0.0          # dispersion: n - 1 = delta(h) (1 + B/l^2)/(1 + B/l_d^2); 0 = none
+    disp_lref: float = 400.0     # nm, the wavelength at which delta(h) holds
 
     @property
     def n_layers(self) -> int:

@@ -181,6 +181,25 @@ def test_straight_line_propagator_is_first_order():
         ctx.close()
 
 
+@pytest.mark.parametrize("B", [20000.0])
+def test_dispersion(ctx, B):
+    """Sec. 1.2 with n(lambda): band-integrated yield, per-photon wavelength
+    by rejection and per-photon Cherenkov angle, delta(h) g(lambda) along
+    each ray (Cauchy form, a stated reading); also through the plain FP64
+    path."""
+    w = I.workload_shower_1tev(n=20_000, seed=61)
+    w.atmosphere.disp_B = B
+    w.atmosphere.disp_lref = 400.0
+    rep, gst, rst = _check(ctx, w)
+    assert rep["n_common"] > 100
+    rep64, gst64, rst64 = _check(ctx, w, fp64=True)
+    assert gst64["rays"] == gst["rays"]
+    # a batch with fluorescence (its photons see g(lambda) too)
+    wb = I.batch_showers(n_showers=4, seed=67, scale=2e-3)
+    wb.atmosphere.disp_B = B
+    _check(ctx, wb)
+
+
 def test_fp64_plain_path(ctx):
     w = I.workload_shower_1tev(n=8000, seed=11)
     rep, gst, rst = _check(ctx, w, fp64=True)

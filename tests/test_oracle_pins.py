@@ -622,3 +622,85 @@ def test_beaming_loses_no_hits_and_keeps_the_mean():
     # means: isotropic photons hit with bunch weight 1 (Poisson); beamed ones carry the cone share
     tot_i, tot_b = si.sum(), sb.sum()
     assert abs(tot_b - tot_i) < 5 * math.sqrt(tot_i) + 5 * math.sqrt(max(1.0, (sb ** 2).sum() / max(1, len(hb)))), (tot_i, tot_b)
+
+
+# ---------------------------------------------------------------- dispersion
+def _disp_atm(B):
+    a = I.atmosphere_layered()
+    a.disp_B = B
+    a.disp_lref = 400.0
+    return a
+
+
+def _one_step(eps, z=8000.0):
+    s = np.zeros(1, dtype=I.SEG_DTYPE)
+    s["z"] = z
+    s["dz"] = -1.0
+    s["L"] = 2.0
+    s["eps"] = eps
+    s["charge"] = -1
+    return s[0]
+
+
+def test_dispersion_yield_against_the_wavelength_integral():
+    """Sec. 1.2's Frank-Tamm double integral with n depending on lambda:
+    the oracle's integral in u = 1/lambda against scipy's quadrature in
+    lambda, below and across the Cherenkov threshold; B -> 0 gives the
+    closed form of the dispersion-free yield."""
+    par = I.Params(bunch=1.0)
+    alpha = SC.fine_structure
+    for B in (5000.0, 20000.0):
+        atm = _disp_atm(B)
+        for eps in (1e-6, 5e-5, 1.5e-4):
+            s = _one_step(eps)
+            y = O.yield_of(s, atm, par)
+            delta = y["delta"]
+            beta = 1.0 - eps
+
+            def integrand(lam):
+                n = 1.0 + delta * O.disp_g(atm, lam)
+                return max(0.0, 1.0 - 1.0 / (beta * n) ** 2) / lam ** 2
+            ref = integrate.quad(integrand, par.lambda1, par.lambda2, limit=400, epsabs=0, epsrel=1e-12)[0]
+            Nref = 2 * math.pi * alpha * 1e9 * ref * float(s["L"])
+            assert (y["Nc"] > 0) == (Nref > 0)
+            if Nref > 0:
+                np.testing.assert_allclose(y["Nc"], Nref, rtol=2e-6)
+    atm0 = _disp_atm(1e-9)
+    s = _one_step(1e-5)
+    y = O.yield_of(s, atm0, par)
+    y_nd = O.yield_of(s, I.atmosphere_layered(), par)
+    np.testing.assert_allclose(y["Nc"], y_nd["Nc"], rtol=1e-9)
+
+
+def test_dispersion_wavelengths_and_cherenkov_angles():
+    """Photon wavelengths follow (1/lambda^2)(1 - 1/(beta n(lambda))^2) on the
+    band above threshold (KS against scipy's CDF), and each photon leaves at
+    cos(theta) = 1/(beta n(lambda)) to its track."""
+    atm = _disp_atm(20000.0)
+    s = _one_step(0.0, z=4000.0)
+    d0 = O.yield_of(s, atm, I.Params())["delta"]
+    eps = 1.02 * d0            # the threshold falls inside 300-600 nm
+    s["eps"] = eps
+    s["L"] = 5.0
+    par = I.Params(bunch=1.0, seed=11)
+    y = O.yield_of(s, atm, par)
+    delta, beta = y["delta"], 1.0 - eps
+    assert y["n_c"] >= 1
+    lams = []
+    segs = np.repeat(s[None], 300)
+    for i in range(300):
+        for k in range(int(y["n_c"])):
+            r, d, te, lam, w, proc = O.photon(segs[i], i, k, atm, par)
+            n = 1.0 + delta * O.disp_g(atm, lam)
+            assert abs(-d[2] - 1.0 / (beta * n)) < 1e-10
+            lams.append(lam)
+    lams = np.array(lams)
+    assert len(lams) >= 300
+
+    def dens(lam):
+        n = 1.0 + delta * O.disp_g(atm, lam)
+        return max(0.0, 1.0 - 1.0 / (beta * n) ** 2) / lam ** 2
+    top = integrate.quad(dens, par.lambda1, par.lambda2, epsrel=1e-10, limit=200)[0]
+    cdf = lambda x: np.array([integrate.quad(dens, par.lambda1, v, epsrel=1e-9, limit=200)[0] / top for v in np.atleast_1d(x)])
+    assert lams.max() < par.lambda2 and dens(lams.max()) > 0
+    assert stats.kstest(lams, cdf).pvalue > 1e-3
