@@ -219,6 +219,7 @@ clight_status clight_set_atmosphere(clight_ctx *c, const clight_atmosphere *a)
     A.h_obs = (float)a->h_obs; A.h_obs_d = a->h_obs;
     A.R_E = (float)a->R_E; A.R_E_d = a->spherical ? a->R_E : 0.0;
     A.r_obs_d = a->R_E + a->h_obs; A.r_obs = (float)A.r_obs_d;
+    A.inv_r_obs_d = 1.0 / A.r_obs_d; A.inv_r_obs = (float)A.inv_r_obs_d;
     auto delta_at = [&](double h) {
         if (h >= a->h_top) return 0.0;
         int i = 0;

@@ -25,7 +25,8 @@ struct DevAtm {
     int n_layers, n_cells, spherical, refraction, absorption, pad;
     float h_lo[kMaxLayers], kb[kMaxLayers], rb[kMaxLayers], nl2c[kMaxLayers];
     double h_lo_d[kMaxLayers], kb_d[kMaxLayers], rb_d[kMaxLayers], inv_c_d[kMaxLayers];
-    float h_top, h_obs, R_E, r_obs;          // binary32 copies
+    float h_top, h_obs, R_E, r_obs, inv_r_obs;  // binary32 copies
+    double inv_r_obs_d;
     double h_top_d, h_obs_d, R_E_d, r_obs_d;  // binary64 copies
     float delta_obs, n_obs;                   // n(h_obs) - 1 and n(h_obs)
     double delta_obs_d;

@@ -1084,15 +1084,21 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
     T chord = 0;
     if (SPH) {
         const T r_obs = sizeof(T) == 4 ? (T)A.r_obs : (T)A.r_obs_d;
+        // the vacuum landing point on the observation sphere; its height
+        // below the tangent plane follows from its horizontal distance
+        // (zv = rho^2 / (r_obs + sqrt(r_obs^2 - rho^2))), so z needs no pair
         P Pvx = xe + s_v * dgx;
         P Pvy = ye + s_v * dgy;
-        P Pvz = ze + s_v * dgz;
-        T RLx = to_t<T>(Pvx), RLy = to_t<T>(Pvy), RLz = to_t<T>(Pvz + pc<P>(A.re_hi, A.re_lo, A.R_E_d));
-        T ir = Num<T>::div((T)1, r_obs);
+        T RLx = to_t<T>(Pvx), RLy = to_t<T>(Pvy);
+        T rho2 = RLx * RLx + RLy * RLy;
+        T zv = Num<T>::div(rho2, r_obs + Num<T>::sqr(r_obs * r_obs - rho2));
+        T RLz = r_obs - zv;
+        T ir = sizeof(T) == 4 ? (T)A.inv_r_obs : (T)A.inv_r_obs_d;
         // T_v = r_obs d + cos(psi_v) R_L: in-plane tangent scaled by p_v
         T Tx = r_obs * dx + sqf * ir * RLx, Ty = r_obs * dy + sqf * ir * RLy, Tz = r_obs * dz + sqf * ir * RLz;
         T Rhx = RLx * ir, Rhy = RLy * ir, Rhz = RLz * ir;
-        P PLx = Pvx, PLy = Pvy, PLz = Pvz;
+        P PLx = Pvx, PLy = Pvy;
+        T zeta = zv;                                          // h_obs - z of the landing point
         if (REFR) {
             T pv = Num<T>::sqr(pv2);
             T dphi = I0 * pv;
@@ -1100,7 +1106,7 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
             T c2 = (T)0.5 * r_obs * dphi * dphi;
             PLx = Pvx + (sfac * Tx - c2 * Rhx);
             PLy = Pvy + (sfac * Ty - c2 * Rhy);
-            PLz = Pvz + (sfac * Tz - c2 * Rhz);
+            zeta = zv - (sfac * Tz - c2 * Rhz);
             T qvL = sqf * sqf;
             T gL = (d_obs - de) * ((T)2 + d_obs + de);
             T qL = n_obs * n_obs * qvL + gL * pv2;
@@ -1116,7 +1122,6 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
             dLx = dx; dLy = dy; dLz = dz;
         }
         // from the observation sphere back to the tangent plane z = h_obs
-        T zeta = -to_t<T>(PLz - Hobs);
         chord = Num<T>::div(zeta, dLz);
         X = PLx + chord * dLx;
         Y = PLy + chord * dLy;
