@@ -173,6 +173,7 @@ template <class T, bool SPH> __device__ __forceinline__ T altitude(const DevAtm 
 template <class T, class P> struct Seg {
     P x0, y0, z0, t0;
     P rz0;               // z0 + R_E (spherical): Earth-centred height of the start
+    P A0, C0;            // spherical: d . R0 and |R0|^2 - r_obs^2, R0 = (x0, y0, z0 + R_E)
     T dx, dy, dz;        // unit direction (binary32 part)
     T lx, ly, lz;        // its normalisation correction (pair low part)
     T e1x, e1y, e1z, e2x, e2y, e2z;   // M_Rod x, M_Rod y
@@ -616,7 +617,7 @@ __device__ void load_segment_f(const clight_segment &s, const DevAtm &A, const D
     if (!segment_ok(s, P) || !(n2 > 0.0f)) {
         g.bad = CLIGHT_ERR_BAD_SEGMENT;
         g.dx = 0; g.dy = 0; g.dz = -1; g.lx = g.ly = g.lz = 0;
-        g.x0 = g.y0 = g.z0 = g.t0 = g.rz0 = df_make(0.0f);
+        g.x0 = g.y0 = g.z0 = g.t0 = g.rz0 = g.A0 = g.C0 = df_make(0.0f);
         g.L = 0; g.inv_bc = 0; g.sin_tc = 0; g.kappa = 0;
         make_frame(g);
         return;
@@ -635,6 +636,15 @@ __device__ void load_segment_f(const clight_segment &s, const DevAtm &A, const D
     g.z0 = df_from_double_bits(s.z);
     g.t0 = df_from_double_bits(s.t0);
     g.rz0 = SPH ? g.z0 + df{A.re_hi, A.re_lo} : g.z0;
+    if (SPH) {
+        // for the vacuum line of every Cherenkov photon of the step:
+        // |R0 + l d|^2 - r_obs^2 = C0 + l (2 A0 + l)
+        g.A0 = df{g.dz, g.lz} * g.rz0 + (g.dx * g.x0.hi + g.dy * g.y0.hi);
+        g.C0 = (g.z0 - df{A.hobs_hi, A.hobs_lo}) * (g.z0 + df{A.k2_hi, A.k2_lo}) +
+               (g.x0.hi * g.x0.hi + g.y0.hi * g.y0.hi);
+    } else {
+        g.A0 = g.C0 = df_make(0.0f);
+    }
     g.L = s.L;
     g.inv_bc = Num<float>::div(3.3356409519815204f, 1.0f - s.eps);   // 1/(beta c), ns/m
     make_frame(g);
@@ -756,6 +766,8 @@ __device__ void load_segment_d(const clight_segment &s, const DevAtm &A, const D
     g.lx = g.ly = g.lz = 0.0;
     g.x0 = s.x; g.y0 = s.y; g.z0 = s.z; g.t0 = s.t0;
     g.rz0 = SPH ? s.z + A.R_E_d : s.z;
+    g.A0 = SPH ? g.dx * s.x + g.dy * s.y + g.dz * g.rz0 : 0.0;
+    g.C0 = SPH ? (s.z - A.h_obs_d) * (s.z + A.k2_d) + s.x * s.x + s.y * s.y : 0.0;
     g.L = s.L;
     g.inv_bc = kInvC / (1.0 - (double)s.eps);
     make_frame(g);
@@ -920,6 +932,7 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
     T u0 = u01<T>(x.x), u1 = u01<T>(x.y), u2 = u01<T>(x.z), u3 = u01<T>(x.w);
     P dgx, dgy, dgz;
     T lam, w;
+    T kapc = (T)0, stc = (T)0, ccc = (T)0, scc = (T)0;      // the Cherenkov cone, for the vacuum line
     if (proc == 0) {
         T st = g.sin_tc, kap = g.kappa;
         if ((FEAT & FEAT_DISP) && A.disp) {
@@ -949,6 +962,7 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
         }
         T sc, cc;
         Num<T>::sincos2pi(u2, &sc, &cc);
+        kapc = kap; stc = st; ccc = cc; scc = sc;
         T sx = -kap * g.dx + st * (cc * g.e1x + sc * g.e2x);
         T sy = -kap * g.dy + st * (cc * g.e1y + sc * g.e2y);
         T sz = -kap * g.dz + st * (cc * g.e1z + sc * g.e2z);
@@ -989,7 +1003,10 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
     o.status = 0;
 
     T dx = to_t<T>(dgx), dy = to_t<T>(dgy), dz = to_t<T>(dgz);
-    T xef = to_t<T>(xe), yef = to_t<T>(ye), zef = to_t<T>(ze);
+    // spherical: z of the emission point enters only binary32 quantities here
+    // (the pairs that need it use C0 and A0, or compute it below)
+    T xef = to_t<T>(xe), yef = to_t<T>(ye);
+    T zef = SPH ? to_t<T>(g.z0) + ell * (g.dz + g.lz) : to_t<T>(ze);
     const T h_obs = sizeof(T) == 4 ? (T)A.h_obs : (T)A.h_obs_d;
     const P Hobs = pc<P>(A.hobs_hi, A.hobs_lo, A.h_obs_d);     // exact constants for the pair arithmetic
 
@@ -998,16 +1015,29 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
     T he, de, pv2, bf2, bf, sqf = 0;
     bool esc = false, under = false, turned = false, grazing = false;
     if (SPH) {
-        P Rz = g.rz0 + ell * (g.dz + g.lz);                 // z_e + R_E
         // b = -(d . R_e) = r_e cos(psi_e); C = |R_e|^2 - r_obs^2
-        P b = -(dgz * Rz) - (dx * xef + dy * yef);
+        P b, C;
+        const T A0f = to_t<T>(g.A0);
+        if (proc == 0) {
+            // Cherenkov: d_g = (1 - kappa) d + sin(theta_c)(cos c e1 + sin c e2) with
+            // e1, e2 orthogonal to d, so d_g . R_e = A0 - kappa A0 + sin(theta_c)(cos c
+            // e1 + sin c e2) . R0 + l (1 - kappa); only A0 and C0 need the pairs
+            const T RZf = to_t<T>(g.z0) + earth_radius<T>(A);
+            T E1 = g.e1x * to_t<T>(g.x0) + g.e1y * to_t<T>(g.y0) + g.e1z * RZf;
+            T E2 = g.e2x * to_t<T>(g.x0) + g.e2y * to_t<T>(g.y0) + g.e2z * RZf;
+            b = (-g.A0) + (kapc * A0f - stc * (ccc * E1 + scc * E2) - ell * ((T)1 - kapc));
+            C = g.C0 + ell * ((T)2 * A0f + ell);
+        } else {
+            P Rz = g.rz0 + ell * (g.dz + g.lz);             // z_e + R_E
+            b = -(dgz * Rz) - (dx * xef + dy * yef);
+            P dzo = ze - Hobs;
+            C = dzo * (ze + pc<P>(A.k2_hi, A.k2_lo, A.k2_d)) + (xef * xef + yef * yef);
+        }
         he = altitude<T, SPH>(A, xef, yef, zef);
         de = AtmT<T>::delta(A, he) * gl;                     // n_e - 1
         esc = !(p_f(b) > 0.0f);
         under = he <= h_obs;
-        P dzo = ze - Hobs;
-        P C = dzo * (ze + pc<P>(A.k2_hi, A.k2_lo, A.k2_d)) + (xef * xef + yef * yef);
-        T Rzf = to_t<T>(Rz);
+        T Rzf = zef + earth_radius<T>(A);
         T c1 = dy * Rzf - dz * yef, c2 = dz * xef - dx * Rzf, c3 = dx * yef - dy * xef;
         pv2 = c1 * c1 + c2 * c2 + c3 * c3;                   // (r_e sin psi_e)^2
         bf = to_t<T>(b);

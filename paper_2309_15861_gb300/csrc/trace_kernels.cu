@@ -17,14 +17,23 @@ namespace clight {
 // Shared-memory record of a warp's 32 segments, one field per row so that
 // lanes reading one field of different segments hit different banks.
 enum SegField {
-    F_X0H, F_X0L, F_Y0H, F_Y0L, F_Z0H, F_Z0L, F_T0H, F_T0L, F_RZH, F_RZL,
+    F_X0H, F_X0L, F_Y0H, F_Y0L, F_Z0H, F_Z0L, F_T0H, F_T0L, F_A0H, F_A0L, F_C0H, F_C0L,
     F_DX, F_DY, F_DZ, F_LX, F_LY, F_LZ, F_E1X, F_E1Y, F_E1Z, F_E2X, F_E2Y, F_E2Z,
-    F_SIN, F_KAP, F_L, F_IBC, F_WC, F_WF, F_NC, F_NF, F_SHOWER, F_SEGI, F_BUX, F_BUY, F_BUZ, F_BOMC,
-    F_INCL, F_COUNT
+    F_SIN, F_KAP, F_L, F_IBC, F_WC, F_WF, F_NC, F_NF, F_SHOWER, F_SEGI, F_INCL,
+    F_BUX, F_BUY, F_BUZ, F_BOMC,          // beamed fluorescence (kernels with FEAT_EXT only)
+    F_COUNT
 };
+__host__ __device__ constexpr int fields_of(bool ext) { return ext ? F_COUNT : F_BUX; }
 
-static int seg_smem_bytes(int block) { return (block / 32) * F_COUNT * 32 * (int)sizeof(float); }
-int fused_smem_bytes(int block, const DevTel &T) { return seg_smem_bytes(block) + (T.clr ? T.clr_bytes : 0); }
+// Segment records of the warps, then (kernels without FEAT_EXT) the
+// clearance map; with FEAT_EXT the records are larger and the map is read
+// from global memory, so that both stay under 48 KB.
+static int seg_smem_bytes(int block, bool ext) { return (block / 32) * fields_of(ext) * 32 * (int)sizeof(float); }
+static int fused_smem_bytes_f(int block, const DevTel &T, bool ext)
+{
+    return seg_smem_bytes(block, ext) + (!ext && T.clr ? T.clr_bytes : 0);
+}
+int fused_smem_bytes(int block, const DevTel &T) { return fused_smem_bytes_f(block, T, true); }
 
 __device__ __forceinline__ void put_df(float *S, int fh, int fl, int l, df v)
 {
@@ -56,13 +65,14 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
               const __grid_constant__ DevTel Tl, const __grid_constant__ DevPar Pp, const __grid_constant__ DevOut O)
 {
     constexpr bool EXT = (FEAT & FEAT_EXT) != 0;
+    constexpr int FC = fields_of(EXT);
     extern __shared__ float smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float *S = smem + warp * (F_COUNT * 32);
+    float *S = smem + warp * (FC * 32);
     // the clearance map, staged once per CTA behind the segment records
-    const uint8_t *clr = nullptr;
-    if (Tl.clr) {
-        uint4 *dst = reinterpret_cast<uint4 *>(smem + (blockDim.x >> 5) * (F_COUNT * 32));
+    const uint8_t *clr = EXT ? Tl.clr : nullptr;
+    if (!EXT && Tl.clr) {
+        uint4 *dst = reinterpret_cast<uint4 *>(smem + (blockDim.x >> 5) * (FC * 32));
         const uint4 *src = reinterpret_cast<const uint4 *>(Tl.clr);
         for (int i = threadIdx.x; i < (Tl.clr_bytes >> 4); i += blockDim.x) dst[i] = __ldg(src + i);
         __syncthreads();
@@ -122,7 +132,8 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
             put_df(S, F_Y0H, F_Y0L, pos, g.y0);
             put_df(S, F_Z0H, F_Z0L, pos, g.z0);
             put_df(S, F_T0H, F_T0L, pos, g.t0);
-            put_df(S, F_RZH, F_RZL, pos, g.rz0);
+            put_df(S, F_A0H, F_A0L, pos, g.A0);
+            put_df(S, F_C0H, F_C0L, pos, g.C0);
             S[F_DX * 32 + pos] = g.dx; S[F_DY * 32 + pos] = g.dy; S[F_DZ * 32 + pos] = g.dz;
             S[F_LX * 32 + pos] = g.lx; S[F_LY * 32 + pos] = g.ly; S[F_LZ * 32 + pos] = g.lz;
             S[F_E1X * 32 + pos] = g.e1x; S[F_E1Y * 32 + pos] = g.e1y; S[F_E1Z * 32 + pos] = g.e1z;
@@ -163,7 +174,9 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
             q.y0 = get_df(S, F_Y0H, F_Y0L, l);
             q.z0 = get_df(S, F_Z0H, F_Z0L, l);
             q.t0 = get_df(S, F_T0H, F_T0L, l);
-            q.rz0 = get_df(S, F_RZH, F_RZL, l);
+            q.A0 = get_df(S, F_A0H, F_A0L, l);
+            q.C0 = get_df(S, F_C0H, F_C0L, l);
+            q.rz0 = SPH ? q.z0 + df{A.re_hi, A.re_lo} : q.z0;  // fluorescence photons only
             q.dx = S[F_DX * 32 + l]; q.dy = S[F_DY * 32 + l]; q.dz = S[F_DZ * 32 + l];
             q.lx = S[F_LX * 32 + l]; q.ly = S[F_LY * 32 + l]; q.lz = S[F_LZ * 32 + l];
             q.e1x = S[F_E1X * 32 + l]; q.e1y = S[F_E1Y * 32 + l]; q.e1z = S[F_E1Z * 32 + l];
@@ -186,6 +199,7 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
                 Seg<float, double> qd;
                 p_from_pair(qd.x0, q.x0); p_from_pair(qd.y0, q.y0); p_from_pair(qd.z0, q.z0);
                 p_from_pair(qd.t0, q.t0); p_from_pair(qd.rz0, q.rz0);
+                p_from_pair(qd.A0, q.A0); p_from_pair(qd.C0, q.C0);
                 qd.dx = q.dx; qd.dy = q.dy; qd.dz = q.dz; qd.lx = q.lx; qd.ly = q.ly; qd.lz = q.lz;
                 qd.e1x = q.e1x; qd.e1y = q.e1y; qd.e1z = q.e1z; qd.e2x = q.e2x; qd.e2y = q.e2y; qd.e2z = q.e2z;
                 qd.sin_tc = q.sin_tc; qd.kappa = q.kappa; qd.L = q.L; qd.inv_bc = q.inv_bc;
@@ -294,7 +308,7 @@ template <class P, int FEAT>
 static void launch_fused_pe(const clight_segment *segs, int64_t n_segs, const DevAtm &A, const DevTel &T,
                             const DevPar &Pp, const DevOut &O, int grid, int block, cudaStream_t s)
 {
-    int smem = fused_smem_bytes(block, T);  // <= 47 KB for block <= 256: no opt-in needed
+    int smem = fused_smem_bytes_f(block, T, (FEAT & FEAT_EXT) != 0);  // < 48 KB for block <= 256
     if (A.spherical && A.refraction)
         k_trace_fused<P, true, true, false, false, FEAT><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
     else if (A.spherical)
