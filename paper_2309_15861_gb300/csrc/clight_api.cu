@@ -85,6 +85,9 @@ struct clight_ctx {
     unsigned long long *h_ctr = nullptr;
     // graph replay
     cudaStream_t cap_stream = nullptr;
+    // host-buffer entry point: chunked copies on their own stream
+    cudaStream_t copy_stream = nullptr;
+    std::vector<cudaEvent_t> chunk_ev;
     cudaEvent_t ev = nullptr;
     cudaEvent_t t0 = nullptr, t1 = nullptr, t2 = nullptr;   // phase timing
     bool timed = false;
@@ -147,6 +150,7 @@ clight_status clight_create(clight_ctx **out, int device)
     if (cudaMalloc((void **)&c->d_ctr, sizeof(unsigned long long) * CTR_N) != cudaSuccess ||
         cudaMallocHost((void **)&c->h_ctr, sizeof(unsigned long long) * CTR_N) != cudaSuccess ||
         cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreate(&c->t0) != cudaSuccess || cudaEventCreate(&c->t1) != cudaSuccess ||
         cudaEventCreate(&c->t2) != cudaSuccess) {
@@ -175,6 +179,8 @@ void clight_destroy(clight_ctx *c)
     c->adj_partial.release(); c->adj_out.release(); c->adj_cand.release(); c->adj_ctr.release();
     if (c->h_ctr) cudaFreeHost(c->h_ctr);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    for (cudaEvent_t e : c->chunk_ev) cudaEventDestroy(e);
     if (c->ev) cudaEventDestroy(c->ev);
     if (c->t0) cudaEventDestroy(c->t0);
     if (c->t1) cudaEventDestroy(c->t1);
@@ -473,6 +479,7 @@ clight_status clight_set_params(clight_ctx *c, const clight_params *p)
     P.seed = p->seed;
     P.stream = p->stream;
     P.seg_base = p->seg_base;
+    P.key_off = 0;
     P.cut_mode = p->cut_mode;
     const double cut_deg = p->cut_deg > 0 ? p->cut_deg : 6.0;
     P.cut_cos_d = std::cos(cut_deg * (3.14159265358979323846 / 180.0));
@@ -562,8 +569,12 @@ clight_status prepare(clight_ctx *c, int64_t n_segs, int32_t n_showers, int64_t 
     return CLIGHT_OK;
 }
 
+// chunk > 0: the fused kernel runs once per `chunk` steps, each launch first
+// waiting on chunk_ev[i] (the copy of its steps), with the sort keys offset
+// to the whole call's step indices; one sort at the end.
 cudaError_t enqueue(clight_ctx *c, const clight_segment *segs, int64_t n_segs, const Plan &pl, clight_hit *hits,
-                    int64_t cap, int64_t *counts, double *sums, bool fp64, cudaStream_t s, bool capturing)
+                    int64_t cap, int64_t *counts, double *sums, bool fp64, cudaStream_t s, bool capturing,
+                    int64_t chunk = 0, const cudaEvent_t *chunk_ev = nullptr)
 {
     // inside a capture an event record is a real graph node only when external
     const unsigned evf = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
@@ -590,10 +601,23 @@ cudaError_t enqueue(clight_ctx *c, const clight_segment *segs, int64_t n_segs, c
         } else {
             int block = c->upar.block > 0 ? c->upar.block : 256;
             int per_sm = c->upar.ctas_per_sm > 0 ? c->upar.ctas_per_sm : 3 * 256 / block;
-            int64_t groups = (n_segs + 31) / 32;
-            int64_t grid = std::min<int64_t>((int64_t)c->n_sm * per_sm, (groups * 32 + block - 1) / block);
-            grid = std::max<int64_t>(grid, 1);
-            e = launch_trace_fused(segs, n_segs, c->atm, c->tel, c->par, O, c->upar.precision, (int)grid, block, s);
+            int64_t step = chunk > 0 ? chunk : n_segs;
+            for (int64_t off = 0, i = 0; off < n_segs && e == cudaSuccess; off += step, ++i) {
+                int64_t n = std::min(step, n_segs - off);
+                int64_t groups = (n + 31) / 32;
+                int64_t grid = std::min<int64_t>((int64_t)c->n_sm * per_sm, (groups * 32 + block - 1) / block);
+                grid = std::max<int64_t>(grid, 1);
+                DevPar P = c->par;
+                if (chunk > 0) {
+                    if ((e = cudaStreamWaitEvent(s, chunk_ev[i], 0)) != cudaSuccess) break;
+                    if (off > 0 && (e = cudaMemsetAsync(c->d_ctr + CTR_WORK, 0, sizeof(unsigned long long), s)) !=
+                                       cudaSuccess)
+                        break;
+                    P.seg_base += off;
+                    P.key_off = off;
+                }
+                e = launch_trace_fused(segs + off, n, c->atm, c->tel, P, O, c->upar.precision, (int)grid, block, s);
+            }
         }
         if (e != cudaSuccess) return e;
     }
@@ -696,10 +720,37 @@ clight_status clight_trace_host(clight_ctx *c, const clight_segment *h_segs, int
     if (c->stage_segs.ensure(n_segs, g) || c->stage_hits.ensure(cap, g) || c->stage_counts.ensure(ng, g) ||
         c->stage_sums.ensure(ng, g))
         return CLIGHT_ERR_CUDA;
-    if (n_segs > 0)
-        CK(cudaMemcpyAsync(c->stage_segs.p, h_segs, sizeof(clight_segment) * (size_t)n_segs, cudaMemcpyHostToDevice, s));
-    clight_status r = run(c, c->stage_segs.p, n_segs, n_showers, c->stage_hits.p, cap, c->stage_counts.p,
-                          c->stage_sums.p, st, h_n_hits, stream, false);
+    clight_status r;
+    const int64_t chunk = int64_t(1) << 22;          // 268 MB of steps per copy
+    if (n_segs >= 2 * chunk) {
+        // copies on the copy stream overlap the tracing of the chunks before
+        Plan pl;
+        if ((r = prepare(c, n_segs, n_showers, cap, pl)) != CLIGHT_OK) return r;
+        int64_t nck = (n_segs + chunk - 1) / chunk;
+        while ((int64_t)c->chunk_ev.size() < nck) {
+            cudaEvent_t e;
+            CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            c->chunk_ev.push_back(e);
+        }
+        CK(cudaEventRecord(c->ev, s));                 // earlier work on the staging buffer
+        CK(cudaStreamWaitEvent(c->copy_stream, c->ev, 0));
+        for (int64_t i = 0; i < nck; ++i) {
+            int64_t off = i * chunk, n = std::min(chunk, n_segs - off);
+            CK(cudaMemcpyAsync(c->stage_segs.p + off, h_segs + off, sizeof(clight_segment) * (size_t)n,
+                               cudaMemcpyHostToDevice, c->copy_stream));
+            CK(cudaEventRecord(c->chunk_ev[i], c->copy_stream));
+        }
+        CK(enqueue(c, c->stage_segs.p, n_segs, pl, c->stage_hits.p, cap, c->stage_counts.p, c->stage_sums.p, false,
+                   s, false, chunk, c->chunk_ev.data()));
+        CK(cudaStreamSynchronize(s));
+        r = finish(c, cap, st, h_n_hits);
+    } else {
+        if (n_segs > 0)
+            CK(cudaMemcpyAsync(c->stage_segs.p, h_segs, sizeof(clight_segment) * (size_t)n_segs,
+                               cudaMemcpyHostToDevice, s));
+        r = run(c, c->stage_segs.p, n_segs, n_showers, c->stage_hits.p, cap, c->stage_counts.p, c->stage_sums.p,
+                st, h_n_hits, stream, false);
+    }
     if (r != CLIGHT_OK && r != CLIGHT_ERR_BAD_SEGMENT && r != CLIGHT_ERR_LIMIT) return r;
     int64_t n = std::min<int64_t>(*h_n_hits, cap);
     if (n > 0) CK(cudaMemcpyAsync(h_hits, c->stage_hits.p, sizeof(clight_hit) * (size_t)n, cudaMemcpyDeviceToHost, s));

@@ -84,6 +84,7 @@ struct DevPar {
     double fyield_d;
     uint32_t seed, stream;
     int64_t seg_base;
+    int64_t key_off;             // added to the launch-local step index in the sort keys (chunked launches)
     int n_showers, seg_bits, k_bits, pad;
     float bunch;
     // angular segment cut (CLIGHT_CUT_*): cos of the angle, the centre, and

@@ -207,7 +207,7 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
                 qd.bux = q.bux; qd.buy = q.buy; qd.buz = q.buz; qd.bomc = q.bomc;
                 RayOut<float, double> o;
                 trace_ray<float, double, true, SPH, REFR, FEAT>(qd, seg_global, k, active, A, Pp, o);
-                nh = hit_test<float, double, true, NOALLOC>(o, seg_local, seg_global, k, q.shower, A, Tl, Pp, O, status_bits, clr);
+                nh = hit_test<float, double, true, NOALLOC>(o, Pp.key_off + seg_local, seg_global, k, q.shower, A, Tl, Pp, O, status_bits, clr);
                 if (active) {
                     ++c_rays;
                     c_esc += o.status == 1; c_under += o.status == 2; c_turn += o.status == 3;
@@ -238,7 +238,7 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
             } else {
                 RayOut<float, df> o;
                 trace_ray<float, df, true, SPH, REFR, FEAT>(q, seg_global, k, active, A, Pp, o);
-                nh = hit_test<float, df, true, NOALLOC>(o, seg_local, seg_global, k, q.shower, A, Tl, Pp, O, status_bits, clr);
+                nh = hit_test<float, df, true, NOALLOC>(o, Pp.key_off + seg_local, seg_global, k, q.shower, A, Tl, Pp, O, status_bits, clr);
                 if (active) {
                     ++c_rays;
                     c_esc += o.status == 1; c_under += o.status == 2; c_turn += o.status == 3;
