@@ -87,12 +87,15 @@ def lib():
         L.or_soft_yield.argtypes = [P, C.c_int64, P, P, P, P, C.c_int, P, C.c_int,
                                     C.c_double, C.c_double, P, C.c_int]
         L.or_eval_rays.argtypes = [P, P, P, P, P, P, C.c_int64, P, P, P, P, C.c_int]
+        L.or_grad_rays.argtypes = [P, P, P, P, P, P, C.c_int64, P, P, P, P, P, P, P, P, C.c_int]
+        L.or_grad_soft.argtypes = [P, C.c_int64, P, P, P, P, C.c_int, P, C.c_int, C.c_double, C.c_double, P, P,
+                                   C.c_int]
         _lib = L
     return _lib
 
 
 def _ptr(a: np.ndarray):
-    return C.c_void_p(a.ctypes.data)
+    return C.c_void_p(0) if a is None else C.c_void_p(a.ctypes.data)
 
 
 def atm_struct(atm) -> _Atm:
@@ -275,4 +278,39 @@ def eval_rays(segs, seg_idx, k, tel, nbc, nbf, atm, tels, par, threads=0, seg_ba
     a, p = atm_struct(atm), par_struct(par, seg_base, tels)
     lib().or_eval_rays(_ptr(segs), _ptr(seg_idx), _ptr(k), _ptr(tel), _ptr(nbc), _ptr(nbf),
                        len(seg_idx), C.byref(a), _ptr(tels), C.byref(p), _ptr(out), int(threads))
+    return out
+
+
+def grad_rays(segs, seg_idx, k, tel, nbc, nbf, atm, tels, par, gx=None, gy=None, gt=None, gw=None,
+              threads=0, seg_base=0):
+    """FP64 gradient (dual numbers) of sum gx x_rel + gy y_rel + gt t + gw weight*exp(-tau)
+    over the given hits with respect to (c_1..c_L, K, L0)."""
+    segs = np.ascontiguousarray(segs)
+    tels = np.ascontiguousarray(tels)
+    seg_idx = np.ascontiguousarray(seg_idx, dtype=np.int64)
+    k = np.ascontiguousarray(k, dtype=np.uint32)
+    tel = np.ascontiguousarray(tel, dtype=np.uint32)
+    nbc = np.ascontiguousarray(nbc, dtype=np.uint32)
+    nbf = np.ascontiguousarray(nbf, dtype=np.uint32)
+    f = lambda v: None if v is None else np.ascontiguousarray(v, dtype=np.float64)
+    gx, gy, gt, gw = f(gx), f(gy), f(gt), f(gw)
+    out = np.zeros(atm.n_layers + 2)
+    a, p = atm_struct(atm), par_struct(par, seg_base, tels)
+    lib().or_grad_rays(_ptr(segs), _ptr(seg_idx), _ptr(k), _ptr(tel), _ptr(nbc), _ptr(nbf), len(seg_idx),
+                       C.byref(a), _ptr(tels), C.byref(p), _ptr(gx), _ptr(gy), _ptr(gt), _ptr(gw), _ptr(out),
+                       int(threads))
+    return out
+
+
+def grad_soft(segs, nbc, nbf, atm, tels, par, gY, n_showers=1, s=0.5, W=10.0, threads=0, seg_base=0):
+    """FP64 gradient (dual numbers) of sum gY Y of the soft yield."""
+    segs = np.ascontiguousarray(segs)
+    tels = np.ascontiguousarray(tels)
+    nbc = np.ascontiguousarray(nbc, dtype=np.uint32)
+    nbf = np.ascontiguousarray(nbf, dtype=np.uint32)
+    gY = np.ascontiguousarray(gY, dtype=np.float64).reshape(-1)
+    out = np.zeros(atm.n_layers + 2)
+    a, p = atm_struct(atm), par_struct(par, seg_base, tels)
+    lib().or_grad_soft(_ptr(segs), len(segs), _ptr(nbc), _ptr(nbf), C.byref(a), _ptr(tels), len(tels),
+                       C.byref(p), int(n_showers), float(s), float(W), _ptr(gY), _ptr(out), int(threads))
     return out

@@ -846,3 +846,347 @@ void or_eval_rays(const or_segment *segs, const int64_t *seg_idx, const uint32_t
         o[0] = xr; o[1] = yr; o[2] = t; o[3] = ph[8] * exp(-pr[8]); o[4] = dperp;
     }
 }
+
+/* ========================================================================
+ * FP64 reference gradient, written separately from the finite differences:
+ * forward-mode dual numbers carried through the same physics with one
+ * tangent per parameter theta = (c_1..c_L, K, L0) (b_i, the layer edges,
+ * the random numbers and the bunch counts fixed).  The propagation
+ * integrals have fixed limits (h_obs, h_e), so their tangents are the
+ * integrals of the differentiated integrands, taken by Gauss-Legendre on
+ * 32 panels per smooth piece.
+ * ====================================================================== */
+#define OR_NP 10
+typedef struct { double v, d[OR_NP]; } dn;
+
+static dn dn_c(double v) { dn r; r.v = v; for (int i = 0; i < OR_NP; i++) r.d[i] = 0; return r; }
+static dn dn_add(dn a, dn b) { dn r; r.v = a.v + b.v; for (int i = 0; i < OR_NP; i++) r.d[i] = a.d[i] + b.d[i]; return r; }
+static dn dn_sub(dn a, dn b) { dn r; r.v = a.v - b.v; for (int i = 0; i < OR_NP; i++) r.d[i] = a.d[i] - b.d[i]; return r; }
+static dn dn_mul(dn a, dn b)
+{
+    dn r; r.v = a.v * b.v;
+    for (int i = 0; i < OR_NP; i++) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
+    return r;
+}
+static dn dn_scale(dn a, double s) { dn r; r.v = a.v * s; for (int i = 0; i < OR_NP; i++) r.d[i] = a.d[i] * s; return r; }
+static dn dn_div(dn a, dn b)
+{
+    dn r; r.v = a.v / b.v;
+    for (int i = 0; i < OR_NP; i++) r.d[i] = (a.d[i] - r.v * b.d[i]) / b.v;
+    return r;
+}
+static dn dn_sqrt(dn a)
+{
+    dn r; r.v = sqrt(a.v);
+    for (int i = 0; i < OR_NP; i++) r.d[i] = r.v > 0 ? a.d[i] / (2.0 * r.v) : 0.0;
+    return r;
+}
+static dn dn_exp(dn a) { dn r; r.v = exp(a.v); for (int i = 0; i < OR_NP; i++) r.d[i] = a.d[i] * r.v; return r; }
+static dn dn_cos(dn a) { dn r; r.v = cos(a.v); double s = -sin(a.v); for (int i = 0; i < OR_NP; i++) r.d[i] = a.d[i] * s; return r; }
+static dn dn_sin(dn a) { dn r; r.v = sin(a.v); double c = cos(a.v); for (int i = 0; i < OR_NP; i++) r.d[i] = a.d[i] * c; return r; }
+
+/* rho(h) and n(h) - 1 with their tangents: d rho/d c_i = rho (h/c_i^2 - 1/c_i)
+ * in the layer of h, d delta / d K = rho */
+static void dn_atm(const or_atmosphere *a, double h, dn *rho, dn *delta)
+{
+    int L = a->n_layers;
+    *rho = dn_c(0);
+    *delta = dn_c(0);
+    if (h >= a->h_top) return;
+    int i = layer_of(a, h);
+    double c = a->c[i];
+    double r = a->b[i] / (100.0 * c) * exp(-h / c);
+    rho->v = r;
+    rho->d[i] = r * (h / (c * c) - 1.0 / c);
+    *delta = dn_scale(*rho, a->K);
+    delta->d[L] = r;
+}
+
+typedef struct {
+    const or_atmosphere *a;
+    dn p;
+    int refr;
+} dn_ray;
+
+static void dn_integrand(const dn_ray *c, double h, dn f[3])
+{
+    const or_atmosphere *a = c->a;
+    dn rho, delta;
+    dn_atm(a, h, &rho, &delta);
+    dn n = dn_add(dn_c(1.0), delta);
+    double rr = a->spherical ? (a->R_E + h) : 1.0;
+    dn nn = c->refr ? n : dn_c(1.0);
+    dn q = dn_sub(dn_scale(dn_mul(nn, nn), rr * rr), dn_mul(c->p, c->p));
+    dn sq = dn_sqrt(q);
+    f[0] = dn_div(c->p, dn_scale(sq, rr));
+    f[1] = dn_div(dn_scale(dn_mul(n, nn), rr), sq);
+    f[2] = dn_div(dn_scale(dn_mul(rho, nn), rr / a->rho_ref), sq);
+}
+
+static void dn_integrate(const dn_ray *c, double h0, double h1, dn out[3])
+{
+    gl_init();
+    const or_atmosphere *a = c->a;
+    double br[12];
+    int nb = 0;
+    br[nb++] = h0;
+    for (int i = 1; i < a->n_layers; i++)
+        if (a->h_lo[i] > h0 && a->h_lo[i] < h1) br[nb++] = a->h_lo[i];
+    if (a->h_top > h0 && a->h_top < h1) br[nb++] = a->h_top;
+    br[nb++] = h1;
+    out[0] = out[1] = out[2] = dn_c(0);
+    const int panels = 32;
+    for (int s = 0; s + 1 < nb; s++) {
+        double w = (br[s + 1] - br[s]) / panels;
+        for (int q = 0; q < panels; q++) {
+            double mid = br[s] + (q + 0.5) * w;
+            for (int i = 0; i < GLN; i++) {
+                dn f[3];
+                dn_integrand(c, mid + 0.5 * w * gl_x[i], f);
+                for (int k = 0; k < 3; k++) out[k] = dn_add(out[k], dn_scale(f[k], 0.5 * w * gl_w[i]));
+            }
+        }
+    }
+}
+
+/* One ray with tangents: landing point P, arrival direction dL, arrival
+ * time t_L, optical depth tau and n_obs, mirroring or_propagate.  Returns
+ * the status. */
+static int dn_propagate(const or_atmosphere *a, const double r_e[3], const dn dg[3], double t_e, double lambda,
+                        dn P[3], dn dL[3], dn *tL, dn *tau, dn *n_obs_out)
+{
+    int L = a->n_layers;
+    double h_e = altitude(a, r_e);
+    dn rho_e, del_e, rho_o, del_o;
+    dn_atm(a, h_e, &rho_e, &del_e);
+    dn_atm(a, a->h_obs, &rho_o, &del_o);
+    dn n_e = dn_add(dn_c(1.0), del_e), n_obs = dn_add(dn_c(1.0), del_o);
+    *n_obs_out = n_obs;
+    dn nd = dn_sqrt(dn_add(dn_add(dn_mul(dg[0], dg[0]), dn_mul(dg[1], dg[1])), dn_mul(dg[2], dg[2])));
+    dn d[3] = {dn_div(dg[0], nd), dn_div(dg[1], nd), dn_div(dg[2], nd)};
+    dn_ray c;
+    c.a = a;
+    c.refr = a->refraction;
+    dn I[3];
+    if (!a->spherical) {
+        dn cos_e = dn_scale(d[2], -1.0);
+        if (cos_e.v <= 0) return OR_ESCAPED;
+        if (h_e <= a->h_obs) return OR_UNDER;
+        dn sin_e = dn_sqrt(dn_add(dn_mul(d[0], d[0]), dn_mul(d[1], d[1])));
+        c.p = a->refraction ? dn_mul(n_e, sin_e) : sin_e;
+        dn_integrate(&c, a->h_obs, h_e, I);
+        dn ux = sin_e.v > 0 ? dn_div(d[0], sin_e) : dn_c(1.0), uy = sin_e.v > 0 ? dn_div(d[1], sin_e) : dn_c(0.0);
+        P[0] = dn_add(dn_c(r_e[0]), dn_mul(I[0], ux));
+        P[1] = dn_add(dn_c(r_e[1]), dn_mul(I[0], uy));
+        P[2] = dn_c(a->h_obs);
+        dn sL, cL;
+        if (a->refraction) {
+            sL = dn_div(c.p, n_obs);
+            cL = dn_div(dn_sqrt(dn_sub(dn_mul(n_obs, n_obs), dn_mul(c.p, c.p))), n_obs);
+        } else {
+            sL = sin_e;
+            cL = cos_e;
+        }
+        dL[0] = dn_mul(sL, ux); dL[1] = dn_mul(sL, uy); dL[2] = dn_scale(cL, -1.0);
+    } else {
+        double R[3] = {r_e[0], r_e[1], r_e[2] + a->R_E};
+        double r = sqrt(R[0] * R[0] + R[1] * R[1] + R[2] * R[2]);
+        double rh[3] = {R[0] / r, R[1] / r, R[2] / r};
+        dn cos_psi = dn_scale(dn_add(dn_add(dn_scale(d[0], rh[0]), dn_scale(d[1], rh[1])), dn_scale(d[2], rh[2])), -1.0);
+        if (cos_psi.v <= 0) return OR_ESCAPED;
+        if (h_e <= a->h_obs) return OR_UNDER;
+        dn cr[3] = {dn_sub(dn_scale(d[1], rh[2]), dn_scale(d[2], rh[1])),
+                    dn_sub(dn_scale(d[2], rh[0]), dn_scale(d[0], rh[2])),
+                    dn_sub(dn_scale(d[0], rh[1]), dn_scale(d[1], rh[0]))};
+        dn sin_psi = dn_sqrt(dn_add(dn_add(dn_mul(cr[0], cr[0]), dn_mul(cr[1], cr[1])), dn_mul(cr[2], cr[2])));
+        double r_obs = a->R_E + a->h_obs;
+        c.p = a->refraction ? dn_scale(dn_mul(n_e, sin_psi), r) : dn_scale(sin_psi, r);
+        dn q_obs = a->refraction ? dn_sub(dn_scale(dn_mul(n_obs, n_obs), r_obs * r_obs), dn_mul(c.p, c.p))
+                                 : dn_sub(dn_c(r_obs * r_obs), dn_mul(c.p, c.p));
+        if (q_obs.v <= 0) return OR_TURNED;
+        dn_integrate(&c, a->h_obs, h_e, I);
+        dn et[3];
+        if (sin_psi.v > 0) {
+            for (int i = 0; i < 3; i++) et[i] = dn_div(dn_add(d[i], dn_scale(cos_psi, rh[i])), sin_psi);
+        } else {
+            double t0[3] = {1, 0, 0};
+            double dd = t0[0] * rh[0] + t0[1] * rh[1] + t0[2] * rh[2];
+            double e3[3];
+            for (int i = 0; i < 3; i++) e3[i] = t0[i] - dd * rh[i];
+            double ne = sqrt(e3[0] * e3[0] + e3[1] * e3[1] + e3[2] * e3[2]);
+            for (int i = 0; i < 3; i++) et[i] = dn_c(e3[i] / ne);
+        }
+        dn cp = dn_cos(I[0]), sp = dn_sin(I[0]);
+        dn rL[3], eL[3];
+        for (int i = 0; i < 3; i++) {
+            rL[i] = dn_add(dn_scale(cp, rh[i]), dn_mul(sp, et[i]));
+            eL[i] = dn_add(dn_scale(sp, -rh[i]), dn_mul(cp, et[i]));
+        }
+        P[0] = dn_scale(rL[0], r_obs);
+        P[1] = dn_scale(rL[1], r_obs);
+        P[2] = dn_sub(dn_scale(rL[2], r_obs), dn_c(a->R_E));
+        dn sL, cL;
+        if (a->refraction) {
+            dn nr = dn_scale(n_obs, r_obs);
+            sL = dn_div(c.p, nr);
+            cL = dn_div(dn_sqrt(q_obs), nr);
+        } else {
+            sL = dn_scale(c.p, 1.0 / r_obs);
+            cL = dn_scale(dn_sqrt(q_obs), 1.0 / r_obs);
+        }
+        for (int i = 0; i < 3; i++) dL[i] = dn_sub(dn_mul(sL, eL[i]), dn_mul(cL, rL[i]));
+    }
+    *tL = dn_add(dn_c(t_e), dn_scale(I[1], 1.0 / OR_C));
+    if (a->absorption) {
+        dn L0 = dn_c(a->L0);
+        L0.d[L + 1] = 1.0;
+        dn Lext = dn_scale(L0, pow(lambda / a->lambda_ref, 4.0));
+        *tau = dn_div(I[2], Lext);
+    } else {
+        *tau = dn_c(0);
+    }
+    return OR_TRACED;
+}
+
+/* The photon with tangents: the step's midpoint refractivity moves theta_c
+ * and the yield (per-bunch weight N / n_b with n_b frozen); fluorescence
+ * emission does not depend on theta. */
+static void dn_photon(const or_segment *s, int64_t seg_index, uint32_t k, uint32_t nbc, uint32_t nbf,
+                      const or_atmosphere *a, const or_params *p, double r_e[3], dn dg[3], double *t_e,
+                      double *lambda, dn *w)
+{
+    int L = a->n_layers;
+    seg_yield y;
+    frozen_yield(s, a, p, nbc, nbf, &y);
+    double ph[10];
+    photon_of(s, seg_index, k, &y, a, p, ph);
+    r_e[0] = ph[0]; r_e[1] = ph[1]; r_e[2] = ph[2];
+    *t_e = ph[6];
+    *lambda = ph[7];
+    if ((int)ph[9] == 1) {
+        for (int i = 0; i < 3; i++) dg[i] = dn_c(ph[3 + i]);
+        *w = dn_c(y.w_f);
+        return;
+    }
+    double d[3];
+    float df[3] = {s->dx, s->dy, s->dz};
+    unit3(df, d);
+    double rm[3] = {s->x + 0.5 * s->L * d[0], s->y + 0.5 * s->L * d[1], s->z + 0.5 * s->L * d[2]};
+    dn rho, delta;
+    dn_atm(a, altitude(a, rm), &rho, &delta);
+    (void)L;
+    double eps = (double)s->eps;
+    dn g1 = dn_sub(dn_scale(delta, 1.0 - eps), dn_c(eps));
+    dn bn = dn_add(dn_c(1.0), g1);
+    dn sin2 = dn_div(dn_mul(g1, dn_add(g1, dn_c(2.0))), dn_mul(bn, bn));
+    dn cos_tc = dn_div(dn_c(1.0), bn), sin_tc = dn_sqrt(sin2);
+    double z2 = (double)s->charge * (double)s->charge;
+    double band = (1.0 / p->lambda1 - 1.0 / p->lambda2) * 1e9;
+    *w = dn_scale(sin2, 2.0 * OR_PI * OR_ALPHA * z2 * band * (double)s->L / (double)nbc);
+    /* the azimuth of bunch k, recovered from the primal direction */
+    double M[9];
+    or_rotation(d, M);
+    double pv[3];                         /* M^T d_gamma = (cos c sin, sin c sin, -cos) */
+    for (int i = 0; i < 3; i++) pv[i] = M[i] * ph[3] + M[3 + i] * ph[4] + M[6 + i] * ph[5];
+    double cc = pv[0], sc = pv[1], sn = sqrt(cc * cc + sc * sc);
+    cc = sn > 0 ? cc / sn : 1.0;
+    sc = sn > 0 ? sc / sn : 0.0;
+    dn pd[3] = {dn_scale(sin_tc, cc), dn_scale(sin_tc, sc), dn_scale(cos_tc, -1.0)};
+    for (int i = 0; i < 3; i++)
+        dg[i] = dn_add(dn_add(dn_scale(pd[0], M[3 * i]), dn_scale(pd[1], M[3 * i + 1])), dn_scale(pd[2], M[3 * i + 2]));
+}
+
+/* Gradient of sum_i (gx_i x_rel_i + gy_i y_rel_i + gt_i t_i + gw_i weight_i)
+ * over the given hits, in FP64 by dual numbers: grad[0 .. n_layers + 1]. */
+void or_grad_rays(const or_segment *segs, const int64_t *seg_idx, const uint32_t *k, const uint32_t *tel,
+                  const uint32_t *n_bunch_c, const uint32_t *n_bunch_f, int64_t n, const or_atmosphere *a,
+                  const or_telescope *tels, const or_params *p, const double *gx, const double *gy,
+                  const double *gt, const double *gw, double *grad, int threads)
+{
+    gl_init();
+    int np = a->n_layers + 2;
+    int nt = 1;
+#ifdef _OPENMP
+    nt = threads > 0 ? threads : omp_get_max_threads();
+#endif
+    double *part = (double *)calloc((size_t)nt * OR_NP, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
+    for (int64_t i = 0; i < n; i++) {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        int64_t si = seg_idx[i];
+        double r_e[3], t_e, lam;
+        dn dg[3], w;
+        dn_photon(&segs[si], p->seg_base + si, k[i], n_bunch_c[si], n_bunch_f[si], a, p, r_e, dg, &t_e, &lam, &w);
+        dn P[3], dL[3], tL, tau, n_obs;
+        if (dn_propagate(a, r_e, dg, t_e, lam, P, dL, &tL, &tau, &n_obs) != OR_TRACED) continue;
+        const or_telescope *T = &tels[tel[i]];
+        dn sj = dn_div(dn_sub(dn_c(T->z), P[2]), dL[2]);
+        dn xr = dn_sub(dn_add(P[0], dn_mul(sj, dL[0])), dn_c(T->x));
+        dn yr = dn_sub(dn_add(P[1], dn_mul(sj, dL[1])), dn_c(T->y));
+        dn tt = dn_add(tL, dn_scale(dn_mul(n_obs, sj), 1.0 / OR_C));
+        dn wt = dn_mul(w, dn_exp(dn_scale(tau, -1.0)));
+        for (int j = 0; j < np; j++)
+            part[(size_t)tid * OR_NP + j] += (gx ? gx[i] * xr.d[j] : 0) + (gy ? gy[i] * yr.d[j] : 0) +
+                                             (gt ? gt[i] * tt.d[j] : 0) + (gw ? gw[i] * wt.d[j] : 0);
+    }
+    for (int j = 0; j < np; j++) {
+        double s = 0;
+        for (int t = 0; t < nt; t++) s += part[(size_t)t * OR_NP + j];
+        grad[j] = s;
+    }
+    free(part);
+}
+
+/* Gradient of sum_g gY_g Y_g for the soft yield of or_soft_yield. */
+void or_grad_soft(const or_segment *segs, int64_t n_segs, const uint32_t *n_bunch_c, const uint32_t *n_bunch_f,
+                  const or_atmosphere *a, const or_telescope *tels, int n_tel, const or_params *p, int n_showers,
+                  double s, double W, const double *gY, double *grad, int threads)
+{
+    gl_init();
+    (void)n_showers;
+    int np = a->n_layers + 2;
+    int nt = 1;
+#ifdef _OPENMP
+    nt = threads > 0 ? threads : omp_get_max_threads();
+#endif
+    double *part = (double *)calloc((size_t)nt * OR_NP, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
+    for (int64_t i = 0; i < n_segs; i++) {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        uint32_t nb = n_bunch_c[i] + n_bunch_f[i];
+        for (uint32_t kk = 0; kk < nb; kk++) {
+            double r_e[3], t_e, lam;
+            dn dg[3], w;
+            dn_photon(&segs[i], p->seg_base + i, kk, n_bunch_c[i], n_bunch_f[i], a, p, r_e, dg, &t_e, &lam, &w);
+            dn P[3], dL[3], tL, tau, n_obs;
+            if (dn_propagate(a, r_e, dg, t_e, lam, P, dL, &tL, &tau, &n_obs) != OR_TRACED) continue;
+            dn wt = dn_mul(w, dn_exp(dn_scale(tau, -1.0)));
+            for (int j = 0; j < n_tel; j++) {
+                const or_telescope *T = &tels[j];
+                dn wv[3] = {dn_sub(dn_c(T->x), P[0]), dn_sub(dn_c(T->y), P[1]), dn_sub(dn_c(T->z), P[2])};
+                dn wd = dn_add(dn_add(dn_mul(wv[0], dL[0]), dn_mul(wv[1], dL[1])), dn_mul(wv[2], dL[2]));
+                dn d2 = dn_sub(dn_add(dn_add(dn_mul(wv[0], wv[0]), dn_mul(wv[1], wv[1])), dn_mul(wv[2], wv[2])),
+                               dn_mul(wd, wd));
+                dn dp = dn_sqrt(d2);
+                if (!(dp.v < T->R + W)) continue;
+                dn u = dn_scale(dn_sub(dn_c(T->R), dp), 1.0 / s);
+                dn sg = dn_div(dn_c(1.0), dn_add(dn_c(1.0), dn_exp(dn_scale(u, -1.0))));
+                double gyv = gY[(size_t)segs[i].shower * n_tel + j];
+                dn y = dn_mul(wt, sg);
+                for (int q = 0; q < np; q++) part[(size_t)tid * OR_NP + q] += gyv * y.d[q];
+            }
+        }
+    }
+    for (int j = 0; j < np; j++) {
+        double sum = 0;
+        for (int t = 0; t < nt; t++) sum += part[(size_t)t * OR_NP + j];
+        grad[j] = sum;
+    }
+    free(part);
+}

@@ -135,4 +135,16 @@ void or_eval_rays(const or_segment *segs, const int64_t *seg_idx, const uint32_t
 #ifdef __cplusplus
 }
 #endif
+/* FP64 reference gradient by forward-mode dual numbers (parameters
+ * c_1..c_L, K, L0; grad has n_layers + 2 entries).  or_grad_rays: of
+ * sum gx x_rel + gy y_rel + gt t + gw weight over the given hits (gx, gy,
+ * gt, gw may be NULL); or_grad_soft: of sum gY_g Y_g for the soft yield. */
+void or_grad_rays(const or_segment *segs, const int64_t *seg_idx, const uint32_t *k, const uint32_t *tel,
+                  const uint32_t *n_bunch_c, const uint32_t *n_bunch_f, int64_t n, const or_atmosphere *a,
+                  const or_telescope *tels, const or_params *p, const double *gx, const double *gy,
+                  const double *gt, const double *gw, double *grad, int threads);
+void or_grad_soft(const or_segment *segs, int64_t n_segs, const uint32_t *n_bunch_c, const uint32_t *n_bunch_f,
+                  const or_atmosphere *a, const or_telescope *tels, int n_tel, const or_params *p, int n_showers,
+                  double s, double W, const double *gY, double *grad, int threads);
+
 #endif

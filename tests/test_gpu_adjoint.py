@@ -64,6 +64,13 @@ def _check(n_segs, seed, rel=1e-4):
         err = np.where(zero, 0.0, np.abs(grad - fd) / np.where(zero, 1.0, np.abs(fd)))
         print("adjoint", grad, "\nfd     ", fd, "\nrel    ", err)
         assert np.all(err < rel), (grad, fd, err)
+        # and the oracle's FP64 gradient by dual numbers
+        gd = (O.grad_rays(w.segments, hits["seg"], hits["k"], hits["tel"], nbc, nbf, w.atmosphere, w.telescopes,
+                          w.params, gx, gy, gt)
+              + O.grad_soft(w.segments, nbc, nbf, w.atmosphere, w.telescopes, w.params, gY, s=0.5, W=20.0))
+        errd = np.where(gd == 0.0, np.abs(grad), np.abs(grad - gd) / np.where(gd == 0.0, 1.0, np.abs(gd)))
+        print("dual   ", gd, "\nrel    ", errd)
+        assert np.all(errd < rel), (grad, gd, errd)
         return grad, fd
     finally:
         ctx.close()

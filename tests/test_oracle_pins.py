@@ -704,3 +704,52 @@ def test_dispersion_wavelengths_and_cherenkov_angles():
     cdf = lambda x: np.array([integrate.quad(dens, par.lambda1, v, epsrel=1e-9, limit=200)[0] / top for v in np.atleast_1d(x)])
     assert lams.max() < par.lambda2 and dens(lams.max()) > 0
     assert stats.kstest(lams, cdf).pvalue > 1e-3
+
+
+# ---------------------------------------------------------------- FP64 reference gradient
+def _atm_at(base, th):
+    a = I.Atmosphere(**{**base.__dict__})
+    L = a.n_layers
+    a.c = list(th[:L])
+    a.K = th[L]
+    a.L0 = th[L + 1]
+    return a
+
+
+@pytest.mark.parametrize("case", ["vertical", "inclined"])
+def test_dual_number_gradient_matches_central_differences(case):
+    """The oracle's FP64 gradient by dual numbers (a separate derivation of
+    the same physics) against its own central differences (h = 1e-4
+    relative): hit positions, times and weights, and the soft yield."""
+    w = (I.workload_shower_1tev(n=2500, seed=41) if case == "vertical"
+         else I.workload_inclined(n=1500, seed=43))
+    h, c, s, st = O.trace(w.segments, w.atmosphere, w.telescopes, w.params)
+    assert len(h) > 20
+    nbc, nbf = O.bunch_counts(w.segments, w.atmosphere, w.params)
+    rng = np.random.default_rng(1)
+    gx, gy, gt, gw = rng.normal(size=(4, len(h)))
+    gY = rng.normal(size=len(w.telescopes))
+    g = O.grad_rays(w.segments, h["seg"], h["k"], h["tel"], nbc, nbf, w.atmosphere, w.telescopes, w.params,
+                    gx, gy, gt, gw)
+    gs = O.grad_soft(w.segments, nbc, nbf, w.atmosphere, w.telescopes, w.params, gY, s=0.5, W=20.0)
+    theta = np.array(list(w.atmosphere.c) + [w.atmosphere.K, w.atmosphere.L0])
+
+    def loss(th):
+        ev = O.eval_rays(w.segments, h["seg"], h["k"], h["tel"], nbc, nbf, _atm_at(w.atmosphere, th),
+                         w.telescopes, w.params)
+        return gx @ ev[:, 0] + gy @ ev[:, 1] + gt @ ev[:, 2] + gw @ ev[:, 3]
+
+    def lsoft(th):
+        return float(gY @ O.soft_yield(w.segments, nbc, nbf, _atm_at(w.atmosphere, th), w.telescopes, w.params,
+                                       s=0.5, W=20.0).ravel())
+    for p in range(len(theta)):
+        hp = 1e-4 * theta[p]
+        tp, tm = theta.copy(), theta.copy()
+        tp[p] += hp
+        tm[p] -= hp
+        fd = (loss(tp) - loss(tm)) / (2 * hp)
+        fds = (lsoft(tp) - lsoft(tm)) / (2 * hp)
+        scale = max(abs(fd), 1e-9 * np.abs(g).max())
+        assert abs(g[p] - fd) <= 2e-5 * scale, (p, g[p], fd)
+        scale_s = max(abs(fds), 1e-9 * np.abs(gs).max())
+        assert abs(gs[p] - fds) <= 1e-4 * scale_s, (p, gs[p], fds)
