@@ -139,8 +139,7 @@ def recorded_traffic(n_steps):
     return rec["bytes_per_step"] * n_steps if "bytes_per_step" in rec else None
 
 
-def cpu_baseline(w, budget_s=12.0, block=256, seed=0):
-    """The FP64 oracle on contiguous blocks of the same workload (host cores)."""
+def _oracle_rate(w, budget_s, block, seed, threads):
     import oracle as O
     O.build()
     rng = np.random.default_rng(seed)
@@ -152,16 +151,27 @@ def cpu_baseline(w, budget_s=12.0, block=256, seed=0):
     for b in starts:
         lo = int(b) * block
         _, _, _, st = O.trace(w.segments[lo:lo + block], w.atmosphere, w.telescopes, w.params,
-                              n_showers=w.n_showers, seg_base=lo)
+                              n_showers=w.n_showers, seg_base=lo, threads=threads)
         rays += st["rays"]
         blocks += 1
         if time.perf_counter() - t0 > budget_s:
             break
-    dt = time.perf_counter() - t0
+    return rays, blocks, time.perf_counter() - t0
+
+
+def cpu_baseline(w, budget_s=12.0, block=256, seed=0, single_s=0.0):
+    """The FP64 oracle on contiguous blocks of the same workload (host cores;
+    optionally also on one thread)."""
+    n = len(w.segments)
+    rays, blocks, dt = _oracle_rate(w, budget_s, block, seed, 0)
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": rays / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{blocks} random blocks of {block} consecutive steps ({blocks * block} of {n} "
-                      f"steps, {rays} rays) of the same shower, {dt:.1f} s, FP64 oracle with OpenMP"}
+    out = {"value": rays / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"{blocks} random blocks of {block} consecutive steps ({blocks * block} of {n} "
+                     f"steps, {rays} rays) of the same shower, {dt:.1f} s, FP64 oracle with OpenMP"}
+    if single_s > 0:
+        r1, b1, d1 = _oracle_rate(w, single_s, block, seed + 1, 1)
+        out["single_thread"] = {"value": r1 / d1, "unit": UNIT, "sample": f"{b1} blocks, {r1} rays, {d1:.1f} s"}
+    return out
 
 
 def reference_arm(args, rank):
@@ -439,7 +449,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(w)
+        cpu = cpu_baseline(w, single_s=4.0)
 
     if rank == 0:
         atm = "5-layer, spherical, absorbing"
