@@ -443,7 +443,9 @@ def main():
         e2e = {"value": st2["rays"] * k2 / wall, "unit": UNIT,
                "h2d_bytes_per_step": int(n * 64),
                "d2h_bytes_per_step": int(len(hh) * 48 + cbuf.numel() * 8 + sbuf.numel() * 8),
-               "ms_per_step": wall * 1e3 / k2}
+               "ms_per_step": wall * 1e3 / k2,
+               "path": "clight_trace_host on pinned host buffers: the kernel reads the steps in place over "
+                       "the CPU-GPU link every step; hits, counts and sums copied back every step"}
         ctx.set_params(w.params, **extra)
         del pinned, hbuf
 

@@ -223,9 +223,15 @@ clight_status clight_trace_fp64(clight_ctx *ctx, const clight_segment *d_segs, i
                                 int64_t *d_counts, double *d_sums, clight_stats *h_stats,
                                 int64_t *h_n_hits, void *stream);
 
-/* clight_trace on HOST buffers: copies the segments to the device, runs the
- * fused path, copies hits, counts and sums back.  Device staging buffers are
- * owned by the context.  h_counts / h_sums may be NULL. */
+/* clight_trace on HOST buffers, results copied back to h_hits / h_counts /
+ * h_sums (the last two may be NULL).  How the steps reach the GPU:
+ *   - page-locked (pinned) h_segs: the kernel reads them in place over the
+ *     CPU-GPU link (coherent on Grace-Blackwell), each record once;
+ *   - pageable h_segs of at least 2 x 2^22 steps: copied in chunks of 2^22
+ *     steps on a second stream while earlier chunks are traced;
+ *   - otherwise one copy, then the trace.
+ * Device staging buffers are owned by the context.  Same results in every
+ * case.  Synchronises `stream`. */
 clight_status clight_trace_host(clight_ctx *ctx, const clight_segment *h_segs, int64_t n_segs,
                                 int32_t n_showers, clight_hit *h_hits, int64_t hit_capacity,
                                 int64_t *h_counts, double *h_sums, clight_stats *h_stats,

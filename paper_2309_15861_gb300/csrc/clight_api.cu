@@ -722,7 +722,19 @@ clight_status clight_trace_host(clight_ctx *c, const clight_segment *h_segs, int
         return CLIGHT_ERR_CUDA;
     clight_status r;
     const int64_t chunk = int64_t(1) << 22;          // 268 MB of steps per copy
-    if (n_segs >= 2 * chunk) {
+    // Pinned (page-locked) host memory is coherent and readable by the GPU
+    // over NVLink-C2C: the kernel then reads every step where it lies, each
+    // record once, with no staging copy.
+    cudaPointerAttributes pa{};
+    const clight_segment *d_direct = nullptr;
+    if (n_segs > 0 && cudaPointerGetAttributes(&pa, h_segs) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+        pa.devicePointer != nullptr)
+        d_direct = static_cast<const clight_segment *>(pa.devicePointer);
+    cudaGetLastError();
+    if (d_direct) {
+        r = run(c, d_direct, n_segs, n_showers, c->stage_hits.p, cap, c->stage_counts.p, c->stage_sums.p, st,
+                h_n_hits, stream, false);
+    } else if (n_segs >= 2 * chunk) {
         // copies on the copy stream overlap the tracing of the chunks before
         Plan pl;
         if ((r = prepare(c, n_segs, n_showers, cap, pl)) != CLIGHT_OK) return r;

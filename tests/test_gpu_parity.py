@@ -260,20 +260,23 @@ def test_host_buffer_entry_point(ctx):
     np.testing.assert_array_equal(s, dev[2])
 
 
-def test_host_buffer_entry_point_chunked(ctx, torch_cuda):
-    """Above 2 x 2^22 steps the host-buffer call copies in chunks on its own
-    stream while earlier chunks are traced: same records as the device call."""
+def test_host_buffer_entry_point_chunked_and_pinned(ctx, torch_cuda):
+    """Host buffers of 9e6 steps: pageable ones are copied in 2^22-step
+    chunks on a second stream while earlier chunks are traced; pinned ones
+    are read in place by the kernel.  Same records as the device call."""
     torch = torch_cuda
     w = I.workload_shower_1tev(n=9_000_000, seed=71, workers=I.default_workers())
     ctx.setup(w)
     dev = G.run_workload(ctx, w, capacity=2_000_000)
+    pageable = np.ascontiguousarray(w.segments).copy()
     pinned = torch.from_numpy(w.segments.view(np.uint8).reshape(-1)).pin_memory()
-    code, h, c, s, st = ctx.trace_host(pinned.numpy().view(I.SEG_DTYPE), 1, 2_000_000)
-    assert code == G.OK and len(h) > 1000
-    assert np.array_equal(h, dev[0])
-    np.testing.assert_array_equal(c, dev[1])
-    np.testing.assert_array_equal(s, dev[2])
-    assert st["rays"] == dev[3]["rays"] and st["hits"] == dev[3]["hits"]
+    for segs in (pageable, pinned.numpy().view(I.SEG_DTYPE)):
+        code, h, c, s, st = ctx.trace_host(segs, 1, 2_000_000)
+        assert code == G.OK and len(h) > 1000
+        assert np.array_equal(h, dev[0])
+        np.testing.assert_array_equal(c, dev[1])
+        np.testing.assert_array_equal(s, dev[2])
+        assert st["rays"] == dev[3]["rays"] and st["hits"] == dev[3]["hits"]
 
 
 def test_edge_cases(ctx, torch_cuda):
