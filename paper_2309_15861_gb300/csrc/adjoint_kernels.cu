@@ -401,7 +401,7 @@ __device__ __forceinline__ void block_partials(double *acc, double *out)
 
 // Hit outputs: sum over hits of gx dx_rel + gy dy_rel + gt dt.
 template <int NP, bool SPH, bool REFR>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 4)
 k_adjoint_hits(const clight_segment *__restrict__ segs, const clight_hit *__restrict__ hits, int64_t n_hits,
                const float *__restrict__ gx, const float *__restrict__ gy, const float *__restrict__ gt,
                const __grid_constant__ DevAtm A, const __grid_constant__ DevTel Tl, const __grid_constant__ DevPar Pp,
@@ -437,7 +437,7 @@ k_adjoint_hits(const clight_segment *__restrict__ segs, const clight_hit *__rest
 // forward kernel's candidate pass compacted (local segment << 32 | bunch),
 // so that every lane of a warp carries a ray that needs its tangents.
 template <int NP, bool SPH, bool REFR>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 4)
 k_adjoint_soft(const clight_segment *__restrict__ segs, const unsigned long long *__restrict__ cand, int64_t n_cand,
                const double *__restrict__ gY, double *__restrict__ yield, const __grid_constant__ DevAtm A,
                const __grid_constant__ DevTel Tl, const __grid_constant__ DevPar Pp, const __grid_constant__ AdjPar J,
