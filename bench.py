@@ -237,6 +237,9 @@ def main():
     ap.add_argument("--fl-beaming", action="store_true",
                     help="beam the fluorescence toward the array (Sec. 1.1.1); the batch workload's default is "
                          "isotropic emission")
+    ap.add_argument("--fl-roulette", action="store_true",
+                    help="fluorescence steps with fewer photons than a bunch emit one full bunch with "
+                         "probability N/B (unbiased; with --fl-beaming this is what removes rays)")
     ap.add_argument("--cut-study", action="store_true",
                     help="also time the Cherenkov angular cut (array centre and per telescope, 6 deg) and "
                          "report its speedup and photon loss against the uncut step")
@@ -277,6 +280,9 @@ def main():
         import dataclasses
         c, r = I.beam_cone(w.telescopes)
         w.params = dataclasses.replace(w.params, fl_beaming=1, beam_centre=c, beam_radius=r)
+    if args.fl_roulette:
+        import dataclasses
+        w.params = dataclasses.replace(w.params, fl_roulette=1)
     ns = w.n_showers
     ctx = G.Context(local)
     extra = dict(use_graph=1, precision=args.precision, block=args.block, ctas_per_sm=args.ctas_per_sm,
@@ -465,7 +471,8 @@ def main():
                        "precision": ["float-pair", "fp64-guard"][args.precision], "graph": True,
                        "l2": f"inputs ({n * 64 / 1e9:.2f} GB) larger than L2; no flush",
                        "parallelism": f"replicas x{world}", "generation_s": round(t_gen, 1),
-                       "fl_beaming": bool(args.fl_beaming), "propagator": args.propagator,
+                       "fl_beaming": bool(args.fl_beaming), "fl_roulette": bool(args.fl_roulette),
+                       "propagator": args.propagator,
                        "dispersion_B_nm2": args.disp_B,
                        "step": "trace + adjoint" if adj is not None else "trace"},
             "roofline": roof, "fp64_plain": fp64, "e2e": e2e, "cpu_baseline": cpu,

@@ -142,6 +142,14 @@ typedef struct {
     int32_t propagator;
     double beam_centre[3];          /* m, local frame */
     double beam_radius;             /* m */
+    /* Count rule of the fluorescence bunches: 0 = ceil(N / B) bunches of
+     * weight N / n_b (every step with N > 0 emits at least one); 1 = a step
+     * with N < B emits one bunch of weight B with probability N / B (its own
+     * Philox draw, counter (step, 0xFFFFFFFF, 1)), else none; N >= B as for 0.
+     * The expected photon number is the same; with beaming it is what turns
+     * the smaller photon numbers into fewer rays. */
+    int32_t fl_roulette;
+    int32_t roulette_pad;
 } clight_params;
 
 enum {

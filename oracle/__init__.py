@@ -56,7 +56,8 @@ class _Par(C.Structure):
                 ("fl_lambda1", C.c_double), ("fl_lambda2", C.c_double),
                 ("seg_base", C.c_int64), ("cut_mode", C.c_int32), ("cut_deg", C.c_double),
                 ("cut_centre", C.c_double * 3), ("cut_tels", C.c_void_p), ("cut_n_tel", C.c_int32),
-                ("fl_beaming", C.c_int32), ("beam_centre", C.c_double * 3), ("beam_radius", C.c_double)]
+                ("fl_beaming", C.c_int32), ("beam_centre", C.c_double * 3), ("beam_radius", C.c_double),
+                ("fl_roulette", C.c_int32)]
 
 
 _lib = None
@@ -72,6 +73,7 @@ def lib():
         L.or_u01.argtypes = [C.c_uint32]
         L.or_u01.restype = C.c_double
         L.or_yield.argtypes = [P, P, P, P]
+        L.or_yield_at.argtypes = [P, C.c_int64, P, P, P]
         L.or_rotation.argtypes = [P, P]
         L.or_photon.argtypes = [P, C.c_int64, C.c_uint32, P, P, P]
         L.or_propagate.argtypes = [P, P, P, C.c_double, C.c_double, P]
@@ -146,6 +148,7 @@ def par_struct(p, seg_base: int = 0, tels=None) -> _Par:
         for i in range(3):
             s.beam_centre[i] = float(p.beam_centre[i])
         s.beam_radius = float(p.beam_radius)
+    s.fl_roulette = int(getattr(p, "fl_roulette", 0))
     return s
 
 
@@ -162,13 +165,14 @@ def u01(x: int) -> float:
     return lib().or_u01(int(x) & 0xFFFFFFFF)
 
 
-def yield_of(seg, atm, par, tels=None):
-    """-> dict(n_c, w_c, n_f, w_f, cos_tc, sin_tc, Nc, Nf, delta, h_mid)."""
+def yield_of(seg, atm, par, tels=None, seg_index=0):
+    """-> dict(n_c, w_c, n_f, w_f, cos_tc, sin_tc, Nc, Nf, delta, h_mid) of the
+    step whose global index is seg_index."""
     s = np.ascontiguousarray(np.asarray(seg).reshape(1))
     o = np.zeros(10)
     tels = None if tels is None else np.ascontiguousarray(tels)
     a, p = atm_struct(atm), par_struct(par, 0, tels)
-    lib().or_yield(_ptr(s), C.byref(a), C.byref(p), _ptr(o))
+    lib().or_yield_at(_ptr(s), int(seg_index), C.byref(a), C.byref(p), _ptr(o))
     keys = ["n_c", "w_c", "n_f", "w_f", "cos_tc", "sin_tc", "Nc", "Nf", "delta", "h_mid"]
     return dict(zip(keys, o.tolist()))
 
@@ -237,13 +241,14 @@ def trace(segs, atm, tels, par, n_showers=1, capacity=None, threads=0, seg_base=
     return hits[:total], counts.reshape(n_showers, n_tel), sums.reshape(n_showers, n_tel), st
 
 
-def bunch_counts(segs, atm, par, tels=None):
+def bunch_counts(segs, atm, par, tels=None, seg_base=0):
     """Nominal Cherenkov and fluorescence bunch counts of every segment
-    (`tels` is needed for the per-telescope angular cut)."""
+    (`tels` is needed for the per-telescope angular cut, seg_base for the
+    fluorescence count rule 1)."""
     nc = np.zeros(len(segs), dtype=np.uint32)
     nf = np.zeros(len(segs), dtype=np.uint32)
     for i in range(len(segs)):
-        y = yield_of(segs[i], atm, par, tels)
+        y = yield_of(segs[i], atm, par, tels, seg_index=seg_base + i)
         nc[i] = int(y["n_c"])
         nf[i] = int(y["n_f"])
     return nc, nf

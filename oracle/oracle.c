@@ -201,6 +201,12 @@ static double disp_integral(const or_atmosphere *a, double delta, double eps, do
 
 void or_yield(const or_segment *s, const or_atmosphere *a, const or_params *p, double out[10])
 {
+    or_yield_at(s, p->seg_base, a, p, out);
+}
+
+void or_yield_at(const or_segment *s, int64_t seg_index, const or_atmosphere *a, const or_params *p,
+                 double out[10])
+{
     double d[3];
     float df[3] = {s->dx, s->dy, s->dz};
     unit3(df, d);
@@ -235,8 +241,19 @@ void or_yield(const or_segment *s, const or_atmosphere *a, const or_params *p, d
         Nf = p->fluor_yield * (double)s->dE;
         double u[3], omc;
         if (beam_cone(s, d, p, u, &omc)) Nf *= 0.5 * omc;
-        n_f = ceil(Nf / p->bunch);
-        w_f = n_f > 0 ? Nf / n_f : 0.0;
+        double x = Nf / p->bunch;
+        if (p->fl_roulette && x < 1.0) {
+            /* reading of an unbiased count for steps with fewer photons than a
+             * bunch: one full bunch with probability N/B */
+            uint32_t ctr[4] = {(uint32_t)(uint64_t)seg_index, (uint32_t)((uint64_t)seg_index >> 32), 0xFFFFFFFFu, 1u};
+            uint32_t key[2] = {p->seed, p->stream}, r[4];
+            or_philox4x32_10(ctr, key, r);
+            n_f = or_u01(r[0]) < x ? 1 : 0;
+            w_f = n_f > 0 ? p->bunch : 0.0;
+        } else {
+            n_f = ceil(x);
+            w_f = n_f > 0 ? Nf / n_f : 0.0;
+        }
     }
     out[0] = n_c; out[1] = w_c; out[2] = n_f; out[3] = w_f;
     out[4] = cos_tc; out[5] = sin_tc; out[6] = Nc; out[7] = Nf;
@@ -361,10 +378,11 @@ static void photon_of(const or_segment *s, int64_t seg_index, uint32_t k, const 
     out[9] = process;
 }
 
-static void yield_struct(const or_segment *s, const or_atmosphere *a, const or_params *p, seg_yield *y)
+static void yield_struct(const or_segment *s, int64_t seg_index, const or_atmosphere *a, const or_params *p,
+                         seg_yield *y)
 {
     double o[10];
-    or_yield(s, a, p, o);
+    or_yield_at(s, seg_index, a, p, o);
     y->n_c = o[0]; y->w_c = o[1]; y->n_f = o[2]; y->w_f = o[3];
     y->cos_tc = o[4]; y->sin_tc = o[5];
     y->delta = o[8];
@@ -374,7 +392,7 @@ void or_photon(const or_segment *s, int64_t seg_index, uint32_t k,
                const or_atmosphere *a, const or_params *p, double out[10])
 {
     seg_yield y;
-    yield_struct(s, a, p, &y);
+    yield_struct(s, seg_index, a, p, &y);
     photon_of(s, seg_index, k, &y, a, p, out);
 }
 
@@ -692,7 +710,7 @@ int64_t or_trace(const or_segment *segs, int64_t n_segs,
 #endif
         const or_segment *s = &segs[i];
         seg_yield y;
-        yield_struct(s, a, p, &y);
+        yield_struct(s, p->seg_base + i, a, p, &y);
         uint32_t nb = (uint32_t)(y.n_c + y.n_f);
         for (uint32_t k = 0; k < nb; k++) {
             double ph[10], pr[10];
@@ -766,7 +784,7 @@ static void frozen_yield(const or_segment *s, const or_atmosphere *a, const or_p
     y->n_c = nbc;
     y->n_f = nbf;
     y->w_c = nbc > 0 ? o[6] / nbc : 0;
-    y->w_f = nbf > 0 ? o[7] / nbf : 0;
+    y->w_f = nbf > 0 ? (p->fl_roulette && o[7] < p->bunch ? p->bunch : o[7] / nbf) : 0;
     y->cos_tc = o[4];
     y->sin_tc = o[5];
     y->delta = o[8];

@@ -72,6 +72,9 @@ typedef struct {
     int32_t fl_beaming;
     double beam_centre[3];
     double beam_radius;
+    /* fluorescence count rule: 0 ceil(N/B); 1 N < B -> one bunch of weight B
+     * with probability N/B (Philox counter (step, 0xFFFFFFFF, 1)) */
+    int32_t fl_roulette;
 } or_params;
 
 typedef struct {            /* oracle output record, all FP64 */
@@ -88,6 +91,10 @@ double or_u01(uint32_t x);
 
 /* out: n_c, w_c, n_f, w_f, cos_tc, sin_tc, Nbar_c, Nbar_f, delta_mid, h_mid */
 void or_yield(const or_segment *s, const or_atmosphere *a, const or_params *p, double out[10]);
+/* The same for the step of global index seg_index (the fluorescence count
+ * rule 1 draws a number keyed by it; or_yield uses p->seg_base). */
+void or_yield_at(const or_segment *s, int64_t seg_index, const or_atmosphere *a, const or_params *p,
+                 double out[10]);
 
 /* Rotation M_Rod for track direction d (normalised inside), row-major. */
 void or_rotation(const double d[3], double M[9]);

@@ -55,7 +55,8 @@ class Params(C.Structure):
                 ("use_graph", C.c_int32), ("cell_width", C.c_float), ("key_bunch_bits", C.c_int32),
                 ("cut_mode", C.c_int32), ("cut_pad", C.c_int32), ("cut_deg", C.c_double),
                 ("cut_centre", C.c_double * 3), ("fl_beaming", C.c_int32), ("propagator", C.c_int32),
-                ("beam_centre", C.c_double * 3), ("beam_radius", C.c_double)]
+                ("beam_centre", C.c_double * 3), ("beam_radius", C.c_double), ("fl_roulette", C.c_int32),
+                ("roulette_pad", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -140,6 +141,7 @@ def params_struct(p: inputs.Params, **kw) -> Params:
         for i in range(3):
             s.beam_centre[i] = float(p.beam_centre[i])
         s.beam_radius = float(p.beam_radius)
+    s.fl_roulette = int(getattr(p, "fl_roulette", 0))
     for k, v in kw.items():
         setattr(s, k, v)
     return s

@@ -415,7 +415,7 @@ k_adjoint_hits(const clight_segment *__restrict__ segs, const clight_hit *__rest
         int64_t sl = h.seg - Pp.seg_base;
         clight_segment s = segs[sl];
         Seg<float, df> g;
-        load_segment_f<SPH>(s, A, Pp, g);
+        load_segment_f<SPH>(s, h.seg, A, Pp, g);
         if (g.bad) continue;
         RayOut<float, df> o;
         trace_ray<float, df, false, SPH, REFR>(g, h.seg, h.k, true, A, Pp, o);
@@ -452,7 +452,7 @@ k_adjoint_soft(const clight_segment *__restrict__ segs, const unsigned long long
         uint32_t k = (uint32_t)ck;
         clight_segment s = segs[si];
         Seg<float, df> g;
-        load_segment_f<SPH>(s, A, Pp, g);
+        load_segment_f<SPH>(s, Pp.seg_base + si, A, Pp, g);
         if (g.bad || k >= g.n_c + g.n_f) continue;
         int64_t seg_global = Pp.seg_base + si;
         RayOut<float, df> o;

@@ -450,6 +450,7 @@ clight_status clight_set_params(clight_ctx *c, const clight_params *p)
                                           !std::isfinite(p->cut_centre[2])))
         return CLIGHT_ERR_ARG;
     if (p->fl_beaming != 0 && p->fl_beaming != 1) return CLIGHT_ERR_ARG;
+    if (p->fl_roulette != 0 && p->fl_roulette != 1) return CLIGHT_ERR_ARG;
     if (p->propagator != CLIGHT_PROP_EXACT && p->propagator != CLIGHT_PROP_STRAIGHT) return CLIGHT_ERR_ARG;
     if (p->fl_beaming && (!(p->beam_radius > 0) || !std::isfinite(p->beam_radius) ||
                           !std::isfinite(p->beam_centre[0]) || !std::isfinite(p->beam_centre[1]) ||
@@ -488,6 +489,7 @@ clight_status clight_set_params(clight_ctx *c, const clight_params *p)
     P.cut_cx = (float)P.cut_cx_d; P.cut_cy = (float)P.cut_cy_d; P.cut_cz = (float)P.cut_cz_d;
     P.cut_rad = (float)(cut_deg * (3.14159265358979323846 / 180.0));
     P.beam = p->fl_beaming;
+    P.roulette = p->fl_roulette;
     P.prop = p->propagator;
     P.beam_cx_d = p->beam_centre[0]; P.beam_cy_d = p->beam_centre[1]; P.beam_cz_d = p->beam_centre[2];
     P.beam_r_d = p->beam_radius;

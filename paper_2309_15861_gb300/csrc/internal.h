@@ -106,7 +106,7 @@ struct DevPar {
     float cut_gx0, cut_gy0, cut_inv_gs;
     int prop;                    // CLIGHT_PROP_*
     // fluorescence beaming: on/off, cone centre and radius
-    int beam;
+    int beam, roulette;
     float beam_cx, beam_cy, beam_cz, beam_r;
     double beam_cx_d, beam_cy_d, beam_cz_d, beam_r_d;
 };

@@ -602,8 +602,19 @@ __device__ __forceinline__ void make_frame(Seg<T, P> &g)
 // binary32 segment set-up with the binary64 guard on the integer bunch count.
 // EXT = false drops the optional angular cut and fluorescence beaming from
 // the compiled code (the launcher picks it when neither is on).
+// Fluorescence count rule 1: the number that decides whether a step with
+// fewer photons than one bunch emits a bunch of weight B (counter word 2 is
+// 0xFFFFFFFF, outside the photon counters, word 3 the fluorescence process).
+template <class T> __device__ __forceinline__ T roulette_u(int64_t seg_global, const DevPar &P)
+{
+    uint4 r = philox4x32_10(make_uint4((uint32_t)(uint64_t)seg_global, (uint32_t)((uint64_t)seg_global >> 32),
+                                       0xFFFFFFFFu, 1u), P.seed, P.stream);
+    return u01<T>(r.x);
+}
+
 template <bool SPH, bool EXT = true, bool DISP = true>
-__device__ void load_segment_f(const clight_segment &s, const DevAtm &A, const DevPar &P, Seg<float, df> &g)
+__device__ void load_segment_f(const clight_segment &s, int64_t seg_global, const DevAtm &A, const DevPar &P,
+                               Seg<float, df> &g)
 {
     g.bad = 0;
     g.guarded = 0;
@@ -707,7 +718,7 @@ __device__ void load_segment_f(const clight_segment &s, const DevAtm &A, const D
     }
     if (!guard && g.n_c == 0 && !(DISP && A.disp)) { g.sin_tc = 0.0f; g.kappa = 0.0f; }
     float Nf = 0.0f;
-    bool fguard = false;
+    bool fguard = false, roul = false;
     if (P.fyield > 0.0f && s.dE > 0.0f && s.L > 0.0f) {
         Nf = P.fyield * s.dE;
         float rel = 1.0e-6f;
@@ -717,8 +728,15 @@ __device__ void load_segment_f(const clight_segment &s, const DevAtm &A, const D
         }
         float x = Nf * P.inv_bunch;
         float ex = x * rel + 1.0e-7f;
-        if (ceilf(x - ex) != ceilf(x + ex)) fguard = true;
-        else g.n_f = (uint32_t)ceilf(x);
+        if (ceilf(x - ex) != ceilf(x + ex)) {
+            fguard = true;
+        } else if (EXT && P.roulette && x < 1.0f) {
+            float u = roulette_u<float>(seg_global, P);
+            if (fabsf(u - x) <= ex) fguard = true;    // decided in binary64 below
+            else { g.n_f = u < x ? 1u : 0u; roul = true; }
+        } else {
+            g.n_f = (uint32_t)ceilf(x);
+        }
     }
     if (g.cut) guard = false;
     if (guard || fguard) {
@@ -735,19 +753,27 @@ __device__ void load_segment_f(const clight_segment &s, const DevAtm &A, const D
             if (g.n_c > 0) g.w_c = (float)(Ncd / nb);
         }
         if (fguard) {
-            double nb = ceil(Nfd / P.bunch_d);
-            g.n_f = (uint32_t)nb;
-            Nf = (float)Nfd;
-            if (g.n_f > 0) g.w_f = (float)(Nfd / nb);
+            double xd = Nfd / P.bunch_d;
+            if (EXT && P.roulette && xd < 1.0) {
+                g.n_f = roulette_u<double>(seg_global, P) < xd ? 1u : 0u;
+                roul = true;
+            } else {
+                double nb = ceil(xd);
+                g.n_f = (uint32_t)nb;
+                Nf = (float)Nfd;
+                if (g.n_f > 0) g.w_f = (float)(Nfd / nb);
+            }
         }
     }
     if (!guard && g.n_c > 0) g.w_c = Nc * rcp_approx((float)g.n_c);
-    if (!fguard && g.n_f > 0) g.w_f = Nf * rcp_approx((float)g.n_f);
+    if (roul) g.w_f = g.n_f > 0 ? (float)P.bunch_d : 0.0f;
+    else if (!fguard && g.n_f > 0) g.w_f = Nf * rcp_approx((float)g.n_f);
 }
 
 // binary64 segment set-up (plain path).
 template <bool SPH>
-__device__ void load_segment_d(const clight_segment &s, const DevAtm &A, const DevPar &P, Seg<double, double> &g)
+__device__ void load_segment_d(const clight_segment &s, int64_t seg_global, const DevAtm &A, const DevPar &P,
+                               Seg<double, double> &g)
 {
     g.bad = 0;
     g.guarded = 0;
@@ -785,7 +811,10 @@ __device__ void load_segment_d(const clight_segment &s, const DevAtm &A, const D
         g.n_c = (uint32_t)nb;
         g.w_c = Nc / nb;
     }
-    if (Nf > 0.0) {
+    if (Nf > 0.0 && P.roulette && Nf < P.bunch_d) {
+        g.n_f = roulette_u<double>(seg_global, P) < Nf / P.bunch_d ? 1u : 0u;
+        g.w_f = g.n_f ? P.bunch_d : 0.0;
+    } else if (Nf > 0.0) {
         double nb = ceil(Nf / P.bunch_d);
         g.n_f = (uint32_t)nb;
         g.w_f = Nf / nb;

@@ -97,7 +97,7 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
             const float4 *src = reinterpret_cast<const float4 *>(segs + si);
             float4 *dst = reinterpret_cast<float4 *>(&s);
             dst[0] = __ldg(src); dst[1] = __ldg(src + 1); dst[2] = __ldg(src + 2); dst[3] = __ldg(src + 3);
-            load_segment_f<SPH, EXT, (FEAT & FEAT_DISP) != 0>(s, A, Pp, g);
+            load_segment_f<SPH, EXT, (FEAT & FEAT_DISP) != 0>(s, Pp.seg_base + si, A, Pp, g);
             if (g.bad) status_bits |= 1u << g.bad;
             c_guard += g.guarded;
             c_cut += g.cut;
@@ -278,7 +278,7 @@ k_trace_fp64(const clight_segment *__restrict__ segs, int64_t n_segs, const __gr
     if (i >= n_segs) return;
     unsigned status_bits = 0;
     Seg<double, double> g;
-    load_segment_d<SPH>(segs[i], A, Pp, g);
+    load_segment_d<SPH>(segs[i], Pp.seg_base + i, A, Pp, g);
     uint32_t c_rays = 0, c_esc = 0, c_under = 0, c_turn = 0, c_reach = 0, c_hits = 0, c_cells = 0;
     uint32_t c_cut = g.cut;
     if (g.bad) {
@@ -324,7 +324,7 @@ template <class P>
 static void launch_fused_p(const clight_segment *segs, int64_t n_segs, const DevAtm &A, const DevTel &T,
                            const DevPar &Pp, const DevOut &O, int grid, int block, cudaStream_t s)
 {
-    const bool ext = Pp.cut_mode != CLIGHT_CUT_OFF || Pp.beam;
+    const bool ext = Pp.cut_mode != CLIGHT_CUT_OFF || Pp.beam || Pp.roulette;
     const bool str = Pp.prop == CLIGHT_PROP_STRAIGHT;
     if (!std::is_same<P, df>::value || (A.disp && (ext || str)))
         launch_fused_pe<P, FEAT_ALL>(segs, n_segs, A, T, Pp, O, grid, block, s);

@@ -168,6 +168,7 @@ class Params:
     fl_beaming: int = 0           # fluorescence beamed toward the array (see beam_cone)
     beam_centre: tuple = None
     beam_radius: float = None
+    fl_roulette: int = 0          # fluorescence steps with N < B: one bunch of weight B with probability N/B
 
 
 def array_centre(tels: np.ndarray) -> tuple:

@@ -142,6 +142,19 @@ def test_fluorescence_beaming(ctx):
     assert gst64["rays"] == gst["rays"]
 
 
+def test_fluorescence_roulette(ctx):
+    """Beamed fluorescence under count rule 1: the per-step bunch decisions
+    (Philox at counter (step, 0xFFFFFFFF, 1)) equal the oracle's, so rays,
+    hits and counts agree."""
+    w = I.batch_showers(n_showers=6, seed=47, scale=2e-3)
+    c, r = I.beam_cone(w.telescopes)
+    w.params = dataclasses.replace(w.params, fl_beaming=1, beam_centre=c, beam_radius=r, fl_roulette=1)
+    rep, gst, rst = _check(ctx, w)
+    assert rep["n_common"] > 0
+    rep64, gst64, rst64 = _check(ctx, w, fp64=True)
+    assert gst64["rays"] == gst["rays"]
+
+
 def _straight_errors(ctx, w):
     ctx.setup(w, propagator=G.PROP_STRAIGHT)
     gh, gc, gs, gst = G.run_workload(ctx, w)

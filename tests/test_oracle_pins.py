@@ -624,6 +624,61 @@ def test_beaming_loses_no_hits_and_keeps_the_mean():
     assert abs(tot_b - tot_i) < 5 * math.sqrt(tot_i) + 5 * math.sqrt(max(1.0, (sb ** 2).sum() / max(1, len(hb)))), (tot_i, tot_b)
 
 
+def test_fluorescence_roulette_is_unbiased_and_keeps_large_counts():
+    """Count rule 1 (the reading that lets beaming cut rays): a step with
+    N_f < B emits one bunch of weight B with probability N_f/B, the number
+    drawn from the (cuRAND-pinned) Philox at counter (step, 0xFFFFFFFF, 1);
+    its expectation is N_f.  Steps with N_f >= B keep ceil bunching."""
+    w = _fluor_workload(1, 7, 0, dE=(1.0, 1.0))
+    s = w.segments[0]
+    par = dataclasses.replace(w.params, bunch=10.0, fl_roulette=1)
+    Nf = O.yield_of(s, w.atmosphere, par)["Nf"]
+    assert Nf == pytest.approx(5.0)
+    x = Nf / par.bunch
+    n = 4000
+    picks = np.zeros(n)
+    for i in range(n):
+        y = O.yield_of(s, w.atmosphere, par, seg_index=i)
+        assert y["n_c"] == 0 and y["n_f"] in (0, 1)
+        assert y["w_f"] == (par.bunch if y["n_f"] else 0.0)
+        u = O.u01(O.philox([i, 0, 0xFFFFFFFF, 1], [par.seed, par.stream])[0])
+        assert y["n_f"] == (1 if u < x else 0)
+        picks[i] = y["n_f"]
+    # mean photon number N_f within 5 sigma of the binomial
+    assert abs(picks.mean() * par.bunch - Nf) < 5 * par.bunch * math.sqrt(x * (1 - x) / n)
+    # a high word of the step index reaches the counter
+    big = (1 << 32) + 17
+    u = O.u01(O.philox([17, 1, 0xFFFFFFFF, 1], [par.seed, par.stream])[0])
+    assert O.yield_of(s, w.atmosphere, par, seg_index=big)["n_f"] == (1 if u < x else 0)
+    # N_f >= B: unchanged
+    s2 = s.copy()
+    s2["dE"] = 7.3
+    y1 = O.yield_of(s2, w.atmosphere, par, seg_index=3)
+    y0 = O.yield_of(s2, w.atmosphere, dataclasses.replace(par, fl_roulette=0), seg_index=3)
+    assert (y1["n_f"], y1["w_f"]) == (y0["n_f"], y0["w_f"]) == (4.0, pytest.approx(36.5 / 4))
+
+
+def test_fluorescence_roulette_keeps_the_mean_photon_sums():
+    """Beamed steps with few photons under count rule 1: far fewer rays,
+    the same expected photon sums at the telescopes."""
+    kw = dict(dE=(50.0, 150.0), xy=1000.0, z=(3000.0, 4500.0))
+    wb = _fluor_workload(100000, 11, 1, **kw)
+    wb.params = dataclasses.replace(wb.params, bunch=10.0)
+    wr = _fluor_workload(100000, 11, 1, **kw)
+    wr.params = dataclasses.replace(wr.params, bunch=10.0, fl_roulette=1)
+    hb, cb, sb, stb = O.trace(wb.segments, wb.atmosphere, wb.telescopes, wb.params)
+    hr, cr, sr, str_ = O.trace(wr.segments, wr.atmosphere, wr.telescopes, wr.params)
+    assert str_["rays"] < 0.5 * stb["rays"]
+    # emitted with weight B (the hit weight is that times the transmission)
+    for h in hr[:20]:
+        assert O.photon(wr.segments[h["seg"]], int(h["seg"]), int(h["k"]), wr.atmosphere, wr.params)[4] == 10.0
+    assert np.all(hr["weight"] <= 10.0)
+    tb, tr = sb.sum(), sr.sum()
+    # roulette hits: counts of weight 10 (Poisson-like); the ceil side is nearly exact
+    assert len(hr) > 30
+    assert abs(tr - tb) < 5 * 10.0 * math.sqrt(tb / 10.0 + 1), (tb, tr)
+
+
 # ---------------------------------------------------------------- dispersion
 def _disp_atm(B):
     a = I.atmosphere_layered()
