@@ -247,6 +247,16 @@ clight_status clight_set_atmosphere(clight_ctx *c, const clight_atmosphere *a)
     A.delta_obs = (float)A.delta_obs_d;
     A.n_obs = (float)(1.0 + A.delta_obs_d);
     {
+        // each layer's largest refractivity above h_obs sits at its bottom
+        double dm = A.delta_obs_d;
+        for (int i = 0; i < a->n_layers; ++i) {
+            double top = i + 1 < a->n_layers ? a->h_lo[i + 1] : a->h_top;
+            if (top <= a->h_obs) continue;
+            dm = std::max(dm, a->K * Bc(i) * std::exp(-std::max(a->h_lo[i], a->h_obs) / a->c[i]));
+        }
+        A.delta_max = (float)dm;
+    }
+    {
         // closed-form layer integrals for the straight-line propagator
         double above_d = 0.0, above_r = 0.0;   // integrals over the layers above layer i
         for (int i = a->n_layers - 1; i >= 0; --i) {

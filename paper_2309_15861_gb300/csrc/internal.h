@@ -30,6 +30,7 @@ struct DevAtm {
     double h_top_d, h_obs_d, R_E_d, r_obs_d;  // binary64 copies
     float delta_obs, n_obs;                   // n(h_obs) - 1 and n(h_obs)
     double delta_obs_d;
+    float delta_max;                          // largest n - 1 between h_obs and h_top
     float inv_L0, lambda_ref;                 // tau = I * (lambda_ref/lambda)^4 * inv_L0
     double inv_L0_d, lambda_ref_d;
     // the same constants as FP32 pairs (hi, lo), so that no ray converts binary64

@@ -948,9 +948,51 @@ __device__ __forceinline__ void straight_corrections(const DevAtm &A, T he, T de
 constexpr int FEAT_EXT = 1, FEAT_STRAIGHT = 2, FEAT_RUNTIME = 4, FEAT_DISP = 8,
               FEAT_ALL = FEAT_EXT | FEAT_RUNTIME | FEAT_DISP;
 
-template <class T, class P, bool WARP, bool SPH, bool REFR, int FEAT = FEAT_ALL>
+// Rays that cannot land near a telescope skip the quadrature.  Bouguer's
+// invariant n r sin(psi) with n growing downward makes the refracted ray
+// steeper than its vacuum line at every radius; the vacuum line's zenith
+// angle is largest at its landing point (sin psi = p_v / r grows as r
+// falls).  With mu that smallest cosine, s = sqrt(1 - mu^2) and delta_max
+// the largest refractivity, tan(psi_v) - tan(psi) <= s delta_max / mu^3 at
+// every height, so the refracted crossing of the plane z = h_obs lies within
+// s delta_max (h_e - h_obs + zeta) / mu^3 of the vacuum crossing (zeta, the
+// depth of the sphere below the plane, adds the stretch from the sphere back
+// up to the plane), and the arrival direction within s delta_max / mu of the
+// vacuum one.  With a factor 1.25 and 5 cm for binary32 rounding: if no
+// centre lies within that distance plus the hit test's search radius of the
+// vacuum crossing, the ray hits nothing.  Returns true for such a ray.
+__device__ __forceinline__ bool clear_miss(float xe, float ye, float ze, float dx, float dy, float dz, float he,
+                                           float cos_obs, float gl, const DevAtm &A, const DevTel &Tl,
+                                           const uint8_t *clr, bool sph, bool refr)
+{
+    const float tp = (ze - A.h_obs) * rcp_approx(-dz);
+    const float Xv = xe + tp * dx, Yv = ye + tp * dy;
+    float mu = (sph ? fminf(cos_obs, -dz) : -dz) - 1.0e-3f;
+    if (!(mu > 0.05f)) return false;
+    const float s = sqrtf(fmaxf(0.0f, 1.0f - mu * mu));
+    const float im = rcp_approx(mu);
+    const float sd = refr ? 1.25f * s * A.delta_max * gl : 0.0f;
+    const float zeta = sph ? (Xv * Xv + Yv * Yv) * A.inv_r_obs : 0.0f;
+    const float B = sd * ((he - A.h_obs) + zeta) * (im * im * im) + 0.05f;
+    const float czb = -dz - sd * im - 1.0e-5f;            // below the arrival |cz|
+    if (!(czb > 0.05f)) return false;
+    const float dzmax = fmaxf(fabsf(Tl.zmax - A.h_obs), fabsf(Tl.zmin - A.h_obs));
+    const float rs = (Tl.Rmax + dzmax * sqrtf(fmaxf(0.0f, 1.0f - czb * czb))) * rcp_approx(czb) + 2.0e-3f + B;
+    if (Xv + rs < Tl.xmin || Xv - rs > Tl.xmax || Yv + rs < Tl.ymin || Yv - rs > Tl.ymax) return true;
+    if (clr) {
+        float fx = (Xv - Tl.cx0) * Tl.inv_cgs, fy = (Yv - Tl.cy0) * Tl.inv_cgs;
+        if (fx >= 0.0f && fy >= 0.0f && fx < (float)Tl.cnx && fy < (float)Tl.cny)
+            return rs < (float)clr[(int)fy * Tl.cnx + (int)fx] * kClrQuantum;
+    }
+    return false;
+}
+
+// CULL (binary32 only): skip the quadrature for rays clear_miss rejects;
+// they end with status 6 (reached the observation level, no telescope near).
+template <class T, class P, bool WARP, bool SPH, bool REFR, int FEAT = FEAT_ALL, bool CULL = false>
 __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global, uint32_t k, bool active,
-                                          const DevAtm &A, const DevPar &Pp, RayOut<T, P> &o)
+                                          const DevAtm &A, const DevPar &Pp, RayOut<T, P> &o,
+                                          const DevTel *Tl = nullptr, const uint8_t *clr = nullptr)
 {
     // ---- generation (Sec. 1.1, 1.2, 1.2.1; Fig. 1)
     uint32_t proc = k < g.n_c ? 0u : 1u;
@@ -1116,6 +1158,12 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
     else if (turned) { o.status = 3; }
     else if (grazing) { o.status = 5; }
     bool go = o.status == 0;
+    if (CULL && sizeof(T) == 4 && go &&
+        clear_miss((float)xef, (float)yef, (float)zef, (float)dx, (float)dy, (float)dz, (float)he,
+                   SPH ? (float)sqf * A.inv_r_obs : 0.0f, (float)gl, A, *Tl, clr, SPH, REFR)) {
+        o.status = 6;
+        go = false;
+    }
 
     // ---- refraction, optical path and optical depth by quadrature
     T htop = sizeof(T) == 4 ? (T)A.h_top : (T)A.h_top_d;

@@ -211,7 +211,7 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
                 if (active) {
                     ++c_rays;
                     c_esc += o.status == 1; c_under += o.status == 2; c_turn += o.status == 3;
-                    c_reach += o.status == 0 || o.status == 5;
+                    c_reach += o.status == 0 || o.status >= 5;
                     c_cells += o.status == 0 ? o.cells : 0;
                 }
             } else if (SOFT) {
@@ -232,17 +232,17 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
                 nh = cand ? 1 : 0;
                 if (active) {
                     ++c_rays;
-                    c_reach += o.status == 0 || o.status == 5;
+                    c_reach += o.status == 0 || o.status >= 5;
                     c_cells += o.status == 0 ? o.cells : 0;
                 }
             } else {
                 RayOut<float, df> o;
-                trace_ray<float, df, true, SPH, REFR, FEAT>(q, seg_global, k, active, A, Pp, o);
+                trace_ray<float, df, true, SPH, REFR, FEAT, true>(q, seg_global, k, active, A, Pp, o, &Tl, clr);
                 nh = hit_test<float, df, true, NOALLOC>(o, Pp.key_off + seg_local, seg_global, k, q.shower, A, Tl, Pp, O, status_bits, clr);
                 if (active) {
                     ++c_rays;
                     c_esc += o.status == 1; c_under += o.status == 2; c_turn += o.status == 3;
-                    c_reach += o.status == 0 || o.status == 5;
+                    c_reach += o.status == 0 || o.status >= 5;
                     c_cells += o.status == 0 ? o.cells : 0;
                 }
             }
@@ -292,7 +292,7 @@ k_trace_fp64(const clight_segment *__restrict__ segs, int64_t n_segs, const __gr
             trace_ray<double, double, false, SPH, REFR>(g, seg_global, k, true, A, Pp, o);
             ++c_rays;
             c_esc += o.status == 1; c_under += o.status == 2; c_turn += o.status == 3;
-            c_reach += o.status == 0 || o.status == 5;
+            c_reach += o.status == 0 || o.status >= 5;
             c_cells += o.status == 0 ? o.cells : 0;
             c_hits += hit_test<double, double, false>(o, i, seg_global, k, g.shower, A, Tl, Pp, O, status_bits);
         }
