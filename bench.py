@@ -35,17 +35,22 @@ METRIC = "traced photons/s, 1 GB300: batched FP32 vs plain FP64 at oracle tolera
 UNIT = "rays/s"
 
 # Algorithmic operations per unit of work on the FMA/ALU pipes, counted
-# from the kernel source (trace_kernels.cu): per quadrature node of the
-# refracted spherical integrand, per altitude cell (node placement and
-# accumulation), and per ray outside the nodes (Philox rounds, cone,
-# emission point, vacuum line and landing point in FP32 pairs, arrival
-# time, absorption, hit search).  MUFU ops (ex2, rsqrt, rcp) counted apart.
+# from the kernel source (trace_kernels.cu, ray.cuh): per quadrature node of
+# the refracted spherical integrand, per altitude cell (node placement and
+# accumulation), per ray traced in full outside the nodes (Philox rounds,
+# cone, emission point, vacuum line and landing point in FP32 pairs, arrival
+# time, absorption, hit search), and per ray that the first pass shows to
+# land clear of every telescope (Philox rounds, cone, emission point and
+# altitude in binary32, the displacement bound and the clearance lookup:
+# skip_ray and clear_miss).  MUFU ops (ex2, rsqrt, rcp, sin, cos) counted apart.
 OPS_NODE = 39
 MUFU_NODE = 5
 NODES_PER_CELL = 3
 OPS_CELL = 8
 OPS_RAY = 680
 MUFU_RAY = 12
+OPS_SKIPPED_RAY = 255
+MUFU_SKIPPED_RAY = 7
 FP32_LANES_PER_SM = 128
 MUFU_LANES_PER_SM = 16
 
@@ -360,12 +365,15 @@ def main():
     value = rays_all * args.steps / (ms / 1e3)
     key_bits = (ng - 1).bit_length() + (n - 1).bit_length() + 16
     passes = (key_bits + 7) // 8
-    launches_per_step = 1 + 5 * passes + 3 + (3 if adj is not None else 0)
+    # the fused kernel, plus the deferred-ray kernel on the default path
+    deferred = args.precision == 0 and args.disp_B == 0 and args.propagator == "exact"
+    launches_per_step = (2 if deferred else 1) + 5 * passes + 3 + (3 if adj is not None else 0)
 
     # ---- roofline of the dominant kernel (generation + propagation + hits)
     k_ms = statistics.mean(kms)
-    ops = st["rays"] * OPS_RAY + st["cells"] * (OPS_CELL + NODES_PER_CELL * OPS_NODE)
-    mufu = st["rays"] * MUFU_RAY + st["cells"] * NODES_PER_CELL * MUFU_NODE
+    full = st["rays"] - st["skipped"]
+    ops = full * OPS_RAY + st["skipped"] * OPS_SKIPPED_RAY + st["cells"] * (OPS_CELL + NODES_PER_CELL * OPS_NODE)
+    mufu = full * MUFU_RAY + st["skipped"] * MUFU_SKIPPED_RAY + st["cells"] * NODES_PER_CELL * MUFU_NODE
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     peaks = {}
     try:
@@ -380,7 +388,7 @@ def main():
             "frac": achieved / peak_ops, "traffic": traffic,
             "traffic_note": "DRAM bytes per launch: ncu capture of 2e6 steps scaled by steps "
                             "(profiles/k_trace_fused_traffic.txt); null if the kernel changed since",
-            "kernel": "k_trace_fused", "kernel_ms": k_ms, "sort_ms": statistics.mean(sms),
+            "kernel": "k_trace_fused + k_trace_deferred" if deferred else "k_trace_fused", "kernel_ms": k_ms, "sort_ms": statistics.mean(sms),
             "mufu_frac": (mufu / (k_ms / 1e3)) / (n_sm * MUFU_LANES_PER_SM * f_max),
             "ops_per_ray": ops / max(1, st["rays"]), "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                                                  f"{f_max / 1e6:.0f} MHz (max SM clock)"}
@@ -450,8 +458,9 @@ def main():
                "h2d_bytes_per_step": int(n * 64),
                "d2h_bytes_per_step": int(len(hh) * 48 + cbuf.numel() * 8 + sbuf.numel() * 8),
                "ms_per_step": wall * 1e3 / k2,
-               "path": "clight_trace_host on pinned host buffers: the kernel reads the steps in place over "
-                       "the CPU-GPU link every step; hits, counts and sums copied back every step"}
+               "path": "clight_trace_host on pinned host buffers: the steps copied to the device every step "
+                       "(2^22-step chunks on a copy stream, each launch waiting for its own chunk); hits, "
+                       "counts and sums copied back every step"}
         ctx.set_params(w.params, **extra)
         del pinned, hbuf
 

@@ -150,6 +150,18 @@ typedef struct {
      * the smaller photon numbers into fewer rays. */
     int32_t fl_roulette;
     int32_t roulette_pad;
+    /* Entries of the deferred-ray queue.  The fused kernel first decides,
+     * from each ray's vacuum line, whether it can land near a telescope;
+     * rays that can are queued and traced in full by a second kernel in
+     * full warps.  0 = 2 per step (at least 2^20, at most 2^28, 8 bytes
+     * each), launches of at most half as many steps; a call that fills it
+     * runs again with twice the queue (remembered by the context, at most
+     * 2^31 entries), then without it.  > 0 = that many entries (<= 2^31); a
+     * call that fills them runs again without the queue.  < 0 = no queue:
+     * every ray is traced in the fused kernel.  The hits are the same in
+     * every case.  Without device memory for the queue the call runs
+     * without it. */
+    int64_t defer_cap;
 } clight_params;
 
 enum {
@@ -180,6 +192,8 @@ typedef struct {
     int64_t status;     /* OR of CLIGHT_ERR_* bits seen in the kernels (1 << code) */
     int64_t cells;      /* altitude cells integrated, summed over arrived rays */
     int64_t cut;        /* steps whose Cherenkov light the angular cut removed */
+    int64_t skipped;    /* arrived rays that provably land clear of every telescope,
+                           decided from their vacuum line (no quadrature, no landing) */
 } clight_stats;
 
 typedef struct clight_ctx clight_ctx;
@@ -233,10 +247,9 @@ clight_status clight_trace_fp64(clight_ctx *ctx, const clight_segment *d_segs, i
 
 /* clight_trace on HOST buffers, results copied back to h_hits / h_counts /
  * h_sums (the last two may be NULL).  How the steps reach the GPU:
- *   - page-locked (pinned) h_segs: the kernel reads them in place over the
- *     CPU-GPU link (coherent on Grace-Blackwell), each record once;
- *   - pageable h_segs of at least 2 x 2^22 steps: copied in chunks of 2^22
- *     steps on a second stream while earlier chunks are traced;
+ *   - at least 2 x 2^22 steps: copied in chunks of 2^22 steps on a second
+ *     stream while earlier chunks are traced (from page-locked memory the
+ *     copies run at the link's DMA rate, about 210 GB/s on GB300);
  *   - otherwise one copy, then the trace.
  * Device staging buffers are owned by the context.  Same results in every
  * case.  Synchronises `stream`. */

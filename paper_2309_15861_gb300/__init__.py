@@ -56,12 +56,13 @@ class Params(C.Structure):
                 ("cut_mode", C.c_int32), ("cut_pad", C.c_int32), ("cut_deg", C.c_double),
                 ("cut_centre", C.c_double * 3), ("fl_beaming", C.c_int32), ("propagator", C.c_int32),
                 ("beam_centre", C.c_double * 3), ("beam_radius", C.c_double), ("fl_roulette", C.c_int32),
-                ("roulette_pad", C.c_int32)]
+                ("roulette_pad", C.c_int32), ("defer_cap", C.c_int64)]
 
 
 class Stats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in
-                ("rays", "escaped", "under", "turned", "reached", "hits", "guarded", "status", "cells", "cut")]
+                ("rays", "escaped", "under", "turned", "reached", "hits", "guarded", "status", "cells", "cut",
+                 "skipped")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}

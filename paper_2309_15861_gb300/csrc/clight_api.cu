@@ -47,10 +47,12 @@ struct GraphKey {
     const void *counts;
     const void *sums;
     uint64_t version;
+    int64_t defer_use;
     bool operator==(const GraphKey &o) const
     {
         return segs == o.segs && n_segs == o.n_segs && n_showers == o.n_showers && hits == o.hits &&
-               cap == o.cap && counts == o.counts && sums == o.sums && version == o.version;
+               cap == o.cap && counts == o.counts && sums == o.sums && version == o.version &&
+               defer_use == o.defer_use;
     }
 };
 
@@ -71,6 +73,11 @@ struct clight_ctx {
     unsigned long long *d_ctr = nullptr;
     Buf<clight_hit> rec;
     Buf<unsigned long long> keys, keys_alt;
+    Buf<unsigned long long> defer;              // rays left to the deferred kernel
+    int64_t defer_use = 0;                      // entries of it in use (0 = no queue)
+    int64_t defer_piece = 0;                    // steps per launch with the default queue
+    int64_t defer_min = 0;                      // queue size learned from calls that filled it
+    bool defer_off = false;                     // this call runs without the queue
     Buf<uint32_t> vals, vals_alt, hist, bsums;
     Buf<int64_t> gstart, gend;
     uint64_t scratch_gen = 0;
@@ -174,6 +181,7 @@ void clight_destroy(clight_ctx *c)
     for (void *p : dev)
         if (p) cudaFree(p);
     c->rec.release(); c->keys.release(); c->keys_alt.release(); c->vals.release(); c->vals_alt.release();
+    c->defer.release();
     c->hist.release(); c->bsums.release(); c->gstart.release(); c->gend.release();
     c->stage_segs.release(); c->stage_hits.release(); c->stage_counts.release(); c->stage_sums.release();
     c->adj_partial.release(); c->adj_out.release(); c->adj_cand.release(); c->adj_ctr.release();
@@ -461,6 +469,7 @@ clight_status clight_set_params(clight_ctx *c, const clight_params *p)
         return CLIGHT_ERR_ARG;
     if (p->fl_beaming != 0 && p->fl_beaming != 1) return CLIGHT_ERR_ARG;
     if (p->fl_roulette != 0 && p->fl_roulette != 1) return CLIGHT_ERR_ARG;
+    if (p->defer_cap > (int64_t(1) << 31)) return CLIGHT_ERR_ARG;
     if (p->propagator != CLIGHT_PROP_EXACT && p->propagator != CLIGHT_PROP_STRAIGHT) return CLIGHT_ERR_ARG;
     if (p->fl_beaming && (!(p->beam_radius > 0) || !std::isfinite(p->beam_radius) ||
                           !std::isfinite(p->beam_centre[0]) || !std::isfinite(p->beam_centre[1]) ||
@@ -578,6 +587,23 @@ clight_status prepare(clight_ctx *c, int64_t n_segs, int32_t n_showers, int64_t 
         c->bsums.ensure(scan_block_sums_needed(256 * pl.tiles), g) || c->gstart.ensure(pl.n_groups, g) ||
         c->gend.ensure(pl.n_groups, g))
         return CLIGHT_ERR_CUDA;
+    // the deferred-ray queue: by default two entries per step (at least
+    // 2^20, at most 2^28) and launches of half as many steps, which covers
+    // every workload measured (0.2 to 0.9 queued rays per step); a call that
+    // fills it runs again with twice the queue (default) or without it
+    const int64_t dc = c->upar.defer_cap;
+    const int64_t dflt = std::min<int64_t>(std::max<int64_t>(2 * n_segs, 1 << 20), 1 << 28);
+    c->defer_piece = dflt / 2;
+    if (c->defer_off || dc < 0)
+        c->defer_use = 0;
+    else if (dc > 0)
+        c->defer_use = dc;
+    else
+        c->defer_use = std::min<int64_t>(std::max(dflt, c->defer_min), int64_t(1) << 31);
+    if (c->defer_use > 0 && c->defer.ensure(c->defer_use, g) != cudaSuccess) {
+        cudaGetLastError();                      // no room for the queue: trace in place
+        c->defer_use = 0;
+    }
     return CLIGHT_OK;
 }
 
@@ -596,6 +622,9 @@ cudaError_t enqueue(clight_ctx *c, const clight_segment *segs, int64_t n_segs, c
     O.vals = c->vals.p;
     O.capacity = cap;
     O.ctr = c->d_ctr;
+    O.soft_w = 0.0f;
+    O.defer = c->defer_use > 0 ? c->defer.p : nullptr;
+    O.defer_cap = c->defer_use;
     SortScratch S;
     S.keys_alt = c->keys_alt.p;
     S.vals_alt = c->vals_alt.p;
@@ -612,18 +641,24 @@ cudaError_t enqueue(clight_ctx *c, const clight_segment *segs, int64_t n_segs, c
             e = launch_trace_fp64(segs, n_segs, c->atm, c->tel, c->par, O, s);
         } else {
             int block = c->upar.block > 0 ? c->upar.block : 256;
-            int per_sm = c->upar.ctas_per_sm > 0 ? c->upar.ctas_per_sm : 3 * 256 / block;
+            // the first pass of the deferred path fits 4 CTAs of 256 per SM, the in-place kernel 3
+            const bool deferred = c->defer_use > 0 && c->upar.precision == CLIGHT_PREC_FLOAT_PAIR && !c->atm.disp &&
+                                  c->par.prop != CLIGHT_PROP_STRAIGHT;
+            int per_sm = c->upar.ctas_per_sm > 0 ? c->upar.ctas_per_sm : (deferred ? 4 : 3) * 256 / block;
             int64_t step = chunk > 0 ? chunk : n_segs;
+            // with the default queue size, launches of at most half as many
+            // steps as the queue holds entries, so that it does not fill
+            if (chunk == 0 && c->defer_use > 0 && c->upar.defer_cap == 0)
+                step = std::min(step, std::max<int64_t>(c->defer_piece, 1));
             for (int64_t off = 0, i = 0; off < n_segs && e == cudaSuccess; off += step, ++i) {
                 int64_t n = std::min(step, n_segs - off);
                 int64_t groups = (n + 31) / 32;
                 int64_t grid = std::min<int64_t>((int64_t)c->n_sm * per_sm, (groups * 32 + block - 1) / block);
                 grid = std::max<int64_t>(grid, 1);
                 DevPar P = c->par;
-                if (chunk > 0) {
-                    if ((e = cudaStreamWaitEvent(s, chunk_ev[i], 0)) != cudaSuccess) break;
-                    if (off > 0 && (e = cudaMemsetAsync(c->d_ctr + CTR_WORK, 0, sizeof(unsigned long long), s)) !=
-                                       cudaSuccess)
+                if (chunk > 0 && (e = cudaStreamWaitEvent(s, chunk_ev[i], 0)) != cudaSuccess) break;
+                if (off > 0) {
+                    if ((e = cudaMemsetAsync(c->d_ctr + CTR_WORK, 0, sizeof(unsigned long long), s)) != cudaSuccess)
                         break;
                     P.seg_base += off;
                     P.key_off = off;
@@ -657,6 +692,7 @@ clight_status finish(clight_ctx *c, int64_t cap, clight_stats *st, int64_t *n_hi
         st->status = (int64_t)bits;
         st->cells = (int64_t)h[CTR_STATS + ST_CELLS];
         st->cut = (int64_t)h[CTR_STATS + ST_CUT];
+        st->skipped = (int64_t)h[CTR_STATS + ST_SKIPPED];
     }
     c->timed = true;
     if ((int64_t)cursor > cap) return CLIGHT_ERR_HIT_CAPACITY;
@@ -665,17 +701,29 @@ clight_status finish(clight_ctx *c, int64_t cap, clight_stats *st, int64_t *n_hi
     return CLIGHT_OK;
 }
 
-clight_status run(clight_ctx *c, const clight_segment *segs, int64_t n_segs, int32_t n_showers, clight_hit *hits,
-                  int64_t cap, int64_t *counts, double *sums, clight_stats *st, int64_t *n_hits, void *stream,
-                  bool fp64)
+// After a call: whether a launch found the deferred-ray queue full, in which
+// case the call must run again -- with twice the queue (default size, up to
+// 2^31 entries, remembered for later calls) or without the queue.
+bool defer_retry(clight_ctx *c)
 {
-    if (!c || (n_segs > 0 && !segs) || (cap > 0 && !hits) || !n_hits) return CLIGHT_ERR_ARG;
+    if (!(c->h_ctr[CTR_STATS + ST_STATUS] & (1ull << kBitDeferFull))) return false;
+    if (c->upar.defer_cap == 0 && c->defer_use < (int64_t(1) << 31))
+        c->defer_min = std::min<int64_t>(2 * c->defer_use, int64_t(1) << 31);
+    else
+        c->defer_off = true;
+    return true;
+}
+
+clight_status run_once(clight_ctx *c, const clight_segment *segs, int64_t n_segs, int32_t n_showers,
+                       clight_hit *hits, int64_t cap, int64_t *counts, double *sums, void *stream, bool fp64)
+{
     Plan pl;
     clight_status r = prepare(c, n_segs, n_showers, cap, pl);
     if (r != CLIGHT_OK) return r;
     cudaStream_t s = (cudaStream_t)stream;
     if (!fp64 && c->upar.use_graph) {
-        GraphKey k{segs, n_segs, n_showers, hits, cap, counts, sums, c->version * 1000003ull + c->scratch_gen};
+        GraphKey k{segs, n_segs, n_showers, hits, cap, counts, sums, c->version * 1000003ull + c->scratch_gen,
+                   c->defer_use};
         if (!c->gexec || !(k == c->gkey)) {
             if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
             cudaGraph_t g;
@@ -698,6 +746,21 @@ clight_status run(clight_ctx *c, const clight_segment *segs, int64_t n_segs, int
         CK(enqueue(c, segs, n_segs, pl, hits, cap, counts, sums, fp64, s, false));
         CK(cudaStreamSynchronize(s));
     }
+    return CLIGHT_OK;
+}
+
+clight_status run(clight_ctx *c, const clight_segment *segs, int64_t n_segs, int32_t n_showers, clight_hit *hits,
+                  int64_t cap, int64_t *counts, double *sums, clight_stats *st, int64_t *n_hits, void *stream,
+                  bool fp64)
+{
+    if (!c || (n_segs > 0 && !segs) || (cap > 0 && !hits) || !n_hits) return CLIGHT_ERR_ARG;
+    clight_status r;
+    c->defer_off = false;
+    do {
+        r = run_once(c, segs, n_segs, n_showers, hits, cap, counts, sums, stream, fp64);
+    } while (r == CLIGHT_OK && defer_retry(c));
+    c->defer_off = false;
+    if (r != CLIGHT_OK) return r;
     return finish(c, cap, st, n_hits);
 }
 
@@ -734,22 +797,11 @@ clight_status clight_trace_host(clight_ctx *c, const clight_segment *h_segs, int
         return CLIGHT_ERR_CUDA;
     clight_status r;
     const int64_t chunk = int64_t(1) << 22;          // 268 MB of steps per copy
-    // Pinned (page-locked) host memory is coherent and readable by the GPU
-    // over NVLink-C2C: the kernel then reads every step where it lies, each
-    // record once, with no staging copy.
-    cudaPointerAttributes pa{};
-    const clight_segment *d_direct = nullptr;
-    if (n_segs > 0 && cudaPointerGetAttributes(&pa, h_segs) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
-        pa.devicePointer != nullptr)
-        d_direct = static_cast<const clight_segment *>(pa.devicePointer);
-    cudaGetLastError();
-    if (d_direct) {
-        r = run(c, d_direct, n_segs, n_showers, c->stage_hits.p, cap, c->stage_counts.p, c->stage_sums.p, st,
-                h_n_hits, stream, false);
-    } else if (n_segs >= 2 * chunk) {
-        // copies on the copy stream overlap the tracing of the chunks before
-        Plan pl;
-        if ((r = prepare(c, n_segs, n_showers, cap, pl)) != CLIGHT_OK) return r;
+    // The steps go to the device by DMA copies (from pinned memory at about
+    // 210 GB/s over NVLink-C2C, faster than the kernel reading them in place
+    // over the same link), chunk by chunk on the copy stream, each launch
+    // waiting for its chunk only, so that copies and tracing overlap.
+    if (n_segs >= 2 * chunk) {
         int64_t nck = (n_segs + chunk - 1) / chunk;
         while ((int64_t)c->chunk_ev.size() < nck) {
             cudaEvent_t e;
@@ -764,9 +816,16 @@ clight_status clight_trace_host(clight_ctx *c, const clight_segment *h_segs, int
                                cudaMemcpyHostToDevice, c->copy_stream));
             CK(cudaEventRecord(c->chunk_ev[i], c->copy_stream));
         }
-        CK(enqueue(c, c->stage_segs.p, n_segs, pl, c->stage_hits.p, cap, c->stage_counts.p, c->stage_sums.p, false,
-                   s, false, chunk, c->chunk_ev.data()));
-        CK(cudaStreamSynchronize(s));
+        c->defer_off = false;
+        do {
+            Plan pl;
+            if ((r = prepare(c, n_segs, n_showers, cap, pl)) != CLIGHT_OK) break;
+            CK(enqueue(c, c->stage_segs.p, n_segs, pl, c->stage_hits.p, cap, c->stage_counts.p, c->stage_sums.p,
+                       false, s, false, chunk, c->chunk_ev.data()));
+            CK(cudaStreamSynchronize(s));
+        } while (defer_retry(c));
+        c->defer_off = false;
+        if (r != CLIGHT_OK) return r;
         r = finish(c, cap, st, h_n_hits);
     } else {
         if (n_segs > 0)

@@ -53,6 +53,18 @@ __device__ __forceinline__ float rsqrt_approx(float x)
     return r;
 }
 
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+// floor of 0 <= x < 2^23 as an integer, by one add rounded down (no F2I)
+__device__ __forceinline__ int floor_small(float x)
+{
+    return (int)(__float_as_uint(__fadd_rd(x, 8388608.0f)) - 0x4B000000u);
+}
+
 template <class T> struct Num;
 template <> struct Num<float> {
     static __device__ __forceinline__ float div(float a, float b) { return a * rcp_approx(b); }
@@ -969,7 +981,7 @@ __device__ __forceinline__ bool clear_miss(float xe, float ye, float ze, float d
     const float Xv = xe + tp * dx, Yv = ye + tp * dy;
     float mu = (sph ? fminf(cos_obs, -dz) : -dz) - 1.0e-3f;
     if (!(mu > 0.05f)) return false;
-    const float s = sqrtf(fmaxf(0.0f, 1.0f - mu * mu));
+    const float s = sqrt_approx(1.0f - mu * mu);           // mu < 0.999
     const float im = rcp_approx(mu);
     const float sd = refr ? 1.25f * s * A.delta_max * gl : 0.0f;
     const float zeta = sph ? (Xv * Xv + Yv * Yv) * A.inv_r_obs : 0.0f;
@@ -977,12 +989,12 @@ __device__ __forceinline__ bool clear_miss(float xe, float ye, float ze, float d
     const float czb = -dz - sd * im - 1.0e-5f;            // below the arrival |cz|
     if (!(czb > 0.05f)) return false;
     const float dzmax = fmaxf(fabsf(Tl.zmax - A.h_obs), fabsf(Tl.zmin - A.h_obs));
-    const float rs = (Tl.Rmax + dzmax * sqrtf(fmaxf(0.0f, 1.0f - czb * czb))) * rcp_approx(czb) + 2.0e-3f + B;
+    const float rs = (Tl.Rmax + dzmax * sqrt_approx(1.0f - czb * czb)) * rcp_approx(czb) + 2.0e-3f + B;
     if (Xv + rs < Tl.xmin || Xv - rs > Tl.xmax || Yv + rs < Tl.ymin || Yv - rs > Tl.ymax) return true;
     if (clr) {
         float fx = (Xv - Tl.cx0) * Tl.inv_cgs, fy = (Yv - Tl.cy0) * Tl.inv_cgs;
         if (fx >= 0.0f && fy >= 0.0f && fx < (float)Tl.cnx && fy < (float)Tl.cny)
-            return rs < (float)clr[(int)fy * Tl.cnx + (int)fx] * kClrQuantum;
+            return rs < (float)clr[floor_small(fy) * Tl.cnx + floor_small(fx)] * kClrQuantum;
     }
     return false;
 }

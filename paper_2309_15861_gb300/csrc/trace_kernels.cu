@@ -17,21 +17,33 @@ namespace clight {
 // Shared-memory record of a warp's 32 segments, one field per row so that
 // lanes reading one field of different segments hit different banks.
 enum SegField {
-    F_X0H, F_X0L, F_Y0H, F_Y0L, F_Z0H, F_Z0L, F_T0H, F_T0L, F_A0H, F_A0L, F_C0H, F_C0L,
-    F_DX, F_DY, F_DZ, F_LX, F_LY, F_LZ, F_E1X, F_E1Y, F_E1Z, F_E2X, F_E2Y, F_E2Z,
-    F_SIN, F_KAP, F_L, F_IBC, F_WC, F_WF, F_NC, F_NF, F_SHOWER, F_SEGI, F_INCL,
+    // what the first pass of the deferred path (skip_ray) and the bunch loop read
+    F_X0H, F_Y0H, F_Z0H, F_DX, F_DY, F_DZ, F_E1X, F_E1Y, F_E1Z, F_E2X, F_E2Y, F_E2Z,
+    F_SIN, F_KAP, F_L, F_NC, F_NF, F_SEGI, F_INCL,
+    F_DEFER_END,
+    // the rest of what a ray traced in the fused kernel needs
+    F_X0L = F_DEFER_END, F_Y0L, F_Z0L, F_T0H, F_T0L, F_A0H, F_A0L, F_C0H, F_C0L, F_LX, F_LY, F_LZ,
+    F_IBC, F_WC, F_WF, F_SHOWER,
     F_BUX, F_BUY, F_BUZ, F_BOMC,          // beamed fluorescence (kernels with FEAT_EXT only)
     F_COUNT
 };
-__host__ __device__ constexpr int fields_of(bool ext) { return ext ? F_COUNT : F_BUX; }
+__host__ __device__ constexpr int fields_of(bool ext, bool defer = false)
+{
+    return ext ? F_COUNT : (defer ? F_DEFER_END : F_BUX);
+}
 
 // Segment records of the warps, then (kernels without FEAT_EXT) the
 // clearance map; with FEAT_EXT the records are larger and the map is read
 // from global memory, so that both stay under 48 KB.
-static int seg_smem_bytes(int block, bool ext) { return (block / 32) * fields_of(ext) * 32 * (int)sizeof(float); }
-static int fused_smem_bytes_f(int block, const DevTel &T, bool ext)
+static int seg_smem_bytes(int block, bool ext, bool defer)
 {
-    return seg_smem_bytes(block, ext) + (!ext && T.clr ? T.clr_bytes : 0);
+    return (block / 32) * fields_of(ext, defer) * 32 * (int)sizeof(float);
+}
+static int fused_smem_bytes_f(int block, const DevTel &T, bool ext, bool defer = false)
+{
+    // the deferred first pass without FEAT_EXT also stages the next group's records
+    return seg_smem_bytes(block, ext, defer) + (!ext && T.clr ? T.clr_bytes : 0) +
+           (defer && !ext ? (block / 32) * 2048 : 0);
 }
 int fused_smem_bytes(int block, const DevTel &T) { return fused_smem_bytes_f(block, T, true); }
 
@@ -59,13 +71,127 @@ __device__ __forceinline__ uint32_t warp_sort_u32(uint32_t key, int lane)
     return key;
 }
 
-template <class P, bool SPH, bool REFR, bool NOALLOC = false, bool SOFT = false, int FEAT = FEAT_ALL>
-__global__ void __launch_bounds__(256, 3)
+// Asynchronous 16-byte global -> shared copies (L2 only), for the next
+// group's step records while the current group is worked on.
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// The 32 records (2 KB, contiguous) of the group starting at s_first, in
+// 16-byte pieces spread over the warp; records at or past n_segs are not read.
+__device__ __forceinline__ void prefetch_group(float4 *stage, const clight_segment *segs, int64_t n_segs,
+                                               int64_t s_first, int lane)
+{
+    if (s_first >= n_segs) return;
+    const float4 *src = reinterpret_cast<const float4 *>(segs + s_first);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int c = lane + 32 * j;
+        if (s_first + (c >> 2) < n_segs) cp_async16(stage + c, src + c);
+    }
+    cp_async_commit();
+}
+constexpr int kStageBytes = 32 * (int)sizeof(clight_segment);   // per warp
+
+// One atomic per warp and counter (the warp's lanes reduced by shuffles).
+__device__ __forceinline__ void flush_stats(const uint32_t (&vals)[ST_N], unsigned status_bits, const DevOut &O,
+                                            int lane)
+{
+#pragma unroll
+    for (int i = 0; i < ST_N; ++i) {
+        if (i == ST_STATUS) continue;
+        uint32_t v = vals[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+        if (lane == 0 && v) atomicAdd(O.ctr + CTR_STATS + i, (unsigned long long)v);
+    }
+    unsigned sb = status_bits;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sb |= __shfl_xor_sync(FULL_MASK, sb, o);
+    if (lane == 0 && sb) atomicOr(O.ctr + CTR_STATS + ST_STATUS, (unsigned long long)sb);
+}
+
+// First pass of the deferred path: ray k of the step in record l, its
+// direction and emission point in binary32 only, and whether it can be left
+// out.  True when the ray certainly reaches the observation level (points
+// down, emitted above it, cannot turn: the vacuum line meets the
+// observation sphere at a zenith cosine above sqrt(2.1 delta_max)) and
+// clear_miss rules out every telescope.  The direction and emission point
+// are those of trace_ray without the low words of the pairs (millimetres
+// at 10 km, inside clear_miss's 5 cm).
+template <bool SPH, bool REFR, bool EXT>
+__device__ __forceinline__ bool skip_ray(const float *S, int l, uint32_t k, uint32_t n_c, int64_t seg_global,
+                                         const DevAtm &A, const DevPar &Pp, const DevTel &Tl, const uint8_t *clr)
+{
+    const uint32_t proc = k < n_c ? 0u : 1u;
+    const uint32_t kk = proc ? k - n_c : k;
+    const uint4 x = philox4x32_10(make_uint4((uint32_t)(uint64_t)seg_global, (uint32_t)((uint64_t)seg_global >> 32),
+                                             kk, proc),
+                                  Pp.seed, Pp.stream);
+    const float u1 = u01<float>(x.y), u2 = u01<float>(x.z), u3 = u01<float>(x.w);
+    const float sdx = S[F_DX * 32 + l], sdy = S[F_DY * 32 + l], sdz = S[F_DZ * 32 + l];
+    float dx, dy, dz;
+    if (proc == 0) {
+        float sc, cc;
+        Num<float>::sincos2pi(u2, &sc, &cc);
+        const float st = S[F_SIN * 32 + l], kap = S[F_KAP * 32 + l];
+        dx = sdx + (-kap * sdx + st * (cc * S[F_E1X * 32 + l] + sc * S[F_E2X * 32 + l]));
+        dy = sdy + (-kap * sdy + st * (cc * S[F_E1Y * 32 + l] + sc * S[F_E2Y * 32 + l]));
+        dz = sdz + (-kap * sdz + st * (cc * S[F_E1Z * 32 + l] + sc * S[F_E2Z * 32 + l]));
+    } else {
+        float sp, cp;
+        Num<float>::sincos2pi(u2, &sp, &cp);
+        const float bomc = EXT ? S[F_BOMC * 32 + l] : 0.0f;
+        if (EXT && bomc > 0.0f) {
+            cone_direction<float>(S[F_BUX * 32 + l], S[F_BUY * 32 + l], S[F_BUZ * 32 + l], u3 * bomc, sp, cp, dx, dy,
+                                  dz);
+        } else {
+            const float cz = 2.0f * u3 - 1.0f;
+            const float sz = Num<float>::sqr((1.0f - cz) * (1.0f + cz));
+            dx = sz * cp; dy = sz * sp; dz = cz;
+        }
+    }
+    if (!(dz < -0.05f)) return false;
+    const float ell = u1 * S[F_L * 32 + l];
+    const float xe = S[F_X0H * 32 + l] + ell * sdx;
+    const float ye = S[F_Y0H * 32 + l] + ell * sdy;
+    const float ze = S[F_Z0H * 32 + l] + ell * sdz;
+    // altitude, cancellation-free (|r| + R_E in the denominator: the
+    // approximate square root moves it by ~1e-7 relative)
+    const float Rz = ze + A.R_E;
+    const float he = SPH ? (xe * xe + ye * ye + ze * (ze + 2.0f * A.R_E)) *
+                               rcp_approx(sqrt_approx(xe * xe + ye * ye + Rz * Rz) + A.R_E)
+                         : ze;
+    if (!(he > A.h_obs + 0.1f)) return false;
+    float cos_obs = 0.0f;
+    if (SPH) {
+        const float c1 = dy * Rz - dz * ye, c2 = dz * xe - dx * Rz, c3 = dx * ye - dy * xe;
+        const float co2 = 1.0f - (c1 * c1 + c2 * c2 + c3 * c3) * (A.inv_r_obs * A.inv_r_obs);
+        if (!(co2 > 2.1f * A.delta_max + 2.6e-3f)) return false;
+        if (!(-(dx * xe + dy * ye + dz * Rz) > 1.0e-3f * Rz)) return false;
+        cos_obs = sqrt_approx(co2);
+    }
+    return clear_miss(xe, ye, ze, dx, dy, dz, he, cos_obs, 1.0f, A, Tl, clr, SPH, REFR);
+}
+
+// DEFER (binary32 pairs, no dispersion): each ray only goes through
+// skip_ray; the rays it cannot leave out are queued in O.defer and traced by
+// k_trace_deferred in full warps, so that no warp integrates for one lane.
+// A ray that finds the queue full sets the kBitDeferFull status bit (the
+// host then runs the call again).  Without the in-place path the kernel
+// fits 4 CTAs of 256 threads per SM.
+template <class P, bool SPH, bool REFR, bool NOALLOC = false, bool SOFT = false, int FEAT = FEAT_ALL,
+          bool DEFER = false>
+__global__ void __launch_bounds__(256, DEFER ? 4 : 3)
 k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid_constant__ DevAtm A,
               const __grid_constant__ DevTel Tl, const __grid_constant__ DevPar Pp, const __grid_constant__ DevOut O)
 {
     constexpr bool EXT = (FEAT & FEAT_EXT) != 0;
-    constexpr int FC = fields_of(EXT);
+    constexpr int FC = fields_of(EXT, DEFER);
     extern __shared__ float smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float *S = smem + warp * (FC * 32);
@@ -79,24 +205,54 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
         clr = reinterpret_cast<const uint8_t *>(dst);
     }
     uint32_t c_rays = 0, c_esc = 0, c_under = 0, c_turn = 0, c_reach = 0, c_hits = 0, c_guard = 0, c_cells = 0;
-    uint32_t c_cut = 0;
+    uint32_t c_cut = 0, c_skip = 0;
     unsigned status_bits = 0;
+    // the deferred first pass (without FEAT_EXT) loads each group's records
+    // while the group before is worked on: the next group is claimed and its
+    // records copied into the warp's stage (behind the map) asynchronously
+    constexpr bool PREF = DEFER && !EXT;
+    float4 *stage = nullptr;
+    unsigned long long grp_next = 0;
+    if (PREF) {
+        stage = reinterpret_cast<float4 *>(reinterpret_cast<char *>(smem) + (blockDim.x >> 5) * (FC * 32) * 4 +
+                                           (Tl.clr ? Tl.clr_bytes : 0) + warp * kStageBytes);
+        if (lane == 0) grp_next = atomicAdd(O.ctr + CTR_WORK, 1ull);
+        grp_next = __shfl_sync(FULL_MASK, grp_next, 0);
+        prefetch_group(stage, segs, n_segs, (int64_t)grp_next * 32, lane);
+    }
     for (;;) {
         unsigned long long grp = 0;
-        if (lane == 0) grp = atomicAdd(O.ctr + CTR_WORK, 1ull);
-        grp = __shfl_sync(FULL_MASK, grp, 0);
+        if (PREF) {
+            grp = grp_next;
+            if (lane == 0) grp_next = atomicAdd(O.ctr + CTR_WORK, 1ull);
+        } else {
+            if (lane == 0) grp = atomicAdd(O.ctr + CTR_WORK, 1ull);
+            grp = __shfl_sync(FULL_MASK, grp, 0);
+        }
         int64_t s_first = (int64_t)grp * 32;
         if (s_first >= n_segs) break;
         int64_t si = s_first + lane;
+        clight_segment s;
+        float4 *sv = reinterpret_cast<float4 *>(&s);
+        if (PREF) {
+            cp_async_wait_all();
+            __syncwarp();
+            if (si < n_segs) {
+                sv[0] = stage[lane * 4]; sv[1] = stage[lane * 4 + 1];
+                sv[2] = stage[lane * 4 + 2]; sv[3] = stage[lane * 4 + 3];
+            }
+            __syncwarp();
+            grp_next = __shfl_sync(FULL_MASK, grp_next, 0);
+            prefetch_group(stage, segs, n_segs, (int64_t)grp_next * 32, lane);
+        } else if (si < n_segs) {
+            const float4 *src = reinterpret_cast<const float4 *>(segs + si);
+            sv[0] = __ldg(src); sv[1] = __ldg(src + 1); sv[2] = __ldg(src + 2); sv[3] = __ldg(src + 3);
+        }
         // ---- per-segment set-up, one segment per lane
         Seg<float, df> g;
         uint32_t nb = 0;
         uint32_t key = 0xFFFFFFE0u | (uint32_t)lane;          // empty lanes sort last
         if (si < n_segs) {
-            clight_segment s;
-            const float4 *src = reinterpret_cast<const float4 *>(segs + si);
-            float4 *dst = reinterpret_cast<float4 *>(&s);
-            dst[0] = __ldg(src); dst[1] = __ldg(src + 1); dst[2] = __ldg(src + 2); dst[3] = __ldg(src + 3);
             load_segment_f<SPH, EXT, (FEAT & FEAT_DISP) != 0>(s, Pp.seg_base + si, A, Pp, g);
             if (g.bad) status_bits |= 1u << g.bad;
             c_guard += g.guarded;
@@ -110,7 +266,8 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
         } else {
             g.n_c = g.n_f = 0;
         }
-        key = warp_sort_u32(key, lane);
+        // (the deferred first pass integrates nothing: its steps keep their order)
+        if (!DEFER) key = warp_sort_u32(key, lane);
         // the segment of source lane (key & 31) takes position `lane`; each
         // source lane learns its position through shared memory
         __syncwarp();
@@ -128,23 +285,24 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
         }
         total = __shfl_sync(FULL_MASK, incl, 31);
         if (si < n_segs) {
-            put_df(S, F_X0H, F_X0L, pos, g.x0);
-            put_df(S, F_Y0H, F_Y0L, pos, g.y0);
-            put_df(S, F_Z0H, F_Z0L, pos, g.z0);
-            put_df(S, F_T0H, F_T0L, pos, g.t0);
-            put_df(S, F_A0H, F_A0L, pos, g.A0);
-            put_df(S, F_C0H, F_C0L, pos, g.C0);
+            S[F_X0H * 32 + pos] = g.x0.hi; S[F_Y0H * 32 + pos] = g.y0.hi; S[F_Z0H * 32 + pos] = g.z0.hi;
             S[F_DX * 32 + pos] = g.dx; S[F_DY * 32 + pos] = g.dy; S[F_DZ * 32 + pos] = g.dz;
-            S[F_LX * 32 + pos] = g.lx; S[F_LY * 32 + pos] = g.ly; S[F_LZ * 32 + pos] = g.lz;
             S[F_E1X * 32 + pos] = g.e1x; S[F_E1Y * 32 + pos] = g.e1y; S[F_E1Z * 32 + pos] = g.e1z;
             S[F_E2X * 32 + pos] = g.e2x; S[F_E2Y * 32 + pos] = g.e2y; S[F_E2Z * 32 + pos] = g.e2z;
-            S[F_SIN * 32 + pos] = g.sin_tc; S[F_KAP * 32 + pos] = g.kappa;
-            S[F_L * 32 + pos] = g.L; S[F_IBC * 32 + pos] = g.inv_bc;
-            S[F_WC * 32 + pos] = g.w_c; S[F_WF * 32 + pos] = g.w_f;
+            S[F_SIN * 32 + pos] = g.sin_tc; S[F_KAP * 32 + pos] = g.kappa; S[F_L * 32 + pos] = g.L;
             S[F_NC * 32 + pos] = __uint_as_float(g.n_c);
             S[F_NF * 32 + pos] = __uint_as_float(g.n_f);
-            S[F_SHOWER * 32 + pos] = __uint_as_float(g.shower);
             S[F_SEGI * 32 + pos] = __uint_as_float((uint32_t)lane);
+            if (!DEFER) {
+                S[F_X0L * 32 + pos] = g.x0.lo; S[F_Y0L * 32 + pos] = g.y0.lo; S[F_Z0L * 32 + pos] = g.z0.lo;
+                put_df(S, F_T0H, F_T0L, pos, g.t0);
+                put_df(S, F_A0H, F_A0L, pos, g.A0);
+                put_df(S, F_C0H, F_C0L, pos, g.C0);
+                S[F_LX * 32 + pos] = g.lx; S[F_LY * 32 + pos] = g.ly; S[F_LZ * 32 + pos] = g.lz;
+                S[F_IBC * 32 + pos] = g.inv_bc;
+                S[F_WC * 32 + pos] = g.w_c; S[F_WF * 32 + pos] = g.w_f;
+                S[F_SHOWER * 32 + pos] = __uint_as_float(g.shower);
+            }
             if (EXT) {
                 S[F_BUX * 32 + pos] = g.bux; S[F_BUY * 32 + pos] = g.buy; S[F_BUZ * 32 + pos] = g.buz;
                 S[F_BOMC * 32 + pos] = g.bomc;
@@ -169,6 +327,28 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
             uint32_t nf_l = __float_as_uint(S[F_NF * 32 + l]);
             uint32_t excl = __float_as_uint(S[F_INCL * 32 + l]) - (nc_l + nf_l);
             uint32_t k = jj - excl;
+            int64_t seg_local = s_first + (int64_t)__float_as_uint(S[F_SEGI * 32 + l]);
+            int64_t seg_global = Pp.seg_base + seg_local;
+            if (DEFER) {
+                bool skip = active && skip_ray<SPH, REFR, EXT>(S, l, k, nc_l, seg_global, A, Pp, Tl, clr);
+                bool push = active && !skip;
+                if (active) { ++c_rays; if (skip) { ++c_reach; ++c_skip; } }
+                unsigned m = __ballot_sync(FULL_MASK, push);
+                if (m) {
+                    unsigned long long base = 0;
+                    if (lane == 0) base = atomicAdd(O.ctr + CTR_DEFER, (unsigned long long)__popc(m));
+                    base = __shfl_sync(FULL_MASK, base, 0);
+                    unsigned long long idx = base + __popc(m & lanemask_lt());
+                    if (push) {
+                        if ((int64_t)idx < O.defer_cap)
+                            O.defer[idx] = ((unsigned long long)seg_local << 32) | (unsigned long long)k;
+                        else
+                            status_bits |= 1u << kBitDeferFull;
+                    }
+                }
+                continue;
+            }
+            const bool act = active;
             Seg<float, df> q;
             q.x0 = get_df(S, F_X0H, F_X0L, l);
             q.y0 = get_df(S, F_Y0H, F_Y0L, l);
@@ -192,8 +372,6 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
             } else {
                 q.bux = q.buy = q.buz = q.bomc = 0.0f;
             }
-            int64_t seg_local = s_first + (int64_t)__float_as_uint(S[F_SEGI * 32 + l]);
-            int64_t seg_global = Pp.seg_base + seg_local;
             int nh = 0;
             if (std::is_same<P, double>::value) {   // binary64 for the precise steps
                 Seg<float, double> qd;
@@ -237,12 +415,13 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
                 }
             } else {
                 RayOut<float, df> o;
-                trace_ray<float, df, true, SPH, REFR, FEAT, true>(q, seg_global, k, active, A, Pp, o, &Tl, clr);
+                trace_ray<float, df, true, SPH, REFR, FEAT, !DEFER>(q, seg_global, k, act, A, Pp, o, &Tl, clr);
                 nh = hit_test<float, df, true, NOALLOC>(o, Pp.key_off + seg_local, seg_global, k, q.shower, A, Tl, Pp, O, status_bits, clr);
-                if (active) {
+                if (act) {
                     ++c_rays;
                     c_esc += o.status == 1; c_under += o.status == 2; c_turn += o.status == 3;
                     c_reach += o.status == 0 || o.status >= 5;
+                    c_skip += o.status == 6;
                     c_cells += o.status == 0 ? o.cells : 0;
                 }
             }
@@ -251,19 +430,63 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
         __syncwarp();
     }
     // ---- statistics: one atomic per warp and counter
-    uint32_t vals[10] = {c_rays, c_esc, c_under, c_turn, c_reach, c_hits, c_guard, 0u, c_cells, c_cut};
-#pragma unroll
-    for (int i = 0; i < 10; ++i) {
-        if (i == ST_STATUS) continue;
-        uint32_t v = vals[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
-        if (lane == 0 && v) atomicAdd(O.ctr + CTR_STATS + i, (unsigned long long)v);
+    const uint32_t vals[ST_N] = {c_rays, c_esc, c_under, c_turn, c_reach, c_hits, c_guard, 0u, c_cells, c_cut, c_skip};
+    flush_stats(vals, status_bits, O, lane);
+}
+
+// Second pass of the deferred path: the queued rays, 32 per warp, each from
+// its step record in global memory (set up again exactly as in the first
+// pass), traced and hit-tested in full.  Ray counts were taken in the first
+// pass.  Persistent grid, each warp taking the next 32 entries from a counter.
+template <bool SPH, bool REFR, int FEAT>
+__global__ void __launch_bounds__(256, 3)
+k_trace_deferred(const clight_segment *__restrict__ segs, const __grid_constant__ DevAtm A,
+                 const __grid_constant__ DevTel Tl, const __grid_constant__ DevPar Pp,
+                 const __grid_constant__ DevOut O)
+{
+    constexpr bool EXT = (FEAT & FEAT_EXT) != 0;
+    extern __shared__ float smem[];
+    const int lane = threadIdx.x & 31;
+    const uint8_t *clr = EXT ? Tl.clr : nullptr;
+    if (!EXT && Tl.clr) {
+        uint4 *dst = reinterpret_cast<uint4 *>(smem);
+        const uint4 *src = reinterpret_cast<const uint4 *>(Tl.clr);
+        for (int i = threadIdx.x; i < (Tl.clr_bytes >> 4); i += blockDim.x) dst[i] = __ldg(src + i);
+        __syncthreads();
+        clr = reinterpret_cast<const uint8_t *>(dst);
     }
-    unsigned sb = status_bits;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sb |= __shfl_xor_sync(FULL_MASK, sb, o);
-    if (lane == 0 && sb) atomicOr(O.ctr + CTR_STATS + ST_STATUS, (unsigned long long)sb);
+    const int64_t n = min((int64_t)O.ctr[CTR_DEFER], O.defer_cap);
+    uint32_t c_esc = 0, c_under = 0, c_turn = 0, c_reach = 0, c_hits = 0, c_cells = 0;
+    unsigned status_bits = 0;
+    for (;;) {
+        unsigned long long grp = 0;
+        if (lane == 0) grp = atomicAdd(O.ctr + CTR_DEFER_WORK, 1ull);
+        const int64_t base = (int64_t)__shfl_sync(FULL_MASK, grp, 0) * 32;
+        if (base >= n) break;
+        const int64_t i = base + lane;
+        const bool active = i < n;
+        const unsigned long long e = O.defer[active ? i : base];
+        const int64_t seg_local = (int64_t)(e >> 32);
+        const uint32_t k = (uint32_t)e;
+        const int64_t seg_global = Pp.seg_base + seg_local;
+        clight_segment s;
+        const float4 *src = reinterpret_cast<const float4 *>(segs + seg_local);
+        float4 *dst = reinterpret_cast<float4 *>(&s);
+        dst[0] = __ldg(src); dst[1] = __ldg(src + 1); dst[2] = __ldg(src + 2); dst[3] = __ldg(src + 3);
+        Seg<float, df> g;
+        load_segment_f<SPH, EXT, false>(s, seg_global, A, Pp, g);
+        RayOut<float, df> o;
+        trace_ray<float, df, true, SPH, REFR, FEAT>(g, seg_global, k, active, A, Pp, o);
+        c_hits += hit_test<float, df, true, false>(o, Pp.key_off + seg_local, seg_global, k, g.shower, A, Tl, Pp, O,
+                                                   status_bits, clr);
+        if (active) {
+            c_esc += o.status == 1; c_under += o.status == 2; c_turn += o.status == 3;
+            c_reach += o.status == 0 || o.status == 5;
+            c_cells += o.status == 0 ? o.cells : 0;
+        }
+    }
+    const uint32_t vals[ST_N] = {0u, c_esc, c_under, c_turn, c_reach, c_hits, 0u, 0u, c_cells, 0u, 0u};
+    flush_stats(vals, status_bits, O, lane);
 }
 
 // ------------------------------------------------------------------ plain FP64
@@ -297,18 +520,51 @@ k_trace_fp64(const clight_segment *__restrict__ segs, int64_t n_segs, const __gr
             c_hits += hit_test<double, double, false>(o, i, seg_global, k, g.shower, A, Tl, Pp, O, status_bits);
         }
     }
-    uint32_t vals[10] = {c_rays, c_esc, c_under, c_turn, c_reach, c_hits, 0u, 0u, c_cells, c_cut};
-    for (int q = 0; q < 10; ++q)
+    uint32_t vals[ST_N] = {c_rays, c_esc, c_under, c_turn, c_reach, c_hits, 0u, 0u, c_cells, c_cut, 0u};
+    for (int q = 0; q < ST_N; ++q)
         if (vals[q] && q != ST_STATUS) atomicAdd(O.ctr + CTR_STATS + q, (unsigned long long)vals[q]);
     if (status_bits) atomicOr(O.ctr + CTR_STATS + ST_STATUS, (unsigned long long)status_bits);
 }
 
 // ------------------------------------------------------------------ launchers
+template <bool SPH, bool REFR, int FEAT>
+static void launch_deferred_pair(const clight_segment *segs, int64_t n_segs, const DevAtm &A, const DevTel &T,
+                                 const DevPar &Pp, const DevOut &O, int grid, int block, cudaStream_t s)
+{
+    constexpr bool EXT = (FEAT & FEAT_EXT) != 0;
+    // the queue's fill and work counters
+    cudaMemsetAsync(O.ctr + CTR_DEFER, 0, 2 * sizeof(unsigned long long), s);
+    k_trace_fused<df, SPH, REFR, false, false, FEAT, true>
+        <<<grid, block, fused_smem_bytes_f(block, T, EXT, true), s>>>(segs, n_segs, A, T, Pp, O);
+    // the second pass as many CTAs as are resident at once (its own
+    // register and shared-memory limits)
+    const int smem2 = !EXT && T.clr ? T.clr_bytes : 0;
+    int dev = 0, n_sm = 1, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_deferred<SPH, REFR, FEAT>, block, smem2);
+    const int grid2 = std::max(1, std::min(grid, n_sm * std::max(per_sm, 1)));
+    k_trace_deferred<SPH, REFR, FEAT><<<grid2, block, smem2, s>>>(segs, A, T, Pp, O);
+}
+
 template <class P, int FEAT>
 static void launch_fused_pe(const clight_segment *segs, int64_t n_segs, const DevAtm &A, const DevTel &T,
                             const DevPar &Pp, const DevOut &O, int grid, int block, cudaStream_t s)
 {
     int smem = fused_smem_bytes_f(block, T, (FEAT & FEAT_EXT) != 0);  // < 48 KB for block <= 256
+    if constexpr (std::is_same<P, df>::value && (FEAT == 0 || FEAT == FEAT_EXT)) {
+        if (O.defer) {
+            if (A.spherical && A.refraction)
+                launch_deferred_pair<true, true, FEAT>(segs, n_segs, A, T, Pp, O, grid, block, s);
+            else if (A.spherical)
+                launch_deferred_pair<true, false, FEAT>(segs, n_segs, A, T, Pp, O, grid, block, s);
+            else if (A.refraction)
+                launch_deferred_pair<false, true, FEAT>(segs, n_segs, A, T, Pp, O, grid, block, s);
+            else
+                launch_deferred_pair<false, false, FEAT>(segs, n_segs, A, T, Pp, O, grid, block, s);
+            return;
+        }
+    }
     if (A.spherical && A.refraction)
         k_trace_fused<P, true, true, false, false, FEAT><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
     else if (A.spherical)
@@ -444,7 +700,7 @@ extern "C" clight_status clight_trace_noalloc(clight_ctx *ctx, const clight_segm
     if (n_segs > 0) {
         DevPar P = v.par;
         P.n_showers = n_showers;
-        DevOut O;
+        DevOut O{};
         O.rec = d_hits;
         O.keys = scr + CTR_N;        // per-group hit counters
         O.vals = nullptr;
@@ -485,6 +741,7 @@ extern "C" clight_status clight_trace_noalloc(clight_ctx *ctx, const clight_segm
         h_stats->status = (int64_t)bits;
         h_stats->cells = (int64_t)h[CTR_STATS + ST_CELLS];
         h_stats->cut = (int64_t)h[CTR_STATS + ST_CUT];
+        h_stats->skipped = (int64_t)h[CTR_STATS + ST_SKIPPED];
     }
     if ((int64_t)h[CTR_CURSOR] > hit_capacity) return CLIGHT_ERR_HIT_CAPACITY;
     if (bits & (1ull << CLIGHT_ERR_BAD_SEGMENT)) return CLIGHT_ERR_BAD_SEGMENT;

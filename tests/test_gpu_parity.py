@@ -103,6 +103,41 @@ def test_shower_spherical_absorbing(ctx):
     w = I.workload_shower_1tev(n=40_000, seed=5)
     rep, gst, rst = _check(ctx, w)
     assert rep["n_common"] > 1000
+    # most rays land provably clear of every telescope and skip the quadrature
+    assert gst["skipped"] > 0.5 * gst["rays"] and gst["cells"] < gst["rays"]
+
+
+@pytest.mark.parametrize("cap", [-1, 1000])
+def test_deferred_queue_off_and_overflowing(ctx, cap):
+    """The queue of rays that may land near a telescope (traced by a second
+    kernel in full warps) changes no result: without it (cap -1, every ray
+    traced in the fused kernel) and with a queue far too small (cap 1000,
+    the overflow traced in place) the hits still match the oracle's."""
+    w = I.workload_shower_1tev(n=40_000, seed=61)
+    rep, gst, rst = _check(ctx, w, defer_cap=cap)
+    assert rep["n_common"] > 1000
+    assert gst["skipped"] > 0.5 * gst["rays"]
+    assert gst["rays"] - gst["skipped"] > 2 * 1000
+
+
+def test_deferred_queue_grows_when_full(ctx):
+    """A dense array (most rays land near a telescope, several queued rays
+    per step) fills the default queue of two entries per step: the call
+    runs again with a larger queue and returns the in-place kernel's hits."""
+    w = I.workload_shower_1tev(n=400_000, seed=71)
+    # 6 m spheres 10 m apart over 800 m x 800 m: about half the rays land on the array
+    w.telescopes = I.telescope_grid(81, 81, 10.0, z=w.atmosphere.h_obs)
+    ctx.setup(w)
+    gh, gc, gs, gst = G.run_workload(ctx, w)
+    ctx.setup(w, defer_cap=-1)
+    rh, rc, rs, rst = G.run_workload(ctx, w)
+    ctx.setup(w)
+    assert gst["rays"] - gst["skipped"] > 1 << 20       # more queued rays than the default 2^20 entries
+    assert gst["rays"] == rst["rays"] and gst["status"] == 0 and len(gh) > 100_000
+    np.testing.assert_array_equal(_parity._key(gh), _parity._key(rh))
+    for f in ("x_rel", "y_rel", "t", "weight"):
+        np.testing.assert_allclose(gh[f], rh[f], rtol=1e-6, atol=1e-5)
+    np.testing.assert_array_equal(np.asarray(gc), np.asarray(rc))
 
 
 def test_inclined_shower_441_telescopes(ctx):
