@@ -371,9 +371,12 @@ def main():
 
     # ---- roofline of the dominant kernel (generation + propagation + hits)
     k_ms = statistics.mean(kms)
-    full = st["rays"] - st["skipped"]
-    ops = full * OPS_RAY + st["skipped"] * OPS_SKIPPED_RAY + st["cells"] * (OPS_CELL + NODES_PER_CELL * OPS_NODE)
-    mufu = full * MUFU_RAY + st["skipped"] * MUFU_SKIPPED_RAY + st["cells"] * NODES_PER_CELL * MUFU_NODE
+    # rays decided without the quadrature and landing: clear of every
+    # telescope, escaping, or emitted below the observation level
+    short = st["skipped"] + st["escaped"] + st["under"]
+    full = st["rays"] - short
+    ops = full * OPS_RAY + short * OPS_SKIPPED_RAY + st["cells"] * (OPS_CELL + NODES_PER_CELL * OPS_NODE)
+    mufu = full * MUFU_RAY + short * MUFU_SKIPPED_RAY + st["cells"] * NODES_PER_CELL * MUFU_NODE
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     peaks = {}
     try:

@@ -275,7 +275,9 @@ clight_status clight_trace_host(clight_ctx *ctx, const clight_segment *h_segs, i
  *   h_grad        n_layers + 2 doubles (host): d loss / d theta
  * Each ray is recomputed from its random-number counter; derivatives are
  * carried as binary32 tangents and summed per block in binary64, then over
- * blocks in a fixed order.  Synchronises `stream` once. */
+ * blocks in a fixed order.  Synchronises `stream` once.  The tangents are
+ * those of the exact propagator without dispersion: with dispersion on or
+ * CLIGHT_PROP_STRAIGHT set it returns CLIGHT_ERR_ARG. */
 clight_status clight_trace_adjoint(clight_ctx *ctx, const clight_segment *d_segs, int64_t n_segs,
                                    int32_t n_showers, const clight_hit *d_hits, int64_t n_hits,
                                    const float *d_gx, const float *d_gy, const float *d_gt,

@@ -926,6 +926,7 @@ extern "C" clight_status clight_trace_adjoint(clight_ctx *c, const clight_segmen
     if (!c || !c->atm_set || !c->tel_set || !h_grad || n_segs < 0 || n_hits < 0 || n_showers < 1)
         return CLIGHT_ERR_ARG;
     if (c->atm.disp) return CLIGHT_ERR_ARG;       // the tangents assume no dispersion
+    if (c->par.prop == CLIGHT_PROP_STRAIGHT) return CLIGHT_ERR_ARG;   // they are those of the exact propagator
     if ((n_segs > 0 && !d_segs) || (n_hits > 0 && !d_hits) || !(soft_s > 0) || !(soft_w >= 0))
         return CLIGHT_ERR_ARG;
     if (n_segs > (int64_t(1) << 31)) return CLIGHT_ERR_LIMIT;

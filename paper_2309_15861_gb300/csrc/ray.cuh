@@ -975,7 +975,7 @@ constexpr int FEAT_EXT = 1, FEAT_STRAIGHT = 2, FEAT_RUNTIME = 4, FEAT_DISP = 8,
 // vacuum crossing, the ray hits nothing.  Returns true for such a ray.
 __device__ __forceinline__ bool clear_miss(float xe, float ye, float ze, float dx, float dy, float dz, float he,
                                            float cos_obs, float gl, const DevAtm &A, const DevTel &Tl,
-                                           const uint8_t *clr, bool sph, bool refr)
+                                           const uint8_t *clr, bool sph, bool refr, float widen = 0.0f)
 {
     const float tp = (ze - A.h_obs) * rcp_approx(-dz);
     const float Xv = xe + tp * dx, Yv = ye + tp * dy;
@@ -989,7 +989,7 @@ __device__ __forceinline__ bool clear_miss(float xe, float ye, float ze, float d
     const float czb = -dz - sd * im - 1.0e-5f;            // below the arrival |cz|
     if (!(czb > 0.05f)) return false;
     const float dzmax = fmaxf(fabsf(Tl.zmax - A.h_obs), fabsf(Tl.zmin - A.h_obs));
-    const float rs = (Tl.Rmax + dzmax * sqrt_approx(1.0f - czb * czb)) * rcp_approx(czb) + 2.0e-3f + B;
+    const float rs = (Tl.Rmax + widen + dzmax * sqrt_approx(1.0f - czb * czb)) * rcp_approx(czb) + 2.0e-3f + B;
     if (Xv + rs < Tl.xmin || Xv - rs > Tl.xmax || Yv + rs < Tl.ymin || Yv - rs > Tl.ymax) return true;
     if (clr) {
         float fx = (Xv - Tl.cx0) * Tl.inv_cgs, fy = (Yv - Tl.cy0) * Tl.inv_cgs;
@@ -1000,11 +1000,13 @@ __device__ __forceinline__ bool clear_miss(float xe, float ye, float ze, float d
 }
 
 // CULL (binary32 only): skip the quadrature for rays clear_miss rejects;
-// they end with status 6 (reached the observation level, no telescope near).
+// they end with status 6 (reached the observation level, no telescope near;
+// `widen` enlarges the telescopes' radius for that test).
 template <class T, class P, bool WARP, bool SPH, bool REFR, int FEAT = FEAT_ALL, bool CULL = false>
 __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global, uint32_t k, bool active,
                                           const DevAtm &A, const DevPar &Pp, RayOut<T, P> &o,
-                                          const DevTel *Tl = nullptr, const uint8_t *clr = nullptr)
+                                          const DevTel *Tl = nullptr, const uint8_t *clr = nullptr,
+                                          float widen = 0.0f)
 {
     // ---- generation (Sec. 1.1, 1.2, 1.2.1; Fig. 1)
     uint32_t proc = k < g.n_c ? 0u : 1u;
@@ -1172,7 +1174,7 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
     bool go = o.status == 0;
     if (CULL && sizeof(T) == 4 && go &&
         clear_miss((float)xef, (float)yef, (float)zef, (float)dx, (float)dy, (float)dz, (float)he,
-                   SPH ? (float)sqf * A.inv_r_obs : 0.0f, (float)gl, A, *Tl, clr, SPH, REFR)) {
+                   SPH ? (float)sqf * A.inv_r_obs : 0.0f, (float)gl, A, *Tl, clr, SPH, REFR, widen)) {
         o.status = 6;
         go = false;
     }

@@ -116,16 +116,18 @@ __device__ __forceinline__ void flush_stats(const uint32_t (&vals)[ST_N], unsign
 }
 
 // First pass of the deferred path: ray k of the step in record l, its
-// direction and emission point in binary32 only, and whether it can be left
-// out.  True when the ray certainly reaches the observation level (points
-// down, emitted above it, cannot turn: the vacuum line meets the
-// observation sphere at a zenith cosine above sqrt(2.1 delta_max)) and
-// clear_miss rules out every telescope.  The direction and emission point
-// are those of trace_ray without the low words of the pairs (millimetres
-// at 10 km, inside clear_miss's 5 cm).
+// direction and emission point in binary32 only, and what the full trace
+// would conclude when that is already certain.  Returns 1 (escapes: points
+// away from the Earth's centre by a wide margin), 2 (emitted below the
+// observation level by more than 10 cm), 6 (reaches the observation level
+// -- points down, emitted above it, cannot turn: the vacuum line meets the
+// observation sphere at a zenith cosine above sqrt(2.1 delta_max) -- and
+// clear_miss rules out every telescope), or 0 (trace it in full).  The
+// direction and emission point are those of trace_ray without the low
+// words of the pairs (millimetres at 10 km, inside the margins).
 template <bool SPH, bool REFR, bool EXT>
-__device__ __forceinline__ bool skip_ray(const float *S, int l, uint32_t k, uint32_t n_c, int64_t seg_global,
-                                         const DevAtm &A, const DevPar &Pp, const DevTel &Tl, const uint8_t *clr)
+__device__ __forceinline__ int skip_ray(const float *S, int l, uint32_t k, uint32_t n_c, int64_t seg_global,
+                                        const DevAtm &A, const DevPar &Pp, const DevTel &Tl, const uint8_t *clr)
 {
     const uint32_t proc = k < n_c ? 0u : 1u;
     const uint32_t kk = proc ? k - n_c : k;
@@ -155,27 +157,31 @@ __device__ __forceinline__ bool skip_ray(const float *S, int l, uint32_t k, uint
             dx = sz * cp; dy = sz * sp; dz = cz;
         }
     }
-    if (!(dz < -0.05f)) return false;
     const float ell = u1 * S[F_L * 32 + l];
     const float xe = S[F_X0H * 32 + l] + ell * sdx;
     const float ye = S[F_Y0H * 32 + l] + ell * sdy;
     const float ze = S[F_Z0H * 32 + l] + ell * sdz;
+    // the outward component (along the Earth radius; flat: d_z) decides escape
+    const float Rz = ze + A.R_E;
+    const float out = SPH ? dx * xe + dy * ye + dz * Rz : dz;
+    const float mo = SPH ? 1.0e-3f * Rz : 1.0e-6f;
+    if (out > mo) return 1;
+    if (!(out < -mo)) return 0;
     // altitude, cancellation-free (|r| + R_E in the denominator: the
     // approximate square root moves it by ~1e-7 relative)
-    const float Rz = ze + A.R_E;
     const float he = SPH ? (xe * xe + ye * ye + ze * (ze + 2.0f * A.R_E)) *
                                rcp_approx(sqrt_approx(xe * xe + ye * ye + Rz * Rz) + A.R_E)
                          : ze;
-    if (!(he > A.h_obs + 0.1f)) return false;
+    if (he < A.h_obs - 0.1f) return 2;
+    if (!(he > A.h_obs + 0.1f) || !(dz < -0.05f)) return 0;
     float cos_obs = 0.0f;
     if (SPH) {
         const float c1 = dy * Rz - dz * ye, c2 = dz * xe - dx * Rz, c3 = dx * ye - dy * xe;
         const float co2 = 1.0f - (c1 * c1 + c2 * c2 + c3 * c3) * (A.inv_r_obs * A.inv_r_obs);
-        if (!(co2 > 2.1f * A.delta_max + 2.6e-3f)) return false;
-        if (!(-(dx * xe + dy * ye + dz * Rz) > 1.0e-3f * Rz)) return false;
+        if (!(co2 > 2.1f * A.delta_max + 2.6e-3f)) return 0;
         cos_obs = sqrt_approx(co2);
     }
-    return clear_miss(xe, ye, ze, dx, dy, dz, he, cos_obs, 1.0f, A, Tl, clr, SPH, REFR);
+    return clear_miss(xe, ye, ze, dx, dy, dz, he, cos_obs, 1.0f, A, Tl, clr, SPH, REFR) ? 6 : 0;
 }
 
 // DEFER (binary32 pairs, no dispersion): each ray only goes through
@@ -330,9 +336,13 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
             int64_t seg_local = s_first + (int64_t)__float_as_uint(S[F_SEGI * 32 + l]);
             int64_t seg_global = Pp.seg_base + seg_local;
             if (DEFER) {
-                bool skip = active && skip_ray<SPH, REFR, EXT>(S, l, k, nc_l, seg_global, A, Pp, Tl, clr);
-                bool push = active && !skip;
-                if (active) { ++c_rays; if (skip) { ++c_reach; ++c_skip; } }
+                const int cls = active ? skip_ray<SPH, REFR, EXT>(S, l, k, nc_l, seg_global, A, Pp, Tl, clr) : -1;
+                const bool push = cls == 0;
+                if (active) {
+                    ++c_rays;
+                    c_esc += cls == 1; c_under += cls == 2;
+                    c_reach += cls == 6; c_skip += cls == 6;
+                }
                 unsigned m = __ballot_sync(FULL_MASK, push);
                 if (m) {
                     unsigned long long base = 0;
@@ -395,8 +405,9 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
             } else if (SOFT) {
                 // candidate pass of the soft-yield adjoint: compact the rays
                 // near a telescope into O.keys
+                // (rays that provably pass farther than R + W from every centre skip the quadrature)
                 RayOut<float, df> o;
-                trace_ray<float, df, true, SPH, REFR, FEAT>(q, seg_global, k, active, A, Pp, o);
+                trace_ray<float, df, true, SPH, REFR, FEAT, true>(q, seg_global, k, active, A, Pp, o, &Tl, clr, O.soft_w);
                 bool cand = active && soft_candidate<float, df>(o, A, Tl, O.soft_w, clr);
                 unsigned m = __ballot_sync(FULL_MASK, cand);
                 if (m) {
@@ -652,18 +663,31 @@ static cudaError_t noalloc_scratch(int device, unsigned long long **out)
     return cudaSuccess;
 }
 
+template <int FEAT>
+static void launch_soft_f(const clight_segment *segs, int64_t n_segs, const DevAtm &A, const DevTel &T,
+                          const DevPar &Pp, const DevOut &O, int grid, int block, cudaStream_t s)
+{
+    const int smem = fused_smem_bytes_f(block, T, (FEAT & FEAT_EXT) != 0);
+    if (A.spherical && A.refraction)
+        k_trace_fused<df, true, true, false, true, FEAT><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
+    else if (A.spherical)
+        k_trace_fused<df, true, false, false, true, FEAT><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
+    else if (A.refraction)
+        k_trace_fused<df, false, true, false, true, FEAT><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
+    else
+        k_trace_fused<df, false, false, false, true, FEAT><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
+}
+
+// The adjoint's candidate pass (exact propagator, no dispersion: the
+// adjoint refuses the others), with the angular cut and beaming compiled in
+// only when on.
 cudaError_t launch_soft_candidates(const clight_segment *segs, int64_t n_segs, const DevAtm &A, const DevTel &T,
                                    const DevPar &Pp, const DevOut &O, int grid, int block, cudaStream_t s)
 {
-    int smem = fused_smem_bytes(block, T);
-    if (A.spherical && A.refraction)
-        k_trace_fused<df, true, true, false, true><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
-    else if (A.spherical)
-        k_trace_fused<df, true, false, false, true><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
-    else if (A.refraction)
-        k_trace_fused<df, false, true, false, true><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
+    if (Pp.cut_mode != CLIGHT_CUT_OFF || Pp.beam || Pp.roulette)
+        launch_soft_f<FEAT_EXT>(segs, n_segs, A, T, Pp, O, grid, block, s);
     else
-        k_trace_fused<df, false, false, false, true><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
+        launch_soft_f<0>(segs, n_segs, A, T, Pp, O, grid, block, s);
     return cudaGetLastError();
 }
 
