@@ -291,8 +291,8 @@ clight_status clight_trace_adjoint(clight_ctx *ctx, const clight_segment *d_segs
  * whose memory budget must not move between events).  The paper has no
  * counterpart; it exists for such callers.
  *
- * It runs the same generation, propagation and hit kernel as clight_trace
- * but keeps no sort keys: the hit records go straight into d_hits in
+ * It runs the in-place form of clight_trace's kernel (every ray traced in
+ * the fused kernel, no deferred-ray queue) and keeps no sort keys: the hit records go straight into d_hits in
  * arbitrary order (not sorted, no photon sums), and d_counts (optional,
  * n_showers * n_tel int64, device) receives the per-(shower, telescope)
  * hit counts.  Its scratch -- counters, ray statistics and one hit counter

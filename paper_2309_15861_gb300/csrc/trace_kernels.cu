@@ -563,7 +563,10 @@ static void launch_fused_pe(const clight_segment *segs, int64_t n_segs, const De
                             const DevPar &Pp, const DevOut &O, int grid, int block, cudaStream_t s)
 {
     int smem = fused_smem_bytes_f(block, T, (FEAT & FEAT_EXT) != 0);  // < 48 KB for block <= 256
-    if constexpr (std::is_same<P, df>::value && (FEAT == 0 || FEAT == FEAT_EXT)) {
+    // the two-pass path for every binary32-pair instance without dispersion
+    // (the straight-line propagator moves a ray by no more than the bound
+    // the first pass uses: its first-order shortfall is that bound's first term)
+    if constexpr (std::is_same<P, df>::value && (FEAT & (FEAT_DISP | FEAT_RUNTIME)) == 0) {
         if (O.defer) {
             if (A.spherical && A.refraction)
                 launch_deferred_pair<true, true, FEAT>(segs, n_segs, A, T, Pp, O, grid, block, s);
