@@ -366,7 +366,8 @@ def main():
     key_bits = (ng - 1).bit_length() + (n - 1).bit_length() + 16
     passes = (key_bits + 7) // 8
     # the fused kernel, plus the deferred-ray kernel on the default path
-    deferred = args.precision == 0 and args.disp_B == 0
+    deferred = args.precision == 0 and not (args.disp_B > 0 and (args.propagator == "straight" or args.fl_beaming
+                                                                  or args.fl_roulette))
     launches_per_step = (2 if deferred else 1) + 5 * passes + 3 + (3 if adj is not None else 0)
 
     # ---- roofline of the dominant kernel (generation + propagation + hits)

@@ -973,20 +973,24 @@ constexpr int FEAT_EXT = 1, FEAT_STRAIGHT = 2, FEAT_RUNTIME = 4, FEAT_DISP = 8,
 // vacuum one.  With a factor 1.25 and 5 cm for binary32 rounding: if no
 // centre lies within that distance plus the hit test's search radius of the
 // vacuum crossing, the ray hits nothing.  Returns true for such a ray.
+// derr > 0: (dx, dy, dz) is known only to within that angle (cos_obs is
+// then already a lower bound); the vacuum crossing moves by up to
+// tp derr (1 + tan) and |d_z| by up to derr.
 __device__ __forceinline__ bool clear_miss(float xe, float ye, float ze, float dx, float dy, float dz, float he,
                                            float cos_obs, float gl, const DevAtm &A, const DevTel &Tl,
-                                           const uint8_t *clr, bool sph, bool refr, float widen = 0.0f)
+                                           const uint8_t *clr, bool sph, bool refr, float widen = 0.0f,
+                                           float derr = 0.0f)
 {
     const float tp = (ze - A.h_obs) * rcp_approx(-dz);
     const float Xv = xe + tp * dx, Yv = ye + tp * dy;
-    float mu = (sph ? fminf(cos_obs, -dz) : -dz) - 1.0e-3f;
+    float mu = (sph ? fminf(cos_obs, -dz - derr) : -dz - derr) - 1.0e-3f;
     if (!(mu > 0.05f)) return false;
     const float s = sqrt_approx(1.0f - mu * mu);           // mu < 0.999
     const float im = rcp_approx(mu);
     const float sd = refr ? 1.25f * s * A.delta_max * gl : 0.0f;
     const float zeta = sph ? (Xv * Xv + Yv * Yv) * A.inv_r_obs : 0.0f;
-    const float B = sd * ((he - A.h_obs) + zeta) * (im * im * im) + 0.05f;
-    const float czb = -dz - sd * im - 1.0e-5f;            // below the arrival |cz|
+    const float B = sd * ((he - A.h_obs) + zeta) * (im * im * im) + 0.05f + 1.05f * derr * tp * (1.0f + im);
+    const float czb = -dz - derr - sd * im - 1.0e-5f;     // below the arrival |cz|
     if (!(czb > 0.05f)) return false;
     const float dzmax = fmaxf(fabsf(Tl.zmax - A.h_obs), fabsf(Tl.zmin - A.h_obs));
     const float rs = (Tl.Rmax + widen + dzmax * sqrt_approx(1.0f - czb * czb)) * rcp_approx(czb) + 2.0e-3f + B;

@@ -20,6 +20,7 @@ enum SegField {
     // what the first pass of the deferred path (skip_ray) and the bunch loop read
     F_X0H, F_Y0H, F_Z0H, F_DX, F_DY, F_DZ, F_E1X, F_E1Y, F_E1Z, F_E2X, F_E2Y, F_E2Z,
     F_SIN, F_KAP, F_L, F_NC, F_NF, F_SEGI, F_INCL,
+    F_DTH, F_GMX,                         // dispersion: cone-angle spread, largest g(lambda) (first pass)
     F_DEFER_END,
     // the rest of what a ray traced in the fused kernel needs
     F_X0L = F_DEFER_END, F_Y0L, F_Z0L, F_T0H, F_T0L, F_A0H, F_A0L, F_C0H, F_C0L, F_LX, F_LY, F_LZ,
@@ -125,7 +126,13 @@ __device__ __forceinline__ void flush_stats(const uint32_t (&vals)[ST_N], unsign
 // clear_miss rules out every telescope), or 0 (trace it in full).  The
 // direction and emission point are those of trace_ray without the low
 // words of the pairs (millimetres at 10 km, inside the margins).
-template <bool SPH, bool REFR, bool EXT>
+//
+// With dispersion (DISP) a Cherenkov photon's cone angle follows its
+// wavelength, drawn by rejection; the first pass takes the cone at the
+// middle of the step's band instead, with derr >= the angle to any
+// photon's true direction (the band's spread), and widens every margin by
+// it; gl is then the band's largest g(lambda).
+template <bool SPH, bool REFR, bool EXT, bool DISP>
 __device__ __forceinline__ int skip_ray(const float *S, int l, uint32_t k, uint32_t n_c, int64_t seg_global,
                                         const DevAtm &A, const DevPar &Pp, const DevTel &Tl, const uint8_t *clr)
 {
@@ -137,6 +144,15 @@ __device__ __forceinline__ int skip_ray(const float *S, int l, uint32_t k, uint3
     const float u1 = u01<float>(x.y), u2 = u01<float>(x.z), u3 = u01<float>(x.w);
     const float sdx = S[F_DX * 32 + l], sdy = S[F_DY * 32 + l], sdz = S[F_DZ * 32 + l];
     float dx, dy, dz;
+    float derr = 0.0f, gl = 1.0f;
+    if (DISP) {
+        if (proc == 0) {
+            derr = S[F_DTH * 32 + l];
+            gl = S[F_GMX * 32 + l];
+        } else {
+            gl = disp_gu<float>(A, rcp_approx(Pp.fl1 + u01<float>(x.x) * Pp.fdl)) * 1.000001f;
+        }
+    }
     if (proc == 0) {
         float sc, cc;
         Num<float>::sincos2pi(u2, &sc, &cc);
@@ -164,7 +180,7 @@ __device__ __forceinline__ int skip_ray(const float *S, int l, uint32_t k, uint3
     // the outward component (along the Earth radius; flat: d_z) decides escape
     const float Rz = ze + A.R_E;
     const float out = SPH ? dx * xe + dy * ye + dz * Rz : dz;
-    const float mo = SPH ? 1.0e-3f * Rz : 1.0e-6f;
+    const float mo = SPH ? (1.0e-3f + derr) * Rz : 1.0e-6f + derr;
     if (out > mo) return 1;
     if (!(out < -mo)) return 0;
     // altitude, cancellation-free (|r| + R_E in the denominator: the
@@ -173,15 +189,19 @@ __device__ __forceinline__ int skip_ray(const float *S, int l, uint32_t k, uint3
                                rcp_approx(sqrt_approx(xe * xe + ye * ye + Rz * Rz) + A.R_E)
                          : ze;
     if (he < A.h_obs - 0.1f) return 2;
-    if (!(he > A.h_obs + 0.1f) || !(dz < -0.05f)) return 0;
+    if (!(he > A.h_obs + 0.1f) || !(dz < -0.05f - derr)) return 0;
     float cos_obs = 0.0f;
     if (SPH) {
+        // zenith sine at the landing point: p_v / r_obs, raised by the
+        // direction's uncertainty (|R| derr / r_obs)
         const float c1 = dy * Rz - dz * ye, c2 = dz * xe - dx * Rz, c3 = dx * ye - dy * xe;
-        const float co2 = 1.0f - (c1 * c1 + c2 * c2 + c3 * c3) * (A.inv_r_obs * A.inv_r_obs);
-        if (!(co2 > 2.1f * A.delta_max + 2.6e-3f)) return 0;
+        float so = sqrt_approx(c1 * c1 + c2 * c2 + c3 * c3) * A.inv_r_obs;
+        if (DISP) so += derr * (1.0f + (he - A.h_obs) * A.inv_r_obs) * 1.001f;
+        const float co2 = 1.0f - so * so;
+        if (!(so < 1.0f) || !(co2 > 2.1f * A.delta_max * gl + 2.6e-3f)) return 0;
         cos_obs = sqrt_approx(co2);
     }
-    return clear_miss(xe, ye, ze, dx, dy, dz, he, cos_obs, 1.0f, A, Tl, clr, SPH, REFR) ? 6 : 0;
+    return clear_miss(xe, ye, ze, dx, dy, dz, he, cos_obs, gl, A, Tl, clr, SPH, REFR, 0.0f, derr) ? 6 : 0;
 }
 
 // DEFER (binary32 pairs, no dispersion): each ray only goes through
@@ -296,6 +316,27 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
             S[F_E1X * 32 + pos] = g.e1x; S[F_E1Y * 32 + pos] = g.e1y; S[F_E1Z * 32 + pos] = g.e1z;
             S[F_E2X * 32 + pos] = g.e2x; S[F_E2Y * 32 + pos] = g.e2y; S[F_E2Z * 32 + pos] = g.e2z;
             S[F_SIN * 32 + pos] = g.sin_tc; S[F_KAP * 32 + pos] = g.kappa; S[F_L * 32 + pos] = g.L;
+            if (DEFER && (FEAT & FEAT_DISP)) {
+                // (db, eps) -> the cone at the middle of the band, the spread
+                // of the cone angle over the band, the band's largest g
+                float ulo, uhi, st = 0.0f, kap = 0.0f, dth = 0.0f, gmx = 1.0f;
+                if (g.n_c > 0 && disp_band<float>(A, Pp, g.sin_tc, g.kappa, ulo, uhi)) {
+                    auto cone = [&](float u, float &s_, float &k_) {
+                        const float g1 = fmaxf(g.sin_tc * disp_gu<float>(A, u) - g.kappa, 0.0f);
+                        const float ib = 1.0f / (1.0f + g1);
+                        s_ = sqrtf(g1 * (2.0f + g1)) * ib;
+                        k_ = g1 * ib;
+                    };
+                    float s_lo, k_lo, s_hi, k_hi;
+                    cone(0.5f * (ulo + uhi), st, kap);
+                    cone(ulo, s_lo, k_lo);
+                    cone(uhi, s_hi, k_hi);
+                    dth = (asinf(fminf(s_hi, 1.0f)) - asinf(s_lo)) * 1.01f + 1.0e-6f;
+                    gmx = disp_gu<float>(A, uhi) * 1.000001f;
+                }
+                S[F_SIN * 32 + pos] = st; S[F_KAP * 32 + pos] = kap;
+                S[F_DTH * 32 + pos] = dth; S[F_GMX * 32 + pos] = gmx;
+            }
             S[F_NC * 32 + pos] = __uint_as_float(g.n_c);
             S[F_NF * 32 + pos] = __uint_as_float(g.n_f);
             S[F_SEGI * 32 + pos] = __uint_as_float((uint32_t)lane);
@@ -336,7 +377,9 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
             int64_t seg_local = s_first + (int64_t)__float_as_uint(S[F_SEGI * 32 + l]);
             int64_t seg_global = Pp.seg_base + seg_local;
             if (DEFER) {
-                const int cls = active ? skip_ray<SPH, REFR, EXT>(S, l, k, nc_l, seg_global, A, Pp, Tl, clr) : -1;
+                const int cls =
+                    active ? skip_ray<SPH, REFR, EXT, (FEAT & FEAT_DISP) != 0>(S, l, k, nc_l, seg_global, A, Pp, Tl, clr)
+                           : -1;
                 const bool push = cls == 0;
                 if (active) {
                     ++c_rays;
@@ -485,7 +528,7 @@ k_trace_deferred(const clight_segment *__restrict__ segs, const __grid_constant_
         float4 *dst = reinterpret_cast<float4 *>(&s);
         dst[0] = __ldg(src); dst[1] = __ldg(src + 1); dst[2] = __ldg(src + 2); dst[3] = __ldg(src + 3);
         Seg<float, df> g;
-        load_segment_f<SPH, EXT, false>(s, seg_global, A, Pp, g);
+        load_segment_f<SPH, EXT, (FEAT & FEAT_DISP) != 0>(s, seg_global, A, Pp, g);
         RayOut<float, df> o;
         trace_ray<float, df, true, SPH, REFR, FEAT>(g, seg_global, k, active, A, Pp, o);
         c_hits += hit_test<float, df, true, false>(o, Pp.key_off + seg_local, seg_global, k, g.shower, A, Tl, Pp, O,
@@ -563,10 +606,11 @@ static void launch_fused_pe(const clight_segment *segs, int64_t n_segs, const De
                             const DevPar &Pp, const DevOut &O, int grid, int block, cudaStream_t s)
 {
     int smem = fused_smem_bytes_f(block, T, (FEAT & FEAT_EXT) != 0);  // < 48 KB for block <= 256
-    // the two-pass path for every binary32-pair instance without dispersion
-    // (the straight-line propagator moves a ray by no more than the bound
-    // the first pass uses: its first-order shortfall is that bound's first term)
-    if constexpr (std::is_same<P, df>::value && (FEAT & (FEAT_DISP | FEAT_RUNTIME)) == 0) {
+    // the two-pass path for every binary32-pair instance with one propagator
+    // compiled in (the straight-line propagator moves a ray by no more than
+    // the bound the first pass uses: its first-order shortfall is that
+    // bound's first term)
+    if constexpr (std::is_same<P, df>::value && (FEAT & FEAT_RUNTIME) == 0) {
         if (O.defer) {
             if (A.spherical && A.refraction)
                 launch_deferred_pair<true, true, FEAT>(segs, n_segs, A, T, Pp, O, grid, block, s);
