@@ -98,3 +98,39 @@ def test_refraction_moves_the_plane_crossing_less_than_the_bound(ai):
     # the bound is not vacuous: it is within a small factor of the worst case
     print("worst fraction of the bound: crossing %.3f, angle %.3f" % (worst_x, worst_a))
     assert worst_x > 0.2 and worst_a > 0.2, (worst_x, worst_a)
+
+
+def test_dispersion_cone_angles_stay_within_the_band_spread():
+    """With dispersion the first pass builds each Cherenkov photon's cone at
+    the middle of its step's band and widens its margins by the band's
+    spread of cone angles, asin(sin theta(u_hi)) - asin(sin theta(u_lo)).
+    That holds because every photon leaves at an angle between the band
+    edges' (n grows with u = 1/lambda): checked on the oracle's photons."""
+    atm = I.atmosphere_layered()
+    atm.disp_B = 20000.0
+    atm.disp_lref = 400.0
+    par = I.Params(bunch=1.0, seed=5)
+    rng = np.random.default_rng(7)
+    checked = 0
+    for i in range(40):
+        s = np.zeros(1, dtype=I.SEG_DTYPE)[0]
+        s["z"] = rng.uniform(3000.0, 15000.0)
+        s["dz"] = -1.0
+        s["L"] = 2.0
+        s["charge"] = -1
+        d0 = O.yield_of(s, atm, I.Params())["delta"]
+        s["eps"] = d0 * rng.uniform(0.2, 1.05)      # some steps with the threshold inside the band
+        y = O.yield_of(s, atm, par, seg_index=i)
+        if y["n_c"] < 1:
+            continue
+        delta, beta = y["delta"], 1.0 - float(s["eps"])
+
+        def theta(lam):
+            return math.acos(min(1.0, 1.0 / (beta * (1.0 + delta * O.disp_g(atm, lam)))))
+        lo, hi = theta(par.lambda2), theta(par.lambda1)       # longest wavelength: smallest angle
+        for k in range(int(y["n_c"])):
+            r, d, te, lam, w, proc = O.photon(s, i, k, atm, par)
+            th = math.acos(min(1.0, -d[2]))
+            assert lo - 1e-12 <= th <= hi + 1e-12, (i, k, lam, th, lo, hi)
+            checked += 1
+    assert checked > 200
