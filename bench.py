@@ -368,7 +368,10 @@ def main():
     # the fused kernel, plus the deferred-ray kernel on the default path
     deferred = args.precision == 0 and not (args.disp_B > 0 and (args.propagator == "straight" or args.fl_beaming
                                                                   or args.fl_roulette))
-    launches_per_step = (2 if deferred else 1) + 5 * passes + 3 + (3 if adj is not None else 0)
+    # a call with the default queue runs in pieces of half the queue's entries
+    piece = min(max(2 * n, 1 << 20), 1 << 28) // 2
+    pieces = -(-n // piece) if deferred else 1
+    launches_per_step = (2 if deferred else 1) * pieces + 5 * passes + 3 + (3 if adj is not None else 0)
 
     # ---- roofline of the dominant kernel (generation + propagation + hits)
     k_ms = statistics.mean(kms)
