@@ -109,3 +109,33 @@ def test_autograd_function_backward_equals_adjoint():
         assert np.all(np.isfinite(direct)) and np.any(direct != 0)
     finally:
         ctx.close()
+
+
+def test_adjoint_refuses_what_its_tangents_do_not_cover():
+    """The tangents are those of the exact propagator without dispersion:
+    with the straight-line propagator or dispersion on, the adjoint returns
+    CLIGHT_ERR_ARG instead of a gradient of another model."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    w = I.workload_shower_1tev(n=2_000, seed=47)
+    ctx = G.Context(0)
+    try:
+        d_segs = torch.from_numpy(w.segments.view(np.uint8).reshape(-1)).cuda()
+        d_hits = torch.zeros(48, dtype=torch.uint8, device="cuda")
+        gY = torch.ones(len(w.telescopes), dtype=torch.float64, device="cuda")
+        ctx.setup(w, propagator=G.PROP_STRAIGHT)
+        with pytest.raises(G.ClightError) as e:
+            ctx.trace_adjoint(d_segs, len(w.segments), 1, d_hits, 0, gY=gY)
+        assert e.value.code == G.ERR_ARG
+        w.atmosphere.disp_B = 20000.0
+        ctx.setup(w)
+        with pytest.raises(G.ClightError) as e:
+            ctx.trace_adjoint(d_segs, len(w.segments), 1, d_hits, 0, gY=gY)
+        assert e.value.code == G.ERR_ARG
+        w.atmosphere.disp_B = 0.0
+        ctx.setup(w)
+        g = ctx.trace_adjoint(d_segs, len(w.segments), 1, d_hits, 0, gY=gY)
+        assert np.all(np.isfinite(g))
+    finally:
+        ctx.close()
