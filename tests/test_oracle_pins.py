@@ -808,3 +808,61 @@ def test_dual_number_gradient_matches_central_differences(case):
         assert abs(g[p] - fd) <= 2e-5 * scale, (p, g[p], fd)
         scale_s = max(abs(fds), 1e-9 * np.abs(gs).max())
         assert abs(gs[p] - fds) <= 1e-4 * scale_s, (p, gs[p], fds)
+
+
+# ---------------------------------------------------------------- the paper's rule of thumb for the cut
+def _cut_rule_workload(n, seed, d_lo, d_hi, R=300.0):
+    """Electron steps at distance D in [d_lo, d_hi] radii from one large
+    telescope sphere (radius R, at the observation level), flying toward it
+    within 0-10 degrees of the direction to its centre."""
+    atm = I.atmosphere_layered()
+    tels = I.telescope_grid(1, 1, 1.0, R=R, z=atm.h_obs)
+    C = np.array([float(tels["x"][0]), float(tels["y"][0]), float(tels["z"][0])])
+    rng = np.random.default_rng(seed)
+    s = np.zeros(n, dtype=I.SEG_DTYPE)
+    for i in range(n):
+        D = rng.uniform(d_lo, d_hi) * R
+        a = math.radians(rng.uniform(0.0, 30.0))
+        ph = rng.uniform(0.0, 2.0 * math.pi)
+        P = C + D * np.array([math.sin(a) * math.cos(ph), math.sin(a) * math.sin(ph), math.cos(a)])
+        u = (C - P) / D
+        # tilt u by 0-10 degrees about a random axis perpendicular to it
+        t = rng.normal(size=3)
+        t -= (t @ u) * u
+        t /= np.linalg.norm(t)
+        b = math.radians(rng.uniform(0.0, 10.0))
+        d = math.cos(b) * u + math.sin(b) * t
+        s[i]["x"], s[i]["y"], s[i]["z"] = P
+        s[i]["dx"], s[i]["dy"], s[i]["dz"] = d
+    s["L"] = 1.0
+    s["eps"] = 1e-5
+    s["charge"] = -1
+    par = I.Params(bunch=5.0, seed=seed)
+    return s, atm, tels, par
+
+
+def test_cut_loses_no_photons_beyond_fifteen_radii_as_the_paper_states():
+    """The paper's rule of thumb for its angular cut (golden fixture
+    tests/golden/angular_cut_rule.json): with a 6 degree cut a telescope more
+    than ~15 radii away loses no photons.  Oracle: per-telescope cut on steps
+    15-25 radii from a 300 m sphere -- same hits as without the cut, though the
+    cut removes a good share of the steps; at 2-3 radii it loses photons."""
+    import json
+    rule = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "angular_cut_rule.json")))
+    s, atm, tels, par = _cut_rule_workload(1500, 3, rule["min_distance_in_radii"], 25.0)
+    cut = dataclasses.replace(par, cut_mode=2, cut_deg=rule["cut_deg"])
+    h0, c0, s0, st0 = O.trace(s, atm, tels, par)
+    h1, c1, s1, st1 = O.trace(s, atm, tels, cut)
+    nc0, _ = O.bunch_counts(s, atm, par, tels)
+    nc1, _ = O.bunch_counts(s, atm, cut, tels)
+    cut_steps = int(np.sum((nc0 > 0) & (nc1 == 0)))
+    assert cut_steps > 0.2 * len(s) and len(h0) > 1000
+    loss = 1.0 - s1.sum() / s0.sum()
+    assert loss == rule["expected_photon_loss"], loss
+    np.testing.assert_array_equal(h1, h0)
+    # the rule is not vacuous: close to the telescope the same cut loses photons
+    s, atm, tels, par = _cut_rule_workload(1500, 4, 2.0, 3.0)
+    cut = dataclasses.replace(par, cut_mode=2, cut_deg=rule["cut_deg"])
+    _, _, s0, _ = O.trace(s, atm, tels, par)
+    _, _, s1, _ = O.trace(s, atm, tels, cut)
+    assert s1.sum() < 0.99 * s0.sum()
