@@ -20,6 +20,8 @@
  *  - Errors are return codes; nothing aborts, throws or faults the GPU to
  *    signal an error.  clight_status_string() names each code.
  *  - A context is used by one host thread and one stream at a time.
+ *  - Every call makes the context's device current while it runs and makes
+ *    the caller's current device current again before it returns.
  *  - Units: metres, nanoseconds, nanometres, g/cm^3, MeV.
  *
  * Limits: at most 8 atmosphere layers, 64 quadrature cells, 2^31 segments
@@ -300,9 +302,12 @@ clight_status clight_trace_adjoint(clight_ctx *ctx, const clight_segment *d_segs
  * on every GPU that loads the library until the process exits).
  *   - n_showers * n_tel above 16384 returns CLIGHT_ERR_LIMIT before any
  *     launch; other errors as clight_trace.
- *   - The first call on a device looks up the array's device address once
- *     (with that device current); make that first call before any stream
- *     capture.
+ *   - The first call with a context looks up the array's device address
+ *     (with the context's device current) and keeps it in the context.
+ *   - The call reads its counters back to the host and synchronises
+ *     `stream`, so it cannot run inside a stream capture: on a capturing
+ *     stream it returns CLIGHT_ERR_ARG before doing anything, and the
+ *     caller's capture is left intact.
  *   - Calls share the one array, which keeps the last call's contents; each
  *     call clears what must start at zero.  Calls that overlap on the GPU
  *     (different streams or threads) race on it: order them.

@@ -209,6 +209,10 @@ class Context:
 
         Returns (status, n_hits, stats dict)."""
         fn = lib().clight_trace_fp64 if fp64 else lib().clight_trace
+        _need(d_segs, int(n_segs) * 64, "d_segs")
+        _need(d_hits, int(capacity) * 48, "d_hits")
+        _need(d_counts, int(n_showers) * self.n_tel * 8, "d_counts")
+        _need(d_sums, int(n_showers) * self.n_tel * 8, "d_sums")
         st = Stats()
         nh = C.c_int64()
         code = fn(self._h, _ptr(d_segs), int(n_segs), int(n_showers), _ptr(d_hits), int(capacity),
@@ -248,6 +252,9 @@ class Context:
         """The path without any allocation: unsorted hits straight into d_hits,
         per-(shower, telescope) hit counts into d_counts.  For callers that
         cannot allocate device memory while they run.  -> (status, n_hits, stats)"""
+        _need(d_segs, int(n_segs) * 64, "d_segs")
+        _need(d_hits, int(capacity) * 48, "d_hits")
+        _need(d_counts, int(n_showers) * self.n_tel * 8, "d_counts")
         st = Stats()
         nh = C.c_int64()
         code = lib().clight_trace_noalloc(self._h, _ptr(d_segs), int(n_segs), int(n_showers), _ptr(d_hits),
@@ -281,6 +288,17 @@ class Context:
             raise ClightError(code, "clight_trace_host")
         n = min(nh.value, capacity)
         return code, hits[:n], counts.reshape(n_showers, self.n_tel), sums.reshape(n_showers, self.n_tel), st.as_dict()
+
+
+def _need(x, nbytes, what):
+    """Refuse a torch buffer smaller than the call would read or write
+    (raw integer pointers cannot be checked and are the caller's risk)."""
+    if x is None or isinstance(x, int) or nbytes <= 0:
+        return
+    if hasattr(x, "numel") and hasattr(x, "element_size"):
+        have = x.numel() * x.element_size()
+        if have < nbytes:
+            raise ValueError(f"{what}: {have} bytes, the call needs {nbytes}")
 
 
 def _ptr(x):

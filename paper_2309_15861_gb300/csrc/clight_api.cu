@@ -100,6 +100,7 @@ struct clight_ctx {
     bool timed = false;
     cudaGraphExec_t gexec = nullptr;
     GraphKey gkey{};
+    void *noalloc_scratch = nullptr;            // device address of the no-allocation scratch array
 };
 
 #define CK(x)                                   \
@@ -150,7 +151,8 @@ clight_status clight_create(clight_ctx **out, int device)
         cudaGetLastError();
         return CLIGHT_ERR_NO_DEVICE;
     }
-    if (cudaSetDevice(device) != cudaSuccess) return CLIGHT_ERR_NO_DEVICE;
+    DeviceGuard dg(device);
+    if (!dg.ok) return CLIGHT_ERR_NO_DEVICE;
     clight_ctx *c = new clight_ctx();
     c->device = device;
     cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device);
@@ -175,7 +177,7 @@ clight_status clight_create(clight_ctx **out, int device)
 void clight_destroy(clight_ctx *c)
 {
     if (!c) return;
-    cudaSetDevice(c->device);
+    DeviceGuard dg(c->device);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     void *dev[] = {c->d_tel, c->d_cell_start, c->d_cell_tel, c->d_clr, c->d_ctr};
     for (void *p : dev)
@@ -410,7 +412,8 @@ clight_status clight_set_telescopes(clight_ctx *c, const clight_telescope *t, in
     int clr_bytes = (int)((clr.size() + 15) / 16 * 16);
     clr.resize(clr_bytes, 0);
 
-    cudaSetDevice(c->device);
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return CLIGHT_ERR_CUDA;
     if (c->d_tel) cudaFree(c->d_tel);
     if (c->d_cell_start) cudaFree(c->d_cell_start);
     if (c->d_cell_tel) cudaFree(c->d_cell_tel);
@@ -546,6 +549,8 @@ bool clight::ctx_view(clight_ctx *c, CtxView *v)
     return true;
 }
 
+void **clight::ctx_noalloc_slot(clight_ctx *c) { return c ? &c->noalloc_scratch : nullptr; }
+
 // ------------------------------------------------------------------ pipeline
 namespace {
 
@@ -580,7 +585,6 @@ clight_status prepare(clight_ctx *c, int64_t n_segs, int32_t n_showers, int64_t 
     c->par.cut_cabs = std::max(c->tel.cabs, (float)(std::fabs(c->par.cut_cx_d) + std::fabs(c->par.cut_cy_d) + std::fabs(c->par.cut_cz_d)));
     c->par.cut_nx = c->tel.nx; c->par.cut_ny = c->tel.ny;
     c->par.cut_gx0 = c->tel.gx0; c->par.cut_gy0 = c->tel.gy0; c->par.cut_inv_gs = c->tel.inv_gs;
-    cudaSetDevice(c->device);
     uint64_t *g = &c->scratch_gen;
     if (c->rec.ensure(cap, g) || c->keys.ensure(cap, g) || c->keys_alt.ensure(cap, g) ||
         c->vals.ensure(cap, g) || c->vals_alt.ensure(cap, g) || c->hist.ensure(256 * pl.tiles, g) ||
@@ -755,6 +759,8 @@ clight_status run(clight_ctx *c, const clight_segment *segs, int64_t n_segs, int
                   bool fp64)
 {
     if (!c || (n_segs > 0 && !segs) || (cap > 0 && !hits) || !n_hits) return CLIGHT_ERR_ARG;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return CLIGHT_ERR_CUDA;
     clight_status r;
     c->defer_off = false;
     do {
@@ -789,7 +795,8 @@ clight_status clight_trace_host(clight_ctx *c, const clight_segment *h_segs, int
 {
     if (!c || (n_segs > 0 && !h_segs) || (cap > 0 && !h_hits) || !h_n_hits || n_showers < 1 || !c->tel_set)
         return CLIGHT_ERR_ARG;
-    cudaSetDevice(c->device);
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return CLIGHT_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
     int64_t ng = (int64_t)n_showers * c->tel.n_tel;
     uint64_t *g = &c->scratch_gen;
@@ -932,7 +939,8 @@ extern "C" clight_status clight_trace_adjoint(clight_ctx *c, const clight_segmen
         return CLIGHT_ERR_ARG;
     if (n_segs > (int64_t(1) << 31)) return CLIGHT_ERR_LIMIT;
     if ((int64_t)n_showers * c->tel.n_tel > (int64_t(1) << 24)) return CLIGHT_ERR_LIMIT;
-    cudaSetDevice(c->device);
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return CLIGHT_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
     int np = adjoint_params(c->atm.n_layers);
     int blocks = c->n_sm * 8;

@@ -135,6 +135,27 @@ static_assert(CTR_STATS + ST_N <= CTR_DEFER, "counter layout");
 // queue filled; the host runs such a call again.
 constexpr int kBitDeferFull = 30;
 
+// Makes a device current for the life of an entry point and gives the
+// caller's current device back when it returns.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            prev = -1;
+            cudaGetLastError();
+        }
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+    DeviceGuard(const DeviceGuard &) = delete;
+    DeviceGuard &operator=(const DeviceGuard &) = delete;
+};
+
 // What the no-allocation entry point reads from a context (clight_api.cu).
 struct CtxView {
     DevAtm atm;
@@ -143,6 +164,9 @@ struct CtxView {
     int device, n_sm, block, ctas_per_sm, precision;
 };
 bool ctx_view(clight_ctx *c, CtxView *v);
+// Per-context slot holding the device address of the no-allocation entry
+// point's static scratch array (looked up on the context's first such call).
+void **ctx_noalloc_slot(clight_ctx *c);
 
 // kernel launchers (trace_kernels.cu)
 cudaError_t launch_trace_fused(const clight_segment *segs, int64_t n_segs, const DevAtm &A,

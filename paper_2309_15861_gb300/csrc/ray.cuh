@@ -1381,7 +1381,10 @@ __device__ __forceinline__ int hit_test(const RayOut<T, P> &o, int64_t seg_local
                         unsigned long long idx = base + __popc(m & lanemask_lt());
                         write_hit_record(O.rec, O.capacity, idx, seg_global, k, (uint32_t)j, xr, yr, cx, cy,
                                          (float)o.lambda, (float)o.weight, tj);
-                        atomicAdd(O.keys + group, 1ull);
+                        // one atomic per group among the lanes hitting together
+                        const unsigned same = __match_any_sync(m, group);
+                        if ((int)(threadIdx.x & 31) == __ffs(same) - 1)
+                            atomicAdd(O.keys + group, (unsigned long long)__popc(same));
                         continue;
                     }
                     unsigned long long key;

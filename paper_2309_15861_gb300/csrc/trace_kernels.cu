@@ -691,22 +691,21 @@ cudaError_t launch_trace_fp64(const clight_segment *segs, int64_t n_segs, const 
 constexpr int kNoallocMaxGroups = 16384;
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[CTR_N + kNoallocMaxGroups];
 
-constexpr int kNoallocMaxDevices = 64;
-static unsigned long long *g_noalloc_ptr[kNoallocMaxDevices];   // device address per device
-
-// The address of the scratch array on the current device.  In host code the
-// array's name is only a stand-in, so the address comes from the runtime,
-// looked up once per device with that device current.
-static cudaError_t noalloc_scratch(int device, unsigned long long **out)
+// The device address of the scratch array on the current device.  In host
+// code the array's name is only a stand-in, so the address comes from the
+// runtime; it is looked up once per context (whose device is current here)
+// and kept in the context, which a device reset invalidates as a whole.
+static cudaError_t noalloc_scratch(clight_ctx *ctx, unsigned long long **out)
 {
-    if (device < 0 || device >= kNoallocMaxDevices) return cudaErrorInvalidDevice;
-    if (!g_noalloc_ptr[device]) {
+    void **slot = ctx_noalloc_slot(ctx);
+    if (!slot) return cudaErrorInvalidValue;
+    if (!*slot) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
-        g_noalloc_ptr[device] = static_cast<unsigned long long *>(p);
+        *slot = p;
     }
-    *out = g_noalloc_ptr[device];
+    *out = static_cast<unsigned long long *>(*slot);
     return cudaSuccess;
 }
 
@@ -761,10 +760,16 @@ extern "C" clight_status clight_trace_noalloc(clight_ctx *ctx, const clight_segm
     if (n_segs > (int64_t(1) << 31)) return CLIGHT_ERR_LIMIT;
     int64_t groups = (int64_t)n_showers * v.tel.n_tel;
     if (groups > kNoallocMaxGroups) return CLIGHT_ERR_LIMIT;     // n_showers x n_tel above 16384
-    if (cudaSetDevice(v.device) != cudaSuccess) return CLIGHT_ERR_CUDA;
-    unsigned long long *scr = nullptr;
-    if (noalloc_scratch(v.device, &scr) != cudaSuccess) return CLIGHT_ERR_CUDA;
+    DeviceGuard dg(v.device);                                    // the caller's device comes back on return
+    if (!dg.ok) return CLIGHT_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
+    // the call reads its counters back and synchronises its stream, which a
+    // stream capture does not allow: refuse one, leaving the capture intact
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return CLIGHT_ERR_CUDA;
+    if (cs != cudaStreamCaptureStatusNone) return CLIGHT_ERR_ARG;
+    unsigned long long *scr = nullptr;
+    if (noalloc_scratch(ctx, &scr) != cudaSuccess) return CLIGHT_ERR_CUDA;
     // counters and group counts left by the previous call start again at zero
     if (cudaMemsetAsync(scr, 0, sizeof(unsigned long long) * (size_t)(CTR_N + groups), s) != cudaSuccess)
         return CLIGHT_ERR_CUDA;
