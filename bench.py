@@ -4,20 +4,27 @@
 Metric: traced photon bunches (rays) per second, batched FP32 path, against
 the plain FP64 GPU path, at oracle tolerance.  One step = one call of the
 whole path (yield, generation, refracted propagation with absorption, hit
-test, sort, per-telescope counts and sums) over the 2e7-step 1 TeV vertical
-gamma shower (5-layer atmosphere, spherical Earth, absorption, bunch size 5,
-10 x 10 telescopes at 100 m).  Inputs are synthetic and seeded; the
-segment array (1.28 GB) is larger than L2, so no flush is needed.
+test, sort, per-telescope counts and sums) over the default workload: 256
+showers (energies log-uniform 10 GeV-10 TeV, 2e4 steps per 10 GeV, 7.92e8
+steps in all, zenith 0-45 deg) with fluorescence (5 photons/MeV), a 5-layer
+spherical absorbing atmosphere and 10 x 10 telescopes at 100 m, in one
+persistent work-stealing launch sequence replayed as a CUDA graph, with the
+bunch size (<= 5), launch shape and work chunk picked by the autotuner.
+Inputs are synthetic and seeded; the step array (50.7 GB) is far larger
+than L2, so no flush is needed.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--workload batch|shower_1tev|inclined|adjoint] [--peaks]
 
-Under torchrun (N > 1) every rank traces its own shower (weak scaling) with
+Under torchrun (N > 1) every rank traces its own batch (weak scaling) with
 no data-path collective; the timed region is bracketed by barriers and the
 maximum over ranks is reported.
 """
 from __future__ import annotations
 
 import argparse
+import dataclasses
+import hashlib
 import json
 import os
 import statistics
@@ -34,25 +41,24 @@ sys.path.insert(0, ROOT)
 METRIC = "traced photons/s, 1 GB300: batched FP32 vs plain FP64 at oracle tolerance"
 UNIT = "rays/s"
 
-# Algorithmic operations per unit of work on the FMA/ALU pipes, counted
-# from the kernel source (trace_kernels.cu, ray.cuh): per quadrature node of
-# the refracted spherical integrand, per altitude cell (node placement and
-# accumulation), per ray traced in full outside the nodes (Philox rounds,
-# cone, emission point, vacuum line and landing point in FP32 pairs, arrival
-# time, absorption, hit search), and per ray that the first pass shows to
-# land clear of every telescope (Philox rounds, cone, emission point and
-# altitude in binary32, the displacement bound and the clearance lookup:
-# skip_ray and clear_miss).  MUFU ops (ex2, rsqrt, rcp, sin, cos) counted apart.
-OPS_NODE = 39
-MUFU_NODE = 5
+# Algorithmic work per unit, as the measurement plan of the path states it
+# (FP32-pipe operations): generation + Philox of a ray; a ray decided from
+# its vacuum line (the line plus one clearance test); a ray traced in full
+# (vacuum line and hit search); one node of the refracted-ray quadrature
+# (3 per altitude cell).
+OPS8D_GEN = 80
+OPS8D_SKIPPED = OPS8D_GEN + 20 + 15
+OPS8D_TRACED = OPS8D_GEN + 135
+OPS8D_NODE = 30
 NODES_PER_CELL = 3
-OPS_CELL = 8
-OPS_RAY = 680
-MUFU_RAY = 12
-OPS_SKIPPED_RAY = 255
-MUFU_SKIPPED_RAY = 7
-FP32_LANES_PER_SM = 128
-MUFU_LANES_PER_SM = 16
+# Operations counted from the kernel source (a second, larger figure: it
+# includes the step set-up, the bunch bookkeeping and the pair arithmetic):
+# per ray decided in the first pass, per ray traced in full outside the
+# quadrature, per altitude cell and per node.
+SRC_OPS_SKIPPED = 255
+SRC_OPS_RAY = 680
+SRC_OPS_CELL = 8
+SRC_OPS_NODE = 39
 
 
 def _env_int(name, default):
@@ -121,11 +127,12 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def recorded_traffic(n_steps):
-    """DRAM bytes of one fused-kernel launch from the recorded ncu capture,
-    scaled by steps, or None when the kernel sources changed since."""
-    import hashlib
-    path = os.path.join(ROOT, "profiles", "k_trace_fused_traffic.txt")
+def recorded_traffic(workload, n_units):
+    """DRAM bytes of one call's tracing kernels from the recorded ncu
+    capture (profiles/<kernel>_<workload>_traffic.txt), scaled by the units
+    of the record, or None when no record exists or a kernel source changed
+    since it was taken."""
+    path = os.path.join(ROOT, "profiles", f"tracing_{workload}_traffic.txt")
     try:
         lines = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
     except OSError:
@@ -141,42 +148,88 @@ def recorded_traffic(n_steps):
                 return None
         else:
             rec[f[0]] = float(f[1])
-    return rec["bytes_per_step"] * n_steps if "bytes_per_step" in rec else None
+    return rec["bytes_per_step"] * n_units if "bytes_per_step" in rec else None
 
 
-def _oracle_rate(w, budget_s, block, seed, threads):
+# ------------------------------------------------------------------ oracle legs
+def _oracle_blocks(w, budget_s, block, seed, threads, keep_hits=False):
+    """The FP64 oracle on contiguous blocks of `block` steps drawn at random
+    from the whole workload, until `budget_s` has passed."""
     import oracle as O
     O.build()
     rng = np.random.default_rng(seed)
     n = len(w.segments)
-    starts = rng.permutation(n // block)
+    starts = rng.permutation(max(1, n // block))
     rays = 0
     t0 = time.perf_counter()
-    blocks = 0
+    done = []
+    hits = []
     for b in starts:
         lo = int(b) * block
-        _, _, _, st = O.trace(w.segments[lo:lo + block], w.atmosphere, w.telescopes, w.params,
+        hi = min(n, lo + block)
+        h, _, _, st = O.trace(w.segments[lo:hi], w.atmosphere, w.telescopes, w.params,
                               n_showers=w.n_showers, seg_base=lo, threads=threads)
         rays += st["rays"]
-        blocks += 1
+        done.append(lo)
+        if keep_hits:
+            hits.append(h)
         if time.perf_counter() - t0 > budget_s:
             break
-    return rays, blocks, time.perf_counter() - t0
+    return rays, done, time.perf_counter() - t0, hits
 
 
-def cpu_baseline(w, budget_s=12.0, block=256, seed=0, single_s=0.0):
-    """The FP64 oracle on contiguous blocks of the same workload (host cores;
+def _block_of(w):
+    # the batch's steps vary widely in cost (isotropic fluorescence): larger
+    # blocks keep every host core busy
+    return 4096 if w.n_showers > 1 else 256
+
+
+def cpu_baseline(w, budget_s=12.0, seed=0, single_s=0.0, keep_hits=False):
+    """The FP64 oracle on random blocks of the same workload (host cores;
     optionally also on one thread)."""
     n = len(w.segments)
-    rays, blocks, dt = _oracle_rate(w, budget_s, block, seed, 0)
+    block = _block_of(w)
+    rays, done, dt, hits = _oracle_blocks(w, budget_s, block, seed, 0, keep_hits)
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     out = {"value": rays / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-           "sample": f"{blocks} random blocks of {block} consecutive steps ({blocks * block} of {n} "
-                     f"steps, {rays} rays) of the same shower, {dt:.1f} s, FP64 oracle with OpenMP"}
+           "sample": f"{len(done)} random blocks of {block} consecutive steps ({len(done) * block} of {n} "
+                     f"steps, {rays} rays) of the same workload, {dt:.1f} s, FP64 oracle with OpenMP"}
     if single_s > 0:
-        r1, b1, d1 = _oracle_rate(w, single_s, block, seed + 1, 1)
-        out["single_thread"] = {"value": r1 / d1, "unit": UNIT, "sample": f"{b1} blocks, {r1} rays, {d1:.1f} s"}
-    return out
+        r1, d1, t1, _ = _oracle_blocks(w, single_s, block, seed + 1, 1)
+        out["single_thread"] = {"value": r1 / t1, "unit": UNIT, "sample": f"{len(d1)} blocks, {r1} rays, {t1:.1f} s"}
+    return out, done, block, hits
+
+
+def oracle_error(gpu_hits, blocks, block, ref_hits, tels):
+    """Per-output errors of the GPU hits against the oracle's on the blocks
+    the CPU baseline traced: max |dx|, |dy| (m), |dt| (ns), relative weight
+    and wavelength, direction cosines; hits present on one side only."""
+    if not blocks:
+        return None
+    ref = np.concatenate(ref_hits) if ref_hits else np.zeros(0, dtype=gpu_hits.dtype)
+    sel = np.isin(gpu_hits["seg"] // block, np.asarray(blocks, dtype=np.int64) // block)
+    g = gpu_hits[sel]
+
+    def key(h):
+        return (h["seg"].astype(np.int64) * (1 << 20) + h["k"].astype(np.int64)) * 65536 + h["tel"].astype(np.int64)
+    kg, kr = key(g), key(ref)
+    common, ig, ir = np.intersect1d(kg, kr, return_indices=True)
+    a, b = g[ig], ref[ir]
+    R = tels["R"].astype(np.float64)
+    only_ref = np.setdiff1d(np.arange(len(ref)), ir)
+    edge = np.abs(ref["dperp"][only_ref] - R[ref["tel"][only_ref]]) < 0.01 if len(only_ref) else np.zeros(0, bool)
+
+    def mx(v):
+        return float(np.max(v)) if len(v) else 0.0
+    return {"steps": int(len(blocks) * block), "hits_compared": int(len(common)),
+            "only_oracle": int(len(only_ref)), "only_oracle_at_edge": int(edge.sum()),
+            "only_gpu": int(len(g) - len(common)),
+            "max_x_m": mx(np.abs(a["x_rel"] - b["x_rel"])), "max_y_m": mx(np.abs(a["y_rel"] - b["y_rel"])),
+            "max_t_ns": mx(np.abs(a["t"] - b["t"])),
+            "max_weight_rel": mx(np.abs(a["weight"] / b["weight"] - 1.0)),
+            "max_lambda_rel": mx(np.abs(a["lambda"] / b["lambda"] - 1.0)),
+            "max_dir": mx(np.maximum(np.abs(a["cx"] - b["cx"]), np.abs(a["cy"] - b["cy"]))),
+            "bars": {"x_m": 0.01, "y_m": 0.01, "t_ns": 0.01}}
 
 
 def reference_arm(args, rank):
@@ -187,15 +240,15 @@ def reference_arm(args, rank):
     per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
     vals = []
     for i in range(args.warmup + args.steps):
-        r = cpu_baseline(w, budget_s=per_step, seed=i)
+        r, _, _, _ = cpu_baseline(w, budget_s=per_step, seed=i)
         if i >= args.warmup:
             vals.append(r)
     v = statistics.median([r["value"] for r in vals])
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "segments": len(w.segments), "telescopes": len(w.telescopes),
-                       "bunch": w.params.bunch},
+            "config": {"workload": w.name, "segments": len(w.segments), "showers": w.n_showers,
+                       "telescopes": len(w.telescopes), "bunch": w.params.bunch},
             "cpu_baseline": {"kind": "oracle", "cores": vals[0]["cores"], "sample": vals[0]["sample"],
                              "value": v, "unit": UNIT},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -203,7 +256,7 @@ def reference_arm(args, rank):
     return 0
 
 
-WORKLOADS = ("shower_1tev", "inclined", "batch", "adjoint")
+WORKLOADS = ("batch", "shower_1tev", "inclined", "adjoint")
 
 
 def make_workload(name, n_segs, rank, scale):
@@ -218,22 +271,57 @@ def make_workload(name, n_segs, rank, scale):
     return I.workload_shower_1tev(n=n_segs or 20_000_000, seed=1 + rank, workers=wk)
 
 
+def strided_sample(torch, segs_u8, n, m, blocks=64):
+    """m steps (a multiple of 32 per block) in `blocks` blocks spread evenly over
+    the n steps of a device step array: every shower of a batch contributes in
+    proportion to its size."""
+    if m >= n:
+        return segs_u8, n
+    b = max(32, (m // blocks) // 32 * 32)
+    nb = min(blocks, max(1, n // b))
+    v = segs_u8.view(n, 64)
+    parts = [v[(i * (n - b)) // max(1, nb - 1):(i * (n - b)) // max(1, nb - 1) + b] for i in range(nb)]
+    return torch.cat(parts).reshape(-1), nb * b
+
+
+def timed_calls(torch, ctx, segs, n, ns, hits, cap, counts, sums, k, warm=1, fp64=False):
+    """Median of k timed calls (CUDA events on the current stream) after `warm` calls."""
+    s = torch.cuda.current_stream()
+    st = None
+    for _ in range(warm):
+        _, _, st = ctx.trace(segs, n, ns, hits, cap, counts, sums, fp64=fp64)
+    ts = []
+    for _ in range(k):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        _, _, st = ctx.trace(segs, n, ns, hits, cap, counts, sums, fp64=fp64)
+        e1.record(s)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts), st
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="shower_1tev", choices=WORKLOADS,
-                    help="shower_1tev: 2e7-step vertical 1 TeV shower (the default); inclined: 1e8 steps at "
-                         "60 deg over 441 telescopes; batch: 256 showers with fluorescence (7.4e8 steps, "
-                         "autotuned); adjoint: 1e6 steps, forward + adjoint per step")
+    ap.add_argument("--workload", default="batch", choices=WORKLOADS,
+                    help="batch: 256 showers with fluorescence, 7.92e8 steps, autotuned (the default); "
+                         "shower_1tev: one 2e7-step vertical 1 TeV shower; inclined: 1e8 steps at 60 deg over "
+                         "441 telescopes; adjoint: 1e6 steps, forward + adjoint per step")
     ap.add_argument("--n-segs", type=int, default=0)
     ap.add_argument("--scale", type=float, default=1.0, help="segment-count scale of the batch workload")
+    ap.add_argument("--peaks", action="store_true", help="only measure the pipe throughputs and print them")
+    ap.add_argument("--no-peaks", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-guard", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true")
+    ap.add_argument("--tune-sample", type=int, default=40_000_000)
     ap.add_argument("--propagator", default="exact", choices=["exact", "straight"],
                     help="exact: the refracted ray's deviation integrated (default); straight: the vacuum "
                          "line with first-order refraction corrections (Sec. 2's method, approximate)")
@@ -252,6 +340,7 @@ def main():
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--cell-width", type=float, default=0.0)
+    ap.add_argument("--work-chunk", type=int, default=0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = _env_int("RANK", 0)
@@ -265,6 +354,9 @@ def main():
     from paper_2309_15861_gb300 import build as B, inputs as I
     B.build()
     torch.cuda.set_device(local)
+    if args.peaks:
+        print(json.dumps({"pipe_rates": G.pipe_rates(local)}), flush=True)
+        return 0
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -282,16 +374,15 @@ def main():
         w.atmosphere.disp_B = args.disp_B
         w.atmosphere.disp_lref = 400.0
     if args.fl_beaming:
-        import dataclasses
         c, r = I.beam_cone(w.telescopes)
         w.params = dataclasses.replace(w.params, fl_beaming=1, beam_centre=c, beam_radius=r)
     if args.fl_roulette:
-        import dataclasses
         w.params = dataclasses.replace(w.params, fl_roulette=1)
     ns = w.n_showers
     ctx = G.Context(local)
     extra = dict(use_graph=1, precision=args.precision, block=args.block, ctas_per_sm=args.ctas_per_sm,
-                 cell_width=args.cell_width, propagator=1 if args.propagator == "straight" else 0)
+                 cell_width=args.cell_width, work_chunk=args.work_chunk,
+                 propagator=1 if args.propagator == "straight" else 0)
     ctx.setup(w, **extra)
     dev = f"cuda:{local}"
     segs = torch.from_numpy(w.segments.view(np.uint8).reshape(-1)).to(dev)
@@ -302,12 +393,17 @@ def main():
     counts = torch.zeros(ng, dtype=torch.int64, device=dev)
     sums = torch.zeros(ng, dtype=torch.float64, device=dev)
 
+    # measured pipe throughputs (the roofline's denominators)
+    pipes = None
+    if not args.no_peaks:
+        pipes = G.pipe_rates(local)
+
     tune = None
     if args.workload == "batch" and not args.no_tune:
-        # a sample of the batch (every shower's share) picks block, CTAs, cell width and bunch <= 5
-        n_sample = min(n, 4_000_000)
-        tune = ctx.autotune(segs, n_sample, ns, hits, cap, bunch_max=w.params.bunch, reps=3)
-        extra.update(block=tune["block"], ctas_per_sm=tune["ctas_per_sm"], cell_width=tune["cell_width"])
+        # a sample spread over every shower picks bunch (<= 5), launch shape, work chunk, cell width
+        tune = ctx.autotune(segs, n, min(n, args.tune_sample), ns, hits, cap, bunch_max=w.params.bunch, reps=5)
+        extra.update(block=tune["block"], ctas_per_sm=tune["ctas_per_sm"], cell_width=tune["cell_width"],
+                     work_chunk=tune["work_chunk"])
         w.params.bunch = tune["bunch"]
         ctx.set_params(w.params, **extra)
 
@@ -325,15 +421,22 @@ def main():
         gt = torch.randn(nh, generator=gen, device=dev)
         gY = torch.randn(ng, generator=gen, device=dev, dtype=torch.float64)
         adj = dict(gx=gx, gy=gy, gt=gt, gY=gY)
+    adj_ms = []
 
     def step():
         out = ctx.trace(segs, n, ns, hits, cap, counts, sums)
         if adj is not None:
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(torch.cuda.current_stream())
             ctx.trace_adjoint(segs, n, ns, hits, out[1], **adj)
+            a1.record(torch.cuda.current_stream())
+            a1.synchronize()
+            adj_ms.append(a0.elapsed_time(a1))
         return out
 
     for _ in range(args.warmup):
         step()
+    adj_ms.clear()
     # ---- timed region (device-resident inputs)
     clocks = Clocks(local)
     barrier()
@@ -365,81 +468,109 @@ def main():
     value = rays_all * args.steps / (ms / 1e3)
     key_bits = (ng - 1).bit_length() + (n - 1).bit_length() + 16
     passes = (key_bits + 7) // 8
-    # the fused kernel, plus the deferred-ray kernel on the default path
-    deferred = args.precision == 0 and not (args.disp_B > 0 and (args.propagator == "straight" or args.fl_beaming
-                                                                  or args.fl_roulette))
+    deferred = st["deferred"] > 0 or (args.precision == 0 and args.disp_B == 0)
     # a call with the default queue runs in pieces of half the queue's entries
     piece = min(max(2 * n, 1 << 20), 1 << 28) // 2
     pieces = -(-n // piece) if deferred else 1
     launches_per_step = (2 if deferred else 1) * pieces + 5 * passes + 3 + (3 if adj is not None else 0)
 
-    # ---- roofline of the dominant kernel (generation + propagation + hits)
+    # ---- roofline of the dominant kernels (generation + propagation + hits)
     k_ms = statistics.mean(kms)
-    # rays decided without the quadrature and landing: clear of every
-    # telescope, escaping, or emitted below the observation level
-    short = st["skipped"] + st["escaped"] + st["under"]
-    full = st["rays"] - short
-    ops = full * OPS_RAY + short * OPS_SKIPPED_RAY + st["cells"] * (OPS_CELL + NODES_PER_CELL * OPS_NODE)
-    mufu = full * MUFU_RAY + short * MUFU_SKIPPED_RAY + st["cells"] * NODES_PER_CELL * MUFU_NODE
+    k_s = k_ms / 1e3
+    skipped = st["skipped"]
+    decided = st["rays"] - skipped
+    nodes = st["cells"] * NODES_PER_CELL
+    ops8 = skipped * OPS8D_SKIPPED + decided * OPS8D_TRACED + nodes * OPS8D_NODE
+    # rays the first pass decided (two-pass path) or the in-place kernel skipped
+    short = st["rays"] - st["deferred"] if st["deferred"] else skipped + st["escaped"] + st["under"]
+    ops_src = (short * SRC_OPS_SKIPPED + (st["rays"] - short) * SRC_OPS_RAY +
+               st["cells"] * (SRC_OPS_CELL + NODES_PER_CELL * SRC_OPS_NODE))
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    peak_ops = n_sm * FP32_LANES_PER_SM * f_max
-    achieved = ops / (k_ms / 1e3)
-    traffic = recorded_traffic(n) if args.workload == "shower_1tev" else None
-    roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s (FP32 pipe)",
-            "frac": achieved / peak_ops, "traffic": traffic,
-            "traffic_note": "DRAM bytes per launch: ncu capture of 2e6 steps scaled by steps "
-                            "(profiles/k_trace_fused_traffic.txt); null if the kernel changed since",
-            "kernel": "k_trace_fused + k_trace_deferred" if deferred else "k_trace_fused", "kernel_ms": k_ms, "sort_ms": statistics.mean(sms),
-            "mufu_frac": (mufu / (k_ms / 1e3)) / (n_sm * MUFU_LANES_PER_SM * f_max),
-            "ops_per_ray": ops / max(1, st["rays"]), "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
-                                                                 f"{f_max / 1e6:.0f} MHz (max SM clock)"}
+    if pipes is not None and pipes["ffma_per_s"] > 0:
+        # the measured FP32-FMA rate, scaled from the probe's clock to the
+        # median SM clock sampled during the timed region
+        f_run = (ck or {}).get("sm_mhz") or pipes["ffma_mhz"]
+        peak = pipes["ffma_per_s"] * f_run / pipes["ffma_mhz"]
+        peak_basis = (f"measured: FP32 FMA probe {pipes['ffma_per_s'] / 1e12:.2f} Tops/s at "
+                      f"{pipes['ffma_mhz']:.0f} MHz ({pipes['ffma_per_s'] / (n_sm * pipes['ffma_mhz'] * 1e6):.1f} "
+                      f"per SM per clock), scaled to {f_run:.0f} MHz")
+    else:
+        peak = n_sm * 128 * 2070e6
+        peak_basis = f"nominal: {n_sm} SMs x 128 FP32 lanes x 2070 MHz"
+    traffic = recorded_traffic(w.name, n) if args.precision == 0 else None
+    roof = {"bound": "alu", "achieved": ops8 / k_s / 1e12, "peak": peak / 1e12, "unit": "Tops/s (FP32 pipe)",
+            "frac": ops8 / k_s / peak, "traffic": traffic,
+            "kernel": "k_classify + k_trace_deferred" if deferred else "k_trace_fused",
+            "kernel_ms": k_ms, "sort_ms": statistics.mean(sms),
+            "work": f"per-unit work of the measurement plan: {OPS8D_SKIPPED} ops per ray decided from its vacuum "
+                    f"line ({skipped}), {OPS8D_TRACED} per other ray ({decided}), {OPS8D_NODE} per quadrature "
+                    f"node ({nodes}); {ops8 / max(1, st['rays']):.1f} ops per ray",
+            "peak_basis": peak_basis,
+            "source_counted": {"achieved": ops_src / k_s / 1e12, "frac": ops_src / k_s / peak,
+                               "ops_per_ray": ops_src / max(1, st["rays"])},
+            "hbm": {"achieved_gbs": (n * 64 + nh * 48) / k_s / 1e9,
+                    "note": "algorithmic bytes: the 64-byte steps read once and the 48-byte hits written"}}
+    if pipes is not None and pipes["mufu_ex2_per_s"] > 0:
+        roof["pipes_measured"] = {k: pipes[k] for k in ("ffma_per_s", "mufu_ex2_per_s", "dfma_per_s", "imad_per_s",
+                                                        "lop3_per_s", "ffma_mhz")}
+
+    # ---- the adjoint's own kernels
+    adjoint = None
+    if adj is not None and adj_ms:
+        adjoint = {"ms_per_step": statistics.mean(adj_ms), "hits": nh,
+                   "note": "candidate pass + tangent kernels + fixed-order sum, CUDA events"}
 
     # ---- angular segment cut: the same step with the cut on
     cut = None
     if args.cut_study:
-        import dataclasses
         base_sum, base_hits = float(sums.sum().item()), nh
         cut = []
         for mode in (1, 2):
             p2 = dataclasses.replace(w.params, cut_mode=mode, cut_deg=6.0, cut_centre=I.array_centre(w.telescopes))
             ctx.set_params(p2, **extra)
-            for _ in range(3):
-                ctx.trace(segs, n, ns, hits, cap, counts, sums)
-            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             kc = max(5, args.steps // 4)
-            c0.record(s)
-            for _ in range(kc):
-                code, nh_c, st_c = ctx.trace(segs, n, ns, hits, cap, counts, sums)
-            c1.record(s)
-            torch.cuda.synchronize()
-            cms = c0.elapsed_time(c1) / kc
+            cms, st_c = timed_calls(torch, ctx, segs, n, ns, hits, cap, counts, sums, kc, warm=3)
             cut.append({"mode": ["", "array centre", "each telescope"][mode], "deg": 6.0,
                         "segments_cut": int(st_c["cut"]), "rays": int(st_c["rays"]), "ms_per_step": cms,
-                        "speedup": ms_step / cms, "hits_kept": nh_c / max(1, base_hits),
+                        "speedup": ms_step / cms, "hits_kept": st_c["hits"] / max(1, base_hits),
                         "photon_loss": 1.0 - float(sums.sum().item()) / base_sum if base_sum else None})
         ctx.set_params(w.params, **extra)
 
-    # ---- plain FP64 GPU path on the same workload (at most its first 2e7 steps)
+    # the GPU's hits of the timed call, for the comparison with the oracle
+    gpu_hits = hits[: nh * 48].cpu().numpy().view(G.HIT_DTYPE).copy() if rank == 0 and not args.no_cpu else None
+
+    # ---- plain FP64 GPU path, and the FP32 path on the same steps with and
+    # without the skip of rays that provably land clear of every telescope
     fp64 = None
     if not args.no_fp64:
-        n64 = min(n, 20_000_000)
-        ctx.trace(segs, n64, ns, hits, cap, counts, sums, fp64=True)
-        torch.cuda.synchronize()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record(s)
-        code, nh64, st64 = ctx.trace(segs, n64, ns, hits, cap, counts, sums, fp64=True)
-        f1.record(s)
-        torch.cuda.synchronize()
-        fms = f0.elapsed_time(f1)
-        v64 = st64["rays"] / (fms / 1e3)
-        fp64 = {"value": v64, "unit": UNIT, "ms_per_step": fms, "segments": n64,
-                "speedup_of_fp32": value / v64 if v64 else None}
+        sub, n64 = strided_sample(torch, segs, n, 20_000_000)
+        f64_ms, st64 = timed_calls(torch, ctx, sub, n64, ns, hits, cap, counts, sums, 1, warm=1, fp64=True)
+        v64 = st64["rays"] / (f64_ms / 1e3)
+        ctx.set_params(w.params, **{**extra, "use_graph": 0, "trace_all": 1})
+        all_ms, st_all = timed_calls(torch, ctx, sub, n64, ns, hits, cap, counts, sums, 3, warm=1)
+        ctx.set_params(w.params, **{**extra, "use_graph": 0})
+        d_ms, st_d = timed_calls(torch, ctx, sub, n64, ns, hits, cap, counts, sums, 3, warm=1)
+        ctx.set_params(w.params, **extra)
+        v_all = st_all["rays"] / (all_ms / 1e3)
+        v_d = st_d["rays"] / (d_ms / 1e3)
+        fp64 = {"value": v64, "unit": UNIT, "ms_per_step": f64_ms, "segments": n64,
+                "sample": f"{n64} steps in 64 blocks spread over the workload",
+                "speedup_of_fp32": value / v64 if v64 else None,
+                "fp32_same_steps": {"value": v_d, "ms_per_step": d_ms, "speedup": v_d / v64},
+                "fp32_trace_all_same_steps": {"value": v_all, "ms_per_step": all_ms, "speedup": v_all / v64,
+                                              "note": "every ray traced in full: the same algorithm as the "
+                                                      "FP64 path, so this ratio is the precision's share"},
+                "split": {"precision": v_all / v64, "algorithm": v_d / v_all}}
+
+    # ---- FP64 at the precise steps (the literal precision pattern), same workload
+    guard = None
+    if not args.no_guard and args.precision == 0:
+        ctx.set_params(w.params, **{**extra, "precision": 1, "use_graph": 0})
+        g_ms, st_g = timed_calls(torch, ctx, segs, n, ns, hits, cap, counts, sums, 2, warm=1)
+        ctx.set_params(w.params, **extra)
+        guard = {"value": st_g["rays"] / (g_ms / 1e3), "unit": UNIT, "ms_per_step": g_ms,
+                 "note": "binary64 at the altitude-from-position and horizontal-distance steps instead of FP32 "
+                         "pairs (in-place kernel); same hits within tolerance"}
 
     # ---- end to end through the host-buffer entry point
     e2e = None
@@ -471,9 +602,25 @@ def main():
         ctx.set_params(w.params, **extra)
         del pinned, hbuf
 
-    cpu = None
+    # ---- the 2e7-step 1 TeV shower as a secondary figure
+    secondary = None
+    if args.workload == "batch" and not args.no_secondary:
+        w1 = make_workload("shower_1tev", 0, rank, 1.0)
+        ctx.setup(w1, use_graph=1)
+        s1 = torch.from_numpy(w1.segments.view(np.uint8).reshape(-1)).to(dev)
+        n1 = len(w1.segments)
+        c1 = torch.zeros(len(w1.telescopes), dtype=torch.int64, device=dev)
+        u1 = torch.zeros(len(w1.telescopes), dtype=torch.float64, device=dev)
+        ms1, st1 = timed_calls(torch, ctx, s1, n1, 1, hits, cap, c1, u1, 10, warm=3)
+        k1, _ = ctx.last_timing()
+        secondary = {"workload": w1.name, "value": st1["rays"] / (ms1 / 1e3), "unit": UNIT, "ms_per_step": ms1,
+                     "kernel_ms": k1, "rays": st1["rays"], "skipped": st1["skipped"], "deferred": st1["deferred"]}
+        del s1
+
+    cpu = err = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(w, single_s=4.0)
+        cpu, blocks, blk, ref_hits = cpu_baseline(w, single_s=4.0, keep_hits=True)
+        err = oracle_error(gpu_hits, blocks, blk, ref_hits, w.telescopes)
 
     if rank == 0:
         atm = "5-layer, spherical, absorbing"
@@ -488,15 +635,20 @@ def main():
                        "l2": f"inputs ({n * 64 / 1e9:.2f} GB) larger than L2; no flush",
                        "parallelism": f"replicas x{world}", "generation_s": round(t_gen, 1),
                        "fl_beaming": bool(args.fl_beaming), "fl_roulette": bool(args.fl_roulette),
-                       "propagator": args.propagator,
-                       "dispersion_B_nm2": args.disp_B,
+                       "propagator": args.propagator, "dispersion_B_nm2": args.disp_B,
                        "step": "trace + adjoint" if adj is not None else "trace"},
-            "roofline": roof, "fp64_plain": fp64, "e2e": e2e, "cpu_baseline": cpu,
-            "clocks": ck, "gpu_launches": launches_per_step * args.steps,
+            "rays_fully_traced_per_s": st["deferred"] * args.steps / (ms / 1e3),
+            "skip_fraction": st["skipped"] / max(1, st["rays"]),
+            "roofline": roof, "fp64_plain": fp64, "fp64_guard": guard, "e2e": e2e, "cpu_baseline": cpu,
+            "oracle_error": err, "clocks": ck, "gpu_launches": launches_per_step * args.steps,
             "stats": {k: int(v) for k, v in st.items()},
         }
         if tune is not None:
             line["autotune"] = tune
+        if secondary is not None:
+            line["secondary"] = secondary
+        if adjoint is not None:
+            line["adjoint"] = adjoint
         if cut is not None:
             line["angular_cut"] = cut
         print(json.dumps(line), flush=True)

@@ -164,6 +164,14 @@ typedef struct {
      * every case.  Without device memory for the queue the call runs
      * without it. */
     int64_t defer_cap;
+    /* 1 = every ray traced in full in the fused kernel: no first pass and no
+     * skip of the rays that provably land clear of every telescope -- the
+     * same algorithm as clight_trace_fp64, for measurements.  The hits are
+     * the same.  0 = default. */
+    int32_t trace_all;
+    /* Work stealing of the two-pass path's first kernel: a warp claims
+     * work_chunk groups of 32 steps per atomic (0 = 1; at most 64). */
+    int32_t work_chunk;
 } clight_params;
 
 enum {
@@ -196,6 +204,8 @@ typedef struct {
     int64_t cut;        /* steps whose Cherenkov light the angular cut removed */
     int64_t skipped;    /* arrived rays that provably land clear of every telescope,
                            decided from their vacuum line (no quadrature, no landing) */
+    int64_t deferred;   /* rays the second pass of the two-pass path traced in full
+                           (0 for a call traced in place) */
 } clight_stats;
 
 typedef struct clight_ctx clight_ctx;
@@ -277,9 +287,16 @@ clight_status clight_trace_host(clight_ctx *ctx, const clight_segment *h_segs, i
  *   h_grad        n_layers + 2 doubles (host): d loss / d theta
  * Each ray is recomputed from its random-number counter; derivatives are
  * carried as binary32 tangents and summed per block in binary64, then over
- * blocks in a fixed order.  Synchronises `stream` once.  The tangents are
- * those of the exact propagator without dispersion: with dispersion on or
- * CLIGHT_PROP_STRAIGHT set it returns CLIGHT_ERR_ARG. */
+ * blocks in a fixed order.  The rays near a telescope (those within
+ * R + soft_w of a centre) are listed by a candidate pass and sorted before
+ * the tangent kernels run, so every thread sees the same rays in the same
+ * order on every call, and Y is summed in integer units of 2^-24 photons
+ * (at most 2^39 photons per shower and telescope): h_grad and d_yield are
+ * bitwise reproducible.  Synchronises `stream` once or twice.  The tangents
+ * are those of the exact propagator without dispersion: with dispersion on
+ * or CLIGHT_PROP_STRAIGHT set it returns CLIGHT_ERR_ARG.  A bunch index
+ * beyond 2^16 (the key_bunch_bits of clight_params) returns
+ * CLIGHT_ERR_LIMIT. */
 clight_status clight_trace_adjoint(clight_ctx *ctx, const clight_segment *d_segs, int64_t n_segs,
                                    int32_t n_showers, const clight_hit *d_hits, int64_t n_hits,
                                    const float *d_gx, const float *d_gy, const float *d_gt,
@@ -321,38 +338,74 @@ clight_status clight_trace_noalloc(clight_ctx *ctx, const clight_segment *d_segs
 /* Result of clight_autotune. */
 typedef struct clight_tune {
     int32_t block;          /* chosen threads per CTA */
-    int32_t ctas_per_sm;    /* chosen persistent CTAs per SM */
+    int32_t ctas_per_sm;    /* chosen persistent CTAs per SM (0 = the path's default) */
     float cell_width;       /* chosen quadrature cell width (scale heights) */
-    float pad;
+    int32_t work_chunk;     /* chosen groups of 32 steps per work claim */
     double bunch;           /* chosen bunch size (<= the caller's maximum) */
     double best_ms;         /* median step time of the chosen settings on the sample */
     double default_ms;      /* the same for the library defaults at the caller's bunch size */
     int32_t n_tried;        /* settings timed */
-    int32_t pad2;
+    int32_t pad;
+    int64_t n_sample;       /* steps in the sample */
 } clight_tune;
 
-/* Pick the launch shape, quadrature cell width and bunch size for a batch
- * (the batching pattern of the forward path: one persistent launch over
- * many showers).  Paper: no counterpart; the paper's GPU code has fixed
- * launch parameters.
- *   - Times `reps` (>= 1; median taken) calls of the whole step (trace,
- *     sort, per-telescope reduction; no graph) on the first `n_sample`
- *     segments of d_segs for each candidate: block x CTAs per SM in
- *     {256x3, 256x2, 128x6, 128x4, 64x12}, cell width in {1.0, 1.5}
- *     scale heights (no wider than the default, whose accuracy the tests
- *     establish), bunch size in {1, 2, 5, bunch_max} capped at bunch_max.
- *     The photon count of a batch does not depend on the bunch size, so the
- *     fastest setting carries the most photons per second.
+/* Pick the bunch size, launch shape, work-stealing granularity and
+ * quadrature cell width for a batch (the batching pattern of the forward
+ * path: one persistent launch over many showers).  Paper: no counterpart;
+ * the paper's GPU code has fixed launch parameters.
+ *   - The sample: n_sample steps in 64 blocks spread evenly over all n_segs
+ *     steps of d_segs (so every shower of a batch contributes in proportion
+ *     to its size), copied into context memory; all of d_segs when
+ *     n_sample >= n_segs.
+ *   - Each setting is timed as the median of `reps` (>= 1; 5 or more
+ *     recommended) calls of the whole step (trace, sort, per-telescope
+ *     reduction; no graph) after one warm-up call.
+ *   - The library defaults (at the caller's bunch size, capped at
+ *     bunch_max) are the first incumbent.  Then one knob at a time: bunch
+ *     size in {1, 2, 5, bunch_max} (<= bunch_max), block x CTAs per SM in
+ *     {256x4, 256x3, 128x8, 128x6, 64x16}, work chunk in {2, 4}, cell width
+ *     1.0 (never wider than the default 1.5, whose accuracy the tests
+ *     establish).  A candidate replaces the incumbent only when its median
+ *     is lower by more than the incumbent's spread (interquartile range for
+ *     5 or more calls, else the range) and by more than 1%.  So best_ms <=
+ *     default_ms.  The photon count of a batch does not depend on the
+ *     bunch size, so the fastest setting carries the most photons per
+ *     second.
  *   - d_hits / hit_capacity: scratch for the sample's hits (the caller's
  *     buffer; overflow only truncates the sample's list and is ignored).
  *   - On success the context keeps the chosen settings (as if set by
  *     clight_set_params with the other fields unchanged) and *out holds
  *     them.  ERR_ARG for a bad argument (bunch_max <= 0, n_sample < 1,
- *     reps < 1, NULL out); the context's settings are unchanged on error.
+ *     n_segs < 1, reps < 1, NULL out); the context's settings are unchanged
+ *     on error.
  * Synchronises `stream`. */
-clight_status clight_autotune(clight_ctx *ctx, const clight_segment *d_segs, int64_t n_sample, int32_t n_showers,
-                              clight_hit *d_hits, int64_t hit_capacity, double bunch_max, int32_t reps,
-                              clight_tune *out, void *stream);
+clight_status clight_autotune(clight_ctx *ctx, const clight_segment *d_segs, int64_t n_segs, int64_t n_sample,
+                              int32_t n_showers, clight_hit *d_hits, int64_t hit_capacity, double bunch_max,
+                              int32_t reps, clight_tune *out, void *stream);
+
+/* Measured instruction throughput of the GPU (operations per second, all
+ * SMs), and the mean SM clock during each probe (MHz, from clock64() against
+ * the global timer on the device).  The tracing path is bound by arithmetic
+ * issue, so these -- not a copy bandwidth or a GEMM rate -- are its roofline
+ * denominators.  The paper has no counterpart. */
+typedef struct {
+    double ffma_per_s;      /* FP32 fused multiply-add (one operation each) */
+    double mufu_ex2_per_s;  /* MUFU ex2.approx (the special-function unit) */
+    double dfma_per_s;      /* FP64 fused multiply-add */
+    double imad_per_s;      /* 32-bit integer multiply-add */
+    double lop3_per_s;      /* 3-input logic operation */
+    double ffma_mhz, mufu_mhz, dfma_mhz, imad_mhz, lop3_mhz;
+    int32_t n_sm;
+    int32_t pad;
+} clight_pipe_rates;
+
+/* Run the throughput probes on `device` (each: 8 independent chains of one
+ * instruction per thread in a grid that fills every SM; best of 3 timed
+ * launches after a warm-up, CUDA events; a few milliseconds each).  Changes
+ * no GPU setting.  Allocates and frees a small scratch buffer.
+ * CLIGHT_ERR_NO_DEVICE without the device, CLIGHT_ERR_CUDA on a runtime
+ * error. */
+clight_status clight_measure_pipes(int device, clight_pipe_rates *out);
 
 /* Device time of the last clight_trace / clight_trace_fp64 call, measured
  * with CUDA events recorded on the launch stream around its phases:

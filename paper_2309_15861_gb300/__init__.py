@@ -56,22 +56,32 @@ class Params(C.Structure):
                 ("cut_mode", C.c_int32), ("cut_pad", C.c_int32), ("cut_deg", C.c_double),
                 ("cut_centre", C.c_double * 3), ("fl_beaming", C.c_int32), ("propagator", C.c_int32),
                 ("beam_centre", C.c_double * 3), ("beam_radius", C.c_double), ("fl_roulette", C.c_int32),
-                ("roulette_pad", C.c_int32), ("defer_cap", C.c_int64)]
+                ("roulette_pad", C.c_int32), ("defer_cap", C.c_int64), ("trace_all", C.c_int32),
+                ("work_chunk", C.c_int32)]
 
 
 class Stats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in
                 ("rays", "escaped", "under", "turned", "reached", "hits", "guarded", "status", "cells", "cut",
-                 "skipped")]
+                 "skipped", "deferred")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
+class PipeRates(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("ffma_per_s", "mufu_ex2_per_s", "dfma_per_s", "imad_per_s", "lop3_per_s",
+                                          "ffma_mhz", "mufu_mhz", "dfma_mhz", "imad_mhz", "lop3_mhz")] + \
+               [("n_sm", C.c_int32), ("pad", C.c_int32)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_ if n != "pad"}
+
+
 class Tune(C.Structure):
-    _fields_ = [("block", C.c_int32), ("ctas_per_sm", C.c_int32), ("cell_width", C.c_float), ("pad", C.c_float),
-                ("bunch", C.c_double), ("best_ms", C.c_double), ("default_ms", C.c_double),
-                ("n_tried", C.c_int32), ("pad2", C.c_int32)]
+    _fields_ = [("block", C.c_int32), ("ctas_per_sm", C.c_int32), ("cell_width", C.c_float),
+                ("work_chunk", C.c_int32), ("bunch", C.c_double), ("best_ms", C.c_double),
+                ("default_ms", C.c_double), ("n_tried", C.c_int32), ("pad", C.c_int32), ("n_sample", C.c_int64)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_ if not n.startswith("pad")}
@@ -104,10 +114,11 @@ def lib():
         L.clight_last_timing.argtypes = [P, P]
         L.clight_trace_adjoint.argtypes = [P, P, C.c_int64, C.c_int32, P, C.c_int64, P, P, P, P,
                                            C.c_float, C.c_float, P, P, P]
-        L.clight_autotune.argtypes = [P, P, C.c_int64, C.c_int32, P, C.c_int64, C.c_double, C.c_int32,
+        L.clight_autotune.argtypes = [P, P, C.c_int64, C.c_int64, C.c_int32, P, C.c_int64, C.c_double, C.c_int32,
                                       C.POINTER(Tune), P]
         L.clight_trace_noalloc.argtypes = [P, P, C.c_int64, C.c_int32, P, C.c_int64, P,
                                            C.POINTER(Stats), C.POINTER(C.c_int64), P]
+        L.clight_measure_pipes.argtypes = [C.c_int, C.POINTER(PipeRates)]
         _lib = L
     return _lib
 
@@ -234,17 +245,21 @@ class Context:
         _check(code, "clight_trace_adjoint")
         return out
 
-    def autotune(self, d_segs, n_sample, n_showers, d_hits, capacity, bunch_max, reps=3, stream=None):
-        """Time candidate launch shapes, cell widths and bunch sizes on the first n_sample
-        segments; the context keeps the fastest.  -> dict of the choice and timings."""
+    def autotune(self, d_segs, n_segs, n_sample, n_showers, d_hits, capacity, bunch_max, reps=5, stream=None):
+        """Time bunch sizes, launch shapes, work chunks and cell widths on a sample of n_sample
+        steps spread over all n_segs; the context keeps the choice (never slower than the
+        defaults by the tuner's own timing).  -> dict of the choice and timings."""
+        _need(d_segs, int(n_segs) * 64, "d_segs")
+        _need(d_hits, int(capacity) * 48, "d_hits")
         t = Tune()
-        code = lib().clight_autotune(self._h, _ptr(d_segs), int(n_sample), int(n_showers), _ptr(d_hits),
-                                     int(capacity), float(bunch_max), int(reps), C.byref(t),
+        code = lib().clight_autotune(self._h, _ptr(d_segs), int(n_segs), int(n_sample), int(n_showers),
+                                     _ptr(d_hits), int(capacity), float(bunch_max), int(reps), C.byref(t),
                                      _stream_handle(stream))
         _check(code, "clight_autotune")
         if self.params is not None:
             self.params.block, self.params.ctas_per_sm = t.block, t.ctas_per_sm
             self.params.cell_width, self.params.bunch = t.cell_width, t.bunch
+            self.params.work_chunk = t.work_chunk
         return t.as_dict()
 
     def trace_noalloc(self, d_segs, n_segs, n_showers, d_hits, capacity, d_counts=None, stream=None,
@@ -288,6 +303,14 @@ class Context:
             raise ClightError(code, "clight_trace_host")
         n = min(nh.value, capacity)
         return code, hits[:n], counts.reshape(n_showers, self.n_tel), sums.reshape(n_showers, self.n_tel), st.as_dict()
+
+
+def pipe_rates(device: int = 0) -> dict:
+    """Measured FP32-FMA, MUFU, FP64-FMA, integer-multiply and logic
+    throughput of the GPU (operations/s) and the SM clock during each probe."""
+    r = PipeRates()
+    _check(lib().clight_measure_pipes(int(device), C.byref(r)), "clight_measure_pipes")
+    return r.as_dict()
 
 
 def _need(x, nbytes, what):

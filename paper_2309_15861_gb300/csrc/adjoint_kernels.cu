@@ -15,6 +15,7 @@
 // summed per block in binary64 and then over blocks in a fixed order.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "ray.cuh"
@@ -185,6 +186,10 @@ __device__ void tangent_ray(const Seg<float, df> &g, const clight_segment &s, in
     atm_d<NP>(A, J, g.h_mid, dmid, rmid);
     float eps = s.eps;
     D g1 = dmid * (1.0f - eps) - eps;                       // beta n - 1
+    // its value from the step set-up (refractivity in FP32 pairs near the
+    // threshold, where binary32 loses kappa/2 of its digits): the tangent of
+    // sin(theta_c) goes like 1 / sqrt(beta n - 1)
+    if (g.n_c > 0 && g.kappa > 0.0f) g1 = with_value(g1, g.kappa / (1.0f - g.kappa));
     D bn = g1 + 1.0f;
     D sin2 = g1 * (g1 + 2.0f) / (bn * bn);
     D sin_tc = dsqrt(sin2);
@@ -439,7 +444,7 @@ k_adjoint_hits(const clight_segment *__restrict__ segs, const clight_hit *__rest
 template <int NP, bool SPH, bool REFR>
 __global__ void __launch_bounds__(128, 4)
 k_adjoint_soft(const clight_segment *__restrict__ segs, const unsigned long long *__restrict__ cand, int64_t n_cand,
-               const double *__restrict__ gY, double *__restrict__ yield, const __grid_constant__ DevAtm A,
+               const double *__restrict__ gY, unsigned long long *__restrict__ yfix, const __grid_constant__ DevAtm A,
                const __grid_constant__ DevTel Tl, const __grid_constant__ DevPar Pp, const __grid_constant__ AdjPar J,
                double *__restrict__ partial)
 {
@@ -448,8 +453,8 @@ k_adjoint_soft(const clight_segment *__restrict__ segs, const unsigned long long
     for (int p = 0; p < NP; ++p) acc[p] = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_cand; i += (int64_t)gridDim.x * blockDim.x) {
         unsigned long long ck = cand[i];
-        int64_t si = (int64_t)(ck >> 32);
-        uint32_t k = (uint32_t)ck;
+        int64_t si = (int64_t)(ck >> Pp.k_bits);
+        uint32_t k = (uint32_t)(ck & ((1ull << Pp.k_bits) - 1ull));
         clight_segment s = segs[si];
         Seg<float, df> g;
         load_segment_f<SPH>(s, Pp.seg_base + si, A, Pp, g);
@@ -488,7 +493,8 @@ k_adjoint_soft(const clight_segment *__restrict__ segs, const unsigned long long
                     float sg = 1.0f / (1.0f + expf(-u));
                     int64_t grp = (int64_t)g.shower * Tl.n_tel + j;
                     float val = (float)o.weight * sg;
-                    if (yield) atomicAdd(yield + grp, (double)val);
+                    // integer units of 2^-24 photons: the sum has the same bits in any order
+                    if (yfix) atomicAdd(yfix + grp, __float2ull_rn(val * 16777216.0f));
                     if (gY) {
                         if (!have_t) {
                             tangent_ray<NP, SPH, REFR>(g, s, seg_global, k, A, Pp, J, T);
@@ -519,15 +525,22 @@ __global__ void k_adjoint_final(const double *__restrict__ partial, int n_blocks
     out[p] = s;
 }
 
+// The soft yield from its fixed-point accumulators.
+__global__ void k_yield_out(const unsigned long long *__restrict__ yfix, int64_t n, double *__restrict__ yield)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        yield[i] = (double)yfix[i] * 5.9604644775390625e-08;
+}
+
 template <int NP, bool SPH, bool REFR>
 static cudaError_t adjoint_np(const clight_segment *segs, const unsigned long long *cand, int64_t n_cand,
                               const clight_hit *hits, int64_t n_hits,
-                              const float *gx, const float *gy, const float *gt, const double *gY, double *yield,
-                              const DevAtm &A, const DevTel &T, const DevPar &P, const AdjPar &J, double *partial,
-                              int blocks, double *d_out, cudaStream_t s)
+                              const float *gx, const float *gy, const float *gt, const double *gY,
+                              unsigned long long *yfix, const DevAtm &A, const DevTel &T, const DevPar &P,
+                              const AdjPar &J, double *partial, int blocks, double *d_out, cudaStream_t s)
 {
     k_adjoint_hits<NP, SPH, REFR><<<blocks, 128, 0, s>>>(segs, hits, n_hits, gx, gy, gt, A, T, P, J, partial);
-    k_adjoint_soft<NP, SPH, REFR><<<blocks, 128, 0, s>>>(segs, cand, n_cand, gY, yield, A, T, P, J,
+    k_adjoint_soft<NP, SPH, REFR><<<blocks, 128, 0, s>>>(segs, cand, n_cand, gY, yfix, A, T, P, J,
                                                          partial + (size_t)blocks * NP);
     k_adjoint_final<NP><<<1, 32, 0, s>>>(partial, 2 * blocks, d_out);
     return cudaGetLastError();
@@ -536,24 +549,25 @@ static cudaError_t adjoint_np(const clight_segment *segs, const unsigned long lo
 template <int NP>
 static cudaError_t adjoint_geo(const clight_segment *segs, const unsigned long long *cand, int64_t n_cand,
                                const clight_hit *hits, int64_t n_hits,
-                               const float *gx, const float *gy, const float *gt, const double *gY, double *yield,
-                               const DevAtm &A, const DevTel &T, const DevPar &P, const AdjPar &J, double *partial,
-                               int blocks, double *d_out, cudaStream_t s)
+                               const float *gx, const float *gy, const float *gt, const double *gY,
+                               unsigned long long *yfix, const DevAtm &A, const DevTel &T, const DevPar &P,
+                               const AdjPar &J, double *partial, int blocks, double *d_out, cudaStream_t s)
 {
     if (A.spherical && A.refraction)
-        return adjoint_np<NP, true, true>(segs, cand, n_cand, hits, n_hits, gx, gy, gt, gY, yield, A, T, P, J, partial, blocks, d_out, s);
+        return adjoint_np<NP, true, true>(segs, cand, n_cand, hits, n_hits, gx, gy, gt, gY, yfix, A, T, P, J, partial, blocks, d_out, s);
     if (A.spherical)
-        return adjoint_np<NP, true, false>(segs, cand, n_cand, hits, n_hits, gx, gy, gt, gY, yield, A, T, P, J, partial, blocks, d_out, s);
+        return adjoint_np<NP, true, false>(segs, cand, n_cand, hits, n_hits, gx, gy, gt, gY, yfix, A, T, P, J, partial, blocks, d_out, s);
     if (A.refraction)
-        return adjoint_np<NP, false, true>(segs, cand, n_cand, hits, n_hits, gx, gy, gt, gY, yield, A, T, P, J, partial, blocks, d_out, s);
-    return adjoint_np<NP, false, false>(segs, cand, n_cand, hits, n_hits, gx, gy, gt, gY, yield, A, T, P, J, partial, blocks, d_out, s);
+        return adjoint_np<NP, false, true>(segs, cand, n_cand, hits, n_hits, gx, gy, gt, gY, yfix, A, T, P, J, partial, blocks, d_out, s);
+    return adjoint_np<NP, false, false>(segs, cand, n_cand, hits, n_hits, gx, gy, gt, gY, yfix, A, T, P, J, partial, blocks, d_out, s);
 }
 
 int adjoint_params(int n_layers) { return n_layers <= 1 ? 3 : (n_layers <= 5 ? 7 : 10); }
 
 cudaError_t launch_adjoint(const clight_segment *segs, const unsigned long long *cand, int64_t n_cand,
                            const clight_hit *hits, int64_t n_hits,
-                           const float *gx, const float *gy, const float *gt, const double *gY, double *yield,
+                           const float *gx, const float *gy, const float *gt, const double *gY,
+                           unsigned long long *yfix, double *yield, int64_t n_groups,
                            const DevAtm &A, const DevTel &T, const DevPar &P, float soft_s, float soft_w, float K,
                            float L0, double *partial, int blocks, double *d_out, cudaStream_t s)
 {
@@ -564,9 +578,16 @@ cudaError_t launch_adjoint(const clight_segment *segs, const unsigned long long 
     J.L0 = L0;
     J.n_layers = A.n_layers;
     int np = adjoint_params(A.n_layers);
-    if (np == 3) return adjoint_geo<3>(segs, cand, n_cand, hits, n_hits, gx, gy, gt, gY, yield, A, T, P, J, partial, blocks, d_out, s);
-    if (np == 7) return adjoint_geo<7>(segs, cand, n_cand, hits, n_hits, gx, gy, gt, gY, yield, A, T, P, J, partial, blocks, d_out, s);
-    return adjoint_geo<10>(segs, cand, n_cand, hits, n_hits, gx, gy, gt, gY, yield, A, T, P, J, partial, blocks, d_out, s);
+    cudaError_t e;
+    if (np == 3) e = adjoint_geo<3>(segs, cand, n_cand, hits, n_hits, gx, gy, gt, gY, yfix, A, T, P, J, partial, blocks, d_out, s);
+    else if (np == 7) e = adjoint_geo<7>(segs, cand, n_cand, hits, n_hits, gx, gy, gt, gY, yfix, A, T, P, J, partial, blocks, d_out, s);
+    else e = adjoint_geo<10>(segs, cand, n_cand, hits, n_hits, gx, gy, gt, gY, yfix, A, T, P, J, partial, blocks, d_out, s);
+    if (e != cudaSuccess) return e;
+    if (yield && yfix && n_groups > 0) {
+        k_yield_out<<<(unsigned)std::min<int64_t>((n_groups + 255) / 256, 1024), 256, 0, s>>>(yfix, n_groups, yield);
+        e = cudaGetLastError();
+    }
+    return e;
 }
 
 }  // namespace clight

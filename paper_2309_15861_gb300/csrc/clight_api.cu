@@ -84,7 +84,10 @@ struct clight_ctx {
     // staging for the host-buffer entry point
     Buf<double> adj_partial, adj_out;
     Buf<unsigned long long> adj_cand, adj_ctr;   // soft-yield candidates and their cursor
+    Buf<unsigned long long> adj_keys_alt, adj_yfix;   // candidate sort; fixed-point soft yield
+    Buf<uint32_t> adj_vals, adj_vals_alt, adj_hist, adj_bsums;
     Buf<clight_segment> stage_segs;
+    Buf<clight_segment> tune_segs;              // the autotuner's sample
     Buf<clight_hit> stage_hits;
     Buf<int64_t> stage_counts;
     Buf<double> stage_sums;
@@ -185,8 +188,10 @@ void clight_destroy(clight_ctx *c)
     c->rec.release(); c->keys.release(); c->keys_alt.release(); c->vals.release(); c->vals_alt.release();
     c->defer.release();
     c->hist.release(); c->bsums.release(); c->gstart.release(); c->gend.release();
-    c->stage_segs.release(); c->stage_hits.release(); c->stage_counts.release(); c->stage_sums.release();
+    c->stage_segs.release(); c->tune_segs.release(); c->stage_hits.release(); c->stage_counts.release(); c->stage_sums.release();
     c->adj_partial.release(); c->adj_out.release(); c->adj_cand.release(); c->adj_ctr.release();
+    c->adj_keys_alt.release(); c->adj_yfix.release(); c->adj_vals.release(); c->adj_vals_alt.release();
+    c->adj_hist.release(); c->adj_bsums.release();
     if (c->h_ctr) cudaFreeHost(c->h_ctr);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
@@ -225,10 +230,12 @@ clight_status clight_set_atmosphere(clight_ctx *c, const clight_atmosphere *a)
         A.h_lo[i] = (float)a->h_lo[i];
         A.h_lo_d[i] = a->h_lo[i];
         A.kb[i] = (float)(a->K * Bc(i));
+        A.kb_lo[i] = (float)(a->K * Bc(i) - (double)A.kb[i]);
         A.kb_d[i] = a->K * Bc(i);
         A.rb[i] = (float)(Bc(i) / a->rho_ref);
         A.rb_d[i] = Bc(i) / a->rho_ref;
         A.nl2c[i] = (float)(-LOG2E / a->c[i]);
+        A.nl2c_lo[i] = (float)(-LOG2E / a->c[i] - (double)A.nl2c[i]);
         A.inv_c_d[i] = 1.0 / a->c[i];
     }
     A.h_top = (float)a->h_top; A.h_top_d = a->h_top;
@@ -473,6 +480,8 @@ clight_status clight_set_params(clight_ctx *c, const clight_params *p)
     if (p->fl_beaming != 0 && p->fl_beaming != 1) return CLIGHT_ERR_ARG;
     if (p->fl_roulette != 0 && p->fl_roulette != 1) return CLIGHT_ERR_ARG;
     if (p->defer_cap > (int64_t(1) << 31)) return CLIGHT_ERR_ARG;
+    if (p->trace_all != 0 && p->trace_all != 1) return CLIGHT_ERR_ARG;
+    if (p->work_chunk < 0 || p->work_chunk > 64) return CLIGHT_ERR_ARG;
     if (p->propagator != CLIGHT_PROP_EXACT && p->propagator != CLIGHT_PROP_STRAIGHT) return CLIGHT_ERR_ARG;
     if (p->fl_beaming && (!(p->beam_radius > 0) || !std::isfinite(p->beam_radius) ||
                           !std::isfinite(p->beam_centre[0]) || !std::isfinite(p->beam_centre[1]) ||
@@ -513,6 +522,8 @@ clight_status clight_set_params(clight_ctx *c, const clight_params *p)
     P.beam = p->fl_beaming;
     P.roulette = p->fl_roulette;
     P.prop = p->propagator;
+    P.cull = p->trace_all ? 0 : 1;
+    P.chunk = p->work_chunk > 0 ? p->work_chunk : 1;
     P.beam_cx_d = p->beam_centre[0]; P.beam_cy_d = p->beam_centre[1]; P.beam_cz_d = p->beam_centre[2];
     P.beam_r_d = p->beam_radius;
     P.beam_cx = (float)P.beam_cx_d; P.beam_cy = (float)P.beam_cy_d; P.beam_cz = (float)P.beam_cz_d;
@@ -598,7 +609,7 @@ clight_status prepare(clight_ctx *c, int64_t n_segs, int32_t n_showers, int64_t 
     const int64_t dc = c->upar.defer_cap;
     const int64_t dflt = std::min<int64_t>(std::max<int64_t>(2 * n_segs, 1 << 20), 1 << 28);
     c->defer_piece = dflt / 2;
-    if (c->defer_off || dc < 0)
+    if (c->defer_off || dc < 0 || c->upar.trace_all)
         c->defer_use = 0;
     else if (dc > 0)
         c->defer_use = dc;
@@ -698,6 +709,7 @@ clight_status finish(clight_ctx *c, int64_t cap, clight_stats *st, int64_t *n_hi
         st->cells = (int64_t)h[CTR_STATS + ST_CELLS];
         st->cut = (int64_t)h[CTR_STATS + ST_CUT];
         st->skipped = (int64_t)h[CTR_STATS + ST_SKIPPED];
+        st->deferred = (int64_t)h[CTR_STATS + ST_DEFERRED];
     }
     c->timed = true;
     if ((int64_t)cursor > cap) return CLIGHT_ERR_HIT_CAPACITY;
@@ -853,72 +865,133 @@ clight_status clight_trace_host(clight_ctx *c, const clight_segment *h_segs, int
 
 }  // extern "C"
 
-extern "C" clight_status clight_autotune(clight_ctx *c, const clight_segment *d_segs, int64_t n_sample,
-                                         int32_t n_showers, clight_hit *d_hits, int64_t hit_capacity,
-                                         double bunch_max, int32_t reps, clight_tune *out, void *stream)
+extern "C" clight_status clight_autotune(clight_ctx *c, const clight_segment *d_segs, int64_t n_segs,
+                                         int64_t n_sample, int32_t n_showers, clight_hit *d_hits,
+                                         int64_t hit_capacity, double bunch_max, int32_t reps, clight_tune *out,
+                                         void *stream)
 {
-    if (!c || !out || !d_segs || n_sample < 1 || reps < 1 || !(bunch_max > 0) || n_showers < 1 ||
+    if (!c || !out || !d_segs || n_segs < 1 || n_sample < 1 || reps < 1 || !(bunch_max > 0) || n_showers < 1 ||
         hit_capacity < 0 || (hit_capacity > 0 && !d_hits))
         return CLIGHT_ERR_ARG;
     if (!c->atm_set || !c->tel_set) return CLIGHT_ERR_ARG;
+    if (n_segs > (int64_t(1) << 31)) return CLIGHT_ERR_LIMIT;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return CLIGHT_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
     const clight_params saved = c->upar;
-    struct Shape { int block, per_sm; };
-    const Shape shapes[] = {{256, 3}, {256, 2}, {128, 6}, {128, 4}, {64, 12}};
-    const float widths[] = {1.0f, 1.5f};
-    std::vector<double> bunches;
-    for (double b : {1.0, 2.0, 5.0, bunch_max})
-        if (b <= bunch_max && std::find(bunches.begin(), bunches.end(), b) == bunches.end()) bunches.push_back(b);
+    // the sample: kBlocks blocks spread evenly over all n_segs steps (every
+    // shower of a batch contributes in proportion to its size), gathered into
+    // context memory
+    const clight_segment *sample = d_segs;
+    int64_t n = n_segs;
+    if (n_sample < n_segs) {
+        const int64_t kBlocks = 64;
+        int64_t blk = std::max<int64_t>(32, (n_sample / kBlocks + 31) / 32 * 32);
+        int64_t nb = std::min<int64_t>(kBlocks, std::max<int64_t>(1, n_segs / blk));
+        n = nb * blk;
+        if (c->tune_segs.ensure(n, &c->scratch_gen)) return CLIGHT_ERR_CUDA;
+        for (int64_t i = 0; i < nb; ++i) {
+            const int64_t off = nb > 1 ? (i * (n_segs - blk)) / (nb - 1) : 0;
+            CK(cudaMemcpyAsync(c->tune_segs.p + i * blk, d_segs + off, sizeof(clight_segment) * (size_t)blk,
+                               cudaMemcpyDeviceToDevice, s));
+        }
+        sample = c->tune_segs.p;
+    }
     int64_t n_hits = 0;
     clight_stats st;
-    // median step time (ms) of one setting; a negative value on failure
-    auto time_of = [&](const clight_params &p) -> double {
-        if (clight_set_params(c, &p) != CLIGHT_OK) return -1.0;
+    struct Timing { double med, spread; };
+    // median step time (ms) of one setting over `reps` calls after one warm-up
+    // call, and its spread (interquartile range for 5 or more calls, else the
+    // range); med < 0 on failure
+    auto time_of = [&](const clight_params &p) -> Timing {
+        if (clight_set_params(c, &p) != CLIGHT_OK) return {-1.0, 0.0};
         std::vector<float> t;
-        for (int r = 0; r < reps + 1; ++r) {     // the first call warms up
-            clight_status s = run(c, d_segs, n_sample, n_showers, d_hits, hit_capacity, nullptr, nullptr, &st,
-                                  &n_hits, stream, false);
-            if (s != CLIGHT_OK && s != CLIGHT_ERR_HIT_CAPACITY) return -1.0;
+        for (int r = 0; r < reps + 1; ++r) {
+            clight_status e = run(c, sample, n, n_showers, d_hits, hit_capacity, nullptr, nullptr, &st, &n_hits,
+                                  stream, false);
+            if (e != CLIGHT_OK && e != CLIGHT_ERR_HIT_CAPACITY) return {-1.0, 0.0};
             float ms = 0;
-            if (cudaEventElapsedTime(&ms, c->t0, c->t2) != cudaSuccess) return -1.0;
+            if (cudaEventElapsedTime(&ms, c->t0, c->t2) != cudaSuccess) return {-1.0, 0.0};
             if (r > 0) t.push_back(ms);
         }
         std::sort(t.begin(), t.end());
-        return t[t.size() / 2];
+        const size_t m = t.size();
+        const double spread = m >= 5 ? (double)(t[(3 * m) / 4] - t[m / 4]) : (double)(t[m - 1] - t[0]);
+        return {(double)t[m / 2], spread};
     };
-    clight_params base = saved;
-    base.use_graph = 0;
-    base.block = 0;
-    base.ctas_per_sm = 0;
-    base.cell_width = 0;
-    double def_ms = time_of(base);
-    if (def_ms < 0) { clight_set_params(c, &saved); return CLIGHT_ERR_CUDA; }
-    clight_tune best{};
-    best.best_ms = 1e300;
+    // the library defaults at the caller's bunch size (capped at bunch_max)
+    clight_params inc = saved;
+    inc.use_graph = 0;
+    inc.block = 0;
+    inc.ctas_per_sm = 0;
+    inc.cell_width = 0;
+    inc.work_chunk = 0;
+    inc.bunch = std::min(saved.bunch, bunch_max);
+    Timing ti = time_of(inc);
+    if (ti.med < 0) { clight_set_params(c, &saved); return CLIGHT_ERR_CUDA; }
+    const double def_ms = ti.med;
     int tried = 1;
-    for (double b : bunches)
-        for (const Shape &sh : shapes)
-            for (float cw : widths) {
-                clight_params p = saved;
-                p.use_graph = 0;
-                p.block = sh.block;
-                p.ctas_per_sm = sh.per_sm;
-                p.cell_width = cw;
-                p.bunch = b;
-                double ms = time_of(p);
-                ++tried;
-                if (ms < 0) { clight_set_params(c, &saved); return CLIGHT_ERR_CUDA; }
-                if (ms < best.best_ms) {
-                    best.block = sh.block; best.ctas_per_sm = sh.per_sm; best.cell_width = cw;
-                    best.bunch = b; best.best_ms = ms;
-                }
-            }
+    // one knob at a time from the defaults; a candidate replaces the
+    // incumbent only when faster by more than the incumbent's spread (and 1%)
+    auto consider = [&](const clight_params &p) -> bool {
+        Timing tc = time_of(p);
+        ++tried;
+        if (tc.med < 0) return false;
+        if (tc.med < ti.med - std::max(0.01 * ti.med, ti.spread)) {
+            inc = p;
+            ti = tc;
+        }
+        return true;
+    };
+    bool ok = true;
+    std::vector<double> bunches;
+    for (double b : {1.0, 2.0, 5.0, bunch_max})
+        if (b <= bunch_max && b != inc.bunch && std::find(bunches.begin(), bunches.end(), b) == bunches.end())
+            bunches.push_back(b);
+    const clight_params base_bunch = inc;
+    for (double b : bunches) {
+        clight_params p = base_bunch;
+        p.bunch = b;
+        ok = ok && consider(p);
+    }
+    struct Shape { int block, per_sm; };
+    const Shape shapes[] = {{256, 4}, {256, 3}, {128, 8}, {128, 6}, {64, 16}};
+    const clight_params base_shape = inc;
+    for (const Shape &sh : shapes) {
+        clight_params p = base_shape;
+        p.block = sh.block;
+        p.ctas_per_sm = sh.per_sm;
+        ok = ok && consider(p);
+    }
+    const clight_params base_chunk = inc;
+    for (int ch : {2, 4}) {
+        clight_params p = base_chunk;
+        p.work_chunk = ch;
+        ok = ok && consider(p);
+    }
+    {
+        clight_params p = inc;
+        p.cell_width = 1.0f;                 // narrower than the default 1.5 scale heights
+        ok = ok && consider(p);
+    }
+    if (!ok) { clight_set_params(c, &saved); return CLIGHT_ERR_CUDA; }
+    clight_tune best{};
+    best.block = inc.block > 0 ? inc.block : 256;
+    best.ctas_per_sm = inc.ctas_per_sm;
+    best.cell_width = inc.cell_width > 0 ? inc.cell_width : 1.5f;
+    best.bunch = inc.bunch;
+    best.best_ms = ti.med;
     best.default_ms = def_ms;
     best.n_tried = tried;
+    best.work_chunk = inc.work_chunk > 0 ? inc.work_chunk : 1;
+    best.n_sample = n;
+    // the context keeps the choice, with the caller's other settings
     clight_params p = saved;
-    p.block = best.block;
-    p.ctas_per_sm = best.ctas_per_sm;
-    p.cell_width = best.cell_width;
-    p.bunch = best.bunch;
+    p.block = inc.block;
+    p.ctas_per_sm = inc.ctas_per_sm;
+    p.cell_width = inc.cell_width;
+    p.work_chunk = inc.work_chunk;
+    p.bunch = inc.bunch;
     clight_status r = clight_set_params(c, &p);
     if (r != CLIGHT_OK) { clight_set_params(c, &saved); return r; }
     *out = best;
@@ -944,12 +1017,16 @@ extern "C" clight_status clight_trace_adjoint(clight_ctx *c, const clight_segmen
     cudaStream_t s = (cudaStream_t)stream;
     int np = adjoint_params(c->atm.n_layers);
     int blocks = c->n_sm * 8;
+    const int64_t n_groups = (int64_t)n_showers * c->tel.n_tel;
     uint64_t *g = &c->scratch_gen;
     if (c->adj_partial.ensure((int64_t)2 * blocks * np, g) || c->adj_out.ensure(np, g) ||
-        c->adj_ctr.ensure(CTR_N, g))
+        c->adj_ctr.ensure(CTR_N, g) || c->adj_yfix.ensure(n_groups, g))
         return CLIGHT_ERR_CUDA;
     DevPar P = c->par;
     P.n_showers = n_showers;
+    // candidate keys: local step << k_bits | bunch
+    P.k_bits = c->upar.key_bunch_bits > 0 ? c->upar.key_bunch_bits : 16;
+    P.seg_bits = bits_for(std::max<int64_t>(n_segs - 1, 0));
     P.cut_tel = c->tel.tel;
     P.cut_n_tel = c->tel.n_tel;
     P.cut_tx = c->tel.mx; P.cut_ty = c->tel.my; P.cut_tz = c->tel.mz; P.cut_tr = c->tel.mr;
@@ -957,11 +1034,12 @@ extern "C" clight_status clight_trace_adjoint(clight_ctx *c, const clight_segmen
     P.cut_cabs = std::max(c->tel.cabs, (float)(std::fabs(P.cut_cx_d) + std::fabs(P.cut_cy_d) + std::fabs(P.cut_cz_d)));
     P.cut_nx = c->tel.nx; P.cut_ny = c->tel.ny;
     P.cut_gx0 = c->tel.gx0; P.cut_gy0 = c->tel.gy0; P.cut_inv_gs = c->tel.inv_gs;
-    if (d_yield)
-        CK(cudaMemsetAsync(d_yield, 0, sizeof(double) * (size_t)n_showers * c->tel.n_tel, s));
+    CK(cudaMemsetAsync(c->adj_yfix.p, 0, sizeof(unsigned long long) * (size_t)n_groups, s));
     // candidate pass: the rays near a telescope, compacted by the forward
-    // kernel (grown and repeated if the list overflows)
+    // kernel (grown and repeated if the list overflows), then sorted, so that
+    // the adjoint kernels see them in one order on every call
     int64_t n_cand = 0;
+    const unsigned long long *cand = nullptr;
     if ((d_gyield || d_yield) && n_segs > 0) {
         int block = c->upar.block > 0 ? c->upar.block : 256;
         int per_sm = c->upar.ctas_per_sm > 0 ? c->upar.ctas_per_sm : 3 * 256 / block;
@@ -977,18 +1055,28 @@ extern "C" clight_status clight_trace_adjoint(clight_ctx *c, const clight_segmen
             Oc.soft_w = soft_w;
             CK(cudaMemsetAsync(c->adj_ctr.p, 0, sizeof(unsigned long long) * CTR_N, s));
             CK(launch_soft_candidates(d_segs, n_segs, c->atm, c->tel, P, Oc, (int)grid, block, s));
-            unsigned long long cur = 0;
-            CK(cudaMemcpyAsync(&cur, c->adj_ctr.p + CTR_CURSOR, sizeof(cur), cudaMemcpyDeviceToHost, s));
+            unsigned long long hc[CTR_N];
+            CK(cudaMemcpyAsync(hc, c->adj_ctr.p, sizeof(hc), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
-            n_cand = (int64_t)cur;
+            if (hc[CTR_STATS + ST_STATUS] & (1ull << CLIGHT_ERR_LIMIT)) return CLIGHT_ERR_LIMIT;
+            n_cand = (int64_t)hc[CTR_CURSOR];
             if (n_cand <= cap) break;
             if (attempt == 1) return CLIGHT_ERR_LIMIT;
             cap = n_cand + n_cand / 8 + 1024;
         }
+        const int64_t tiles = std::max<int64_t>(1, (cap + sort_tile_items() - 1) / sort_tile_items());
+        if (c->adj_keys_alt.ensure(cap, g) || c->adj_vals.ensure(cap, g) || c->adj_vals_alt.ensure(cap, g) ||
+            c->adj_hist.ensure(256 * tiles, g) || c->adj_bsums.ensure(scan_block_sums_needed(256 * tiles), g))
+            return CLIGHT_ERR_CUDA;
+        unsigned long long *kin = c->adj_cand.p, *kout = c->adj_keys_alt.p;
+        uint32_t *vin = c->adj_vals.p, *vout = c->adj_vals_alt.p;
+        CK(radix_sort_pairs(&kin, &vin, &kout, &vout, c->adj_ctr.p, cap, P.seg_bits + P.k_bits, c->adj_hist.p,
+                            c->adj_bsums.p, tiles, s));
+        cand = kin;
     }
-    CK(launch_adjoint(d_segs, c->adj_cand.p, n_cand, d_hits, n_hits, d_gx, d_gy, d_gt, d_gyield, d_yield, c->atm,
-                      c->tel, P, soft_s, soft_w, (float)c->uatm.K, (float)c->uatm.L0, c->adj_partial.p, blocks,
-                      c->adj_out.p, s));
+    CK(launch_adjoint(d_segs, cand, n_cand, d_hits, n_hits, d_gx, d_gy, d_gt, d_gyield, c->adj_yfix.p, d_yield,
+                      n_groups, c->atm, c->tel, P, soft_s, soft_w, (float)c->uatm.K, (float)c->uatm.L0,
+                      c->adj_partial.p, blocks, c->adj_out.p, s));
     double out[10];
     CK(cudaMemcpyAsync(out, c->adj_out.p, sizeof(double) * (size_t)np, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));

@@ -24,6 +24,7 @@ struct DevCell {
 struct DevAtm {
     int n_layers, n_cells, spherical, refraction, absorption, pad;
     float h_lo[kMaxLayers], kb[kMaxLayers], rb[kMaxLayers], nl2c[kMaxLayers];
+    float kb_lo[kMaxLayers], nl2c_lo[kMaxLayers];   // low words: kb, nl2c as FP32 pairs
     double h_lo_d[kMaxLayers], kb_d[kMaxLayers], rb_d[kMaxLayers], inv_c_d[kMaxLayers];
     float h_top, h_obs, R_E, r_obs, inv_r_obs;  // binary32 copies
     double inv_r_obs_d;
@@ -106,6 +107,8 @@ struct DevPar {
     int cut_nx, cut_ny;
     float cut_gx0, cut_gy0, cut_inv_gs;
     int prop;                    // CLIGHT_PROP_*
+    int cull;                    // 1: rays provably clear of every telescope skip the quadrature
+    int chunk;                   // groups of 32 steps per work claim (two-pass first kernel)
     // fluorescence beaming: on/off, cone centre and radius
     int beam, roulette;
     float beam_cx, beam_cy, beam_cz, beam_r;
@@ -129,7 +132,7 @@ struct DevOut {
 // Offsets inside DevOut::ctr.
 enum { CTR_WORK = 0, CTR_CURSOR = 1, CTR_STATS = 2, CTR_DEFER = 14, CTR_DEFER_WORK = 15, CTR_N = 16 };
 enum { ST_RAYS = 0, ST_ESCAPED, ST_UNDER, ST_TURNED, ST_REACHED, ST_HITS, ST_GUARDED, ST_STATUS, ST_CELLS, ST_CUT,
-       ST_SKIPPED, ST_N };
+       ST_SKIPPED, ST_DEFERRED, ST_N };
 static_assert(CTR_STATS + ST_N <= CTR_DEFER, "counter layout");
 // Status bit (above the CLIGHT_ERR_* codes) of a launch whose deferred-ray
 // queue filled; the host runs such a call again.
@@ -184,9 +187,14 @@ int fused_smem_bytes(int block, const DevTel &T);
 
 // tangent-linear adjoint (adjoint_kernels.cu)
 int adjoint_params(int n_layers);   // tangents carried: >= n_layers + 2
+// cand: the candidate rays (local step << P.k_bits | bunch), sorted; yfix:
+// n_groups accumulators of the soft yield in units of 2^-24 photons, zeroed
+// by the caller (integer sums: the same bits in any order), converted into
+// yield when that is not NULL.
 cudaError_t launch_adjoint(const clight_segment *segs, const unsigned long long *cand, int64_t n_cand,
                            const clight_hit *hits, int64_t n_hits,
-                           const float *gx, const float *gy, const float *gt, const double *gY, double *yield,
+                           const float *gx, const float *gy, const float *gt, const double *gY,
+                           unsigned long long *yfix, double *yield, int64_t n_groups,
                            const DevAtm &A, const DevTel &T, const DevPar &P, float soft_s, float soft_w, float K,
                            float L0, double *partial, int blocks, double *d_out, cudaStream_t s);
 
@@ -201,6 +209,12 @@ struct SortScratch {
 };
 int sort_tile_items();
 int64_t scan_block_sums_needed(int64_t n);
+// Stable LSD radix sort of the first ctr[CTR_CURSOR] (key, value) pairs by
+// the low key_bits bits of the key (nothing when that count exceeds
+// capacity); the sorted pairs end in (*kin, *vin), the pointers swapped.
+cudaError_t radix_sort_pairs(unsigned long long **kin, uint32_t **vin, unsigned long long **kout, uint32_t **vout,
+                             const unsigned long long *ctr, int64_t capacity, int key_bits, uint32_t *hist,
+                             uint32_t *block_sums, int64_t tiles, cudaStream_t s);
 cudaError_t launch_sort_and_finalize(const DevOut &O, const SortScratch &S, int key_bits,
                                      int group_shift, int64_t n_groups, clight_hit *out,
                                      int64_t *counts, double *sums, cudaStream_t s);

@@ -178,6 +178,65 @@ template <class T, bool SPH> __device__ __forceinline__ T altitude(const DevAtm 
     return Num<T>::div(num, Num<T>::sqr(x * x + y * y + zc * zc) + RE);
 }
 
+// ------------------------------------------------------------------ pair refractivity
+// Near the Cherenkov threshold beta n - 1 = delta - eps - eps delta is a
+// small difference, whose relative error is that of delta times about
+// kappa / 2, kappa = (delta + eps) / (beta n - 1).  binary32 delta is good to
+// ~1e-6 (the millimetre rounding of the altitude, the exponential), so where
+// kappa is large the step's refractivity is recomputed in FP32 pairs.
+struct DfConst { float hi, lo; };
+__host__ __device__ constexpr DfConst df_const(double x) { return {(float)x, (float)(x - (double)(float)x)}; }
+
+// 2^a for a pair a (|a| < 120): a = n + f with n the integer nearest a.hi;
+// 2^f = (e^x)^8 with x = f ln(2) / 8 (|x| < 0.044), e^x by its Taylor
+// polynomial of degree 7 (truncation below 4e-16) in pair arithmetic, then
+// three squarings and an exact scaling by 2^n.
+__device__ __forceinline__ df df_exp2(df a)
+{
+    constexpr DfConst ln2_8 = df_const(0.69314718055994530942 / 8.0);
+    constexpr DfConst c3 = df_const(1.0 / 6.0), c4 = df_const(1.0 / 24.0), c5 = df_const(1.0 / 120.0),
+                      c6 = df_const(1.0 / 720.0), c7 = df_const(1.0 / 5040.0);
+    const float n = rintf(a.hi);
+    const df f = two_sum(a.hi - n, a.lo);              // a.hi - n is exact
+    const df x = f * df{ln2_8.hi, ln2_8.lo};
+    df p = df{c7.hi, c7.lo};
+    p = p * x + df{c6.hi, c6.lo};
+    p = p * x + df{c5.hi, c5.lo};
+    p = p * x + df{c4.hi, c4.lo};
+    p = p * x + df{c3.hi, c3.lo};
+    p = p * x + 0.5f;
+    p = p * x + 1.0f;
+    p = p * x + 1.0f;
+    p = p * p;
+    p = p * p;
+    p = p * p;
+    const float sc = __uint_as_float((uint32_t)((int)n + 127) << 23);   // 2^n, exact
+    return {p.hi * sc, p.lo * sc};
+}
+
+// Refractivity at the midpoint of a step (start x0, y0, z0 and unit
+// direction d as pairs, length L) in FP32 pairs: the altitude without
+// cancellation, delta = kb 2^(h nl2c) with both constants as pairs.
+template <bool SPH>
+__device__ __forceinline__ df delta_pair(const DevAtm &A, df x0, df y0, df z0, df dx, df dy, df dz, float L)
+{
+    const float hL = 0.5f * L;
+    const df xm = x0 + dx * hL, ym = y0 + dy * hL, zm = z0 + dz * hL;
+    df h = zm;
+    if (SPH) {
+        const df RE = {A.re_hi, A.re_lo};
+        const df zc = zm + RE;
+        const df num = xm * xm + ym * ym + zm * (zc + RE);
+        h = num / (df_sqrt(xm * xm + ym * ym + zc * zc) + RE);
+    }
+    if (h.hi >= A.h_top) return {0.0f, 0.0f};
+    int i = 0;
+#pragma unroll
+    for (int j = 1; j < kMaxLayers; ++j)
+        if (j < A.n_layers && h.hi >= A.h_lo[j]) i = j;
+    return df{A.kb[i], A.kb_lo[i]} * df_exp2(df{A.nl2c[i], A.nl2c_lo[i]} * h);
+}
+
 // ------------------------------------------------------------------ segment
 // Everything one track step contributes to its photons (Sec. 1.2: the
 // atmosphere is homogeneous over a step, so theta_c and the yield are
@@ -208,6 +267,22 @@ __device__ __forceinline__ bool finite_f(float v) { return (__float_as_uint(v) &
 __device__ __forceinline__ bool finite_d(double v)
 {
     return ((unsigned long long)__double_as_longlong(v) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
+}
+
+// A step record from its four 16-byte words, field by field, so that it
+// stays in registers (no copy through local memory).
+__device__ __forceinline__ clight_segment seg_from_words(float4 a, float4 b, float4 c, float4 d)
+{
+    clight_segment s;
+    s.x = __hiloint2double(__float_as_int(a.y), __float_as_int(a.x));
+    s.y = __hiloint2double(__float_as_int(a.w), __float_as_int(a.z));
+    s.z = __hiloint2double(__float_as_int(b.y), __float_as_int(b.x));
+    s.t0 = __hiloint2double(__float_as_int(b.w), __float_as_int(b.z));
+    s.dx = c.x; s.dy = c.y; s.dz = c.z; s.L = c.w;
+    s.eps = d.x; s.dE = d.y;
+    s.charge = __float_as_int(d.z);
+    s.shower = __float_as_uint(d.w);
+    return s;
 }
 
 __device__ __forceinline__ bool segment_ok(const clight_segment &s, const DevPar &P)
@@ -689,6 +764,15 @@ __device__ void load_segment_f(const clight_segment &s, int64_t seg_global, cons
     float g1 = __fmaf_rn(-eps, dl, dl - eps);
     // error bound of g1 (delta known to ~1.5e-6 relative; generous factor)
     float eg = 4.0e-6f * dl + 2.4e-7f * (dl + eps);
+    // near the threshold (kappa = (delta + eps) / g1 above 16, or the sign of
+    // g1 not certain) the refractivity in FP32 pairs: g1 to ~1e-12 relative
+    if (!(DISP && A.disp) && z2 > 0.0f && s.L > 0.0f && g1 > -eg && 16.0f * g1 < dl + eps) {
+        const df dlp = delta_pair<SPH>(A, g.x0, g.y0, g.z0, df{g.dx, g.lx}, df{g.dy, g.ly}, df{g.dz, g.lz}, s.L);
+        const df g1p = (dlp - eps) - dlp * eps;
+        dl = p_f(dlp);
+        g1 = p_f(g1p);
+        eg = 1.0e-11f * (dl + eps);
+    }
     bool guard = false;
     float Nc = 0.0f;
     if (DISP && A.disp) {
@@ -1176,7 +1260,7 @@ __device__ __forceinline__ void trace_ray(const Seg<T, P> &g, int64_t seg_global
     else if (turned) { o.status = 3; }
     else if (grazing) { o.status = 5; }
     bool go = o.status == 0;
-    if (CULL && sizeof(T) == 4 && go &&
+    if (CULL && sizeof(T) == 4 && go && Pp.cull &&
         clear_miss((float)xef, (float)yef, (float)zef, (float)dx, (float)dy, (float)dz, (float)he,
                    SPH ? (float)sqf * A.inv_r_obs : 0.0f, (float)gl, A, *Tl, clr, SPH, REFR, widen)) {
         o.status = 6;

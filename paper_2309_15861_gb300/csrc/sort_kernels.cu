@@ -281,6 +281,22 @@ k_group_sums(const clight_hit *__restrict__ hits, const int64_t *__restrict__ gs
     }
 }
 
+cudaError_t radix_sort_pairs(unsigned long long **kin, uint32_t **vin, unsigned long long **kout, uint32_t **vout,
+                             const unsigned long long *ctr, int64_t capacity, int key_bits, uint32_t *hist,
+                             uint32_t *block_sums, int64_t tiles, cudaStream_t s)
+{
+    for (int shift = 0; shift < key_bits; shift += 8) {
+        k_radix_hist<<<(unsigned)tiles, kSortThreads, 0, s>>>(*kin, ctr, capacity, shift, hist, tiles);
+        cudaError_t e = exclusive_scan(hist, 256 * tiles, block_sums, s);
+        if (e != cudaSuccess) return e;
+        k_radix_scatter<<<(unsigned)tiles, kSortThreads, 0, s>>>(*kin, *vin, *kout, *vout, ctr, capacity, shift,
+                                                                 hist, tiles);
+        unsigned long long *tk = *kin; *kin = *kout; *kout = tk;
+        uint32_t *tv = *vin; *vin = *vout; *vout = tv;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sort_and_finalize(const DevOut &O, const SortScratch &S, int key_bits, int group_shift,
                                      int64_t n_groups, clight_hit *out, int64_t *counts, double *sums,
                                      cudaStream_t s)
@@ -288,15 +304,9 @@ cudaError_t launch_sort_and_finalize(const DevOut &O, const SortScratch &S, int 
     const int64_t tiles = S.max_tiles;
     unsigned long long *kin = O.keys, *kout = S.keys_alt;
     uint32_t *vin = O.vals, *vout = S.vals_alt;
-    for (int shift = 0; shift < key_bits; shift += 8) {
-        k_radix_hist<<<(unsigned)tiles, kSortThreads, 0, s>>>(kin, O.ctr, O.capacity, shift, S.hist, tiles);
-        cudaError_t e = exclusive_scan(S.hist, 256 * tiles, S.block_sums, s);
-        if (e != cudaSuccess) return e;
-        k_radix_scatter<<<(unsigned)tiles, kSortThreads, 0, s>>>(kin, vin, kout, vout, O.ctr, O.capacity, shift,
-                                                                 S.hist, tiles);
-        unsigned long long *tk = kin; kin = kout; kout = tk;
-        uint32_t *tv = vin; vin = vout; vout = tv;
-    }
+    cudaError_t e = radix_sort_pairs(&kin, &vin, &kout, &vout, O.ctr, O.capacity, key_bits, S.hist, S.block_sums,
+                                     tiles, s);
+    if (e != cudaSuccess) return e;
     int gg = 4 * 152;
     k_gather<<<gg, 256, 0, s>>>(O.rec, vin, O.ctr, O.capacity, out);
     cudaMemsetAsync(S.gstart, 0, sizeof(int64_t) * n_groups, s);

@@ -258,22 +258,22 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
         int64_t s_first = (int64_t)grp * 32;
         if (s_first >= n_segs) break;
         int64_t si = s_first + lane;
-        clight_segment s;
-        float4 *sv = reinterpret_cast<float4 *>(&s);
+        float4 w0 = make_float4(0.f, 0.f, 0.f, 0.f), w1 = w0, w2 = w0, w3 = w0;
         if (PREF) {
             cp_async_wait_all();
             __syncwarp();
             if (si < n_segs) {
-                sv[0] = stage[lane * 4]; sv[1] = stage[lane * 4 + 1];
-                sv[2] = stage[lane * 4 + 2]; sv[3] = stage[lane * 4 + 3];
+                w0 = stage[lane * 4]; w1 = stage[lane * 4 + 1];
+                w2 = stage[lane * 4 + 2]; w3 = stage[lane * 4 + 3];
             }
             __syncwarp();
             grp_next = __shfl_sync(FULL_MASK, grp_next, 0);
             prefetch_group(stage, segs, n_segs, (int64_t)grp_next * 32, lane);
         } else if (si < n_segs) {
             const float4 *src = reinterpret_cast<const float4 *>(segs + si);
-            sv[0] = __ldg(src); sv[1] = __ldg(src + 1); sv[2] = __ldg(src + 2); sv[3] = __ldg(src + 3);
+            w0 = __ldg(src); w1 = __ldg(src + 1); w2 = __ldg(src + 2); w3 = __ldg(src + 3);
         }
+        const clight_segment s = seg_from_words(w0, w1, w2, w3);
         // ---- per-segment set-up, one segment per lane
         Seg<float, df> g;
         uint32_t nb = 0;
@@ -452,6 +452,11 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
                 RayOut<float, df> o;
                 trace_ray<float, df, true, SPH, REFR, FEAT, true>(q, seg_global, k, active, A, Pp, o, &Tl, clr, O.soft_w);
                 bool cand = active && soft_candidate<float, df>(o, A, Tl, O.soft_w, clr);
+                // key: local step << k_bits | bunch (sorted before the adjoint)
+                if (cand && Pp.k_bits < 32 && k >= (1u << Pp.k_bits)) {
+                    status_bits |= 1u << CLIGHT_ERR_LIMIT;
+                    cand = false;
+                }
                 unsigned m = __ballot_sync(FULL_MASK, cand);
                 if (m) {
                     unsigned long long base = 0;
@@ -459,7 +464,7 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
                     base = __shfl_sync(FULL_MASK, base, 0);
                     unsigned long long idx = base + __popc(m & lanemask_lt());
                     if (cand && (int64_t)idx < O.capacity)
-                        O.keys[idx] = ((unsigned long long)seg_local << 32) | (unsigned long long)k;
+                        O.keys[idx] = ((unsigned long long)seg_local << Pp.k_bits) | (unsigned long long)k;
                 }
                 nh = cand ? 1 : 0;
                 if (active) {
@@ -484,7 +489,328 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
         __syncwarp();
     }
     // ---- statistics: one atomic per warp and counter
-    const uint32_t vals[ST_N] = {c_rays, c_esc, c_under, c_turn, c_reach, c_hits, c_guard, 0u, c_cells, c_cut, c_skip};
+    const uint32_t vals[ST_N] = {c_rays, c_esc, c_under, c_turn, c_reach, c_hits, c_guard, 0u, c_cells, c_cut, c_skip, 0u};
+    flush_stats(vals, status_bits, O, lane);
+}
+
+// ------------------------------------------------------------------ classification pass
+// First pass of the two-pass path for the default feature set (no angular
+// cut, beaming or dispersion; either propagator).  It decides, for every
+// ray, what the full trace would conclude wherever that is certain -- 1
+// escapes, 2 emitted below the observation level, 6 reaches it and lands
+// provably clear of every telescope -- and queues the rest for
+// k_trace_deferred, as k_trace_fused<..., DEFER> does, with less work per
+// ray:
+//  - the Cherenkov bunches of a warp's 32 steps come first and the
+//    fluorescence bunches after them, so that a round of 32 rays rarely
+//    mixes the two code paths;
+//  - each round finds the step of every lane from one OR-reduction over the
+//    warp of the steps' start positions (no search per ray), and the step
+//    records are read with 128-bit shared loads;
+//  - for a Cherenkov step every photon direction lies on the cone of half-
+//    angle theta_c about the flight direction d, so the quantities the
+//    per-ray test bounds -- the smallest landing zenith cosine mu, the
+//    refraction displacement coefficient and the hit search radius -- are
+//    bounded once per step by their worst case over the cone (the landing
+//    zenith angle is at most the emission zenith angle of d plus theta_c,
+//    widened by the step length over the Earth radius).  Each bound is at
+//    least the per-ray value clear_miss would use, so a ray skipped here
+//    would be skipped by the per-ray test too.  A step whose cone comes
+//    within about 87 degrees of the horizon (or turns rays before the
+//    observation level) has no such bound and its rays take the per-ray
+//    test;
+//  - the emission altitude is linear along the step (h_mid + (l - L/2) dh/dl:
+//    off by at most L^2 / (2 R_E), micrometres, against a 10 cm margin).
+struct alignas(16) ClsRec {
+    float x0, y0, z0, L;        // start of the step (binary32), length
+    float dx, dy, dz, h_mid;    // unit direction, midpoint altitude
+    float ax, ay, az, hd;       // cos(theta_c) d, dh/dl along the step
+    float b1x, b1y, b1z, rsb;   // sin(theta_c) M_Rod x, search radius without the refraction term
+    float b2x, b2y, b2z, cB;    // sin(theta_c) M_Rod y, refraction term per metre of height
+    uint32_t nc, pad0, pad1, pad2;
+};
+static_assert(sizeof(ClsRec) == 96, "ClsRec layout");
+constexpr int kClsVmax = 64;                     // virtual steps per warp: 32 Cherenkov + 32 fluorescence
+constexpr int kClsWarpBytes = 32 * (int)sizeof(ClsRec) + kClsVmax * 8;
+constexpr uint32_t kVGated = 1u << 6;            // virtual-step flag: the step's Cherenkov bounds hold
+
+static int cls_smem_bytes(int block, const DevTel &T)
+{
+    return (block / 32) * (kClsWarpBytes + kStageBytes) + (T.clr ? T.clr_bytes : 0);
+}
+
+// Per-ray part of the classification of a Cherenkov ray of a gated step:
+// the per-step bounds stand in for the ray's own.
+template <bool SPH>
+__device__ __forceinline__ int classify_cherenkov_gated(const ClsRec &R, float ell, float dgx, float dgy, float dgz,
+                                                        const DevAtm &A, const DevTel &Tl, const uint8_t *clr)
+{
+    // escape is impossible and every ray reaches the observation level (gate)
+    const float he = R.h_mid + (ell - 0.5f * R.L) * R.hd;
+    if (he < A.h_obs - 0.1f) return 2;
+    if (!(he > A.h_obs + 0.1f)) return 0;
+    const float xe = R.x0 + ell * R.dx, ye = R.y0 + ell * R.dy, ze = R.z0 + ell * R.dz;
+    const float tp = (ze - A.h_obs) * rcp_approx(-dgz);
+    const float Xv = xe + tp * dgx, Yv = ye + tp * dgy;
+    const float zeta = SPH ? (Xv * Xv + Yv * Yv) * A.inv_r_obs : 0.0f;
+    const float rs = R.rsb + R.cB * ((he - A.h_obs) + zeta);
+    if (Xv + rs < Tl.xmin || Xv - rs > Tl.xmax || Yv + rs < Tl.ymin || Yv - rs > Tl.ymax) return 6;
+    if (clr) {
+        const float fx = (Xv - Tl.cx0) * Tl.inv_cgs, fy = (Yv - Tl.cy0) * Tl.inv_cgs;
+        if (fx >= 0.0f && fy >= 0.0f && fx < (float)Tl.cnx && fy < (float)Tl.cny)
+            return rs < (float)clr[floor_small(fy) * Tl.cnx + floor_small(fx)] * kClrQuantum ? 6 : 0;
+    }
+    return 0;
+}
+
+// The per-ray test (ray direction d, emission at l along the step), as in
+// skip_ray: for fluorescence photons and the Cherenkov photons of steps
+// without per-step bounds.
+template <bool SPH, bool REFR>
+__device__ __forceinline__ int classify_ray(const ClsRec &R, float ell, float dx, float dy, float dz,
+                                            const DevAtm &A, const DevTel &Tl, const uint8_t *clr)
+{
+    const float xe = R.x0 + ell * R.dx, ye = R.y0 + ell * R.dy, ze = R.z0 + ell * R.dz;
+    const float Rz = ze + A.R_E;
+    const float out = SPH ? dx * xe + dy * ye + dz * Rz : dz;
+    const float mo = SPH ? 1.0e-3f * Rz : 1.0e-6f;
+    if (out > mo) return 1;
+    if (!(out < -mo)) return 0;
+    const float he = R.h_mid + (ell - 0.5f * R.L) * R.hd;
+    if (he < A.h_obs - 0.1f) return 2;
+    if (!(he > A.h_obs + 0.1f) || !(dz < -0.05f)) return 0;
+    float cos_obs = 0.0f;
+    if (SPH) {
+        const float c1 = dy * Rz - dz * ye, c2 = dz * xe - dx * Rz, c3 = dx * ye - dy * xe;
+        const float so = sqrt_approx(c1 * c1 + c2 * c2 + c3 * c3) * A.inv_r_obs;
+        const float co2 = 1.0f - so * so;
+        if (!(so < 1.0f) || !(co2 > 2.1f * A.delta_max + 2.6e-3f)) return 0;
+        cos_obs = sqrt_approx(co2);
+    }
+    return clear_miss(xe, ye, ze, dx, dy, dz, he, cos_obs, 1.0f, A, Tl, clr, SPH, REFR) ? 6 : 0;
+}
+
+template <bool SPH, bool REFR>
+__global__ void __launch_bounds__(256, 4)
+k_classify(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid_constant__ DevAtm A,
+           const __grid_constant__ DevTel Tl, const __grid_constant__ DevPar Pp, const __grid_constant__ DevOut O)
+{
+    extern __shared__ __align__(16) unsigned char smem_c[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    ClsRec *rec = reinterpret_cast<ClsRec *>(smem_c + warp * kClsWarpBytes);
+    uint2 *vl = reinterpret_cast<uint2 *>(smem_c + warp * kClsWarpBytes + 32 * sizeof(ClsRec));
+    float4 *stage = reinterpret_cast<float4 *>(smem_c + nwarp * kClsWarpBytes + warp * kStageBytes);
+    const uint8_t *clr = nullptr;
+    if (Tl.clr) {
+        uint4 *dst = reinterpret_cast<uint4 *>(smem_c + nwarp * (kClsWarpBytes + kStageBytes));
+        const uint4 *src = reinterpret_cast<const uint4 *>(Tl.clr);
+        for (int i = threadIdx.x; i < (Tl.clr_bytes >> 4); i += blockDim.x) dst[i] = __ldg(src + i);
+        __syncthreads();
+        clr = reinterpret_cast<const uint8_t *>(dst);
+    }
+    // bound pieces that depend on the array and the atmosphere only
+    const float dzmax = fmaxf(fabsf(Tl.zmax - A.h_obs), fabsf(Tl.zmin - A.h_obs));
+    const float co2_min = 2.1f * A.delta_max + 2.6e-3f;
+    uint32_t c_rays = 0, c_esc = 0, c_under = 0, c_skip = 0, c_guard = 0;
+    unsigned status_bits = 0;
+    // queue appends are completed one round later, so that the atomic that
+    // reserves their slots returns while the next round is worked on
+    unsigned pend_m = 0;
+    unsigned long long pend_base = 0, pend_entry = 0;
+    auto complete_appends = [&](unsigned lt_mask) {
+        if (pend_m) {
+            const unsigned long long qb = __shfl_sync(FULL_MASK, pend_base, 0);
+            if (pend_m & (1u << lane)) {
+                const unsigned long long qi = qb + __popc(pend_m & lt_mask);
+                if ((int64_t)qi < O.defer_cap) O.defer[qi] = pend_entry;
+                else status_bits |= 1u << kBitDeferFull;
+            }
+            pend_m = 0;
+        }
+    };
+    // work stealing: a claim is Pp.chunk consecutive groups of 32 steps; the
+    // next claim's atomic is issued one group before it is needed, and each
+    // group's records are copied in while the group before is worked on
+    const unsigned long long chunk = (unsigned long long)Pp.chunk;
+    unsigned long long cur = 0, end = 0;
+    {
+        unsigned long long c = 0;
+        if (lane == 0) c = atomicAdd(O.ctr + CTR_WORK, 1ull);
+        cur = __shfl_sync(FULL_MASK, c, 0) * chunk;
+        end = cur + chunk;
+    }
+    prefetch_group(stage, segs, n_segs, (int64_t)cur * 32, lane);
+    for (;;) {
+        const unsigned long long grp = cur;
+        const bool claim = cur + 1 == end;
+        unsigned long long c = 0;
+        if (claim && lane == 0) c = atomicAdd(O.ctr + CTR_WORK, 1ull);
+        const int64_t s_first = (int64_t)grp * 32;
+        if (s_first >= n_segs) break;
+        const int64_t si = s_first + lane;
+        float4 w0 = make_float4(0.f, 0.f, 0.f, 0.f), w1 = w0, w2 = w0, w3 = w0;
+        cp_async_wait_all();
+        __syncwarp();
+        if (si < n_segs) {
+            w0 = stage[lane * 4]; w1 = stage[lane * 4 + 1];
+            w2 = stage[lane * 4 + 2]; w3 = stage[lane * 4 + 3];
+        }
+        __syncwarp();
+        const clight_segment s = seg_from_words(w0, w1, w2, w3);
+        if (claim) {
+            cur = __shfl_sync(FULL_MASK, c, 0) * chunk;
+            end = cur + chunk;
+        } else {
+            ++cur;
+        }
+        prefetch_group(stage, segs, n_segs, (int64_t)cur * 32, lane);
+
+        // ---- per-step set-up: the counts exactly as the second pass forms them
+        uint32_t nc = 0, nf = 0;
+        ClsRec r;
+        bool gated = false;
+        if (si < n_segs) {
+            Seg<float, df> g;
+            load_segment_f<SPH, false, false>(s, Pp.seg_base + si, A, Pp, g);
+            if (g.bad) status_bits |= 1u << g.bad;
+            c_guard += g.guarded;
+            nc = g.n_c;
+            nf = g.n_f;
+            if (nc > 0x7fffffffu || nf > 0x7fffffffu - nc) { status_bits |= 1u << CLIGHT_ERR_LIMIT; nc = nf = 0; }
+            const float ct = 1.0f - g.kappa, st = g.sin_tc;
+            r.x0 = g.x0.hi; r.y0 = g.y0.hi; r.z0 = g.z0.hi; r.L = g.L;
+            r.dx = g.dx; r.dy = g.dy; r.dz = g.dz; r.h_mid = g.h_mid;
+            r.ax = ct * g.dx; r.ay = ct * g.dy; r.az = ct * g.dz;
+            r.b1x = st * g.e1x; r.b1y = st * g.e1y; r.b1z = st * g.e1z;
+            r.b2x = st * g.e2x; r.b2y = st * g.e2y; r.b2z = st * g.e2z;
+            // dh/dl: the step direction's component along the local vertical
+            float sdz = -g.dz;                                  // cos of the step's zenith angle (flat frame)
+            float szd = sqrtf(g.dx * g.dx + g.dy * g.dy);        // its sine
+            float cps = sdz, sps = szd;                          // the same about the Earth radius at the start
+            if (SPH) {
+                const float Rz0 = r.z0 + A.R_E;
+                const float r0 = sqrtf(r.x0 * r.x0 + r.y0 * r.y0 + Rz0 * Rz0);
+                const float ir0 = 1.0f / r0;
+                const float c1 = g.dy * Rz0 - g.dz * r.y0, c2 = g.dz * r.x0 - g.dx * Rz0, c3 = g.dx * r.y0 - g.dy * r.x0;
+                sps = sqrtf(c1 * c1 + c2 * c2 + c3 * c3) * ir0;
+                cps = -(g.dx * r.x0 + g.dy * r.y0 + g.dz * Rz0) * ir0;
+                r.hd = -cps;
+            } else {
+                r.hd = g.dz;
+            }
+            // Cherenkov bounds over the cone (half-angle theta_c: cos ct, sin st)
+            r.rsb = 0.0f; r.cB = 0.0f;
+            if (nc > 0) {
+                // -d_gamma,z >= cos(zeta_d + theta_c)
+                const float dzlo = sdz * ct - szd * st - 4.0e-6f;
+                float cobs_lo = dzlo;
+                bool ok = dzlo > 0.05f;
+                if (SPH) {
+                    // landing zenith sine: (r_e / r_obs) sin(psi_e), psi_e <= psi_d + theta_c + L / r0
+                    const float csum = cps * ct - sps * st;
+                    const float Rz0 = r.z0 + A.R_E;
+                    const float r0 = sqrtf(r.x0 * r.x0 + r.y0 * r.y0 + Rz0 * Rz0);
+                    const float se = sps * ct + cps * st + (r.L + 1.0f) / r0 + 4.0e-6f;
+                    const float so = (r0 + r.L) * se * A.inv_r_obs * 1.000001f;
+                    const float co2 = 1.0f - so * so;
+                    ok = ok && csum > 0.0f && so < 1.0f && co2 > co2_min;
+                    cobs_lo = ok ? sqrtf(co2) * 0.999999f : 0.0f;
+                }
+                const float mu = fminf(cobs_lo, dzlo) - 1.0e-3f;
+                ok = ok && mu > 0.05f;
+                if (ok) {
+                    const float im = 1.0f / mu;
+                    const float sd = REFR ? 1.25f * sqrtf(1.0f - mu * mu) * A.delta_max : 0.0f;
+                    const float czb = dzlo - sd * im - 1.0e-5f;
+                    ok = czb > 0.05f;
+                    if (ok) {
+                        r.cB = sd * (im * im * im) * 1.0001f;
+                        r.rsb = ((Tl.Rmax + dzmax * sqrtf(1.0f - czb * czb)) / czb + 2.0e-3f + 0.05f) * 1.0001f +
+                                1.0e-3f;
+                    }
+                }
+                gated = ok;
+            }
+            r.nc = nc;
+        }
+        // ---- virtual steps: the Cherenkov steps with bunches, then the fluorescence ones
+        const unsigned bC = __ballot_sync(FULL_MASK, nc > 0), bF = __ballot_sync(FULL_MASK, nf > 0);
+        const unsigned lt = lanemask_lt();
+        uint32_t incC = nc, incF = nf;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t vc = __shfl_up_sync(FULL_MASK, incC, o), vf = __shfl_up_sync(FULL_MASK, incF, o);
+            if (lane >= o) { incC += vc; incF += vf; }
+        }
+        const uint32_t totC = __shfl_sync(FULL_MASK, incC, 31), totF = __shfl_sync(FULL_MASK, incF, 31);
+        const uint32_t eC = incC - nc, eF = totC + incF - nf;  // start positions in the group's ray sequence
+        if (totF > 0x7fffffffu - totC) { status_bits |= 1u << CLIGHT_ERR_LIMIT; continue; }
+        if (si < n_segs) rec[lane] = r;
+        if (nc > 0) vl[__popc(bC & lt)] = make_uint2(eC, (uint32_t)lane | (gated ? kVGated : 0u));
+        if (nf > 0) vl[__popc(bC) + __popc(bF & lt)] = make_uint2(eF, (uint32_t)lane | 32u);
+        __syncwarp();
+        const uint32_t total = totC + totF;
+        if (lane == 0) c_rays += total;
+        // ---- the rays, 32 per round
+        int carry = -1;
+        for (uint32_t base = 0; base < total; base += 32) {
+            uint32_t bits = 0;
+            if (nc > 0 && eC - base < 32u) bits |= 1u << (eC - base);
+            if (nf > 0 && eF - base < 32u) bits |= 1u << (eF - base);
+            const unsigned M = __reduce_or_sync(FULL_MASK, bits);
+            const int idx = carry + __popc(M & (lt | (1u << lane)));
+            carry += __popc(M);
+            const uint32_t pos = base + (uint32_t)lane;
+            const bool active = pos < total;
+            int cls = -1;
+            int64_t seg_local = 0;
+            uint32_t kq = 0;
+            if (active) {
+                const uint2 v = vl[idx];
+                const int l = (int)(v.y & 31u);
+                const uint32_t proc = (v.y >> 5) & 1u;
+                const uint32_t kk = pos - v.x;
+                seg_local = s_first + l;
+                const int64_t seg_global = Pp.seg_base + seg_local;
+                const uint4 x = philox4x32_10(make_uint4((uint32_t)(uint64_t)seg_global,
+                                                         (uint32_t)((uint64_t)seg_global >> 32), kk, proc),
+                                              Pp.seed, Pp.stream);
+                const float u1 = u01<float>(x.y), u2 = u01<float>(x.z);
+                float sn, cs;
+                Num<float>::sincos2pi(u2, &sn, &cs);
+                const ClsRec &R = rec[l];
+                const float ell = u1 * R.L;
+                if (proc == 0) {
+                    kq = kk;
+                    const float dgx = R.ax + (cs * R.b1x + sn * R.b2x);
+                    const float dgy = R.ay + (cs * R.b1y + sn * R.b2y);
+                    const float dgz = R.az + (cs * R.b1z + sn * R.b2z);
+                    cls = (v.y & kVGated) ? classify_cherenkov_gated<SPH>(R, ell, dgx, dgy, dgz, A, Tl, clr)
+                                          : classify_ray<SPH, REFR>(R, ell, dgx, dgy, dgz, A, Tl, clr);
+                } else {
+                    kq = R.nc + kk;
+                    const float u3 = u01<float>(x.w);
+                    const float cz = 2.0f * u3 - 1.0f;
+                    const float sz = sqrtf((1.0f - cz) * (1.0f + cz));
+                    cls = classify_ray<SPH, REFR>(R, ell, sz * cs, sz * sn, cz, A, Tl, clr);
+                }
+                c_esc += cls == 1;
+                c_under += cls == 2;
+                c_skip += cls == 6;
+            }
+            const bool push = cls == 0;
+            complete_appends(lt);
+            const unsigned m = __ballot_sync(FULL_MASK, push);
+            if (m) {
+                if (lane == 0) pend_base = atomicAdd(O.ctr + CTR_DEFER, (unsigned long long)__popc(m));
+                pend_m = m;
+                pend_entry = ((unsigned long long)seg_local << 32) | (unsigned long long)kq;
+            }
+        }
+        __syncwarp();
+    }
+    complete_appends(lanemask_lt());
+    const uint32_t vals[ST_N] = {c_rays, c_esc, c_under, 0u, c_skip, 0u, c_guard, 0u, 0u, 0u, c_skip, 0u};
     flush_stats(vals, status_bits, O, lane);
 }
 
@@ -510,7 +836,7 @@ k_trace_deferred(const clight_segment *__restrict__ segs, const __grid_constant_
         clr = reinterpret_cast<const uint8_t *>(dst);
     }
     const int64_t n = min((int64_t)O.ctr[CTR_DEFER], O.defer_cap);
-    uint32_t c_esc = 0, c_under = 0, c_turn = 0, c_reach = 0, c_hits = 0, c_cells = 0;
+    uint32_t c_esc = 0, c_under = 0, c_turn = 0, c_reach = 0, c_hits = 0, c_cells = 0, c_def = 0;
     unsigned status_bits = 0;
     for (;;) {
         unsigned long long grp = 0;
@@ -523,10 +849,8 @@ k_trace_deferred(const clight_segment *__restrict__ segs, const __grid_constant_
         const int64_t seg_local = (int64_t)(e >> 32);
         const uint32_t k = (uint32_t)e;
         const int64_t seg_global = Pp.seg_base + seg_local;
-        clight_segment s;
         const float4 *src = reinterpret_cast<const float4 *>(segs + seg_local);
-        float4 *dst = reinterpret_cast<float4 *>(&s);
-        dst[0] = __ldg(src); dst[1] = __ldg(src + 1); dst[2] = __ldg(src + 2); dst[3] = __ldg(src + 3);
+        const clight_segment s = seg_from_words(__ldg(src), __ldg(src + 1), __ldg(src + 2), __ldg(src + 3));
         Seg<float, df> g;
         load_segment_f<SPH, EXT, (FEAT & FEAT_DISP) != 0>(s, seg_global, A, Pp, g);
         RayOut<float, df> o;
@@ -537,9 +861,10 @@ k_trace_deferred(const clight_segment *__restrict__ segs, const __grid_constant_
             c_esc += o.status == 1; c_under += o.status == 2; c_turn += o.status == 3;
             c_reach += o.status == 0 || o.status == 5;
             c_cells += o.status == 0 ? o.cells : 0;
+            ++c_def;
         }
     }
-    const uint32_t vals[ST_N] = {0u, c_esc, c_under, c_turn, c_reach, c_hits, 0u, 0u, c_cells, 0u, 0u};
+    const uint32_t vals[ST_N] = {0u, c_esc, c_under, c_turn, c_reach, c_hits, 0u, 0u, c_cells, 0u, 0u, c_def};
     flush_stats(vals, status_bits, O, lane);
 }
 
@@ -574,7 +899,7 @@ k_trace_fp64(const clight_segment *__restrict__ segs, int64_t n_segs, const __gr
             c_hits += hit_test<double, double, false>(o, i, seg_global, k, g.shower, A, Tl, Pp, O, status_bits);
         }
     }
-    uint32_t vals[ST_N] = {c_rays, c_esc, c_under, c_turn, c_reach, c_hits, 0u, 0u, c_cells, c_cut, 0u};
+    uint32_t vals[ST_N] = {c_rays, c_esc, c_under, c_turn, c_reach, c_hits, 0u, 0u, c_cells, c_cut, 0u, 0u};
     for (int q = 0; q < ST_N; ++q)
         if (vals[q] && q != ST_STATUS) atomicAdd(O.ctr + CTR_STATS + q, (unsigned long long)vals[q]);
     if (status_bits) atomicOr(O.ctr + CTR_STATS + ST_STATUS, (unsigned long long)status_bits);
@@ -588,8 +913,15 @@ static void launch_deferred_pair(const clight_segment *segs, int64_t n_segs, con
     constexpr bool EXT = (FEAT & FEAT_EXT) != 0;
     // the queue's fill and work counters
     cudaMemsetAsync(O.ctr + CTR_DEFER, 0, 2 * sizeof(unsigned long long), s);
-    k_trace_fused<df, SPH, REFR, false, false, FEAT, true>
-        <<<grid, block, fused_smem_bytes_f(block, T, EXT, true), s>>>(segs, n_segs, A, T, Pp, O);
+    if constexpr ((FEAT & (FEAT_EXT | FEAT_DISP)) == 0) {
+        // the default feature set: the classification kernel
+        const int smem = cls_smem_bytes(block, T);
+        cudaFuncSetAttribute(k_classify<SPH, REFR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_classify<SPH, REFR><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
+    } else {
+        k_trace_fused<df, SPH, REFR, false, false, FEAT, true>
+            <<<grid, block, fused_smem_bytes_f(block, T, EXT, true), s>>>(segs, n_segs, A, T, Pp, O);
+    }
     // the second pass as many CTAs as are resident at once (its own
     // register and shared-memory limits)
     const int smem2 = !EXT && T.clr ? T.clr_bytes : 0;
@@ -818,6 +1150,7 @@ extern "C" clight_status clight_trace_noalloc(clight_ctx *ctx, const clight_segm
         h_stats->cells = (int64_t)h[CTR_STATS + ST_CELLS];
         h_stats->cut = (int64_t)h[CTR_STATS + ST_CUT];
         h_stats->skipped = (int64_t)h[CTR_STATS + ST_SKIPPED];
+        h_stats->deferred = (int64_t)h[CTR_STATS + ST_DEFERRED];
     }
     if ((int64_t)h[CTR_CURSOR] > hit_capacity) return CLIGHT_ERR_HIT_CAPACITY;
     if (bits & (1ull << CLIGHT_ERR_BAD_SEGMENT)) return CLIGHT_ERR_BAD_SEGMENT;

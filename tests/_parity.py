@@ -3,10 +3,10 @@
 Tolerances (from the path's stated accuracy):
   x_rel, y_rel   1 cm
   t              0.01 ns
-  weight         2e-5 + 8e-6 kappa relative, kappa = (delta + eps)/(beta n - 1)
-                 the condition number of the threshold factor: binary32
-                 delta carries ~1e-6 relative error, which beta n - 1
-                 amplifies by kappa near the Cherenkov threshold
+  weight         2e-5 relative (near the Cherenkov threshold, where binary32
+                 would lose kappa/2 of its digits in beta n - 1, kappa =
+                 (delta + eps)/(beta n - 1), the kernels compute the
+                 refractivity in FP32 pairs from kappa = 16 on)
   lambda         2e-6 relative
   cx, cy         2e-6 absolute
 A hit whose impact parameter lies within 1 cm of the aperture edge may be
@@ -31,25 +31,9 @@ def _key(h):
 
 
 def weight_tolerance(segs, ref, atm, par, seg_base=0):
-    """Per-hit weight tolerance of the oracle hits (see the module docstring)."""
-    import dataclasses
-    import oracle as O
-    # the angular cut only removes whole steps: the kept steps' yields are the uncut ones
-    if getattr(par, "cut_mode", 0):
-        par = dataclasses.replace(par, cut_mode=0)
-    tol = np.full(len(ref), TOL_W)
-    cache = {}
-    for i, h in enumerate(ref):
-        s = int(h["seg"]) - seg_base
-        if s not in cache:
-            y = O.yield_of(segs[s], atm, par)
-            g1 = 1.0 / y["cos_tc"] - 1.0 if y["n_c"] > 0 else 0.0
-            eps = float(segs[s]["eps"])
-            cache[s] = (y["n_c"], (y["delta"] + eps) / g1 if g1 > 0 else 0.0)
-        nc, kappa = cache[s]
-        if h["k"] < nc:
-            tol[i] = TOL_W + 8e-6 * kappa
-    return tol
+    """Per-hit weight tolerance of the oracle hits: the fixed bound TOL_W for
+    every hit (the arguments are kept for the callers)."""
+    return np.full(len(ref), TOL_W)
 
 
 def compare(gpu, ref, tels, edge=EDGE, tol_xy=TOL_XY, tol_t=TOL_T, ref_dperp_of=None, w_tol=None):

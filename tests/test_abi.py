@@ -30,8 +30,8 @@ def test_library_exports_every_declared_symbol():
 def test_record_layouts_match_the_header():
     assert I.SEG_DTYPE.itemsize == 64
     assert G.HIT_DTYPE.itemsize == 48
-    assert ctypes.sizeof(G.Stats) == 88
-    assert ctypes.sizeof(G.Params) == 184
+    assert ctypes.sizeof(G.Stats) == 96
+    assert ctypes.sizeof(G.Params) == 192
     assert ctypes.sizeof(G.Atmosphere) == 8 + 3 * 64 + 7 * 8 + 8 + 16
     offs = {n: I.SEG_DTYPE.fields[n][1] for n in I.SEG_DTYPE.names}
     assert offs == {"x": 0, "y": 8, "z": 16, "t0": 24, "dx": 32, "dy": 36, "dz": 40, "L": 44,

@@ -25,11 +25,17 @@ def test_autotune_batch_then_parity_at_chosen_bunch():
         segs = torch.from_numpy(w.segments.view(np.uint8).reshape(-1)).cuda()
         cap = 1 << 20
         hits = torch.empty(cap * 48, dtype=torch.uint8, device="cuda")
-        t = ctx.autotune(segs, len(w.segments), w.n_showers, hits, cap, bunch_max=5.0, reps=2)
-        assert (t["block"], t["ctas_per_sm"]) in {(256, 3), (256, 2), (128, 6), (128, 4), (64, 12)}
-        assert t["cell_width"] in (1.0, 1.5)
-        assert t["bunch"] in (1.0, 2.0, 5.0) and t["n_tried"] == 1 + 5 * 2 * 3
-        assert 0 < t["best_ms"] <= 1.2 * t["default_ms"]
+        n = len(w.segments)
+        # a sample of a third of the steps, in blocks spread over every shower
+        t = ctx.autotune(segs, n, n // 3, w.n_showers, hits, cap, bunch_max=5.0, reps=5)
+        assert (t["block"], t["ctas_per_sm"]) in {(256, 0), (256, 4), (256, 3), (128, 8), (128, 6), (64, 16)}
+        assert t["cell_width"] in (1.0, 1.5) and t["work_chunk"] in (1, 2, 4)
+        assert t["bunch"] in (1.0, 2.0, 5.0)
+        # defaults, bunch 1 and 2, five shapes, two chunks, one cell width
+        assert t["n_tried"] == 1 + 2 + 5 + 2 + 1
+        assert 0 < t["n_sample"] <= n // 3 + 64 * 32
+        # the defaults compete: the choice is never slower by the tuner's own timing
+        assert 0 < t["best_ms"] <= t["default_ms"]
         # the context traces with the chosen settings; the oracle runs at the chosen bunch size
         par = dataclasses.replace(w.params, bunch=t["bunch"])
         tuned = I.Workload(w.name, w.segments, w.atmosphere, w.telescopes, par, n_showers=w.n_showers)
@@ -61,8 +67,10 @@ def test_autotune_rejects_bad_arguments():
         hits = torch.empty(1024 * 48, dtype=torch.uint8, device="cuda")
         for kw in ({"bunch_max": 0.0}, {"bunch_max": 5.0, "reps": 0}):
             with pytest.raises(G.ClightError):
-                ctx.autotune(segs, 1000, 1, hits, 1024, **kw)
+                ctx.autotune(segs, 1000, 1000, 1, hits, 1024, **kw)
         with pytest.raises(G.ClightError):
-            ctx.autotune(segs, 0, 1, hits, 1024, bunch_max=5.0)
+            ctx.autotune(segs, 1000, 0, 1, hits, 1024, bunch_max=5.0)
+        with pytest.raises(G.ClightError):
+            ctx.autotune(segs, 0, 100, 1, hits, 1024, bunch_max=5.0)
     finally:
         ctx.close()

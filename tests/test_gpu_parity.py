@@ -140,6 +140,71 @@ def test_deferred_queue_grows_when_full(ctx):
     np.testing.assert_array_equal(np.asarray(gc), np.asarray(rc))
 
 
+def _guard_steps(n=6000, seed=97):
+    """Hand-built steps over a dense array (31 x 31 telescopes at 10 m) that
+    exercise the precision guards of the yield: a third whose mean photon
+    number sits exactly on a bunch-count boundary (N / B an integer, so that
+    ceil(N / B) is decided in binary64), a third whose beta n - 1 is 1e-3,
+    1e-5 or 1e-7 of the refractivity (kappa up to 2e7: the refractivity in
+    FP32 pairs, and the binary64 guard for the narrowest cones), and a third
+    just below the threshold (no light on either side).  Directions within 2
+    degrees of the vertical, so that the narrow cones land on the array."""
+    atm = I.atmosphere_layered()
+    rng = np.random.default_rng(seed)
+    s = np.zeros(n, dtype=I.SEG_DTYPE)
+    s["x"] = rng.uniform(-150.0, 150.0, n)
+    s["y"] = rng.uniform(-150.0, 150.0, n)
+    s["z"] = rng.uniform(3000.0, 15000.0, n)
+    th = np.radians(rng.uniform(0.0, 2.0, n))
+    ph = rng.uniform(0.0, 2.0 * np.pi, n)
+    d = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), -np.cos(th)], 1)
+    s["dx"], s["dy"], s["dz"] = d[:, 0], d[:, 1], d[:, 2]
+    s["L"] = rng.uniform(0.5, 5.0, n).astype(np.float32)
+    s["t0"] = (100000.0 - s["z"]) / I.C_M_PER_NS
+    s["charge"] = np.where(rng.random(n) < 0.5, -1, 1)
+    s["eps"] = rng.uniform(2e-5, 6e-5, n).astype(np.float32)
+    par = I.Params(bunch=5.0, seed=seed)
+    # the midpoint refractivity in binary64, as the oracle forms it
+    dd = np.stack([s["dx"], s["dy"], s["dz"]], 1).astype(np.float64)
+    dd /= np.linalg.norm(dd, axis=1)[:, None]
+    m = np.stack([s["x"], s["y"], s["z"]], 1) + 0.5 * s["L"].astype(np.float64)[:, None] * dd
+    h = np.sqrt(m[:, 0] ** 2 + m[:, 1] ** 2 + (m[:, 2] + atm.R_E) ** 2) - atm.R_E
+    delta = np.array([O.delta(atm, float(v)) for v in h])
+    third = n // 3
+    # near the threshold: beta n - 1 = r delta (eps does not move the midpoint)
+    r = np.array([1e-3, 1e-5, 1e-7])[np.arange(third) % 3]
+    s["eps"][third:2 * third] = (delta[third:2 * third] * (1.0 - r) / (1.0 + delta[third:2 * third])).astype(np.float32)
+    s["eps"][2 * third:] = (delta[2 * third:] * (1.0 + 1e-6) / (1.0 + delta[2 * third:])).astype(np.float32)
+    # on a count boundary: scale L until N / B is an integer
+    for i in range(third):
+        for _ in range(3):
+            y = O.yield_of(s[i], atm, par)
+            x = y["Nc"] / par.bunch
+            if x <= 0:
+                break
+            s["L"][i] = np.float32(s["L"][i] * max(1.0, round(x)) / x)
+    w = I.Workload("guard_steps", s, atm, I.telescope_grid(31, 31, 10.0, z=atm.h_obs), par)
+    return w
+
+
+def test_guard_paths_near_threshold_and_count_boundaries(ctx):
+    """The precision guards of the yield (count boundaries decided in
+    binary64, beta n - 1 in FP32 pairs near the threshold, binary64 for the
+    narrowest cones) give the oracle's bunch counts, weights and hits, with
+    the fixed weight bound; the guarded steps are counted."""
+    w = _guard_steps()
+    rep, gst, rst = _check(ctx, w)
+    assert gst["guarded"] > 0, gst
+    assert rep["n_common"] > 500
+    # per-step bunch counts equal the oracle's on every step
+    nbc, nbf = O.bunch_counts(w.segments, w.atmosphere, w.params)
+    assert gst["rays"] == int(nbc.sum() + nbf.sum())
+    # the plain binary64 path and the binary64-guard mode agree as well
+    _check(ctx, w, fp64=True)
+    _check(ctx, w, precision=G.PREC_FP64_GUARD)
+    ctx.setup(w)
+
+
 def test_inclined_shower_441_telescopes(ctx):
     w = I.workload_inclined(n=40_000, seed=7)
     rep, gst, rst = _check(ctx, w)
