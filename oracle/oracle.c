@@ -76,11 +76,17 @@ double or_delta(const or_atmosphere *a, double h)
     return a->K * or_density(a, h);
 }
 
+/* h = |r + R_E z| - R_E, written as (x^2 + y^2 + z (z + 2 R_E)) /
+   (|r + R_E z| + R_E): the same quantity without subtracting two numbers of
+   6.4e6 m (which would lose ~1e-9 m, and near the Cherenkov threshold the
+   yield's relative error is the refractivity's times (delta + eps) /
+   (beta n - 1)). */
 static double altitude(const or_atmosphere *a, const double r[3])
 {
     if (!a->spherical) return r[2];
     double zc = r[2] + a->R_E;
-    return sqrt(r[0] * r[0] + r[1] * r[1] + zc * zc) - a->R_E;
+    double num = r[0] * r[0] + r[1] * r[1] + r[2] * (r[2] + 2.0 * a->R_E);
+    return num / (sqrt(r[0] * r[0] + r[1] * r[1] + zc * zc) + a->R_E);
 }
 
 static void unit3(const float d[3], double u[3])
@@ -213,8 +219,8 @@ void or_yield_at(const or_segment *s, int64_t seg_index, const or_atmosphere *a,
     double rm[3] = {s->x + 0.5 * s->L * d[0], s->y + 0.5 * s->L * d[1], s->z + 0.5 * s->L * d[2]};
     double h_mid = altitude(a, rm);
     double delta = or_delta(a, h_mid);
-    double n = 1.0 + delta;
-    double beta = 1.0 - (double)s->eps;
+    double eps_d = (double)s->eps;
+    double g1 = delta - eps_d - eps_d * delta;          /* beta n - 1 */
     double z2 = (double)s->charge * (double)s->charge;
     if (p->cut_mode != 0 && z2 > 0 && !cut_keeps(d, rm, p)) z2 = 0;
     double n_c = 0, w_c = 0, cos_tc = 1, sin_tc = 0, Nc = 0;
@@ -227,9 +233,14 @@ void or_yield_at(const or_segment *s, int64_t seg_index, const or_atmosphere *a,
             n_c = ceil(Nc / p->bunch);
             w_c = n_c > 0 ? Nc / n_c : 0.0;
         }
-    } else if (z2 > 0 && beta * n > 1.0 && s->L > 0) {
-        cos_tc = 1.0 / (beta * n);
-        double sin2 = 1.0 - 1.0 / (beta * beta * n * n);
+    } else if (z2 > 0 && g1 > 0.0 && s->L > 0) {
+        /* beta n > 1 and 1 - 1/(beta n)^2 = (beta n - 1)(beta n + 1)/(beta n)^2,
+           with beta n - 1 = (1 - eps)(1 + delta) - 1 = delta - eps - eps delta:
+           the same quantities without the cancellation of 1 - 1/(beta n)^2
+           (which keeps only ~16 + log10(beta n - 1) digits near threshold) */
+        double bn = 1.0 + g1;
+        cos_tc = 1.0 / bn;
+        double sin2 = g1 * (2.0 + g1) / (bn * bn);
         sin_tc = sqrt(sin2);
         double band = (1.0 / p->lambda1 - 1.0 / p->lambda2) * 1e9;   /* 1/m */
         Nc = 2.0 * OR_PI * OR_ALPHA * z2 * band * sin2 * (double)s->L;

@@ -866,3 +866,43 @@ def test_cut_loses_no_photons_beyond_fifteen_radii_as_the_paper_states():
     _, _, s0, _ = O.trace(s, atm, tels, par)
     _, _, s1, _ = O.trace(s, atm, tels, cut)
     assert s1.sum() < 0.99 * s0.sum()
+
+
+def test_yield_near_threshold_matches_high_precision():
+    """Sec. 1.2: N = 2 pi alpha z^2 (1/l1 - 1/l2)(1 - 1/(beta n)^2) L above the
+    threshold beta n > 1, n = 1 + delta(h_mid).  Near the threshold the
+    oracle's yield equals a 50-digit evaluation of that formula (written as
+    printed, 1 - 1/(beta n)^2) to binary64's conditioning, 4e-16 over the
+    relative distance r of beta n - 1 from the threshold (r down to 1e-9 of
+    the refractivity), and both sides agree which steps emit."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    atm = I.atmosphere_layered()
+    par = I.Params(bunch=5.0)
+    rng = np.random.default_rng(11)
+    for r in (1e-2, 1e-4, 1e-6, 1e-8, 1e-9, -1e-8):
+        s = np.zeros(1, dtype=I.SEG_DTYPE)
+        s["x"], s["y"], s["z"] = rng.uniform(-100, 100), rng.uniform(-100, 100), rng.uniform(3e3, 1.5e4)
+        s["dx"], s["dy"], s["dz"] = 0.01, -0.02, -1.0
+        s["L"] = 2.5
+        s["charge"] = -1
+        d = [mp.mpf(float(s["dx"][0])), mp.mpf(float(s["dy"][0])), mp.mpf(float(s["dz"][0]))]
+        nrm = mp.sqrt(sum(v * v for v in d))
+        d = [v / nrm for v in d]
+        L = mp.mpf(float(s["L"][0]))
+        m = [mp.mpf(float(s[k][0])) + L / 2 * d[i] for i, k in enumerate(("x", "y", "z"))]
+        RE = mp.mpf(atm.R_E)
+        h = mp.sqrt(m[0] ** 2 + m[1] ** 2 + (m[2] + RE) ** 2) - RE
+        i = int(np.searchsorted(np.asarray(atm.h_lo), float(h), side="right") - 1)
+        delta = mp.mpf(atm.K) * mp.mpf(atm.b[i]) / (100 * mp.mpf(atm.c[i])) * mp.exp(-h / mp.mpf(atm.c[i]))
+        s["eps"] = np.float32(float(delta * (1 - r) / (1 + delta)))
+        beta_n = (1 - mp.mpf(float(s["eps"][0]))) * (1 + delta)
+        y = O.yield_of(s[0], atm, par)
+        if beta_n <= 1:
+            assert y["Nc"] == 0.0 and y["n_c"] == 0.0
+            continue
+        N = 2 * mp.pi * mp.mpf(7.2973525643e-3) * (mp.mpf(1) / 300 - mp.mpf(1) / 600) * mp.mpf(10) ** 9 * \
+            (1 - 1 / beta_n ** 2) * L
+        # binary64 conditioning: delta's ~1e-16 relative error, times
+        # delta / (beta n - 1) ~ 1 / r
+        assert abs(y["Nc"] / float(N) - 1.0) < 4e-16 / abs(r) + 1e-12, (r, y["Nc"], float(N))
