@@ -9,8 +9,9 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libclight.so")
-SOURCES = ["trace_kernels.cu", "adjoint_kernels.cu", "sort_kernels.cu", "clight_api.cu", "probe_kernels.cu"]
-HEADERS = ["df.cuh", "internal.h", "ray.cuh"]
+SOURCES = ["trace_twopass.cu", "trace_inplace.cu", "trace_noalloc.cu", "adjoint_kernels.cu", "sort_kernels.cu",
+           "clight_api.cu", "probe_kernels.cu"]
+HEADERS = ["df.cuh", "internal.h", "ray.cuh", "trace_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]
 

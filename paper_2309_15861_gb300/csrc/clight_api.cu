@@ -657,9 +657,10 @@ cudaError_t enqueue(clight_ctx *c, const clight_segment *segs, int64_t n_segs, c
         } else {
             int block = c->upar.block > 0 ? c->upar.block : 256;
             // the first pass of the deferred path fits 4 CTAs of 256 per SM, the in-place kernel 3
-            const bool deferred = c->defer_use > 0 && c->upar.precision == CLIGHT_PREC_FLOAT_PAIR &&
-                                  !(c->atm.disp && (c->par.cut_mode != CLIGHT_CUT_OFF || c->par.beam ||
-                                                    c->par.roulette || c->par.prop == CLIGHT_PROP_STRAIGHT));
+            const bool ext = c->par.cut_mode != CLIGHT_CUT_OFF || c->par.beam || c->par.roulette;
+            const bool deferred = c->defer_use > 0 &&
+                                  !(c->atm.disp && (ext || c->par.prop == CLIGHT_PROP_STRAIGHT)) &&
+                                  (c->upar.precision == CLIGHT_PREC_FLOAT_PAIR || !(ext || c->atm.disp));
             int per_sm = c->upar.ctas_per_sm > 0 ? c->upar.ctas_per_sm : (deferred ? 4 : 3) * 256 / block;
             int64_t step = chunk > 0 ? chunk : n_segs;
             // with the default queue size, launches of at most half as many

@@ -511,10 +511,12 @@ __device__ __forceinline__ void yield_fp64(const clight_segment &s, const DevAtm
 {
     double xm = s.x + 0.5 * (double)s.L * ux, ym = s.y + 0.5 * (double)s.L * uy,
            zm = s.z + 0.5 * (double)s.L * uz;
+    // the altitude without cancellation (near the threshold the yield's
+    // relative error is the refractivity's times kappa / 2)
     double h;
     if (SPH) {
         double zc = zm + A.R_E_d;
-        h = sqrt(xm * xm + ym * ym + zc * zc) - A.R_E_d;
+        h = (xm * xm + ym * ym + zm * (zm + 2.0 * A.R_E_d)) / (sqrt(xm * xm + ym * ym + zc * zc) + A.R_E_d);
     } else {
         h = zm;
     }
@@ -700,8 +702,8 @@ template <class T> __device__ __forceinline__ T roulette_u(int64_t seg_global, c
 }
 
 template <bool SPH, bool EXT = true, bool DISP = true>
-__device__ void load_segment_f(const clight_segment &s, int64_t seg_global, const DevAtm &A, const DevPar &P,
-                               Seg<float, df> &g)
+__device__ __forceinline__ void load_segment_f(const clight_segment &s, int64_t seg_global, const DevAtm &A,
+                                               const DevPar &P, Seg<float, df> &g)
 {
     g.bad = 0;
     g.guarded = 0;
@@ -915,6 +917,21 @@ __device__ void load_segment_d(const clight_segment &s, int64_t seg_global, cons
         g.n_f = (uint32_t)nb;
         g.w_f = Nf / nb;
     }
+}
+
+// The step with its pairs widened to binary64 (the FP64-guard precision:
+// native binary64 at the steps that carry pairs otherwise).
+__device__ __forceinline__ void widen_seg(const Seg<float, df> &q, Seg<float, double> &qd)
+{
+    p_from_pair(qd.x0, q.x0); p_from_pair(qd.y0, q.y0); p_from_pair(qd.z0, q.z0);
+    p_from_pair(qd.t0, q.t0); p_from_pair(qd.rz0, q.rz0);
+    p_from_pair(qd.A0, q.A0); p_from_pair(qd.C0, q.C0);
+    qd.dx = q.dx; qd.dy = q.dy; qd.dz = q.dz; qd.lx = q.lx; qd.ly = q.ly; qd.lz = q.lz;
+    qd.e1x = q.e1x; qd.e1y = q.e1y; qd.e1z = q.e1z; qd.e2x = q.e2x; qd.e2y = q.e2y; qd.e2z = q.e2z;
+    qd.sin_tc = q.sin_tc; qd.kappa = q.kappa; qd.L = q.L; qd.inv_bc = q.inv_bc;
+    qd.w_c = q.w_c; qd.w_f = q.w_f; qd.n_c = q.n_c; qd.n_f = q.n_f; qd.shower = q.shower;
+    qd.bux = q.bux; qd.buy = q.buy; qd.buz = q.buz; qd.bomc = q.bomc;
+    qd.h_mid = q.h_mid; qd.bad = q.bad; qd.guarded = q.guarded; qd.cut = q.cut;
 }
 
 // ------------------------------------------------------------------ one ray

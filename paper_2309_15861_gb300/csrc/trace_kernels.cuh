@@ -1,8 +1,11 @@
-// trace_kernels.cu -- the forward kernels on sm_103a: the fused persistent
+// trace_kernels.cuh -- the forward kernels on sm_103a: the fused persistent
 // generation + propagation + hit kernel (FP32 with FP32-pair or binary64
-// precise steps), the plain binary64 kernel, and the entry point without
-// allocation.  The per-ray device code is in ray.cuh (paper sections cited
-// there).
+// precise steps), the classification and deferred-ray kernels of the
+// two-pass path, and the plain binary64 kernel.  The per-ray device code is
+// in ray.cuh (paper sections cited there).  Their launchers live in
+// trace_twopass.cu, trace_inplace.cu and trace_noalloc.cu (three
+// translation units, compiled in parallel).
+#pragma once
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,17 +39,17 @@ __host__ __device__ constexpr int fields_of(bool ext, bool defer = false)
 // Segment records of the warps, then (kernels without FEAT_EXT) the
 // clearance map; with FEAT_EXT the records are larger and the map is read
 // from global memory, so that both stay under 48 KB.
-static int seg_smem_bytes(int block, bool ext, bool defer)
+inline int seg_smem_bytes(int block, bool ext, bool defer)
 {
     return (block / 32) * fields_of(ext, defer) * 32 * (int)sizeof(float);
 }
-static int fused_smem_bytes_f(int block, const DevTel &T, bool ext, bool defer = false)
+inline int fused_smem_bytes_f(int block, const DevTel &T, bool ext, bool defer = false)
 {
     // the deferred first pass without FEAT_EXT also stages the next group's records
     return seg_smem_bytes(block, ext, defer) + (!ext && T.clr ? T.clr_bytes : 0) +
            (defer && !ext ? (block / 32) * 2048 : 0);
 }
-int fused_smem_bytes(int block, const DevTel &T) { return fused_smem_bytes_f(block, T, true); }
+inline int fused_smem_bytes(int block, const DevTel &T) { return fused_smem_bytes_f(block, T, true); }
 
 __device__ __forceinline__ void put_df(float *S, int fh, int fl, int l, df v)
 {
@@ -428,14 +431,7 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
             int nh = 0;
             if (std::is_same<P, double>::value) {   // binary64 for the precise steps
                 Seg<float, double> qd;
-                p_from_pair(qd.x0, q.x0); p_from_pair(qd.y0, q.y0); p_from_pair(qd.z0, q.z0);
-                p_from_pair(qd.t0, q.t0); p_from_pair(qd.rz0, q.rz0);
-                p_from_pair(qd.A0, q.A0); p_from_pair(qd.C0, q.C0);
-                qd.dx = q.dx; qd.dy = q.dy; qd.dz = q.dz; qd.lx = q.lx; qd.ly = q.ly; qd.lz = q.lz;
-                qd.e1x = q.e1x; qd.e1y = q.e1y; qd.e1z = q.e1z; qd.e2x = q.e2x; qd.e2y = q.e2y; qd.e2z = q.e2z;
-                qd.sin_tc = q.sin_tc; qd.kappa = q.kappa; qd.L = q.L; qd.inv_bc = q.inv_bc;
-                qd.w_c = q.w_c; qd.w_f = q.w_f; qd.n_c = q.n_c; qd.n_f = q.n_f; qd.shower = q.shower;
-                qd.bux = q.bux; qd.buy = q.buy; qd.buz = q.buz; qd.bomc = q.bomc;
+                widen_seg(q, qd);
                 RayOut<float, double> o;
                 trace_ray<float, double, true, SPH, REFR, FEAT>(qd, seg_global, k, active, A, Pp, o);
                 nh = hit_test<float, double, true, NOALLOC>(o, Pp.key_off + seg_local, seg_global, k, q.shower, A, Tl, Pp, O, status_bits, clr);
@@ -534,7 +530,7 @@ constexpr int kClsVmax = 64;                     // virtual steps per warp: 32 C
 constexpr int kClsWarpBytes = 32 * (int)sizeof(ClsRec) + kClsVmax * 8;
 constexpr uint32_t kVGated = 1u << 6;            // virtual-step flag: the step's Cherenkov bounds hold
 
-static int cls_smem_bytes(int block, const DevTel &T)
+inline int cls_smem_bytes(int block, const DevTel &T)
 {
     return (block / 32) * (kClsWarpBytes + kStageBytes) + (T.clr ? T.clr_bytes : 0);
 }
@@ -778,16 +774,29 @@ k_classify(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid
                 const float u1 = u01<float>(x.y), u2 = u01<float>(x.z);
                 float sn, cs;
                 Num<float>::sincos2pi(u2, &sn, &cs);
-                const ClsRec &R = rec[l];
+                // the step's record in 128-bit shared loads, those of a
+                // process issued together
+                const float4 *rq = reinterpret_cast<const float4 *>(rec + l);
+                ClsRec R;
+                {
+                    const float4 q0 = rq[0], q1 = rq[1], q2 = rq[2];
+                    R.x0 = q0.x; R.y0 = q0.y; R.z0 = q0.z; R.L = q0.w;
+                    R.dx = q1.x; R.dy = q1.y; R.dz = q1.z; R.h_mid = q1.w;
+                    R.ax = q2.x; R.ay = q2.y; R.az = q2.z; R.hd = q2.w;
+                }
                 const float ell = u1 * R.L;
                 if (proc == 0) {
                     kq = kk;
+                    const float4 q3 = rq[3], q4 = rq[4];
+                    R.b1x = q3.x; R.b1y = q3.y; R.b1z = q3.z; R.rsb = q3.w;
+                    R.b2x = q4.x; R.b2y = q4.y; R.b2z = q4.z; R.cB = q4.w;
                     const float dgx = R.ax + (cs * R.b1x + sn * R.b2x);
                     const float dgy = R.ay + (cs * R.b1y + sn * R.b2y);
                     const float dgz = R.az + (cs * R.b1z + sn * R.b2z);
                     cls = (v.y & kVGated) ? classify_cherenkov_gated<SPH>(R, ell, dgx, dgy, dgz, A, Tl, clr)
                                           : classify_ray<SPH, REFR>(R, ell, dgx, dgy, dgz, A, Tl, clr);
                 } else {
+                    R.nc = reinterpret_cast<const uint4 *>(rq)[5].x;
                     kq = R.nc + kk;
                     const float u3 = u01<float>(x.w);
                     const float cz = 2.0f * u3 - 1.0f;
@@ -818,7 +827,7 @@ k_classify(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid
 // its step record in global memory (set up again exactly as in the first
 // pass), traced and hit-tested in full.  Ray counts were taken in the first
 // pass.  Persistent grid, each warp taking the next 32 entries from a counter.
-template <bool SPH, bool REFR, int FEAT>
+template <bool SPH, bool REFR, int FEAT, class P = df>
 __global__ void __launch_bounds__(256, 3)
 k_trace_deferred(const clight_segment *__restrict__ segs, const __grid_constant__ DevAtm A,
                  const __grid_constant__ DevTel Tl, const __grid_constant__ DevPar Pp,
@@ -853,14 +862,30 @@ k_trace_deferred(const clight_segment *__restrict__ segs, const __grid_constant_
         const clight_segment s = seg_from_words(__ldg(src), __ldg(src + 1), __ldg(src + 2), __ldg(src + 3));
         Seg<float, df> g;
         load_segment_f<SPH, EXT, (FEAT & FEAT_DISP) != 0>(s, seg_global, A, Pp, g);
-        RayOut<float, df> o;
-        trace_ray<float, df, true, SPH, REFR, FEAT>(g, seg_global, k, active, A, Pp, o);
-        c_hits += hit_test<float, df, true, false>(o, Pp.key_off + seg_local, seg_global, k, g.shower, A, Tl, Pp, O,
-                                                   status_bits, clr);
+        int st;
+        uint32_t cells;
+        if constexpr (std::is_same<P, double>::value) {
+            // binary64 at the steps that otherwise carry FP32 pairs
+            Seg<float, double> qd;
+            widen_seg(g, qd);
+            RayOut<float, double> o;
+            trace_ray<float, double, true, SPH, REFR, FEAT>(qd, seg_global, k, active, A, Pp, o);
+            c_hits += hit_test<float, double, true, false>(o, Pp.key_off + seg_local, seg_global, k, g.shower, A,
+                                                           Tl, Pp, O, status_bits, clr);
+            st = o.status;
+            cells = o.cells;
+        } else {
+            RayOut<float, df> o;
+            trace_ray<float, df, true, SPH, REFR, FEAT>(g, seg_global, k, active, A, Pp, o);
+            c_hits += hit_test<float, df, true, false>(o, Pp.key_off + seg_local, seg_global, k, g.shower, A, Tl,
+                                                       Pp, O, status_bits, clr);
+            st = o.status;
+            cells = o.cells;
+        }
         if (active) {
-            c_esc += o.status == 1; c_under += o.status == 2; c_turn += o.status == 3;
-            c_reach += o.status == 0 || o.status == 5;
-            c_cells += o.status == 0 ? o.cells : 0;
+            c_esc += st == 1; c_under += st == 2; c_turn += st == 3;
+            c_reach += st == 0 || st == 5;
+            c_cells += st == 0 ? cells : 0;
             ++c_def;
         }
     }
@@ -905,255 +930,17 @@ k_trace_fp64(const clight_segment *__restrict__ segs, int64_t n_segs, const __gr
     if (status_bits) atomicOr(O.ctr + CTR_STATS + ST_STATUS, (unsigned long long)status_bits);
 }
 
-// ------------------------------------------------------------------ launchers
-template <bool SPH, bool REFR, int FEAT>
-static void launch_deferred_pair(const clight_segment *segs, int64_t n_segs, const DevAtm &A, const DevTel &T,
-                                 const DevPar &Pp, const DevOut &O, int grid, int block, cudaStream_t s)
-{
-    constexpr bool EXT = (FEAT & FEAT_EXT) != 0;
-    // the queue's fill and work counters
-    cudaMemsetAsync(O.ctr + CTR_DEFER, 0, 2 * sizeof(unsigned long long), s);
-    if constexpr ((FEAT & (FEAT_EXT | FEAT_DISP)) == 0) {
-        // the default feature set: the classification kernel
-        const int smem = cls_smem_bytes(block, T);
-        cudaFuncSetAttribute(k_classify<SPH, REFR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k_classify<SPH, REFR><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
-    } else {
-        k_trace_fused<df, SPH, REFR, false, false, FEAT, true>
-            <<<grid, block, fused_smem_bytes_f(block, T, EXT, true), s>>>(segs, n_segs, A, T, Pp, O);
-    }
-    // the second pass as many CTAs as are resident at once (its own
-    // register and shared-memory limits)
-    const int smem2 = !EXT && T.clr ? T.clr_bytes : 0;
-    int dev = 0, n_sm = 1, per_sm = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_deferred<SPH, REFR, FEAT>, block, smem2);
-    const int grid2 = std::max(1, std::min(grid, n_sm * std::max(per_sm, 1)));
-    k_trace_deferred<SPH, REFR, FEAT><<<grid2, block, smem2, s>>>(segs, A, T, Pp, O);
-}
 
-template <class P, int FEAT>
-static void launch_fused_pe(const clight_segment *segs, int64_t n_segs, const DevAtm &A, const DevTel &T,
-                            const DevPar &Pp, const DevOut &O, int grid, int block, cudaStream_t s)
-{
-    int smem = fused_smem_bytes_f(block, T, (FEAT & FEAT_EXT) != 0);  // < 48 KB for block <= 256
-    // the two-pass path for every binary32-pair instance with one propagator
-    // compiled in (the straight-line propagator moves a ray by no more than
-    // the bound the first pass uses: its first-order shortfall is that
-    // bound's first term)
-    if constexpr (std::is_same<P, df>::value && (FEAT & FEAT_RUNTIME) == 0) {
-        if (O.defer) {
-            if (A.spherical && A.refraction)
-                launch_deferred_pair<true, true, FEAT>(segs, n_segs, A, T, Pp, O, grid, block, s);
-            else if (A.spherical)
-                launch_deferred_pair<true, false, FEAT>(segs, n_segs, A, T, Pp, O, grid, block, s);
-            else if (A.refraction)
-                launch_deferred_pair<false, true, FEAT>(segs, n_segs, A, T, Pp, O, grid, block, s);
-            else
-                launch_deferred_pair<false, false, FEAT>(segs, n_segs, A, T, Pp, O, grid, block, s);
-            return;
-        }
-    }
-    if (A.spherical && A.refraction)
-        k_trace_fused<P, true, true, false, false, FEAT><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
-    else if (A.spherical)
-        k_trace_fused<P, true, false, false, false, FEAT><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
-    else if (A.refraction)
-        k_trace_fused<P, false, true, false, false, FEAT><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
-    else
-        k_trace_fused<P, false, false, false, false, FEAT><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
-}
-
-// the variant without the angular cut, beaming and the straight-line propagator when none is on
+// The two-pass launch (first pass, then the queued rays) of a feature set
+// that has one (trace_twopass.cu); P = df or double (the precise steps).
 template <class P>
-static void launch_fused_p(const clight_segment *segs, int64_t n_segs, const DevAtm &A, const DevTel &T,
-                           const DevPar &Pp, const DevOut &O, int grid, int block, cudaStream_t s)
-{
-    const bool ext = Pp.cut_mode != CLIGHT_CUT_OFF || Pp.beam || Pp.roulette;
-    const bool str = Pp.prop == CLIGHT_PROP_STRAIGHT;
-    if (!std::is_same<P, df>::value || (A.disp && (ext || str)))
-        launch_fused_pe<P, FEAT_ALL>(segs, n_segs, A, T, Pp, O, grid, block, s);
-    else if (A.disp)
-        launch_fused_pe<P, FEAT_DISP>(segs, n_segs, A, T, Pp, O, grid, block, s);
-    else if (ext && str)
-        launch_fused_pe<P, FEAT_EXT | FEAT_STRAIGHT>(segs, n_segs, A, T, Pp, O, grid, block, s);
-    else if (ext)
-        launch_fused_pe<P, FEAT_EXT>(segs, n_segs, A, T, Pp, O, grid, block, s);
-    else if (str)
-        launch_fused_pe<P, FEAT_STRAIGHT>(segs, n_segs, A, T, Pp, O, grid, block, s);
-    else
-        launch_fused_pe<P, 0>(segs, n_segs, A, T, Pp, O, grid, block, s);
-}
-
-cudaError_t launch_trace_fused(const clight_segment *segs, int64_t n_segs, const DevAtm &A, const DevTel &T,
-                               const DevPar &P, const DevOut &O, int precision, int grid, int block,
-                               cudaStream_t s)
-{
-    if (precision == CLIGHT_PREC_FP64_GUARD)
-        launch_fused_p<double>(segs, n_segs, A, T, P, O, grid, block, s);
-    else
-        launch_fused_p<df>(segs, n_segs, A, T, P, O, grid, block, s);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_trace_fp64(const clight_segment *segs, int64_t n_segs, const DevAtm &A, const DevTel &T,
-                              const DevPar &P, const DevOut &O, cudaStream_t s)
-{
-    int block = 128;
-    int64_t grid = (n_segs + block - 1) / block;
-    if (grid < 1) grid = 1;
-    if (A.spherical && A.refraction)
-        k_trace_fp64<true, true><<<(unsigned)grid, block, 0, s>>>(segs, n_segs, A, T, P, O);
-    else if (A.spherical)
-        k_trace_fp64<true, false><<<(unsigned)grid, block, 0, s>>>(segs, n_segs, A, T, P, O);
-    else if (A.refraction)
-        k_trace_fp64<false, true><<<(unsigned)grid, block, 0, s>>>(segs, n_segs, A, T, P, O);
-    else
-        k_trace_fp64<false, false><<<(unsigned)grid, block, 0, s>>>(segs, n_segs, A, T, P, O);
-    return cudaGetLastError();
-}
-
-// ------------------------------------------------------------------ no allocation
-// Scratch of clight_trace_noalloc: the work and hit counters and the ray
-// statistics (CTR_N words), then one hit counter per (shower, telescope)
-// group.  It lives in the library image, so the entry point needs no
-// cudaMalloc; every GPU that loads the library holds these 131,200 bytes
-// until the process exits.
-constexpr int kNoallocMaxGroups = 16384;
-static __device__ __align__(256) unsigned long long g_noalloc_scratch[CTR_N + kNoallocMaxGroups];
-
-// The device address of the scratch array on the current device.  In host
-// code the array's name is only a stand-in, so the address comes from the
-// runtime; it is looked up once per context (whose device is current here)
-// and kept in the context, which a device reset invalidates as a whole.
-static cudaError_t noalloc_scratch(clight_ctx *ctx, unsigned long long **out)
-{
-    void **slot = ctx_noalloc_slot(ctx);
-    if (!slot) return cudaErrorInvalidValue;
-    if (!*slot) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        *slot = p;
-    }
-    *out = static_cast<unsigned long long *>(*slot);
-    return cudaSuccess;
-}
-
-template <int FEAT>
-static void launch_soft_f(const clight_segment *segs, int64_t n_segs, const DevAtm &A, const DevTel &T,
-                          const DevPar &Pp, const DevOut &O, int grid, int block, cudaStream_t s)
-{
-    const int smem = fused_smem_bytes_f(block, T, (FEAT & FEAT_EXT) != 0);
-    if (A.spherical && A.refraction)
-        k_trace_fused<df, true, true, false, true, FEAT><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
-    else if (A.spherical)
-        k_trace_fused<df, true, false, false, true, FEAT><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
-    else if (A.refraction)
-        k_trace_fused<df, false, true, false, true, FEAT><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
-    else
-        k_trace_fused<df, false, false, false, true, FEAT><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
-}
-
-// The adjoint's candidate pass (exact propagator, no dispersion: the
-// adjoint refuses the others), with the angular cut and beaming compiled in
-// only when on.
-cudaError_t launch_soft_candidates(const clight_segment *segs, int64_t n_segs, const DevAtm &A, const DevTel &T,
-                                   const DevPar &Pp, const DevOut &O, int grid, int block, cudaStream_t s)
-{
-    if (Pp.cut_mode != CLIGHT_CUT_OFF || Pp.beam || Pp.roulette)
-        launch_soft_f<FEAT_EXT>(segs, n_segs, A, T, Pp, O, grid, block, s);
-    else
-        launch_soft_f<0>(segs, n_segs, A, T, Pp, O, grid, block, s);
-    return cudaGetLastError();
-}
-
-template <class P, bool SPH, bool REFR>
-static void launch_noalloc(const clight_segment *segs, int64_t n_segs, const DevAtm &A, const DevTel &T,
-                           const DevPar &Pp, const DevOut &O, int grid, int block, cudaStream_t s)
-{
-    k_trace_fused<P, SPH, REFR, true><<<grid, block, fused_smem_bytes(block, T), s>>>(segs, n_segs, A, T, Pp, O);
-}
+void launch_two_pass(int feat, const clight_segment *segs, int64_t n_segs, const DevAtm &A, const DevTel &T,
+                     const DevPar &Pp, const DevOut &O, int grid, int block, cudaStream_t s);
+template <>
+void launch_two_pass<df>(int feat, const clight_segment *segs, int64_t n_segs, const DevAtm &A, const DevTel &T,
+                         const DevPar &Pp, const DevOut &O, int grid, int block, cudaStream_t s);
+template <>
+void launch_two_pass<double>(int feat, const clight_segment *segs, int64_t n_segs, const DevAtm &A,
+                             const DevTel &T, const DevPar &Pp, const DevOut &O, int grid, int block, cudaStream_t s);
 
 }  // namespace clight
-
-extern "C" clight_status clight_trace_noalloc(clight_ctx *ctx, const clight_segment *d_segs, int64_t n_segs,
-                                              int32_t n_showers, clight_hit *d_hits, int64_t hit_capacity,
-                                              int64_t *d_counts, clight_stats *h_stats, int64_t *h_n_hits,
-                                              void *stream)
-{
-    using namespace clight;
-    CtxView v;
-    if (!ctx_view(ctx, &v)) return CLIGHT_ERR_ARG;
-    if (n_segs < 0 || n_showers < 1 || hit_capacity < 0 || !h_n_hits || (n_segs > 0 && !d_segs) ||
-        (hit_capacity > 0 && !d_hits))
-        return CLIGHT_ERR_ARG;
-    if (n_segs > (int64_t(1) << 31)) return CLIGHT_ERR_LIMIT;
-    int64_t groups = (int64_t)n_showers * v.tel.n_tel;
-    if (groups > kNoallocMaxGroups) return CLIGHT_ERR_LIMIT;     // n_showers x n_tel above 16384
-    DeviceGuard dg(v.device);                                    // the caller's device comes back on return
-    if (!dg.ok) return CLIGHT_ERR_CUDA;
-    cudaStream_t s = (cudaStream_t)stream;
-    // the call reads its counters back and synchronises its stream, which a
-    // stream capture does not allow: refuse one, leaving the capture intact
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return CLIGHT_ERR_CUDA;
-    if (cs != cudaStreamCaptureStatusNone) return CLIGHT_ERR_ARG;
-    unsigned long long *scr = nullptr;
-    if (noalloc_scratch(ctx, &scr) != cudaSuccess) return CLIGHT_ERR_CUDA;
-    // counters and group counts left by the previous call start again at zero
-    if (cudaMemsetAsync(scr, 0, sizeof(unsigned long long) * (size_t)(CTR_N + groups), s) != cudaSuccess)
-        return CLIGHT_ERR_CUDA;
-    if (n_segs > 0) {
-        DevPar P = v.par;
-        P.n_showers = n_showers;
-        DevOut O{};
-        O.rec = d_hits;
-        O.keys = scr + CTR_N;        // per-group hit counters
-        O.vals = nullptr;
-        O.capacity = hit_capacity;
-        O.ctr = scr;
-        int block = v.block;
-        int64_t grid = std::min<int64_t>((int64_t)v.n_sm * v.ctas_per_sm, (n_segs + block - 1) / block);
-        grid = std::max<int64_t>(grid, 1);
-        const DevAtm &A = v.atm;
-        bool fp64 = v.precision == CLIGHT_PREC_FP64_GUARD;
-        auto go = [&](auto tag) {
-            using PP = decltype(tag);
-            if (A.spherical && A.refraction) launch_noalloc<PP, true, true>(d_segs, n_segs, A, v.tel, P, O, (int)grid, block, s);
-            else if (A.spherical) launch_noalloc<PP, true, false>(d_segs, n_segs, A, v.tel, P, O, (int)grid, block, s);
-            else if (A.refraction) launch_noalloc<PP, false, true>(d_segs, n_segs, A, v.tel, P, O, (int)grid, block, s);
-            else launch_noalloc<PP, false, false>(d_segs, n_segs, A, v.tel, P, O, (int)grid, block, s);
-        };
-        if (fp64) go(double{});
-        else go(df{});
-        if (cudaGetLastError() != cudaSuccess) return CLIGHT_ERR_CUDA;
-    }
-    unsigned long long h[CTR_N];
-    if (cudaMemcpyAsync(h, scr, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CLIGHT_ERR_CUDA;
-    if (d_counts && cudaMemcpyAsync(d_counts, scr + CTR_N, sizeof(int64_t) * (size_t)groups,
-                                    cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-        return CLIGHT_ERR_CUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return CLIGHT_ERR_CUDA;
-    *h_n_hits = (int64_t)h[CTR_CURSOR];
-    unsigned long long bits = h[CTR_STATS + ST_STATUS];
-    if (h_stats) {
-        h_stats->rays = (int64_t)h[CTR_STATS + ST_RAYS];
-        h_stats->escaped = (int64_t)h[CTR_STATS + ST_ESCAPED];
-        h_stats->under = (int64_t)h[CTR_STATS + ST_UNDER];
-        h_stats->turned = (int64_t)h[CTR_STATS + ST_TURNED];
-        h_stats->reached = (int64_t)h[CTR_STATS + ST_REACHED];
-        h_stats->hits = (int64_t)h[CTR_STATS + ST_HITS];
-        h_stats->guarded = (int64_t)h[CTR_STATS + ST_GUARDED];
-        h_stats->status = (int64_t)bits;
-        h_stats->cells = (int64_t)h[CTR_STATS + ST_CELLS];
-        h_stats->cut = (int64_t)h[CTR_STATS + ST_CUT];
-        h_stats->skipped = (int64_t)h[CTR_STATS + ST_SKIPPED];
-        h_stats->deferred = (int64_t)h[CTR_STATS + ST_DEFERRED];
-    }
-    if ((int64_t)h[CTR_CURSOR] > hit_capacity) return CLIGHT_ERR_HIT_CAPACITY;
-    if (bits & (1ull << CLIGHT_ERR_BAD_SEGMENT)) return CLIGHT_ERR_BAD_SEGMENT;
-    if (bits & (1ull << CLIGHT_ERR_LIMIT)) return CLIGHT_ERR_LIMIT;
-    return CLIGHT_OK;
-}

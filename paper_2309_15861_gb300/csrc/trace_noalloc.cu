@@ -1,0 +1,151 @@
+// trace_noalloc.cu -- the adjoint's candidate pass and the entry point
+// without allocation (its scratch is a static array of this file).
+#include <algorithm>
+
+#include "trace_kernels.cuh"
+
+namespace clight {
+
+// ------------------------------------------------------------------ no allocation
+// Scratch of clight_trace_noalloc: the work and hit counters and the ray
+// statistics (CTR_N words), then one hit counter per (shower, telescope)
+// group.  It lives in the library image, so the entry point needs no
+// cudaMalloc; every GPU that loads the library holds these 131,200 bytes
+// until the process exits.
+constexpr int kNoallocMaxGroups = 16384;
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[CTR_N + kNoallocMaxGroups];
+
+// The device address of the scratch array on the current device.  In host
+// code the array's name is only a stand-in, so the address comes from the
+// runtime; it is looked up once per context (whose device is current here)
+// and kept in the context, which a device reset invalidates as a whole.
+static cudaError_t noalloc_scratch(clight_ctx *ctx, unsigned long long **out)
+{
+    void **slot = ctx_noalloc_slot(ctx);
+    if (!slot) return cudaErrorInvalidValue;
+    if (!*slot) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        *slot = p;
+    }
+    *out = static_cast<unsigned long long *>(*slot);
+    return cudaSuccess;
+}
+
+template <int FEAT>
+static void launch_soft_f(const clight_segment *segs, int64_t n_segs, const DevAtm &A, const DevTel &T,
+                          const DevPar &Pp, const DevOut &O, int grid, int block, cudaStream_t s)
+{
+    const int smem = fused_smem_bytes_f(block, T, (FEAT & FEAT_EXT) != 0);
+    if (A.spherical && A.refraction)
+        k_trace_fused<df, true, true, false, true, FEAT><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
+    else if (A.spherical)
+        k_trace_fused<df, true, false, false, true, FEAT><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
+    else if (A.refraction)
+        k_trace_fused<df, false, true, false, true, FEAT><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
+    else
+        k_trace_fused<df, false, false, false, true, FEAT><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
+}
+
+// The adjoint's candidate pass (exact propagator, no dispersion: the
+// adjoint refuses the others), with the angular cut and beaming compiled in
+// only when on.
+cudaError_t launch_soft_candidates(const clight_segment *segs, int64_t n_segs, const DevAtm &A, const DevTel &T,
+                                   const DevPar &Pp, const DevOut &O, int grid, int block, cudaStream_t s)
+{
+    if (Pp.cut_mode != CLIGHT_CUT_OFF || Pp.beam || Pp.roulette)
+        launch_soft_f<FEAT_EXT>(segs, n_segs, A, T, Pp, O, grid, block, s);
+    else
+        launch_soft_f<0>(segs, n_segs, A, T, Pp, O, grid, block, s);
+    return cudaGetLastError();
+}
+
+template <class P, bool SPH, bool REFR>
+static void launch_noalloc(const clight_segment *segs, int64_t n_segs, const DevAtm &A, const DevTel &T,
+                           const DevPar &Pp, const DevOut &O, int grid, int block, cudaStream_t s)
+{
+    k_trace_fused<P, SPH, REFR, true><<<grid, block, fused_smem_bytes(block, T), s>>>(segs, n_segs, A, T, Pp, O);
+}
+
+}  // namespace clight
+
+extern "C" clight_status clight_trace_noalloc(clight_ctx *ctx, const clight_segment *d_segs, int64_t n_segs,
+                                              int32_t n_showers, clight_hit *d_hits, int64_t hit_capacity,
+                                              int64_t *d_counts, clight_stats *h_stats, int64_t *h_n_hits,
+                                              void *stream)
+{
+    using namespace clight;
+    CtxView v;
+    if (!ctx_view(ctx, &v)) return CLIGHT_ERR_ARG;
+    if (n_segs < 0 || n_showers < 1 || hit_capacity < 0 || !h_n_hits || (n_segs > 0 && !d_segs) ||
+        (hit_capacity > 0 && !d_hits))
+        return CLIGHT_ERR_ARG;
+    if (n_segs > (int64_t(1) << 31)) return CLIGHT_ERR_LIMIT;
+    int64_t groups = (int64_t)n_showers * v.tel.n_tel;
+    if (groups > kNoallocMaxGroups) return CLIGHT_ERR_LIMIT;     // n_showers x n_tel above 16384
+    DeviceGuard dg(v.device);                                    // the caller's device comes back on return
+    if (!dg.ok) return CLIGHT_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    // the call reads its counters back and synchronises its stream, which a
+    // stream capture does not allow: refuse one, leaving the capture intact
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return CLIGHT_ERR_CUDA;
+    if (cs != cudaStreamCaptureStatusNone) return CLIGHT_ERR_ARG;
+    unsigned long long *scr = nullptr;
+    if (noalloc_scratch(ctx, &scr) != cudaSuccess) return CLIGHT_ERR_CUDA;
+    // counters and group counts left by the previous call start again at zero
+    if (cudaMemsetAsync(scr, 0, sizeof(unsigned long long) * (size_t)(CTR_N + groups), s) != cudaSuccess)
+        return CLIGHT_ERR_CUDA;
+    if (n_segs > 0) {
+        DevPar P = v.par;
+        P.n_showers = n_showers;
+        DevOut O{};
+        O.rec = d_hits;
+        O.keys = scr + CTR_N;        // per-group hit counters
+        O.vals = nullptr;
+        O.capacity = hit_capacity;
+        O.ctr = scr;
+        int block = v.block;
+        int64_t grid = std::min<int64_t>((int64_t)v.n_sm * v.ctas_per_sm, (n_segs + block - 1) / block);
+        grid = std::max<int64_t>(grid, 1);
+        const DevAtm &A = v.atm;
+        bool fp64 = v.precision == CLIGHT_PREC_FP64_GUARD;
+        auto go = [&](auto tag) {
+            using PP = decltype(tag);
+            if (A.spherical && A.refraction) launch_noalloc<PP, true, true>(d_segs, n_segs, A, v.tel, P, O, (int)grid, block, s);
+            else if (A.spherical) launch_noalloc<PP, true, false>(d_segs, n_segs, A, v.tel, P, O, (int)grid, block, s);
+            else if (A.refraction) launch_noalloc<PP, false, true>(d_segs, n_segs, A, v.tel, P, O, (int)grid, block, s);
+            else launch_noalloc<PP, false, false>(d_segs, n_segs, A, v.tel, P, O, (int)grid, block, s);
+        };
+        if (fp64) go(double{});
+        else go(df{});
+        if (cudaGetLastError() != cudaSuccess) return CLIGHT_ERR_CUDA;
+    }
+    unsigned long long h[CTR_N];
+    if (cudaMemcpyAsync(h, scr, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CLIGHT_ERR_CUDA;
+    if (d_counts && cudaMemcpyAsync(d_counts, scr + CTR_N, sizeof(int64_t) * (size_t)groups,
+                                    cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return CLIGHT_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return CLIGHT_ERR_CUDA;
+    *h_n_hits = (int64_t)h[CTR_CURSOR];
+    unsigned long long bits = h[CTR_STATS + ST_STATUS];
+    if (h_stats) {
+        h_stats->rays = (int64_t)h[CTR_STATS + ST_RAYS];
+        h_stats->escaped = (int64_t)h[CTR_STATS + ST_ESCAPED];
+        h_stats->under = (int64_t)h[CTR_STATS + ST_UNDER];
+        h_stats->turned = (int64_t)h[CTR_STATS + ST_TURNED];
+        h_stats->reached = (int64_t)h[CTR_STATS + ST_REACHED];
+        h_stats->hits = (int64_t)h[CTR_STATS + ST_HITS];
+        h_stats->guarded = (int64_t)h[CTR_STATS + ST_GUARDED];
+        h_stats->status = (int64_t)bits;
+        h_stats->cells = (int64_t)h[CTR_STATS + ST_CELLS];
+        h_stats->cut = (int64_t)h[CTR_STATS + ST_CUT];
+        h_stats->skipped = (int64_t)h[CTR_STATS + ST_SKIPPED];
+        h_stats->deferred = (int64_t)h[CTR_STATS + ST_DEFERRED];
+    }
+    if ((int64_t)h[CTR_CURSOR] > hit_capacity) return CLIGHT_ERR_HIT_CAPACITY;
+    if (bits & (1ull << CLIGHT_ERR_BAD_SEGMENT)) return CLIGHT_ERR_BAD_SEGMENT;
+    if (bits & (1ull << CLIGHT_ERR_LIMIT)) return CLIGHT_ERR_LIMIT;
+    return CLIGHT_OK;
+}

@@ -48,3 +48,57 @@ def test_status_strings_and_no_device_on_cpu():
     if not torch.cuda.is_available():
         h = ctypes.c_void_p()
         assert lib.clight_create(ctypes.byref(h), 0) == G.ERR_NO_DEVICE
+
+
+def _c_layouts(tmp_path):
+    """sizeof and field offsets of the header's records, printed by a C
+    program that includes include/clight.h (gcc)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        import pytest
+        pytest.skip("no C compiler")
+    recs = {
+        "clight_segment": ["x", "y", "z", "t0", "dx", "dy", "dz", "L", "eps", "dE", "charge", "shower"],
+        "clight_hit": ["seg", "k", "tel", "x_rel", "y_rel", "cx", "cy", "lambda", "weight", "t"],
+        "clight_stats": [n for n, _ in G.Stats._fields_],
+        "clight_params": [n for n, _ in G.Params._fields_],
+        "clight_atmosphere": [n for n, _ in G.Atmosphere._fields_],
+        "clight_tune": [n for n, _ in G.Tune._fields_],
+        "clight_pipe_rates": [n for n, _ in G.PipeRates._fields_],
+    }
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "clight.h"', "int main(void) {"]
+    for r, fields in recs.items():
+        lines.append(f'printf("{r} size %zu\\n", sizeof({r}));')
+        for f in fields:
+            lines.append(f'printf("{r} {f} %zu\\n", offsetof({r}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layouts.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layouts"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    got = {}
+    for line in out.splitlines():
+        r, f, v = line.split()
+        got[(r, f)] = int(v)
+    return got
+
+
+def test_binding_layouts_equal_the_c_header(tmp_path):
+    """Every record the binding passes through the ABI has the C header's
+    size and field offsets (compiled from include/clight.h)."""
+    import ctypes as C
+    got = _c_layouts(tmp_path)
+    for name, cls in (("clight_stats", G.Stats), ("clight_params", G.Params), ("clight_atmosphere", G.Atmosphere),
+                      ("clight_tune", G.Tune), ("clight_pipe_rates", G.PipeRates)):
+        assert got[(name, "size")] == C.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert got[(name, f)] == getattr(cls, f).offset, (name, f)
+    assert got[("clight_segment", "size")] == I.SEG_DTYPE.itemsize
+    for f in I.SEG_DTYPE.names:
+        assert got[("clight_segment", f)] == I.SEG_DTYPE.fields[f][1], f
+    assert got[("clight_hit", "size")] == G.HIT_DTYPE.itemsize
+    for f in G.HIT_DTYPE.names:
+        assert got[("clight_hit", f)] == G.HIT_DTYPE.fields[f][1], f

@@ -7,11 +7,11 @@ counts and random numbers are held at their nominal values on both sides.
 The oracle's loss is evaluated at theta (1 +- 1e-4) per component.
 Agreement: 1e-4 relative, component by component (a component that is
 exactly zero in the oracle, a layer no ray reaches, must be zero on the GPU
-too).  The central differences are Richardson-extrapolated from h = 1e-4
-and h/2 (the 0.5 m soft edge curves the loss enough for plain h = 1e-4
-differences to carry ~1e-4 truncation error at 1e6 steps), and hits of
-steps within kappa = 1e3 of the Cherenkov threshold get no upstream
-gradient there (their arrival points are not smooth on the FD scale).  The GPU carries the tangents in binary32 and sums them over every hit,
+too).  Hits of steps within kappa = (delta + eps) / (beta n - 1) = 1e3 of
+the Cherenkov threshold get no upstream gradient in the central-difference
+check (their cone angle, ~ sqrt(beta n - 1), makes their arrival points
+non-smooth on the FD scale); they stay in a second comparison with the
+oracle's dual-number gradient.  The GPU carries the tangents in binary32 and sums them over every hit,
 whose upstream gradients have random signs, so its relative error is of the
 order of 1e-5; the central difference's own error is about 1e-8.
 """
@@ -46,7 +46,7 @@ def _kappa_of_hits(w, hits):
     return kap
 
 
-def _check(n_segs, seed, rel=1e-4, zenith_deg=0.0):
+def _check(n_segs, seed, rel=1e-4, zenith_deg=0.0, h=1e-4):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -88,24 +88,17 @@ def _check(n_segs, seed, rel=1e-4, zenith_deg=0.0):
             assert np.all(erra < rel), (ga, gda, erra)
         gx, gy, gt = gx * far, gy * far, gt * far
         grad = ctx.trace_adjoint(d_segs, len(w.segments), 1, d_hits, len(hits), tg(gx), tg(gy), tg(gt), tg(gY))[:7]
-        # central differences of the FP64 oracle at h = 1e-4 relative and h / 2,
-        # Richardson-extrapolated: the soft edge (sigma = 0.5 m) curves the loss
-        # enough that plain h = 1e-4 differences carry ~1e-4 truncation error
+        # central differences of the FP64 oracle at h relative
         theta = np.array(list(w.atmosphere.c) + [w.atmosphere.K, w.atmosphere.L0])
-
-        def cd(p, rh):
-            hp = rh * theta[p]
+        fd = np.zeros(7)
+        for p in range(7):
+            hp = h * theta[p]
             tp, tm = theta.copy(), theta.copy()
             tp[p] += hp
             tm[p] -= hp
             lp = _oracle_loss(w, atmosphere_at(w.atmosphere, tp), hits, gx, gy, gt, gY, nbc, nbf)
             lm = _oracle_loss(w, atmosphere_at(w.atmosphere, tm), hits, gx, gy, gt, gY, nbc, nbf)
-            return (lp - lm) / (2 * hp)
-        fd = np.zeros(7)
-        for p in range(7):
-            f1 = cd(p, 1e-4)
-            f2 = cd(p, 5e-5)
-            fd[p] = (4.0 * f2 - f1) / 3.0
+            fd[p] = (lp - lm) / (2 * hp)
         zero = fd == 0.0
         assert np.all(grad[zero] == 0.0), (grad, fd)
         err = np.where(zero, 0.0, np.abs(grad - fd) / np.where(zero, 1.0, np.abs(fd)))
@@ -133,8 +126,13 @@ def test_adjoint_matches_oracle_finite_differences_large():
 
 def test_adjoint_matches_oracle_at_the_differentiation_size():
     """10^6 steps of the 1 TeV vertical generator: the size the
-    differentiation workload is stated at."""
-    _check(1_000_000, seed=2)
+    differentiation workload is stated at.  Among 10^6 steps some sit so
+    close to the Cherenkov threshold that their cone angle, ~ sqrt(beta n - 1),
+    moves by a large fraction under a 1e-4 change of the refractivity: the
+    soft yield is then not smooth on that scale (the oracle's own h = 1e-4
+    central differences miss its exact dual-number derivative by 2-5e-4, at
+    h = 1e-6 by 1e-6 to 1e-5), so the differences here take h = 1e-6."""
+    _check(1_000_000, seed=2, h=1e-6)
 
 
 def test_adjoint_matches_oracle_at_60_degrees():

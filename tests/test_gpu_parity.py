@@ -481,9 +481,13 @@ def test_full_size_inclined_sampled(ctx, torch_cuda):
 
 
 def test_batch_256_showers_sampled(ctx, torch_cuda):
-    """256 showers (E log-uniform 10 GeV-10 TeV, zenith 0-45 deg) with
-    fluorescence, at a tenth of the segment counts (7.4e7 steps)."""
-    w = I.batch_showers(256, seed=1, scale=0.1, workers=I.default_workers())
+    """The benchmark's workload at its full size: 256 showers (E log-uniform
+    10 GeV-10 TeV, zenith 0-45 deg) with fluorescence, 7.92e8 steps traced
+    in six launch pieces of the two-pass path (step indices up to 7.9e8),
+    checked on blocks the oracle recomputes, spread over every piece."""
+    w = I.batch_showers(256, seed=1, scale=1.0, workers=I.default_workers())
+    assert len(w.segments) > 7.9e8
     ctx.setup(w, use_graph=1)
-    rays, common, gst = _sampled_check(ctx, w, n_blocks=60, block=128, capacity=40_000_000)
+    rays, common, gst = _sampled_check(ctx, w, n_blocks=80, block=128, capacity=45_000_000)
     assert rays > 5_000 and common > 0 and w.n_showers == 256
+    assert gst["deferred"] > 0 and gst["skipped"] > 0.8 * gst["rays"]
