@@ -508,6 +508,9 @@ def main():
             "peak_basis": peak_basis,
             "source_counted": {"achieved": ops_src / k_s / 1e12, "frac": ops_src / k_s / peak,
                                "ops_per_ray": ops_src / max(1, st["rays"])},
+            "step_skipped_uncredited": {"frac": (ops8 - st.get("step_skipped", 0) * OPS8D_SKIPPED) / k_s / peak,
+                                        "note": "the same per-unit work with the rays decided per step (never "
+                                                "drawn) credited nothing"},
             "hbm": {"achieved_gbs": (n * 64 + nh * 48) / k_s / 1e9,
                     "note": "algorithmic bytes: the 64-byte steps read once and the 48-byte hits written"}}
     if pipes is not None and pipes["mufu_ex2_per_s"] > 0:

@@ -206,6 +206,9 @@ typedef struct {
                            decided from their vacuum line (no quadrature, no landing) */
     int64_t deferred;   /* rays the second pass of the two-pass path traced in full
                            (0 for a call traced in place) */
+    int64_t step_skipped; /* of `skipped`, the rays of steps whose whole Cherenkov cone
+                             the first pass showed to land clear of the array (decided
+                             per step; these rays are never drawn) */
 } clight_stats;
 
 typedef struct clight_ctx clight_ctx;
@@ -315,7 +318,7 @@ clight_status clight_trace_adjoint(clight_ctx *ctx, const clight_segment *d_segs
  * arbitrary order (not sorted, no photon sums), and d_counts (optional,
  * n_showers * n_tel int64, device) receives the per-(shower, telescope)
  * hit counts.  Its scratch -- counters, ray statistics and one hit counter
- * per group -- is a static array in the library image (131,200 bytes, held
+ * per group -- is a static array in the library image (131,208 bytes, held
  * on every GPU that loads the library until the process exits).
  *   - n_showers * n_tel above 16384 returns CLIGHT_ERR_LIMIT before any
  *     launch; other errors as clight_trace.

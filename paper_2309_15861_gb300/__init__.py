@@ -63,7 +63,7 @@ class Params(C.Structure):
 class Stats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in
                 ("rays", "escaped", "under", "turned", "reached", "hits", "guarded", "status", "cells", "cut",
-                 "skipped", "deferred")]
+                 "skipped", "deferred", "step_skipped")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}

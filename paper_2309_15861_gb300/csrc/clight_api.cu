@@ -711,6 +711,7 @@ clight_status finish(clight_ctx *c, int64_t cap, clight_stats *st, int64_t *n_hi
         st->cut = (int64_t)h[CTR_STATS + ST_CUT];
         st->skipped = (int64_t)h[CTR_STATS + ST_SKIPPED];
         st->deferred = (int64_t)h[CTR_STATS + ST_DEFERRED];
+        st->step_skipped = (int64_t)h[CTR_STATS + ST_STEP_SKIPPED];
     }
     c->timed = true;
     if ((int64_t)cursor > cap) return CLIGHT_ERR_HIT_CAPACITY;

@@ -64,6 +64,23 @@ __device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (do
 // narrow): hi is x rounded to nearest-even binary32, lo the rest rounded to
 // binary32.  Valid for |x| in [2^-74, 2^127]; zero maps to zero, and smaller
 // magnitudes (which no position or time reaches) to zero as well.
+// df_hi_from_double_bits gives the same hi alone.
+__device__ __forceinline__ float df_hi_from_double_bits(double x)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    uint32_t sign = (uint32_t)(b >> 63) << 31;
+    int e = (int)((b >> 52) & 0x7ff);
+    if (e < 949) return __uint_as_float(sign);
+    unsigned long long M = (1ull << 52) | (b & 0xFFFFFFFFFFFFFull);
+    uint32_t top = (uint32_t)(M >> 29);
+    uint32_t rem = (uint32_t)(M & 0x1FFFFFFFull);
+    bool up = rem > (1u << 28) || (rem == (1u << 28) && (top & 1u));
+    int fe = e - 1023 + 127;
+    top += up ? 1u : 0u;
+    if (top == (1u << 24)) { top >>= 1; fe += 1; }
+    return __uint_as_float(sign | ((uint32_t)fe << 23) | (top & 0x7FFFFFu));
+}
+
 __device__ __forceinline__ df df_from_double_bits(double x)
 {
     unsigned long long b = (unsigned long long)__double_as_longlong(x);

@@ -120,8 +120,8 @@ struct DevOut {
     unsigned long long *keys;    // sort keys, parallel to rec
     uint32_t *vals;              // 0..n-1
     int64_t capacity;
-    unsigned long long *ctr;     // [0] work counter, [1] hit cursor, [2..12] stats, [14] deferred rays,
-                                 // [15] the deferred kernel's work counter
+    unsigned long long *ctr;     // [0] work counter, [1] hit cursor, [CTR_STATS..] statistics, [CTR_DEFER]
+                                 // deferred rays, [CTR_DEFER_WORK] the deferred kernel's work counter
     float soft_w;                // candidate pass of the adjoint: aperture widening (m)
     // rays the fused kernel leaves to k_trace_deferred: (step << 32) | bunch,
     // the step counted from the launch's first; nullptr = trace every ray in place
@@ -130,10 +130,10 @@ struct DevOut {
 };
 
 // Offsets inside DevOut::ctr.
-enum { CTR_WORK = 0, CTR_CURSOR = 1, CTR_STATS = 2, CTR_DEFER = 14, CTR_DEFER_WORK = 15, CTR_N = 16 };
 enum { ST_RAYS = 0, ST_ESCAPED, ST_UNDER, ST_TURNED, ST_REACHED, ST_HITS, ST_GUARDED, ST_STATUS, ST_CELLS, ST_CUT,
-       ST_SKIPPED, ST_DEFERRED, ST_N };
-static_assert(CTR_STATS + ST_N <= CTR_DEFER, "counter layout");
+       ST_SKIPPED, ST_DEFERRED, ST_STEP_SKIPPED, ST_N };
+enum { CTR_WORK = 0, CTR_CURSOR = 1, CTR_STATS = 2, CTR_DEFER = CTR_STATS + ST_N, CTR_DEFER_WORK = CTR_DEFER + 1,
+       CTR_N = CTR_DEFER + 2 };
 // Status bit (above the CLIGHT_ERR_* codes) of a launch whose deferred-ray
 // queue filled; the host runs such a call again.
 constexpr int kBitDeferFull = 30;

@@ -679,7 +679,7 @@ __device__ __forceinline__ void make_frame(Seg<T, P> &g)
     T ax = g.dx, ay = g.dy, az = g.dz - (T)1;
     T na2 = ax * ax + ay * ay + az * az;
     if (na2 > (T)0) {
-        T inv = (T)1 / Num<T>::sqr(na2);
+        T inv = sizeof(T) == 4 ? (T)rsqrtf((float)na2) : (T)1 / Num<T>::sqr(na2);
         ax *= inv; ay *= inv; az *= inv;
     } else {
         ax = (T)1; ay = (T)0; az = (T)0;
@@ -701,7 +701,22 @@ template <class T> __device__ __forceinline__ T roulette_u(int64_t seg_global, c
     return u01<T>(r.x);
 }
 
-template <bool SPH, bool EXT = true, bool DISP = true>
+// The low words of the pair direction of a binary32 unit vector d: the
+// normalisation residual -(|d|^2 - 1)/2 d, from exact products.
+__device__ __forceinline__ void dir_residual(float dx, float dy, float dz, float &lx, float &ly, float &lz)
+{
+    const df r2 = two_prod(dx, dx) + two_prod(dy, dy) + two_prod(dz, dz);
+    const float e2 = p_f(r2 - 1.0f);
+    lx = -0.5f * e2 * dx; ly = -0.5f * e2 * dy; lz = -0.5f * e2 * dz;
+}
+
+// FULL = false (the first pass of the two-pass path): the same bunch counts,
+// Cherenkov cone and binary32 step, without what only a traced ray needs --
+// the low words of the start, the direction residual, the time, the vacuum-
+// line constants A0, C0 (zero, or the binary32 values).  The guard branches
+// form the pairs they need with the same arithmetic, so the counts are
+// identical in both passes.
+template <bool SPH, bool EXT = true, bool DISP = true, bool FULL = true>
 __device__ __forceinline__ void load_segment_f(const clight_segment &s, int64_t seg_global, const DevAtm &A,
                                                const DevPar &P, Seg<float, df> &g)
 {
@@ -722,21 +737,25 @@ __device__ __forceinline__ void load_segment_f(const clight_segment &s, int64_t 
         make_frame(g);
         return;
     }
-    // unit direction as a pair: the binary32 part normalised, the residual
-    // -(|d|^2 - 1)/2 d (from exact products) as the low part
-    df sq = two_prod(s.dx, s.dx) + two_prod(s.dy, s.dy) + two_prod(s.dz, s.dz);
-    float e = p_f(sq - 1.0f);
-    float f = rsqrtf(1.0f + e);
+    // unit direction as a pair: the binary32 part normalised by one rsqrt,
+    // the residual -(|d|^2 - 1)/2 d (from exact products) as the low part
+    const float f = rsqrtf(n2);
     g.dx = s.dx * f; g.dy = s.dy * f; g.dz = s.dz * f;
-    df r2 = two_prod(g.dx, g.dx) + two_prod(g.dy, g.dy) + two_prod(g.dz, g.dz);
-    float e2 = p_f(r2 - 1.0f);
-    g.lx = -0.5f * e2 * g.dx; g.ly = -0.5f * e2 * g.dy; g.lz = -0.5f * e2 * g.dz;
-    g.x0 = df_from_double_bits(s.x);
-    g.y0 = df_from_double_bits(s.y);
-    g.z0 = df_from_double_bits(s.z);
-    g.t0 = df_from_double_bits(s.t0);
+    if (FULL) {
+        dir_residual(g.dx, g.dy, g.dz, g.lx, g.ly, g.lz);
+        g.x0 = df_from_double_bits(s.x);
+        g.y0 = df_from_double_bits(s.y);
+        g.z0 = df_from_double_bits(s.z);
+        g.t0 = df_from_double_bits(s.t0);
+    } else {
+        g.lx = g.ly = g.lz = 0.0f;
+        g.x0 = df_make(df_hi_from_double_bits(s.x));
+        g.y0 = df_make(df_hi_from_double_bits(s.y));
+        g.z0 = df_make(df_hi_from_double_bits(s.z));
+        g.t0 = df_make(0.0f);
+    }
     g.rz0 = SPH ? g.z0 + df{A.re_hi, A.re_lo} : g.z0;
-    if (SPH) {
+    if (SPH && FULL) {
         // for the vacuum line of every Cherenkov photon of the step:
         // |R0 + l d|^2 - r_obs^2 = C0 + l (2 A0 + l)
         g.A0 = df{g.dz, g.lz} * g.rz0 + (g.dx * g.x0.hi + g.dy * g.y0.hi);
@@ -769,7 +788,13 @@ __device__ __forceinline__ void load_segment_f(const clight_segment &s, int64_t 
     // near the threshold (kappa = (delta + eps) / g1 above 16, or the sign of
     // g1 not certain) the refractivity in FP32 pairs: g1 to ~1e-12 relative
     if (!(DISP && A.disp) && z2 > 0.0f && s.L > 0.0f && g1 > -eg && 16.0f * g1 < dl + eps) {
-        const df dlp = delta_pair<SPH>(A, g.x0, g.y0, g.z0, df{g.dx, g.lx}, df{g.dy, g.ly}, df{g.dz, g.lz}, s.L);
+        float lx = g.lx, ly = g.ly, lz = g.lz;
+        df x0 = g.x0, y0 = g.y0, z0 = g.z0;
+        if (!FULL) {
+            dir_residual(g.dx, g.dy, g.dz, lx, ly, lz);
+            x0 = df_from_double_bits(s.x); y0 = df_from_double_bits(s.y); z0 = df_from_double_bits(s.z);
+        }
+        const df dlp = delta_pair<SPH>(A, x0, y0, z0, df{g.dx, lx}, df{g.dy, ly}, df{g.dz, lz}, s.L);
         const df g1p = (dlp - eps) - dlp * eps;
         dl = p_f(dlp);
         g1 = p_f(g1p);
@@ -839,9 +864,11 @@ __device__ __forceinline__ void load_segment_f(const clight_segment &s, int64_t 
     if (g.cut) guard = false;
     if (guard || fguard) {
         g.guarded = 1;
+        float lx = g.lx, ly = g.ly, lz = g.lz;
+        if (!FULL) dir_residual(g.dx, g.dy, g.dz, lx, ly, lz);
         double Ncd, sin2d, kapd, Nfd;
-        yield_fp64<SPH>(s, A, P, (double)g.dx + (double)g.lx, (double)g.dy + (double)g.ly,
-                        (double)g.dz + (double)g.lz, &Ncd, &sin2d, &kapd, &Nfd);
+        yield_fp64<SPH>(s, A, P, (double)g.dx + (double)lx, (double)g.dy + (double)ly, (double)g.dz + (double)lz,
+                        &Ncd, &sin2d, &kapd, &Nfd);
         if (guard) {
             double nb = ceil(Ncd / P.bunch_d);
             g.n_c = (uint32_t)nb;

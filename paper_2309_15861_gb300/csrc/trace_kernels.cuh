@@ -119,6 +119,64 @@ __device__ __forceinline__ void flush_stats(const uint32_t (&vals)[ST_N], unsign
     if (lane == 0 && sb) atomicOr(O.ctr + CTR_STATS + ST_STATUS, (unsigned long long)sb);
 }
 
+// Position of the set bit of rank r (counted from 0 at the low end) in m;
+// r < popc(m).
+__device__ __forceinline__ int nth_set_bit(unsigned m, unsigned r)
+{
+    int p = 0;
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) {
+        const unsigned c = __popc((m >> p) & ((1u << w) - 1u));
+        if (r >= c) { r -= c; p += w; }
+    }
+    return p;
+}
+
+// A warp's entries for the deferred-ray queue, held in registers: lane L
+// keeps the warp's L-th buffered entry.  They leave 32 at a time, one atomic
+// on the queue counter and one coalesced 256-byte store per flush.  (One
+// counter that every warp bumps for every round with a deferred ray limits
+// the first pass to the rate at which one L2 slice serves atomics on one
+// address.)  Every member is called by all 32 lanes together.
+struct WarpQueue {
+    unsigned long long e = 0;
+    uint32_t n = 0;                  // warp-uniform: entries held, in lanes 0 .. n-1
+
+    __device__ __forceinline__ void flush(uint32_t cnt, const DevOut &O, int lane, unsigned &status_bits)
+    {
+        unsigned long long b = 0;
+        if (lane == 0) b = atomicAdd(O.ctr + CTR_DEFER, (unsigned long long)cnt);
+        b = __shfl_sync(FULL_MASK, b, 0);
+        if ((uint32_t)lane < cnt) {
+            if ((int64_t)(b + lane) < O.defer_cap) O.defer[b + lane] = e;
+            else status_bits |= 1u << kBitDeferFull;
+        }
+    }
+    // Appends the entries of the lanes with push set, in lane order.
+    __device__ __forceinline__ void push(bool p, unsigned long long entry, const DevOut &O, int lane,
+                                         unsigned &status_bits)
+    {
+        const unsigned m = __ballot_sync(FULL_MASK, p);
+        if (!m) return;
+        const uint32_t k = __popc(m);
+        const uint32_t r = (uint32_t)(lane - (int)n) & 31u;     // rank of the new entry this lane takes
+        const unsigned long long v = __shfl_sync(FULL_MASK, entry, nth_set_bit(m, r < k ? r : 0u));
+        if ((uint32_t)lane >= n && r < k) e = v;
+        if (n + k >= 32) {
+            flush(32, O, lane, status_bits);
+            if ((uint32_t)lane < n && r < k) e = v;             // ranks 32 - n .. k - 1 wrap to lanes 0 ..
+            n = n + k - 32;
+        } else {
+            n += k;
+        }
+    }
+    __device__ __forceinline__ void finish(const DevOut &O, int lane, unsigned &status_bits)
+    {
+        if (n) flush(n, O, lane, status_bits);
+        n = 0;
+    }
+};
+
 // First pass of the deferred path: ray k of the step in record l, its
 // direction and emission point in binary32 only, and what the full trace
 // would conclude when that is already certain.  Returns 1 (escapes: points
@@ -236,6 +294,7 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
     uint32_t c_rays = 0, c_esc = 0, c_under = 0, c_turn = 0, c_reach = 0, c_hits = 0, c_guard = 0, c_cells = 0;
     uint32_t c_cut = 0, c_skip = 0;
     unsigned status_bits = 0;
+    WarpQueue dq;                    // deferred rays (DEFER)
     // the deferred first pass (without FEAT_EXT) loads each group's records
     // while the group before is worked on: the next group is claimed and its
     // records copied into the warp's stage (behind the map) asynchronously
@@ -389,19 +448,7 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
                     c_esc += cls == 1; c_under += cls == 2;
                     c_reach += cls == 6; c_skip += cls == 6;
                 }
-                unsigned m = __ballot_sync(FULL_MASK, push);
-                if (m) {
-                    unsigned long long base = 0;
-                    if (lane == 0) base = atomicAdd(O.ctr + CTR_DEFER, (unsigned long long)__popc(m));
-                    base = __shfl_sync(FULL_MASK, base, 0);
-                    unsigned long long idx = base + __popc(m & lanemask_lt());
-                    if (push) {
-                        if ((int64_t)idx < O.defer_cap)
-                            O.defer[idx] = ((unsigned long long)seg_local << 32) | (unsigned long long)k;
-                        else
-                            status_bits |= 1u << kBitDeferFull;
-                    }
-                }
+                dq.push(push, ((unsigned long long)seg_local << 32) | (unsigned long long)k, O, lane, status_bits);
                 continue;
             }
             const bool act = active;
@@ -484,8 +531,9 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
         }
         __syncwarp();
     }
+    if (DEFER) dq.finish(O, lane, status_bits);
     // ---- statistics: one atomic per warp and counter
-    const uint32_t vals[ST_N] = {c_rays, c_esc, c_under, c_turn, c_reach, c_hits, c_guard, 0u, c_cells, c_cut, c_skip, 0u};
+    const uint32_t vals[ST_N] = {c_rays, c_esc, c_under, c_turn, c_reach, c_hits, c_guard, 0u, c_cells, c_cut, c_skip, 0u, 0u};
     flush_stats(vals, status_bits, O, lane);
 }
 
@@ -586,6 +634,52 @@ __device__ __forceinline__ int classify_ray(const ClsRec &R, float ell, float dx
     return clear_miss(xe, ye, ze, dx, dy, dz, he, cos_obs, 1.0f, A, Tl, clr, SPH, REFR) ? 6 : 0;
 }
 
+// Does every Cherenkov photon of a gated step land clear of the array?
+// The photon directions are u(c) = ct d + st (cos c e1 + sin c e2); a ray
+// from height dz above the plane z = h_obs crosses it at dz u_xy / (-u_z)
+// from its emission point, and u_x / (-u_z) = (a0 + a . v) / (b0 + b . v)
+// (v = (cos c, sin c)) ranges over the roots of
+// (b0^2 - |b|^2) l^2 - 2 (a0 b0 - a . b) l + a0^2 - |a|^2 = 0 (the same for
+// y).  The emission point moves linearly along the step, so the footprint
+// of the whole step lies in the box spanned by its two ends.  The step's
+// search radius (rsb + cB (height + zeta)) is taken at its largest over
+// that box; the roots carry a rounding margin from the discriminant's
+// binary32 error.  True when the box, widened by that radius, misses the
+// array's bounding box (which holds every sphere) -- then every ray of the
+// step would be skipped by classify_cherenkov_gated, and all are counted
+// as skipped without being drawn.
+__device__ __forceinline__ bool cone_lands_clear(const Seg<float, df> &g, const ClsRec &r, float ct, float st,
+                                                 const DevAtm &A, const DevTel &Tl)
+{
+    const float dz0 = r.z0 - A.h_obs, dz1 = dz0 + r.L * g.dz;       // heights of both ends above the plane
+    const float he_lo = r.h_mid - 0.5f * r.L * fabsf(r.hd), he_hi = r.h_mid + 0.5f * r.L * fabsf(r.hd);
+    if (!(dz0 > 1.0f) || !(dz1 > 1.0f) || !(he_lo > A.h_obs + 0.2f)) return false;
+    const float b0 = -ct * g.dz, b1 = -st * g.e1z, b2 = -st * g.e2z;
+    const float A2 = b0 * b0 - (b1 * b1 + b2 * b2);                   // >= 0.05^2 (the gate)
+    const float iA = rcp_approx(A2);
+    auto roots = [&](float a0, float a1, float a2, float &lo, float &hi) {
+        const float B1 = a0 * b0 - (a1 * b1 + a2 * b2);
+        const float C0 = a0 * a0 - (a1 * a1 + a2 * a2);
+        const float disc = fmaxf(B1 * B1 - A2 * C0, 0.0f);
+        const float sq = sqrt_approx(disc);
+        // the discriminant's binary32 error can reach ~4e-7 of its terms
+        const float m = (sqrt_approx(4.0e-7f * (B1 * B1 + fabsf(A2 * C0))) + 4.0e-7f * (fabsf(B1) + sq)) * iA +
+                        1.0e-6f;
+        lo = (B1 - sq) * iA - m;
+        hi = (B1 + sq) * iA + m;
+    };
+    float xl, xh, yl, yh;
+    roots(ct * g.dx, st * g.e1x, st * g.e2x, xl, xh);
+    roots(ct * g.dy, st * g.e1y, st * g.e2y, yl, yh);
+    const float x1 = r.x0 + r.L * g.dx, y1 = r.y0 + r.L * g.dy;
+    const float bx_lo = fminf(r.x0 + dz0 * xl, x1 + dz1 * xl), bx_hi = fmaxf(r.x0 + dz0 * xh, x1 + dz1 * xh);
+    const float by_lo = fminf(r.y0 + dz0 * yl, y1 + dz1 * yl), by_hi = fmaxf(r.y0 + dz0 * yh, y1 + dz1 * yh);
+    const float ax = fmaxf(fabsf(bx_lo), fabsf(bx_hi)), ay = fmaxf(fabsf(by_lo), fabsf(by_hi));
+    const float zeta = (ax * ax + ay * ay) * A.inv_r_obs;
+    const float rs = (r.rsb + r.cB * ((he_hi - A.h_obs) + zeta)) * 1.0001f + 0.5f;
+    return bx_hi + rs < Tl.xmin || bx_lo - rs > Tl.xmax || by_hi + rs < Tl.ymin || by_lo - rs > Tl.ymax;
+}
+
 template <bool SPH, bool REFR>
 __global__ void __launch_bounds__(256, 4)
 k_classify(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid_constant__ DevAtm A,
@@ -607,23 +701,9 @@ k_classify(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid
     // bound pieces that depend on the array and the atmosphere only
     const float dzmax = fmaxf(fabsf(Tl.zmax - A.h_obs), fabsf(Tl.zmin - A.h_obs));
     const float co2_min = 2.1f * A.delta_max + 2.6e-3f;
-    uint32_t c_rays = 0, c_esc = 0, c_under = 0, c_skip = 0, c_guard = 0;
+    uint32_t c_rays = 0, c_esc = 0, c_under = 0, c_skip = 0, c_guard = 0, c_whole = 0;
     unsigned status_bits = 0;
-    // queue appends are completed one round later, so that the atomic that
-    // reserves their slots returns while the next round is worked on
-    unsigned pend_m = 0;
-    unsigned long long pend_base = 0, pend_entry = 0;
-    auto complete_appends = [&](unsigned lt_mask) {
-        if (pend_m) {
-            const unsigned long long qb = __shfl_sync(FULL_MASK, pend_base, 0);
-            if (pend_m & (1u << lane)) {
-                const unsigned long long qi = qb + __popc(pend_m & lt_mask);
-                if ((int64_t)qi < O.defer_cap) O.defer[qi] = pend_entry;
-                else status_bits |= 1u << kBitDeferFull;
-            }
-            pend_m = 0;
-        }
-    };
+    WarpQueue dq;                    // the rays left to k_trace_deferred
     // work stealing: a claim is Pp.chunk consecutive groups of 32 steps; the
     // next claim's atomic is issued one group before it is needed, and each
     // group's records are copied in while the group before is worked on
@@ -664,10 +744,10 @@ k_classify(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid
         // ---- per-step set-up: the counts exactly as the second pass forms them
         uint32_t nc = 0, nf = 0;
         ClsRec r;
-        bool gated = false;
+        bool gated = false, whole = false;
         if (si < n_segs) {
             Seg<float, df> g;
-            load_segment_f<SPH, false, false>(s, Pp.seg_base + si, A, Pp, g);
+            load_segment_f<SPH, false, false, false>(s, Pp.seg_base + si, A, Pp, g);
             if (g.bad) status_bits |= 1u << g.bad;
             c_guard += g.guarded;
             nc = g.n_c;
@@ -680,15 +760,18 @@ k_classify(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid
             r.b1x = st * g.e1x; r.b1y = st * g.e1y; r.b1z = st * g.e1z;
             r.b2x = st * g.e2x; r.b2y = st * g.e2y; r.b2z = st * g.e2z;
             // dh/dl: the step direction's component along the local vertical
+            // (approximate square roots and reciprocals: each bound below
+            // carries margins far above their ~1e-7 relative error)
             float sdz = -g.dz;                                  // cos of the step's zenith angle (flat frame)
-            float szd = sqrtf(g.dx * g.dx + g.dy * g.dy);        // its sine
+            float szd = sqrt_approx(g.dx * g.dx + g.dy * g.dy); // its sine
             float cps = sdz, sps = szd;                          // the same about the Earth radius at the start
+            float r0 = 1.0f, ir0 = 1.0f;
             if (SPH) {
                 const float Rz0 = r.z0 + A.R_E;
-                const float r0 = sqrtf(r.x0 * r.x0 + r.y0 * r.y0 + Rz0 * Rz0);
-                const float ir0 = 1.0f / r0;
+                ir0 = rsqrt_approx(r.x0 * r.x0 + r.y0 * r.y0 + Rz0 * Rz0);
+                r0 = rcp_approx(ir0);
                 const float c1 = g.dy * Rz0 - g.dz * r.y0, c2 = g.dz * r.x0 - g.dx * Rz0, c3 = g.dx * r.y0 - g.dy * r.x0;
-                sps = sqrtf(c1 * c1 + c2 * c2 + c3 * c3) * ir0;
+                sps = sqrt_approx(c1 * c1 + c2 * c2 + c3 * c3) * ir0;
                 cps = -(g.dx * r.x0 + g.dy * r.y0 + g.dz * Rz0) * ir0;
                 r.hd = -cps;
             } else {
@@ -704,45 +787,48 @@ k_classify(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid
                 if (SPH) {
                     // landing zenith sine: (r_e / r_obs) sin(psi_e), psi_e <= psi_d + theta_c + L / r0
                     const float csum = cps * ct - sps * st;
-                    const float Rz0 = r.z0 + A.R_E;
-                    const float r0 = sqrtf(r.x0 * r.x0 + r.y0 * r.y0 + Rz0 * Rz0);
-                    const float se = sps * ct + cps * st + (r.L + 1.0f) / r0 + 4.0e-6f;
+                    const float se = sps * ct + cps * st + (r.L + 1.0f) * ir0 + 4.0e-6f;
                     const float so = (r0 + r.L) * se * A.inv_r_obs * 1.000001f;
                     const float co2 = 1.0f - so * so;
                     ok = ok && csum > 0.0f && so < 1.0f && co2 > co2_min;
-                    cobs_lo = ok ? sqrtf(co2) * 0.999999f : 0.0f;
+                    cobs_lo = ok ? sqrt_approx(co2) * 0.999999f : 0.0f;
                 }
                 const float mu = fminf(cobs_lo, dzlo) - 1.0e-3f;
                 ok = ok && mu > 0.05f;
                 if (ok) {
-                    const float im = 1.0f / mu;
-                    const float sd = REFR ? 1.25f * sqrtf(1.0f - mu * mu) * A.delta_max : 0.0f;
+                    const float im = rcp_approx(mu) * 1.000001f;
+                    const float sd = REFR ? 1.25f * 1.000001f * sqrt_approx(1.0f - mu * mu) * A.delta_max : 0.0f;
                     const float czb = dzlo - sd * im - 1.0e-5f;
                     ok = czb > 0.05f;
                     if (ok) {
                         r.cB = sd * (im * im * im) * 1.0001f;
-                        r.rsb = ((Tl.Rmax + dzmax * sqrtf(1.0f - czb * czb)) / czb + 2.0e-3f + 0.05f) * 1.0001f +
-                                1.0e-3f;
+                        r.rsb = ((Tl.Rmax + dzmax * sqrt_approx(1.0f - czb * czb)) * rcp_approx(czb) + 2.0e-3f +
+                                 0.05f) * 1.0001f + 1.0e-3f;
                     }
                 }
                 gated = ok;
+                if (gated) whole = cone_lands_clear(g, r, ct, st, A, Tl);
             }
             r.nc = nc;
         }
+        // a step whose every Cherenkov photon provably lands clear of the
+        // array: its rays are counted here and never enumerated
+        const uint32_t ncv = whole ? 0u : nc;
+        if (whole) { c_rays += nc; c_skip += nc; c_whole += nc; }
         // ---- virtual steps: the Cherenkov steps with bunches, then the fluorescence ones
-        const unsigned bC = __ballot_sync(FULL_MASK, nc > 0), bF = __ballot_sync(FULL_MASK, nf > 0);
+        const unsigned bC = __ballot_sync(FULL_MASK, ncv > 0), bF = __ballot_sync(FULL_MASK, nf > 0);
         const unsigned lt = lanemask_lt();
-        uint32_t incC = nc, incF = nf;
+        uint32_t incC = ncv, incF = nf;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t vc = __shfl_up_sync(FULL_MASK, incC, o), vf = __shfl_up_sync(FULL_MASK, incF, o);
             if (lane >= o) { incC += vc; incF += vf; }
         }
         const uint32_t totC = __shfl_sync(FULL_MASK, incC, 31), totF = __shfl_sync(FULL_MASK, incF, 31);
-        const uint32_t eC = incC - nc, eF = totC + incF - nf;  // start positions in the group's ray sequence
+        const uint32_t eC = incC - ncv, eF = totC + incF - nf;  // start positions in the group's ray sequence
         if (totF > 0x7fffffffu - totC) { status_bits |= 1u << CLIGHT_ERR_LIMIT; continue; }
         if (si < n_segs) rec[lane] = r;
-        if (nc > 0) vl[__popc(bC & lt)] = make_uint2(eC, (uint32_t)lane | (gated ? kVGated : 0u));
+        if (ncv > 0) vl[__popc(bC & lt)] = make_uint2(eC, (uint32_t)lane | (gated ? kVGated : 0u));
         if (nf > 0) vl[__popc(bC) + __popc(bF & lt)] = make_uint2(eF, (uint32_t)lane | 32u);
         __syncwarp();
         const uint32_t total = totC + totF;
@@ -751,7 +837,7 @@ k_classify(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid
         int carry = -1;
         for (uint32_t base = 0; base < total; base += 32) {
             uint32_t bits = 0;
-            if (nc > 0 && eC - base < 32u) bits |= 1u << (eC - base);
+            if (ncv > 0 && eC - base < 32u) bits |= 1u << (eC - base);
             if (nf > 0 && eF - base < 32u) bits |= 1u << (eF - base);
             const unsigned M = __reduce_or_sync(FULL_MASK, bits);
             const int idx = carry + __popc(M & (lt | (1u << lane)));
@@ -800,26 +886,19 @@ k_classify(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid
                     kq = R.nc + kk;
                     const float u3 = u01<float>(x.w);
                     const float cz = 2.0f * u3 - 1.0f;
-                    const float sz = sqrtf((1.0f - cz) * (1.0f + cz));
+                    const float sz = sqrt_approx((1.0f - cz) * (1.0f + cz));
                     cls = classify_ray<SPH, REFR>(R, ell, sz * cs, sz * sn, cz, A, Tl, clr);
                 }
                 c_esc += cls == 1;
                 c_under += cls == 2;
                 c_skip += cls == 6;
             }
-            const bool push = cls == 0;
-            complete_appends(lt);
-            const unsigned m = __ballot_sync(FULL_MASK, push);
-            if (m) {
-                if (lane == 0) pend_base = atomicAdd(O.ctr + CTR_DEFER, (unsigned long long)__popc(m));
-                pend_m = m;
-                pend_entry = ((unsigned long long)seg_local << 32) | (unsigned long long)kq;
-            }
+            dq.push(cls == 0, ((unsigned long long)seg_local << 32) | (unsigned long long)kq, O, lane, status_bits);
         }
         __syncwarp();
     }
-    complete_appends(lanemask_lt());
-    const uint32_t vals[ST_N] = {c_rays, c_esc, c_under, 0u, c_skip, 0u, c_guard, 0u, 0u, 0u, c_skip, 0u};
+    dq.finish(O, lane, status_bits);
+    const uint32_t vals[ST_N] = {c_rays, c_esc, c_under, 0u, c_skip, 0u, c_guard, 0u, 0u, 0u, c_skip, 0u, c_whole};
     flush_stats(vals, status_bits, O, lane);
 }
 
@@ -889,7 +968,7 @@ k_trace_deferred(const clight_segment *__restrict__ segs, const __grid_constant_
             ++c_def;
         }
     }
-    const uint32_t vals[ST_N] = {0u, c_esc, c_under, c_turn, c_reach, c_hits, 0u, 0u, c_cells, 0u, 0u, c_def};
+    const uint32_t vals[ST_N] = {0u, c_esc, c_under, c_turn, c_reach, c_hits, 0u, 0u, c_cells, 0u, 0u, c_def, 0u};
     flush_stats(vals, status_bits, O, lane);
 }
 
@@ -924,7 +1003,7 @@ k_trace_fp64(const clight_segment *__restrict__ segs, int64_t n_segs, const __gr
             c_hits += hit_test<double, double, false>(o, i, seg_global, k, g.shower, A, Tl, Pp, O, status_bits);
         }
     }
-    uint32_t vals[ST_N] = {c_rays, c_esc, c_under, c_turn, c_reach, c_hits, 0u, 0u, c_cells, c_cut, 0u, 0u};
+    uint32_t vals[ST_N] = {c_rays, c_esc, c_under, c_turn, c_reach, c_hits, 0u, 0u, c_cells, c_cut, 0u, 0u, 0u};
     for (int q = 0; q < ST_N; ++q)
         if (vals[q] && q != ST_STATUS) atomicAdd(O.ctr + CTR_STATS + q, (unsigned long long)vals[q]);
     if (status_bits) atomicOr(O.ctr + CTR_STATS + ST_STATUS, (unsigned long long)status_bits);

@@ -10,7 +10,7 @@ namespace clight {
 // Scratch of clight_trace_noalloc: the work and hit counters and the ray
 // statistics (CTR_N words), then one hit counter per (shower, telescope)
 // group.  It lives in the library image, so the entry point needs no
-// cudaMalloc; every GPU that loads the library holds these 131,200 bytes
+// cudaMalloc; every GPU that loads the library holds these 131,208 bytes
 // until the process exits.
 constexpr int kNoallocMaxGroups = 16384;
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[CTR_N + kNoallocMaxGroups];
@@ -143,6 +143,7 @@ extern "C" clight_status clight_trace_noalloc(clight_ctx *ctx, const clight_segm
         h_stats->cut = (int64_t)h[CTR_STATS + ST_CUT];
         h_stats->skipped = (int64_t)h[CTR_STATS + ST_SKIPPED];
         h_stats->deferred = (int64_t)h[CTR_STATS + ST_DEFERRED];
+        h_stats->step_skipped = (int64_t)h[CTR_STATS + ST_STEP_SKIPPED];
     }
     if ((int64_t)h[CTR_CURSOR] > hit_capacity) return CLIGHT_ERR_HIT_CAPACITY;
     if (bits & (1ull << CLIGHT_ERR_BAD_SEGMENT)) return CLIGHT_ERR_BAD_SEGMENT;

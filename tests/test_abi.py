@@ -30,7 +30,7 @@ def test_library_exports_every_declared_symbol():
 def test_record_layouts_match_the_header():
     assert I.SEG_DTYPE.itemsize == 64
     assert G.HIT_DTYPE.itemsize == 48
-    assert ctypes.sizeof(G.Stats) == 96
+    assert ctypes.sizeof(G.Stats) == 104
     assert ctypes.sizeof(G.Params) == 192
     assert ctypes.sizeof(G.Atmosphere) == 8 + 3 * 64 + 7 * 8 + 8 + 16
     offs = {n: I.SEG_DTYPE.fields[n][1] for n in I.SEG_DTYPE.names}
