@@ -321,6 +321,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-secondary", action="store_true")
+    ap.add_argument("--noalloc", action="store_true",
+                    help="also time clight_trace_noalloc (unsorted hits, no allocation) on the same steps")
     ap.add_argument("--tune-sample", type=int, default=40_000_000)
     ap.add_argument("--propagator", default="exact", choices=["exact", "straight"],
                     help="exact: the refracted ray's deviation integrated (default); straight: the vacuum "
@@ -620,6 +622,24 @@ def main():
                      "kernel_ms": k1, "rays": st1["rays"], "skipped": st1["skipped"], "deferred": st1["deferred"]}
         del s1
 
+    # ---- the entry point that allocates nothing (in-place kernel, unsorted hits)
+    noalloc = None
+    if args.noalloc:
+        s0 = torch.cuda.current_stream()
+        for _ in range(2):
+            code_n, nh_n, st_n = ctx.trace_noalloc(segs, n, ns, hits, cap, counts, raise_on_error=False)
+        na_ms = []
+        for _ in range(max(3, args.steps // 4)):
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(s0)
+            code_n, nh_n, st_n = ctx.trace_noalloc(segs, n, ns, hits, cap, counts, raise_on_error=False)
+            a1.record(s0)
+            torch.cuda.synchronize()
+            na_ms.append(a0.elapsed_time(a1))
+        m_na = statistics.median(na_ms)
+        noalloc = {"status": int(code_n), "ms_per_step": m_na, "value": st_n["rays"] / (m_na / 1e3), "unit": UNIT,
+                   "hits": int(nh_n), "note": "clight_trace_noalloc: static scratch, unsorted hits, per-group counts"}
+
     cpu = err = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu, blocks, blk, ref_hits = cpu_baseline(w, single_s=4.0, keep_hits=True)
@@ -654,6 +674,8 @@ def main():
             line["adjoint"] = adjoint
         if cut is not None:
             line["angular_cut"] = cut
+        if noalloc is not None:
+            line["noalloc"] = noalloc
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
