@@ -236,7 +236,9 @@ clight_status clight_set_params(clight_ctx *ctx, const clight_params *par);
  * launch over the segments, then a sort of the hits by
  * (shower, telescope, segment, bunch) and per-(shower, telescope) counts and
  * FP64 photon sums.
- *   d_segs        n_segs segments (device, read only)
+ *   d_segs        n_segs segments (device, read only, 16-byte aligned: a
+ *                 misaligned array is refused with CLIGHT_ERR_ARG; this holds
+ *                 for every entry point that takes d_segs)
  *   d_hits        hit_capacity records (device); the first *h_n_hits are
  *                 written, sorted
  *   d_counts      n_showers * n_tel int64 (device) or NULL

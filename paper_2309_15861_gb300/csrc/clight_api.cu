@@ -773,6 +773,7 @@ clight_status run(clight_ctx *c, const clight_segment *segs, int64_t n_segs, int
                   bool fp64)
 {
     if (!c || (n_segs > 0 && !segs) || (cap > 0 && !hits) || !n_hits) return CLIGHT_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(segs) & 15u) return CLIGHT_ERR_ARG;   // records are copied in 16-byte pieces
     DeviceGuard dg(c->device);
     if (!dg.ok) return CLIGHT_ERR_CUDA;
     clight_status r;
@@ -873,7 +874,7 @@ extern "C" clight_status clight_autotune(clight_ctx *c, const clight_segment *d_
                                          void *stream)
 {
     if (!c || !out || !d_segs || n_segs < 1 || n_sample < 1 || reps < 1 || !(bunch_max > 0) || n_showers < 1 ||
-        hit_capacity < 0 || (hit_capacity > 0 && !d_hits))
+        hit_capacity < 0 || (hit_capacity > 0 && !d_hits) || (reinterpret_cast<uintptr_t>(d_segs) & 15u))
         return CLIGHT_ERR_ARG;
     if (!c->atm_set || !c->tel_set) return CLIGHT_ERR_ARG;
     if (n_segs > (int64_t(1) << 31)) return CLIGHT_ERR_LIMIT;
@@ -1010,7 +1011,8 @@ extern "C" clight_status clight_trace_adjoint(clight_ctx *c, const clight_segmen
         return CLIGHT_ERR_ARG;
     if (c->atm.disp) return CLIGHT_ERR_ARG;       // the tangents assume no dispersion
     if (c->par.prop == CLIGHT_PROP_STRAIGHT) return CLIGHT_ERR_ARG;   // they are those of the exact propagator
-    if ((n_segs > 0 && !d_segs) || (n_hits > 0 && !d_hits) || !(soft_s > 0) || !(soft_w >= 0))
+    if ((n_segs > 0 && !d_segs) || (n_hits > 0 && !d_hits) || !(soft_s > 0) || !(soft_w >= 0) ||
+        (reinterpret_cast<uintptr_t>(d_segs) & 15u))
         return CLIGHT_ERR_ARG;
     if (n_segs > (int64_t(1) << 31)) return CLIGHT_ERR_LIMIT;
     if ((int64_t)n_showers * c->tel.n_tel > (int64_t(1) << 24)) return CLIGHT_ERR_LIMIT;

@@ -145,11 +145,16 @@ template <> struct AtmT<float> {
     static __device__ __forceinline__ float delta(const DevAtm &A, float h)
     {
         if (h >= A.h_top) return 0.0f;
-        int i = 0;
+        // the layer's constants picked by selects (every parameter read at a
+        // constant index, so no lane-dependent constant-bank access)
+        float kb = A.kb[0], nl = A.nl2c[0];
 #pragma unroll
-        for (int j = 1; j < kMaxLayers; ++j)
-            if (j < A.n_layers && h >= A.h_lo[j]) i = j;
-        return A.kb[i] * exp2f(h * A.nl2c[i]);
+        for (int j = 1; j < kMaxLayers; ++j) {
+            const bool in = j < A.n_layers && h >= A.h_lo[j];
+            kb = in ? A.kb[j] : kb;
+            nl = in ? A.nl2c[j] : nl;
+        }
+        return kb * exp2f(h * nl);
     }
 };
 template <> struct AtmT<double> {

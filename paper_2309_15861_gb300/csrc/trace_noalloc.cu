@@ -79,7 +79,7 @@ extern "C" clight_status clight_trace_noalloc(clight_ctx *ctx, const clight_segm
     CtxView v;
     if (!ctx_view(ctx, &v)) return CLIGHT_ERR_ARG;
     if (n_segs < 0 || n_showers < 1 || hit_capacity < 0 || !h_n_hits || (n_segs > 0 && !d_segs) ||
-        (hit_capacity > 0 && !d_hits))
+        (hit_capacity > 0 && !d_hits) || (reinterpret_cast<uintptr_t>(d_segs) & 15u))
         return CLIGHT_ERR_ARG;
     if (n_segs > (int64_t(1) << 31)) return CLIGHT_ERR_LIMIT;
     int64_t groups = (int64_t)n_showers * v.tel.n_tel;

@@ -428,6 +428,13 @@ def test_edge_cases(ctx, torch_cuda):
         ctx.trace(segs, -1, 1, hits, 4096)
     with pytest.raises(G.ClightError):
         ctx.trace(segs, 10, 0, hits, 4096)
+    # a step array not on a 16-byte boundary is refused before any launch
+    code, _, _ = ctx.trace(segs[8:], 10, 1, hits, 4096, raise_on_error=False)
+    assert code == G.ERR_ARG
+    code, _, _ = ctx.trace_noalloc(segs[8:], 10, 1, hits, 4096, raise_on_error=False)
+    assert code == G.ERR_ARG
+    code, nh, st = ctx.trace(segs[64:], 10, 1, hits, 4096)      # one record in: aligned
+    assert code == G.OK and st["rays"] > 0
 
 
 def _sampled_check(ctx, w, n_blocks=60, block=256, capacity=8_000_000, seed=0):
