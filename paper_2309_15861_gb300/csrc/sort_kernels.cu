@@ -13,6 +13,7 @@
 // caller's capacity the count is taken as zero and nothing is written.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "internal.h"
@@ -20,13 +21,21 @@
 namespace clight {
 
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
-constexpr int kTile = kSortThreads * kSortItems;        // 4096 keys per tile
+constexpr int kSortItems = 8;
+constexpr int kTile = kSortThreads * kSortItems;        // 2048 keys per tile
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanChunk = kScanThreads * kScanItems;   // 4096 entries per block
 
 int sort_tile_items() { return kTile; }
+
+static int device_sms()
+{
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        n = 0;
+    return n > 0 ? n : 1;
+}
 int64_t scan_block_sums_needed(int64_t n) { return (n + kScanChunk - 1) / kScanChunk; }
 
 __device__ __forceinline__ int64_t valid_hits(const unsigned long long *ctr, int64_t capacity)
@@ -42,25 +51,32 @@ __device__ __forceinline__ unsigned lane_lt()
     return m;
 }
 
-// Per-tile digit histogram, stored digit-major: hist[d * max_tiles + tile].
+__device__ __forceinline__ int64_t live_tiles(int64_t n) { return (n + kTile - 1) / kTile; }
+
+// Per-tile digit histograms of the live tiles (those holding hits), stored
+// digit-major with the live tile count as stride: hist[d * nt + tile].  A
+// bounded grid walks the tiles, so the work follows the hit count, not the
+// buffer's capacity.
 __global__ void __launch_bounds__(kSortThreads)
 k_radix_hist(const unsigned long long *__restrict__ keys, const unsigned long long *ctr, int64_t capacity,
-             int shift, uint32_t *__restrict__ hist, int64_t max_tiles)
+             int shift, uint32_t *__restrict__ hist)
 {
     __shared__ uint32_t cnt[256];
-    int64_t n = valid_hits(ctr, capacity);
-    cnt[threadIdx.x] = 0;
-    __syncthreads();
-    int64_t base = (int64_t)blockIdx.x * kTile;
-    if (base < n) {
+    const int64_t n = valid_hits(ctr, capacity);
+    const int64_t nt = live_tiles(n);
+    for (int64_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+        cnt[threadIdx.x] = 0;
+        __syncthreads();
+        const int64_t base = tile * kTile;
 #pragma unroll 4
         for (int i = 0; i < kSortItems; ++i) {
             int64_t idx = base + (int64_t)i * kSortThreads + threadIdx.x;
             if (idx < n) atomicAdd(&cnt[(keys[idx] >> shift) & 0xFF], 1u);
         }
+        __syncthreads();
+        hist[(int64_t)threadIdx.x * nt + tile] = cnt[threadIdx.x];
+        __syncthreads();
     }
-    __syncthreads();
-    hist[(int64_t)threadIdx.x * max_tiles + blockIdx.x] = cnt[threadIdx.x];
 }
 
 // ---- exclusive scan of a uint32 array (three kernels) ---------------------
@@ -92,34 +108,47 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *w
     return r;
 }
 
+// The histograms' live length: 256 digits x the live tiles.
+__device__ __forceinline__ int64_t live_hist(const unsigned long long *ctr, int64_t capacity)
+{
+    return 256 * live_tiles(valid_hits(ctr, capacity));
+}
+
 __global__ void __launch_bounds__(kScanThreads)
-k_scan_reduce(const uint32_t *__restrict__ a, int64_t n, uint32_t *__restrict__ sums)
+k_scan_reduce(const uint32_t *__restrict__ a, const unsigned long long *ctr, int64_t capacity,
+              uint32_t *__restrict__ sums)
 {
     __shared__ uint32_t red[kScanThreads / 32];
-    int64_t base = (int64_t)blockIdx.x * kScanChunk;
-    uint32_t s = 0;
+    const int64_t n = live_hist(ctr, capacity);
+    const int64_t nb = (n + kScanChunk - 1) / kScanChunk;
+    for (int64_t blk = blockIdx.x; blk < nb; blk += gridDim.x) {
+        const int64_t base = blk * kScanChunk;
+        uint32_t s = 0;
 #pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-        int64_t idx = base + (int64_t)threadIdx.x * kScanItems + i;
-        if (idx < n) s += a[idx];
-    }
+        for (int i = 0; i < kScanItems; ++i) {
+            int64_t idx = base + (int64_t)threadIdx.x * kScanItems + i;
+            if (idx < n) s += a[idx];
+        }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        uint32_t t = red[threadIdx.x];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            uint32_t t = red[threadIdx.x];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (threadIdx.x == 0) sums[blockIdx.x] = t;
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (threadIdx.x == 0) sums[blk] = t;
+        }
+        __syncthreads();
     }
 }
 
 __global__ void __launch_bounds__(kScanThreads)
-k_scan_top(uint32_t *__restrict__ sums, int64_t n)
+k_scan_top(uint32_t *__restrict__ sums, const unsigned long long *ctr, int64_t capacity)
 {
     __shared__ uint32_t wt[32];
     __shared__ uint32_t tot;
+    const int64_t n = (live_hist(ctr, capacity) + kScanChunk - 1) / kScanChunk;
     uint32_t carry = 0;
     for (int64_t base = 0; base < n; base += kScanThreads) {
         int64_t idx = base + threadIdx.x;
@@ -132,37 +161,45 @@ k_scan_top(uint32_t *__restrict__ sums, int64_t n)
 }
 
 __global__ void __launch_bounds__(kScanThreads)
-k_scan_apply(uint32_t *__restrict__ a, int64_t n, const uint32_t *__restrict__ sums)
+k_scan_apply(uint32_t *__restrict__ a, const unsigned long long *ctr, int64_t capacity,
+             const uint32_t *__restrict__ sums)
 {
     __shared__ uint32_t wt[32];
     __shared__ uint32_t tot;
-    int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanItems;
-    uint32_t v[kScanItems];
-    uint32_t s = 0;
+    const int64_t n = live_hist(ctr, capacity);
+    const int64_t nb = (n + kScanChunk - 1) / kScanChunk;
+    for (int64_t blk = blockIdx.x; blk < nb; blk += gridDim.x) {
+        const int64_t base = blk * kScanChunk + (int64_t)threadIdx.x * kScanItems;
+        uint32_t v[kScanItems];
+        uint32_t s = 0;
 #pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-        v[i] = base + i < n ? a[base + i] : 0;
-        s += v[i];
-    }
-    uint32_t e = block_exclusive_scan(s, wt, &tot) + sums[blockIdx.x];
+        for (int i = 0; i < kScanItems; ++i) {
+            v[i] = base + i < n ? a[base + i] : 0;
+            s += v[i];
+        }
+        uint32_t e = block_exclusive_scan(s, wt, &tot) + sums[blk];
 #pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-        if (base + i < n) a[base + i] = e;
-        e += v[i];
+        for (int i = 0; i < kScanItems; ++i) {
+            if (base + i < n) a[base + i] = e;
+            e += v[i];
+        }
     }
 }
 
-static cudaError_t exclusive_scan(uint32_t *a, int64_t n, uint32_t *sums, cudaStream_t s)
+// In-place exclusive scan of the live histograms; grid: blocks for at most
+// `max_n` entries, capped at `cap_blocks`.
+static cudaError_t exclusive_scan(uint32_t *a, int64_t max_n, const unsigned long long *ctr, int64_t capacity,
+                                  uint32_t *sums, int cap_blocks, cudaStream_t s)
 {
-    int64_t nb = scan_block_sums_needed(n);
-    k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(a, n, sums);
-    k_scan_top<<<1, kScanThreads, 0, s>>>(sums, nb);
-    k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(a, n, sums);
+    const int64_t nb = std::max<int64_t>(1, std::min<int64_t>(scan_block_sums_needed(max_n), cap_blocks));
+    k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(a, ctr, capacity, sums);
+    k_scan_top<<<1, kScanThreads, 0, s>>>(sums, ctr, capacity);
+    k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(a, ctr, capacity, sums);
     return cudaGetLastError();
 }
 
 // Stable scatter of one 8-bit digit.  Warp w of a tile owns items
-// [w*512, (w+1)*512) and walks them in 16 rounds of 32 consecutive keys;
+// [w*256, (w+1)*256) and walks them in 8 rounds of 32 consecutive keys;
 // __match_any_sync groups equal digits inside a round, a per-warp counter
 // per digit carries ranks across rounds, and a prefix over the warps per
 // digit places each warp after the ones before it.
@@ -170,60 +207,63 @@ __global__ void __launch_bounds__(kSortThreads)
 k_radix_scatter(const unsigned long long *__restrict__ kin, const uint32_t *__restrict__ vin,
                 unsigned long long *__restrict__ kout, uint32_t *__restrict__ vout,
                 const unsigned long long *ctr, int64_t capacity, int shift,
-                const uint32_t *__restrict__ hist, int64_t max_tiles)
+                const uint32_t *__restrict__ hist)
 {
     __shared__ uint32_t wcount[kSortThreads / 32][256];
     __shared__ uint32_t gbase[256];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int64_t n = valid_hits(ctr, capacity);
-    int64_t tile0 = (int64_t)blockIdx.x * kTile;
-    if (tile0 >= n) return;     // uniform over the block
-    for (int d = lane; d < 256; d += 32) wcount[w][d] = 0;
-    gbase[threadIdx.x] = hist[(int64_t)threadIdx.x * max_tiles + blockIdx.x];
-    __syncwarp();
-    unsigned long long key[kSortItems];
-    uint32_t val[kSortItems];
-    uint32_t loc[kSortItems];
-    int dig[kSortItems];
-    int64_t wbase = tile0 + (int64_t)w * (kSortItems * 32);
-#pragma unroll
-    for (int r = 0; r < kSortItems; ++r) {
-        int64_t idx = wbase + r * 32 + lane;
-        bool ok = idx < n;
-        key[r] = ok ? kin[idx] : 0ull;
-        val[r] = ok ? vin[idx] : 0u;
-        int d = ok ? (int)((key[r] >> shift) & 0xFF) : 256;
-        dig[r] = d;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        uint32_t before = ok ? wcount[w][d] : 0;
-        loc[r] = before + __popc(peers & lane_lt());
+    const int64_t n = valid_hits(ctr, capacity);
+    const int64_t nt = live_tiles(n);
+    for (int64_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+        const int64_t tile0 = tile * kTile;
+        for (int d = lane; d < 256; d += 32) wcount[w][d] = 0;
+        gbase[threadIdx.x] = hist[(int64_t)threadIdx.x * nt + tile];
         __syncwarp();
-        int leader = __ffs(peers) - 1;
-        if (ok && lane == leader) wcount[w][d] = before + __popc(peers);
-        __syncwarp();
-    }
-    __syncthreads();
-    {   // exclusive prefix over warps, per digit
-        int d = threadIdx.x;
-        uint32_t run = 0;
+        unsigned long long key[kSortItems];
+        uint32_t val[kSortItems];
+        uint32_t loc[kSortItems];
+        int dig[kSortItems];
+        int64_t wbase = tile0 + (int64_t)w * (kSortItems * 32);
 #pragma unroll
-        for (int q = 0; q < kSortThreads / 32; ++q) {
-            uint32_t t = wcount[q][d];
-            wcount[q][d] = run;
-            run += t;
+        for (int r = 0; r < kSortItems; ++r) {
+            int64_t idx = wbase + r * 32 + lane;
+            bool ok = idx < n;
+            key[r] = ok ? kin[idx] : 0ull;
+            val[r] = ok ? vin[idx] : 0u;
+            int d = ok ? (int)((key[r] >> shift) & 0xFF) : 256;
+            dig[r] = d;
+            unsigned peers = __match_any_sync(0xffffffffu, d);
+            uint32_t before = ok ? wcount[w][d] : 0;
+            loc[r] = before + __popc(peers & lane_lt());
+            __syncwarp();
+            int leader = __ffs(peers) - 1;
+            if (ok && lane == leader) wcount[w][d] = before + __popc(peers);
+            __syncwarp();
         }
-    }
-    __syncthreads();
+        __syncthreads();
+        {   // exclusive prefix over warps, per digit
+            int d = threadIdx.x;
+            uint32_t run = 0;
 #pragma unroll
-    for (int r = 0; r < kSortItems; ++r) {
-        int d = dig[r];
-        if (d < 256) {
-            uint32_t pos = gbase[d] + wcount[w][d] + loc[r];
-            if ((int64_t)pos < n) {          // always true for a consistent histogram
-                kout[pos] = key[r];
-                vout[pos] = val[r];
+            for (int q = 0; q < kSortThreads / 32; ++q) {
+                uint32_t t = wcount[q][d];
+                wcount[q][d] = run;
+                run += t;
             }
         }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kSortItems; ++r) {
+            int d = dig[r];
+            if (d < 256) {
+                uint32_t pos = gbase[d] + wcount[w][d] + loc[r];
+                if ((int64_t)pos < n) {          // always true for a consistent histogram
+                    kout[pos] = key[r];
+                    vout[pos] = val[r];
+                }
+            }
+        }
+        __syncthreads();                 // wcount and gbase are reset for the next tile
     }
 }
 
@@ -285,12 +325,18 @@ cudaError_t radix_sort_pairs(unsigned long long **kin, uint32_t **vin, unsigned 
                              const unsigned long long *ctr, int64_t capacity, int key_bits, uint32_t *hist,
                              uint32_t *block_sums, int64_t tiles, cudaStream_t s)
 {
+    // grids bounded by the SM count: the kernels walk the live tiles
+    const int n_sm = device_sms();
+    int oh = 0, os = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oh, k_radix_hist, kSortThreads, 0) != cudaSuccess) oh = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&os, k_radix_scatter, kSortThreads, 0) != cudaSuccess) os = 1;
+    const unsigned gh = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)n_sm * std::max(oh, 1)));
+    const unsigned gs = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)n_sm * std::max(os, 1)));
     for (int shift = 0; shift < key_bits; shift += 8) {
-        k_radix_hist<<<(unsigned)tiles, kSortThreads, 0, s>>>(*kin, ctr, capacity, shift, hist, tiles);
-        cudaError_t e = exclusive_scan(hist, 256 * tiles, block_sums, s);
+        k_radix_hist<<<gh, kSortThreads, 0, s>>>(*kin, ctr, capacity, shift, hist);
+        cudaError_t e = exclusive_scan(hist, 256 * tiles, ctr, capacity, block_sums, 2 * n_sm, s);
         if (e != cudaSuccess) return e;
-        k_radix_scatter<<<(unsigned)tiles, kSortThreads, 0, s>>>(*kin, *vin, *kout, *vout, ctr, capacity, shift,
-                                                                 hist, tiles);
+        k_radix_scatter<<<gs, kSortThreads, 0, s>>>(*kin, *vin, *kout, *vout, ctr, capacity, shift, hist);
         unsigned long long *tk = *kin; *kin = *kout; *kout = tk;
         uint32_t *tv = *vin; *vin = *vout; *vout = tv;
     }
@@ -307,7 +353,7 @@ cudaError_t launch_sort_and_finalize(const DevOut &O, const SortScratch &S, int 
     cudaError_t e = radix_sort_pairs(&kin, &vin, &kout, &vout, O.ctr, O.capacity, key_bits, S.hist, S.block_sums,
                                      tiles, s);
     if (e != cudaSuccess) return e;
-    int gg = 4 * 152;
+    const int gg = 4 * device_sms();
     k_gather<<<gg, 256, 0, s>>>(O.rec, vin, O.ctr, O.capacity, out);
     cudaMemsetAsync(S.gstart, 0, sizeof(int64_t) * n_groups, s);
     cudaMemsetAsync(S.gend, 0, sizeof(int64_t) * n_groups, s);
