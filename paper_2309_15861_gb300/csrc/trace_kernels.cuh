@@ -577,6 +577,11 @@ static_assert(sizeof(ClsRec) == 96, "ClsRec layout");
 constexpr int kClsVmax = 64;                     // virtual steps per warp: 32 Cherenkov + 32 fluorescence
 constexpr int kClsWarpBytes = 32 * (int)sizeof(ClsRec) + kClsVmax * 8;
 constexpr uint32_t kVGated = 1u << 6;            // virtual-step flag: the step's Cherenkov bounds hold
+// Bound on the error of (cos c, sin c) from the MUFU sine and cosine: each
+// within 2^-21.41 = 3.6e-7 of the value at its argument (the vector moves by
+// at most 5.1e-7), and the binary32 argument 2 pi (u - 1/2) within
+// 2 pi |u - 1/2| 2^-23 <= 3.8e-7 of the exact angle: 8.9e-7, rounded up.
+constexpr float kAzErr = 1.0e-6f;
 
 inline int cls_smem_bytes(int block, const DevTel &T)
 {
@@ -585,19 +590,23 @@ inline int cls_smem_bytes(int block, const DevTel &T)
 
 // Per-ray part of the classification of a Cherenkov ray of a gated step:
 // the per-step bounds stand in for the ray's own.
+// cd: the direction's error bound (rad) times 1.05; the crossing moves by up
+// to tp cd (1 + 1/|d_z|).
 template <bool SPH>
 __device__ __forceinline__ int classify_cherenkov_gated(const ClsRec &R, float ell, float dgx, float dgy, float dgz,
-                                                        const DevAtm &A, const DevTel &Tl, const uint8_t *clr)
+                                                        float cd, const DevAtm &A, const DevTel &Tl,
+                                                        const uint8_t *clr)
 {
     // escape is impossible and every ray reaches the observation level (gate)
     const float he = R.h_mid + (ell - 0.5f * R.L) * R.hd;
     if (he < A.h_obs - 0.1f) return 2;
     if (!(he > A.h_obs + 0.1f)) return 0;
     const float xe = R.x0 + ell * R.dx, ye = R.y0 + ell * R.dy, ze = R.z0 + ell * R.dz;
-    const float tp = (ze - A.h_obs) * rcp_approx(-dgz);
+    const float idz = rcp_approx(-dgz);
+    const float tp = (ze - A.h_obs) * idz;
     const float Xv = xe + tp * dgx, Yv = ye + tp * dgy;
     const float zeta = SPH ? (Xv * Xv + Yv * Yv) * A.inv_r_obs : 0.0f;
-    const float rs = R.rsb + R.cB * ((he - A.h_obs) + zeta);
+    const float rs = R.rsb + R.cB * ((he - A.h_obs) + zeta) + cd * tp * (1.0f + idz);
     if (Xv + rs < Tl.xmin || Xv - rs > Tl.xmax || Yv + rs < Tl.ymin || Yv - rs > Tl.ymax) return 6;
     if (clr) {
         const float fx = (Xv - Tl.cx0) * Tl.inv_cgs, fy = (Yv - Tl.cy0) * Tl.inv_cgs;
@@ -609,9 +618,10 @@ __device__ __forceinline__ int classify_cherenkov_gated(const ClsRec &R, float e
 
 // The per-ray test (ray direction d, emission at l along the step), as in
 // skip_ray: for fluorescence photons and the Cherenkov photons of steps
-// without per-step bounds.
+// without per-step bounds.  derr: a bound on the angle between (dx, dy, dz)
+// and the direction the full trace forms (the azimuth's error here).
 template <bool SPH, bool REFR>
-__device__ __forceinline__ int classify_ray(const ClsRec &R, float ell, float dx, float dy, float dz,
+__device__ __forceinline__ int classify_ray(const ClsRec &R, float ell, float dx, float dy, float dz, float derr,
                                             const DevAtm &A, const DevTel &Tl, const uint8_t *clr)
 {
     const float xe = R.x0 + ell * R.dx, ye = R.y0 + ell * R.dy, ze = R.z0 + ell * R.dz;
@@ -631,7 +641,7 @@ __device__ __forceinline__ int classify_ray(const ClsRec &R, float ell, float dx
         if (!(so < 1.0f) || !(co2 > 2.1f * A.delta_max + 2.6e-3f)) return 0;
         cos_obs = sqrt_approx(co2);
     }
-    return clear_miss(xe, ye, ze, dx, dy, dz, he, cos_obs, 1.0f, A, Tl, clr, SPH, REFR) ? 6 : 0;
+    return clear_miss(xe, ye, ze, dx, dy, dz, he, cos_obs, 1.0f, A, Tl, clr, SPH, REFR, 0.0f, derr) ? 6 : 0;
 }
 
 // Does every Cherenkov photon of a gated step land clear of the array?
@@ -701,6 +711,10 @@ k_classify(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid
     // bound pieces that depend on the array and the atmosphere only
     const float dzmax = fmaxf(fabsf(Tl.zmax - A.h_obs), fabsf(Tl.zmin - A.h_obs));
     const float co2_min = 2.1f * A.delta_max + 2.6e-3f;
+    // direction error of a Cherenkov ray from its azimuth: cos c e1 + sin c e2
+    // moves by at most kAzErr, scaled by sin theta_c <= sqrt(2 delta_max (1 + delta_max))
+    const float de_c = kAzErr * sqrtf(2.0f * A.delta_max * (1.0f + A.delta_max)) * 1.01f;
+    const float cd_c = 1.05f * de_c;
     uint32_t c_rays = 0, c_esc = 0, c_under = 0, c_skip = 0, c_guard = 0, c_whole = 0;
     unsigned status_bits = 0;
     WarpQueue dq;                    // the rays left to k_trace_deferred
@@ -858,8 +872,15 @@ k_classify(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid
                                                          (uint32_t)((uint64_t)seg_global >> 32), kk, proc),
                                               Pp.seed, Pp.stream);
                 const float u1 = u01<float>(x.y), u2 = u01<float>(x.z);
+                // the azimuth 2 pi u2 by the MUFU sine and cosine at
+                // 2 pi (u2 - 1/2), inside [-pi, pi] where their absolute error
+                // is at most 2^-21.41 (sin 2 pi u = -sin 2 pi (u - 1/2)); the
+                // decisions below carry that error (kAzErr) as a direction
+                // error, and the full trace forms the azimuth with sincospif
                 float sn, cs;
-                Num<float>::sincos2pi(u2, &sn, &cs);
+                __sincosf(6.28318531f * (u2 - 0.5f), &sn, &cs);
+                sn = -sn;
+                cs = -cs;
                 // the step's record in 128-bit shared loads, those of a
                 // process issued together
                 const float4 *rq = reinterpret_cast<const float4 *>(rec + l);
@@ -879,15 +900,15 @@ k_classify(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid
                     const float dgx = R.ax + (cs * R.b1x + sn * R.b2x);
                     const float dgy = R.ay + (cs * R.b1y + sn * R.b2y);
                     const float dgz = R.az + (cs * R.b1z + sn * R.b2z);
-                    cls = (v.y & kVGated) ? classify_cherenkov_gated<SPH>(R, ell, dgx, dgy, dgz, A, Tl, clr)
-                                          : classify_ray<SPH, REFR>(R, ell, dgx, dgy, dgz, A, Tl, clr);
+                    cls = (v.y & kVGated) ? classify_cherenkov_gated<SPH>(R, ell, dgx, dgy, dgz, cd_c, A, Tl, clr)
+                                          : classify_ray<SPH, REFR>(R, ell, dgx, dgy, dgz, de_c, A, Tl, clr);
                 } else {
                     R.nc = reinterpret_cast<const uint4 *>(rq)[5].x;
                     kq = R.nc + kk;
                     const float u3 = u01<float>(x.w);
                     const float cz = 2.0f * u3 - 1.0f;
                     const float sz = sqrt_approx((1.0f - cz) * (1.0f + cz));
-                    cls = classify_ray<SPH, REFR>(R, ell, sz * cs, sz * sn, cz, A, Tl, clr);
+                    cls = classify_ray<SPH, REFR>(R, ell, sz * cs, sz * sn, cz, kAzErr, A, Tl, clr);
                 }
                 c_esc += cls == 1;
                 c_under += cls == 2;
