@@ -254,6 +254,7 @@ template <class T, class P> struct Seg {
     T lx, ly, lz;        // its normalisation correction (pair low part)
     T e1x, e1y, e1z, e2x, e2y, e2z;   // M_Rod x, M_Rod y
     T sin_tc, kappa;     // sin(theta_c), 1 - cos(theta_c)
+    T gerr;              // bound on the error of the beta n - 1 they came from (0: binary64)
     T L, inv_bc;         // step length, 1/(beta c) in ns/m
     T w_c, w_f;
     T h_mid;             // midpoint altitude
@@ -791,15 +792,13 @@ __device__ __forceinline__ void load_segment_f(const clight_segment &s, int64_t 
     // error bound of g1 (delta known to ~1.5e-6 relative; generous factor)
     float eg = 4.0e-6f * dl + 2.4e-7f * (dl + eps);
     // near the threshold (kappa = (delta + eps) / g1 above 16, or the sign of
-    // g1 not certain) the refractivity in FP32 pairs: g1 to ~1e-12 relative
-    if (!(DISP && A.disp) && z2 > 0.0f && s.L > 0.0f && g1 > -eg && 16.0f * g1 < dl + eps) {
-        float lx = g.lx, ly = g.ly, lz = g.lz;
-        df x0 = g.x0, y0 = g.y0, z0 = g.z0;
-        if (!FULL) {
-            dir_residual(g.dx, g.dy, g.dz, lx, ly, lz);
-            x0 = df_from_double_bits(s.x); y0 = df_from_double_bits(s.y); z0 = df_from_double_bits(s.z);
-        }
-        const df dlp = delta_pair<SPH>(A, x0, y0, z0, df{g.dx, lx}, df{g.dy, ly}, df{g.dz, lz}, s.L);
+    // g1 not certain) the refractivity in FP32 pairs: g1 to ~1e-12 relative.
+    // The lean set-up (FULL = false: counts and cone bounds only) keeps the
+    // binary32 g1 and its bound eg: its counts are exact all the same (the
+    // guard takes what eg leaves uncertain), and the classification carries
+    // the cone's resulting direction error (gerr)
+    if (FULL && !(DISP && A.disp) && z2 > 0.0f && s.L > 0.0f && g1 > -eg && 16.0f * g1 < dl + eps) {
+        const df dlp = delta_pair<SPH>(A, g.x0, g.y0, g.z0, df{g.dx, g.lx}, df{g.dy, g.ly}, df{g.dz, g.lz}, s.L);
         const df g1p = (dlp - eps) - dlp * eps;
         dl = p_f(dlp);
         g1 = p_f(g1p);
@@ -807,6 +806,7 @@ __device__ __forceinline__ void load_segment_f(const clight_segment &s, int64_t 
     }
     bool guard = false;
     float Nc = 0.0f;
+    g.gerr = eg;
     if (DISP && A.disp) {
         // dispersion: the band integral; per-photon angles from (db, eps)
         float db = dl * (1.0f - eps), ulo, uhi;
@@ -880,6 +880,7 @@ __device__ __forceinline__ void load_segment_f(const clight_segment &s, int64_t 
             Nc = (float)Ncd;
             g.sin_tc = (DISP && A.disp) ? (float)sin2d : (float)sqrt(sin2d);
             g.kappa = (float)kapd;
+            g.gerr = 0.0f;
             if (g.n_c > 0) g.w_c = (float)(Ncd / nb);
         }
         if (fguard) {
@@ -906,6 +907,7 @@ __device__ void load_segment_d(const clight_segment &s, int64_t seg_global, cons
                                Seg<double, double> &g)
 {
     g.bad = 0;
+    g.gerr = 0.0;
     g.guarded = 0;
     g.cut = 0;
     g.n_c = g.n_f = 0;
@@ -960,7 +962,7 @@ __device__ __forceinline__ void widen_seg(const Seg<float, df> &q, Seg<float, do
     p_from_pair(qd.A0, q.A0); p_from_pair(qd.C0, q.C0);
     qd.dx = q.dx; qd.dy = q.dy; qd.dz = q.dz; qd.lx = q.lx; qd.ly = q.ly; qd.lz = q.lz;
     qd.e1x = q.e1x; qd.e1y = q.e1y; qd.e1z = q.e1z; qd.e2x = q.e2x; qd.e2y = q.e2y; qd.e2z = q.e2z;
-    qd.sin_tc = q.sin_tc; qd.kappa = q.kappa; qd.L = q.L; qd.inv_bc = q.inv_bc;
+    qd.sin_tc = q.sin_tc; qd.kappa = q.kappa; qd.gerr = q.gerr; qd.L = q.L; qd.inv_bc = q.inv_bc;
     qd.w_c = q.w_c; qd.w_f = q.w_f; qd.n_c = q.n_c; qd.n_f = q.n_f; qd.shower = q.shower;
     qd.bux = q.bux; qd.buy = q.buy; qd.buz = q.buz; qd.bomc = q.bomc;
     qd.h_mid = q.h_mid; qd.bad = q.bad; qd.guarded = q.guarded; qd.cut = q.cut;

@@ -571,7 +571,8 @@ struct alignas(16) ClsRec {
     float ax, ay, az, hd;       // cos(theta_c) d, dh/dl along the step
     float b1x, b1y, b1z, rsb;   // sin(theta_c) M_Rod x, search radius without the refraction term
     float b2x, b2y, b2z, cB;    // sin(theta_c) M_Rod y, refraction term per metre of height
-    uint32_t nc, pad0, pad1, pad2;
+    uint32_t nc;                // Cherenkov bunches
+    float derr, pad1, pad2;     // bound on a Cherenkov ray's direction error (rad)
 };
 static_assert(sizeof(ClsRec) == 96, "ClsRec layout");
 constexpr int kClsVmax = 64;                     // virtual steps per warp: 32 Cherenkov + 32 fluorescence
@@ -590,23 +591,20 @@ inline int cls_smem_bytes(int block, const DevTel &T)
 
 // Per-ray part of the classification of a Cherenkov ray of a gated step:
 // the per-step bounds stand in for the ray's own.
-// cd: the direction's error bound (rad) times 1.05; the crossing moves by up
-// to tp cd (1 + 1/|d_z|).
+// The step's cB carries the direction error of its rays as well.
 template <bool SPH>
 __device__ __forceinline__ int classify_cherenkov_gated(const ClsRec &R, float ell, float dgx, float dgy, float dgz,
-                                                        float cd, const DevAtm &A, const DevTel &Tl,
-                                                        const uint8_t *clr)
+                                                        const DevAtm &A, const DevTel &Tl, const uint8_t *clr)
 {
     // escape is impossible and every ray reaches the observation level (gate)
     const float he = R.h_mid + (ell - 0.5f * R.L) * R.hd;
     if (he < A.h_obs - 0.1f) return 2;
     if (!(he > A.h_obs + 0.1f)) return 0;
     const float xe = R.x0 + ell * R.dx, ye = R.y0 + ell * R.dy, ze = R.z0 + ell * R.dz;
-    const float idz = rcp_approx(-dgz);
-    const float tp = (ze - A.h_obs) * idz;
+    const float tp = (ze - A.h_obs) * rcp_approx(-dgz);
     const float Xv = xe + tp * dgx, Yv = ye + tp * dgy;
     const float zeta = SPH ? (Xv * Xv + Yv * Yv) * A.inv_r_obs : 0.0f;
-    const float rs = R.rsb + R.cB * ((he - A.h_obs) + zeta) + cd * tp * (1.0f + idz);
+    const float rs = R.rsb + R.cB * ((he - A.h_obs) + zeta);
     if (Xv + rs < Tl.xmin || Xv - rs > Tl.xmax || Yv + rs < Tl.ymin || Yv - rs > Tl.ymax) return 6;
     if (clr) {
         const float fx = (Xv - Tl.cx0) * Tl.inv_cgs, fy = (Yv - Tl.cy0) * Tl.inv_cgs;
@@ -714,7 +712,6 @@ k_classify(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid
     // direction error of a Cherenkov ray from its azimuth: cos c e1 + sin c e2
     // moves by at most kAzErr, scaled by sin theta_c <= sqrt(2 delta_max (1 + delta_max))
     const float de_c = kAzErr * sqrtf(2.0f * A.delta_max * (1.0f + A.delta_max)) * 1.01f;
-    const float cd_c = 1.05f * de_c;
     uint32_t c_rays = 0, c_esc = 0, c_under = 0, c_skip = 0, c_guard = 0, c_whole = 0;
     unsigned status_bits = 0;
     WarpQueue dq;                    // the rays left to k_trace_deferred
@@ -792,16 +789,21 @@ k_classify(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid
                 r.hd = g.dz;
             }
             // Cherenkov bounds over the cone (half-angle theta_c: cos ct, sin st)
-            r.rsb = 0.0f; r.cB = 0.0f;
+            r.rsb = 0.0f; r.cB = 0.0f; r.derr = 0.0f;
             if (nc > 0) {
+                // a ray's direction error against the full trace's: the
+                // azimuth's, and the cone's from a binary32 beta n - 1 (error
+                // gerr moves sin^2 theta_c by ~2 gerr and cos theta_c by gerr)
+                const float dstep = de_c + 1.1f * g.gerr * (rcp_approx(st) + 1.0f);
+                r.derr = dstep;
                 // -d_gamma,z >= cos(zeta_d + theta_c)
-                const float dzlo = sdz * ct - szd * st - 4.0e-6f;
+                const float dzlo = sdz * ct - szd * st - 4.0e-6f - dstep;
                 float cobs_lo = dzlo;
                 bool ok = dzlo > 0.05f;
                 if (SPH) {
                     // landing zenith sine: (r_e / r_obs) sin(psi_e), psi_e <= psi_d + theta_c + L / r0
                     const float csum = cps * ct - sps * st;
-                    const float se = sps * ct + cps * st + (r.L + 1.0f) * ir0 + 4.0e-6f;
+                    const float se = sps * ct + cps * st + (r.L + 1.0f) * ir0 + 4.0e-6f + dstep;
                     const float so = (r0 + r.L) * se * A.inv_r_obs * 1.000001f;
                     const float co2 = 1.0f - so * so;
                     ok = ok && csum > 0.0f && so < 1.0f && co2 > co2_min;
@@ -815,7 +817,11 @@ k_classify(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid
                     const float czb = dzlo - sd * im - 1.0e-5f;
                     ok = czb > 0.05f;
                     if (ok) {
-                        r.cB = sd * (im * im * im) * 1.0001f;
+                        // the refraction term per metre of height, plus the
+                        // direction error's: the crossing moves by at most
+                        // dstep tp (1 + 1/|d_z|), tp <= (h - h_obs) / dzlo
+                        const float iz = rcp_approx(dzlo) * 1.000001f;
+                        r.cB = sd * (im * im * im) * 1.0001f + 1.05f * dstep * iz * (1.0f + iz);
                         r.rsb = ((Tl.Rmax + dzmax * sqrt_approx(1.0f - czb * czb)) * rcp_approx(czb) + 2.0e-3f +
                                  0.05f) * 1.0001f + 1.0e-3f;
                     }
@@ -900,8 +906,10 @@ k_classify(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid
                     const float dgx = R.ax + (cs * R.b1x + sn * R.b2x);
                     const float dgy = R.ay + (cs * R.b1y + sn * R.b2y);
                     const float dgz = R.az + (cs * R.b1z + sn * R.b2z);
-                    cls = (v.y & kVGated) ? classify_cherenkov_gated<SPH>(R, ell, dgx, dgy, dgz, cd_c, A, Tl, clr)
-                                          : classify_ray<SPH, REFR>(R, ell, dgx, dgy, dgz, de_c, A, Tl, clr);
+                    cls = (v.y & kVGated)
+                              ? classify_cherenkov_gated<SPH>(R, ell, dgx, dgy, dgz, A, Tl, clr)
+                              : classify_ray<SPH, REFR>(R, ell, dgx, dgy, dgz, reinterpret_cast<const float4 *>(rq)[5].y,
+                                                        A, Tl, clr);
                 } else {
                     R.nc = reinterpret_cast<const uint4 *>(rq)[5].x;
                     kq = R.nc + kk;
