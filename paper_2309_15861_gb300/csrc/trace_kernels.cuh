@@ -119,61 +119,45 @@ __device__ __forceinline__ void flush_stats(const uint32_t (&vals)[ST_N], unsign
     if (lane == 0 && sb) atomicOr(O.ctr + CTR_STATS + ST_STATUS, (unsigned long long)sb);
 }
 
-// Position of the set bit of rank r (counted from 0 at the low end) in m;
-// r < popc(m).
-__device__ __forceinline__ int nth_set_bit(unsigned m, unsigned r)
-{
-    int p = 0;
-#pragma unroll
-    for (int w = 16; w > 0; w >>= 1) {
-        const unsigned c = __popc((m >> p) & ((1u << w) - 1u));
-        if (r >= c) { r -= c; p += w; }
-    }
-    return p;
-}
-
-// A warp's entries for the deferred-ray queue, held in registers: lane L
-// keeps the warp's L-th buffered entry.  They leave 32 at a time, one atomic
-// on the queue counter and one coalesced 256-byte store per flush.  (One
-// counter that every warp bumps for every round with a deferred ray limits
-// the first pass to the rate at which one L2 slice serves atomics on one
-// address.)  Every member is called by all 32 lanes together.
+// A warp's entries for the deferred-ray queue, held in registers: each lane
+// keeps at most one (the last it queued), `occ` marks the lanes that hold
+// one.  When a lane would queue a second, the warp flushes: one atomic on the
+// queue counter reserves a slot for every held entry and the holders write
+// them to consecutive slots (one coalesced store).  One counter that every
+// warp bumped for every round with a deferred ray limited the first pass to
+// the rate at which one L2 slice serves atomics on one address; a flush
+// carries ~7 entries on average.  Every member is called by all 32 lanes
+// together.
 struct WarpQueue {
     unsigned long long e = 0;
-    uint32_t n = 0;                  // warp-uniform: entries held, in lanes 0 .. n-1
+    unsigned occ = 0;                // warp-uniform
 
-    __device__ __forceinline__ void flush(uint32_t cnt, const DevOut &O, int lane, unsigned &status_bits)
+    __device__ __forceinline__ void flush(const DevOut &O, int lane, unsigned &status_bits)
     {
+        const unsigned m = occ;
         unsigned long long b = 0;
-        if (lane == 0) b = atomicAdd(O.ctr + CTR_DEFER, (unsigned long long)cnt);
+        if (lane == 0) b = atomicAdd(O.ctr + CTR_DEFER, (unsigned long long)__popc(m));
         b = __shfl_sync(FULL_MASK, b, 0);
-        if ((uint32_t)lane < cnt) {
-            if ((int64_t)(b + lane) < O.defer_cap) O.defer[b + lane] = e;
+        if (m & (1u << lane)) {
+            const unsigned long long qi = b + __popc(m & lanemask_lt());
+            if ((int64_t)qi < O.defer_cap) O.defer[qi] = e;
             else status_bits |= 1u << kBitDeferFull;
         }
+        occ = 0;
     }
-    // Appends the entries of the lanes with push set, in lane order.
+    // Queues the entries of the lanes with p set.
     __device__ __forceinline__ void push(bool p, unsigned long long entry, const DevOut &O, int lane,
                                          unsigned &status_bits)
     {
         const unsigned m = __ballot_sync(FULL_MASK, p);
         if (!m) return;
-        const uint32_t k = __popc(m);
-        const uint32_t r = (uint32_t)(lane - (int)n) & 31u;     // rank of the new entry this lane takes
-        const unsigned long long v = __shfl_sync(FULL_MASK, entry, nth_set_bit(m, r < k ? r : 0u));
-        if ((uint32_t)lane >= n && r < k) e = v;
-        if (n + k >= 32) {
-            flush(32, O, lane, status_bits);
-            if ((uint32_t)lane < n && r < k) e = v;             // ranks 32 - n .. k - 1 wrap to lanes 0 ..
-            n = n + k - 32;
-        } else {
-            n += k;
-        }
+        if (m & occ) flush(O, lane, status_bits);
+        if (p) e = entry;
+        occ |= m;
     }
     __device__ __forceinline__ void finish(const DevOut &O, int lane, unsigned &status_bits)
     {
-        if (n) flush(n, O, lane, status_bits);
-        n = 0;
+        if (occ) flush(O, lane, status_bits);
     }
 };
 
