@@ -69,6 +69,7 @@ struct clight_ctx {
     float4 *d_tel = nullptr;
     int *d_cell_start = nullptr, *d_cell_tel = nullptr;
     uint8_t *d_clr = nullptr;
+    uint8_t *d_fclr = nullptr;
     // scratch (device)
     unsigned long long *d_ctr = nullptr;
     Buf<clight_hit> rec;
@@ -182,7 +183,7 @@ void clight_destroy(clight_ctx *c)
     if (!c) return;
     DeviceGuard dg(c->device);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
-    void *dev[] = {c->d_tel, c->d_cell_start, c->d_cell_tel, c->d_clr, c->d_ctr};
+    void *dev[] = {c->d_tel, c->d_cell_start, c->d_cell_tel, c->d_clr, c->d_fclr, c->d_ctr};
     for (void *p : dev)
         if (p) cudaFree(p);
     c->rec.release(); c->keys.release(); c->keys_alt.release(); c->vals.release(); c->vals_alt.release();
@@ -357,6 +358,53 @@ clight_status clight_set_atmosphere(clight_ctx *c, const clight_atmosphere *a)
     return CLIGHT_OK;
 }
 
+// A clearance map of at most max_cells square cells over the array's box
+// widened by 20 m.  A cell's value is the distance from the closed cell to
+// the nearest centre, less 1 cm (rounding of the cell index), rounded down to
+// kClrQuantum (255: at least 255 quanta).  The byte count is padded to 16.
+struct ClrMap {
+    std::vector<uint8_t> map;
+    int nx, ny;
+    double x0, y0, cs;
+};
+static ClrMap build_clearance(const clight_telescope *t, int n, float xmin, float xmax, float ymin, float ymax,
+                              int max_cells)
+{
+    const double margin = 20.0, q = kClrQuantum, reach = 255.0 * q;
+    ClrMap m;
+    m.x0 = xmin - margin;
+    m.y0 = ymin - margin;
+    const double wx = (double)(xmax - xmin) + 2 * margin, wy = (double)(ymax - ymin) + 2 * margin;
+    m.cs = std::max(0.5, std::sqrt(wx * wy / max_cells));
+    m.nx = (int)std::ceil(wx / m.cs);
+    m.ny = (int)std::ceil(wy / m.cs);
+    while ((int64_t)m.nx * m.ny > max_cells) {
+        m.cs *= 1.05;
+        m.nx = (int)std::ceil(wx / m.cs);
+        m.ny = (int)std::ceil(wy / m.cs);
+    }
+    m.map.assign((size_t)m.nx * m.ny, 255);
+    for (int i = 0; i < n; ++i) {
+        const int ix0 = std::max(0, (int)std::floor((t[i].x - reach - m.x0) / m.cs) - 1);
+        const int ix1 = std::min(m.nx - 1, (int)std::floor((t[i].x + reach - m.x0) / m.cs) + 1);
+        const int iy0 = std::max(0, (int)std::floor((t[i].y - reach - m.y0) / m.cs) - 1);
+        const int iy1 = std::min(m.ny - 1, (int)std::floor((t[i].y + reach - m.y0) / m.cs) + 1);
+        for (int iy = iy0; iy <= iy1; ++iy)
+            for (int ix = ix0; ix <= ix1; ++ix) {
+                const double lx = m.x0 + ix * m.cs, ly = m.y0 + iy * m.cs;
+                const double dx = std::max(0.0, std::max(lx - t[i].x, t[i].x - (lx + m.cs)));
+                const double dy = std::max(0.0, std::max(ly - t[i].y, t[i].y - (ly + m.cs)));
+                const double d = std::sqrt(dx * dx + dy * dy) - 0.01;
+                const double v = d <= 0 ? 0.0 : std::floor(d / q);
+                const uint8_t u = (uint8_t)std::min(255.0, v);
+                uint8_t &cell = m.map[(size_t)iy * m.nx + ix];
+                if (u < cell) cell = u;
+            }
+    }
+    m.map.resize((m.map.size() + 15) / 16 * 16, 0);
+    return m;
+}
+
 clight_status clight_set_telescopes(clight_ctx *c, const clight_telescope *t, int32_t n)
 {
     if (!c || !t || n < 1) return CLIGHT_ERR_ARG;
@@ -387,37 +435,18 @@ clight_status clight_set_telescopes(clight_ctx *c, const clight_telescope *t, in
     std::vector<float4> tv(n);
     for (int i = 0; i < n; ++i) tv[i] = make_float4(t[i].x, t[i].y, t[i].z, t[i].R);
 
-    // clearance map over the array's box widened by 20 m: a ray whose search
-    // radius is below its cell's value cannot reach any sphere, so the hit
-    // test of most rays ends with one shared-memory byte.  A cell's value is
-    // the distance from the closed cell to the nearest centre, less 1 cm
-    // (rounding of the cell index), rounded down to the quantum.
-    const double margin = 20.0, q = kClrQuantum, reach = 255.0 * q;
-    double bx0 = xmin - margin, by0 = ymin - margin;
-    double wx = (double)(xmax - xmin) + 2 * margin, wy = (double)(ymax - ymin) + 2 * margin;
-    double cgs = std::max(0.5, std::sqrt(wx * wy / kClrMaxCells));
-    int cnx = (int)std::ceil(wx / cgs), cny = (int)std::ceil(wy / cgs);
-    while ((int64_t)cnx * cny > kClrMaxCells) { cgs *= 1.05; cnx = (int)std::ceil(wx / cgs); cny = (int)std::ceil(wy / cgs); }
-    std::vector<uint8_t> clr((size_t)cnx * cny, 255);
-    for (int i = 0; i < n; ++i) {
-        int ix0 = std::max(0, (int)std::floor((t[i].x - reach - bx0) / cgs) - 1);
-        int ix1 = std::min(cnx - 1, (int)std::floor((t[i].x + reach - bx0) / cgs) + 1);
-        int iy0 = std::max(0, (int)std::floor((t[i].y - reach - by0) / cgs) - 1);
-        int iy1 = std::min(cny - 1, (int)std::floor((t[i].y + reach - by0) / cgs) + 1);
-        for (int iy = iy0; iy <= iy1; ++iy)
-            for (int ix = ix0; ix <= ix1; ++ix) {
-                double lx = bx0 + ix * cgs, ly = by0 + iy * cgs;
-                double dx = std::max(0.0, std::max(lx - t[i].x, t[i].x - (lx + cgs)));
-                double dy = std::max(0.0, std::max(ly - t[i].y, t[i].y - (ly + cgs)));
-                double d = std::sqrt(dx * dx + dy * dy) - 0.01;
-                double v = d <= 0 ? 0.0 : std::floor(d / q);
-                uint8_t u = (uint8_t)std::min(255.0, v);
-                uint8_t &cell = clr[(size_t)iy * cnx + ix];
-                if (u < cell) cell = u;
-            }
-    }
-    int clr_bytes = (int)((clr.size() + 15) / 16 * 16);
-    clr.resize(clr_bytes, 0);
+    // clearance maps over the array's box widened by 20 m: a ray whose search
+    // radius is below its cell's value cannot reach any sphere.  The coarse
+    // map (<= kClrMaxCells) is staged in shared memory by the kernels that
+    // trace rays (the hit test of most rays ends with one shared-memory
+    // byte); the fine one (<= kClrFineMaxCells) is read through L1 by the
+    // classification, where a smaller cell defers fewer rays.
+    ClrMap cm = build_clearance(t, n, xmin, xmax, ymin, ymax, kClrMaxCells);
+    ClrMap fm = build_clearance(t, n, xmin, xmax, ymin, ymax, kClrFineMaxCells);
+    std::vector<uint8_t> &clr = cm.map;
+    const int cnx = cm.nx, cny = cm.ny;
+    const double bx0 = cm.x0, by0 = cm.y0, cgs = cm.cs;
+    int clr_bytes = (int)clr.size();
 
     DeviceGuard dg(c->device);
     if (!dg.ok) return CLIGHT_ERR_CUDA;
@@ -425,15 +454,18 @@ clight_status clight_set_telescopes(clight_ctx *c, const clight_telescope *t, in
     if (c->d_cell_start) cudaFree(c->d_cell_start);
     if (c->d_cell_tel) cudaFree(c->d_cell_tel);
     if (c->d_clr) cudaFree(c->d_clr);
-    c->d_tel = nullptr; c->d_cell_start = nullptr; c->d_cell_tel = nullptr; c->d_clr = nullptr;
+    if (c->d_fclr) cudaFree(c->d_fclr);
+    c->d_tel = nullptr; c->d_cell_start = nullptr; c->d_cell_tel = nullptr; c->d_clr = nullptr; c->d_fclr = nullptr;
     CK(cudaMalloc((void **)&c->d_tel, sizeof(float4) * n));
     CK(cudaMalloc((void **)&c->d_cell_start, sizeof(int) * count.size()));
     CK(cudaMalloc((void **)&c->d_cell_tel, sizeof(int) * n));
     CK(cudaMalloc((void **)&c->d_clr, (size_t)clr_bytes));
+    CK(cudaMalloc((void **)&c->d_fclr, fm.map.size()));
     CK(cudaMemcpy(c->d_tel, tv.data(), sizeof(float4) * n, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->d_cell_start, count.data(), sizeof(int) * count.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->d_cell_tel, tel_idx.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->d_clr, clr.data(), (size_t)clr_bytes, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_fclr, fm.map.data(), fm.map.size(), cudaMemcpyHostToDevice));
     DevTel &T = c->tel;
     {
         double sx = 0, sy = 0, sz = 0;
@@ -452,6 +484,8 @@ clight_status clight_set_telescopes(clight_ctx *c, const clight_telescope *t, in
     }
     T.clr = c->d_clr; T.cnx = cnx; T.cny = cny; T.clr_bytes = clr_bytes;
     T.cx0 = (float)bx0; T.cy0 = (float)by0; T.inv_cgs = (float)(1.0 / cgs);
+    T.fclr = c->d_fclr; T.fcnx = fm.nx; T.fcny = fm.ny;
+    T.fcx0 = (float)fm.x0; T.fcy0 = (float)fm.y0; T.finv_cgs = (float)(1.0 / fm.cs);
     T.tel = c->d_tel; T.cell_start = c->d_cell_start; T.cell_tel = c->d_cell_tel;
     T.n_tel = n; T.nx = nx; T.ny = ny;
     T.gx0 = xmin; T.gy0 = ymin; T.gs = (float)gs; T.inv_gs = (float)(1.0 / gs);

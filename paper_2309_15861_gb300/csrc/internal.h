@@ -69,9 +69,14 @@ struct DevTel {
     float cx0, cy0, inv_cgs, pad4;
     float mx, my, mz, mr;           // mean centre, largest distance of a centre from it (rounded up)
     float cabs;                     // largest |x| + |y| + |z| of a centre
+    // the same map at a finer cell (read through L1 by the classification)
+    const uint8_t *fclr;
+    int fcnx, fcny;
+    float fcx0, fcy0, finv_cgs;
 };
 constexpr float kClrQuantum = 0.25f;     // metres per unit of the clearance map
 constexpr int kClrMaxCells = 10240;      // 10 KB of shared memory per CTA
+constexpr int kClrFineMaxCells = 65536;  // 64 KB in global memory
 
 struct DevPar {
     float band, inv_bunch;       // 2 pi alpha (1/l1 - 1/l2) [1/m], 1/B

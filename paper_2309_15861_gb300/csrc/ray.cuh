@@ -1111,6 +1111,9 @@ constexpr int FEAT_EXT = 1, FEAT_STRAIGHT = 2, FEAT_RUNTIME = 4, FEAT_DISP = 8,
 // derr > 0: (dx, dy, dz) is known only to within that angle (cos_obs is
 // then already a lower bound); the vacuum crossing moves by up to
 // tp derr (1 + tan) and |d_z| by up to derr.
+template <bool FINE>
+__device__ __forceinline__ bool clr_clear(const DevTel &Tl, const uint8_t *clr, float x, float y, float rs);
+template <bool FINE = false>
 __device__ __forceinline__ bool clear_miss(float xe, float ye, float ze, float dx, float dy, float dz, float he,
                                            float cos_obs, float gl, const DevAtm &A, const DevTel &Tl,
                                            const uint8_t *clr, bool sph, bool refr, float widen = 0.0f,
@@ -1130,12 +1133,23 @@ __device__ __forceinline__ bool clear_miss(float xe, float ye, float ze, float d
     const float dzmax = fmaxf(fabsf(Tl.zmax - A.h_obs), fabsf(Tl.zmin - A.h_obs));
     const float rs = (Tl.Rmax + widen + dzmax * sqrt_approx(1.0f - czb * czb)) * rcp_approx(czb) + 2.0e-3f + B;
     if (Xv + rs < Tl.xmin || Xv - rs > Tl.xmax || Yv + rs < Tl.ymin || Yv - rs > Tl.ymax) return true;
-    if (clr) {
-        float fx = (Xv - Tl.cx0) * Tl.inv_cgs, fy = (Yv - Tl.cy0) * Tl.inv_cgs;
-        if (fx >= 0.0f && fy >= 0.0f && fx < (float)Tl.cnx && fy < (float)Tl.cny)
-            return rs < (float)clr[floor_small(fy) * Tl.cnx + floor_small(fx)] * kClrQuantum;
-    }
-    return false;
+    return clr_clear<FINE>(Tl, clr, Xv, Yv, rs);
+}
+
+// Does the clearance map rule out every centre within rs of (x, y)?  FINE:
+// the fine map (global memory, through L1); else the coarse one at clr
+// (shared memory; nullptr: no map).
+template <bool FINE>
+__device__ __forceinline__ bool clr_clear(const DevTel &Tl, const uint8_t *clr, float x, float y, float rs)
+{
+    const uint8_t *m = FINE ? Tl.fclr : clr;
+    if (!m) return false;
+    const float inv = FINE ? Tl.finv_cgs : Tl.inv_cgs;
+    const float fx = (x - (FINE ? Tl.fcx0 : Tl.cx0)) * inv, fy = (y - (FINE ? Tl.fcy0 : Tl.cy0)) * inv;
+    const int nx = FINE ? Tl.fcnx : Tl.cnx, ny = FINE ? Tl.fcny : Tl.cny;
+    if (!(fx >= 0.0f && fy >= 0.0f && fx < (float)nx && fy < (float)ny)) return false;
+    const int ci = floor_small(fy) * nx + floor_small(fx);
+    return rs < (float)(FINE ? __ldg(m + ci) : m[ci]) * kClrQuantum;
 }
 
 // CULL (binary32 only): skip the quadrature for rays clear_miss rejects;

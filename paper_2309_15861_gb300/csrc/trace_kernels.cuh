@@ -568,9 +568,9 @@ constexpr uint32_t kVGated = 1u << 6;            // virtual-step flag: the step'
 // 2 pi |u - 1/2| 2^-23 <= 3.8e-7 of the exact angle: 8.9e-7, rounded up.
 constexpr float kAzErr = 1.0e-6f;
 
-inline int cls_smem_bytes(int block, const DevTel &T)
+inline int cls_smem_bytes(int block, const DevTel &)
 {
-    return (block / 32) * (kClsWarpBytes + kStageBytes) + (T.clr ? T.clr_bytes : 0);
+    return (block / 32) * (kClsWarpBytes + kStageBytes);
 }
 
 // Per-ray part of the classification of a Cherenkov ray of a gated step:
@@ -590,12 +590,7 @@ __device__ __forceinline__ int classify_cherenkov_gated(const ClsRec &R, float e
     const float zeta = SPH ? (Xv * Xv + Yv * Yv) * A.inv_r_obs : 0.0f;
     const float rs = R.rsb + R.cB * ((he - A.h_obs) + zeta);
     if (Xv + rs < Tl.xmin || Xv - rs > Tl.xmax || Yv + rs < Tl.ymin || Yv - rs > Tl.ymax) return 6;
-    if (clr) {
-        const float fx = (Xv - Tl.cx0) * Tl.inv_cgs, fy = (Yv - Tl.cy0) * Tl.inv_cgs;
-        if (fx >= 0.0f && fy >= 0.0f && fx < (float)Tl.cnx && fy < (float)Tl.cny)
-            return rs < (float)clr[floor_small(fy) * Tl.cnx + floor_small(fx)] * kClrQuantum ? 6 : 0;
-    }
-    return 0;
+    return clr_clear<true>(Tl, clr, Xv, Yv, rs) ? 6 : 0;
 }
 
 // The per-ray test (ray direction d, emission at l along the step), as in
@@ -623,7 +618,7 @@ __device__ __forceinline__ int classify_ray(const ClsRec &R, float ell, float dx
         if (!(so < 1.0f) || !(co2 > 2.1f * A.delta_max + 2.6e-3f)) return 0;
         cos_obs = sqrt_approx(co2);
     }
-    return clear_miss(xe, ye, ze, dx, dy, dz, he, cos_obs, 1.0f, A, Tl, clr, SPH, REFR, 0.0f, derr) ? 6 : 0;
+    return clear_miss<true>(xe, ye, ze, dx, dy, dz, he, cos_obs, 1.0f, A, Tl, clr, SPH, REFR, 0.0f, derr) ? 6 : 0;
 }
 
 // Does every Cherenkov photon of a gated step land clear of the array?
@@ -682,14 +677,7 @@ k_classify(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid
     ClsRec *rec = reinterpret_cast<ClsRec *>(smem_c + warp * kClsWarpBytes);
     uint2 *vl = reinterpret_cast<uint2 *>(smem_c + warp * kClsWarpBytes + 32 * sizeof(ClsRec));
     float4 *stage = reinterpret_cast<float4 *>(smem_c + nwarp * kClsWarpBytes + warp * kStageBytes);
-    const uint8_t *clr = nullptr;
-    if (Tl.clr) {
-        uint4 *dst = reinterpret_cast<uint4 *>(smem_c + nwarp * (kClsWarpBytes + kStageBytes));
-        const uint4 *src = reinterpret_cast<const uint4 *>(Tl.clr);
-        for (int i = threadIdx.x; i < (Tl.clr_bytes >> 4); i += blockDim.x) dst[i] = __ldg(src + i);
-        __syncthreads();
-        clr = reinterpret_cast<const uint8_t *>(dst);
-    }
+    const uint8_t *clr = nullptr;                // the classification reads the fine map (Tl.fclr)
     // bound pieces that depend on the array and the atmosphere only
     const float dzmax = fmaxf(fabsf(Tl.zmax - A.h_obs), fabsf(Tl.zmin - A.h_obs));
     const float co2_min = 2.1f * A.delta_max + 2.6e-3f;
