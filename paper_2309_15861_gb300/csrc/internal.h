@@ -76,7 +76,7 @@ struct DevTel {
 };
 constexpr float kClrQuantum = 0.25f;     // metres per unit of the clearance map
 constexpr int kClrMaxCells = 10240;      // 10 KB of shared memory per CTA
-constexpr int kClrFineMaxCells = 65536;  // 64 KB in global memory
+constexpr int kClrFineMaxCells = 524288; // 512 KB in global memory
 
 struct DevPar {
     float band, inv_bunch;       // 2 pi alpha (1/l1 - 1/l2) [1/m], 1/B
