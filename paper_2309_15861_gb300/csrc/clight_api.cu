@@ -439,8 +439,8 @@ clight_status clight_set_telescopes(clight_ctx *c, const clight_telescope *t, in
     // radius is below its cell's value cannot reach any sphere.  The coarse
     // map (<= kClrMaxCells) is staged in shared memory by the kernels that
     // trace rays (the hit test of most rays ends with one shared-memory
-    // byte); the fine one (<= kClrFineMaxCells) is read through L1 by the
-    // classification, where a smaller cell defers fewer rays.
+    // byte); the fine one (<= kClrFineMaxCells) is read from global memory
+    // (L1/L2) by the classification, where a smaller cell defers fewer rays.
     ClrMap cm = build_clearance(t, n, xmin, xmax, ymin, ymax, kClrMaxCells);
     ClrMap fm = build_clearance(t, n, xmin, xmax, ymin, ymax, kClrFineMaxCells);
     std::vector<uint8_t> &clr = cm.map;

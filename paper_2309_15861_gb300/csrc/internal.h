@@ -69,7 +69,7 @@ struct DevTel {
     float cx0, cy0, inv_cgs, pad4;
     float mx, my, mz, mr;           // mean centre, largest distance of a centre from it (rounded up)
     float cabs;                     // largest |x| + |y| + |z| of a centre
-    // the same map at a finer cell (read through L1 by the classification)
+    // the same map at a finer cell (read from global memory by the classification)
     const uint8_t *fclr;
     int fcnx, fcny;
     float fcx0, fcy0, finv_cgs;

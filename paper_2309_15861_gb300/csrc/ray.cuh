@@ -1137,7 +1137,7 @@ __device__ __forceinline__ bool clear_miss(float xe, float ye, float ze, float d
 }
 
 // Does the clearance map rule out every centre within rs of (x, y)?  FINE:
-// the fine map (global memory, through L1); else the coarse one at clr
+// the fine map (global memory); else the coarse one at clr
 // (shared memory; nullptr: no map).
 template <bool FINE>
 __device__ __forceinline__ bool clr_clear(const DevTel &Tl, const uint8_t *clr, float x, float y, float rs)
