@@ -202,8 +202,10 @@ static cudaError_t exclusive_scan(uint32_t *a, int64_t max_n, const unsigned lon
 // [w*256, (w+1)*256) and walks them in 8 rounds of 32 consecutive keys;
 // __match_any_sync groups equal digits inside a round, a per-warp counter
 // per digit carries ranks across rounds, and a prefix over the warps per
-// digit places each warp after the ones before it.
-__global__ void __launch_bounds__(kSortThreads)
+// digit places each warp after the ones before it.  The tile is first
+// ordered by digit in shared memory, then written out in that order, so each
+// digit's run leaves as consecutive addresses (coalesced stores).
+__global__ void __launch_bounds__(kSortThreads, 3)
 k_radix_scatter(const unsigned long long *__restrict__ kin, const uint32_t *__restrict__ vin,
                 unsigned long long *__restrict__ kout, uint32_t *__restrict__ vout,
                 const unsigned long long *ctr, int64_t capacity, int shift,
@@ -211,11 +213,16 @@ k_radix_scatter(const unsigned long long *__restrict__ kin, const uint32_t *__re
 {
     __shared__ uint32_t wcount[kSortThreads / 32][256];
     __shared__ uint32_t gbase[256];
+    __shared__ uint32_t tdo[256];                 // the tile's first position of each digit
+    __shared__ uint32_t wt[32], tot;
+    __shared__ unsigned long long skey[kTile];
+    __shared__ uint32_t sval[kTile];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t n = valid_hits(ctr, capacity);
     const int64_t nt = live_tiles(n);
     for (int64_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
         const int64_t tile0 = tile * kTile;
+        const int tile_n = (int)min((int64_t)kTile, n - tile0);
         for (int d = lane; d < 256; d += 32) wcount[w][d] = 0;
         gbase[threadIdx.x] = hist[(int64_t)threadIdx.x * nt + tile];
         __syncwarp();
@@ -223,47 +230,61 @@ k_radix_scatter(const unsigned long long *__restrict__ kin, const uint32_t *__re
         uint32_t val[kSortItems];
         uint32_t loc[kSortItems];
         int dig[kSortItems];
-        int64_t wbase = tile0 + (int64_t)w * (kSortItems * 32);
+        const int64_t wbase = tile0 + (int64_t)w * (kSortItems * 32);
 #pragma unroll
         for (int r = 0; r < kSortItems; ++r) {
-            int64_t idx = wbase + r * 32 + lane;
-            bool ok = idx < n;
+            const int64_t idx = wbase + r * 32 + lane;
+            const bool ok = idx < n;
             key[r] = ok ? kin[idx] : 0ull;
             val[r] = ok ? vin[idx] : 0u;
-            int d = ok ? (int)((key[r] >> shift) & 0xFF) : 256;
+            const int d = ok ? (int)((key[r] >> shift) & 0xFF) : 256;
             dig[r] = d;
-            unsigned peers = __match_any_sync(0xffffffffu, d);
-            uint32_t before = ok ? wcount[w][d] : 0;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t before = ok ? wcount[w][d] : 0;
             loc[r] = before + __popc(peers & lane_lt());
             __syncwarp();
-            int leader = __ffs(peers) - 1;
+            const int leader = __ffs(peers) - 1;
             if (ok && lane == leader) wcount[w][d] = before + __popc(peers);
             __syncwarp();
         }
         __syncthreads();
+        uint32_t run = 0;
         {   // exclusive prefix over warps, per digit
-            int d = threadIdx.x;
-            uint32_t run = 0;
+            const int d = threadIdx.x;
 #pragma unroll
             for (int q = 0; q < kSortThreads / 32; ++q) {
-                uint32_t t = wcount[q][d];
+                const uint32_t t = wcount[q][d];
                 wcount[q][d] = run;
                 run += t;
             }
         }
+        // and over digits: where each digit's run starts in the tile
+        tdo[threadIdx.x] = block_exclusive_scan(run, wt, &tot);
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < kSortItems; ++r) {
-            int d = dig[r];
+            const int d = dig[r];
             if (d < 256) {
-                uint32_t pos = gbase[d] + wcount[w][d] + loc[r];
+                const uint32_t p = tdo[d] + wcount[w][d] + loc[r];
+                skey[p] = key[r];
+                sval[p] = val[r];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {
+            const int i = j * kSortThreads + threadIdx.x;
+            if (i < tile_n) {
+                const unsigned long long k = skey[i];
+                const int d = (int)((k >> shift) & 0xFF);
+                const uint32_t pos = gbase[d] + (uint32_t)i - tdo[d];
                 if ((int64_t)pos < n) {          // always true for a consistent histogram
-                    kout[pos] = key[r];
-                    vout[pos] = val[r];
+                    kout[pos] = k;
+                    vout[pos] = sval[i];
                 }
             }
         }
-        __syncthreads();                 // wcount and gbase are reset for the next tile
+        __syncthreads();                 // the shared arrays are reset for the next tile
     }
 }
 
