@@ -58,6 +58,11 @@ NODES_PER_CELL = 3
 SRC_OPS_SKIPPED = 255
 SRC_OPS_RAY = 680
 SRC_OPS_CELL = 8
+# Adjoint: a candidate ray (or hit) recomputes a traced ray -- generation and
+# hit search (OPS8D_TRACED) and ~5 quadrature nodes -- in forward-mode dual
+# numbers carrying the value and one tangent per parameter.
+ADJ_NODES = 5
+ADJ_OPS_PER_UNIT = OPS8D_TRACED + ADJ_NODES * OPS8D_NODE
 SRC_OPS_NODE = 39
 
 
@@ -522,8 +527,21 @@ def main():
     # ---- the adjoint's own kernels
     adjoint = None
     if adj is not None and adj_ms:
-        adjoint = {"ms_per_step": statistics.mean(adj_ms), "hits": nh,
-                   "note": "candidate pass + tangent kernels + fixed-order sum, CUDA events"}
+        info = ctx.last_adjoint()
+        n_par = len(w.atmosphere.c) + 2
+        units = info["candidates"] + info["hits"]
+        work = units * ADJ_OPS_PER_UNIT * (1 + n_par)
+        adjoint = {"ms_per_step": statistics.mean(adj_ms), "hits": info["hits"], "candidates": info["candidates"],
+                   "phases_ms": {"candidate_pass": info["candidate_ms"], "candidate_sort": info["sort_ms"],
+                                 "tangent_kernels": info["tangent_ms"]},
+                   "note": "candidate pass + sort + tangent kernels + fixed-order sum, CUDA events (last call)"}
+        if pipes is not None and info["tangent_ms"] > 0:
+            adjoint["roofline"] = {
+                "bound": "alu", "kernel": "k_adjoint_soft + k_adjoint_hits",
+                "achieved": work / (info["tangent_ms"] * 1e-3) / 1e12, "peak": peak / 1e12,
+                "unit": "Tops/s (FP32 pipe)", "frac": work / (info["tangent_ms"] * 1e-3) / peak,
+                "work": f"{ADJ_OPS_PER_UNIT} ops per candidate ray or hit (a traced ray, {ADJ_NODES} quadrature nodes) "
+                        f"x (1 + {n_par}) for the value and {n_par} tangents; {units} units"}
 
     # ---- angular segment cut: the same step with the cut on
     cut = None

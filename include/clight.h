@@ -418,6 +418,15 @@ clight_status clight_measure_pipes(int device, clight_pipe_rates *out);
  * telescope reduction.  ERR_ARG if ms is NULL or no call has run. */
 clight_status clight_last_timing(clight_ctx *ctx, float ms[2]);
 
+/* The last clight_trace_adjoint call of the context: the candidate rays of
+ * the soft-yield term (rays whose arrival line passes within R + soft_w of a
+ * centre; 0 without d_gyield / d_yield), the hits it was given, and the
+ * device time of its phases from CUDA events on its stream: ms[0] candidate
+ * pass, ms[1] candidate sort, ms[2] tangent kernels and the fixed-order
+ * sums.  Any pointer may be NULL.  ERR_ARG if no adjoint call has completed
+ * on the context. */
+clight_status clight_last_adjoint(clight_ctx *ctx, int64_t *h_candidates, int64_t *h_hits, float ms[3]);
+
 /* Human-readable name of a status code (static string). */
 const char *clight_status_string(clight_status s);
 

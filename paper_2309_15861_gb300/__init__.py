@@ -119,6 +119,7 @@ def lib():
         L.clight_trace_noalloc.argtypes = [P, P, C.c_int64, C.c_int32, P, C.c_int64, P,
                                            C.POINTER(Stats), C.POINTER(C.c_int64), P]
         L.clight_measure_pipes.argtypes = [C.c_int, C.POINTER(PipeRates)]
+        L.clight_last_adjoint.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), P]
         _lib = L
     return _lib
 
@@ -244,6 +245,15 @@ class Context:
                                           _stream_handle(stream))
         _check(code, "clight_trace_adjoint")
         return out
+
+    def last_adjoint(self):
+        """The last trace_adjoint: candidate rays, hits, and device ms of its
+        candidate pass, candidate sort and tangent kernels."""
+        nc, nh = C.c_int64(), C.c_int64()
+        ms = (C.c_float * 3)()
+        _check(lib().clight_last_adjoint(self._h, C.byref(nc), C.byref(nh), ms), "clight_last_adjoint")
+        return {"candidates": nc.value, "hits": nh.value, "candidate_ms": float(ms[0]), "sort_ms": float(ms[1]),
+                "tangent_ms": float(ms[2])}
 
     def autotune(self, d_segs, n_segs, n_sample, n_showers, d_hits, capacity, bunch_max, reps=5, stream=None):
         """Time bunch sizes, launch shapes, work chunks and cell widths on a sample of n_sample

@@ -102,6 +102,10 @@ struct clight_ctx {
     cudaEvent_t ev = nullptr;
     cudaEvent_t t0 = nullptr, t1 = nullptr, t2 = nullptr;   // phase timing
     bool timed = false;
+    // the last clight_trace_adjoint: phase events and counts
+    cudaEvent_t a_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool a_timed = false;
+    int64_t a_cand = 0, a_hits = 0;
     cudaGraphExec_t gexec = nullptr;
     GraphKey gkey{};
     void *noalloc_scratch = nullptr;            // device address of the no-allocation scratch array
@@ -146,6 +150,17 @@ clight_status clight_last_timing(clight_ctx *c, float ms[2])
     return CLIGHT_OK;
 }
 
+clight_status clight_last_adjoint(clight_ctx *c, int64_t *h_candidates, int64_t *h_hits, float ms[3])
+{
+    if (!c || !c->a_timed) return CLIGHT_ERR_ARG;
+    if (h_candidates) *h_candidates = c->a_cand;
+    if (h_hits) *h_hits = c->a_hits;
+    if (ms)
+        for (int i = 0; i < 3; ++i)
+            if (cudaEventElapsedTime(&ms[i], c->a_ev[i], c->a_ev[i + 1]) != cudaSuccess) return CLIGHT_ERR_CUDA;
+    return CLIGHT_OK;
+}
+
 clight_status clight_create(clight_ctx **out, int device)
 {
     if (!out) return CLIGHT_ERR_ARG;
@@ -166,7 +181,9 @@ clight_status clight_create(clight_ctx **out, int device)
         cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreate(&c->t0) != cudaSuccess || cudaEventCreate(&c->t1) != cudaSuccess ||
-        cudaEventCreate(&c->t2) != cudaSuccess) {
+        cudaEventCreate(&c->t2) != cudaSuccess || cudaEventCreate(&c->a_ev[0]) != cudaSuccess ||
+        cudaEventCreate(&c->a_ev[1]) != cudaSuccess || cudaEventCreate(&c->a_ev[2]) != cudaSuccess ||
+        cudaEventCreate(&c->a_ev[3]) != cudaSuccess) {
         clight_destroy(c);
         return CLIGHT_ERR_CUDA;
     }
@@ -201,6 +218,8 @@ void clight_destroy(clight_ctx *c)
     if (c->t0) cudaEventDestroy(c->t0);
     if (c->t1) cudaEventDestroy(c->t1);
     if (c->t2) cudaEventDestroy(c->t2);
+    for (cudaEvent_t e : c->a_ev)
+        if (e) cudaEventDestroy(e);
     delete c;
 }
 
@@ -1073,6 +1092,8 @@ extern "C" clight_status clight_trace_adjoint(clight_ctx *c, const clight_segmen
     P.cut_nx = c->tel.nx; P.cut_ny = c->tel.ny;
     P.cut_gx0 = c->tel.gx0; P.cut_gy0 = c->tel.gy0; P.cut_inv_gs = c->tel.inv_gs;
     CK(cudaMemsetAsync(c->adj_yfix.p, 0, sizeof(unsigned long long) * (size_t)n_groups, s));
+    c->a_timed = false;
+    CK(cudaEventRecord(c->a_ev[0], s));
     // candidate pass: the rays near a telescope, compacted by the forward
     // kernel (grown and repeated if the list overflows), then sorted, so that
     // the adjoint kernels see them in one order on every call
@@ -1102,6 +1123,7 @@ extern "C" clight_status clight_trace_adjoint(clight_ctx *c, const clight_segmen
             if (attempt == 1) return CLIGHT_ERR_LIMIT;
             cap = n_cand + n_cand / 8 + 1024;
         }
+        CK(cudaEventRecord(c->a_ev[1], s));
         const int64_t tiles = std::max<int64_t>(1, (cap + sort_tile_items() - 1) / sort_tile_items());
         if (c->adj_keys_alt.ensure(cap, g) || c->adj_vals.ensure(cap, g) || c->adj_vals_alt.ensure(cap, g) ||
             c->adj_hist.ensure(256 * tiles, g) || c->adj_bsums.ensure(scan_block_sums_needed(256 * tiles), g))
@@ -1111,13 +1133,20 @@ extern "C" clight_status clight_trace_adjoint(clight_ctx *c, const clight_segmen
         CK(radix_sort_pairs(&kin, &vin, &kout, &vout, c->adj_ctr.p, cap, P.seg_bits + P.k_bits, c->adj_hist.p,
                             c->adj_bsums.p, tiles, s));
         cand = kin;
+    } else {
+        CK(cudaEventRecord(c->a_ev[1], s));
     }
+    CK(cudaEventRecord(c->a_ev[2], s));
     CK(launch_adjoint(d_segs, cand, n_cand, d_hits, n_hits, d_gx, d_gy, d_gt, d_gyield, c->adj_yfix.p, d_yield,
                       n_groups, c->atm, c->tel, P, soft_s, soft_w, (float)c->uatm.K, (float)c->uatm.L0,
                       c->adj_partial.p, blocks, c->adj_out.p, s));
+    CK(cudaEventRecord(c->a_ev[3], s));
     double out[10];
     CK(cudaMemcpyAsync(out, c->adj_out.p, sizeof(double) * (size_t)np, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     for (int i = 0; i < c->atm.n_layers + 2; ++i) h_grad[i] = out[i];
+    c->a_cand = n_cand;
+    c->a_hits = n_hits;
+    c->a_timed = true;
     return CLIGHT_OK;
 }

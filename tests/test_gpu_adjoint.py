@@ -153,6 +153,8 @@ def test_adjoint_is_bitwise_reproducible():
     ctx = G.Context(0)
     try:
         ctx.setup(w)
+        with pytest.raises(G.ClightError):                 # no adjoint call yet
+            ctx.last_adjoint()
         hits, counts, sums, st = G.run_workload(ctx, w)
         dev = "cuda"
         d_segs = torch.from_numpy(w.segments.view(np.uint8).reshape(-1)).to(dev)
@@ -174,6 +176,10 @@ def test_adjoint_is_bitwise_reproducible():
         nbc, nbf = O.bunch_counts(w.segments, w.atmosphere, w.params)
         Yr = O.soft_yield(w.segments, nbc, nbf, w.atmosphere, w.telescopes, w.params, s=0.5, W=20.0).ravel()
         np.testing.assert_allclose(outs[0][1], Yr, rtol=1e-4, atol=1e-3)
+        # the last call's counts and phase times
+        info = ctx.last_adjoint()
+        assert info["hits"] == len(hits) and info["candidates"] >= len(hits) // 2 > 0
+        assert min(info["candidate_ms"], info["sort_ms"], info["tangent_ms"]) >= 0.0 and info["tangent_ms"] > 0.0
     finally:
         ctx.close()
 
