@@ -315,17 +315,23 @@ clight_status clight_trace_adjoint(clight_ctx *ctx, const clight_segment *d_segs
  * whose memory budget must not move between events).  The paper has no
  * counterpart; it exists for such callers.
  *
- * It runs the in-place form of clight_trace's kernel (every ray traced in
- * the fused kernel, no deferred-ray queue) and keeps no sort keys: the hit records go straight into d_hits in
+ * It keeps no sort keys: the hit records go straight into d_hits in
  * arbitrary order (not sorted, no photon sums), and d_counts (optional,
  * n_showers * n_tel int64, device) receives the per-(shower, telescope)
- * hit counts.  Its scratch -- counters, ray statistics and one hit counter
- * per group -- is a static array in the library image (131,208 bytes, held
- * on every GPU that loads the library until the process exits).
+ * hit counts.  With the default feature set (spherical, refracting
+ * atmosphere, exact propagator, float-pair precision, no cut, beaming or
+ * dispersion) it runs clight_trace's two passes, 2^24 steps at a time, with
+ * a static queue of 2^22 rays; a chunk whose rays overflow the queue is
+ * traced again by the in-place kernel.  Otherwise it runs the in-place
+ * kernel (every ray traced where it is generated).  Its scratch --
+ * counters, ray statistics, one hit counter per group and a copy of these
+ * taken before each chunk -- and the queue are static arrays in the
+ * library image (262,416 + 33,554,432 bytes, held on every GPU that loads
+ * the library until the process exits).
  *   - n_showers * n_tel above 16384 returns CLIGHT_ERR_LIMIT before any
  *     launch; other errors as clight_trace.
- *   - The first call with a context looks up the array's device address
- *     (with the context's device current) and keeps it in the context.
+ *   - The first call with a context looks up the arrays' device addresses
+ *     (with the context's device current) and keeps them in the context.
  *   - The call reads its counters back to the host and synchronises
  *     `stream`, so it cannot run inside a stream capture: on a capturing
  *     stream it returns CLIGHT_ERR_ARG before doing anything, and the
@@ -335,7 +341,7 @@ clight_status clight_trace_adjoint(clight_ctx *ctx, const clight_segment *d_segs
  *     (different streams or threads) race on it: order them.
  *   - The context must already hold its atmosphere and telescopes (their
  *     tables were allocated by clight_set_*); this call allocates nothing.
- * Synchronises `stream` once. */
+ * Synchronises `stream` once, and once more per chunk of the two passes. */
 clight_status clight_trace_noalloc(clight_ctx *ctx, const clight_segment *d_segs, int64_t n_segs,
                                    int32_t n_showers, clight_hit *d_hits, int64_t hit_capacity,
                                    int64_t *d_counts, clight_stats *h_stats, int64_t *h_n_hits, void *stream);

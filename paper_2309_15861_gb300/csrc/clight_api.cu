@@ -108,7 +108,7 @@ struct clight_ctx {
     int64_t a_cand = 0, a_hits = 0;
     cudaGraphExec_t gexec = nullptr;
     GraphKey gkey{};
-    void *noalloc_scratch = nullptr;            // device address of the no-allocation scratch array
+    void *noalloc_slots[2] = {nullptr, nullptr};  // device addresses of the no-allocation scratch and queue
 };
 
 #define CK(x)                                   \
@@ -613,7 +613,7 @@ bool clight::ctx_view(clight_ctx *c, CtxView *v)
     return true;
 }
 
-void **clight::ctx_noalloc_slot(clight_ctx *c) { return c ? &c->noalloc_scratch : nullptr; }
+void **clight::ctx_noalloc_slot(clight_ctx *c) { return c ? c->noalloc_slots : nullptr; }
 
 // ------------------------------------------------------------------ pipeline
 namespace {

@@ -172,8 +172,9 @@ struct CtxView {
     int device, n_sm, block, ctas_per_sm, precision;
 };
 bool ctx_view(clight_ctx *c, CtxView *v);
-// Per-context slot holding the device address of the no-allocation entry
-// point's static scratch array (looked up on the context's first such call).
+// Per-context slots holding the device addresses of the no-allocation entry
+// point's static arrays, [0] the scratch and [1] the deferred-ray queue
+// (looked up on the context's first such call).
 void **ctx_noalloc_slot(clight_ctx *c);
 
 // kernel launchers (trace_kernels.cu)

@@ -907,7 +907,7 @@ k_classify(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid
 // its step record in global memory (set up again exactly as in the first
 // pass), traced and hit-tested in full.  Ray counts were taken in the first
 // pass.  Persistent grid, each warp taking the next 32 entries from a counter.
-template <bool SPH, bool REFR, int FEAT, class P = df>
+template <bool SPH, bool REFR, int FEAT, class P = df, bool NOALLOC = false>
 __global__ void __launch_bounds__(256, 3)
 k_trace_deferred(const clight_segment *__restrict__ segs, const __grid_constant__ DevAtm A,
                  const __grid_constant__ DevTel Tl, const __grid_constant__ DevPar Pp,
@@ -950,15 +950,15 @@ k_trace_deferred(const clight_segment *__restrict__ segs, const __grid_constant_
             widen_seg(g, qd);
             RayOut<float, double> o;
             trace_ray<float, double, true, SPH, REFR, FEAT>(qd, seg_global, k, active, A, Pp, o);
-            c_hits += hit_test<float, double, true, false>(o, Pp.key_off + seg_local, seg_global, k, g.shower, A,
-                                                           Tl, Pp, O, status_bits, clr);
+            c_hits += hit_test<float, double, true, NOALLOC>(o, Pp.key_off + seg_local, seg_global, k, g.shower, A,
+                                                             Tl, Pp, O, status_bits, clr);
             st = o.status;
             cells = o.cells;
         } else {
             RayOut<float, df> o;
             trace_ray<float, df, true, SPH, REFR, FEAT>(g, seg_global, k, active, A, Pp, o);
-            c_hits += hit_test<float, df, true, false>(o, Pp.key_off + seg_local, seg_global, k, g.shower, A, Tl,
-                                                       Pp, O, status_bits, clr);
+            c_hits += hit_test<float, df, true, NOALLOC>(o, Pp.key_off + seg_local, seg_global, k, g.shower, A, Tl,
+                                                         Pp, O, status_bits, clr);
             st = o.status;
             cells = o.cells;
         }

@@ -131,6 +131,45 @@ def test_noalloc_two_showers_and_capacity_overflow():
         ctx.close()
 
 
+def test_noalloc_queue_overflow_traces_the_chunk_in_place():
+    """The default feature set takes the two passes with a static queue of
+    2^22 rays per chunk of steps.  A dense array (6 m spheres 10 m apart)
+    queues more rays than that: the chunk is traced again by the in-place
+    kernel from the counters saved before it (so its statistics show no
+    queued ray), and hits, counts and ray totals equal clight_trace's, whose
+    queue grows instead."""
+    torch = _torch()
+    w = I.workload_shower_1tev(n=2_000_000, seed=71, workers=I.default_workers())
+    w.telescopes = I.telescope_grid(81, 81, 10.0, z=w.atmosphere.h_obs)
+    ctx = G.Context(0)
+    try:
+        ctx.setup(w)
+        ref_h, ref_c, ref_s, ref_st = G.run_workload(ctx, w)
+        assert ref_st["deferred"] > (1 << 22)
+        n = len(w.segments)
+        segs = torch.from_numpy(w.segments.view(np.uint8).reshape(-1)).cuda()
+        cap = len(ref_h) + 1000
+        hits = torch.empty(cap * 48, dtype=torch.uint8, device="cuda")
+        counts = torch.full((len(w.telescopes),), -1, dtype=torch.int64, device="cuda")
+        code, nh, st = ctx.trace_noalloc(segs, n, 1, hits, cap, counts)
+        assert code == G.OK and nh == len(ref_h)
+        assert st["rays"] == ref_st["rays"] and st["hits"] == ref_st["hits"]
+        assert st["deferred"] == 0 and st["step_skipped"] == 0      # the in-place kernel traced the chunk
+        got = _sorted(hits[: nh * 48].cpu().numpy().view(G.HIT_DTYPE).copy())
+        for f in ("seg", "k", "tel"):
+            np.testing.assert_array_equal(got[f], ref_h[f])
+        np.testing.assert_allclose(got["weight"], ref_h["weight"], rtol=_parity.TOL_W)
+        np.testing.assert_array_equal(counts.cpu().numpy(), ref_c.reshape(-1))
+        # a small call right after takes the two passes again
+        w2 = I.workload_shower_1tev(n=60_000, seed=37)
+        ctx.setup(w2)
+        segs2 = torch.from_numpy(w2.segments.view(np.uint8).reshape(-1)).cuda()
+        code, nh2, st2 = ctx.trace_noalloc(segs2, len(w2.segments), 1, hits, cap)
+        assert code == G.OK and st2["deferred"] > 0
+    finally:
+        ctx.close()
+
+
 def test_noalloc_refuses_stream_capture():
     """The call reads its counters back to the host, which a stream capture
     does not allow: it returns an argument error and leaves the caller's
