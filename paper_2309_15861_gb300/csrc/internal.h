@@ -177,7 +177,7 @@ bool ctx_view(clight_ctx *c, CtxView *v);
 // (looked up on the context's first such call).
 void **ctx_noalloc_slot(clight_ctx *c);
 
-// kernel launchers (trace_kernels.cu)
+// kernel launchers (trace_twopass.cu, trace_inplace.cu, trace_noalloc.cu)
 cudaError_t launch_trace_fused(const clight_segment *segs, int64_t n_segs, const DevAtm &A,
                                const DevTel &T, const DevPar &P, const DevOut &O, int precision,
                                int grid, int block, cudaStream_t s);

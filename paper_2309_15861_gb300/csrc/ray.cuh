@@ -1,4 +1,4 @@
-// ray.cuh -- device code shared by the forward kernels (trace_kernels.cu)
+// ray.cuh -- device code shared by the forward kernels (trace_kernels.cuh)
 // and the tangent-linear adjoint (adjoint_kernels.cu): numerics, Philox,
 // the atmosphere, the segment set-up, one ray, the hit test.
 //
