@@ -568,9 +568,10 @@ constexpr uint32_t kVGated = 1u << 6;            // virtual-step flag: the step'
 // 2 pi |u - 1/2| 2^-23 <= 3.8e-7 of the exact angle: 8.9e-7, rounded up.
 constexpr float kAzErr = 1.0e-6f;
 
-inline int cls_smem_bytes(int block, const DevTel &)
+constexpr int kClsBeamBytes = 32 * 16;         // EXT: each step's fluorescence beam cone (axis, 1 - cos)
+inline int cls_smem_bytes(int block, const DevTel &, bool ext = false)
 {
-    return (block / 32) * (kClsWarpBytes + kStageBytes);
+    return (block / 32) * (kClsWarpBytes + (ext ? kClsBeamBytes : 0) + kStageBytes);
 }
 
 // Per-ray part of the classification of a Cherenkov ray of a gated step:
@@ -667,16 +668,19 @@ __device__ __forceinline__ bool cone_lands_clear(const Seg<float, df> &g, const 
     return bx_hi + rs < Tl.xmin || bx_lo - rs > Tl.xmax || by_hi + rs < Tl.ymin || by_lo - rs > Tl.ymax;
 }
 
-template <bool SPH, bool REFR>
+// EXT: the angular cut, fluorescence beaming and count rule 1 compiled in.
+template <bool SPH, bool REFR, bool EXT = false>
 __global__ void __launch_bounds__(256, 4)
 k_classify(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid_constant__ DevAtm A,
            const __grid_constant__ DevTel Tl, const __grid_constant__ DevPar Pp, const __grid_constant__ DevOut O)
 {
     extern __shared__ __align__(16) unsigned char smem_c[];
+    constexpr int kWB = kClsWarpBytes + (EXT ? kClsBeamBytes : 0);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    ClsRec *rec = reinterpret_cast<ClsRec *>(smem_c + warp * kClsWarpBytes);
-    uint2 *vl = reinterpret_cast<uint2 *>(smem_c + warp * kClsWarpBytes + 32 * sizeof(ClsRec));
-    float4 *stage = reinterpret_cast<float4 *>(smem_c + nwarp * kClsWarpBytes + warp * kStageBytes);
+    ClsRec *rec = reinterpret_cast<ClsRec *>(smem_c + warp * kWB);
+    uint2 *vl = reinterpret_cast<uint2 *>(smem_c + warp * kWB + 32 * sizeof(ClsRec));
+    float4 *bc = reinterpret_cast<float4 *>(smem_c + warp * kWB + kClsWarpBytes);   // EXT only
+    float4 *stage = reinterpret_cast<float4 *>(smem_c + nwarp * kWB + warp * kStageBytes);
     const uint8_t *clr = nullptr;                // the classification reads the fine map (Tl.fclr)
     // bound pieces that depend on the array and the atmosphere only
     const float dzmax = fmaxf(fabsf(Tl.zmax - A.h_obs), fabsf(Tl.zmin - A.h_obs));
@@ -684,7 +688,7 @@ k_classify(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid
     // direction error of a Cherenkov ray from its azimuth: cos c e1 + sin c e2
     // moves by at most kAzErr, scaled by sin theta_c <= sqrt(2 delta_max (1 + delta_max))
     const float de_c = kAzErr * sqrtf(2.0f * A.delta_max * (1.0f + A.delta_max)) * 1.01f;
-    uint32_t c_rays = 0, c_esc = 0, c_under = 0, c_skip = 0, c_guard = 0, c_whole = 0;
+    uint32_t c_rays = 0, c_esc = 0, c_under = 0, c_skip = 0, c_guard = 0, c_whole = 0, c_cut = 0;
     unsigned status_bits = 0;
     WarpQueue dq;                    // the rays left to k_trace_deferred
     // work stealing: a claim is Pp.chunk consecutive groups of 32 steps; the
@@ -730,9 +734,13 @@ k_classify(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid
         bool gated = false, whole = false;
         if (si < n_segs) {
             Seg<float, df> g;
-            load_segment_f<SPH, false, false, false>(s, Pp.seg_base + si, A, Pp, g);
+            load_segment_f<SPH, EXT, false, false>(s, Pp.seg_base + si, A, Pp, g);
             if (g.bad) status_bits |= 1u << g.bad;
             c_guard += g.guarded;
+            if (EXT) {
+                c_cut += g.cut;
+                bc[lane] = make_float4(g.bux, g.buy, g.buz, g.bomc);
+            }
             nc = g.n_c;
             nf = g.n_f;
             if (nc > 0x7fffffffu || nf > 0x7fffffffu - nc) { status_bits |= 1u << CLIGHT_ERR_LIMIT; nc = nf = 0; }
@@ -886,9 +894,18 @@ k_classify(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid
                     R.nc = reinterpret_cast<const uint4 *>(rq)[5].x;
                     kq = R.nc + kk;
                     const float u3 = u01<float>(x.w);
-                    const float cz = 2.0f * u3 - 1.0f;
-                    const float sz = sqrt_approx((1.0f - cz) * (1.0f + cz));
-                    cls = classify_ray<SPH, REFR>(R, ell, sz * cs, sz * sn, cz, kAzErr, A, Tl, clr);
+                    float fx, fy, fz;
+                    const float4 b = EXT ? bc[l] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (EXT && b.w > 0.0f) {
+                        // beamed: the full trace's cone direction, from the same azimuth
+                        cone_direction<float>(b.x, b.y, b.z, u3 * b.w, sn, cs, fx, fy, fz);
+                    } else {
+                        fz = 2.0f * u3 - 1.0f;
+                        const float sz = sqrt_approx((1.0f - fz) * (1.0f + fz));
+                        fx = sz * cs;
+                        fy = sz * sn;
+                    }
+                    cls = classify_ray<SPH, REFR>(R, ell, fx, fy, fz, kAzErr, A, Tl, clr);
                 }
                 c_esc += cls == 1;
                 c_under += cls == 2;
@@ -899,7 +916,7 @@ k_classify(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid
         __syncwarp();
     }
     dq.finish(O, lane, status_bits);
-    const uint32_t vals[ST_N] = {c_rays, c_esc, c_under, 0u, c_skip, 0u, c_guard, 0u, 0u, 0u, c_skip, 0u, c_whole};
+    const uint32_t vals[ST_N] = {c_rays, c_esc, c_under, 0u, c_skip, 0u, c_guard, 0u, 0u, c_cut, c_skip, 0u, c_whole};
     flush_stats(vals, status_bits, O, lane);
 }
 

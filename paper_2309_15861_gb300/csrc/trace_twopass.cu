@@ -13,11 +13,11 @@ static void launch_deferred_pair(const clight_segment *segs, int64_t n_segs, con
     constexpr bool EXT = (FEAT & FEAT_EXT) != 0;
     // the queue's fill and work counters
     cudaMemsetAsync(O.ctr + CTR_DEFER, 0, 2 * sizeof(unsigned long long), s);
-    if constexpr ((FEAT & (FEAT_EXT | FEAT_DISP)) == 0) {
-        // the default feature set: the classification kernel
-        const int smem = cls_smem_bytes(block, T);
-        cudaFuncSetAttribute(k_classify<SPH, REFR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k_classify<SPH, REFR><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
+    if constexpr ((FEAT & FEAT_DISP) == 0) {
+        // every feature set but dispersion: the classification kernel
+        const int smem = cls_smem_bytes(block, T, EXT);
+        cudaFuncSetAttribute(k_classify<SPH, REFR, EXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_classify<SPH, REFR, EXT><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
     } else {
         k_trace_fused<df, SPH, REFR, false, false, FEAT, true>
             <<<grid, block, fused_smem_bytes_f(block, T, EXT, true), s>>>(segs, n_segs, A, T, Pp, O);
