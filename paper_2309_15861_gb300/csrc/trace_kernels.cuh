@@ -161,6 +161,32 @@ struct WarpQueue {
     }
 };
 
+// Dispersion, first pass: a step's Cherenkov cone at the middle of its
+// wavelength band (sine st, 1 - cos kap), the spread dth of the cone angle
+// over the band (a bound on any photon's angle to that cone, widened) and
+// the band's largest g(lambda).  (db, eps) come in the set-up's sin_tc and
+// kappa.  A step without light in the band keeps st = kap = dth = 0, gmx = 1.
+__device__ __forceinline__ void disp_band_cone(const DevAtm &A, const DevPar &Pp, const Seg<float, df> &g, float &st,
+                                               float &kap, float &dth, float &gmx)
+{
+    st = 0.0f; kap = 0.0f; dth = 0.0f; gmx = 1.0f;
+    float ulo, uhi;
+    if (g.n_c > 0 && disp_band<float>(A, Pp, g.sin_tc, g.kappa, ulo, uhi)) {
+        auto cone = [&](float u, float &s_, float &k_) {
+            const float g1 = fmaxf(g.sin_tc * disp_gu<float>(A, u) - g.kappa, 0.0f);
+            const float ib = 1.0f / (1.0f + g1);
+            s_ = sqrtf(g1 * (2.0f + g1)) * ib;
+            k_ = g1 * ib;
+        };
+        float s_lo, k_lo, s_hi, k_hi;
+        cone(0.5f * (ulo + uhi), st, kap);
+        cone(ulo, s_lo, k_lo);
+        cone(uhi, s_hi, k_hi);
+        dth = (asinf(fminf(s_hi, 1.0f)) - asinf(s_lo)) * 1.01f + 1.0e-6f;
+        gmx = disp_gu<float>(A, uhi) * 1.000001f;
+    }
+}
+
 // First pass of the deferred path: ray k of the step in record l, its
 // direction and emission point in binary32 only, and what the full trace
 // would conclude when that is already certain.  Returns 1 (escapes: points
@@ -365,21 +391,8 @@ k_trace_fused(const clight_segment *__restrict__ segs, int64_t n_segs, const __g
             if (DEFER && (FEAT & FEAT_DISP)) {
                 // (db, eps) -> the cone at the middle of the band, the spread
                 // of the cone angle over the band, the band's largest g
-                float ulo, uhi, st = 0.0f, kap = 0.0f, dth = 0.0f, gmx = 1.0f;
-                if (g.n_c > 0 && disp_band<float>(A, Pp, g.sin_tc, g.kappa, ulo, uhi)) {
-                    auto cone = [&](float u, float &s_, float &k_) {
-                        const float g1 = fmaxf(g.sin_tc * disp_gu<float>(A, u) - g.kappa, 0.0f);
-                        const float ib = 1.0f / (1.0f + g1);
-                        s_ = sqrtf(g1 * (2.0f + g1)) * ib;
-                        k_ = g1 * ib;
-                    };
-                    float s_lo, k_lo, s_hi, k_hi;
-                    cone(0.5f * (ulo + uhi), st, kap);
-                    cone(ulo, s_lo, k_lo);
-                    cone(uhi, s_hi, k_hi);
-                    dth = (asinf(fminf(s_hi, 1.0f)) - asinf(s_lo)) * 1.01f + 1.0e-6f;
-                    gmx = disp_gu<float>(A, uhi) * 1.000001f;
-                }
+                float st, kap, dth, gmx;
+                disp_band_cone(A, Pp, g, st, kap, dth, gmx);
                 S[F_SIN * 32 + pos] = st; S[F_KAP * 32 + pos] = kap;
                 S[F_DTH * 32 + pos] = dth; S[F_GMX * 32 + pos] = gmx;
             }
@@ -556,7 +569,9 @@ struct alignas(16) ClsRec {
     float b1x, b1y, b1z, rsb;   // sin(theta_c) M_Rod x, search radius without the refraction term
     float b2x, b2y, b2z, cB;    // sin(theta_c) M_Rod y, refraction term per metre of height
     uint32_t nc;                // Cherenkov bunches
-    float derr, pad1, pad2;     // bound on a Cherenkov ray's direction error (rad)
+    float derr;                 // bound on a Cherenkov ray's direction error (rad)
+    float gl;                   // largest g(lambda) of its refractivity (dispersion; else 1)
+    float pad;
 };
 static_assert(sizeof(ClsRec) == 96, "ClsRec layout");
 constexpr int kClsVmax = 64;                     // virtual steps per warp: 32 Cherenkov + 32 fluorescence
@@ -597,29 +612,34 @@ __device__ __forceinline__ int classify_cherenkov_gated(const ClsRec &R, float e
 // The per-ray test (ray direction d, emission at l along the step), as in
 // skip_ray: for fluorescence photons and the Cherenkov photons of steps
 // without per-step bounds.  derr: a bound on the angle between (dx, dy, dz)
-// and the direction the full trace forms (the azimuth's error here).
-template <bool SPH, bool REFR>
+// and the direction the full trace forms (the azimuth's error here; under
+// dispersion (DISP) the cone-angle spread over the band as well, which also
+// widens the escape, steepness and landing-angle tests, as in skip_ray).  gl:
+// the largest g(lambda) of the photon's refractivity (1 without dispersion).
+template <bool SPH, bool REFR, bool DISP = false>
 __device__ __forceinline__ int classify_ray(const ClsRec &R, float ell, float dx, float dy, float dz, float derr,
-                                            const DevAtm &A, const DevTel &Tl, const uint8_t *clr)
+                                            float gl, const DevAtm &A, const DevTel &Tl, const uint8_t *clr)
 {
     const float xe = R.x0 + ell * R.dx, ye = R.y0 + ell * R.dy, ze = R.z0 + ell * R.dz;
     const float Rz = ze + A.R_E;
     const float out = SPH ? dx * xe + dy * ye + dz * Rz : dz;
-    const float mo = SPH ? 1.0e-3f * Rz : 1.0e-6f;
+    const float dm = DISP ? derr : 0.0f;
+    const float mo = SPH ? (1.0e-3f + dm) * Rz : 1.0e-6f + dm;
     if (out > mo) return 1;
     if (!(out < -mo)) return 0;
     const float he = R.h_mid + (ell - 0.5f * R.L) * R.hd;
     if (he < A.h_obs - 0.1f) return 2;
-    if (!(he > A.h_obs + 0.1f) || !(dz < -0.05f)) return 0;
+    if (!(he > A.h_obs + 0.1f) || !(dz < -0.05f - dm)) return 0;
     float cos_obs = 0.0f;
     if (SPH) {
         const float c1 = dy * Rz - dz * ye, c2 = dz * xe - dx * Rz, c3 = dx * ye - dy * xe;
-        const float so = sqrt_approx(c1 * c1 + c2 * c2 + c3 * c3) * A.inv_r_obs;
+        float so = sqrt_approx(c1 * c1 + c2 * c2 + c3 * c3) * A.inv_r_obs;
+        if (DISP) so += dm * (1.0f + (he - A.h_obs) * A.inv_r_obs) * 1.001f;
         const float co2 = 1.0f - so * so;
-        if (!(so < 1.0f) || !(co2 > 2.1f * A.delta_max + 2.6e-3f)) return 0;
+        if (!(so < 1.0f) || !(co2 > 2.1f * A.delta_max * gl + 2.6e-3f)) return 0;
         cos_obs = sqrt_approx(co2);
     }
-    return clear_miss<true>(xe, ye, ze, dx, dy, dz, he, cos_obs, 1.0f, A, Tl, clr, SPH, REFR, 0.0f, derr) ? 6 : 0;
+    return clear_miss<true>(xe, ye, ze, dx, dy, dz, he, cos_obs, gl, A, Tl, clr, SPH, REFR, 0.0f, derr) ? 6 : 0;
 }
 
 // Does every Cherenkov photon of a gated step land clear of the array?
@@ -668,8 +688,11 @@ __device__ __forceinline__ bool cone_lands_clear(const Seg<float, df> &g, const 
     return bx_hi + rs < Tl.xmin || bx_lo - rs > Tl.xmax || by_hi + rs < Tl.ymin || by_lo - rs > Tl.ymax;
 }
 
-// EXT: the angular cut, fluorescence beaming and count rule 1 compiled in.
-template <bool SPH, bool REFR, bool EXT = false>
+// EXT: the angular cut, fluorescence beaming and count rule 1 compiled in;
+// DISP: dispersion (a Cherenkov ray's direction from the cone at the middle
+// of its step's band, with the band's spread as a direction error and its
+// largest g(lambda) in the refraction bounds).
+template <bool SPH, bool REFR, bool EXT = false, bool DISP = false>
 __global__ void __launch_bounds__(256, 4)
 k_classify(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid_constant__ DevAtm A,
            const __grid_constant__ DevTel Tl, const __grid_constant__ DevPar Pp, const __grid_constant__ DevOut O)
@@ -734,7 +757,7 @@ k_classify(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid
         bool gated = false, whole = false;
         if (si < n_segs) {
             Seg<float, df> g;
-            load_segment_f<SPH, EXT, false, false>(s, Pp.seg_base + si, A, Pp, g);
+            load_segment_f<SPH, EXT, DISP, false>(s, Pp.seg_base + si, A, Pp, g);
             if (g.bad) status_bits |= 1u << g.bad;
             c_guard += g.guarded;
             if (EXT) {
@@ -744,7 +767,13 @@ k_classify(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid
             nc = g.n_c;
             nf = g.n_f;
             if (nc > 0x7fffffffu || nf > 0x7fffffffu - nc) { status_bits |= 1u << CLIGHT_ERR_LIMIT; nc = nf = 0; }
-            const float ct = 1.0f - g.kappa, st = g.sin_tc;
+            float ct = 1.0f - g.kappa, st = g.sin_tc, dth = 0.0f, glc = 1.0f;
+            if (DISP && A.disp) {
+                float kap;
+                disp_band_cone(A, Pp, g, st, kap, dth, glc);
+                ct = 1.0f - kap;
+            }
+            r.gl = glc;
             r.x0 = g.x0.hi; r.y0 = g.y0.hi; r.z0 = g.z0.hi; r.L = g.L;
             r.dx = g.dx; r.dy = g.dy; r.dz = g.dz; r.h_mid = g.h_mid;
             r.ax = ct * g.dx; r.ay = ct * g.dy; r.az = ct * g.dz;
@@ -774,7 +803,7 @@ k_classify(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid
                 // a ray's direction error against the full trace's: the
                 // azimuth's, and the cone's from a binary32 beta n - 1 (error
                 // gerr moves sin^2 theta_c by ~2 gerr and cos theta_c by gerr)
-                const float dstep = de_c + 1.1f * g.gerr * (rcp_approx(st) + 1.0f);
+                const float dstep = de_c + 1.1f * g.gerr * (rcp_approx(st) + 1.0f) + dth;
                 r.derr = dstep;
                 // -d_gamma,z >= cos(zeta_d + theta_c)
                 const float dzlo = sdz * ct - szd * st - 4.0e-6f - dstep;
@@ -786,14 +815,14 @@ k_classify(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid
                     const float se = sps * ct + cps * st + (r.L + 1.0f) * ir0 + 4.0e-6f + dstep;
                     const float so = (r0 + r.L) * se * A.inv_r_obs * 1.000001f;
                     const float co2 = 1.0f - so * so;
-                    ok = ok && csum > 0.0f && so < 1.0f && co2 > co2_min;
+                    ok = ok && csum > 0.0f && so < 1.0f && co2 > (DISP ? 2.1f * A.delta_max * glc + 2.6e-3f : co2_min);
                     cobs_lo = ok ? sqrt_approx(co2) * 0.999999f : 0.0f;
                 }
                 const float mu = fminf(cobs_lo, dzlo) - 1.0e-3f;
                 ok = ok && mu > 0.05f;
                 if (ok) {
                     const float im = rcp_approx(mu) * 1.000001f;
-                    const float sd = REFR ? 1.25f * 1.000001f * sqrt_approx(1.0f - mu * mu) * A.delta_max : 0.0f;
+                    const float sd = REFR ? 1.25f * 1.000001f * sqrt_approx(1.0f - mu * mu) * A.delta_max * glc : 0.0f;
                     const float czb = dzlo - sd * im - 1.0e-5f;
                     ok = czb > 0.05f;
                     if (ok) {
@@ -888,8 +917,9 @@ k_classify(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid
                     const float dgz = R.az + (cs * R.b1z + sn * R.b2z);
                     cls = (v.y & kVGated)
                               ? classify_cherenkov_gated<SPH>(R, ell, dgx, dgy, dgz, A, Tl, clr)
-                              : classify_ray<SPH, REFR>(R, ell, dgx, dgy, dgz, reinterpret_cast<const float4 *>(rq)[5].y,
-                                                        A, Tl, clr);
+                              : classify_ray<SPH, REFR, DISP>(R, ell, dgx, dgy, dgz,
+                                                              reinterpret_cast<const float4 *>(rq)[5].y,
+                                                              reinterpret_cast<const float4 *>(rq)[5].z, A, Tl, clr);
                 } else {
                     R.nc = reinterpret_cast<const uint4 *>(rq)[5].x;
                     kq = R.nc + kk;
@@ -905,7 +935,11 @@ k_classify(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid
                         fx = sz * cs;
                         fy = sz * sn;
                     }
-                    cls = classify_ray<SPH, REFR>(R, ell, fx, fy, fz, kAzErr, A, Tl, clr);
+                    // dispersion: this photon's refractivity is delta(h) g(lambda)
+                    const float glf = (DISP && A.disp)
+                                          ? disp_gu<float>(A, rcp_approx(Pp.fl1 + u01<float>(x.x) * Pp.fdl)) * 1.000001f
+                                          : 1.0f;
+                    cls = classify_ray<SPH, REFR, DISP>(R, ell, fx, fy, fz, kAzErr, glf, A, Tl, clr);
                 }
                 c_esc += cls == 1;
                 c_under += cls == 2;

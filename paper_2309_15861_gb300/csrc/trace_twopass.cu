@@ -13,14 +13,12 @@ static void launch_deferred_pair(const clight_segment *segs, int64_t n_segs, con
     constexpr bool EXT = (FEAT & FEAT_EXT) != 0;
     // the queue's fill and work counters
     cudaMemsetAsync(O.ctr + CTR_DEFER, 0, 2 * sizeof(unsigned long long), s);
-    if constexpr ((FEAT & FEAT_DISP) == 0) {
-        // every feature set but dispersion: the classification kernel
+    {
+        // the classification kernel, with the features the call uses
+        constexpr bool DISP = (FEAT & FEAT_DISP) != 0;
         const int smem = cls_smem_bytes(block, T, EXT);
-        cudaFuncSetAttribute(k_classify<SPH, REFR, EXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k_classify<SPH, REFR, EXT><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
-    } else {
-        k_trace_fused<df, SPH, REFR, false, false, FEAT, true>
-            <<<grid, block, fused_smem_bytes_f(block, T, EXT, true), s>>>(segs, n_segs, A, T, Pp, O);
+        cudaFuncSetAttribute(k_classify<SPH, REFR, EXT, DISP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_classify<SPH, REFR, EXT, DISP><<<grid, block, smem, s>>>(segs, n_segs, A, T, Pp, O);
     }
     // the second pass as many CTAs as are resident at once (its own
     // register and shared-memory limits)
