@@ -275,9 +275,11 @@ __device__ __forceinline__ int skip_ray(const float *S, int l, uint32_t k, uint3
     return clear_miss(xe, ye, ze, dx, dy, dz, he, cos_obs, gl, A, Tl, clr, SPH, REFR, 0.0f, derr) ? 6 : 0;
 }
 
-// DEFER (binary32 pairs, no dispersion): each ray only goes through
-// skip_ray; the rays it cannot leave out are queued in O.defer and traced by
-// k_trace_deferred in full warps, so that no warp integrates for one lane.
+// DEFER (binary32 pairs): each ray only goes through skip_ray; the rays it
+// cannot leave out are queued in O.defer and traced by k_trace_deferred in
+// full warps, so that no warp integrates for one lane.  No launcher uses
+// this form any more (k_classify is the first pass for every feature set);
+// the in-place forms (DEFER = false) are unchanged by it.
 // A ray that finds the queue full sets the kBitDeferFull status bit (the
 // host then runs the call again).  Without the in-place path the kernel
 // fits 4 CTAs of 256 threads per SM.

@@ -1,7 +1,6 @@
 // trace_twopass.cu -- launches of the two-pass forward path: the first
-// pass (k_classify for the default feature set, k_trace_fused<..., DEFER>
-// with the angular cut, beaming or dispersion) and k_trace_deferred for the
-// rays it queued.
+// pass (k_classify, with the features the call uses) and k_trace_deferred
+// for the rays it queued.
 #include "trace_kernels.cuh"
 
 namespace clight {
