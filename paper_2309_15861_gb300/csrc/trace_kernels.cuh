@@ -803,9 +803,12 @@ k_classify(const clight_segment *__restrict__ segs, int64_t n_segs, const __grid
             r.rsb = 0.0f; r.cB = 0.0f; r.derr = 0.0f;
             if (nc > 0) {
                 // a ray's direction error against the full trace's: the
-                // azimuth's, and the cone's from a binary32 beta n - 1 (error
-                // gerr moves sin^2 theta_c by ~2 gerr and cos theta_c by gerr)
-                const float dstep = de_c + 1.1f * g.gerr * (rcp_approx(st) + 1.0f) + dth;
+                // azimuth's, and the cone's from a binary32 beta n - 1 g' (the
+                // exact one within gerr of it).  theta_c ~ sqrt(2 g) is concave,
+                // so the largest change is toward g' - gerr: sqrt(2 g') -
+                // sqrt(2 (g' - gerr)) <= 2 gerr / theta_c'; cos theta_c moves by
+                // at most gerr.  Margins 1.1.
+                const float dstep = de_c + g.gerr * (2.2f * rcp_approx(st) + 1.1f) + dth;
                 r.derr = dstep;
                 // -d_gamma,z >= cos(zeta_d + theta_c)
                 const float dzlo = sdz * ct - szd * st - 4.0e-6f - dstep;
