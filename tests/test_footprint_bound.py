@@ -95,3 +95,31 @@ def test_box_of_the_step_ends_holds_every_crossing():
             tol = 1e-9 * (1 + np.abs(X).max() + np.abs(Y).max())
             assert X.min() >= box[0] - tol and X.max() <= box[1] + tol
             assert Y.min() >= box[2] - tol and Y.max() <= box[3] + tol
+
+
+def test_binary32_roots_with_their_margin_contain_the_exact_roots():
+    """The kernel forms the roots in binary32 with approximate square roots and
+    reciprocals (within a few ulp) and widens them by
+    m = (sqrt(4e-7 (B1^2 + |A2 C0|)) + 4e-7 (|B1| + sqrt(disc))) / A2 + 1e-6.
+    Emulated here in binary32 with every approximate result perturbed by up
+    to 4 ulp: the widened interval holds the binary64 roots."""
+    f = np.float32
+    rng = np.random.default_rng(11)
+    for d, th in _cases(rng, 4000):
+        e1, e2 = _frame(d)
+        ct, st = np.cos(th), np.sin(th)
+        d32, e132, e232 = d.astype(f), e1.astype(f), e2.astype(f)
+        ct32, st32 = f(ct), f(st)
+        b0, b1, b2 = -ct32 * d32[2], -st32 * e132[2], -st32 * e232[2]
+        A2 = b0 * b0 - (b1 * b1 + b2 * b2)
+        iA = f(1.0) / A2 * f(1.0 + rng.uniform(-4, 4) * 2.0 ** -23)
+        for k in (0, 1):
+            a0, a1, a2 = ct32 * d32[k], st32 * e132[k], st32 * e232[k]
+            B1 = a0 * b0 - (a1 * b1 + a2 * b2)
+            C0 = a0 * a0 - (a1 * a1 + a2 * a2)
+            disc = max(B1 * B1 - A2 * C0, f(0.0))
+            sq = np.sqrt(disc) * f(1.0 + rng.uniform(-4, 4) * 2.0 ** -23)
+            m = (np.sqrt(f(4.0e-7) * (B1 * B1 + abs(A2 * C0))) + f(4.0e-7) * (abs(B1) + sq)) * iA + f(1.0e-6)
+            lo, hi = (B1 - sq) * iA - m, (B1 + sq) * iA + m
+            lo64, hi64 = _roots(ct * d[k], st * e1[k], st * e2[k], -ct * d[2], -st * e1[2], -st * e2[2])
+            assert lo <= lo64 and hi >= hi64, (lo, lo64, hi, hi64)
