@@ -156,6 +156,31 @@ def recorded_traffic(workload, n_units):
     return rec["bytes_per_step"] * n_units if "bytes_per_step" in rec else None
 
 
+def traffic_record(workload):
+    """The traffic record as written, whatever the sources now hold:
+    {"bytes_per_step", "current"} (current = every source hash still
+    matches), or None without a record."""
+    path = os.path.join(ROOT, "profiles", f"tracing_{workload}_traffic.txt")
+    try:
+        lines = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    except OSError:
+        return None
+    rec, current = {}, True
+    for f in lines:
+        if f[0] == "sha256":
+            try:
+                src = os.path.join(ROOT, "paper_2309_15861_gb300", "csrc", f[1])
+                current &= hashlib.sha256(open(src, "rb").read()).hexdigest() == f[2]
+            except OSError:
+                current = False
+        else:
+            rec[f[0]] = float(f[1])
+    if "bytes_per_step" not in rec:
+        return None
+    return {"bytes_per_step": rec["bytes_per_step"], "current": current,
+            "file": f"profiles/tracing_{workload}_traffic.txt"}
+
+
 # ------------------------------------------------------------------ oracle legs
 def _oracle_blocks(w, budget_s, block, seed, threads, keep_hits=False):
     """The FP64 oracle on contiguous blocks of `block` steps drawn at random
@@ -505,6 +530,7 @@ def main():
         peak = n_sm * 128 * 2070e6
         peak_basis = f"nominal: {n_sm} SMs x 128 FP32 lanes x 2070 MHz"
     traffic = recorded_traffic(w.name, n) if args.precision == 0 else None
+    trec = traffic_record(w.name) if args.precision == 0 else None
     roof = {"bound": "alu", "achieved": ops8 / k_s / 1e12, "peak": peak / 1e12, "unit": "Tops/s (FP32 pipe)",
             "frac": ops8 / k_s / peak, "traffic": traffic,
             "kernel": "k_classify + k_trace_deferred" if deferred else "k_trace_fused",
@@ -520,6 +546,10 @@ def main():
                                                 "drawn) credited nothing"},
             "hbm": {"achieved_gbs": (n * 64 + nh * 48) / k_s / 1e9,
                     "note": "algorithmic bytes: the 64-byte steps read once and the 48-byte hits written"}}
+    if trec is not None:
+        # the last capture's figure; `traffic` above is null unless it was
+        # taken from the sources that now run
+        roof["traffic_record"] = trec
     if pipes is not None and pipes["mufu_ex2_per_s"] > 0:
         roof["pipes_measured"] = {k: pipes[k] for k in ("ffma_per_s", "mufu_ex2_per_s", "dfma_per_s", "imad_per_s",
                                                         "lop3_per_s", "ffma_mhz")}

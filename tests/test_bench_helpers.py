@@ -49,7 +49,10 @@ def test_recorded_traffic_is_reported_only_for_the_sources_it_was_taken_from(tmp
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.recorded_traffic("wl", 2000) == pytest.approx(170000.0)   # scaled by the steps
     assert bench.recorded_traffic("other", 2000) is None                   # no record
+    assert bench.traffic_record("wl") == {"bytes_per_step": 85.0, "current": True,
+                                          "file": "profiles/tracing_wl_traffic.txt"}
     f.write_bytes(b"kernel v2\n")                                           # a kernel changed
     assert bench.recorded_traffic("wl", 2000) is None
+    assert bench.traffic_record("wl")["current"] is False                   # the figure, marked stale
     os.remove(f)                                                            # or is gone
     assert bench.recorded_traffic("wl", 2000) is None
