@@ -48,6 +48,35 @@ def test_status_strings_and_no_device_on_cpu():
     if not torch.cuda.is_available():
         h = ctypes.c_void_p()
         assert lib.clight_create(ctypes.byref(h), 0) == G.ERR_NO_DEVICE
+        rates = G.PipeRates()
+        assert lib.clight_measure_pipes(0, ctypes.byref(rates)) == G.ERR_NO_DEVICE
+
+
+def test_entry_points_refuse_what_they_cannot_use_before_any_device_call():
+    """Argument checks on the host: a NULL context or output is refused with
+    CLIGHT_ERR_ARG before any CUDA call (so this runs without a GPU)."""
+    lib = G.lib()
+    n64 = ctypes.c_int64()
+    st = G.Stats()
+    assert lib.clight_measure_pipes(0, None) == G.ERR_ARG
+    assert lib.clight_trace(None, None, 0, 1, None, 0, None, None, ctypes.byref(st), ctypes.byref(n64), None) == G.ERR_ARG
+    assert lib.clight_trace_fp64(None, None, 0, 1, None, 0, None, None, ctypes.byref(st), ctypes.byref(n64),
+                                 None) == G.ERR_ARG
+    assert lib.clight_trace_host(None, None, 0, 1, None, 0, None, None, ctypes.byref(st), ctypes.byref(n64),
+                                 None) == G.ERR_ARG
+    assert lib.clight_trace_noalloc(None, None, 0, 1, None, 0, None, ctypes.byref(st), ctypes.byref(n64),
+                                    None) == G.ERR_ARG
+    grad = (ctypes.c_double * 10)()
+    assert lib.clight_trace_adjoint(None, None, 0, 1, None, 0, None, None, None, None, 0.5, 20.0, None, grad,
+                                    None) == G.ERR_ARG
+    t = G.Tune()
+    assert lib.clight_autotune(None, None, 1, 1, 1, None, 0, 5.0, 1, ctypes.byref(t), None) == G.ERR_ARG
+    ms = (ctypes.c_float * 3)()
+    assert lib.clight_last_timing(None, ms) == G.ERR_ARG
+    assert lib.clight_last_adjoint(None, None, None, ms) == G.ERR_ARG
+    assert lib.clight_set_atmosphere(None, None) == G.ERR_ARG
+    assert lib.clight_set_telescopes(None, None, 0) == G.ERR_ARG
+    assert lib.clight_set_params(None, None) == G.ERR_ARG
 
 
 def _c_layouts(tmp_path):
